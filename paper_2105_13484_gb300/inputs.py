@@ -1,0 +1,113 @@
+"""Seeded synthetic workloads shaped like the paper's test cases.
+
+Input generation only: meshes (from ``mesh.py``), physical parameters and
+initial states.  Nothing here performs any step of the time-stepping method;
+both the CUDA path and the CPU oracle are fed from these generators.
+
+Workloads (the paper's MPAS meshes and data are not available, so these
+stand in for them):
+
+* ``channel_10km``  16 x 32 hexagonal channel, 10 km spacing, 10 layers x 100 m,
+  flat 1000 m bottom, f-plane f = 1.2e-4, temperature-only linear EOS,
+  tanh temperature front across y plus a 1 K sinusoidal perturbation with a
+  seeded phase (the baroclinic-eddies setup of Sec. 5.1 in miniature).
+  SSPRK2-SE, dt = 300 s, M = 20, 10 steps.
+* ``channel_1km``   160 x 578 cells at 1 km (160 km x 500 km, 92,480 cells),
+  20 layers x 50 m, beta plane, same front.  SSPRK3-SE, dt = 60 s, M = 30.
+* ``sphere_l7``     icosahedral geodesic sphere (163,842 cells), 60 z-star
+  layers, seeded bathymetry, ~30 % land, T and S, wind stress.
+  SSPRK3-SE, dt = 600 s, M = 40.
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+
+from . import mesh as _mesh
+
+PHYS = dict(g=9.80616, rho0=1000.0, eos_rho_ref=1000.0, eos_alpha=0.2, eos_beta=0.8,
+            eos_T_ref=10.0, eos_S_ref=35.0)
+
+
+def channel_state(m, L, *, seed=0, width=40e3, dT=5.0, amp=1.0, perturb=False,
+                  nTracers=1):
+    """Initial (u [E,L], h [C,L], tracers [nT,C,L]) on a planar channel mesh.
+
+    Temperature: linear from 20 C at the surface to 10 C at the bottom, a tanh
+    front of height dT across the channel middle and an amp-K perturbation
+    cos(2 pi m x / Lx + phase) (m in {1, 2}, seeded phase) confined to the
+    front.  With ``perturb`` a smooth seeded velocity field and SSH
+    perturbation are added so that every term of the tendencies is active.
+    """
+    rng = np.random.default_rng(seed)
+    xc, yc = m.xCell[:, 0], m.xCell[:, 1]
+    Lx = _channel_lx(m)
+    y0 = 0.5 * (yc.min() + yc.max())
+    mode = int(rng.integers(1, 3))
+    phase = float(rng.uniform(0, 2 * np.pi))
+    s = np.full(L, 1.0 / L)
+    zeta = np.zeros(m.nCells)
+    if perturb:
+        kx = 2 * np.pi / Lx
+        zeta = 0.2 * np.cos(kx * xc + rng.uniform(0, 6.3)) * np.exp(-((yc - y0) / (2 * width)) ** 2)
+    H = m.bottomDepth
+    h = (H + zeta)[:, None] * s[None, :]
+    # layer mid depths as fractions of the column (at rest)
+    zfrac = -(np.cumsum(s) - 0.5 * s)
+    eta = (yc - y0) / width
+    T = (20.0 + 10.0 * zfrac[None, :]
+         - 0.5 * dT * np.tanh(eta)[:, None]
+         + amp * (np.cos(mode * 2 * np.pi * xc / Lx + phase) / np.cosh(eta) ** 2)[:, None])
+    tr = [T]
+    if nTracers >= 2:
+        S = 35.0 + 0.5 * np.tanh(eta)[:, None] - 0.2 * zfrac[None, :] + 0.0 * T[:, :1]
+        tr.append(S)
+    tr = np.stack(tr)
+    u = np.zeros((m.nEdges, L))
+    if perturb:
+        xe, ye = m.xEdge[:, 0], m.xEdge[:, 1]
+        n = m.normalEdge
+        ky = np.pi / (yc.max() - yc.min())
+        prof = np.exp(zfrac)  # decays with depth
+        a, b = rng.uniform(0, 6.3, 2)
+        U = 0.3 * np.sin(2 * np.pi * xe / Lx + a) * np.sin(ky * (ye - yc.min()))
+        Vv = 0.3 * np.cos(4 * np.pi * xe / Lx + b) * np.sin(ky * (ye - yc.min()))
+        un = U * n[:, 0] + Vv * n[:, 1]
+        u = un[:, None] * prof[None, :] + 0.05 * np.sin(3 * ky * ye)[:, None] * (s[None, :] - s.mean())
+    return u, h, tr
+
+
+def _channel_lx(m):
+    dc = float(np.median(m.dcEdge))
+    return float(round((m.xCell[:, 0].max() - m.xCell[:, 0].min()) / dc + 0.5)) * dc
+
+
+def channel_case(nx, ny, dc, L, *, depth=1000.0, f0=1.2e-4, beta=0.0, seed=0, perturb=False,
+                 nTracers=1, **params):
+    """(mesh, L, params, (u, h, tr)) for a planar channel."""
+    m = _mesh.planar_hex(nx, ny, dc, depth=depth, f0=f0, beta=beta)
+    u, h, tr = channel_state(m, L, seed=seed, perturb=perturb, nTracers=nTracers)
+    p = dict(PHYS)
+    p.update(nTracers=nTracers, recon="consistent", nu_h=10.0, nu_v=1e-4, kappa_h=0.0, kappa_v=0.0,
+             c_drag=1e-3)
+    p.update(params)
+    return m, L, p, (u, h, tr)
+
+
+WORKLOADS = {
+    "channel_10km": dict(nx=16, ny=32, dc=10e3, L=10, depth=1000.0, f0=1.2e-4, beta=0.0,
+                         order=2, dt=300.0, M=20, steps=10),
+    "channel_1km": dict(nx=160, ny=578, dc=1e3, L=20, depth=1000.0, f0=1.2e-4, beta=1.6e-11,
+                        order=3, dt=60.0, M=30, steps=200),
+}
+
+
+def workload(name, *, seed=0, perturb=False, **override):
+    """Build a named workload: returns (mesh, L, params, state, run)."""
+    w = dict(WORKLOADS[name])
+    w.update(override)
+    run = {k: w.pop(k) for k in ("order", "dt", "M", "steps")}
+    m, L, p, st = channel_case(w.pop("nx"), w.pop("ny"), w.pop("dc"), w.pop("L"), seed=seed,
+                               perturb=perturb, **w)
+    return m, L, p, st, run
