@@ -1,0 +1,180 @@
+/*
+ * sse.h -- C ABI of libsse.so: GB300 (sm_103a) multirate split-explicit
+ * SSPRK2-SE / SSPRK3-SE time stepping of the layered primitive equations on
+ * an unstructured TRiSK C-grid (Lan, Ju, Wang, Gunzburger, Jones, "High-order
+ * multirate explicit time-stepping schemes for the baroclinic-barotropic
+ * split dynamics in primitive equations").
+ *
+ * Conventions
+ *   - Indices are 0-based int32; -1 marks an absent entry where allowed.
+ *   - All host arrays passed in are owned by the caller and only read during
+ *     the call.  All device memory is owned by the library.
+ *   - Field arrays on the host are layer-fastest: X[i*nLayers + k], k = 0 is
+ *     the top layer.  The device layout is the library's own (layer-major,
+ *     padded); it is never exposed.
+ *   - Every function returns SSE_OK (0) or a negative SSE_ERR_* code and
+ *     never throws; sse_strerror() names the code.  After a non-fatal error
+ *     (INVALID_ARG, BAD_MESH, NONFINITE) the objects stay valid.  After
+ *     SSE_ERR_CUDA or SSE_ERR_SYNC_TIMEOUT the state must be re-set with
+ *     sse_state_set before it is stepped again.
+ *   - Work is issued on the stream given at sse_state_create (NULL = the
+ *     legacy default stream).  sse_step is asynchronous; sse_state_get and
+ *     sse_diagnostics synchronise that stream.
+ */
+#ifndef SSE_H
+#define SSE_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- return codes ---- */
+#define SSE_OK 0
+#define SSE_ERR_INVALID_ARG (-1)   /* bad pointer, size, order, dt or M        */
+#define SSE_ERR_BAD_MESH (-2)      /* index out of range, non-positive geometry */
+#define SSE_ERR_OOM (-3)           /* device or host allocation failed          */
+#define SSE_ERR_CUDA (-4)          /* a CUDA call failed                        */
+#define SSE_ERR_NONFINITE (-5)     /* NaN/Inf found by sse_diagnostics          */
+#define SSE_ERR_SYNC_TIMEOUT (-6)  /* a grid barrier of the sub-cycle timed out */
+#define SSE_ERR_UNSUPPORTED (-7)   /* size beyond a compiled limit              */
+
+/* ---- precision of the device arithmetic ---- */
+#define SSE_FP64 0   /* everything in FP64                                       */
+#define SSE_MIXED 1  /* FP32 tendencies, velocities and tracers; FP64 layer
+                        thickness, SSH, accumulated barotropic flux, flux
+                        deficits and global sums                                 */
+
+/* ---- SSH reconciliation (Sec. 3.4) ---- */
+#define SSE_RECON_OFF 0         /* no transport-velocity adjustment             */
+#define SSE_RECON_PAPER 1       /* F^h exactly as printed in Sec. 3.4           */
+#define SSE_RECON_CONSISTENT 2  /* F^h from the already adjusted stage fluxes,
+                                   so sum(h) - H equals the sub-cycle SSH       */
+
+/* ---- fields for sse_state_set / sse_state_get ---- */
+#define SSE_FIELD_U 0        /* normal velocity u      [nEdges][nLayers]        */
+#define SSE_FIELD_H 1        /* layer thickness h      [nCells][nLayers]        */
+#define SSE_FIELD_TRACER0 2  /* temperature            [nCells][nLayers]        */
+#define SSE_FIELD_TRACER1 3  /* salinity (nTracers=2)  [nCells][nLayers]        */
+#define SSE_FIELD_WIND 4     /* normal wind stress     [nEdges], N m^-2 (set)   */
+#define SSE_FIELD_ZETA 5     /* SSH zeta = sum h - H   [nCells] (get)           */
+#define SSE_FIELD_UBAR 6     /* barotropic velocity    [nEdges]                 */
+#define SSE_FIELD_UTILDE 7   /* baroclinic velocity    [nEdges][nLayers]        */
+#define SSE_FIELD_G 8        /* barotropic forcing G   [nEdges]                 */
+#define SSE_FIELD_FZETA 9    /* accumulated sub-cycle flux F^zeta [nEdges] (get)*/
+#define SSE_FIELD_ZETA_SUB 10 /* SSH at the end of the last sub-cycle [nCells]  */
+
+typedef struct sse_mesh sse_mesh;
+typedef struct sse_state sse_state;
+
+/* Unstructured C-grid (MPAS/TRiSK conventions).  Edge normal n_e points from
+ * cellsOnEdge[e][0] to cellsOnEdge[e][1]; tangent k x n_e points from
+ * verticesOnEdge[e][0] to verticesOnEdge[e][1].  The tangential velocity is
+ * u^t_e = (1/dcEdge_e) sum_j weightsOnEdge[e][j] dvEdge_{e'} u_{e'} over
+ * e' = edgesOnEdge[e][j], j < nEdgesOnEdge[e] (TRiSK, Sec. 5 of the paper).
+ * Land is expressed by leaving it out: every listed cell is ocean and every
+ * listed edge joins two ocean cells; cellsOnVertex / edgesOnVertex may hold
+ * -1 where the vertex touches land.  Limits: maxEdges <= 8,
+ * maxEdges2 <= 16, 1 <= nLayers <= 64. */
+typedef struct {
+    int32_t nCells, nEdges, nVertices, maxEdges, maxEdges2, nLayers;
+    const int32_t *cellsOnEdge;      /* [nEdges][2]                        */
+    const int32_t *verticesOnEdge;   /* [nEdges][2]                        */
+    const int32_t *nEdgesOnCell;     /* [nCells]                           */
+    const int32_t *edgesOnCell;      /* [nCells][maxEdges]                 */
+    const int32_t *cellsOnVertex;    /* [nVertices][3], -1 = land          */
+    const int32_t *edgesOnVertex;    /* [nVertices][3], -1 = absent        */
+    const int32_t *nEdgesOnEdge;     /* [nEdges]                           */
+    const int32_t *edgesOnEdge;      /* [nEdges][maxEdges2]                */
+    const double *weightsOnEdge;     /* [nEdges][maxEdges2]                */
+    const double *dcEdge;            /* [nEdges] cell-centre distance (m)  */
+    const double *dvEdge;            /* [nEdges] edge length (m)           */
+    const double *areaCell;          /* [nCells] (m^2)                     */
+    const double *areaTriangle;      /* [nVertices] dual-cell area (m^2)   */
+    const double *kiteAreasOnVertex; /* [nVertices][3] (m^2)               */
+    const double *fEdge;             /* [nEdges] Coriolis parameter (1/s)  */
+    const double *fVertex;           /* [nVertices]                        */
+    const double *bottomDepth;       /* [nCells] resting depth H (m) > 0   */
+    const double *restThicknessFrac; /* [nLayers] z-star fractions, sum 1  */
+} sse_mesh_desc;
+
+/* Physics and numerics.  Linear equation of state (Eq. eqstate):
+ *   rho = eos_rho_ref - eos_alpha (T - eos_T_ref) + eos_beta (S - eos_S_ref). */
+typedef struct {
+    int32_t precision;  /* SSE_FP64 or SSE_MIXED                             */
+    int32_t recon;      /* SSE_RECON_*                                        */
+    int32_t nTracers;   /* 1 (T) or 2 (T, S)                                  */
+    int32_t reserved;   /* must be 0                                          */
+    double g, rho0;     /* gravity (m s^-2), reference density (kg m^-3)      */
+    double nu_h, nu_v;  /* horizontal / vertical viscosity (m^2 s^-1)         */
+    double kappa_h, kappa_v; /* tracer diffusivities (m^2 s^-1)               */
+    double c_drag;      /* quadratic bottom-drag coefficient                  */
+    double eos_rho_ref, eos_alpha, eos_beta, eos_T_ref, eos_S_ref;
+} sse_params;
+
+/* Global diagnostics, reduced on the device in a fixed order (FP64). */
+typedef struct {
+    double volume;            /* sum_i A_i sum_k h_ik (m^3)                   */
+    double tracer_content[2]; /* sum_i A_i sum_k h_ik phi_ik                  */
+    double kinetic_energy;    /* sum_e (l_e d_e / 2) sum_k h_e u_ek^2 / 2     */
+    double max_speed;         /* max |u_ek|                                    */
+    double min_thickness;     /* min h_ik                                      */
+    double zeta_min, zeta_max;
+    int64_t step;             /* large steps taken since the last state set    */
+    int32_t nonfinite;        /* 1 if any u, h or tracer is NaN/Inf            */
+    int32_t reserved;
+} sse_diag;
+
+/* Copy and validate a mesh; uploads connectivity and derived coefficients
+ * (divergence, curl, kinetic-energy, TRiSK and Coriolis coefficients) to the
+ * current CUDA device.  *out receives the handle.  BAD_MESH on any index out
+ * of range or non-positive geometry; UNSUPPORTED beyond the stated limits. */
+int sse_mesh_create(const sse_mesh_desc *desc, sse_mesh **out);
+void sse_mesh_destroy(sse_mesh *mesh);
+
+/* Allocate a model state on `mesh` with parameters `params`; `cuda_stream`
+ * is a cudaStream_t (or NULL).  The state starts at rest with h = 0 and must
+ * be filled with sse_state_set (at least U, H and the tracers). */
+int sse_state_create(const sse_mesh *mesh, const sse_params *params, void *cuda_stream,
+                     sse_state **out);
+void sse_state_destroy(sse_state *state);
+
+/* Host -> device copy of one field (FP64 host array, layout per SSE_FIELD_*).
+ * Setting U splits it into barotropic and baroclinic parts at the next step
+ * (Eq. BBspl); setting H recomputes zeta.  Settable: U, H, TRACER0/1, WIND,
+ * UBAR, UTILDE, G (the last three feed the algorithm-level calls below). */
+int sse_state_set(sse_state *state, int field, const double *host);
+/* Device -> host copy of one field as FP64; synchronises the stream. */
+int sse_state_get(sse_state *state, int field, double *host_out);
+
+/* Advance n_steps large steps of SSPRK{order}-SE (order 2: Sec. 3.2 with
+ * Algorithm 3; order 3: Sec. 3.3 with Algorithm 4), time step dt (s) and
+ * n_substeps barotropic sub-steps of dt/n_substeps, with the reconciliation
+ * of Sec. 3.4 chosen in params.  Asynchronous on the state's stream.
+ * INVALID_ARG for order not in {2,3}, dt <= 0 or non-finite, n_substeps < 1,
+ * n_steps < 0. */
+int sse_step(sse_state *state, int order, double dt, int n_substeps, int n_steps);
+
+/* Algorithm 1 (Baroclinic_FEuler) alone, on the state's u (= UBAR + UTILDE),
+ * UTILDE, h, tracers and zeta = sum h - H: overwrites UTILDE with the
+ * output tilde-u^1 and G with the barotropic forcing. */
+int sse_baroclinic_feuler(sse_state *state, double dt);
+/* Algorithm 3 (order 2) or Algorithm 4 (order 3) alone: sub-cycles UBAR and
+ * zeta with frozen G; overwrites UBAR with ubar^1, FZETA with the
+ * accumulated flux of Sec. 3.4 and ZETA_SUB with the sub-cycle's own SSH. */
+int sse_barotropic_substep(sse_state *state, int order, double dt, int n_substeps);
+
+/* Global sums and extrema (synchronises the stream).  Returns NONFINITE if
+ * any u, h or tracer value is NaN or Inf (out is filled either way). */
+int sse_diagnostics(sse_state *state, sse_diag *out);
+
+/* Number of kernels sse_step launches per large step for `order`. */
+int sse_kernels_per_step(const sse_state *state, int order);
+
+const char *sse_strerror(int code);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SSE_H */

@@ -1,0 +1,249 @@
+"""Thin ctypes binding of libsse.so (include/sse.h).
+
+Argument marshalling only: every step of the method runs in the CUDA library.
+Importing this module loads ``_lib/libsse.so`` and fails loudly if it is
+missing; there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as ct
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_lib", "libsse.so")
+
+SSE_OK = 0
+ERRORS = {-1: "INVALID_ARG", -2: "BAD_MESH", -3: "OOM", -4: "CUDA", -5: "NONFINITE",
+          -6: "SYNC_TIMEOUT", -7: "UNSUPPORTED"}
+FP64, MIXED = 0, 1
+RECON = {"off": 0, "paper": 1, "consistent": 2}
+FIELD = {"u": 0, "h": 1, "tracer0": 2, "tracer1": 3, "wind": 4, "zeta": 5, "ubar": 6,
+         "utilde": 7, "G": 8, "Fzeta": 9, "zeta_sub": 10}
+
+_ip = ct.POINTER(ct.c_int32)
+_dp = ct.POINTER(ct.c_double)
+
+
+class SSEError(RuntimeError):
+    def __init__(self, code, what=""):
+        self.code = code
+        super().__init__(f"{what}: {ERRORS.get(code, code)} ({code})")
+
+
+class MeshDesc(ct.Structure):
+    _fields_ = [("nCells", ct.c_int32), ("nEdges", ct.c_int32), ("nVertices", ct.c_int32),
+                ("maxEdges", ct.c_int32), ("maxEdges2", ct.c_int32), ("nLayers", ct.c_int32),
+                ("cellsOnEdge", _ip), ("verticesOnEdge", _ip), ("nEdgesOnCell", _ip),
+                ("edgesOnCell", _ip), ("cellsOnVertex", _ip), ("edgesOnVertex", _ip),
+                ("nEdgesOnEdge", _ip), ("edgesOnEdge", _ip), ("weightsOnEdge", _dp),
+                ("dcEdge", _dp), ("dvEdge", _dp), ("areaCell", _dp), ("areaTriangle", _dp),
+                ("kiteAreasOnVertex", _dp), ("fEdge", _dp), ("fVertex", _dp),
+                ("bottomDepth", _dp), ("restThicknessFrac", _dp)]
+
+
+class Params(ct.Structure):
+    _fields_ = [("precision", ct.c_int32), ("recon", ct.c_int32), ("nTracers", ct.c_int32),
+                ("reserved", ct.c_int32)] + [
+        (n, ct.c_double) for n in ("g", "rho0", "nu_h", "nu_v", "kappa_h", "kappa_v", "c_drag",
+                                   "eos_rho_ref", "eos_alpha", "eos_beta", "eos_T_ref",
+                                   "eos_S_ref")]
+
+
+class Diag(ct.Structure):
+    _fields_ = [("volume", ct.c_double), ("tracer_content", ct.c_double * 2),
+                ("kinetic_energy", ct.c_double), ("max_speed", ct.c_double),
+                ("min_thickness", ct.c_double), ("zeta_min", ct.c_double),
+                ("zeta_max", ct.c_double), ("step", ct.c_int64), ("nonfinite", ct.c_int32),
+                ("reserved", ct.c_int32)]
+
+
+EXPORTS = ["sse_mesh_create", "sse_mesh_destroy", "sse_state_create", "sse_state_destroy",
+           "sse_state_set", "sse_state_get", "sse_step", "sse_baroclinic_feuler",
+           "sse_barotropic_substep", "sse_diagnostics", "sse_kernels_per_step", "sse_strerror"]
+
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Load libsse.so once; raise if it is not built."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise ImportError(f"{path} is missing: build it with paper_2105_13484_gb300.build.build()")
+    lib = ct.CDLL(path)
+    lib.sse_mesh_create.argtypes = [ct.POINTER(MeshDesc), ct.POINTER(ct.c_void_p)]
+    lib.sse_mesh_destroy.argtypes = [ct.c_void_p]
+    lib.sse_mesh_destroy.restype = None
+    lib.sse_state_create.argtypes = [ct.c_void_p, ct.POINTER(Params), ct.c_void_p,
+                                     ct.POINTER(ct.c_void_p)]
+    lib.sse_state_destroy.argtypes = [ct.c_void_p]
+    lib.sse_state_destroy.restype = None
+    lib.sse_state_set.argtypes = [ct.c_void_p, ct.c_int, ct.c_void_p]
+    lib.sse_state_get.argtypes = [ct.c_void_p, ct.c_int, ct.c_void_p]
+    lib.sse_step.argtypes = [ct.c_void_p, ct.c_int, ct.c_double, ct.c_int, ct.c_int]
+    lib.sse_baroclinic_feuler.argtypes = [ct.c_void_p, ct.c_double]
+    lib.sse_barotropic_substep.argtypes = [ct.c_void_p, ct.c_int, ct.c_double, ct.c_int]
+    lib.sse_diagnostics.argtypes = [ct.c_void_p, ct.POINTER(Diag)]
+    lib.sse_kernels_per_step.argtypes = [ct.c_void_p, ct.c_int]
+    lib.sse_strerror.argtypes = [ct.c_int]
+    lib.sse_strerror.restype = ct.c_char_p
+    _lib = lib
+    return lib
+
+
+def _check(rc, what):
+    if rc != SSE_OK:
+        raise SSEError(rc, what)
+
+
+class Mesh:
+    """Device copy of a TRiSK mesh (any object with the mesh.Mesh attributes)."""
+
+    def __init__(self, mesh, nLayers: int, rest_frac=None):
+        self.lib = load()
+        self.L = int(nLayers)
+        self.nCells, self.nEdges, self.nVertices = int(mesh.nCells), int(mesh.nEdges), int(
+            mesh.nVertices)
+        keep = []
+
+        def ia(x):
+            a = np.ascontiguousarray(x, dtype=np.int32)
+            keep.append(a)
+            return a.ctypes.data_as(_ip)
+
+        def da(x):
+            a = np.ascontiguousarray(x, dtype=np.float64)
+            keep.append(a)
+            return a.ctypes.data_as(_dp)
+
+        rf = np.full(self.L, 1.0 / self.L) if rest_frac is None else rest_frac
+        self.desc = MeshDesc(self.nCells, self.nEdges, self.nVertices, int(mesh.maxEdges),
+                             int(mesh.maxEdges2), self.L, ia(mesh.cellsOnEdge),
+                             ia(mesh.verticesOnEdge), ia(mesh.nEdgesOnCell),
+                             ia(mesh.edgesOnCell), ia(mesh.cellsOnVertex),
+                             ia(mesh.edgesOnVertex), ia(mesh.nEdgesOnEdge),
+                             ia(mesh.edgesOnEdge), da(mesh.weightsOnEdge), da(mesh.dcEdge),
+                             da(mesh.dvEdge), da(mesh.areaCell), da(mesh.areaTriangle),
+                             da(mesh.kiteAreasOnVertex), da(mesh.fEdge), da(mesh.fVertex),
+                             da(mesh.bottomDepth), da(rf))
+        self._keep = keep
+        h = ct.c_void_p()
+        _check(self.lib.sse_mesh_create(ct.byref(self.desc), ct.byref(h)), "sse_mesh_create")
+        self.handle = h
+
+    def close(self):
+        if self.handle:
+            self.lib.sse_mesh_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def make_params(params: dict, precision="fp64") -> Params:
+    q = dict(params)
+    recon = q.get("recon", "consistent")
+    recon = RECON[recon] if isinstance(recon, str) else int(recon)
+    prec = {"fp64": FP64, "mixed": MIXED}[precision] if isinstance(precision, str) else int(
+        precision)
+    return Params(prec, recon, int(q.get("nTracers", 1)), 0, *[float(q.get(n, d)) for n, d in (
+        ("g", 9.80616), ("rho0", 1000.0), ("nu_h", 0.0), ("nu_v", 0.0), ("kappa_h", 0.0),
+        ("kappa_v", 0.0), ("c_drag", 0.0), ("eos_rho_ref", 1000.0), ("eos_alpha", 0.2),
+        ("eos_beta", 0.8), ("eos_T_ref", 10.0), ("eos_S_ref", 35.0))])
+
+
+class State:
+    """A model state on the GPU (the library owns its device memory)."""
+
+    def __init__(self, mesh: Mesh, params: dict, precision="fp64", stream=None):
+        self.lib = load()
+        self.mesh = mesh
+        self.params = make_params(params, precision)
+        self.nT = self.params.nTracers
+        h = ct.c_void_p()
+        _check(self.lib.sse_state_create(mesh.handle, ct.byref(self.params),
+                                          ct.c_void_p(stream or 0), ct.byref(h)),
+               "sse_state_create")
+        self.handle = h
+        ws = params.get("windStress")
+        if ws is not None:
+            self.set("wind", ws)
+
+    def _shape(self, field):
+        E, C, L = self.mesh.nEdges, self.mesh.nCells, self.mesh.L
+        return {"u": (E, L), "utilde": (E, L), "h": (C, L), "tracer0": (C, L),
+                "tracer1": (C, L), "wind": (E,), "ubar": (E,), "G": (E,), "Fzeta": (E,),
+                "zeta": (C,), "zeta_sub": (C,)}[field]
+
+    def set(self, field: str, x):
+        a = np.ascontiguousarray(x, dtype=np.float64)
+        if a.size != int(np.prod(self._shape(field))):
+            raise ValueError(f"{field}: expected shape {self._shape(field)}, got {a.shape}")
+        _check(self.lib.sse_state_set(self.handle, FIELD[field], a.ctypes.data), f"set {field}")
+
+    def set_ptr(self, field: str, ptr: int):
+        """Set from a host pointer (e.g. a pinned torch tensor's data_ptr())."""
+        _check(self.lib.sse_state_set(self.handle, FIELD[field], ct.c_void_p(ptr)),
+               f"set {field}")
+
+    def get(self, field: str, out=None) -> np.ndarray:
+        if out is None:
+            out = np.empty(self._shape(field), dtype=np.float64)
+        _check(self.lib.sse_state_get(self.handle, FIELD[field], out.ctypes.data), f"get {field}")
+        return out
+
+    def get_ptr(self, field: str, ptr: int):
+        _check(self.lib.sse_state_get(self.handle, FIELD[field], ct.c_void_p(ptr)),
+               f"get {field}")
+
+    def load_state(self, u, h, tr):
+        self.set("u", u)
+        self.set("h", h)
+        tr = np.asarray(tr)
+        for t in range(self.nT):
+            self.set(f"tracer{t}", tr[t])
+
+    def read_state(self):
+        tr = np.stack([self.get(f"tracer{t}") for t in range(self.nT)])
+        return self.get("u"), self.get("h"), tr
+
+    def step(self, order: int, dt: float, M: int, n_steps: int = 1):
+        _check(self.lib.sse_step(self.handle, int(order), float(dt), int(M), int(n_steps)),
+               "sse_step")
+
+    def baroclinic_feuler(self, dt: float):
+        _check(self.lib.sse_baroclinic_feuler(self.handle, float(dt)), "sse_baroclinic_feuler")
+
+    def barotropic_substep(self, order: int, dt: float, M: int):
+        _check(self.lib.sse_barotropic_substep(self.handle, int(order), float(dt), int(M)),
+               "sse_barotropic_substep")
+
+    def diagnostics(self, check=True) -> dict:
+        d = Diag()
+        rc = self.lib.sse_diagnostics(self.handle, ct.byref(d))
+        if check:
+            _check(rc, "sse_diagnostics")
+        return dict(volume=d.volume, tracer_content=(d.tracer_content[0], d.tracer_content[1]),
+                    kinetic_energy=d.kinetic_energy, max_speed=d.max_speed,
+                    min_thickness=d.min_thickness, zeta_min=d.zeta_min, zeta_max=d.zeta_max,
+                    step=d.step, nonfinite=bool(d.nonfinite), rc=rc)
+
+    def kernels_per_step(self, order: int) -> int:
+        return int(self.lib.sse_kernels_per_step(self.handle, int(order)))
+
+    def close(self):
+        if self.handle:
+            self.lib.sse_state_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,687 @@
+// api.cu -- C ABI of libsse.so (include/sse.h): mesh validation and upload,
+// state management and the SSPRK2-SE / SSPRK3-SE step driver.
+//
+// The driver issues, per large step, the stage kernels in the order of the
+// paper's schemes (Sec. 3.2 for SSPRK2-SE, Sec. 3.3 for SSPRK3-SE, with the
+// reconciliation of Sec. 3.4).  The state is kept as (ubar, utilde, h,
+// tracers, zeta) on the device; u = ubar + utilde is formed where it is read.
+#include <math.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <memory>
+#include <new>
+#include <vector>
+
+#include "../../include/sse.h"
+#include "sse_internal.cuh"
+
+using namespace sse;
+
+namespace {
+
+constexpr int kAlign = 32;
+inline int pad(int n) { return (n + kAlign - 1) / kAlign * kAlign; }
+
+// RAII list of device allocations
+struct DevArena {
+    std::vector<void *> ptrs;
+    bool failed = false;
+    template <class T> T *alloc(size_t n) {
+        void *p = nullptr;
+        if (cudaMalloc(&p, std::max<size_t>(n, 1) * sizeof(T)) != cudaSuccess) {
+            failed = true;
+            cudaGetLastError();
+            return nullptr;
+        }
+        cudaMemset(p, 0, std::max<size_t>(n, 1) * sizeof(T));
+        ptrs.push_back(p);
+        return (T *)p;
+    }
+    template <class T> T *upload(const std::vector<T> &v) {
+        T *d = alloc<T>(v.size());
+        if (d && !v.empty() &&
+            cudaMemcpy(d, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice) != cudaSuccess)
+            failed = true;
+        return d;
+    }
+    ~DevArena() {
+        for (void *p : ptrs) cudaFree(p);
+    }
+};
+
+}  // namespace
+
+struct sse_mesh {
+    DMesh dm;
+    DevArena arena;
+    int device = 0;
+};
+
+// ---------------------------------------------------------------------------
+// mesh
+// ---------------------------------------------------------------------------
+extern "C" int sse_mesh_create(const sse_mesh_desc *d, sse_mesh **out) {
+    if (!d || !out) return SSE_ERR_INVALID_ARG;
+    *out = nullptr;
+    const int C = d->nCells, E = d->nEdges, V = d->nVertices, mE = d->maxEdges,
+              mE2 = d->maxEdges2, L = d->nLayers;
+    if (C < 1 || E < 1 || V < 1 || mE < 3 || mE2 < 1 || L < 1) return SSE_ERR_INVALID_ARG;
+    if (mE > MAXE || mE2 > MAXE2 || L > LMAX) return SSE_ERR_UNSUPPORTED;
+    if (!d->cellsOnEdge || !d->verticesOnEdge || !d->nEdgesOnCell || !d->edgesOnCell ||
+        !d->cellsOnVertex || !d->edgesOnVertex || !d->nEdgesOnEdge || !d->edgesOnEdge ||
+        !d->weightsOnEdge || !d->dcEdge || !d->dvEdge || !d->areaCell || !d->areaTriangle ||
+        !d->kiteAreasOnVertex || !d->fEdge || !d->fVertex || !d->bottomDepth ||
+        !d->restThicknessFrac)
+        return SSE_ERR_INVALID_ARG;
+    // ---- validation
+    for (int e = 0; e < E; e++) {
+        for (int s = 0; s < 2; s++) {
+            int c = d->cellsOnEdge[2 * e + s], v = d->verticesOnEdge[2 * e + s];
+            if (c < 0 || c >= C || v < 0 || v >= V) return SSE_ERR_BAD_MESH;
+        }
+        if (d->cellsOnEdge[2 * e] == d->cellsOnEdge[2 * e + 1]) return SSE_ERR_BAD_MESH;
+        if (!(d->dcEdge[e] > 0) || !(d->dvEdge[e] > 0) || !isfinite(d->fEdge[e]))
+            return SSE_ERR_BAD_MESH;
+        int n = d->nEdgesOnEdge[e];
+        if (n < 0 || n > mE2) return SSE_ERR_BAD_MESH;
+        for (int j = 0; j < n; j++) {
+            int ep = d->edgesOnEdge[(size_t)e * mE2 + j];
+            if (ep < 0 || ep >= E || !isfinite(d->weightsOnEdge[(size_t)e * mE2 + j]))
+                return SSE_ERR_BAD_MESH;
+        }
+    }
+    for (int i = 0; i < C; i++) {
+        int n = d->nEdgesOnCell[i];
+        if (n < 1 || n > mE || !(d->areaCell[i] > 0) || !(d->bottomDepth[i] > 0))
+            return SSE_ERR_BAD_MESH;
+        for (int j = 0; j < n; j++) {
+            int e = d->edgesOnCell[(size_t)i * mE + j];
+            if (e < 0 || e >= E) return SSE_ERR_BAD_MESH;
+            if (d->cellsOnEdge[2 * e] != i && d->cellsOnEdge[2 * e + 1] != i) return SSE_ERR_BAD_MESH;
+        }
+    }
+    for (int v = 0; v < V; v++) {
+        double ksum = 0.0;
+        if (!(d->areaTriangle[v] > 0) || !isfinite(d->fVertex[v])) return SSE_ERR_BAD_MESH;
+        for (int j = 0; j < 3; j++) {
+            int c = d->cellsOnVertex[3 * v + j], e = d->edgesOnVertex[3 * v + j];
+            if (c < -1 || c >= C || e < -1 || e >= E) return SSE_ERR_BAD_MESH;
+            if (e >= 0 && d->verticesOnEdge[2 * e] != v && d->verticesOnEdge[2 * e + 1] != v)
+                return SSE_ERR_BAD_MESH;
+            if (c >= 0) {
+                if (!(d->kiteAreasOnVertex[3 * v + j] >= 0)) return SSE_ERR_BAD_MESH;
+                ksum += d->kiteAreasOnVertex[3 * v + j];
+            }
+        }
+        if (!(ksum > 0)) return SSE_ERR_BAD_MESH;
+    }
+    {
+        double s = 0.0;
+        for (int k = 0; k < L; k++) {
+            if (!(d->restThicknessFrac[k] > 0)) return SSE_ERR_BAD_MESH;
+            s += d->restThicknessFrac[k];
+        }
+        if (fabs(s - 1.0) > 1e-12) return SSE_ERR_BAD_MESH;
+    }
+
+    // ---- derived, padded, layer-major arrays
+    const int Cp = pad(C), Ep = pad(E), Vp = pad(V);
+    std::vector<int2> coe(Ep, make_int2(0, 0)), voe(Ep, make_int2(0, 0));
+    std::vector<int> neoc(Cp, 0), eoc((size_t)mE * Cp, 0), ooc((size_t)mE * Cp, 0);
+    std::vector<int> neoe(Ep, 0), eoe((size_t)mE2 * Ep, 0), eov(3 * Vp, 0), cov(3 * Vp, 0);
+    std::vector<double> H(Cp, 1.0), sfrac(d->restThicknessFrac, d->restThicknessFrac + L);
+    std::vector<double> divc((size_t)mE * Cp, 0.0), kec((size_t)mE * Cp, 0.0);
+    std::vector<double> wl((size_t)mE2 * Ep, 0.0), cfc((size_t)mE2 * Ep, 0.0);
+    std::vector<double> curlc(3 * Vp, 0.0), kw(3 * Vp, 0.0), invdc(Ep, 1.0), invdv(Ep, 1.0);
+    std::vector<double> fV(Vp, 0.0), area(Cp, 0.0), ld2(Ep, 0.0);
+    for (int e = 0; e < E; e++) {
+        coe[e] = make_int2(d->cellsOnEdge[2 * e], d->cellsOnEdge[2 * e + 1]);
+        voe[e] = make_int2(d->verticesOnEdge[2 * e], d->verticesOnEdge[2 * e + 1]);
+        invdc[e] = 1.0 / d->dcEdge[e];
+        invdv[e] = 1.0 / d->dvEdge[e];
+        ld2[e] = 0.5 * d->dvEdge[e] * d->dcEdge[e];
+        neoe[e] = d->nEdgesOnEdge[e];
+        for (int j = 0; j < neoe[e]; j++) {
+            int ep = d->edgesOnEdge[(size_t)e * mE2 + j];
+            eoe[(size_t)j * Ep + e] = ep;
+            double w = d->weightsOnEdge[(size_t)e * mE2 + j] * d->dvEdge[ep] / d->dcEdge[e];
+            wl[(size_t)j * Ep + e] = w;
+            cfc[(size_t)j * Ep + e] = w * 0.5 * (d->fEdge[e] + d->fEdge[ep]);
+        }
+    }
+    for (int i = 0; i < C; i++) {
+        H[i] = d->bottomDepth[i];
+        area[i] = d->areaCell[i];
+        neoc[i] = d->nEdgesOnCell[i];
+        for (int j = 0; j < neoc[i]; j++) {
+            int e = d->edgesOnCell[(size_t)i * mE + j];
+            int c1 = d->cellsOnEdge[2 * e], c2 = d->cellsOnEdge[2 * e + 1];
+            eoc[(size_t)j * Cp + i] = e;
+            ooc[(size_t)j * Cp + i] = (c1 == i) ? c2 : c1;
+            divc[(size_t)j * Cp + i] = ((c1 == i) ? 1.0 : -1.0) * d->dvEdge[e] / d->areaCell[i];
+            kec[(size_t)j * Cp + i] = 0.25 * d->dvEdge[e] * d->dcEdge[e] / d->areaCell[i];
+        }
+    }
+    for (int v = 0; v < V; v++) {
+        fV[v] = d->fVertex[v];
+        double ksum = 0.0;
+        for (int j = 0; j < 3; j++)
+            if (d->cellsOnVertex[3 * v + j] >= 0) ksum += d->kiteAreasOnVertex[3 * v + j];
+        for (int j = 0; j < 3; j++) {
+            int e = d->edgesOnVertex[3 * v + j], c = d->cellsOnVertex[3 * v + j];
+            if (e >= 0) {
+                eov[(size_t)j * Vp + v] = e;
+                double sign = (d->verticesOnEdge[2 * e + 1] == v) ? 1.0 : -1.0;
+                curlc[(size_t)j * Vp + v] = sign * d->dcEdge[e] / d->areaTriangle[v];
+            }
+            if (c >= 0) {
+                cov[(size_t)j * Vp + v] = c;
+                kw[(size_t)j * Vp + v] = d->kiteAreasOnVertex[3 * v + j] / ksum;
+            }
+        }
+    }
+    auto tof = [](const std::vector<double> &x) {
+        return std::vector<float>(x.begin(), x.end());
+    };
+
+    sse_mesh *m = new (std::nothrow) sse_mesh();
+    if (!m) return SSE_ERR_OOM;
+    cudaGetDevice(&m->device);
+    DevArena &A = m->arena;
+    DMesh &dm = m->dm;
+    dm.C = C; dm.E = E; dm.V = V; dm.L = L; dm.Cp = Cp; dm.Ep = Ep; dm.Vp = Vp;
+    dm.maxE = mE; dm.maxE2 = mE2;
+    dm.coe = A.upload(coe); dm.voe = A.upload(voe);
+    dm.neoc = A.upload(neoc); dm.eoc = A.upload(eoc); dm.ooc = A.upload(ooc);
+    dm.neoe = A.upload(neoe); dm.eoe = A.upload(eoe); dm.eov = A.upload(eov);
+    dm.cov = A.upload(cov); dm.H = A.upload(H); dm.sfrac = A.upload(sfrac);
+    dm.divc_d = A.upload(divc); dm.area = A.upload(area); dm.ld2 = A.upload(ld2);
+    dm.d.divc = dm.divc_d; dm.d.kec = A.upload(kec); dm.d.wl = A.upload(wl);
+    dm.d.cfc = A.upload(cfc); dm.d.curlc = A.upload(curlc); dm.d.kw = A.upload(kw);
+    dm.d.invdc = A.upload(invdc); dm.d.invdv = A.upload(invdv); dm.d.fV = A.upload(fV);
+    dm.f.divc = A.upload(tof(divc)); dm.f.kec = A.upload(tof(kec)); dm.f.wl = A.upload(tof(wl));
+    dm.f.cfc = A.upload(tof(cfc)); dm.f.curlc = A.upload(tof(curlc)); dm.f.kw = A.upload(tof(kw));
+    dm.f.invdc = A.upload(tof(invdc)); dm.f.invdv = A.upload(tof(invdv));
+    dm.f.fV = A.upload(tof(fV));
+    if (A.failed) {
+        delete m;
+        return SSE_ERR_OOM;
+    }
+    *out = m;
+    return SSE_OK;
+}
+
+extern "C" void sse_mesh_destroy(sse_mesh *m) { delete m; }
+
+// ---------------------------------------------------------------------------
+// state: a precision-specific engine behind a small virtual interface
+// ---------------------------------------------------------------------------
+struct EngineBase {
+    virtual ~EngineBase() {}
+    virtual int set(int field, const double *host) = 0;
+    virtual int get(int field, double *host) = 0;
+    virtual int step(int order, double dt, int M) = 0;
+    virtual int bcl_feuler(double dt) = 0;
+    virtual int btr_substep(int order, double dt, int M) = 0;
+    virtual int diagnostics(sse_diag *out) = 0;
+    long long steps = 0;
+};
+
+#define CK(x)                                                        \
+    do {                                                             \
+        cudaError_t _e = (x);                                        \
+        if (_e != cudaSuccess) {                                     \
+            fprintf(stderr, "libsse: %s -> %s\n", #x, cudaGetErrorString(_e)); \
+            return SSE_ERR_CUDA;                                     \
+        }                                                            \
+    } while (0)
+
+template <class R>
+struct Engine : EngineBase {
+    DMesh m;
+    DParams p{};
+    int recon = SSE_RECON_CONSISTENT;
+    bool mixed = false;
+    cudaStream_t s = nullptr;
+    DevArena A;
+    // state
+    R *ubar_n, *ut_n;
+    double *h_n, *zeta_n;
+    R *hR_n, *tr_n;
+    // stage buffers
+    R *ut_1, *ut_c, *ut_3, *ubar_1, *ubar_h, *ubar_np1;
+    R *G0, *G1, *G2, *Gw;
+    double *Fz1, *Fz2, *Fz3, *S1, *S2, *zeta_sub, *last_Fz;
+    double *h_1, *h_h, *zeta_1, *zeta_h;
+    R *hR_1, *hR_h, *tr_1, *tr_h;
+    R *flux;
+    DiagBufs<R> db;
+    R *bu0, *bua, *buh, *bz0, *bza, *bzh;
+    unsigned int *barwords;
+    int *barerr;
+    double *stage;   // staging for host transfers
+    double *wind;
+    double *dpart, *dout;
+    int dparts = 0;
+    int btr_blocks = 1;
+
+    int init(const sse_mesh *mesh, const sse_params *prm, cudaStream_t st) {
+        m = mesh->dm;
+        s = st;
+        mixed = (prm->precision == SSE_MIXED);
+        recon = prm->recon;
+        p.g = prm->g; p.rho0 = prm->rho0; p.nu_h = prm->nu_h; p.nu_v = prm->nu_v;
+        p.kappa_h = prm->kappa_h; p.kappa_v = prm->kappa_v; p.c_drag = prm->c_drag;
+        p.alpha = prm->eos_alpha; p.beta = prm->eos_beta; p.T_ref = prm->eos_T_ref;
+        p.S_ref = prm->eos_S_ref; p.zcoef = prm->g * (1.0 - prm->eos_rho_ref / prm->rho0);
+        p.nT = prm->nTracers; p.recon = prm->recon; p.wind = nullptr;
+        const size_t EL = (size_t)m.L * m.Ep, CL = (size_t)m.L * m.Cp, VL = (size_t)m.L * m.Vp;
+        const int nT = p.nT;
+        ubar_n = A.alloc<R>(m.Ep); ut_n = A.alloc<R>(EL);
+        h_n = A.alloc<double>(CL); zeta_n = A.alloc<double>(m.Cp);
+        tr_n = A.alloc<R>(nT * CL);
+        ut_1 = A.alloc<R>(EL); ut_c = A.alloc<R>(EL); ut_3 = A.alloc<R>(EL);
+        ubar_1 = A.alloc<R>(m.Ep); ubar_h = A.alloc<R>(m.Ep); ubar_np1 = A.alloc<R>(m.Ep);
+        G0 = A.alloc<R>(m.Ep); G1 = A.alloc<R>(m.Ep); G2 = A.alloc<R>(m.Ep); Gw = A.alloc<R>(m.Ep);
+        Fz1 = A.alloc<double>(m.Ep); Fz2 = A.alloc<double>(m.Ep); Fz3 = A.alloc<double>(m.Ep);
+        S1 = A.alloc<double>(m.Ep); S2 = A.alloc<double>(m.Ep);
+        zeta_sub = A.alloc<double>(m.Cp);
+        last_Fz = Fz1;
+        h_1 = A.alloc<double>(CL); h_h = A.alloc<double>(CL);
+        zeta_1 = A.alloc<double>(m.Cp); zeta_h = A.alloc<double>(m.Cp);
+        if (mixed) {
+            hR_n = A.alloc<R>(CL); hR_1 = A.alloc<R>(CL); hR_h = A.alloc<R>(CL);
+        } else {
+            hR_n = (R *)h_n; hR_1 = (R *)h_1; hR_h = (R *)h_h;
+        }
+        tr_1 = A.alloc<R>(nT * CL); tr_h = A.alloc<R>(nT * CL);
+        flux = A.alloc<R>(EL);
+        db.ke = A.alloc<R>(CL); db.delta = A.alloc<R>(CL); db.rhop = A.alloc<R>(CL);
+        db.pp = A.alloc<R>(CL); db.zm = A.alloc<R>(CL); db.w = A.alloc<R>(CL);
+        db.omega = A.alloc<R>(VL); db.q = A.alloc<R>(VL);
+        db.hu = A.alloc<R>(EL); db.qe = A.alloc<R>(EL);
+        bu0 = A.alloc<R>(m.Ep); bua = A.alloc<R>(m.Ep); buh = A.alloc<R>(m.Ep);
+        bz0 = A.alloc<R>(m.Cp); bza = A.alloc<R>(m.Cp); bzh = A.alloc<R>(m.Cp);
+        barwords = A.alloc<unsigned int>(2);
+        barerr = A.alloc<int>(1);
+        stage = A.alloc<double>((size_t)std::max(m.Ep, m.Cp) * m.L);
+        wind = A.alloc<double>(m.Ep);
+        dparts = 256;
+        dpart = A.alloc<double>((size_t)dparts * 9);
+        dout = A.alloc<double>(9);
+        if (A.failed) return SSE_ERR_OOM;
+        // persistent sub-cycle grid: all co-resident blocks, no more than needed
+        int dev = 0, nsm = 0, occ = 0;
+        CK(cudaGetDevice(&dev));
+        CK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+        const int bt = btr_block_size<R>();
+        int occ2 = 0;
+        CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, btr_kernel_ptr<R>(2), bt, 0));
+        CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ2, btr_kernel_ptr<R>(3), bt, 0));
+        occ = std::min(occ, occ2);
+        if (occ < 1) return SSE_ERR_UNSUPPORTED;
+        const int need = (std::max(m.E, m.C) + bt - 1) / bt;
+        btr_blocks = std::max(1, std::min(need, occ * nsm));
+        CK(cudaStreamSynchronize(s));
+        return SSE_OK;
+    }
+
+    Barrier bar() const { return Barrier{barwords, barwords + 1, barerr}; }
+
+    int check_launch() {
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) {
+            fprintf(stderr, "libsse: launch failed: %s\n", cudaGetErrorString(e));
+            return SSE_ERR_CUDA;
+        }
+        return SSE_OK;
+    }
+
+    // ---- host <-> device
+    int set(int field, const double *host) override {
+        const int L = m.L;
+        switch (field) {
+        case SSE_FIELD_U:
+        case SSE_FIELD_UTILDE:
+            CK(cudaMemcpyAsync(stage, host, sizeof(double) * m.E * L, cudaMemcpyHostToDevice, s));
+            launch_to_device<R>(stage, ut_n, m.E, L, m.Ep, s);
+            if (field == SSE_FIELD_U) CK(cudaMemsetAsync(ubar_n, 0, sizeof(R) * m.Ep, s));
+            break;
+        case SSE_FIELD_UBAR:
+        case SSE_FIELD_G:
+            CK(cudaMemcpyAsync(stage, host, sizeof(double) * m.E, cudaMemcpyHostToDevice, s));
+            launch_to_device<R>(stage, field == SSE_FIELD_UBAR ? ubar_n : G0, m.E, 1, m.Ep, s);
+            break;
+        case SSE_FIELD_H:
+            CK(cudaMemcpyAsync(stage, host, sizeof(double) * m.C * L, cudaMemcpyHostToDevice, s));
+            launch_to_device<double>(stage, h_n, m.C, L, m.Cp, s);
+            if (mixed) launch_h_to_float(h_n, (float *)hR_n, L * m.Cp, s);
+            launch_ssh(m, h_n, zeta_n, s);
+            break;
+        case SSE_FIELD_TRACER0:
+        case SSE_FIELD_TRACER1: {
+            const int t = field - SSE_FIELD_TRACER0;
+            if (t >= p.nT) return SSE_ERR_INVALID_ARG;
+            CK(cudaMemcpyAsync(stage, host, sizeof(double) * m.C * L, cudaMemcpyHostToDevice, s));
+            launch_to_device<R>(stage, tr_n + (size_t)t * L * m.Cp, m.C, L, m.Cp, s);
+            break;
+        }
+        case SSE_FIELD_WIND:
+            CK(cudaMemcpyAsync(wind, host, sizeof(double) * m.E, cudaMemcpyHostToDevice, s));
+            p.wind = wind;
+            break;
+        default:
+            return SSE_ERR_INVALID_ARG;
+        }
+        CK(cudaMemsetAsync(barerr, 0, sizeof(int), s));
+        steps = 0;
+        int rc = check_launch();
+        if (rc) return rc;
+        CK(cudaStreamSynchronize(s));
+        return SSE_OK;
+    }
+
+    int get(int field, double *host) override {
+        const int L = m.L;
+        size_t n = 0;
+        switch (field) {
+        case SSE_FIELD_U:
+            launch_add_bar<R>(ubar_n, ut_n, stage, m.E, L, m.Ep, s);
+            n = (size_t)m.E * L;
+            break;
+        case SSE_FIELD_UTILDE:
+            launch_from_device<R>(ut_n, stage, m.E, L, m.Ep, s);
+            n = (size_t)m.E * L;
+            break;
+        case SSE_FIELD_UBAR:
+        case SSE_FIELD_G:
+            launch_from_device<R>(field == SSE_FIELD_UBAR ? ubar_n : G0, stage, m.E, 1, m.Ep, s);
+            n = m.E;
+            break;
+        case SSE_FIELD_H:
+            launch_from_device<double>(h_n, stage, m.C, L, m.Cp, s);
+            n = (size_t)m.C * L;
+            break;
+        case SSE_FIELD_TRACER0:
+        case SSE_FIELD_TRACER1: {
+            const int t = field - SSE_FIELD_TRACER0;
+            if (t >= p.nT) return SSE_ERR_INVALID_ARG;
+            launch_from_device<R>(tr_n + (size_t)t * L * m.Cp, stage, m.C, L, m.Cp, s);
+            n = (size_t)m.C * L;
+            break;
+        }
+        case SSE_FIELD_ZETA:
+            CK(cudaMemcpyAsync(stage, zeta_n, sizeof(double) * m.C, cudaMemcpyDeviceToDevice, s));
+            n = m.C;
+            break;
+        case SSE_FIELD_ZETA_SUB:
+            CK(cudaMemcpyAsync(stage, zeta_sub, sizeof(double) * m.C, cudaMemcpyDeviceToDevice, s));
+            n = m.C;
+            break;
+        case SSE_FIELD_FZETA:
+            CK(cudaMemcpyAsync(stage, last_Fz, sizeof(double) * m.E, cudaMemcpyDeviceToDevice, s));
+            n = m.E;
+            break;
+        case SSE_FIELD_WIND:
+            CK(cudaMemcpyAsync(stage, wind, sizeof(double) * m.E, cudaMemcpyDeviceToDevice, s));
+            n = m.E;
+            break;
+        default:
+            return SSE_ERR_INVALID_ARG;
+        }
+        int rc = check_launch();
+        if (rc) return rc;
+        CK(cudaMemcpyAsync(host, stage, sizeof(double) * n, cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        return barrier_status();
+    }
+
+    int barrier_status() {
+        int err = 0;
+        CK(cudaMemcpyAsync(&err, barerr, sizeof(int), cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        return err ? SSE_ERR_SYNC_TIMEOUT : SSE_OK;
+    }
+
+    // ---- pieces
+    void bcl_stage(R *ubar, R *ut, R *hR, R *tr, const double *zeta, bool split, const R *utn,
+                   double a, double b, double dt, R *out, R *G) {
+        launch_cell_diag<R>(m, p, ubar, ut, hR, tr, db, s);
+        launch_vertex<R>(m, ubar, ut, hR, db, s);
+        launch_edge_pre<R>(m, ubar, ut, hR, db, split, s);
+        launch_bcl_edge<R>(m, p, ubar, ut, hR, zeta, db, utn, a, b, dt, out, G, s);
+    }
+
+    cudaError_t btr(int order, const R *ub_start, const double *z_start, const R *Ga,
+                    double tau_dt, int M, const R *X, double al, double be, R *ub_out,
+                    double *Fz, double *z_out) {
+        BtrArgs<R> a{};
+        a.ub_start = ub_start; a.z_start = z_start; a.G = Ga; a.X = X; a.alpha = al;
+        a.beta = be; a.ub_out = ub_out; a.Fz = Fz; a.z_out = z_out;
+        a.u0 = bu0; a.ua = bua; a.uh = buh; a.z0 = bz0; a.za = bza; a.zh = bzh;
+        a.tau = tau_dt / M; a.g = p.g; a.M = M; a.order = order;
+        last_Fz = Fz;
+        return launch_btr<R>(m, a, bar(), btr_blocks, btr_block_size<R>(), s);
+    }
+
+    void transport(const double *h, const R *ubA, const R *utA, double wA, const R *ubB,
+                   const R *utB, double wB, const double *Fz, const double *e1, const double *e2,
+                   double cF, double cE, double cA, double *S_out) {
+        TransportArgs<R> a{};
+        a.h = h; a.ubA = ubA; a.utA = utA; a.ubB = ubB; a.utB = utB; a.wA = wA; a.wB = wB;
+        a.Fz = Fz; a.ex1 = e1; a.ex2 = e2; a.cF = cF; a.cE = cE; a.cA = cA;
+        a.recon = (recon != SSE_RECON_OFF); a.S_out = S_out; a.flux = flux;
+        launch_transport<R>(m, a, s);
+    }
+
+    void thickness(const double *h_s, const R *tr_s, double a, double b, double dt, double *h_out,
+                   R *hR_out, R *tr_out, double *zeta_out) {
+        ThickArgs<R> t{};
+        t.flux = flux; t.h_s = h_s; t.tr_s = tr_s; t.h_n = h_n; t.tr_n = tr_n;
+        t.a = a; t.b = b; t.dt = dt; t.h_out = h_out; t.hR_out = mixed ? hR_out : nullptr;
+        t.tr_out = tr_out; t.zeta_out = zeta_out;
+        launch_thickness<R>(m, p, t, s);
+    }
+
+    // combined forcing for the corrector: Gw = w0 G0 + w1 G1 (+ w2 G2)
+    void combine_G(double w0, double w1, double w2);
+
+    int step(int order, double dt, int M) override {
+        const bool consistent = (recon == SSE_RECON_CONSISTENT);
+        if (order == 2) {
+            // Stage 1 (Sec. 3.2): Algorithm 1, predictor sub-cycle, thickness
+            bcl_stage(ubar_n, ut_n, hR_n, tr_n, zeta_n, true, nullptr, 0.0, 1.0, dt, ut_1, G0);
+            CK(btr(2, ubar_n, zeta_n, G0, dt, M, nullptr, 0, 1, ubar_1, Fz1, nullptr));
+            transport(h_n, ubar_n, ut_n, 1.0, nullptr, nullptr, 0.0, Fz1, nullptr, nullptr, 1.0,
+                      0.0, 1.0, S1);
+            thickness(h_n, tr_n, 0.0, 1.0, dt, h_1, hR_1, tr_1, zeta_1);
+            // Stage 2: baroclinic, utilde^{n+1} = (ut^n + ut^{n+2})/2
+            bcl_stage(ubar_1, ut_1, hR_1, tr_1, zeta_1, false, ut_n, 0.5, 0.5, dt, ut_c, G1);
+            // Step 2: corrector with Interp_2(G0, G1)
+            combine_G(0.5, 0.5, 0.0);
+            CK(btr(2, ubar_n, zeta_n, Gw, dt, M, nullptr, 0, 1, ubar_np1, Fz2, zeta_sub));
+            // Step 3: thickness stage 2 with F^h_2 and the factor 2 of Sec. 3.4
+            transport(h_1, ubar_np1, ut_c, 1.0, nullptr, nullptr, 0.0, Fz2,
+                      consistent ? Fz1 : S1, nullptr, 0.5, 0.5, 2.0, nullptr);
+            thickness(h_1, tr_1, 0.5, 0.5, dt, h_n, hR_n, tr_n, zeta_n);
+            std::swap(ut_n, ut_c);
+            std::swap(ubar_n, ubar_np1);
+        } else {
+            // Stage 1 (Sec. 3.3)
+            bcl_stage(ubar_n, ut_n, hR_n, tr_n, zeta_n, true, nullptr, 0.0, 1.0, dt, ut_1, G0);
+            CK(btr(3, ubar_n, zeta_n, G0, dt, M, nullptr, 0, 1, ubar_1, Fz1, nullptr));
+            transport(h_n, ubar_n, ut_n, 1.0, nullptr, nullptr, 0.0, Fz1, nullptr, nullptr, 1.0,
+                      0.0, 1.0, S1);
+            thickness(h_n, tr_n, 0.0, 1.0, dt, h_1, hR_1, tr_1, zeta_1);
+            // Stage 2
+            bcl_stage(ubar_1, ut_1, hR_1, tr_1, zeta_1, false, ut_n, 0.75, 0.25, dt, ut_c, G1);
+            CK(btr(3, ubar_1, zeta_1, G1, dt, M, ubar_n, 0.75, 0.25, ubar_h, Fz2, nullptr));
+            transport(h_1, ubar_1, ut_1, 1.0, nullptr, nullptr, 0.0, Fz2, nullptr, nullptr, 1.0,
+                      0.0, 1.0, S2);
+            thickness(h_1, tr_1, 0.75, 0.25, dt, h_h, hR_h, tr_h, zeta_h);
+            // Stage 3
+            bcl_stage(ubar_h, ut_c, hR_h, tr_h, zeta_h, false, ut_n, 1.0 / 3.0, 2.0 / 3.0, dt,
+                      ut_3, G2);
+            // Step 2: corrector with Interp_3(G0, G1, G_{1/2})
+            combine_G(1.0 / 6.0, 1.0 / 6.0, 2.0 / 3.0);
+            CK(btr(3, ubar_n, zeta_n, Gw, dt, M, nullptr, 0, 1, ubar_np1, Fz3, zeta_sub));
+            // Step 3: F^h_3 of Sec. 3.4 and the factor 3/2
+            transport(h_h, ubar_n, ut_n, 0.5, ubar_np1, ut_3, 0.5, Fz3, consistent ? Fz1 : S1,
+                      consistent ? Fz2 : S2, 2.0 / 3.0, 1.0 / 6.0, 1.5, nullptr);
+            thickness(h_h, tr_h, 1.0 / 3.0, 2.0 / 3.0, dt, h_n, hR_n, tr_n, zeta_n);
+            std::swap(ut_n, ut_3);
+            std::swap(ubar_n, ubar_np1);
+        }
+        steps++;
+        return check_launch();
+    }
+
+    int bcl_feuler(double dt) override {
+        launch_ssh(m, h_n, zeta_n, s);
+        bcl_stage(ubar_n, ut_n, hR_n, tr_n, zeta_n, false, nullptr, 0.0, 1.0, dt, ut_1, G0);
+        CK(cudaMemcpyAsync(ut_n, ut_1, sizeof(R) * m.L * m.Ep, cudaMemcpyDeviceToDevice, s));
+        return check_launch();
+    }
+
+    int btr_substep(int order, double dt, int M) override {
+        launch_ssh(m, h_n, zeta_n, s);
+        CK(btr(order, ubar_n, zeta_n, G0, dt, M, nullptr, 0, 1, ubar_1, Fz1, zeta_sub));
+        CK(cudaMemcpyAsync(ubar_n, ubar_1, sizeof(R) * m.Ep, cudaMemcpyDeviceToDevice, s));
+        return check_launch();
+    }
+
+    int diagnostics(sse_diag *out) override {
+        launch_diag<R>(m, ubar_n, ut_n, h_n, tr_n, p.nT, zeta_n, dpart, dparts, dout, s);
+        int rc = check_launch();
+        if (rc) return rc;
+        double v[9];
+        CK(cudaMemcpyAsync(v, dout, sizeof(v), cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        memset(out, 0, sizeof(*out));
+        out->volume = v[0];
+        out->tracer_content[0] = v[1];
+        out->tracer_content[1] = v[2];
+        out->kinetic_energy = v[3];
+        out->max_speed = v[4];
+        out->min_thickness = v[5];
+        out->zeta_min = v[6];
+        out->zeta_max = v[7];
+        out->nonfinite = v[8] != 0.0;
+        out->step = steps;
+        rc = barrier_status();
+        if (rc) return rc;
+        return out->nonfinite ? SSE_ERR_NONFINITE : SSE_OK;
+    }
+};
+
+template <class R>
+__global__ void k_combine_G(const R *__restrict__ a, const R *__restrict__ b,
+                            const R *__restrict__ c, R *__restrict__ out, double wa, double wb,
+                            double wc, int n) {
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= n) return;
+    out[e] = (R)(wa * (double)a[e] + wb * (double)b[e] + wc * (double)c[e]);
+}
+
+template <class R> void Engine<R>::combine_G(double w0, double w1, double w2) {
+    k_combine_G<R><<<(m.E + 255) / 256, 256, 0, s>>>(G0, G1, G2, Gw, w0, w1, w2, m.E);
+}
+
+struct sse_state {
+    std::unique_ptr<EngineBase> eng;
+    int device = 0;
+};
+
+extern "C" int sse_state_create(const sse_mesh *mesh, const sse_params *prm, void *stream,
+                                sse_state **out) {
+    if (!mesh || !prm || !out) return SSE_ERR_INVALID_ARG;
+    *out = nullptr;
+    if ((prm->precision != SSE_FP64 && prm->precision != SSE_MIXED) || prm->recon < 0 ||
+        prm->recon > 2 || prm->nTracers < 1 || prm->nTracers > 2 || prm->reserved != 0 ||
+        !(prm->g > 0) || !(prm->rho0 > 0) || !(prm->nu_h >= 0) || !(prm->nu_v >= 0) ||
+        !(prm->kappa_h >= 0) || !(prm->kappa_v >= 0) || !(prm->c_drag >= 0) ||
+        !isfinite(prm->eos_rho_ref) || !isfinite(prm->eos_alpha) || !isfinite(prm->eos_beta) ||
+        !isfinite(prm->eos_T_ref) || !isfinite(prm->eos_S_ref))
+        return SSE_ERR_INVALID_ARG;
+    sse_state *st = new (std::nothrow) sse_state();
+    if (!st) return SSE_ERR_OOM;
+    int rc;
+    if (prm->precision == SSE_FP64) {
+        auto *e = new (std::nothrow) Engine<double>();
+        if (!e) { delete st; return SSE_ERR_OOM; }
+        st->eng.reset(e);
+        rc = e->init(mesh, prm, (cudaStream_t)stream);
+    } else {
+        auto *e = new (std::nothrow) Engine<float>();
+        if (!e) { delete st; return SSE_ERR_OOM; }
+        st->eng.reset(e);
+        rc = e->init(mesh, prm, (cudaStream_t)stream);
+    }
+    if (rc != SSE_OK) {
+        delete st;
+        return rc;
+    }
+    *out = st;
+    return SSE_OK;
+}
+
+extern "C" void sse_state_destroy(sse_state *st) { delete st; }
+
+extern "C" int sse_state_set(sse_state *st, int field, const double *host) {
+    if (!st || !host) return SSE_ERR_INVALID_ARG;
+    return st->eng->set(field, host);
+}
+
+extern "C" int sse_state_get(sse_state *st, int field, double *host) {
+    if (!st || !host) return SSE_ERR_INVALID_ARG;
+    return st->eng->get(field, host);
+}
+
+extern "C" int sse_step(sse_state *st, int order, double dt, int n_substeps, int n_steps) {
+    if (!st || (order != 2 && order != 3) || !(dt > 0) || !isfinite(dt) || n_substeps < 1 ||
+        n_steps < 0)
+        return SSE_ERR_INVALID_ARG;
+    for (int i = 0; i < n_steps; i++) {
+        int rc = st->eng->step(order, dt, n_substeps);
+        if (rc) return rc;
+    }
+    return SSE_OK;
+}
+
+extern "C" int sse_baroclinic_feuler(sse_state *st, double dt) {
+    if (!st || !(dt > 0) || !isfinite(dt)) return SSE_ERR_INVALID_ARG;
+    return st->eng->bcl_feuler(dt);
+}
+
+extern "C" int sse_barotropic_substep(sse_state *st, int order, double dt, int n_substeps) {
+    if (!st || (order != 2 && order != 3) || !(dt > 0) || !isfinite(dt) || n_substeps < 1)
+        return SSE_ERR_INVALID_ARG;
+    return st->eng->btr_substep(order, dt, n_substeps);
+}
+
+extern "C" int sse_diagnostics(sse_state *st, sse_diag *out) {
+    if (!st || !out) return SSE_ERR_INVALID_ARG;
+    return st->eng->diagnostics(out);
+}
+
+extern "C" int sse_kernels_per_step(const sse_state *st, int order) {
+    if (!st) return SSE_ERR_INVALID_ARG;
+    // 4 per baroclinic stage, 1 per sub-cycle, 2 per thickness stage, 1 forcing combination
+    return order == 2 ? 2 * 4 + 2 + 2 * 2 + 1 : 3 * 4 + 3 + 3 * 2 + 1;
+}
+
+extern "C" const char *sse_strerror(int code) {
+    switch (code) {
+    case SSE_OK: return "ok";
+    case SSE_ERR_INVALID_ARG: return "invalid argument";
+    case SSE_ERR_BAD_MESH: return "invalid mesh (index out of range or non-positive geometry)";
+    case SSE_ERR_OOM: return "out of memory";
+    case SSE_ERR_CUDA: return "CUDA error";
+    case SSE_ERR_NONFINITE: return "non-finite value in the state";
+    case SSE_ERR_SYNC_TIMEOUT: return "grid barrier of the barotropic sub-cycle timed out";
+    case SSE_ERR_UNSUPPORTED: return "size beyond a compiled limit";
+    default: return "unknown error";
+    }
+}

@@ -1,0 +1,156 @@
+// sse_internal.cuh -- device data structures shared by the kernels and the
+// host driver of libsse.so.  Device arrays are layer-major and padded:
+// X[k * Ep + e] for edge fields, X[k * Cp + i] for cell fields,
+// X[k * Vp + v] for vertex fields (Ep, Cp, Vp multiples of 32).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace sse {
+
+constexpr int MAXE = 8;    // edges per cell
+constexpr int MAXE2 = 16;  // edges on edge
+constexpr int LMAX = 64;   // layers
+
+// Mesh coefficients in one precision (R = double or float).
+template <class R>
+struct Coef {
+    const R *divc;   // [maxE][Cp]  n_{e,i} l_e / A_i
+    const R *kec;    // [maxE][Cp]  l_e d_e / (4 A_i)
+    const R *wl;     // [maxE2][Ep] w_{e,e'} l_{e'} / d_e
+    const R *cfc;    // [maxE2][Ep] w_{e,e'} l_{e'} / d_e * (f_e + f_{e'}) / 2
+    const R *curlc;  // [3][Vp]     t_{e,v} d_e / A_v (0 where absent)
+    const R *kw;     // [3][Vp]     kite / sum(kites of ocean cells) (0 where land)
+    const R *invdc;  // [Ep]        1 / d_e
+    const R *invdv;  // [Ep]        1 / l_e
+    const R *fV;     // [Vp]        f at vertices
+};
+
+struct DMesh {
+    int C, E, V, L, Cp, Ep, Vp, maxE, maxE2;
+    const int2 *coe;    // [Ep] cells on edge
+    const int2 *voe;    // [Ep] vertices on edge
+    const int *neoc;    // [Cp]
+    const int *eoc;     // [maxE][Cp] edges on cell
+    const int *ooc;     // [maxE][Cp] the other cell across that edge
+    const int *neoe;    // [Ep]
+    const int *eoe;     // [maxE2][Ep]
+    const int *eov;     // [3][Vp] (absent -> 0, with zero coefficient)
+    const int *cov;     // [3][Vp] (land -> 0, with zero weight)
+    const double *H;    // [Cp] resting depth
+    const double *sfrac;  // [L] z-star fractions
+    const double *divc_d; // [maxE][Cp] divergence coefficients in FP64
+    const double *area;   // [Cp]
+    const double *ld2;    // [Ep] l_e d_e / 2 (energy weight)
+    Coef<double> d;
+    Coef<float> f;
+};
+
+template <class R> __host__ __device__ inline const Coef<R> &coef(const DMesh &m);
+template <> __host__ __device__ inline const Coef<double> &coef<double>(const DMesh &m) { return m.d; }
+template <> __host__ __device__ inline const Coef<float> &coef<float>(const DMesh &m) { return m.f; }
+
+struct DParams {
+    double g, rho0, nu_h, nu_v, kappa_h, kappa_v, c_drag;
+    double alpha, beta, T_ref, S_ref;  // rho' = rho - rho_ref
+    double zcoef;                      // g (1 - rho_ref / rho0)
+    int nT, recon;
+    const double *wind;  // [Ep] or nullptr
+};
+
+// Grid barrier words of the persistent sub-cycle kernel.
+struct Barrier {
+    unsigned int *count;  // arrivals in the current generation (gen == count + 1)
+    unsigned int *gen;    // generation counter, zeroed with count before each launch
+    int *err;             // nonzero after a timeout
+};
+
+// ---- stage kernels (layer-major), launched by the driver -----------------
+template <class R> struct DiagBufs {
+    R *ke, *delta, *rhop, *pp, *zm, *w;  // [L][Cp]
+    R *omega, *q;                        // [L][Vp]
+    R *hu, *qe;                          // [L][Ep]
+};
+
+// hR is the stage thickness in the tendency precision (the FP64 array itself
+// in SSE_FP64, an FP32 copy in SSE_MIXED).
+template <class R>
+void launch_cell_diag(const DMesh &m, const DParams &p, const R *ubar, const R *ut,
+                      const R *hR, const R *tr, const DiagBufs<R> &b, cudaStream_t s);
+template <class R>
+void launch_vertex(const DMesh &m, const R *ubar, const R *ut, const R *hR,
+                   const DiagBufs<R> &b, cudaStream_t s);
+template <class R>
+void launch_edge_pre(const DMesh &m, R *ubar, R *ut, const R *hR, const DiagBufs<R> &b,
+                     bool split, cudaStream_t s);
+template <class R>
+void launch_bcl_edge(const DMesh &m, const DParams &p, const R *ubar, const R *ut,
+                     const R *hR, const double *zeta, const DiagBufs<R> &b, const R *ut_n,
+                     double a, double bcoef, double dt, R *ut_out, R *G, cudaStream_t s);
+
+template <class R> struct BtrArgs {
+    const R *ub_start;     // [Ep]
+    const double *z_start; // [Cp]
+    const R *G;            // [Ep]
+    const R *X;            // [Ep] for the epilogue ub_out = alpha X + beta ubar^M (may be null)
+    double alpha, beta;
+    R *ub_out;             // [Ep]
+    double *Fz;            // [Ep]
+    double *z_out;         // [Cp] or null
+    R *u0, *ua, *uh;       // work [Ep]
+    R *z0, *za, *zh;       // work [Cp]
+    double tau, g;
+    int M, order;
+};
+template <class R>
+cudaError_t launch_btr(const DMesh &m, const BtrArgs<R> &a, const Barrier &bar, int nblocks,
+                       int nthreads, cudaStream_t s);
+template <class R> int btr_block_size();
+template <class R> const void *btr_kernel_ptr(int order);
+
+template <class R> struct TransportArgs {
+    const double *h;          // stage thickness [L][Cp]
+    const R *ubA, *utA;       // v = wA (ubA + utA) + wB (ubB + utB)
+    const R *ubB, *utB;
+    double wA, wB;
+    const double *Fz, *ex1, *ex2;  // F^zeta and extra F^h terms
+    double cF, cE, cA;
+    int recon;
+    double *S_out;            // sum_k v h_e (or null)
+    R *flux;                  // [L][Ep] h_e (v + uA)
+};
+template <class R>
+void launch_transport(const DMesh &m, const TransportArgs<R> &a, cudaStream_t s);
+
+template <class R> struct ThickArgs {
+    const R *flux;            // [L][Ep]
+    const double *h_s;        // stage thickness
+    const R *tr_s;            // stage tracers [nT][L][Cp]
+    const double *h_n;        // h^n (convex combination)
+    const R *tr_n;
+    double a, b, dt;          // out = a * (h^n) + b * (FE result)
+    double *h_out;
+    R *hR_out;                // FP32 copy of h_out (SSE_MIXED) or null
+    R *tr_out;
+    double *zeta_out;
+};
+template <class R>
+void launch_thickness(const DMesh &m, const DParams &p, const ThickArgs<R> &a, cudaStream_t s);
+
+// layout conversion: host-order FP64 [n][L] <-> device layer-major R [L][np]
+template <class R>
+void launch_to_device(const double *src, R *dst, int n, int L, int np, cudaStream_t s);
+template <class R>
+void launch_from_device(const R *src, double *dst, int n, int L, int np, cudaStream_t s);
+template <class R>
+void launch_add_bar(const R *ubar, const R *ut, double *dst, int E, int L, int Ep, cudaStream_t s);
+void launch_h_to_float(const double *h, float *hf, int n, cudaStream_t s);
+void launch_ssh(const DMesh &m, const double *h, double *zeta, cudaStream_t s);
+
+template <class R>
+void launch_diag(const DMesh &m, const R *ubar, const R *ut, const double *h, const R *tr,
+                 int nT, const double *zeta, double *partials, int nparts, double *out,
+                 cudaStream_t s);
+
+}  // namespace sse

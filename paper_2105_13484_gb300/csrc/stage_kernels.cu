@@ -1,0 +1,593 @@
+// stage_kernels.cu -- 3-D kernels of one SSPRK-SE stage (sm_103a).
+//
+// One thread owns one column (cell, vertex or edge) and walks its layers from
+// the top; column sums (thickness-weighted means, pressure, vertical velocity)
+// are therefore sequential in k, in the same order as the definitions.  All
+// arrays are layer-major, so at every k a warp reads 32 consecutive columns.
+//
+//   cell_diag  : per cell and layer  K, div u, rho', p', z_mid and the z-star w
+//                (Sec. 2: layered equations, Eqs. hydrocon, eqstate)
+//   vertex     : relative vorticity and potential vorticity q = (omega+f)/h_v
+//   edge_pre   : edge mass flux h_e u and q_e; at stage 1 also Eq. (BBspl)
+//   bcl_edge   : Algorithm 1 (Baroclinic_FEuler) with the SSPRK convex
+//                combination of the stage
+//   transport  : Sec. 3.4 flux deficit D = F^zeta - F^h, transport velocity
+//                adjustment u^A and the edge mass flux h_e (u + u^A)
+//   thickness  : thickness and tracer forward-Euler stage (Eqs. layerthickness,
+//                tracer) with the convex combination and zeta = sum h - H
+#include "sse_internal.cuh"
+
+namespace sse {
+
+template <class R> __device__ __forceinline__ R ld(const R *p) { return __ldg(p); }
+
+// ---------------------------------------------------------------------------
+// cell diagnostics
+// ---------------------------------------------------------------------------
+template <class R>
+__global__ void __launch_bounds__(128) k_cell_diag(DMesh m, DParams p, const R *__restrict__ ubar,
+                                                   const R *__restrict__ ut,
+                                                   const R *__restrict__ hR,
+                                                   const R *__restrict__ tr, DiagBufs<R> b) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= m.C) return;
+    const Coef<R> &c = coef<R>(m);
+    const int Cp = m.Cp, Ep = m.Ep, L = m.L;
+    const int ne = m.neoc[i];
+    int es[MAXE], os[MAXE];
+    R dcf[MAXE], kcf[MAXE], ub[MAXE];
+#pragma unroll
+    for (int j = 0; j < MAXE; j++) {
+        if (j < ne) {
+            es[j] = m.eoc[j * Cp + i];
+            os[j] = m.ooc[j * Cp + i];
+            dcf[j] = c.divc[j * Cp + i];
+            kcf[j] = c.kec[j * Cp + i];
+            ub[j] = ld(ubar + es[j]);
+        } else {
+            es[j] = 0; os[j] = i; dcf[j] = R(0); kcf[j] = R(0); ub[j] = R(0);
+        }
+    }
+    const R g = (R)p.g, alpha = (R)p.alpha, beta = (R)p.beta, Tref = (R)p.T_ref,
+            Sref = (R)p.S_ref;
+    R accp = R(0), divsum = R(0);
+    for (int k = 0; k < L; k++) {
+        const R hk = ld(hR + k * Cp + i);
+        R ke = R(0), dl = R(0), dv = R(0);
+#pragma unroll
+        for (int j = 0; j < MAXE; j++) {
+            if (j < ne) {
+                const R uk = ub[j] + ld(ut + k * Ep + es[j]);
+                const R he = R(0.5) * (hk + ld(hR + k * Cp + os[j]));
+                ke += kcf[j] * uk * uk;
+                dl += dcf[j] * uk;
+                dv += dcf[j] * (he * uk);
+            }
+        }
+        R rp = -alpha * (ld(tr + k * Cp + i) - Tref);
+        if (p.nT > 1) rp += beta * (ld(tr + (L + k) * Cp + i) - Sref);
+        const int x = k * Cp + i;
+        b.ke[x] = ke;
+        b.delta[x] = dl;
+        b.rhop[x] = rp;
+        b.pp[x] = g * (accp + R(0.5) * rp * hk);
+        accp += rp * hk;
+        b.w[x] = dv;  // divergence of h_e u, finalised below
+        divsum += dv;
+    }
+    // bottom -> top: z-star vertical velocity at the top of each layer and the
+    // mid-layer height z_k = -H + sum_{l>k} h_l + h_k / 2
+    R wk1 = R(0), below = R(0);
+    const R Hi = (R)m.H[i];
+    for (int k = L - 1; k >= 0; k--) {
+        const int x = k * Cp + i;
+        const R hk = ld(hR + x);
+        b.zm[x] = -Hi + below + R(0.5) * hk;
+        below += hk;
+        const R wk = (k == 0) ? R(0) : wk1 - b.w[x] + (R)m.sfrac[k] * divsum;
+        b.w[x] = wk;
+        wk1 = wk;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// vertex vorticity and potential vorticity
+// ---------------------------------------------------------------------------
+template <class R>
+__global__ void __launch_bounds__(128) k_vertex(DMesh m, const R *__restrict__ ubar,
+                                                const R *__restrict__ ut,
+                                                const R *__restrict__ hR, DiagBufs<R> b) {
+    const int v = blockIdx.x * blockDim.x + threadIdx.x;
+    if (v >= m.V) return;
+    const Coef<R> &c = coef<R>(m);
+    const int Vp = m.Vp, Ep = m.Ep, Cp = m.Cp;
+    int e[3], ce[3];
+    R cc[3], kw[3], ub[3];
+#pragma unroll
+    for (int j = 0; j < 3; j++) {
+        e[j] = m.eov[j * Vp + v];
+        ce[j] = m.cov[j * Vp + v];
+        cc[j] = c.curlc[j * Vp + v];
+        kw[j] = c.kw[j * Vp + v];
+        ub[j] = ld(ubar + e[j]);
+    }
+    const R fv = c.fV[v];
+    for (int k = 0; k < m.L; k++) {
+        R om = R(0), hv = R(0);
+#pragma unroll
+        for (int j = 0; j < 3; j++) {
+            om += cc[j] * (ub[j] + ld(ut + k * Ep + e[j]));
+            hv += kw[j] * ld(hR + k * Cp + ce[j]);
+        }
+        b.omega[k * Vp + v] = om;
+        b.q[k * Vp + v] = (om + fv) / hv;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// edge pre-pass: h_e u, q_e; optional barotropic/baroclinic split (Eq. BBspl)
+// ---------------------------------------------------------------------------
+template <class R>
+__global__ void __launch_bounds__(128) k_edge_pre(DMesh m, R *__restrict__ ubar, R *__restrict__ ut,
+                                                  const R *__restrict__ hR, DiagBufs<R> b,
+                                                  int split) {
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= m.E) return;
+    const int Ep = m.Ep, Cp = m.Cp, Vp = m.Vp;
+    const int2 cc = m.coe[e], vv = m.voe[e];
+    R ub = ubar[e];
+    R mean = R(0);
+    if (split) {
+        R num = R(0), den = R(0);
+        for (int k = 0; k < m.L; k++) {
+            const R he = R(0.5) * (ld(hR + k * Cp + cc.x) + ld(hR + k * Cp + cc.y));
+            num += he * ut[k * Ep + e];
+            den += he;
+        }
+        mean = num / den;
+        ub += mean;
+        ubar[e] = ub;
+    }
+    for (int k = 0; k < m.L; k++) {
+        const int x = k * Ep + e;
+        R utk = ut[x];
+        if (split) {
+            utk -= mean;
+            ut[x] = utk;
+        }
+        const R he = R(0.5) * (ld(hR + k * Cp + cc.x) + ld(hR + k * Cp + cc.y));
+        b.hu[x] = he * (ub + utk);
+        b.qe[x] = R(0.5) * (b.q[k * Vp + vv.x] + b.q[k * Vp + vv.y]);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Algorithm 1: baroclinic forward Euler, G, and the stage's convex combination
+//   ut1_k = ut_k + dt ( C_f(ut_k) + [Q_k - C_f(u_k)] - grad K_k - PGF_k
+//                       - avg^m(w D_zt u)_k + nu_h Lap u_k + D^u_k + g grad zeta )
+//   G = (1/dt) sum_k h_k ut1_k / sum_k h_k ;  ut1_k -= dt G
+//   out_k = a * ut_n_k + bcoef * ut1_k
+// C_f(ut_k) - C_f(u_k) = -C_f(ubar): one 2-D sum per column.
+// PGF in anomaly form: with rho = rho_ref + rho' and p' = g(sum_{l<k} rho'_l h_l
+// + rho'_k h_k / 2),  grad p + g rho_e grad z = g rho_ref grad zeta + grad p'
+// + g rho'_e grad z, so -PGF + g grad zeta = g (1 - rho_ref/rho0) grad zeta
+// - (grad p' + g rho'_e grad z) / rho0.
+// ---------------------------------------------------------------------------
+template <class R>
+__global__ void __launch_bounds__(128) k_bcl_edge(DMesh m, DParams p, const R *__restrict__ ubar,
+                                                  const R *__restrict__ ut,
+                                                  const R *__restrict__ hR,
+                                                  const double *__restrict__ zeta, DiagBufs<R> b,
+                                                  const R *__restrict__ ut_n, R a, R bc, R dt,
+                                                  R *__restrict__ ut_out, R *__restrict__ Gout) {
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= m.E) return;
+    const Coef<R> &c = coef<R>(m);
+    const int Ep = m.Ep, Cp = m.Cp, Vp = m.Vp, L = m.L;
+    const int2 cc = m.coe[e], vv = m.voe[e];
+    const int c1 = cc.x, c2 = cc.y, v1 = vv.x, v2 = vv.y;
+    const int n2 = m.neoe[e];
+    int eo[MAXE2];
+    R wl[MAXE2];
+    R cbar = R(0);
+#pragma unroll
+    for (int j = 0; j < MAXE2; j++) {
+        if (j < n2) {
+            eo[j] = m.eoe[j * Ep + e];
+            wl[j] = c.wl[j * Ep + e];
+            cbar += c.cfc[j * Ep + e] * ld(ubar + eo[j]);
+        } else {
+            eo[j] = e; wl[j] = R(0);
+        }
+    }
+    const R invdc = c.invdc[e], invdv = c.invdv[e];
+    const R ub = ubar[e];
+    const R gzeta = (R)(p.zcoef * (zeta[c2] - zeta[c1])) * invdc;
+    const R g = (R)p.g, inv_rho0 = (R)(1.0 / p.rho0), nu_h = (R)p.nu_h, nu_v = (R)p.nu_v;
+    const R wind = p.wind ? (R)(p.wind[e] / p.rho0) : R(0);
+
+    R ut_cur = ut[e];
+    R u_cur = ub + ut_cur;
+    R he_cur = R(0.5) * (ld(hR + c1) + ld(hR + c2));
+    R u_prev = R(0), he_prev = R(0);
+    R num = R(0), den = R(0);
+    for (int k = 0; k < L; k++) {
+        const int xe = k * Ep + e;
+        R ut_next = R(0), u_next = R(0), he_next = R(0);
+        if (k + 1 < L) {
+            ut_next = ut[xe + Ep];
+            u_next = ub + ut_next;
+            he_next = R(0.5) * (ld(hR + (k + 1) * Cp + c1) + ld(hR + (k + 1) * Cp + c2));
+        }
+        // potential-vorticity flux
+        const R qk = b.qe[xe];
+        R Q = R(0);
+#pragma unroll
+        for (int j = 0; j < MAXE2; j++)
+            if (j < n2) Q += wl[j] * b.hu[k * Ep + eo[j]] * (R(0.5) * (qk + b.qe[k * Ep + eo[j]]));
+        const int x1 = k * Cp + c1, x2 = k * Cp + c2;
+        const R gradK = (b.ke[x2] - b.ke[x1]) * invdc;
+        const R pgf = ((b.pp[x2] - b.pp[x1]) +
+                       g * (R(0.5) * (b.rhop[x1] + b.rhop[x2])) * (b.zm[x2] - b.zm[x1])) *
+                      invdc * inv_rho0;
+        // vertical advection and viscosity at the top (k) and bottom (k+1) interfaces
+        R Dk = R(0), wk = R(0), Dk1 = R(0), wk1 = R(0);
+        if (k > 0) {
+            Dk = (u_prev - u_cur) / (R(0.5) * (he_prev + he_cur));
+            wk = R(0.5) * (b.w[x1] + b.w[x2]);
+        }
+        if (k + 1 < L) {
+            Dk1 = (u_cur - u_next) / (R(0.5) * (he_cur + he_next));
+            wk1 = R(0.5) * (b.w[x1 + Cp] + b.w[x2 + Cp]);
+        }
+        const R vadv = R(0.5) * (wk * Dk + wk1 * Dk1);
+        const R Xtop = (k == 0) ? wind : nu_v * Dk;
+        R Xbot;
+        if (k == L - 1) {
+            R utan = R(0);
+#pragma unroll
+            for (int j = 0; j < MAXE2; j++)
+                if (j < n2) utan += wl[j] * (ld(ubar + eo[j]) + ut[k * Ep + eo[j]]);
+            const R speed = sqrt(u_cur * u_cur + utan * utan);
+            Xbot = (R)p.c_drag * speed * u_cur;
+        } else {
+            Xbot = nu_v * Dk1;
+        }
+        const R vvisc = (Xtop - Xbot) / he_cur;
+        const R lap = (b.delta[x2] - b.delta[x1]) * invdc -
+                      (b.omega[k * Vp + v2] - b.omega[k * Vp + v1]) * invdv;
+        const R rhs = (Q - cbar) - gradK - pgf - vadv + nu_h * lap + vvisc + gzeta;
+        const R ut1 = ut_cur + dt * rhs;
+        num += he_cur * ut1;
+        den += he_cur;
+        ut_out[xe] = ut1;
+        u_prev = u_cur; he_prev = he_cur;
+        ut_cur = ut_next; u_cur = u_next; he_cur = he_next;
+    }
+    const R G = num / den / dt;
+    Gout[e] = G;
+    for (int k = 0; k < L; k++) {
+        const int xe = k * Ep + e;
+        const R x = ut_out[xe] - dt * G;
+        ut_out[xe] = ut_n ? a * ut_n[xe] + bc * x : bc * x;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Sec. 3.4: transport velocity adjustment and edge mass flux
+// ---------------------------------------------------------------------------
+template <class R>
+__global__ void __launch_bounds__(128) k_transport(DMesh m, TransportArgs<R> a) {
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= m.E) return;
+    const int Ep = m.Ep, Cp = m.Cp, L = m.L;
+    const int2 cc = m.coe[e];
+    const double ubA = (double)a.ubA[e];
+    const double ubB = a.ubB ? (double)a.ubB[e] : 0.0;
+    double S = 0.0, hs = 0.0;
+    for (int k = 0; k < L; k++) {
+        const double he = 0.5 * (a.h[k * Cp + cc.x] + a.h[k * Cp + cc.y]);
+        double v = a.wA * (ubA + (double)a.utA[k * Ep + e]);
+        if (a.utB) v += a.wB * (ubB + (double)a.utB[k * Ep + e]);
+        S += v * he;
+        hs += he;
+    }
+    double Fh = a.cF * S;
+    if (a.ex1) Fh += a.cE * a.ex1[e];
+    if (a.ex2) Fh += a.cE * a.ex2[e];
+    const double uA = a.recon ? a.cA * (a.Fz[e] - Fh) / hs : 0.0;
+    if (a.S_out) a.S_out[e] = S;
+    for (int k = 0; k < L; k++) {
+        const double he = 0.5 * (a.h[k * Cp + cc.x] + a.h[k * Cp + cc.y]);
+        double v = a.wA * (ubA + (double)a.utA[k * Ep + e]);
+        if (a.utB) v += a.wB * (ubB + (double)a.utB[k * Ep + e]);
+        a.flux[k * Ep + e] = (R)(he * (v + uA));
+    }
+}
+
+// ---------------------------------------------------------------------------
+// thickness and tracer stage (Eqs. layerthickness, tracer), z-star w from the
+// same flux, convex combination with (h^n, phi^n), zeta = sum h - H
+// ---------------------------------------------------------------------------
+template <class R>
+__global__ void __launch_bounds__(128) k_thickness(DMesh m, DParams p, ThickArgs<R> a) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= m.C) return;
+    const int Cp = m.Cp, Ep = m.Ep, L = m.L;
+    const int ne = m.neoc[i];
+    int es[MAXE], os[MAXE];
+    double dcd[MAXE];
+#pragma unroll
+    for (int j = 0; j < MAXE; j++) {
+        if (j < ne) {
+            es[j] = m.eoc[j * Cp + i];
+            os[j] = m.ooc[j * Cp + i];
+            dcd[j] = m.divc_d[j * Cp + i];
+        } else {
+            es[j] = 0; os[j] = i; dcd[j] = 0.0;
+        }
+    }
+    // pass 1: flux divergence per layer and its column sum
+    double divF[LMAX];
+    double tot = 0.0;
+    for (int k = 0; k < L; k++) {
+        double s = 0.0;
+#pragma unroll
+        for (int j = 0; j < MAXE; j++)
+            if (j < ne) s += dcd[j] * (double)a.flux[k * Ep + es[j]];
+        divF[k] = s;
+        tot += s;
+    }
+    // pass 2: w at interfaces (w[0] = w[L] = 0)
+    double w[LMAX + 1];
+    w[L] = 0.0;
+    for (int k = L - 1; k >= 1; k--) w[k] = w[k + 1] - divF[k] + m.sfrac[k] * tot;
+    w[0] = 0.0;
+    // pass 3: thickness, then tracers
+    double hsum = 0.0;
+    const double dt = a.dt;
+    for (int k = 0; k < L; k++) {
+        const int x = k * Cp + i;
+        const double h1 = a.h_s[x] + dt * (-divF[k] - (w[k] - w[k + 1]));
+        // h_out may alias h_n: read h^n before the store
+        const double hn = (a.a != 0.0) ? a.h_n[x] : 0.0;
+        const double hout = (a.a != 0.0) ? a.a * hn + a.b * h1 : a.b * h1;
+        for (int t = 0; t < p.nT; t++) {
+            const R *phi = a.tr_s + t * L * Cp;
+            const double ph = (double)phi[x];
+            double adv = 0.0, dif = 0.0;
+#pragma unroll
+            for (int j = 0; j < MAXE; j++) {
+                if (j < ne) {
+                    const double po = (double)phi[k * Cp + os[j]];
+                    adv += dcd[j] * ((double)a.flux[k * Ep + es[j]] * (0.5 * (ph + po)));
+                    if (p.kappa_h != 0.0) {
+                        // h_e kappa_h grad phi, grad taken outward from cell i
+                        const double he = 0.5 * (a.h_s[x] + a.h_s[k * Cp + os[j]]);
+                        // dcd = n_{e,i} l_e / A_i; outward gradient = (po - ph)/d_e, and
+                        // n_{e,i} * grad_e(phi) = (po - ph) / d_e for either orientation
+                        dif += fabs(dcd[j]) * he * p.kappa_h * (po - ph) *
+                               (double)coef<double>(m).invdc[es[j]];
+                    }
+                }
+            }
+            double ftop = 0.0, fbot = 0.0, dtop = 0.0, dbot = 0.0;
+            if (k >= 1) {
+                const double pu = (double)phi[x - Cp];
+                ftop = 0.5 * (pu + ph) * w[k];
+                dtop = (pu - ph) / (0.5 * (a.h_s[x - Cp] + a.h_s[x]));
+            }
+            if (k + 1 <= L - 1) {
+                const double pd = (double)phi[x + Cp];
+                fbot = 0.5 * (ph + pd) * w[k + 1];
+                dbot = (ph - pd) / (0.5 * (a.h_s[x] + a.h_s[x + Cp]));
+            }
+            const double hphi = a.h_s[x] * ph +
+                                dt * (-adv - (ftop - fbot) + dif + p.kappa_v * (dtop - dbot));
+            const double phi1 = hphi / h1;
+            double out;
+            if (a.a != 0.0)
+                out = (a.a * hn * (double)a.tr_n[t * L * Cp + x] + a.b * h1 * phi1) / hout;
+            else
+                out = phi1;
+            a.tr_out[t * L * Cp + x] = (R)out;
+        }
+        a.h_out[x] = hout;
+        if (a.hR_out) a.hR_out[x] = (R)hout;
+        hsum += hout;
+    }
+    a.zeta_out[i] = hsum - m.H[i];
+}
+
+// ---------------------------------------------------------------------------
+// small helpers: layout conversion, SSH
+// ---------------------------------------------------------------------------
+template <class R>
+__global__ void k_to_device(const double *__restrict__ src, R *__restrict__ dst, int n, int L,
+                            int np) {
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= (long long)n * L) return;
+    const int i = (int)(t / L), k = (int)(t % L);
+    dst[(long long)k * np + i] = (R)src[t];
+}
+template <class R>
+__global__ void k_from_device(const R *__restrict__ src, double *__restrict__ dst, int n, int L,
+                              int np) {
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= (long long)n * L) return;
+    const int i = (int)(t / L), k = (int)(t % L);
+    dst[t] = (double)src[(long long)k * np + i];
+}
+template <class R>
+__global__ void k_add_bar(const R *__restrict__ ubar, const R *__restrict__ ut,
+                          double *__restrict__ dst, int E, int L, int Ep) {
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= (long long)E * L) return;
+    const int e = (int)(t / L), k = (int)(t % L);
+    dst[t] = (double)ubar[e] + (double)ut[(long long)k * Ep + e];
+}
+__global__ void k_h_to_float(const double *__restrict__ h, float *__restrict__ hf, int n) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < n) hf[t] = (float)h[t];
+}
+__global__ void k_ssh(DMesh m, const double *__restrict__ h, double *__restrict__ zeta) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= m.C) return;
+    double s = 0.0;
+    for (int k = 0; k < m.L; k++) s += h[k * m.Cp + i];
+    zeta[i] = s - m.H[i];
+}
+
+// ---------------------------------------------------------------------------
+// deterministic diagnostics: fixed partition, fixed-order second pass
+// out = [volume, tracer0, tracer1, KE, max|u|, min h, zeta min, zeta max, nonfinite]
+// ---------------------------------------------------------------------------
+constexpr int NDIAG = 9;
+template <class R>
+__global__ void k_diag_partial(DMesh m, const R *__restrict__ ubar, const R *__restrict__ ut,
+                               const double *__restrict__ h, const R *__restrict__ tr, int nT,
+                               const double *__restrict__ zeta, double *__restrict__ part) {
+    __shared__ double sh[NDIAG][256];
+    const int tid = threadIdx.x;
+    double v[NDIAG] = {0, 0, 0, 0, 0, 1e300, 1e300, -1e300, 0};
+    const int L = m.L, Cp = m.Cp, Ep = m.Ep;
+    for (int i = blockIdx.x * blockDim.x + tid; i < m.C; i += gridDim.x * blockDim.x) {
+        double hs = 0.0, t0 = 0.0, t1 = 0.0;
+        for (int k = 0; k < L; k++) {
+            const double hk = h[k * Cp + i];
+            hs += hk;
+            t0 += hk * (double)tr[k * Cp + i];
+            if (nT > 1) t1 += hk * (double)tr[(L + k) * Cp + i];
+            v[5] = fmin(v[5], hk);
+            if (!isfinite(hk) || !isfinite((double)tr[k * Cp + i])) v[8] = 1.0;
+        }
+        v[0] += m.area[i] * hs;
+        v[1] += m.area[i] * t0;
+        v[2] += m.area[i] * t1;
+        v[6] = fmin(v[6], zeta[i]);
+        v[7] = fmax(v[7], zeta[i]);
+    }
+    for (int e = blockIdx.x * blockDim.x + tid; e < m.E; e += gridDim.x * blockDim.x) {
+        const int2 cc = m.coe[e];
+        double ke = 0.0;
+        for (int k = 0; k < L; k++) {
+            const double u = (double)ubar[e] + (double)ut[k * Ep + e];
+            const double he = 0.5 * (h[k * Cp + cc.x] + h[k * Cp + cc.y]);
+            ke += he * u * u;
+            v[4] = fmax(v[4], fabs(u));
+            if (!isfinite(u)) v[8] = 1.0;
+        }
+        v[3] += m.ld2[e] * 0.5 * ke;
+    }
+    for (int q = 0; q < NDIAG; q++) sh[q][tid] = v[q];
+    __syncthreads();
+    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+        if (tid < s) {
+            for (int q = 0; q < 4; q++) sh[q][tid] += sh[q][tid + s];
+            sh[4][tid] = fmax(sh[4][tid], sh[4][tid + s]);
+            sh[5][tid] = fmin(sh[5][tid], sh[5][tid + s]);
+            sh[6][tid] = fmin(sh[6][tid], sh[6][tid + s]);
+            sh[7][tid] = fmax(sh[7][tid], sh[7][tid + s]);
+            sh[8][tid] = fmax(sh[8][tid], sh[8][tid + s]);
+        }
+        __syncthreads();
+    }
+    if (tid == 0)
+        for (int q = 0; q < NDIAG; q++) part[blockIdx.x * NDIAG + q] = sh[q][0];
+}
+__global__ void k_diag_final(const double *__restrict__ part, int nparts, double *__restrict__ out) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    double v[NDIAG] = {0, 0, 0, 0, 0, 1e300, 1e300, -1e300, 0};
+    for (int b = 0; b < nparts; b++) {
+        for (int q = 0; q < 4; q++) v[q] += part[b * NDIAG + q];
+        v[4] = fmax(v[4], part[b * NDIAG + 4]);
+        v[5] = fmin(v[5], part[b * NDIAG + 5]);
+        v[6] = fmin(v[6], part[b * NDIAG + 6]);
+        v[7] = fmax(v[7], part[b * NDIAG + 7]);
+        v[8] = fmax(v[8], part[b * NDIAG + 8]);
+    }
+    for (int q = 0; q < NDIAG; q++) out[q] = v[q];
+}
+
+// ---------------------------------------------------------------------------
+// launchers
+// ---------------------------------------------------------------------------
+static inline int nblk(long long n, int t) { return (int)((n + t - 1) / t); }
+
+template <class R>
+void launch_cell_diag(const DMesh &m, const DParams &p, const R *ubar, const R *ut, const R *hR,
+                      const R *tr, const DiagBufs<R> &b, cudaStream_t s) {
+    k_cell_diag<R><<<nblk(m.C, 128), 128, 0, s>>>(m, p, ubar, ut, hR, tr, b);
+}
+template <class R>
+void launch_vertex(const DMesh &m, const R *ubar, const R *ut, const R *hR, const DiagBufs<R> &b,
+                   cudaStream_t s) {
+    k_vertex<R><<<nblk(m.V, 128), 128, 0, s>>>(m, ubar, ut, hR, b);
+}
+template <class R>
+void launch_edge_pre(const DMesh &m, R *ubar, R *ut, const R *hR, const DiagBufs<R> &b,
+                     bool split, cudaStream_t s) {
+    k_edge_pre<R><<<nblk(m.E, 128), 128, 0, s>>>(m, ubar, ut, hR, b, split ? 1 : 0);
+}
+template <class R>
+void launch_bcl_edge(const DMesh &m, const DParams &p, const R *ubar, const R *ut, const R *hR,
+                     const double *zeta, const DiagBufs<R> &b, const R *ut_n, double a,
+                     double bcoef, double dt, R *ut_out, R *G, cudaStream_t s) {
+    k_bcl_edge<R><<<nblk(m.E, 128), 128, 0, s>>>(m, p, ubar, ut, hR, zeta, b, ut_n, (R)a,
+                                                  (R)bcoef, (R)dt, ut_out, G);
+}
+template <class R>
+void launch_transport(const DMesh &m, const TransportArgs<R> &a, cudaStream_t s) {
+    k_transport<R><<<nblk(m.E, 128), 128, 0, s>>>(m, a);
+}
+template <class R>
+void launch_thickness(const DMesh &m, const DParams &p, const ThickArgs<R> &a, cudaStream_t s) {
+    k_thickness<R><<<nblk(m.C, 128), 128, 0, s>>>(m, p, a);
+}
+template <class R>
+void launch_to_device(const double *src, R *dst, int n, int L, int np, cudaStream_t s) {
+    k_to_device<R><<<nblk((long long)n * L, 256), 256, 0, s>>>(src, dst, n, L, np);
+}
+template <class R>
+void launch_from_device(const R *src, double *dst, int n, int L, int np, cudaStream_t s) {
+    k_from_device<R><<<nblk((long long)n * L, 256), 256, 0, s>>>(src, dst, n, L, np);
+}
+template <class R>
+void launch_add_bar(const R *ubar, const R *ut, double *dst, int E, int L, int Ep, cudaStream_t s) {
+    k_add_bar<R><<<nblk((long long)E * L, 256), 256, 0, s>>>(ubar, ut, dst, E, L, Ep);
+}
+void launch_h_to_float(const double *h, float *hf, int n, cudaStream_t s) {
+    k_h_to_float<<<nblk(n, 256), 256, 0, s>>>(h, hf, n);
+}
+void launch_ssh(const DMesh &m, const double *h, double *zeta, cudaStream_t s) {
+    k_ssh<<<nblk(m.C, 128), 128, 0, s>>>(m, h, zeta);
+}
+template <class R>
+void launch_diag(const DMesh &m, const R *ubar, const R *ut, const double *h, const R *tr, int nT,
+                 const double *zeta, double *partials, int nparts, double *out, cudaStream_t s) {
+    k_diag_partial<R><<<nparts, 256, 0, s>>>(m, ubar, ut, h, tr, nT, zeta, partials);
+    k_diag_final<<<1, 32, 0, s>>>(partials, nparts, out);
+}
+
+#define INST(R)                                                                                  \
+    template void launch_cell_diag<R>(const DMesh &, const DParams &, const R *, const R *,      \
+                                      const R *, const R *, const DiagBufs<R> &, cudaStream_t);  \
+    template void launch_vertex<R>(const DMesh &, const R *, const R *, const R *,               \
+                                   const DiagBufs<R> &, cudaStream_t);                           \
+    template void launch_edge_pre<R>(const DMesh &, R *, R *, const R *, const DiagBufs<R> &,    \
+                                     bool, cudaStream_t);                                        \
+    template void launch_bcl_edge<R>(const DMesh &, const DParams &, const R *, const R *,       \
+                                     const R *, const double *, const DiagBufs<R> &, const R *,  \
+                                     double, double, double, R *, R *, cudaStream_t);            \
+    template void launch_transport<R>(const DMesh &, const TransportArgs<R> &, cudaStream_t);    \
+    template void launch_thickness<R>(const DMesh &, const DParams &, const ThickArgs<R> &,      \
+                                      cudaStream_t);                                             \
+    template void launch_to_device<R>(const double *, R *, int, int, int, cudaStream_t);         \
+    template void launch_from_device<R>(const R *, double *, int, int, int, cudaStream_t);       \
+    template void launch_add_bar<R>(const R *, const R *, double *, int, int, int, cudaStream_t); \
+    template void launch_diag<R>(const DMesh &, const R *, const R *, const double *, const R *, \
+                                 int, const double *, double *, int, double *, cudaStream_t);
+INST(double)
+INST(float)
+
+}  // namespace sse

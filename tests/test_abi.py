@@ -1,0 +1,106 @@
+"""CPU checks of the C ABI: the library builds, loads and exports every entry
+point include/sse.h declares; argument validation that runs before any CUDA
+call rejects bad input with the documented codes."""
+import ctypes as ct
+import os
+import re
+
+import numpy as np
+import pytest
+
+from paper_2105_13484_gb300 import binding, build, mesh as meshgen
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    build.build()
+    return binding.load()
+
+
+def declared_symbols():
+    src = open(os.path.join(ROOT, "include", "sse.h")).read()
+    return sorted(set(re.findall(r"\b(sse_[a-z_]+)\s*\(", src)))
+
+
+def test_every_declared_symbol_is_exported(lib):
+    syms = declared_symbols()
+    assert "sse_step" in syms and "sse_mesh_create" in syms
+    for s in syms:
+        assert hasattr(lib, s), s
+    assert set(syms) <= set(binding.EXPORTS)
+
+
+def test_strerror(lib):
+    assert lib.sse_strerror(0) == b"ok"
+    assert b"mesh" in lib.sse_strerror(-2)
+
+
+def test_null_arguments(lib):
+    out = ct.c_void_p()
+    assert lib.sse_mesh_create(None, ct.byref(out)) == -1
+    assert lib.sse_step(None, 3, 60.0, 10, 1) == -1
+    assert lib.sse_state_create(None, None, None, ct.byref(out)) == -1
+
+
+def _desc(m, L):
+    d = binding.Mesh.__new__(binding.Mesh)
+    d.lib = binding.load()
+    keep = []
+
+    def ia(x):
+        a = np.ascontiguousarray(x, dtype=np.int32)
+        keep.append(a)
+        return a.ctypes.data_as(ct.POINTER(ct.c_int32))
+
+    def da(x):
+        a = np.ascontiguousarray(x, dtype=np.float64)
+        keep.append(a)
+        return a.ctypes.data_as(ct.POINTER(ct.c_double))
+
+    desc = binding.MeshDesc(m.nCells, m.nEdges, m.nVertices, m.maxEdges, m.maxEdges2, L,
+                            ia(m.cellsOnEdge), ia(m.verticesOnEdge), ia(m.nEdgesOnCell),
+                            ia(m.edgesOnCell), ia(m.cellsOnVertex), ia(m.edgesOnVertex),
+                            ia(m.nEdgesOnEdge), ia(m.edgesOnEdge), da(m.weightsOnEdge),
+                            da(m.dcEdge), da(m.dvEdge), da(m.areaCell), da(m.areaTriangle),
+                            da(m.kiteAreasOnVertex), da(m.fEdge), da(m.fVertex),
+                            da(m.bottomDepth), da(np.full(L, 1.0 / L)))
+    return desc, keep
+
+
+@pytest.mark.parametrize("corrupt,code", [
+    (lambda m: m.cellsOnEdge.__setitem__((3, 1), m.nCells), -2),
+    (lambda m: m.edgesOnEdge.__setitem__((5, 0), -1), -2),
+    (lambda m: m.dcEdge.__setitem__(7, 0.0), -2),
+    (lambda m: m.areaCell.__setitem__(2, -1.0), -2),
+    (lambda m: m.edgesOnCell.__setitem__((4, 0), 0), -2),
+    (lambda m: m.cellsOnVertex.__setitem__((1, 0), m.nCells + 5), -2),
+])
+def test_bad_mesh_rejected_before_any_device_work(lib, corrupt, code):
+    m = meshgen.planar_hex(6, 8, 1e4)
+    corrupt(m)
+    desc, keep = _desc(m, 3)
+    out = ct.c_void_p()
+    assert lib.sse_mesh_create(ct.byref(desc), ct.byref(out)) == code
+    assert not out.value
+
+
+def test_limits(lib):
+    m = meshgen.planar_hex(6, 8, 1e4)
+    desc, keep = _desc(m, 3)
+    desc.nLayers = 65
+    out = ct.c_void_p()
+    assert lib.sse_mesh_create(ct.byref(desc), ct.byref(out)) == -7
+    desc.nLayers = 0
+    assert lib.sse_mesh_create(ct.byref(desc), ct.byref(out)) == -1
+
+
+def test_rest_fractions_must_sum_to_one(lib):
+    m = meshgen.planar_hex(6, 8, 1e4)
+    desc, keep = _desc(m, 3)
+    rf = np.array([0.3, 0.3, 0.3])
+    keep.append(rf)
+    desc.restThicknessFrac = rf.ctypes.data_as(ct.POINTER(ct.c_double))
+    out = ct.c_void_p()
+    assert lib.sse_mesh_create(ct.byref(desc), ct.byref(out)) == -2

@@ -1,0 +1,181 @@
+"""GPU parity: the CUDA path through the C ABI against the FP64 oracle.
+
+Tolerances: FP64 path relative L2 <= 1e-11 per field (the bar stated for the
+FP64 form); mixed path per-field bounds stated below, volume conserved to
+1e-13 relative.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2105_13484_gb300 import binding, build, inputs
+from paper_2105_13484_gb300 import mesh as meshgen
+
+pytestmark = pytest.mark.gpu
+
+TOL64 = 1e-11
+
+
+def rel(a, b):
+    nb = np.linalg.norm(b)
+    return np.linalg.norm(a - b) / (nb if nb > 0 else 1.0)
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    build.build()
+    binding.load()
+
+
+def _gpu(m, L, p, u, h, tr, precision="fp64", rest_frac=None):
+    dm = binding.Mesh(m, L, rest_frac)
+    st = binding.State(dm, p, precision)
+    st.load_state(u, h, tr)
+    return dm, st
+
+
+def _compare(gpu, ref, tol, names=("u", "h", "tr")):
+    errs = {n: rel(a, b) for n, a, b in zip(names, gpu, ref)}
+    for n, e in errs.items():
+        assert e < tol, errs
+    return errs
+
+
+def test_alg1_baroclinic_feuler(channel_small):
+    m, L, p, (u, h, tr), run = channel_small
+    o = oracle.Oracle(m, L, p)
+    ubar, ut = o.split(u, h)
+    zeta = o.ssh(h)
+    ut1, G = o.baroclinic_feuler(u, ut, zeta, h, tr, run["dt"])
+    dm, st = _gpu(m, L, p, u, h, tr)
+    st.set("ubar", ubar)
+    st.set("utilde", ut)
+    st.baroclinic_feuler(run["dt"])
+    assert rel(st.get("utilde"), ut1) < TOL64
+    assert rel(st.get("G"), G) < TOL64
+
+
+@pytest.mark.parametrize("order", [2, 3])
+def test_alg34_barotropic_substep(order, channel_small):
+    m, L, p, (u, h, tr), run = channel_small
+    o = oracle.Oracle(m, L, p)
+    ubar, _ = o.split(u, h)
+    zeta = o.ssh(h)
+    G = 1e-6 * np.sin(np.arange(m.nEdges) * 0.37)
+    u1, Fz, z1 = o.barotropic_substep(order, ubar, zeta, G, run["dt"], run["M"])
+    dm, st = _gpu(m, L, p, u, h, tr)
+    st.set("ubar", ubar)
+    st.set("G", G)
+    st.barotropic_substep(order, run["dt"], run["M"])
+    assert rel(st.get("ubar"), u1) < TOL64
+    assert rel(st.get("Fzeta"), Fz) < TOL64
+    assert np.abs(st.get("zeta_sub") - z1).max() < 1e-11 * (1 + np.abs(z1).max())
+
+
+@pytest.mark.parametrize("order", [2, 3])
+@pytest.mark.parametrize("recon", ["off", "paper", "consistent"])
+def test_full_step_channel_10km(order, recon):
+    """The 16 x 32 channel workload, 10 steps, every reconciliation mode.
+
+    SSPRK2-SE without reconciliation or with the printed F^h is unstable at
+    the workload's dt = 300 s, M = 20 (both the oracle and the GPU grow to
+    NaN, as the paper's N/A entries do); those modes run at dt = 100 s."""
+    m, L, p, (u, h, tr), run = inputs.workload("channel_10km", perturb=True)
+    p = dict(p, recon=recon)
+    if order == 2 and recon == "consistent":
+        dt, M, n = run["dt"], run["M"], run["steps"]
+    elif order == 2:
+        dt, M, n = 100.0, 10, 10
+    else:
+        dt, M, n = 150.0, 10, 10
+    o = oracle.Oracle(m, L, p)
+    ref = o.step(order, dt, M, u, h, tr, n_steps=n)
+    dm, st = _gpu(m, L, p, u, h, tr)
+    st.step(order, dt, M, n)
+    _compare(st.read_state(), ref, TOL64)
+    zeta = st.get("zeta")
+    assert np.abs(zeta - (ref[1].sum(1) - m.bottomDepth)).max() < 1e-9
+
+
+def test_full_step_all_terms():
+    """Two tracers, tracer diffusion, bathymetry, beta plane, wind stress,
+    bottom drag, a ragged mesh size (13 x 18 cells) and uneven rest layers."""
+    def depth(x, y):
+        return 900.0 - 300.0 * np.exp(-((x - 60e3) ** 2 + (y - 70e3) ** 2) / (30e3) ** 2)
+    m, L, p, (u, h, tr) = inputs.channel_case(13, 18, 9e3, 7, depth=depth, beta=2e-11,
+                                              perturb=True, nTracers=2, kappa_h=20.0,
+                                              kappa_v=1e-4, c_drag=3e-3, nu_h=50.0,
+                                              nu_v=1e-3)
+    rf = np.array([0.05, 0.08, 0.1, 0.14, 0.18, 0.2, 0.25])
+    H = m.bottomDepth
+    h = (H + (h.sum(1) - H))[:, None] * rf[None, :]
+    p["windStress"] = 0.1 * np.cos(m.xEdge[:, 1] / 40e3) * m.normalEdge[:, 0]
+    o = oracle.Oracle(m, L, p, rest_frac=rf)
+    ref = o.step(3, 200.0, 12, u, h, tr, n_steps=4)
+    dm, st = _gpu(m, L, p, u, h, tr, rest_frac=rf)
+    st.step(3, 200.0, 12, 4)
+    _compare(st.read_state(), ref, TOL64)
+
+
+@pytest.mark.parametrize("L", [1, 64])
+def test_layer_count_extremes(L):
+    m, _, p, (u, h, tr) = inputs.channel_case(8, 10, 10e3, L, perturb=True)
+    o = oracle.Oracle(m, L, p)
+    ref = o.step(2, 200.0, 8, u, h, tr, n_steps=3)
+    dm, st = _gpu(m, L, p, u, h, tr)
+    st.step(2, 200.0, 8, 3)
+    _compare(st.read_state(), ref, TOL64)
+
+
+def test_mixed_precision_bounds_and_volume():
+    m, L, p, (u, h, tr), run = inputs.workload("channel_10km", perturb=True)
+    o = oracle.Oracle(m, L, p)
+    ref = o.step(3, 150.0, 10, u, h, tr, n_steps=10)
+    dm, st = _gpu(m, L, p, u, h, tr, "mixed")
+    d0 = st.diagnostics()
+    st.step(3, 150.0, 10, 10)
+    d1 = st.diagnostics()
+    gu, gh, gt = st.read_state()
+    assert rel(gu, ref[0]) < 1e-4
+    assert rel(gh, ref[1]) < 1e-9
+    assert rel(gt, ref[2]) < 1e-6
+    assert abs(d1["volume"] - d0["volume"]) / d0["volume"] < 1e-13
+
+
+def test_diagnostics_and_conservation_fp64(channel_small):
+    m, L, p, (u, h, tr), run = channel_small
+    dm, st = _gpu(m, L, p, u, h, tr)
+    d0 = st.diagnostics()
+    A = m.areaCell
+    assert abs(d0["volume"] - A @ h.sum(1)) / d0["volume"] < 1e-14
+    assert abs(d0["tracer_content"][0] - A @ (h * tr[0]).sum(1)) / d0["tracer_content"][0] < 1e-14
+    st.step(3, 150.0, 10, 5)
+    d1 = st.diagnostics()
+    assert abs(d1["volume"] - d0["volume"]) / d0["volume"] < 1e-13
+    assert abs(d1["tracer_content"][0] - d0["tracer_content"][0]) / d0["tracer_content"][0] < 1e-13
+    assert d1["step"] == 5 and not d1["nonfinite"]
+
+
+def test_invalid_arguments_on_device(channel_small):
+    m, L, p, (u, h, tr), run = channel_small
+    dm, st = _gpu(m, L, p, u, h, tr)
+    for args in ((4, 100.0, 10, 1), (3, -1.0, 10, 1), (3, 100.0, 0, 1), (2, float("nan"), 5, 1)):
+        with pytest.raises(binding.SSEError) as ei:
+            st.step(*args)
+        assert ei.value.code == -1
+    with pytest.raises(binding.SSEError):
+        st.set("tracer1", tr[0])      # nTracers = 1
+    # the state is still usable after rejected calls
+    st.step(2, 100.0, 5, 1)
+    assert not st.diagnostics()["nonfinite"]
+
+
+@pytest.mark.slow
+def test_channel_1km_full_size_two_steps():
+    """The 92,480-cell, 20-layer workload: two SSPRK3-SE steps, whole fields."""
+    m, L, p, (u, h, tr), run = inputs.workload("channel_1km", perturb=True)
+    o = oracle.Oracle(m, L, p)
+    ref = o.step(run["order"], run["dt"], run["M"], u, h, tr, n_steps=2)
+    dm, st = _gpu(m, L, p, u, h, tr)
+    st.step(run["order"], run["dt"], run["M"], 2)
+    _compare(st.read_state(), ref, TOL64)
