@@ -1,0 +1,401 @@
+#!/usr/bin/env python
+"""Throughput of one SSPRK3-SE large step on the 92,480-cell channel.
+
+Workload (the synthetic stand-in for the paper's baroclinic-channel case):
+160 x 578 hexagonal cells at 1 km (160 km x 500 km), 20 z-star layers, beta
+plane, seeded temperature front, SSPRK3-SE with dt = 60 s and M = 30
+barotropic sub-steps, reconciliation "consistent".  A "step" is one large
+step: three baroclinic stages, three sub-cycles and three thickness stages.
+
+Metric: cell-layer-steps/s = cells x layers x steps / device time.  The
+headline form is the mixed-precision path; the FP64 path is measured in the
+same run and reported under "forms".  L2 is flushed (a 512 MB write) between
+timed steps and the flush is excluded from the per-step CUDA-event times.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun with N > 1 every rank runs an independent replica (the method
+has no cross-replica exchange): value = N x per-replica units / max time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import platform
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "cell-layer-steps/s"
+WORKLOAD = "channel_1km"
+
+# algorithmic HBM bytes per launch of each kernel class (inputs read once,
+# outputs written once); sR = 8 (FP64) or 4 (mixed); h and zeta are FP64
+# except the FP32 copy of h the mixed form's tendency kernels read.
+
+
+def kernel_bytes(cls, C, E, V, L, nT, sR, stage_has_old=True, mixed=False):
+    CL, EL, VL = C * L, E * L, V * L
+    if cls == "cell_diag":
+        return (EL + E + CL + nT * CL) * sR + 6 * CL * sR
+    if cls == "vertex":
+        return (EL + E + CL) * sR + 2 * VL * sR
+    if cls == "edge_pre":
+        return (EL + E + CL + VL) * sR + 2 * EL * sR
+    if cls == "bcl_edge":
+        ins = (EL + (EL if stage_has_old else 0) + E + CL + 6 * CL + VL + 2 * EL) * sR + 8 * C
+        return ins + (EL + E) * sR
+    if cls == "btr":
+        return (3 * E + E) * sR + 8 * C + 8 * E
+    if cls == "transport":
+        return 8 * CL + 2 * EL * sR + 2 * E * sR + 3 * 8 * E + EL * sR
+    if cls == "thickness":
+        return (EL * sR + 8 * CL + nT * CL * sR + 8 * CL + nT * CL * sR +
+                8 * CL + (4 * CL if mixed else 0) + nT * CL * sR + 8 * C)
+    if cls == "combine":
+        return 4 * E * sR
+    return 0
+
+
+def step_bytes_per_cell_layer(mixed: bool, nT: int = 1) -> float:
+    """Algorithmic bytes per cell-layer of one SSPRK3-SE step: every 3-D
+    array read or written once per stage (E ~ 3C counts 3 words per cell):
+    baroclinic stages 7+nT, 10+nT, 10+nT words, thickness stages 5+2nT,
+    6+3nT, 6+3nT words; mixed: h 8 B, everything else 4 B."""
+    if not mixed:
+        return 8.0 * ((7 + nT) + 2 * (10 + nT) + (5 + 2 * nT) + 2 * (6 + 3 * nT))
+    # mixed: h words (8 B): bcl reads h once per stage (3), thickness stages
+    # read h_stage + h^n and write h (stage 1: 2 words, stages 2-3: 3 words)
+    h_words = 3 + 2 + 3 + 3
+    total_words = (7 + nT) + 2 * (10 + nT) + (5 + 2 * nT) + 2 * (6 + 3 * nT)
+    return 8.0 * h_words + 4.0 * (total_words - h_words)
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            return json.load(f), "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled while the GPU works."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
+
+    def start(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "100"], stdout=self.f,
+                stderr=subprocess.DEVNULL)
+            time.sleep(0.3)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 7:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax.append(float(parts[1]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[3:7]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        if not sm:
+            return None
+        busy = [s for s in sm if s > 0.5 * max(sm)] or sm
+        return {"sm_mhz": float(np.median(busy)), "sm_max_mhz": float(max(smax)),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def build_workload(seed=0, scale=None):
+    from paper_2105_13484_gb300 import inputs
+    over = {}
+    if scale is not None:
+        over = dict(nx=scale[0], ny=scale[1])
+    m, L, p, st, run = inputs.workload(WORKLOAD, seed=seed, perturb=True, **over)
+    return m, L, p, st, run
+
+
+# ---------------------------------------------------------------------------
+# the oracle (CPU baseline / reference arm)
+# ---------------------------------------------------------------------------
+def time_oracle(steps, warmup, sample=(40, 200)):
+    """The FP64 C oracle, single thread, on a bounded sample of the workload:
+    the same channel at 1 km cut to sample[0] x sample[1] cells."""
+    import oracle
+    m, L, p, (u, h, tr), run = build_workload(scale=sample)
+    o = oracle.Oracle(m, L, p)
+    for _ in range(warmup):
+        u, h, tr = o.step(run["order"], run["dt"], run["M"], u, h, tr)
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        u, h, tr = o.step(run["order"], run["dt"], run["M"], u, h, tr)
+    dt = time.perf_counter() - t0
+    units = m.nCells * L * steps
+    return units / dt, dt / steps * 1e3, f"{m.nCells} cells x {L} layers ({sample[0]}x{sample[1]} " \
+        f"of the 160x578 channel), {steps} SSPRK3-SE steps, 1 thread"
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    steps, warmup = args.steps, args.warmup
+    value, ms, sample = time_oracle(steps, warmup)
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": METRIC,
+            "n_gpus": args.gpus, "steps": steps, "warmup": warmup, "ms_per_step": ms,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": WORKLOAD + " (bounded sample)",
+                                            "sample": sample, "l2": "n/a (CPU)"},
+            "cpu_baseline": {"value": value, "unit": METRIC, "cores": 1, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": METRIC, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0},
+            "host": platform.machine()}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------------------
+# our arm
+# ---------------------------------------------------------------------------
+def measure_form(torch, binding, dm, m, L, p, state0, run, precision, steps, warmup, stream,
+                 flush, sampler=None):
+    u, h, tr = state0
+    st = binding.State(dm, p, precision, stream=stream.cuda_stream)
+    st.load_state(u, h, tr)
+    order, dt, M = run["order"], run["dt"], run["M"]
+    for _ in range(warmup):
+        st.step(order, dt, M, 1)
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(steps)]
+    st.profile(True)
+    if sampler:
+        sampler.start()
+    torch.cuda.synchronize()
+    t_wall = time.perf_counter()
+    with torch.cuda.stream(stream):
+        for i in range(steps):
+            flush.zero_()
+            ev[i][0].record(stream)
+            st.step(order, dt, M, 1)
+            ev[i][1].record(stream)
+    torch.cuda.synchronize()
+    t_wall = time.perf_counter() - t_wall
+    clocks = sampler.stop() if sampler else None
+    prof = st.profile_read()
+    st.profile(False)
+    ms = sum(a.elapsed_time(b) for a, b in ev)
+    d = st.diagnostics(check=False)
+    res = {"device_ms": ms, "ms_per_step": ms / steps, "wall_s": t_wall, "prof": prof,
+           "clocks": clocks, "diag": d, "kernels_per_step": st.kernels_per_step(order)}
+    gu, gh, gt = st.read_state()
+    res["final"] = (gu, gh, gt)
+    st.close()
+    return res
+
+
+def measure_e2e(torch, binding, dm, p, state0, run, precision, steps, stream):
+    """Through the public C ABI with pinned host buffers: per step, H2D of
+    (u, h, T), one large step, D2H of (u, h, T)."""
+    u, h, tr = state0
+    st = binding.State(dm, p, precision, stream=stream.cuda_stream)
+    hu = torch.from_numpy(np.ascontiguousarray(u)).pin_memory()
+    hh = torch.from_numpy(np.ascontiguousarray(h)).pin_memory()
+    ht = torch.from_numpy(np.ascontiguousarray(tr[0])).pin_memory()
+    ou, oh, ot = (torch.empty_like(x).pin_memory() for x in (hu, hh, ht))
+    order, dt, M = run["order"], run["dt"], run["M"]
+    st.set_ptr("u", hu.data_ptr())
+    st.set_ptr("h", hh.data_ptr())
+    st.set_ptr("tracer0", ht.data_ptr())
+    st.step(order, dt, M, 1)
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for _ in range(steps):
+        st.set_ptr("u", hu.data_ptr())
+        st.set_ptr("h", hh.data_ptr())
+        st.set_ptr("tracer0", ht.data_ptr())
+        st.step(order, dt, M, 1)
+        st.get_ptr("u", ou.data_ptr())
+        st.get_ptr("h", oh.data_ptr())
+        st.get_ptr("tracer0", ot.data_ptr())
+    b.record(stream)
+    torch.cuda.synchronize()
+    ms = a.elapsed_time(b)
+    nbytes = (hu.numel() + hh.numel() + ht.numel()) * 8
+    st.close()
+    return ms, nbytes
+
+
+def run_ours(args):
+    import torch
+    from paper_2105_13484_gb300 import binding, build
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py: no CUDA device (the CUDA path has no CPU fallback)")
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    build.build()
+    binding.load()
+    m, L, p, state0, run = build_workload(seed=rank)
+    dm = binding.Mesh(m, L)
+    stream = torch.cuda.Stream()
+    flush = torch.empty(512 * 2 ** 20 // 4, dtype=torch.float32, device="cuda")
+    forms = {}
+    order = run["order"]
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    sampler = ClockSampler(local)
+    for prec in ("mixed", "fp64"):
+        forms[prec] = measure_form(torch, binding, dm, m, L, p, state0, run, prec, args.steps,
+                                   args.warmup, stream, flush,
+                                   sampler if prec == args.precision else None)
+    head = forms[args.precision]
+    units = m.nCells * L * args.steps
+    t_max = head["device_ms"]
+    if dist:
+        t = torch.tensor([t_max], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_max = float(t.item())
+    value = world * units / (t_max / 1e3)
+
+    # error of the mixed form against the FP64 form at the horizon (per field)
+    fu, fh, ft = forms["fp64"]["final"]
+    mu, mh, mt = forms["mixed"]["final"]
+
+    def rel(a, b):
+        return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+    mixed_err = {"u": rel(mu, fu), "h": rel(mh, fh), "zeta": rel(mh.sum(1) - m.bottomDepth,
+                                                                 fh.sum(1) - m.bottomDepth),
+                 "T": rel(mt, ft)}
+
+    # roofline of the dominant kernel class (by summed device time)
+    peaks, peak_kind = measured_peaks()
+    mixed = args.precision == "mixed"
+    sR = 4 if mixed else 8
+    prof = head["prof"]
+    dom = max(prof, key=lambda k: prof[k][0])
+    nlaunch = prof[dom][1]
+    per_launch_ms = prof[dom][0] / max(nlaunch, 1)
+    nT = int(p.get("nTracers", 1))
+    if dom == "bcl_edge":
+        # 1 of 3 launches per step has no utilde^n input
+        b = (kernel_bytes(dom, m.nCells, m.nEdges, m.nVertices, L, nT, sR, False, mixed) +
+             2 * kernel_bytes(dom, m.nCells, m.nEdges, m.nVertices, L, nT, sR, True, mixed)) / 3
+    else:
+        b = kernel_bytes(dom, m.nCells, m.nEdges, m.nVertices, L, nT, sR, True, mixed)
+    achieved = b / (per_launch_ms / 1e3) / 1e9
+    roof = {"kernel": dom, "bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"],
+            "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"], "traffic": None,
+            "peak_source": f"{peak_kind} hbm_gbs (copy)", "bytes_per_launch": b,
+            "ms_per_launch": per_launch_ms}
+    step_b = step_bytes_per_cell_layer(mixed, nT) * m.nCells * L
+    step_roof = {"bytes_per_step": step_b,
+                 "achieved_gbs": step_b / (head["ms_per_step"] / 1e3) / 1e9,
+                 "frac_of_hbm": step_b / (head["ms_per_step"] / 1e3) / 1e9 / peaks["hbm_gbs"]}
+    kernels = {k: {"ms_per_step": v[0] / args.steps, "share": v[0] / max(head["device_ms"], 1e-9),
+                   "launches_per_step": v[1] / args.steps} for k, v in prof.items()}
+
+    e2e_steps = min(args.steps, 20)
+    e2e_ms, nbytes = measure_e2e(torch, binding, dm, p, state0, run, args.precision, e2e_steps,
+                                 stream)
+    e2e_val = world * m.nCells * L * e2e_steps / (e2e_ms / 1e3)
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        v, ms, sample = time_oracle(2, 0, sample=(160, 578))
+        cpu = {"value": v, "unit": METRIC, "cores": 1, "kind": "oracle", "sample": sample}
+
+    vol0 = float(m.areaCell @ state0[1].sum(1))
+    line = {
+        "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_max / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32+f64" if mixed else "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "cells": m.nCells, "edges": m.nEdges, "layers": L,
+                   "scheme": f"SSPRK{order}-SE", "dt": run["dt"], "M": run["M"],
+                   "recon": p.get("recon"), "precision": args.precision,
+                   "l2": "flushed (512 MB write) between timed steps, flush excluded",
+                   "parallelism": f"replicas x{world}"},
+        "roofline": roof, "step_roofline": step_roof, "kernels": kernels,
+        "forms": {k: {"value": world * units / (v["device_ms"] / 1e3),
+                      "ms_per_step": v["ms_per_step"],
+                      "volume_rel_change": abs(v["diag"]["volume"] - vol0) / vol0}
+                  for k, v in forms.items()},
+        "mixed_vs_fp64_rel_l2": mixed_err,
+        "e2e": {"value": e2e_val, "unit": METRIC, "h2d_bytes_per_step": nbytes,
+                "d2h_bytes_per_step": nbytes},
+        "gpu_launches": head["kernels_per_step"] * args.steps,
+        "clocks": head["clocks"],
+        "cpu_baseline": cpu,
+    }
+    if dist:
+        dist.barrier()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
+    ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -172,6 +172,24 @@ int sse_diagnostics(sse_state *state, sse_diag *out);
 /* Number of kernels sse_step launches per large step for `order`. */
 int sse_kernels_per_step(const sse_state *state, int order);
 
+/* Per-kernel timing with CUDA events on the state's stream.  Kernel classes: */
+#define SSE_K_CELL_DIAG 0   /* cell diagnostics (K, div u, rho', p', z, w)   */
+#define SSE_K_VERTEX 1      /* vorticity and potential vorticity             */
+#define SSE_K_EDGE_PRE 2    /* edge mass flux, q_e, split (Eq. BBspl)        */
+#define SSE_K_BCL_EDGE 3    /* Algorithm 1 edge kernel                        */
+#define SSE_K_BTR 4         /* Algorithms 3/4 persistent sub-cycle            */
+#define SSE_K_TRANSPORT 5   /* Sec. 3.4 adjustment and edge mass flux         */
+#define SSE_K_THICKNESS 6   /* thickness and tracer stage                     */
+#define SSE_K_COMBINE 7     /* Interp_2 / Interp_3 forcing combination        */
+#define SSE_K_NCLASS 8
+/* enable != 0 starts recording an event pair around every launch of sse_step
+ * (and clears earlier records); enable == 0 stops recording. */
+int sse_profile(sse_state *state, int enable);
+/* Synchronises the stream; fills ms[SSE_K_NCLASS] with the summed device time
+ * of each class and launches[SSE_K_NCLASS] with the launch counts recorded
+ * since the last sse_profile(state, 1). */
+int sse_profile_read(sse_state *state, double *ms, int32_t *launches);
+
 const char *sse_strerror(int code);
 
 #ifdef __cplusplus

@@ -61,7 +61,10 @@ class Diag(ct.Structure):
 
 EXPORTS = ["sse_mesh_create", "sse_mesh_destroy", "sse_state_create", "sse_state_destroy",
            "sse_state_set", "sse_state_get", "sse_step", "sse_baroclinic_feuler",
-           "sse_barotropic_substep", "sse_diagnostics", "sse_kernels_per_step", "sse_strerror"]
+           "sse_barotropic_substep", "sse_diagnostics", "sse_kernels_per_step", "sse_profile",
+           "sse_profile_read", "sse_strerror"]
+KERNEL_CLASSES = ["cell_diag", "vertex", "edge_pre", "bcl_edge", "btr", "transport", "thickness",
+                  "combine"]
 
 _lib = None
 
@@ -88,6 +91,8 @@ def load(path: str = LIB_PATH):
     lib.sse_barotropic_substep.argtypes = [ct.c_void_p, ct.c_int, ct.c_double, ct.c_int]
     lib.sse_diagnostics.argtypes = [ct.c_void_p, ct.POINTER(Diag)]
     lib.sse_kernels_per_step.argtypes = [ct.c_void_p, ct.c_int]
+    lib.sse_profile.argtypes = [ct.c_void_p, ct.c_int]
+    lib.sse_profile_read.argtypes = [ct.c_void_p, ct.c_void_p, ct.c_void_p]
     lib.sse_strerror.argtypes = [ct.c_int]
     lib.sse_strerror.restype = ct.c_char_p
     _lib = lib
@@ -233,6 +238,16 @@ class State:
                     kinetic_energy=d.kinetic_energy, max_speed=d.max_speed,
                     min_thickness=d.min_thickness, zeta_min=d.zeta_min, zeta_max=d.zeta_max,
                     step=d.step, nonfinite=bool(d.nonfinite), rc=rc)
+
+    def profile(self, enable: bool):
+        _check(self.lib.sse_profile(self.handle, 1 if enable else 0), "sse_profile")
+
+    def profile_read(self) -> dict:
+        ms = np.zeros(len(KERNEL_CLASSES))
+        n = np.zeros(len(KERNEL_CLASSES), dtype=np.int32)
+        _check(self.lib.sse_profile_read(self.handle, ms.ctypes.data, n.ctypes.data),
+               "sse_profile_read")
+        return {k: (float(ms[i]), int(n[i])) for i, k in enumerate(KERNEL_CLASSES)}
 
     def kernels_per_step(self, order: int) -> int:
         return int(self.lib.sse_kernels_per_step(self.handle, int(order)))

@@ -219,7 +219,6 @@ extern "C" void sse_mesh_destroy(sse_mesh *m) { delete m; }
 // state: a precision-specific engine behind a small virtual interface
 // ---------------------------------------------------------------------------
 struct EngineBase {
-    virtual ~EngineBase() {}
     virtual int set(int field, const double *host) = 0;
     virtual int get(int field, double *host) = 0;
     virtual int step(int order, double dt, int M) = 0;
@@ -227,6 +226,52 @@ struct EngineBase {
     virtual int btr_substep(int order, double dt, int M) = 0;
     virtual int diagnostics(sse_diag *out) = 0;
     long long steps = 0;
+
+    // ---- optional per-launch event timing
+    bool prof = false;
+    std::vector<cudaEvent_t> pool;
+    struct Rec { int cls; cudaEvent_t a, b; };
+    std::vector<Rec> recs;
+    cudaStream_t ps = nullptr;
+    cudaEvent_t take() {
+        if (!pool.empty()) {
+            cudaEvent_t e = pool.back();
+            pool.pop_back();
+            return e;
+        }
+        cudaEvent_t e = nullptr;
+        cudaEventCreate(&e);
+        return e;
+    }
+    void pbeg(int cls) {
+        if (!prof) return;
+        Rec r{cls, take(), take()};
+        cudaEventRecord(r.a, ps);
+        recs.push_back(r);
+    }
+    void pend() {
+        if (!prof || recs.empty()) return;
+        cudaEventRecord(recs.back().b, ps);
+    }
+    void prof_clear() {
+        for (auto &r : recs) { pool.push_back(r.a); pool.push_back(r.b); }
+        recs.clear();
+    }
+    int prof_read(double *ms, int32_t *n) {
+        for (int c = 0; c < SSE_K_NCLASS; c++) { ms[c] = 0.0; n[c] = 0; }
+        if (cudaStreamSynchronize(ps) != cudaSuccess) return SSE_ERR_CUDA;
+        for (auto &r : recs) {
+            float t = 0.f;
+            if (cudaEventElapsedTime(&t, r.a, r.b) != cudaSuccess) return SSE_ERR_CUDA;
+            ms[r.cls] += t;
+            n[r.cls] += 1;
+        }
+        return SSE_OK;
+    }
+    virtual ~EngineBase() {
+        prof_clear();
+        for (auto e : pool) cudaEventDestroy(e);
+    }
 };
 
 #define CK(x)                                                        \
@@ -270,6 +315,7 @@ struct Engine : EngineBase {
     int init(const sse_mesh *mesh, const sse_params *prm, cudaStream_t st) {
         m = mesh->dm;
         s = st;
+        ps = st;
         mixed = (prm->precision == SSE_MIXED);
         recon = prm->recon;
         p.g = prm->g; p.rho0 = prm->rho0; p.nu_h = prm->nu_h; p.nu_v = prm->nu_v;
@@ -448,10 +494,18 @@ struct Engine : EngineBase {
     // ---- pieces
     void bcl_stage(R *ubar, R *ut, R *hR, R *tr, const double *zeta, bool split, const R *utn,
                    double a, double b, double dt, R *out, R *G) {
+        pbeg(SSE_K_CELL_DIAG);
         launch_cell_diag<R>(m, p, ubar, ut, hR, tr, db, s);
+        pend();
+        pbeg(SSE_K_VERTEX);
         launch_vertex<R>(m, ubar, ut, hR, db, s);
+        pend();
+        pbeg(SSE_K_EDGE_PRE);
         launch_edge_pre<R>(m, ubar, ut, hR, db, split, s);
+        pend();
+        pbeg(SSE_K_BCL_EDGE);
         launch_bcl_edge<R>(m, p, ubar, ut, hR, zeta, db, utn, a, b, dt, out, G, s);
+        pend();
     }
 
     cudaError_t btr(int order, const R *ub_start, const double *z_start, const R *Ga,
@@ -463,7 +517,13 @@ struct Engine : EngineBase {
         a.u0 = bu0; a.ua = bua; a.uh = buh; a.z0 = bz0; a.za = bza; a.zh = bzh;
         a.tau = tau_dt / M; a.g = p.g; a.M = M; a.order = order;
         last_Fz = Fz;
-        return launch_btr<R>(m, a, bar(), btr_blocks, btr_block_size<R>(), s);
+        // the barrier reset (a memset) sits outside the timed pair
+        cudaError_t me = cudaMemsetAsync(barwords, 0, 2 * sizeof(unsigned int), s);
+        if (me != cudaSuccess) return me;
+        pbeg(SSE_K_BTR);
+        cudaError_t e = launch_btr<R>(m, a, bar(), btr_blocks, btr_block_size<R>(), s);
+        pend();
+        return e;
     }
 
     void transport(const double *h, const R *ubA, const R *utA, double wA, const R *ubB,
@@ -473,7 +533,9 @@ struct Engine : EngineBase {
         a.h = h; a.ubA = ubA; a.utA = utA; a.ubB = ubB; a.utB = utB; a.wA = wA; a.wB = wB;
         a.Fz = Fz; a.ex1 = e1; a.ex2 = e2; a.cF = cF; a.cE = cE; a.cA = cA;
         a.recon = (recon != SSE_RECON_OFF); a.S_out = S_out; a.flux = flux;
+        pbeg(SSE_K_TRANSPORT);
         launch_transport<R>(m, a, s);
+        pend();
     }
 
     void thickness(const double *h_s, const R *tr_s, double a, double b, double dt, double *h_out,
@@ -482,7 +544,9 @@ struct Engine : EngineBase {
         t.flux = flux; t.h_s = h_s; t.tr_s = tr_s; t.h_n = h_n; t.tr_n = tr_n;
         t.a = a; t.b = b; t.dt = dt; t.h_out = h_out; t.hR_out = mixed ? hR_out : nullptr;
         t.tr_out = tr_out; t.zeta_out = zeta_out;
+        pbeg(SSE_K_THICKNESS);
         launch_thickness<R>(m, p, t, s);
+        pend();
     }
 
     // combined forcing for the corrector: Gw = w0 G0 + w1 G1 (+ w2 G2)
@@ -586,7 +650,9 @@ __global__ void k_combine_G(const R *__restrict__ a, const R *__restrict__ b,
 }
 
 template <class R> void Engine<R>::combine_G(double w0, double w1, double w2) {
+    pbeg(SSE_K_COMBINE);
     k_combine_G<R><<<(m.E + 255) / 256, 256, 0, s>>>(G0, G1, G2, Gw, w0, w1, w2, m.E);
+    pend();
 }
 
 struct sse_state {
@@ -670,6 +736,18 @@ extern "C" int sse_kernels_per_step(const sse_state *st, int order) {
     if (!st) return SSE_ERR_INVALID_ARG;
     // 4 per baroclinic stage, 1 per sub-cycle, 2 per thickness stage, 1 forcing combination
     return order == 2 ? 2 * 4 + 2 + 2 * 2 + 1 : 3 * 4 + 3 + 3 * 2 + 1;
+}
+
+extern "C" int sse_profile(sse_state *st, int enable) {
+    if (!st) return SSE_ERR_INVALID_ARG;
+    st->eng->prof_clear();
+    st->eng->prof = (enable != 0);
+    return SSE_OK;
+}
+
+extern "C" int sse_profile_read(sse_state *st, double *ms, int32_t *launches) {
+    if (!st || !ms || !launches) return SSE_ERR_INVALID_ARG;
+    return st->eng->prof_read(ms, launches);
 }
 
 extern "C" const char *sse_strerror(int code) {

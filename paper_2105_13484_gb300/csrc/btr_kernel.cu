@@ -104,8 +104,8 @@ __global__ void __launch_bounds__(BTR_THREADS) k_btr(DMesh m, BtrArgs<R> a, Barr
     const unsigned int nb = gridDim.x;
     const int stride = gridDim.x * blockDim.x;
     const int t0 = blockIdx.x * blockDim.x + threadIdx.x;
-    // the launcher zeroes count and gen on the stream right before the launch,
-    // so every block starts from generation 0
+    // count and gen are zeroed on the stream right before the launch, so every
+    // block starts from generation 0
     unsigned int gen = 0;
     const R tau = (R)a.tau, g = (R)a.g;
     const int M = a.M;
@@ -179,10 +179,9 @@ cudaError_t launch_btr(const DMesh &m, const BtrArgs<R> &a, const Barrier &bar, 
     DMesh mm = m;
     BtrArgs<R> aa = a;
     Barrier bb = bar;
+    // the caller zeroes bar.count and bar.gen (adjacent words) on stream s
+    // before every launch
     void *args[] = {&mm, &aa, &bb};
-    // count and gen are adjacent words; reset both before every launch
-    cudaError_t err = cudaMemsetAsync(bar.count, 0, 2 * sizeof(unsigned int), s);
-    if (err != cudaSuccess) return err;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(nblocks);
     cfg.blockDim = dim3(nthreads);
