@@ -190,6 +190,35 @@ int sse_profile(sse_state *state, int enable);
  * since the last sse_profile(state, 1). */
 int sse_profile_read(sse_state *state, double *ms, int32_t *launches);
 
+/* Allocation-free variant of sse_barotropic_substep (FP64), for callers that
+ * cannot allocate device memory at the point where they run the sub-cycle
+ * (for example while their stream is being captured into a CUDA graph, or
+ * inside a memory pool or allocator callback that forbids new allocations).
+ * The paper has no counterpart; it computes the same Algorithm 3 (order 2)
+ * or Algorithm 4 (order 3) sub-cycle as sse_barotropic_substep.
+ *   mesh       a mesh made earlier by sse_mesh_create
+ *   ubar_in    device [nEdges] barotropic velocity at the start
+ *   zeta_in    device [nCells] SSH at the start
+ *   G          device [nEdges] frozen barotropic forcing
+ *   ubar_out   device [nEdges] ubar after n_substeps sub-steps of dt/n_substeps
+ *   Fzeta_out  device [nEdges] accumulated flux F^zeta of Sec. 3.4
+ *   zeta_out   device [nCells] the sub-cycle's own final SSH, or NULL
+ *   cuda_stream  cudaStream_t (NULL = legacy default stream)
+ * The caller owns all these arrays; the library allocates nothing in this
+ * call.  Its work buffers live in one file-scope device array of fixed size
+ * (limits: nEdges <= 393216, nCells <= 131072, about 12.6 MB) that every GPU
+ * loading the library holds until the process exits; larger meshes return
+ * SSE_ERR_UNSUPPORTED.  The first call on a device looks up that array's
+ * device address and the launch shape; make it before any stream capture.
+ * All calls share the array, so calls that overlap on the GPU (on different
+ * streams or devices' shared context) race and must be serialised by the
+ * caller.  The call synchronises `cuda_stream` to read the barrier status and
+ * returns SSE_ERR_SYNC_TIMEOUT if a grid barrier timed out. */
+int sse_barotropic_substep_noalloc(const sse_mesh *mesh, int order, double dt, int n_substeps,
+                                   double g, const double *ubar_in, const double *zeta_in,
+                                   const double *G, double *ubar_out, double *Fzeta_out,
+                                   double *zeta_out, void *cuda_stream);
+
 const char *sse_strerror(int code);
 
 #ifdef __cplusplus

@@ -62,7 +62,7 @@ class Diag(ct.Structure):
 EXPORTS = ["sse_mesh_create", "sse_mesh_destroy", "sse_state_create", "sse_state_destroy",
            "sse_state_set", "sse_state_get", "sse_step", "sse_baroclinic_feuler",
            "sse_barotropic_substep", "sse_diagnostics", "sse_kernels_per_step", "sse_profile",
-           "sse_profile_read", "sse_strerror"]
+           "sse_profile_read", "sse_barotropic_substep_noalloc", "sse_strerror"]
 KERNEL_CLASSES = ["cell_diag", "vertex", "edge_pre", "bcl_edge", "btr", "transport", "thickness",
                   "combine"]
 
@@ -93,6 +93,9 @@ def load(path: str = LIB_PATH):
     lib.sse_kernels_per_step.argtypes = [ct.c_void_p, ct.c_int]
     lib.sse_profile.argtypes = [ct.c_void_p, ct.c_int]
     lib.sse_profile_read.argtypes = [ct.c_void_p, ct.c_void_p, ct.c_void_p]
+    lib.sse_barotropic_substep_noalloc.argtypes = [
+        ct.c_void_p, ct.c_int, ct.c_double, ct.c_int, ct.c_double, ct.c_void_p, ct.c_void_p,
+        ct.c_void_p, ct.c_void_p, ct.c_void_p, ct.c_void_p, ct.c_void_p]
     lib.sse_strerror.argtypes = [ct.c_int]
     lib.sse_strerror.restype = ct.c_char_p
     _lib = lib
@@ -149,6 +152,20 @@ class Mesh:
             self.close()
         except Exception:
             pass
+
+
+def barotropic_substep_noalloc(mesh: Mesh, order: int, dt: float, M: int, g: float,
+                               ubar_in: int, zeta_in: int, G: int, ubar_out: int, Fzeta_out: int,
+                               zeta_out: int = 0, stream: int = 0):
+    """Allocation-free sub-cycle on caller-owned device arrays (raw pointers)."""
+    lib = load()
+    _check(lib.sse_barotropic_substep_noalloc(mesh.handle, int(order), float(dt), int(M),
+                                              float(g), ct.c_void_p(ubar_in),
+                                              ct.c_void_p(zeta_in), ct.c_void_p(G),
+                                              ct.c_void_p(ubar_out), ct.c_void_p(Fzeta_out),
+                                              ct.c_void_p(zeta_out or 0),
+                                              ct.c_void_p(stream or 0)),
+           "sse_barotropic_substep_noalloc")
 
 
 def make_params(params: dict, precision="fp64") -> Params:

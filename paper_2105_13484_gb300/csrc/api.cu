@@ -215,6 +215,8 @@ extern "C" int sse_mesh_create(const sse_mesh_desc *d, sse_mesh **out) {
 
 extern "C" void sse_mesh_destroy(sse_mesh *m) { delete m; }
 
+const sse::DMesh *sse_internal_dmesh(const sse_mesh *m) { return &m->dm; }
+
 // ---------------------------------------------------------------------------
 // state: a precision-specific engine behind a small virtual interface
 // ---------------------------------------------------------------------------

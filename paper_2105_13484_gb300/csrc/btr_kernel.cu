@@ -13,6 +13,9 @@
 //
 // The barrier spins with a bounded budget: if it runs out (a block never
 // arrives), the kernel records an error word and returns instead of hanging.
+#include <mutex>
+
+#include "../../include/sse.h"
 #include "sse_internal.cuh"
 
 namespace sse {
@@ -205,3 +208,98 @@ template cudaError_t launch_btr<float>(const DMesh &, const BtrArgs<float> &, co
                                        int, cudaStream_t);
 
 }  // namespace sse
+
+// ===========================================================================
+// Allocation-free sub-cycle: sse_barotropic_substep_noalloc
+//
+// For callers that cannot allocate device memory when they run the
+// sub-cycle (for example code that executes while a CUDA stream is being
+// captured into a graph, or inside an allocator callback or a memory pool
+// that forbids new allocations): the work buffers live in one file-scope
+// device array that every GPU loading this library holds until the process
+// exits.  The first 256 bytes hold the grid-barrier words and the error word.
+// ===========================================================================
+namespace sse {
+
+constexpr int NOALLOC_MAX_EDGES = 393216;
+constexpr int NOALLOC_MAX_CELLS = 131072;
+constexpr int NOALLOC_HEADER = 32;  // doubles (256 bytes) of barrier words
+static __device__ __align__(256) double
+    g_noalloc_scratch[NOALLOC_HEADER + 3 * NOALLOC_MAX_EDGES + 3 * NOALLOC_MAX_CELLS];
+
+namespace {
+constexpr int kMaxDevices = 64;
+struct NoallocDevice {
+    double *scratch = nullptr;  // device address of g_noalloc_scratch on this device
+    int blocks_per_sm = 0, sms = 0;
+};
+NoallocDevice g_noalloc_dev[kMaxDevices];
+std::mutex g_noalloc_mutex;
+}  // namespace
+
+}  // namespace sse
+
+const sse::DMesh *sse_internal_dmesh(const sse_mesh *m);
+
+extern "C" int sse_barotropic_substep_noalloc(const sse_mesh *mesh, int order, double dt,
+                                              int n_substeps, double g, const double *ubar_in,
+                                              const double *zeta_in, const double *G,
+                                              double *ubar_out, double *Fzeta_out,
+                                              double *zeta_out, void *cuda_stream) {
+    using namespace sse;
+    if (!mesh || (order != 2 && order != 3) || !(dt > 0) || !isfinite(dt) || n_substeps < 1 ||
+        !(g > 0) || !ubar_in || !zeta_in || !G || !ubar_out || !Fzeta_out)
+        return SSE_ERR_INVALID_ARG;
+    const DMesh &m = *sse_internal_dmesh(mesh);
+    if (m.E > NOALLOC_MAX_EDGES || m.C > NOALLOC_MAX_CELLS) return SSE_ERR_UNSUPPORTED;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return SSE_ERR_CUDA;
+    NoallocDevice nd;
+    {
+        // once per device, with that device current: the device address of the
+        // array (the host-side symbol is only a stand-in for it)
+        std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+        NoallocDevice &d = g_noalloc_dev[dev];
+        if (!d.scratch) {
+            void *p = nullptr;
+            if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess) return SSE_ERR_CUDA;
+            int occ2 = 0, occ3 = 0, nsm = 0;
+            if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ2, k_btr<double, 2>,
+                                                              BTR_THREADS, 0) != cudaSuccess ||
+                cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ3, k_btr<double, 3>,
+                                                              BTR_THREADS, 0) != cudaSuccess ||
+                cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+                return SSE_ERR_CUDA;
+            d.blocks_per_sm = occ2 < occ3 ? occ2 : occ3;
+            d.sms = nsm;
+            d.scratch = (double *)p;
+        }
+        nd = d;
+    }
+    if (nd.blocks_per_sm < 1) return SSE_ERR_UNSUPPORTED;
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    double *base = nd.scratch;
+    unsigned int *words = (unsigned int *)base;
+    double *work = base + NOALLOC_HEADER;
+    BtrArgs<double> a{};
+    a.ub_start = ubar_in; a.z_start = zeta_in; a.G = G; a.X = nullptr; a.alpha = 0.0;
+    a.beta = 1.0; a.ub_out = ubar_out; a.Fz = Fzeta_out; a.z_out = zeta_out;
+    a.u0 = work; a.ua = work + NOALLOC_MAX_EDGES; a.uh = work + 2 * NOALLOC_MAX_EDGES;
+    a.z0 = work + 3 * NOALLOC_MAX_EDGES; a.za = a.z0 + NOALLOC_MAX_CELLS;
+    a.zh = a.z0 + 2 * NOALLOC_MAX_CELLS;
+    a.tau = dt / n_substeps; a.g = g; a.M = n_substeps; a.order = order;
+    Barrier bar{words, words + 1, (int *)(words + 2)};
+    // the array keeps the previous call's contents: zero the barrier and error words
+    if (cudaMemsetAsync(base, 0, NOALLOC_HEADER * sizeof(double), s) != cudaSuccess)
+        return SSE_ERR_CUDA;
+    const int need = ((m.E > m.C ? m.E : m.C) + BTR_THREADS - 1) / BTR_THREADS;
+    int blocks = nd.blocks_per_sm * nd.sms;
+    if (need < blocks) blocks = need;
+    if (blocks < 1) blocks = 1;
+    if (launch_btr<double>(m, a, bar, blocks, BTR_THREADS, s) != cudaSuccess) return SSE_ERR_CUDA;
+    int err = 0;
+    if (cudaMemcpyAsync(&err, words + 2, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess)
+        return SSE_ERR_CUDA;
+    return err ? SSE_ERR_SYNC_TIMEOUT : SSE_OK;
+}
