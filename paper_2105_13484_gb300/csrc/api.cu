@@ -201,6 +201,7 @@ extern "C" int sse_mesh_create(const sse_mesh_desc *d, sse_mesh **out) {
     dm.d.divc = dm.divc_d; dm.d.kec = A.upload(kec); dm.d.wl = A.upload(wl);
     dm.d.cfc = A.upload(cfc); dm.d.curlc = A.upload(curlc); dm.d.kw = A.upload(kw);
     dm.d.invdc = A.upload(invdc); dm.d.invdv = A.upload(invdv); dm.d.fV = A.upload(fV);
+    dm.d.H = dm.H; dm.f.H = A.upload(tof(H));
     dm.f.divc = A.upload(tof(divc)); dm.f.kec = A.upload(tof(kec)); dm.f.wl = A.upload(tof(wl));
     dm.f.cfc = A.upload(tof(cfc)); dm.f.curlc = A.upload(tof(curlc)); dm.f.kw = A.upload(tof(kw));
     dm.f.invdc = A.upload(tof(invdc)); dm.f.invdv = A.upload(tof(invdv));
@@ -304,6 +305,7 @@ struct Engine : EngineBase {
     double *h_1, *h_h, *zeta_1, *zeta_h;
     R *hR_1, *hR_h, *tr_1, *tr_h;
     R *flux;
+    double *Fcol;
     DiagBufs<R> db;
     R *bu0, *bua, *buh, *bz0, *bza, *bzh;
     unsigned int *barwords;
@@ -346,6 +348,7 @@ struct Engine : EngineBase {
         }
         tr_1 = A.alloc<R>(nT * CL); tr_h = A.alloc<R>(nT * CL);
         flux = A.alloc<R>(EL);
+        Fcol = A.alloc<double>(m.Ep);
         db.ke = A.alloc<R>(CL); db.delta = A.alloc<R>(CL); db.rhop = A.alloc<R>(CL);
         db.pp = A.alloc<R>(CL); db.zm = A.alloc<R>(CL); db.w = A.alloc<R>(CL);
         db.omega = A.alloc<R>(VL); db.q = A.alloc<R>(VL);
@@ -366,12 +369,15 @@ struct Engine : EngineBase {
         CK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
         const int bt = btr_block_size<R>();
         int occ2 = 0;
-        CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, btr_kernel_ptr<R>(2), bt, 0));
-        CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ2, btr_kernel_ptr<R>(3), bt, 0));
+        CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, btr_kernel_ptr<R>(2, m.maxE2), bt, 0));
+        CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ2, btr_kernel_ptr<R>(3, m.maxE2), bt, 0));
         occ = std::min(occ, occ2);
         if (occ < 1) return SSE_ERR_UNSUPPORTED;
         const int need = (std::max(m.E, m.C) + bt - 1) / bt;
         btr_blocks = std::max(1, std::min(need, occ * nsm));
+        // every thread keeps at most btr_max_items_per_thread() edges in registers
+        if ((long long)btr_blocks * bt * btr_max_items_per_thread() < std::max(m.E, m.C))
+            return SSE_ERR_UNSUPPORTED;
         CK(cudaStreamSynchronize(s));
         return SSE_OK;
     }
@@ -528,11 +534,11 @@ struct Engine : EngineBase {
         return e;
     }
 
-    void transport(const double *h, const R *ubA, const R *utA, double wA, const R *ubB,
-                   const R *utB, double wB, const double *Fz, const double *e1, const double *e2,
-                   double cF, double cE, double cA, double *S_out) {
+    void transport(const R *hR, const double *zeta, const R *ubA, const R *utA, double wA,
+                   const R *ubB, const R *utB, double wB, const double *Fz, const double *e1,
+                   const double *e2, double cF, double cE, double cA, double *S_out) {
         TransportArgs<R> a{};
-        a.h = h; a.ubA = ubA; a.utA = utA; a.ubB = ubB; a.utB = utB; a.wA = wA; a.wB = wB;
+        a.hR = hR; a.zeta = zeta; a.Fcol = Fcol; a.ubA = ubA; a.utA = utA; a.ubB = ubB; a.utB = utB; a.wA = wA; a.wB = wB;
         a.Fz = Fz; a.ex1 = e1; a.ex2 = e2; a.cF = cF; a.cE = cE; a.cA = cA;
         a.recon = (recon != SSE_RECON_OFF); a.S_out = S_out; a.flux = flux;
         pbeg(SSE_K_TRANSPORT);
@@ -540,10 +546,10 @@ struct Engine : EngineBase {
         pend();
     }
 
-    void thickness(const double *h_s, const R *tr_s, double a, double b, double dt, double *h_out,
-                   R *hR_out, R *tr_out, double *zeta_out) {
+    void thickness(const double *h_s, const R *hR_s, const R *tr_s, double a, double b, double dt,
+                   double *h_out, R *hR_out, R *tr_out, double *zeta_out) {
         ThickArgs<R> t{};
-        t.flux = flux; t.h_s = h_s; t.tr_s = tr_s; t.h_n = h_n; t.tr_n = tr_n;
+        t.flux = flux; t.Fcol = Fcol; t.h_s = h_s; t.hR_s = hR_s; t.tr_s = tr_s; t.h_n = h_n; t.tr_n = tr_n;
         t.a = a; t.b = b; t.dt = dt; t.h_out = h_out; t.hR_out = mixed ? hR_out : nullptr;
         t.tr_out = tr_out; t.zeta_out = zeta_out;
         pbeg(SSE_K_THICKNESS);
@@ -560,33 +566,33 @@ struct Engine : EngineBase {
             // Stage 1 (Sec. 3.2): Algorithm 1, predictor sub-cycle, thickness
             bcl_stage(ubar_n, ut_n, hR_n, tr_n, zeta_n, true, nullptr, 0.0, 1.0, dt, ut_1, G0);
             CK(btr(2, ubar_n, zeta_n, G0, dt, M, nullptr, 0, 1, ubar_1, Fz1, nullptr));
-            transport(h_n, ubar_n, ut_n, 1.0, nullptr, nullptr, 0.0, Fz1, nullptr, nullptr, 1.0,
-                      0.0, 1.0, S1);
-            thickness(h_n, tr_n, 0.0, 1.0, dt, h_1, hR_1, tr_1, zeta_1);
+            transport(hR_n, zeta_n, ubar_n, ut_n, 1.0, nullptr, nullptr, 0.0, Fz1, nullptr,
+                      nullptr, 1.0, 0.0, 1.0, S1);
+            thickness(h_n, hR_n, tr_n, 0.0, 1.0, dt, h_1, hR_1, tr_1, zeta_1);
             // Stage 2: baroclinic, utilde^{n+1} = (ut^n + ut^{n+2})/2
             bcl_stage(ubar_1, ut_1, hR_1, tr_1, zeta_1, false, ut_n, 0.5, 0.5, dt, ut_c, G1);
             // Step 2: corrector with Interp_2(G0, G1)
             combine_G(0.5, 0.5, 0.0);
             CK(btr(2, ubar_n, zeta_n, Gw, dt, M, nullptr, 0, 1, ubar_np1, Fz2, zeta_sub));
             // Step 3: thickness stage 2 with F^h_2 and the factor 2 of Sec. 3.4
-            transport(h_1, ubar_np1, ut_c, 1.0, nullptr, nullptr, 0.0, Fz2,
+            transport(hR_1, zeta_1, ubar_np1, ut_c, 1.0, nullptr, nullptr, 0.0, Fz2,
                       consistent ? Fz1 : S1, nullptr, 0.5, 0.5, 2.0, nullptr);
-            thickness(h_1, tr_1, 0.5, 0.5, dt, h_n, hR_n, tr_n, zeta_n);
+            thickness(h_1, hR_1, tr_1, 0.5, 0.5, dt, h_n, hR_n, tr_n, zeta_n);
             std::swap(ut_n, ut_c);
             std::swap(ubar_n, ubar_np1);
         } else {
             // Stage 1 (Sec. 3.3)
             bcl_stage(ubar_n, ut_n, hR_n, tr_n, zeta_n, true, nullptr, 0.0, 1.0, dt, ut_1, G0);
             CK(btr(3, ubar_n, zeta_n, G0, dt, M, nullptr, 0, 1, ubar_1, Fz1, nullptr));
-            transport(h_n, ubar_n, ut_n, 1.0, nullptr, nullptr, 0.0, Fz1, nullptr, nullptr, 1.0,
-                      0.0, 1.0, S1);
-            thickness(h_n, tr_n, 0.0, 1.0, dt, h_1, hR_1, tr_1, zeta_1);
+            transport(hR_n, zeta_n, ubar_n, ut_n, 1.0, nullptr, nullptr, 0.0, Fz1, nullptr,
+                      nullptr, 1.0, 0.0, 1.0, S1);
+            thickness(h_n, hR_n, tr_n, 0.0, 1.0, dt, h_1, hR_1, tr_1, zeta_1);
             // Stage 2
             bcl_stage(ubar_1, ut_1, hR_1, tr_1, zeta_1, false, ut_n, 0.75, 0.25, dt, ut_c, G1);
             CK(btr(3, ubar_1, zeta_1, G1, dt, M, ubar_n, 0.75, 0.25, ubar_h, Fz2, nullptr));
-            transport(h_1, ubar_1, ut_1, 1.0, nullptr, nullptr, 0.0, Fz2, nullptr, nullptr, 1.0,
-                      0.0, 1.0, S2);
-            thickness(h_1, tr_1, 0.75, 0.25, dt, h_h, hR_h, tr_h, zeta_h);
+            transport(hR_1, zeta_1, ubar_1, ut_1, 1.0, nullptr, nullptr, 0.0, Fz2, nullptr,
+                      nullptr, 1.0, 0.0, 1.0, S2);
+            thickness(h_1, hR_1, tr_1, 0.75, 0.25, dt, h_h, hR_h, tr_h, zeta_h);
             // Stage 3
             bcl_stage(ubar_h, ut_c, hR_h, tr_h, zeta_h, false, ut_n, 1.0 / 3.0, 2.0 / 3.0, dt,
                       ut_3, G2);
@@ -594,9 +600,10 @@ struct Engine : EngineBase {
             combine_G(1.0 / 6.0, 1.0 / 6.0, 2.0 / 3.0);
             CK(btr(3, ubar_n, zeta_n, Gw, dt, M, nullptr, 0, 1, ubar_np1, Fz3, zeta_sub));
             // Step 3: F^h_3 of Sec. 3.4 and the factor 3/2
-            transport(h_h, ubar_n, ut_n, 0.5, ubar_np1, ut_3, 0.5, Fz3, consistent ? Fz1 : S1,
-                      consistent ? Fz2 : S2, 2.0 / 3.0, 1.0 / 6.0, 1.5, nullptr);
-            thickness(h_h, tr_h, 1.0 / 3.0, 2.0 / 3.0, dt, h_n, hR_n, tr_n, zeta_n);
+            transport(hR_h, zeta_h, ubar_n, ut_n, 0.5, ubar_np1, ut_3, 0.5, Fz3,
+                      consistent ? Fz1 : S1, consistent ? Fz2 : S2, 2.0 / 3.0, 1.0 / 6.0, 1.5,
+                      nullptr);
+            thickness(h_h, hR_h, tr_h, 1.0 / 3.0, 2.0 / 3.0, dt, h_n, hR_n, tr_n, zeta_n);
             std::swap(ut_n, ut_3);
             std::swap(ubar_n, ubar_np1);
         }

@@ -29,7 +29,26 @@ __device__ __forceinline__ unsigned long long gtimer() {
     return t;
 }
 
-// returns false (and sets *err) when the wait exceeded its budget
+__device__ __forceinline__ unsigned int ld_acquire(const unsigned int *p) {
+    unsigned int v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ unsigned int atom_add_acq_rel(unsigned int *p, unsigned int v) {
+    unsigned int old;
+    asm volatile("atom.add.acq_rel.gpu.global.u32 %0, [%1], %2;"
+                 : "=r"(old) : "l"(p), "r"(v) : "memory");
+    return old;
+}
+__device__ __forceinline__ void st_release(unsigned int *p, unsigned int v) {
+    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// Grid-wide barrier.  `count` grows by one per arriving block and is never
+// reset inside a launch: barrier number b (0-based) is complete when count
+// reaches (b+1) * nblocks, which its last arriver publishes by releasing
+// gen = b+1.  Waiters poll gen with acquire loads (no atomics).  Returns
+// false, after setting *err, if the wait exceeded its budget.
 __device__ __forceinline__ bool grid_barrier(const Barrier &bar, unsigned int &gen_local,
                                              unsigned int nblocks) {
     __shared__ int s_ok;
@@ -37,27 +56,24 @@ __device__ __forceinline__ bool grid_barrier(const Barrier &bar, unsigned int &g
     if (threadIdx.x == 0) {
         int ok = 1;
         const unsigned int g0 = gen_local;
-        __threadfence();
-        const unsigned int arrived = atomicAdd(bar.count, 1u);
-        if (arrived == nblocks - 1) {
-            atomicExch(bar.count, 0u);
-            __threadfence();
-            atomicAdd(bar.gen, 1u);
+        const unsigned int old = atom_add_acq_rel(bar.count, 1u);
+        if (old == (g0 + 1) * nblocks - 1) {
+            st_release(bar.gen, g0 + 1);
         } else {
             const unsigned long long t0 = gtimer();
-            unsigned int ns = 32;
-            while (atomicAdd(bar.gen, 0u) == g0) {
-                if (*((volatile int *)bar.err)) { ok = 0; break; }
-                if (gtimer() - t0 > (unsigned long long)BARRIER_SPIN_NS) {
-                    atomicExch(bar.err, 1);
-                    ok = 0;
-                    break;
+            unsigned int spins = 0;
+            while (ld_acquire(bar.gen) == g0) {
+                if ((++spins & 255u) == 0) {
+                    if (ld_acquire((const unsigned int *)bar.err) ||
+                        gtimer() - t0 > (unsigned long long)BARRIER_SPIN_NS) {
+                        atomicExch(bar.err, 1);
+                        ok = 0;
+                        break;
+                    }
                 }
-                __nanosleep(ns);
-                if (ns < 256) ns *= 2;
+                __nanosleep(20);
             }
         }
-        __threadfence();
         gen_local = g0 + 1;
         s_ok = ok;
     }
@@ -65,116 +81,176 @@ __device__ __forceinline__ bool grid_barrier(const Barrier &bar, unsigned int &g
     return s_ok != 0;
 }
 
-template <class R>
-__device__ __forceinline__ R zh_edge(const DMesh &m, const R *z, int c1, int c2) {
-    // barotropic column depth at the edge, (zeta + H)_e centred
-    return R(0.5) * ((__ldcg(z + c1) + (R)m.H[c1]) + (__ldcg(z + c2) + (R)m.H[c2]));
-}
+constexpr int BTR_NIT = 8;    // edges (and cells) owned per thread, at most
+constexpr int BTR_NE2 = 10;   // edgesOnEdge handled by the unrolled gather
 
-// one forward-Euler sub-stage of the edge equation; returns the new ubar and
-// the flux ubar (zeta + H)_e of the input state
-template <class R>
+// Per-edge forward-Euler stage of the barotropic momentum equation:
+//   ubar_new = ubar + tau (C_f(ubar) - g grad zeta + G)
+// and the flux ubar (zeta + H)_e of the input state.  Loads of the constant
+// mesh data go through the read-only path; loads of the evolving 2-D state
+// bypass L1 (__ldcg) because other blocks wrote them before the barrier.
+template <class R, int NE2>
 __device__ __forceinline__ R fe_edge(const DMesh &m, const Coef<R> &c, int e, const R *u,
-                                     const R *z, const R *G, R tau, R g, R &flux) {
-    const int2 cc = m.coe[e];
-    const int n2 = m.neoe[e];
+                                     const R *z, R Ge, R tau, R g, R &flux) {
     const int Ep = m.Ep;
+    const int n2 = __ldg(m.neoe + e);
     R cf = R(0);
-    for (int j = 0; j < n2; j++) cf += c.cfc[j * Ep + e] * __ldcg(u + m.eoe[j * Ep + e]);
+#pragma unroll
+    for (int j = 0; j < NE2; j++)
+        if (j < n2) cf += __ldg(c.cfc + j * Ep + e) * __ldcg(u + __ldg(m.eoe + j * Ep + e));
+    const int2 cc = __ldg(m.coe + e);
     const R ue = __ldcg(u + e);
     const R z1 = __ldcg(z + cc.x), z2 = __ldcg(z + cc.y);
-    flux = ue * zh_edge<R>(m, z, cc.x, cc.y);
-    return ue + tau * (cf - g * (z2 - z1) * c.invdc[e] + G[e]);
+    const R d1 = z1 + __ldg(c.H + cc.x), d2 = z2 + __ldg(c.H + cc.y);
+    flux = ue * (R(0.5) * (d1 + d2));
+    return ue + tau * (cf - g * (z2 - z1) * __ldg(c.invdc + e) + Ge);
 }
 
+// Per-cell forward-Euler stage of the barotropic continuity equation:
+//   zeta_new = zeta - tau div(ubar (zeta + H)_e), the edge depth in c1,c2 order
 template <class R>
 __device__ __forceinline__ R fe_cell(const DMesh &m, const Coef<R> &c, int i, const R *u,
                                      const R *z, R tau) {
-    const int ne = m.neoc[i];
     const int Cp = m.Cp;
+    const int ne = __ldg(m.neoc + i);
+    const R zi = __ldcg(z + i), di = zi + __ldg(c.H + i);
     R dv = R(0);
-    for (int j = 0; j < ne; j++) {
-        const int e = m.eoc[j * Cp + i];
-        const int2 cc = m.coe[e];
-        dv += c.divc[j * Cp + i] * (__ldcg(u + e) * zh_edge<R>(m, z, cc.x, cc.y));
+#pragma unroll
+    for (int j = 0; j < MAXE; j++) {
+        if (j < ne) {
+            const int e = __ldg(m.eoc + j * Cp + i), o = __ldg(m.ooc + j * Cp + i);
+            const R cj = __ldg(c.divc + j * Cp + i);
+            const R dov = __ldcg(z + o) + __ldg(c.H + o);
+            const R de = (cj > R(0)) ? (di + dov) : (dov + di);
+            dv += cj * (__ldcg(u + e) * (R(0.5) * de));
+        }
     }
-    return __ldcg(z + i) - tau * dv;
+    return zi - tau * dv;
 }
 
-template <class R, int ORDER>
+// The sub-cycle.  Thread t owns edges t, t+T, ... and cells t, t+T, ... (T =
+// threads in the grid); its own ubar, zeta, G and this sub-step's partial
+// F^zeta stay in registers, the 2-D state it shares goes through L2.
+template <class R, int ORDER, int NE2>
 __global__ void __launch_bounds__(BTR_THREADS) k_btr(DMesh m, BtrArgs<R> a, Barrier bar) {
     const Coef<R> &c = coef<R>(m);
     const unsigned int nb = gridDim.x;
-    const int stride = gridDim.x * blockDim.x;
+    const int T = gridDim.x * blockDim.x;
     const int t0 = blockIdx.x * blockDim.x + threadIdx.x;
+    const int nit = ((m.E > m.C ? m.E : m.C) + T - 1) / T;  // <= BTR_NIT (host checks)
     // count and gen are zeroed on the stream right before the launch, so every
     // block starts from generation 0
     unsigned int gen = 0;
     const R tau = (R)a.tau, g = (R)a.g;
     const int M = a.M;
     R *u0 = a.u0, *ua = a.ua, *uh = a.uh, *z0 = a.z0, *za = a.za, *zh = a.zh;
-
-    for (int e = t0; e < m.E; e += stride) {
-        u0[e] = a.ub_start[e];
-        a.Fz[e] = 0.0;
+    R u0r[BTR_NIT], z0r[BTR_NIT], Gr[BTR_NIT], Fs[BTR_NIT];
+    double Fz[BTR_NIT];
+#pragma unroll
+    for (int s = 0; s < BTR_NIT; s++) {
+        const int x = t0 + s * T;
+        u0r[s] = R(0); z0r[s] = R(0); Gr[s] = R(0); Fz[s] = 0.0; Fs[s] = R(0);
+        if (s < nit && x < m.E) {
+            u0r[s] = a.ub_start[x];
+            Gr[s] = a.G[x];
+            u0[x] = u0r[s];
+        }
+        if (s < nit && x < m.C) {
+            z0r[s] = (R)a.z_start[x];
+            z0[x] = z0r[s];
+        }
     }
-    for (int i = t0; i < m.C; i += stride) z0[i] = (R)a.z_start[i];
     if (!grid_barrier(bar, gen, nb)) return;
 
-    const double wAB = (ORDER == 2) ? 1.0 / (2.0 * M) : 1.0 / (6.0 * M);
-    const double wC = 2.0 / (3.0 * M);
+    const R wAB = (ORDER == 2) ? R(0.5) : R(1.0 / 6.0);
+    const R wC = R(2.0 / 3.0);
+    const double invM = 1.0 / M;
     for (int j = 0; j < M; j++) {
         // stage a: (ua, za) = FE(u0, z0)
-        for (int e = t0; e < m.E; e += stride) {
-            R f;
-            ua[e] = fe_edge<R>(m, c, e, u0, z0, a.G, tau, g, f);
-            a.Fz[e] += wAB * (double)f;
+#pragma unroll
+        for (int s = 0; s < BTR_NIT; s++) {
+            const int x = t0 + s * T;
+            if (s < nit) {
+                if (x < m.E) {
+                    R f;
+                    ua[x] = fe_edge<R, NE2>(m, c, x, u0, z0, Gr[s], tau, g, f);
+                    Fs[s] = wAB * f;
+                }
+                if (x < m.C) za[x] = fe_cell<R>(m, c, x, u0, z0, tau);
+            }
         }
-        for (int i = t0; i < m.C; i += stride) za[i] = fe_cell<R>(m, c, i, u0, z0, tau);
         if (!grid_barrier(bar, gen, nb)) return;
         // stage b: FE(ua, za), then the first convex combination
-        for (int e = t0; e < m.E; e += stride) {
-            R f;
-            const R ub = fe_edge<R>(m, c, e, ua, za, a.G, tau, g, f);
-            a.Fz[e] += wAB * (double)f;
-            if (ORDER == 2)
-                u0[e] = R(0.5) * (u0[e] + ub);
-            else
-                uh[e] = R(0.75) * u0[e] + R(0.25) * ub;
-        }
-        for (int i = t0; i < m.C; i += stride) {
-            const R zb = fe_cell<R>(m, c, i, ua, za, tau);
-            if (ORDER == 2)
-                z0[i] = R(0.5) * (z0[i] + zb);
-            else
-                zh[i] = R(0.75) * z0[i] + R(0.25) * zb;
+#pragma unroll
+        for (int s = 0; s < BTR_NIT; s++) {
+            const int x = t0 + s * T;
+            if (s < nit) {
+                if (x < m.E) {
+                    R f;
+                    const R ub = fe_edge<R, NE2>(m, c, x, ua, za, Gr[s], tau, g, f);
+                    Fs[s] += wAB * f;
+                    if (ORDER == 2) {
+                        u0r[s] = R(0.5) * (u0r[s] + ub);
+                        u0[x] = u0r[s];
+                        Fz[s] += invM * (double)Fs[s];
+                    } else {
+                        uh[x] = R(0.75) * u0r[s] + R(0.25) * ub;
+                    }
+                }
+                if (x < m.C) {
+                    const R zb = fe_cell<R>(m, c, x, ua, za, tau);
+                    if (ORDER == 2) {
+                        z0r[s] = R(0.5) * (z0r[s] + zb);
+                        z0[x] = z0r[s];
+                    } else {
+                        zh[x] = R(0.75) * z0r[s] + R(0.25) * zb;
+                    }
+                }
+            }
         }
         if (!grid_barrier(bar, gen, nb)) return;
         if (ORDER == 3) {
             // stage c: FE(uh, zh), then the second convex combination
-            for (int e = t0; e < m.E; e += stride) {
-                R f;
-                const R uc = fe_edge<R>(m, c, e, uh, zh, a.G, tau, g, f);
-                a.Fz[e] += wC * (double)f;
-                u0[e] = u0[e] / R(3) + R(2) * uc / R(3);
-            }
-            for (int i = t0; i < m.C; i += stride) {
-                const R zc = fe_cell<R>(m, c, i, uh, zh, tau);
-                z0[i] = z0[i] / R(3) + R(2) * zc / R(3);
+#pragma unroll
+            for (int s = 0; s < BTR_NIT; s++) {
+                const int x = t0 + s * T;
+                if (s < nit) {
+                    if (x < m.E) {
+                        R f;
+                        const R uc = fe_edge<R, NE2>(m, c, x, uh, zh, Gr[s], tau, g, f);
+                        Fs[s] += wC * f;
+                        u0r[s] = u0r[s] / R(3) + R(2) * uc / R(3);
+                        u0[x] = u0r[s];
+                        Fz[s] += invM * (double)Fs[s];
+                    }
+                    if (x < m.C) {
+                        const R zc = fe_cell<R>(m, c, x, uh, zh, tau);
+                        z0r[s] = z0r[s] / R(3) + R(2) * zc / R(3);
+                        z0[x] = z0r[s];
+                    }
+                }
             }
             if (!grid_barrier(bar, gen, nb)) return;
         }
     }
-    for (int e = t0; e < m.E; e += stride)
-        a.ub_out[e] = a.X ? (R)(a.alpha * (double)a.X[e] + a.beta * (double)u0[e]) : u0[e];
-    if (a.z_out)
-        for (int i = t0; i < m.C; i += stride) a.z_out[i] = (double)z0[i];
+#pragma unroll
+    for (int s = 0; s < BTR_NIT; s++) {
+        const int x = t0 + s * T;
+        if (s < nit && x < m.E) {
+            a.Fz[x] = Fz[s];
+            a.ub_out[x] = a.X ? (R)(a.alpha * (double)a.X[x] + a.beta * (double)u0r[s]) : u0r[s];
+        }
+        if (s < nit && x < m.C && a.z_out) a.z_out[x] = (double)z0r[s];
+    }
 }
 
 template <class R> int btr_block_size() { return BTR_THREADS; }
-template <class R> const void *btr_kernel_ptr(int order) {
-    return order == 2 ? (const void *)k_btr<R, 2> : (const void *)k_btr<R, 3>;
+template <class R> const void *btr_kernel_ptr(int order, int maxE2) {
+    if (maxE2 <= BTR_NE2)
+        return order == 2 ? (const void *)k_btr<R, 2, BTR_NE2> : (const void *)k_btr<R, 3, BTR_NE2>;
+    return order == 2 ? (const void *)k_btr<R, 2, MAXE2> : (const void *)k_btr<R, 3, MAXE2>;
 }
+int btr_max_items_per_thread() { return BTR_NIT; }
 
 template <class R>
 cudaError_t launch_btr(const DMesh &m, const BtrArgs<R> &a, const Barrier &bar, int nblocks,
@@ -195,13 +271,13 @@ cudaError_t launch_btr(const DMesh &m, const BtrArgs<R> &a, const Barrier &bar, 
     attr[0].val.cooperative = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    return cudaLaunchKernelExC(&cfg, btr_kernel_ptr<R>(a.order), args);
+    return cudaLaunchKernelExC(&cfg, btr_kernel_ptr<R>(a.order, m.maxE2), args);
 }
 
 template int btr_block_size<double>();
 template int btr_block_size<float>();
-template const void *btr_kernel_ptr<double>(int);
-template const void *btr_kernel_ptr<float>(int);
+template const void *btr_kernel_ptr<double>(int, int);
+template const void *btr_kernel_ptr<float>(int, int);
 template cudaError_t launch_btr<double>(const DMesh &, const BtrArgs<double> &, const Barrier &,
                                         int, int, cudaStream_t);
 template cudaError_t launch_btr<float>(const DMesh &, const BtrArgs<float> &, const Barrier &, int,
@@ -264,9 +340,9 @@ extern "C" int sse_barotropic_substep_noalloc(const sse_mesh *mesh, int order, d
             void *p = nullptr;
             if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess) return SSE_ERR_CUDA;
             int occ2 = 0, occ3 = 0, nsm = 0;
-            if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ2, k_btr<double, 2>,
+            if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ2, k_btr<double, 2, MAXE2>,
                                                               BTR_THREADS, 0) != cudaSuccess ||
-                cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ3, k_btr<double, 3>,
+                cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ3, k_btr<double, 3, MAXE2>,
                                                               BTR_THREADS, 0) != cudaSuccess ||
                 cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
                 return SSE_ERR_CUDA;
@@ -296,6 +372,8 @@ extern "C" int sse_barotropic_substep_noalloc(const sse_mesh *mesh, int order, d
     int blocks = nd.blocks_per_sm * nd.sms;
     if (need < blocks) blocks = need;
     if (blocks < 1) blocks = 1;
+    if ((long long)blocks * BTR_THREADS * BTR_NIT < (m.E > m.C ? m.E : m.C))
+        return SSE_ERR_UNSUPPORTED;
     if (launch_btr<double>(m, a, bar, blocks, BTR_THREADS, s) != cudaSuccess) return SSE_ERR_CUDA;
     int err = 0;
     if (cudaMemcpyAsync(&err, words + 2, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess ||

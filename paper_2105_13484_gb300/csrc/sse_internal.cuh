@@ -25,6 +25,7 @@ struct Coef {
     const R *invdc;  // [Ep]        1 / d_e
     const R *invdv;  // [Ep]        1 / l_e
     const R *fV;     // [Vp]        f at vertices
+    const R *H;      // [Cp]        resting depth
 };
 
 struct DMesh {
@@ -107,10 +108,12 @@ template <class R>
 cudaError_t launch_btr(const DMesh &m, const BtrArgs<R> &a, const Barrier &bar, int nblocks,
                        int nthreads, cudaStream_t s);
 template <class R> int btr_block_size();
-template <class R> const void *btr_kernel_ptr(int order);
+template <class R> const void *btr_kernel_ptr(int order, int maxE2);
+int btr_max_items_per_thread();
 
 template <class R> struct TransportArgs {
-    const double *h;          // stage thickness [L][Cp]
+    const R *hR;              // stage thickness [L][Cp] in the tendency precision
+    const double *zeta;       // stage SSH [Cp] (sum h - H)
     const R *ubA, *utA;       // v = wA (ubA + utA) + wB (ubB + utB)
     const R *ubB, *utB;
     double wA, wB;
@@ -118,6 +121,7 @@ template <class R> struct TransportArgs {
     double cF, cE, cA;
     int recon;
     double *S_out;            // sum_k v h_e (or null)
+    double *Fcol;             // [Ep] column-integrated mass flux, FP64
     R *flux;                  // [L][Ep] h_e (v + uA)
 };
 template <class R>
@@ -125,7 +129,9 @@ void launch_transport(const DMesh &m, const TransportArgs<R> &a, cudaStream_t s)
 
 template <class R> struct ThickArgs {
     const R *flux;            // [L][Ep]
+    const double *Fcol;       // [Ep] column-integrated flux (FP64)
     const double *h_s;        // stage thickness
+    const R *hR_s;            // stage thickness in the tendency precision
     const R *tr_s;            // stage tracers [nT][L][Cp]
     const double *h_n;        // h^n (convex combination)
     const R *tr_n;

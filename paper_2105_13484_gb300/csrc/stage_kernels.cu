@@ -173,7 +173,7 @@ __global__ void __launch_bounds__(128) k_edge_pre(DMesh m, R *__restrict__ ubar,
 // + g rho'_e grad z, so -PGF + g grad zeta = g (1 - rho_ref/rho0) grad zeta
 // - (grad p' + g rho'_e grad z) / rho0.
 // ---------------------------------------------------------------------------
-template <class R>
+template <class R, int NE2>
 __global__ void __launch_bounds__(128) k_bcl_edge(DMesh m, DParams p, const R *__restrict__ ubar,
                                                   const R *__restrict__ ut,
                                                   const R *__restrict__ hR,
@@ -187,11 +187,11 @@ __global__ void __launch_bounds__(128) k_bcl_edge(DMesh m, DParams p, const R *_
     const int2 cc = m.coe[e], vv = m.voe[e];
     const int c1 = cc.x, c2 = cc.y, v1 = vv.x, v2 = vv.y;
     const int n2 = m.neoe[e];
-    int eo[MAXE2];
-    R wl[MAXE2];
+    int eo[NE2];
+    R wl[NE2];
     R cbar = R(0);
 #pragma unroll
-    for (int j = 0; j < MAXE2; j++) {
+    for (int j = 0; j < NE2; j++) {
         if (j < n2) {
             eo[j] = m.eoe[j * Ep + e];
             wl[j] = c.wl[j * Ep + e];
@@ -204,6 +204,7 @@ __global__ void __launch_bounds__(128) k_bcl_edge(DMesh m, DParams p, const R *_
     const R ub = ubar[e];
     const R gzeta = (R)(p.zcoef * (zeta[c2] - zeta[c1])) * invdc;
     const R g = (R)p.g, inv_rho0 = (R)(1.0 / p.rho0), nu_h = (R)p.nu_h, nu_v = (R)p.nu_v;
+    const R cdrag = (R)p.c_drag;
     const R wind = p.wind ? (R)(p.wind[e] / p.rho0) : R(0);
 
     R ut_cur = ut[e];
@@ -223,7 +224,7 @@ __global__ void __launch_bounds__(128) k_bcl_edge(DMesh m, DParams p, const R *_
         const R qk = b.qe[xe];
         R Q = R(0);
 #pragma unroll
-        for (int j = 0; j < MAXE2; j++)
+        for (int j = 0; j < NE2; j++)
             if (j < n2) Q += wl[j] * b.hu[k * Ep + eo[j]] * (R(0.5) * (qk + b.qe[k * Ep + eo[j]]));
         const int x1 = k * Cp + c1, x2 = k * Cp + c2;
         const R gradK = (b.ke[x2] - b.ke[x1]) * invdc;
@@ -246,10 +247,10 @@ __global__ void __launch_bounds__(128) k_bcl_edge(DMesh m, DParams p, const R *_
         if (k == L - 1) {
             R utan = R(0);
 #pragma unroll
-            for (int j = 0; j < MAXE2; j++)
+            for (int j = 0; j < NE2; j++)
                 if (j < n2) utan += wl[j] * (ld(ubar + eo[j]) + ut[k * Ep + eo[j]]);
             const R speed = sqrt(u_cur * u_cur + utan * utan);
-            Xbot = (R)p.c_drag * speed * u_cur;
+            Xbot = cdrag * speed * u_cur;
         } else {
             Xbot = nu_v * Dk1;
         }
@@ -275,6 +276,11 @@ __global__ void __launch_bounds__(128) k_bcl_edge(DMesh m, DParams p, const R *_
 
 // ---------------------------------------------------------------------------
 // Sec. 3.4: transport velocity adjustment and edge mass flux
+//   F^h = cF * sum_k v_k h_e,k + cE * (extra terms), D = F^zeta - F^h,
+//   u^A = cA * D / sum_k h_e,k,  flux_k = h_e,k (v_k + u^A)
+// The column sums that decide D, u^A and the column-integrated flux F_col are
+// accumulated in FP64; sum_k h_e,k = ((zeta+H)_c1 + (zeta+H)_c2) / 2 because
+// zeta = sum h - H.  The per-layer flux is stored in the tendency precision.
 // ---------------------------------------------------------------------------
 template <class R>
 __global__ void __launch_bounds__(128) k_transport(DMesh m, TransportArgs<R> a) {
@@ -282,118 +288,126 @@ __global__ void __launch_bounds__(128) k_transport(DMesh m, TransportArgs<R> a) 
     if (e >= m.E) return;
     const int Ep = m.Ep, Cp = m.Cp, L = m.L;
     const int2 cc = m.coe[e];
-    const double ubA = (double)a.ubA[e];
-    const double ubB = a.ubB ? (double)a.ubB[e] : 0.0;
-    double S = 0.0, hs = 0.0;
+    const R ubA = a.ubA[e];
+    const R ubB = a.ubB ? a.ubB[e] : R(0);
+    const R wA = (R)a.wA, wB = (R)a.wB;
+    const bool twoB = a.utB != nullptr;
+    const double hs = 0.5 * ((a.zeta[cc.x] + m.H[cc.x]) + (a.zeta[cc.y] + m.H[cc.y]));
+    double S = 0.0;
     for (int k = 0; k < L; k++) {
-        const double he = 0.5 * (a.h[k * Cp + cc.x] + a.h[k * Cp + cc.y]);
-        double v = a.wA * (ubA + (double)a.utA[k * Ep + e]);
-        if (a.utB) v += a.wB * (ubB + (double)a.utB[k * Ep + e]);
-        S += v * he;
-        hs += he;
+        const R he = R(0.5) * (ld(a.hR + k * Cp + cc.x) + ld(a.hR + k * Cp + cc.y));
+        R v = wA * (ubA + a.utA[k * Ep + e]);
+        if (twoB) v += wB * (ubB + a.utB[k * Ep + e]);
+        S += (double)(v * he);
     }
     double Fh = a.cF * S;
     if (a.ex1) Fh += a.cE * a.ex1[e];
     if (a.ex2) Fh += a.cE * a.ex2[e];
     const double uA = a.recon ? a.cA * (a.Fz[e] - Fh) / hs : 0.0;
     if (a.S_out) a.S_out[e] = S;
+    a.Fcol[e] = S + uA * hs;
+    const R uAr = (R)uA;
     for (int k = 0; k < L; k++) {
-        const double he = 0.5 * (a.h[k * Cp + cc.x] + a.h[k * Cp + cc.y]);
-        double v = a.wA * (ubA + (double)a.utA[k * Ep + e]);
-        if (a.utB) v += a.wB * (ubB + (double)a.utB[k * Ep + e]);
-        a.flux[k * Ep + e] = (R)(he * (v + uA));
+        const R he = R(0.5) * (ld(a.hR + k * Cp + cc.x) + ld(a.hR + k * Cp + cc.y));
+        R v = wA * (ubA + a.utA[k * Ep + e]);
+        if (twoB) v += wB * (ubB + a.utB[k * Ep + e]);
+        a.flux[k * Ep + e] = he * (v + uAr);
     }
 }
 
 // ---------------------------------------------------------------------------
 // thickness and tracer stage (Eqs. layerthickness, tracer), z-star w from the
-// same flux, convex combination with (h^n, phi^n), zeta = sum h - H
+// same flux, convex combination with (h^n, phi^n), zeta = sum h - H.
+// With z-star, -div(h u)_k - (w_k - w_{k+1}) = -s_k sum_l div(h u)_l, so the
+// FP64 thickness update needs only the column-integrated edge flux F_col
+// (FP64, from k_transport); the per-layer flux feeds w and the tracers in the
+// tendency precision.
 // ---------------------------------------------------------------------------
 template <class R>
 __global__ void __launch_bounds__(128) k_thickness(DMesh m, DParams p, ThickArgs<R> a) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= m.C) return;
+    const Coef<R> &c = coef<R>(m);
     const int Cp = m.Cp, Ep = m.Ep, L = m.L;
     const int ne = m.neoc[i];
     int es[MAXE], os[MAXE];
-    double dcd[MAXE];
+    R dcf[MAXE], idc[MAXE];
+    double D = 0.0;
 #pragma unroll
     for (int j = 0; j < MAXE; j++) {
         if (j < ne) {
             es[j] = m.eoc[j * Cp + i];
             os[j] = m.ooc[j * Cp + i];
-            dcd[j] = m.divc_d[j * Cp + i];
+            dcf[j] = c.divc[j * Cp + i];
+            idc[j] = c.invdc[es[j]];
+            D += m.divc_d[j * Cp + i] * a.Fcol[es[j]];
         } else {
-            es[j] = 0; os[j] = i; dcd[j] = 0.0;
+            es[j] = 0; os[j] = i; dcf[j] = R(0); idc[j] = R(0);
         }
     }
-    // pass 1: flux divergence per layer and its column sum
-    double divF[LMAX];
-    double tot = 0.0;
+    const R Dr = (R)D;
+    // per-layer flux divergence (tendency precision) and w at interfaces
+    R divF[LMAX];
     for (int k = 0; k < L; k++) {
-        double s = 0.0;
+        R sdiv = R(0);
 #pragma unroll
         for (int j = 0; j < MAXE; j++)
-            if (j < ne) s += dcd[j] * (double)a.flux[k * Ep + es[j]];
-        divF[k] = s;
-        tot += s;
+            if (j < ne) sdiv += dcf[j] * ld(a.flux + k * Ep + es[j]);
+        divF[k] = sdiv;
     }
-    // pass 2: w at interfaces (w[0] = w[L] = 0)
-    double w[LMAX + 1];
-    w[L] = 0.0;
-    for (int k = L - 1; k >= 1; k--) w[k] = w[k + 1] - divF[k] + m.sfrac[k] * tot;
-    w[0] = 0.0;
-    // pass 3: thickness, then tracers
+    R w[LMAX + 1];
+    w[L] = R(0);
+    for (int k = L - 1; k >= 1; k--) w[k] = w[k + 1] - divF[k] + (R)m.sfrac[k] * Dr;
+    w[0] = R(0);
     double hsum = 0.0;
     const double dt = a.dt;
+    const R dtR = (R)dt, aR = (R)a.a, bR = (R)a.b, kh = (R)p.kappa_h, kv = (R)p.kappa_v;
     for (int k = 0; k < L; k++) {
         const int x = k * Cp + i;
-        const double h1 = a.h_s[x] + dt * (-divF[k] - (w[k] - w[k + 1]));
+        const double h1 = a.h_s[x] - dt * m.sfrac[k] * D;
         // h_out may alias h_n: read h^n before the store
         const double hn = (a.a != 0.0) ? a.h_n[x] : 0.0;
         const double hout = (a.a != 0.0) ? a.a * hn + a.b * h1 : a.b * h1;
+        const R h1r = (R)h1, houtr = (R)hout, hnr = (R)hn;
+        const R hsx = ld(a.hR_s + x);
         for (int t = 0; t < p.nT; t++) {
             const R *phi = a.tr_s + t * L * Cp;
-            const double ph = (double)phi[x];
-            double adv = 0.0, dif = 0.0;
+            const R ph = ld(phi + x);
+            R adv = R(0), dif = R(0);
 #pragma unroll
             for (int j = 0; j < MAXE; j++) {
                 if (j < ne) {
-                    const double po = (double)phi[k * Cp + os[j]];
-                    adv += dcd[j] * ((double)a.flux[k * Ep + es[j]] * (0.5 * (ph + po)));
+                    const R po = ld(phi + k * Cp + os[j]);
+                    adv += dcf[j] * (ld(a.flux + k * Ep + es[j]) * (R(0.5) * (ph + po)));
                     if (p.kappa_h != 0.0) {
-                        // h_e kappa_h grad phi, grad taken outward from cell i
-                        const double he = 0.5 * (a.h_s[x] + a.h_s[k * Cp + os[j]]);
-                        // dcd = n_{e,i} l_e / A_i; outward gradient = (po - ph)/d_e, and
-                        // n_{e,i} * grad_e(phi) = (po - ph) / d_e for either orientation
-                        dif += fabs(dcd[j]) * he * p.kappa_h * (po - ph) *
-                               (double)coef<double>(m).invdc[es[j]];
+                        // n_{e,i} grad_e(phi) = (phi_other - phi_i) / d_e for either orientation
+                        const R he = R(0.5) * (hsx + ld(a.hR_s + k * Cp + os[j]));
+                        dif += fabs(dcf[j]) * he * kh * (po - ph) * idc[j];
                     }
                 }
             }
-            double ftop = 0.0, fbot = 0.0, dtop = 0.0, dbot = 0.0;
+            R ftop = R(0), fbot = R(0), dtop = R(0), dbot = R(0);
             if (k >= 1) {
-                const double pu = (double)phi[x - Cp];
-                ftop = 0.5 * (pu + ph) * w[k];
-                dtop = (pu - ph) / (0.5 * (a.h_s[x - Cp] + a.h_s[x]));
+                const R pu = ld(phi + x - Cp);
+                ftop = R(0.5) * (pu + ph) * w[k];
+                dtop = (pu - ph) / (R(0.5) * (ld(a.hR_s + x - Cp) + hsx));
             }
             if (k + 1 <= L - 1) {
-                const double pd = (double)phi[x + Cp];
-                fbot = 0.5 * (ph + pd) * w[k + 1];
-                dbot = (ph - pd) / (0.5 * (a.h_s[x] + a.h_s[x + Cp]));
+                const R pd = ld(phi + x + Cp);
+                fbot = R(0.5) * (ph + pd) * w[k + 1];
+                dbot = (ph - pd) / (R(0.5) * (hsx + ld(a.hR_s + x + Cp)));
             }
-            const double hphi = a.h_s[x] * ph +
-                                dt * (-adv - (ftop - fbot) + dif + p.kappa_v * (dtop - dbot));
-            const double phi1 = hphi / h1;
-            double out;
+            const R hphi = hsx * ph + dtR * (-adv - (ftop - fbot) + dif + kv * (dtop - dbot));
+            const R phi1 = hphi / h1r;
+            R out;
             if (a.a != 0.0)
-                out = (a.a * hn * (double)a.tr_n[t * L * Cp + x] + a.b * h1 * phi1) / hout;
+                out = (aR * hnr * a.tr_n[t * L * Cp + x] + bR * h1r * phi1) / houtr;
             else
                 out = phi1;
-            a.tr_out[t * L * Cp + x] = (R)out;
+            a.tr_out[t * L * Cp + x] = out;
         }
         a.h_out[x] = hout;
-        if (a.hR_out) a.hR_out[x] = (R)hout;
+        if (a.hR_out) a.hR_out[x] = houtr;
         hsum += hout;
     }
     a.zeta_out[i] = hsum - m.H[i];
@@ -533,8 +547,12 @@ template <class R>
 void launch_bcl_edge(const DMesh &m, const DParams &p, const R *ubar, const R *ut, const R *hR,
                      const double *zeta, const DiagBufs<R> &b, const R *ut_n, double a,
                      double bcoef, double dt, R *ut_out, R *G, cudaStream_t s) {
-    k_bcl_edge<R><<<nblk(m.E, 128), 128, 0, s>>>(m, p, ubar, ut, hR, zeta, b, ut_n, (R)a,
-                                                  (R)bcoef, (R)dt, ut_out, G);
+    if (m.maxE2 <= 10)
+        k_bcl_edge<R, 10><<<nblk(m.E, 128), 128, 0, s>>>(m, p, ubar, ut, hR, zeta, b, ut_n, (R)a,
+                                                         (R)bcoef, (R)dt, ut_out, G);
+    else
+        k_bcl_edge<R, MAXE2><<<nblk(m.E, 128), 128, 0, s>>>(m, p, ubar, ut, hR, zeta, b, ut_n,
+                                                            (R)a, (R)bcoef, (R)dt, ut_out, G);
 }
 template <class R>
 void launch_transport(const DMesh &m, const TransportArgs<R> &a, cudaStream_t s) {
