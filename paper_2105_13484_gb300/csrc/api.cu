@@ -7,6 +7,7 @@
 // tracers, zeta) on the device; u = ubar + utilde is formed where it is read.
 #include <math.h>
 #include <stdio.h>
+#include <stdlib.h>
 #include <string.h>
 
 #include <algorithm>
@@ -16,6 +17,7 @@
 
 #include "../../include/sse.h"
 #include "sse_internal.cuh"
+#include "tiles.h"
 
 using namespace sse;
 
@@ -57,6 +59,7 @@ struct sse_mesh {
     DMesh dm;
     DevArena arena;
     int device = 0;
+    HostMesh host;  // connectivity kept for the tiled sub-cycle plan
 };
 
 // ---------------------------------------------------------------------------
@@ -188,6 +191,29 @@ extern "C" int sse_mesh_create(const sse_mesh_desc *d, sse_mesh **out) {
 
     sse_mesh *m = new (std::nothrow) sse_mesh();
     if (!m) return SSE_ERR_OOM;
+    {
+        HostMesh &hm = m->host;
+        hm.C = C; hm.E = E; hm.maxE = mE; hm.maxE2 = mE2;
+        hm.c1.resize(E); hm.c2.resize(E); hm.neoe.resize(E); hm.invdc.resize(E);
+        hm.eoe.assign((size_t)E * mE2, 0); hm.cfc.assign((size_t)E * mE2, 0.0);
+        for (int e = 0; e < E; e++) {
+            hm.c1[e] = coe[e].x; hm.c2[e] = coe[e].y; hm.neoe[e] = neoe[e];
+            hm.invdc[e] = invdc[e];
+            for (int j = 0; j < neoe[e]; j++) {
+                hm.eoe[(size_t)e * mE2 + j] = eoe[(size_t)j * Ep + e];
+                hm.cfc[(size_t)e * mE2 + j] = cfc[(size_t)j * Ep + e];
+            }
+        }
+        hm.neoc.resize(C); hm.eoc.assign((size_t)C * mE, 0); hm.divc.assign((size_t)C * mE, 0.0);
+        hm.H.resize(C);
+        for (int i = 0; i < C; i++) {
+            hm.neoc[i] = neoc[i]; hm.H[i] = H[i];
+            for (int j = 0; j < neoc[i]; j++) {
+                hm.eoc[(size_t)i * mE + j] = eoc[(size_t)j * Cp + i];
+                hm.divc[(size_t)i * mE + j] = divc[(size_t)j * Cp + i];
+            }
+        }
+    }
     cudaGetDevice(&m->device);
     DevArena &A = m->arena;
     DMesh &dm = m->dm;
@@ -315,6 +341,96 @@ struct Engine : EngineBase {
     double *dpart, *dout;
     int dparts = 0;
     int btr_blocks = 1;
+    bool tiled = false;
+    DTiles<R> tiles{};
+
+    // Plan the tiled sub-cycle: patches of >= 64 owned cells, one or two
+    // blocks per SM, halo of 3 rings (one SSPRK3 sub-step per exchange).
+    int plan_tiles(const sse_mesh *mesh, int dev, int nsm) {
+        const char *env = getenv("SSE_BTR_KERNEL");
+        if (env && strcmp(env, "global") == 0) return SSE_OK;
+        int smem_block = 0, smem_sm = 0;
+        CK(cudaDeviceGetAttribute(&smem_block, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+        CK(cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev));
+        for (int k = 1; k <= 1; k++) {
+            const int P = std::max(1, std::min(nsm * k, m.C / 64));
+            const int nthreads = 1024;
+            TilePlan plan;
+            const bool verbose = getenv("SSE_VERBOSE") != nullptr;
+            if (!build_tile_plan(mesh->host, P, 3, plan)) {
+                if (verbose) fprintf(stderr, "libsse: tile plan k=%d: 16-bit local index overflow\n", k);
+                continue;
+            }
+            const size_t smem = tile_smem_bytes(plan, m.maxE, m.maxE2, sizeof(R));
+            if (smem > (size_t)smem_block || smem * k > (size_t)smem_sm - 1024 * k) {
+                if (verbose)
+                    fprintf(stderr, "libsse: tile plan k=%d P=%d: smem %zu > limits %d/%d\n", k, P,
+                            smem, smem_block, smem_sm);
+                continue;
+            }
+
+            for (int o = 2; o <= 3; o++)
+                CK(cudaFuncSetAttribute(btr_tiled_kernel_ptr<R>(o),
+                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+            int occ = 0;
+            CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, btr_tiled_kernel_ptr<R>(3),
+                                                             nthreads, smem));
+            if (occ * nsm < P) {
+                if (verbose)
+                    fprintf(stderr, "libsse: tile plan k=%d P=%d: occupancy %d x %d SMs\n", k, P,
+                            occ, nsm);
+                continue;
+            }
+            if (verbose) {
+                int mne = 0, mnc = 0, moe = 0;
+                long long tne = 0, tnc = 0;
+                for (const TilePatch &t : plan.patches) {
+                    mne = std::max(mne, t.ne); mnc = std::max(mnc, t.nc);
+                    moe = std::max(moe, t.n_own_e); tne += t.ne; tnc += t.nc;
+                }
+                fprintf(stderr, "libsse: tiled sub-cycle P=%d smem=%zu max(ne,nc,own_e)=(%d,%d,%d) "
+                        "halo overhead edges %.2f cells %.2f\n", P, smem, mne, mnc, moe,
+                        (double)tne / m.E, (double)tnc / m.C);
+            }
+            return upload_tiles(plan, nthreads, smem);
+        }
+        return SSE_OK;  // no plan fits: the global-memory sub-cycle is used
+    }
+
+    int upload_tiles(const TilePlan &plan, int nthreads, size_t smem) {
+        std::vector<int> noc, noe, cg, eg, c12;
+        std::vector<short> n2, eo, nce, ce;
+        std::vector<R> cf, idc, dv, Hh;
+        for (const TilePatch &t : plan.patches) {
+            noc.push_back(t.n_own_c); noe.push_back(t.n_own_e);
+            cg.insert(cg.end(), t.cell_gid.begin(), t.cell_gid.end());
+            eg.insert(eg.end(), t.edge_gid.begin(), t.edge_gid.end());
+            c12.insert(c12.end(), t.c12.begin(), t.c12.end());
+            n2.insert(n2.end(), t.n2.begin(), t.n2.end());
+            eo.insert(eo.end(), t.eoe.begin(), t.eoe.end());
+            for (double x : t.cfc) cf.push_back((R)x);
+            for (double x : t.invdc) idc.push_back((R)x);
+            nce.insert(nce.end(), t.nce.begin(), t.nce.end());
+            ce.insert(ce.end(), t.ce.begin(), t.ce.end());
+            for (double x : t.divc) dv.push_back((R)x);
+            for (double x : t.H) Hh.push_back((R)x);
+        }
+        DTiles<R> &t = tiles;
+        t.P = plan.P; t.maxE = m.maxE; t.maxE2 = m.maxE2; t.nthreads = nthreads;
+        t.fs_per_thread = 4; t.smem = smem;
+        t.cell_off = A.upload(plan.cell_off); t.edge_off = A.upload(plan.edge_off);
+        t.n_own_c = A.upload(noc); t.n_own_e = A.upload(noe);
+        t.cell_gid = A.upload(cg); t.edge_gid = A.upload(eg); t.c12 = A.upload(c12);
+        t.n2 = A.upload(n2); t.eoe = A.upload(eo); t.cfc = A.upload(cf); t.invdc = A.upload(idc);
+        t.nce = A.upload(nce); t.ce = A.upload(ce); t.divc = A.upload(dv); t.H = A.upload(Hh);
+        for (int b = 0; b < 2; b++) {
+            t.xu[b] = A.alloc<R>(m.Ep);
+            t.xz[b] = A.alloc<R>(m.Cp);
+        }
+        if (A.failed) return SSE_ERR_OOM;
+        tiled = true;
+        return SSE_OK;
+    }
 
     int init(const sse_mesh *mesh, const sse_params *prm, cudaStream_t st) {
         m = mesh->dm;
@@ -378,6 +494,8 @@ struct Engine : EngineBase {
         // every thread keeps at most btr_max_items_per_thread() edges in registers
         if ((long long)btr_blocks * bt * btr_max_items_per_thread() < std::max(m.E, m.C))
             return SSE_ERR_UNSUPPORTED;
+        int rc = plan_tiles(mesh, dev, nsm);
+        if (rc) return rc;
         CK(cudaStreamSynchronize(s));
         return SSE_OK;
     }
@@ -529,7 +647,8 @@ struct Engine : EngineBase {
         cudaError_t me = cudaMemsetAsync(barwords, 0, 2 * sizeof(unsigned int), s);
         if (me != cudaSuccess) return me;
         pbeg(SSE_K_BTR);
-        cudaError_t e = launch_btr<R>(m, a, bar(), btr_blocks, btr_block_size<R>(), s);
+        cudaError_t e = tiled ? launch_btr_tiled<R>(tiles, a, bar(), s)
+                              : launch_btr<R>(m, a, bar(), btr_blocks, btr_block_size<R>(), s);
         pend();
         return e;
     }

@@ -244,6 +244,235 @@ __global__ void __launch_bounds__(BTR_THREADS) k_btr(DMesh m, BtrArgs<R> a, Barr
     }
 }
 
+// ---------------------------------------------------------------------------
+// Tiled, communication-avoiding sub-cycle.  One block per patch.  The patch's
+// 2-D state (ubar, zeta and the sub-stage copies), forcing, depths and local
+// connectivity live in shared memory; the TRiSK Coriolis coefficients stream
+// from global memory.  All forward-Euler sub-stages of one sub-step run on
+// the patch with block-level barriers only (the halo of K >= 3 rings keeps
+// the owned values exact); after each sub-step the owned ubar and zeta go
+// through a double-buffered exchange array and one grid barrier refreshes the
+// halo.  M grid barriers per call instead of 2M or 3M.
+// ---------------------------------------------------------------------------
+constexpr int TILE_THREADS = 1024;
+
+template <class R> struct TileSmem {
+    double *Fz;                       // [n_own_e] accumulated flux of the call
+    R *u0, *ua, *uh, *fl, *z0, *za, *zh, *G, *H, *Fs;
+    int *c12;
+    short *n2, *nce, *eoe, *ce;
+    const R *idc, *dvc;  // read-only coefficients, left in global memory
+};
+
+template <class R>
+__device__ __forceinline__ TileSmem<R> carve(char *base, int ne, int nc, int noe, int maxE,
+                                             int maxE2) {
+    TileSmem<R> s;
+    double *d = (double *)base;
+    s.Fz = d; d += noe;
+    R *r = (R *)d;
+    const int ne1 = ne + 1, nc1 = nc + 1;
+    s.u0 = r; r += ne1; s.ua = r; r += ne1; s.uh = r; r += ne1; s.fl = r; r += ne1;
+    s.z0 = r; r += nc1; s.za = r; r += nc1; s.zh = r; r += nc1;
+    s.G = r; r += ne1; s.H = r; r += nc1; s.Fs = r; r += noe;
+    int *ip = (int *)r;
+    s.c12 = ip; ip += ne1;
+    short *sp = (short *)ip;
+    s.n2 = sp; sp += ne1; s.nce = sp; sp += nc1;
+    s.eoe = sp; sp += (size_t)maxE2 * ne1;
+    s.ce = sp;
+    return s;
+}
+
+// forward-Euler edge update on the patch: returns the new ubar, sets the flux
+template <class R, int NE2>
+__device__ __forceinline__ R tile_fe_edge(const TileSmem<R> &S, const R *__restrict__ cfc, int l,
+                                          int ne, const R *u, const R *z, R tau, R g, R &flux) {
+    const int n2 = S.n2[l];
+    const short *eo = S.eoe + l;
+    const R *cf_l = cfc + l;
+    const int se = ne + 1;
+    R cf = R(0);
+#pragma unroll
+    for (int j = 0; j < NE2; j++)
+        if (j < n2) cf += __ldg(cf_l + j * ne) * u[eo[j * se]];
+    const int cc = S.c12[l];
+    const int a = cc & 0xffff, b = (cc >> 16) & 0xffff;
+    const R za = z[a], zb = z[b];
+    const R ue = u[l];
+    flux = ue * (R(0.5) * ((za + S.H[a]) + (zb + S.H[b])));
+    return ue + tau * (cf - g * (zb - za) * __ldg(S.idc + l) + S.G[l]);
+}
+
+template <class R>
+__device__ __forceinline__ R tile_fe_cell(const TileSmem<R> &S, int l, int nc, const R *z,
+                                          R tau) {
+    const int n = S.nce[l];
+    const short *ce = S.ce + l;
+    const R *dv_l = S.dvc + l;
+    const int sc = nc + 1;
+    R dv = R(0);
+#pragma unroll
+    for (int j = 0; j < MAXE; j++)
+        if (j < n) dv += __ldg(dv_l + j * nc) * S.fl[ce[j * sc]];
+    return z[l] - tau * dv;
+}
+
+template <class R, int ORDER, int NE2>
+__global__ void __launch_bounds__(TILE_THREADS, 1) k_btr_tiled(DTiles<R> t, BtrArgs<R> a,
+                                                               Barrier bar) {
+    extern __shared__ __align__(16) char smem_raw[];
+    const int p = blockIdx.x, tid = threadIdx.x, nt = blockDim.x;
+    const int coff = t.cell_off[p], eoff = t.edge_off[p];
+    const int nc = t.cell_off[p + 1] - coff, ne = t.edge_off[p + 1] - eoff;
+    const int noc = t.n_own_c[p], noe = t.n_own_e[p];
+    const int maxE = t.maxE, maxE2 = t.maxE2;
+    TileSmem<R> S = carve<R>(smem_raw, ne, nc, noe, maxE, maxE2);
+    S.idc = t.invdc + eoff;
+    S.dvc = t.divc + (size_t)coff * maxE;
+    const R *cfc = t.cfc + (size_t)eoff * maxE2;
+    const R tau = (R)a.tau, g = (R)a.g;
+    unsigned int gen = 0;
+
+    // ---- load the patch
+    for (int l = tid; l <= ne; l += nt) {
+        if (l < ne) {
+            const int gid = t.edge_gid[eoff + l];
+            S.u0[l] = a.ub_start[gid];
+            S.G[l] = a.G[gid];
+            S.c12[l] = t.c12[eoff + l];
+            S.n2[l] = t.n2[eoff + l];
+        } else {
+            S.u0[l] = R(0); S.G[l] = R(0);
+            S.c12[l] = nc | (nc << 16);
+            S.n2[l] = 0;
+        }
+        S.ua[l] = R(0); S.uh[l] = R(0); S.fl[l] = R(0);
+    }
+    for (int l = tid; l < noe; l += nt) { S.Fz[l] = 0.0; S.Fs[l] = R(0); }
+    for (int x = tid; x < maxE2 * ne; x += nt) {
+        const int j = x / ne, l = x - j * ne;
+        S.eoe[j * (ne + 1) + l] = t.eoe[(size_t)eoff * maxE2 + x];
+    }
+    for (int l = tid; l <= nc; l += nt) {
+        if (l < nc) {
+            S.z0[l] = (R)a.z_start[t.cell_gid[coff + l]];
+            S.nce[l] = t.nce[coff + l];
+        } else {
+            S.z0[l] = R(0);
+            S.nce[l] = 0;
+        }
+        S.H[l] = t.H[coff + p + l];
+        S.za[l] = S.z0[l]; S.zh[l] = S.z0[l];
+    }
+    for (int x = tid; x < maxE * nc; x += nt) {
+        const int j = x / nc, l = x - j * nc;
+        S.ce[j * (nc + 1) + l] = t.ce[(size_t)coff * maxE + x];
+    }
+    __syncthreads();
+
+    const R wAB = (ORDER == 2) ? R(0.5) : R(1.0 / 6.0);
+    const R wC = R(2.0 / 3.0);
+    const double invM = 1.0 / a.M;
+    int buf = 0;
+    for (int j = 0; j < a.M; j++) {
+        // ---- stage a: (ua, za) = FE(u0, z0)
+        for (int l = tid; l < ne; l += nt) {
+            R f;
+            S.ua[l] = tile_fe_edge<R, NE2>(S, cfc, l, ne, S.u0, S.z0, tau, g, f);
+            S.fl[l] = f;
+            if (l < noe) S.Fs[l] = wAB * f;
+        }
+        __syncthreads();
+        for (int l = tid; l < nc; l += nt) S.za[l] = tile_fe_cell<R>(S, l, nc, S.z0, tau);
+        __syncthreads();
+        // ---- stage b: FE(ua, za), first convex combination
+        for (int l = tid; l < ne; l += nt) {
+            R f;
+            const R ub = tile_fe_edge<R, NE2>(S, cfc, l, ne, S.ua, S.za, tau, g, f);
+            S.fl[l] = f;
+            if (l < noe) S.Fs[l] += wAB * f;
+            if (ORDER == 2) S.u0[l] = R(0.5) * (S.u0[l] + ub);
+            else S.uh[l] = R(0.75) * S.u0[l] + R(0.25) * ub;
+        }
+        __syncthreads();
+        for (int l = tid; l < nc; l += nt) {
+            const R zb = tile_fe_cell<R>(S, l, nc, S.za, tau);
+            if (ORDER == 2) S.z0[l] = R(0.5) * (S.z0[l] + zb);
+            else S.zh[l] = R(0.75) * S.z0[l] + R(0.25) * zb;
+        }
+        __syncthreads();
+        if (ORDER == 3) {
+            // ---- stage c: FE(uh, zh), second convex combination
+            for (int l = tid; l < ne; l += nt) {
+                R f;
+                const R uc = tile_fe_edge<R, NE2>(S, cfc, l, ne, S.uh, S.zh, tau, g, f);
+                S.fl[l] = f;
+                if (l < noe) S.Fs[l] += wC * f;
+                S.u0[l] = S.u0[l] / R(3) + R(2) * uc / R(3);
+            }
+            __syncthreads();
+            for (int l = tid; l < nc; l += nt) {
+                const R zc = tile_fe_cell<R>(S, l, nc, S.zh, tau);
+                S.z0[l] = S.z0[l] / R(3) + R(2) * zc / R(3);
+            }
+            __syncthreads();
+        }
+        for (int l = tid; l < noe; l += nt) S.Fz[l] += invM * (double)S.Fs[l];
+        if (j + 1 == a.M) break;
+        // ---- exchange the owned values, refresh the halo
+        R *xu = t.xu[buf], *xz = t.xz[buf];
+        for (int l = tid; l < noe; l += nt) xu[t.edge_gid[eoff + l]] = S.u0[l];
+        for (int l = tid; l < noc; l += nt) xz[t.cell_gid[coff + l]] = S.z0[l];
+        if (!grid_barrier(bar, gen, gridDim.x)) return;
+        for (int l = noe + tid; l < ne; l += nt) S.u0[l] = __ldcg(xu + t.edge_gid[eoff + l]);
+        for (int l = noc + tid; l < nc; l += nt) S.z0[l] = __ldcg(xz + t.cell_gid[coff + l]);
+        buf ^= 1;
+        __syncthreads();
+    }
+    // ---- outputs for the owned edges and cells
+    for (int l = tid; l < noe; l += nt) {
+        const int gid = t.edge_gid[eoff + l];
+        a.Fz[gid] = S.Fz[l];
+        a.ub_out[gid] = a.X ? (R)(a.alpha * (double)a.X[gid] + a.beta * (double)S.u0[l])
+                            : S.u0[l];
+    }
+    if (a.z_out)
+        for (int l = tid; l < noc; l += nt) a.z_out[t.cell_gid[coff + l]] = (double)S.z0[l];
+}
+
+template <class R> const void *btr_tiled_kernel_ptr(int order) {
+    return order == 2 ? (const void *)k_btr_tiled<R, 2, BTR_NE2>
+                      : (const void *)k_btr_tiled<R, 3, BTR_NE2>;
+}
+
+template <class R>
+cudaError_t launch_btr_tiled(const DTiles<R> &t, const BtrArgs<R> &a, const Barrier &bar,
+                             cudaStream_t s) {
+    DTiles<R> tt = t;
+    BtrArgs<R> aa = a;
+    Barrier bb = bar;
+    void *args[] = {&tt, &aa, &bb};
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(t.P);
+    cfg.blockDim = dim3(t.nthreads);
+    cfg.dynamicSmemBytes = t.smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelExC(&cfg, btr_tiled_kernel_ptr<R>(a.order), args);
+}
+
+template const void *btr_tiled_kernel_ptr<double>(int);
+template const void *btr_tiled_kernel_ptr<float>(int);
+template cudaError_t launch_btr_tiled<double>(const DTiles<double> &, const BtrArgs<double> &,
+                                              const Barrier &, cudaStream_t);
+template cudaError_t launch_btr_tiled<float>(const DTiles<float> &, const BtrArgs<float> &,
+                                             const Barrier &, cudaStream_t);
+
 template <class R> int btr_block_size() { return BTR_THREADS; }
 template <class R> const void *btr_kernel_ptr(int order, int maxE2) {
     if (maxE2 <= BTR_NE2)

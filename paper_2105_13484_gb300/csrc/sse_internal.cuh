@@ -111,6 +111,31 @@ template <class R> int btr_block_size();
 template <class R> const void *btr_kernel_ptr(int order, int maxE2);
 int btr_max_items_per_thread();
 
+// Device copy of the tiled sub-cycle plan (see tiles.h): per-patch arrays
+// flattened with the offsets cell_off / edge_off.
+template <class R> struct DTiles {
+    int P, maxE, maxE2, nthreads, fs_per_thread;
+    const int *cell_off, *edge_off;  // [P + 1]
+    const int *n_own_c, *n_own_e;    // [P]
+    const int *cell_gid, *edge_gid;  // local -> global
+    const int *c12;                  // [sum ne] packed local c1 | c2 << 16
+    const short *n2;                 // [sum ne]
+    const short *eoe;                // patch p at edge_off[p] * maxE2: [maxE2][ne_p]
+    const R *cfc;                    // same layout as eoe
+    const R *invdc;                  // [sum ne]
+    const short *nce;                // [sum nc]
+    const short *ce;                 // patch p at cell_off[p] * maxE: [maxE][nc_p]
+    const R *divc;                   // same layout as ce
+    const R *H;                      // patch p at cell_off[p] + p: [nc_p + 1]
+    R *xu[2];                        // [Ep] exchange of owned ubar, double-buffered
+    R *xz[2];                        // [Cp] exchange of owned zeta
+    size_t smem;                     // dynamic shared memory per block
+};
+template <class R>
+cudaError_t launch_btr_tiled(const DTiles<R> &t, const BtrArgs<R> &a, const Barrier &bar,
+                             cudaStream_t s);
+template <class R> const void *btr_tiled_kernel_ptr(int order);
+
 template <class R> struct TransportArgs {
     const R *hR;              // stage thickness [L][Cp] in the tendency precision
     const double *zeta;       // stage SSH [Cp] (sum h - H)

@@ -1,0 +1,48 @@
+// tiles.h -- host-side patch plan of the tiled barotropic sub-cycle.
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+#include <vector>
+
+namespace sse {
+
+// host copy of the connectivity and coefficients the plan needs
+struct HostMesh {
+    int C = 0, E = 0, maxE = 0, maxE2 = 0;
+    std::vector<int> c1, c2;      // [E]
+    std::vector<int> neoc, eoc;   // [C], [C][maxE]
+    std::vector<int> neoe, eoe;   // [E], [E][maxE2]
+    std::vector<double> cfc;      // [E][maxE2] w l'/d (f+f')/2
+    std::vector<double> divc;     // [C][maxE]  n l / A
+    std::vector<double> invdc;    // [E]
+    std::vector<double> H;        // [C]
+};
+
+struct TilePatch {
+    int nc = 0, ne = 0, n_own_c = 0, n_own_e = 0;
+    std::vector<int> cell_gid, edge_gid;   // local -> global (owned first)
+    std::vector<int32_t> c12;              // [ne] local c1 | c2 << 16
+    std::vector<int16_t> n2;               // [ne]
+    std::vector<int16_t> eoe;              // [maxE2][ne] local (dummy = ne)
+    std::vector<double> cfc;               // [maxE2][ne]
+    std::vector<double> invdc;             // [ne]
+    std::vector<int16_t> nce;              // [nc]
+    std::vector<int16_t> ce;               // [maxE][nc] local edges (dummy = ne)
+    std::vector<double> divc;              // [maxE][nc]
+    std::vector<double> H;                 // [nc + 1]
+};
+
+struct TilePlan {
+    int P = 0, K = 0;
+    std::vector<TilePatch> patches;
+    std::vector<int> cell_off, edge_off;   // [P + 1] prefix sums of nc, ne
+};
+
+// Partition into P patches with halos of K rings; false if a patch would
+// need more than 32766 local entries.
+bool build_tile_plan(const HostMesh &hm, int P, int K, TilePlan &plan);
+// Dynamic shared memory of the largest patch for element size sR.
+size_t tile_smem_bytes(const TilePlan &plan, int maxE, int maxE2, size_t sR);
+
+}  // namespace sse
