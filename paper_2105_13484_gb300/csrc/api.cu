@@ -352,6 +352,7 @@ struct Engine : EngineBase {
         int smem_block = 0, smem_sm = 0;
         CK(cudaDeviceGetAttribute(&smem_block, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
         CK(cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev));
+        if (m.maxE2 > 10 || m.maxE > TILE_NCEP) return SSE_OK;
         for (int k = 1; k <= 1; k++) {
             const int P = std::max(1, std::min(nsm * k, m.C / 64));
             const int nthreads = 1024;
@@ -359,6 +360,16 @@ struct Engine : EngineBase {
             const bool verbose = getenv("SSE_VERBOSE") != nullptr;
             if (!build_tile_plan(mesh->host, P, 3, plan)) {
                 if (verbose) fprintf(stderr, "libsse: tile plan k=%d: 16-bit local index overflow\n", k);
+                continue;
+            }
+            bool small = true;  // 16-bit byte offsets; <= 2 entries of each kind per thread
+            for (const TilePatch &t : plan.patches)
+                if ((size_t)(t.ne + 1) * sizeof(R) >= 65536 || (size_t)(t.nc + 1) * sizeof(R) >= 65536 ||
+                    t.n_own_e > 2 * nthreads || t.ne - t.n_own_e > 2 * nthreads ||
+                    t.n_own_c > 2 * nthreads || t.nc - t.n_own_c > 2 * nthreads)
+                    small = false;
+            if (!small) {
+                if (verbose) fprintf(stderr, "libsse: tile plan k=%d: patch too large\n", k);
                 continue;
             }
             const size_t smem = tile_smem_bytes(plan, m.maxE, m.maxE2, sizeof(R));
@@ -398,31 +409,43 @@ struct Engine : EngineBase {
     }
 
     int upload_tiles(const TilePlan &plan, int nthreads, size_t smem) {
+        const unsigned int sR = sizeof(R);
         std::vector<int> noc, noe, cg, eg, c12;
-        std::vector<short> n2, eo, nce, ce;
+        std::vector<unsigned short> eo, ce;
         std::vector<R> cf, idc, dv, Hh;
         for (const TilePatch &t : plan.patches) {
             noc.push_back(t.n_own_c); noe.push_back(t.n_own_e);
             cg.insert(cg.end(), t.cell_gid.begin(), t.cell_gid.end());
             eg.insert(eg.end(), t.edge_gid.begin(), t.edge_gid.end());
-            c12.insert(c12.end(), t.c12.begin(), t.c12.end());
-            n2.insert(n2.end(), t.n2.begin(), t.n2.end());
-            eo.insert(eo.end(), t.eoe.begin(), t.eoe.end());
-            for (double x : t.cfc) cf.push_back((R)x);
-            for (double x : t.invdc) idc.push_back((R)x);
-            nce.insert(nce.end(), t.nce.begin(), t.nce.end());
-            ce.insert(ce.end(), t.ce.begin(), t.ce.end());
-            for (double x : t.divc) dv.push_back((R)x);
+            for (int32_t x : t.c12) {
+                const unsigned int a = (unsigned int)x & 0xffffu, b = (unsigned int)x >> 16;
+                c12.push_back((int)((a * sR) | ((b * sR) << 16)));
+            }
+            for (int k = 0; k < t.ne; k++) {
+                for (int j = 0; j < TILE_NE2P; j++) {
+                    const bool on = j < t.n2[k];
+                    const int le = on ? t.eoe[(size_t)k * m.maxE2 + j] : t.ne;
+                    eo.push_back((unsigned short)(le * sR));
+                    cf.push_back(on ? (R)t.cfc[(size_t)k * m.maxE2 + j] : R(0));
+                }
+                idc.push_back((R)t.invdc[k]);
+            }
+            for (int k = 0; k < t.nc; k++)
+                for (int j = 0; j < TILE_NCEP; j++) {
+                    const bool on = j < t.nce[k];
+                    const int le = on ? t.ce[(size_t)k * m.maxE + j] : t.ne;
+                    ce.push_back((unsigned short)(le * sR));
+                    dv.push_back(on ? (R)t.divc[(size_t)k * m.maxE + j] : R(0));
+                }
             for (double x : t.H) Hh.push_back((R)x);
         }
         DTiles<R> &t = tiles;
-        t.P = plan.P; t.maxE = m.maxE; t.maxE2 = m.maxE2; t.nthreads = nthreads;
-        t.fs_per_thread = 4; t.smem = smem;
+        t.P = plan.P; t.nthreads = nthreads; t.smem = smem;
         t.cell_off = A.upload(plan.cell_off); t.edge_off = A.upload(plan.edge_off);
         t.n_own_c = A.upload(noc); t.n_own_e = A.upload(noe);
         t.cell_gid = A.upload(cg); t.edge_gid = A.upload(eg); t.c12 = A.upload(c12);
-        t.n2 = A.upload(n2); t.eoe = A.upload(eo); t.cfc = A.upload(cf); t.invdc = A.upload(idc);
-        t.nce = A.upload(nce); t.ce = A.upload(ce); t.divc = A.upload(dv); t.H = A.upload(Hh);
+        t.eoe = A.upload(eo); t.cfc = A.upload(cf); t.invdc = A.upload(idc);
+        t.ce = A.upload(ce); t.divc = A.upload(dv); t.H = A.upload(Hh);
         for (int b = 0; b < 2; b++) {
             t.xu[b] = A.alloc<R>(m.Ep);
             t.xz[b] = A.alloc<R>(m.Cp);

@@ -17,6 +17,7 @@
 
 #include "../../include/sse.h"
 #include "sse_internal.cuh"
+#include "tiles.h"
 
 namespace sse {
 
@@ -219,13 +220,13 @@ __global__ void __launch_bounds__(BTR_THREADS) k_btr(DMesh m, BtrArgs<R> a, Barr
                         R f;
                         const R uc = fe_edge<R, NE2>(m, c, x, uh, zh, Gr[s], tau, g, f);
                         Fs[s] += wC * f;
-                        u0r[s] = u0r[s] / R(3) + R(2) * uc / R(3);
+                        u0r[s] = R(1.0 / 3.0) * u0r[s] + R(2.0 / 3.0) * uc;
                         u0[x] = u0r[s];
                         Fz[s] += invM * (double)Fs[s];
                     }
                     if (x < m.C) {
                         const R zc = fe_cell<R>(m, c, x, uh, zh, tau);
-                        z0r[s] = z0r[s] / R(3) + R(2) * zc / R(3);
+                        z0r[s] = R(1.0 / 3.0) * z0r[s] + R(2.0 / 3.0) * zc;
                         z0[x] = z0r[s];
                     }
                 }
@@ -255,70 +256,98 @@ __global__ void __launch_bounds__(BTR_THREADS) k_btr(DMesh m, BtrArgs<R> a, Barr
 // halo.  M grid barriers per call instead of 2M or 3M.
 // ---------------------------------------------------------------------------
 constexpr int TILE_THREADS = 1024;
+constexpr int TILE_NE2 = 10;  // edgesOnEdge terms evaluated per edge (padding -> dummy, 0)
 
 template <class R> struct TileSmem {
-    double *Fz;                       // [n_own_e] accumulated flux of the call
-    R *u0, *ua, *uh, *fl, *z0, *za, *zh, *G, *H, *Fs;
-    int *c12;
-    short *n2, *nce, *eoe, *ce;
-    const R *idc, *dvc;  // read-only coefficients, left in global memory
+    R *u0, *ua, *uh, *fl, *z0, *za, *zh, *G, *H, *idc;
+    unsigned int *c12;                // packed byte offsets of (c1, c2) into the cell arrays
+    unsigned short *eoe;              // [ne+1][TILE_NE2P] byte offsets into the edge arrays
+    unsigned short *ce;               // [nc+1][TILE_NCEP] byte offsets into fl
 };
 
+__device__ __forceinline__ char *align16(char *p) {
+    return (char *)(((uintptr_t)p + 15) & ~(uintptr_t)15);
+}
+
 template <class R>
-__device__ __forceinline__ TileSmem<R> carve(char *base, int ne, int nc, int noe, int maxE,
-                                             int maxE2) {
+__device__ __forceinline__ TileSmem<R> carve(char *base, int ne, int nc) {
     TileSmem<R> s;
-    double *d = (double *)base;
-    s.Fz = d; d += noe;
-    R *r = (R *)d;
+    char *c = align16(base);
     const int ne1 = ne + 1, nc1 = nc + 1;
+    R *r = (R *)c;
     s.u0 = r; r += ne1; s.ua = r; r += ne1; s.uh = r; r += ne1; s.fl = r; r += ne1;
     s.z0 = r; r += nc1; s.za = r; r += nc1; s.zh = r; r += nc1;
-    s.G = r; r += ne1; s.H = r; r += nc1; s.Fs = r; r += noe;
-    int *ip = (int *)r;
-    s.c12 = ip; ip += ne1;
-    short *sp = (short *)ip;
-    s.n2 = sp; sp += ne1; s.nce = sp; sp += nc1;
-    s.eoe = sp; sp += (size_t)maxE2 * ne1;
-    s.ce = sp;
+    s.G = r; r += ne1; s.H = r; r += nc1; s.idc = r; r += ne1;
+    c = align16((char *)r);
+    s.c12 = (unsigned int *)c; c = align16(c + 4 * ne1);
+    s.eoe = (unsigned short *)c; c = align16(c + 2 * TILE_NE2P * (size_t)ne1);
+    s.ce = (unsigned short *)c;
     return s;
 }
 
+template <class R> __device__ __forceinline__ R at(const R *base, unsigned int off) {
+    return *(const R *)((const char *)base + off);
+}
+
+// the coefficients of one edge (TILE_NE2P) or one cell (TILE_NCEP) with 128-bit loads
+__device__ __forceinline__ void ldc(const float *p, float *c, int n) {
+    for (int i = 0; i < n / 4; i++) {
+        const float4 v = __ldg((const float4 *)p + i);
+        c[4 * i] = v.x; c[4 * i + 1] = v.y; c[4 * i + 2] = v.z; c[4 * i + 3] = v.w;
+    }
+}
+__device__ __forceinline__ void ldc(const double *p, double *c, int n) {
+    for (int i = 0; i < n / 2; i++) {
+        const double2 v = __ldg((const double2 *)p + i);
+        c[2 * i] = v.x; c[2 * i + 1] = v.y;
+    }
+}
+
 // forward-Euler edge update on the patch: returns the new ubar, sets the flux
-template <class R, int NE2>
+template <class R>
 __device__ __forceinline__ R tile_fe_edge(const TileSmem<R> &S, const R *__restrict__ cfc, int l,
-                                          int ne, const R *u, const R *z, R tau, R g, R &flux) {
-    const int n2 = S.n2[l];
-    const short *eo = S.eoe + l;
-    const R *cf_l = cfc + l;
-    const int se = ne + 1;
-    R cf = R(0);
+                                          const R *u, const R *z, R tau, R g, R &flux) {
+    R cf[TILE_NE2P];
+    ldc(cfc + (size_t)l * TILE_NE2P, cf, TILE_NE2P);
+    const uint2 *eo = (const uint2 *)(S.eoe + (size_t)l * TILE_NE2P);
+    unsigned int o[TILE_NE2P];
 #pragma unroll
-    for (int j = 0; j < NE2; j++)
-        if (j < n2) cf += __ldg(cf_l + j * ne) * u[eo[j * se]];
-    const int cc = S.c12[l];
-    const int a = cc & 0xffff, b = (cc >> 16) & 0xffff;
-    const R za = z[a], zb = z[b];
+    for (int i = 0; i < TILE_NE2P / 4; i++) {
+        const uint2 v = eo[i];
+        o[4 * i] = v.x & 0xffffu; o[4 * i + 1] = v.x >> 16;
+        o[4 * i + 2] = v.y & 0xffffu; o[4 * i + 3] = v.y >> 16;
+    }
+    R acc = R(0);
+#pragma unroll
+    for (int j = 0; j < TILE_NE2; j++) acc += cf[j] * at(u, o[j]);
+    const unsigned int cc = S.c12[l];
+    const unsigned int a = cc & 0xffffu, b = cc >> 16;
+    const R za = at(z, a), zb = at(z, b);
     const R ue = u[l];
-    flux = ue * (R(0.5) * ((za + S.H[a]) + (zb + S.H[b])));
-    return ue + tau * (cf - g * (zb - za) * __ldg(S.idc + l) + S.G[l]);
+    flux = ue * (R(0.5) * ((za + at(S.H, a)) + (zb + at(S.H, b))));
+    return ue + tau * (acc - g * (zb - za) * S.idc[l] + S.G[l]);
 }
 
 template <class R>
-__device__ __forceinline__ R tile_fe_cell(const TileSmem<R> &S, int l, int nc, const R *z,
-                                          R tau) {
-    const int n = S.nce[l];
-    const short *ce = S.ce + l;
-    const R *dv_l = S.dvc + l;
-    const int sc = nc + 1;
+__device__ __forceinline__ R tile_fe_cell(const TileSmem<R> &S, const R *__restrict__ dvc, int l,
+                                          const R *z, R tau) {
+    R dc[TILE_NCEP];
+    ldc(dvc + (size_t)l * TILE_NCEP, dc, TILE_NCEP);
+    const uint4 v = *(const uint4 *)(S.ce + (size_t)l * TILE_NCEP);
+    const unsigned int o[8] = {v.x & 0xffffu, v.x >> 16, v.y & 0xffffu, v.y >> 16,
+                               v.z & 0xffffu, v.z >> 16, v.w & 0xffffu, v.w >> 16};
     R dv = R(0);
 #pragma unroll
-    for (int j = 0; j < MAXE; j++)
-        if (j < n) dv += __ldg(dv_l + j * nc) * S.fl[ce[j * sc]];
+    for (int j = 0; j < TILE_NCEP; j++) dv += dc[j] * at(S.fl, o[j]);
     return z[l] - tau * dv;
 }
 
-template <class R, int ORDER, int NE2>
+// Each thread owns at most TILE_OWN owned edges, halo edges, owned cells and
+// halo cells of its patch (the plan checks this); their global indices, the
+// sub-step's partial F^zeta and the FP64 accumulators stay in registers.
+constexpr int TILE_OWN = 2;
+
+template <class R, int ORDER>
 __global__ void __launch_bounds__(TILE_THREADS, 1) k_btr_tiled(DTiles<R> t, BtrArgs<R> a,
                                                                Barrier bar) {
     extern __shared__ __align__(16) char smem_raw[];
@@ -326,49 +355,62 @@ __global__ void __launch_bounds__(TILE_THREADS, 1) k_btr_tiled(DTiles<R> t, BtrA
     const int coff = t.cell_off[p], eoff = t.edge_off[p];
     const int nc = t.cell_off[p + 1] - coff, ne = t.edge_off[p + 1] - eoff;
     const int noc = t.n_own_c[p], noe = t.n_own_e[p];
-    const int maxE = t.maxE, maxE2 = t.maxE2;
-    TileSmem<R> S = carve<R>(smem_raw, ne, nc, noe, maxE, maxE2);
-    S.idc = t.invdc + eoff;
-    S.dvc = t.divc + (size_t)coff * maxE;
-    const R *cfc = t.cfc + (size_t)eoff * maxE2;
+    const TileSmem<R> S = carve<R>(smem_raw, ne, nc);
+    const R *cfc = t.cfc + (size_t)eoff * TILE_NE2P;
+    const R *dvc = t.divc + (size_t)coff * TILE_NCEP;
     const R tau = (R)a.tau, g = (R)a.g;
+    const R third = R(1.0 / 3.0), two_thirds = R(2.0 / 3.0);
     unsigned int gen = 0;
 
-    // ---- load the patch
+    // global indices of this thread's owned and halo entries
+    int oe[TILE_OWN], he[TILE_OWN], oc[TILE_OWN], hc[TILE_OWN];
+#pragma unroll
+    for (int k = 0; k < TILE_OWN; k++) {
+        const int lo = tid + k * nt, lh = noe + tid + k * nt;
+        const int co = tid + k * nt, ch = noc + tid + k * nt;
+        oe[k] = lo < noe ? t.edge_gid[eoff + lo] : -1;
+        he[k] = lh < ne ? t.edge_gid[eoff + lh] : -1;
+        oc[k] = co < noc ? t.cell_gid[coff + co] : -1;
+        hc[k] = ch < nc ? t.cell_gid[coff + ch] : -1;
+    }
+
+    // ---- load the patch (the extra slot ne / nc is the zero-valued dummy)
     for (int l = tid; l <= ne; l += nt) {
+        R u = R(0), G = R(0), d = R(0);
+        unsigned int cc = (unsigned int)(nc * sizeof(R)) | ((unsigned int)(nc * sizeof(R)) << 16);
         if (l < ne) {
             const int gid = t.edge_gid[eoff + l];
-            S.u0[l] = a.ub_start[gid];
-            S.G[l] = a.G[gid];
-            S.c12[l] = t.c12[eoff + l];
-            S.n2[l] = t.n2[eoff + l];
-        } else {
-            S.u0[l] = R(0); S.G[l] = R(0);
-            S.c12[l] = nc | (nc << 16);
-            S.n2[l] = 0;
+            u = a.ub_start[gid];
+            G = a.G[gid];
+            d = t.invdc[eoff + l];
+            cc = (unsigned int)t.c12[eoff + l];
         }
+        S.u0[l] = u; S.G[l] = G; S.idc[l] = d; S.c12[l] = cc;
         S.ua[l] = R(0); S.uh[l] = R(0); S.fl[l] = R(0);
     }
-    for (int l = tid; l < noe; l += nt) { S.Fz[l] = 0.0; S.Fs[l] = R(0); }
-    for (int x = tid; x < maxE2 * ne; x += nt) {
-        const int j = x / ne, l = x - j * ne;
-        S.eoe[j * (ne + 1) + l] = t.eoe[(size_t)eoff * maxE2 + x];
+    {
+        // rows are TILE_NE2P * 2 = 24 bytes: copy in 8-byte words (every row and the
+        // patch base edge_off * 24 bytes are 8-byte aligned)
+        const uint2 *src = (const uint2 *)(t.eoe + (size_t)eoff * TILE_NE2P);
+        uint2 *dst = (uint2 *)S.eoe;
+        const int n8 = ne * (TILE_NE2P * 2 / 8);
+        for (int x = tid; x < n8; x += nt) dst[x] = src[x];
+        if (tid < TILE_NE2P) S.eoe[(size_t)ne * TILE_NE2P + tid] = (unsigned short)(ne * sizeof(R));
     }
     for (int l = tid; l <= nc; l += nt) {
-        if (l < nc) {
-            S.z0[l] = (R)a.z_start[t.cell_gid[coff + l]];
-            S.nce[l] = t.nce[coff + l];
-        } else {
-            S.z0[l] = R(0);
-            S.nce[l] = 0;
-        }
+        const R z = (l < nc) ? (R)a.z_start[t.cell_gid[coff + l]] : R(0);
+        S.z0[l] = z; S.za[l] = z; S.zh[l] = z;
         S.H[l] = t.H[coff + p + l];
-        S.za[l] = S.z0[l]; S.zh[l] = S.z0[l];
     }
-    for (int x = tid; x < maxE * nc; x += nt) {
-        const int j = x / nc, l = x - j * nc;
-        S.ce[j * (nc + 1) + l] = t.ce[(size_t)coff * maxE + x];
+    {
+        const uint4 *src = (const uint4 *)(t.ce + (size_t)coff * TILE_NCEP);
+        uint4 *dst = (uint4 *)S.ce;
+        for (int x = tid; x < nc; x += nt) dst[x] = src[x];
     }
+    R Fs[TILE_OWN];
+    double Fz[TILE_OWN];
+#pragma unroll
+    for (int k = 0; k < TILE_OWN; k++) { Fs[k] = R(0); Fz[k] = 0.0; }
     __syncthreads();
 
     const R wAB = (ORDER == 2) ? R(0.5) : R(1.0 / 6.0);
@@ -377,73 +419,110 @@ __global__ void __launch_bounds__(TILE_THREADS, 1) k_btr_tiled(DTiles<R> t, BtrA
     int buf = 0;
     for (int j = 0; j < a.M; j++) {
         // ---- stage a: (ua, za) = FE(u0, z0)
-        for (int l = tid; l < ne; l += nt) {
+#pragma unroll
+        for (int k = 0; k < TILE_OWN; k++) {
+            const int l = tid + k * nt;
+            if (l < noe) {
+                R f;
+                S.ua[l] = tile_fe_edge<R>(S, cfc, l, S.u0, S.z0, tau, g, f);
+                S.fl[l] = f;
+                Fs[k] = wAB * f;
+            }
+        }
+        for (int l = noe + tid; l < ne; l += nt) {
             R f;
-            S.ua[l] = tile_fe_edge<R, NE2>(S, cfc, l, ne, S.u0, S.z0, tau, g, f);
+            S.ua[l] = tile_fe_edge<R>(S, cfc, l, S.u0, S.z0, tau, g, f);
             S.fl[l] = f;
-            if (l < noe) S.Fs[l] = wAB * f;
         }
         __syncthreads();
-        for (int l = tid; l < nc; l += nt) S.za[l] = tile_fe_cell<R>(S, l, nc, S.z0, tau);
+        for (int l = tid; l < nc; l += nt) S.za[l] = tile_fe_cell<R>(S, dvc, l, S.z0, tau);
         __syncthreads();
         // ---- stage b: FE(ua, za), first convex combination
-        for (int l = tid; l < ne; l += nt) {
+#pragma unroll
+        for (int k = 0; k < TILE_OWN; k++) {
+            const int l = tid + k * nt;
+            if (l < noe) {
+                R f;
+                const R ub = tile_fe_edge<R>(S, cfc, l, S.ua, S.za, tau, g, f);
+                S.fl[l] = f;
+                Fs[k] += wAB * f;
+                if (ORDER == 2) S.u0[l] = R(0.5) * (S.u0[l] + ub);
+                else S.uh[l] = R(0.75) * S.u0[l] + R(0.25) * ub;
+            }
+        }
+        for (int l = noe + tid; l < ne; l += nt) {
             R f;
-            const R ub = tile_fe_edge<R, NE2>(S, cfc, l, ne, S.ua, S.za, tau, g, f);
+            const R ub = tile_fe_edge<R>(S, cfc, l, S.ua, S.za, tau, g, f);
             S.fl[l] = f;
-            if (l < noe) S.Fs[l] += wAB * f;
             if (ORDER == 2) S.u0[l] = R(0.5) * (S.u0[l] + ub);
             else S.uh[l] = R(0.75) * S.u0[l] + R(0.25) * ub;
         }
         __syncthreads();
         for (int l = tid; l < nc; l += nt) {
-            const R zb = tile_fe_cell<R>(S, l, nc, S.za, tau);
+            const R zb = tile_fe_cell<R>(S, dvc, l, S.za, tau);
             if (ORDER == 2) S.z0[l] = R(0.5) * (S.z0[l] + zb);
             else S.zh[l] = R(0.75) * S.z0[l] + R(0.25) * zb;
         }
         __syncthreads();
         if (ORDER == 3) {
             // ---- stage c: FE(uh, zh), second convex combination
-            for (int l = tid; l < ne; l += nt) {
+#pragma unroll
+            for (int k = 0; k < TILE_OWN; k++) {
+                const int l = tid + k * nt;
+                if (l < noe) {
+                    R f;
+                    const R uc = tile_fe_edge<R>(S, cfc, l, S.uh, S.zh, tau, g, f);
+                    S.fl[l] = f;
+                    Fs[k] += wC * f;
+                    S.u0[l] = third * S.u0[l] + two_thirds * uc;
+                }
+            }
+            for (int l = noe + tid; l < ne; l += nt) {
                 R f;
-                const R uc = tile_fe_edge<R, NE2>(S, cfc, l, ne, S.uh, S.zh, tau, g, f);
+                const R uc = tile_fe_edge<R>(S, cfc, l, S.uh, S.zh, tau, g, f);
                 S.fl[l] = f;
-                if (l < noe) S.Fs[l] += wC * f;
-                S.u0[l] = S.u0[l] / R(3) + R(2) * uc / R(3);
+                S.u0[l] = third * S.u0[l] + two_thirds * uc;
             }
             __syncthreads();
             for (int l = tid; l < nc; l += nt) {
-                const R zc = tile_fe_cell<R>(S, l, nc, S.zh, tau);
-                S.z0[l] = S.z0[l] / R(3) + R(2) * zc / R(3);
+                const R zc = tile_fe_cell<R>(S, dvc, l, S.zh, tau);
+                S.z0[l] = third * S.z0[l] + two_thirds * zc;
             }
             __syncthreads();
         }
-        for (int l = tid; l < noe; l += nt) S.Fz[l] += invM * (double)S.Fs[l];
+#pragma unroll
+        for (int k = 0; k < TILE_OWN; k++) Fz[k] += invM * (double)Fs[k];
         if (j + 1 == a.M) break;
         // ---- exchange the owned values, refresh the halo
         R *xu = t.xu[buf], *xz = t.xz[buf];
-        for (int l = tid; l < noe; l += nt) xu[t.edge_gid[eoff + l]] = S.u0[l];
-        for (int l = tid; l < noc; l += nt) xz[t.cell_gid[coff + l]] = S.z0[l];
+#pragma unroll
+        for (int k = 0; k < TILE_OWN; k++) {
+            if (oe[k] >= 0) xu[oe[k]] = S.u0[tid + k * nt];
+            if (oc[k] >= 0) xz[oc[k]] = S.z0[tid + k * nt];
+        }
         if (!grid_barrier(bar, gen, gridDim.x)) return;
-        for (int l = noe + tid; l < ne; l += nt) S.u0[l] = __ldcg(xu + t.edge_gid[eoff + l]);
-        for (int l = noc + tid; l < nc; l += nt) S.z0[l] = __ldcg(xz + t.cell_gid[coff + l]);
+#pragma unroll
+        for (int k = 0; k < TILE_OWN; k++) {
+            if (he[k] >= 0) S.u0[noe + tid + k * nt] = __ldcg(xu + he[k]);
+            if (hc[k] >= 0) S.z0[noc + tid + k * nt] = __ldcg(xz + hc[k]);
+        }
         buf ^= 1;
         __syncthreads();
     }
     // ---- outputs for the owned edges and cells
-    for (int l = tid; l < noe; l += nt) {
-        const int gid = t.edge_gid[eoff + l];
-        a.Fz[gid] = S.Fz[l];
-        a.ub_out[gid] = a.X ? (R)(a.alpha * (double)a.X[gid] + a.beta * (double)S.u0[l])
-                            : S.u0[l];
+#pragma unroll
+    for (int k = 0; k < TILE_OWN; k++) {
+        if (oe[k] >= 0) {
+            const R u0 = S.u0[tid + k * nt];
+            a.Fz[oe[k]] = Fz[k];
+            a.ub_out[oe[k]] = a.X ? (R)(a.alpha * (double)a.X[oe[k]] + a.beta * (double)u0) : u0;
+        }
+        if (a.z_out && oc[k] >= 0) a.z_out[oc[k]] = (double)S.z0[tid + k * nt];
     }
-    if (a.z_out)
-        for (int l = tid; l < noc; l += nt) a.z_out[t.cell_gid[coff + l]] = (double)S.z0[l];
 }
 
 template <class R> const void *btr_tiled_kernel_ptr(int order) {
-    return order == 2 ? (const void *)k_btr_tiled<R, 2, BTR_NE2>
-                      : (const void *)k_btr_tiled<R, 3, BTR_NE2>;
+    return order == 2 ? (const void *)k_btr_tiled<R, 2> : (const void *)k_btr_tiled<R, 3>;
 }
 
 template <class R>

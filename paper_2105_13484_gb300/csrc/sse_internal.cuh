@@ -114,18 +114,16 @@ int btr_max_items_per_thread();
 // Device copy of the tiled sub-cycle plan (see tiles.h): per-patch arrays
 // flattened with the offsets cell_off / edge_off.
 template <class R> struct DTiles {
-    int P, maxE, maxE2, nthreads, fs_per_thread;
+    int P, nthreads;
     const int *cell_off, *edge_off;  // [P + 1]
     const int *n_own_c, *n_own_e;    // [P]
     const int *cell_gid, *edge_gid;  // local -> global
-    const int *c12;                  // [sum ne] packed local c1 | c2 << 16
-    const short *n2;                 // [sum ne]
-    const short *eoe;                // patch p at edge_off[p] * maxE2: [maxE2][ne_p]
-    const R *cfc;                    // same layout as eoe
+    const int *c12;                  // [sum ne] byte offsets of local (c1, c2): c1 | c2 << 16
+    const unsigned short *eoe;       // [sum ne][TILE_NE2P] byte offsets of local edgesOnEdge
+    const R *cfc;                    // [sum ne][TILE_NE2P] Coriolis coefficients (0 on padding)
     const R *invdc;                  // [sum ne]
-    const short *nce;                // [sum nc]
-    const short *ce;                 // patch p at cell_off[p] * maxE: [maxE][nc_p]
-    const R *divc;                   // same layout as ce
+    const unsigned short *ce;        // [sum nc][TILE_NCEP] byte offsets of local edgesOnCell
+    const R *divc;                   // [sum nc][TILE_NCEP] divergence coefficients
     const R *H;                      // patch p at cell_off[p] + p: [nc_p + 1]
     R *xu[2];                        // [Ep] exchange of owned ubar, double-buffered
     R *xz[2];                        // [Cp] exchange of owned zeta

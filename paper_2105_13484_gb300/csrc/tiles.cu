@@ -151,7 +151,7 @@ bool build_tile_plan(const HostMesh &hm, int P, int K, TilePlan &plan) {
         tp.edge_gid = Ed;
         tp.c12.resize(ne);
         tp.n2.resize(ne);
-        tp.eoe.assign((size_t)hm.maxE2 * ne, (int16_t)dummyE);
+        tp.eoe.assign((size_t)hm.maxE2 * ne, (int16_t)dummyE);   // [ne][maxE2]
         tp.cfc.assign((size_t)hm.maxE2 * ne, 0.0);
         tp.invdc.resize(ne);
         for (int k = 0; k < ne; k++) {
@@ -163,12 +163,12 @@ bool build_tile_plan(const HostMesh &hm, int P, int K, TilePlan &plan) {
             tp.invdc[k] = hm.invdc[e];
             for (int j = 0; j < hm.neoe[e]; j++) {
                 const int ep = hm.eoe[(size_t)e * hm.maxE2 + j];
-                tp.eoe[(size_t)j * ne + k] = (int16_t)(le[ep] >= 0 ? le[ep] : dummyE);
-                tp.cfc[(size_t)j * ne + k] = le[ep] >= 0 ? hm.cfc[(size_t)e * hm.maxE2 + j] : 0.0;
+                tp.eoe[(size_t)k * hm.maxE2 + j] = (int16_t)(le[ep] >= 0 ? le[ep] : dummyE);
+                tp.cfc[(size_t)k * hm.maxE2 + j] = le[ep] >= 0 ? hm.cfc[(size_t)e * hm.maxE2 + j] : 0.0;
             }
         }
         tp.nce.resize(nc);
-        tp.ce.assign((size_t)hm.maxE * nc, (int16_t)dummyE);
+        tp.ce.assign((size_t)hm.maxE * nc, (int16_t)dummyE);      // [nc][maxE]
         tp.divc.assign((size_t)hm.maxE * nc, 0.0);
         tp.H.resize(nc + 1);
         for (int k = 0; k < nc; k++) {
@@ -177,8 +177,8 @@ bool build_tile_plan(const HostMesh &hm, int P, int K, TilePlan &plan) {
             tp.nce[k] = (int16_t)hm.neoc[c];
             for (int j = 0; j < hm.neoc[c]; j++) {
                 const int e = hm.eoc[(size_t)c * hm.maxE + j];
-                tp.ce[(size_t)j * nc + k] = (int16_t)le[e];
-                tp.divc[(size_t)j * nc + k] = hm.divc[(size_t)c * hm.maxE + j];
+                tp.ce[(size_t)k * hm.maxE + j] = (int16_t)le[e];
+                tp.divc[(size_t)k * hm.maxE + j] = hm.divc[(size_t)c * hm.maxE + j];
             }
         }
         tp.H[nc] = 1.0;  // dummy cell: finite depth
@@ -192,19 +192,20 @@ bool build_tile_plan(const HostMesh &hm, int P, int K, TilePlan &plan) {
 }
 
 size_t tile_smem_bytes(const TilePlan &plan, int maxE, int maxE2, size_t sR) {
+    (void)maxE;
+    (void)maxE2;
     size_t best = 0;
     for (const TilePatch &t : plan.patches) {
         const size_t ne = t.ne + 1, nc = t.nc + 1;
         size_t b = 0;
-        b += sR * (4 * ne);            // u0, ua, uh, flux
-        b += sR * (3 * nc);            // z0, za, zh
-        b += sR * (ne + nc);           // G, H
-        b += (8 + sR) * (size_t)t.n_own_e;  // F^zeta accumulators (FP64) and sub-step partials
-        b += 4 * ne;                   // packed local (c1, c2)
-        b += 2 * ne + 2 * nc;          // counts
-        b += 2 * (size_t)maxE2 * ne;   // local edgesOnEdge
-        b += 2 * (size_t)maxE * nc;    // local edgesOnCell
-        b += 64 * 8;                   // alignment slack
+        b += sR * (4 * ne);                 // u0, ua, uh, flux
+        b += sR * ne;                       // 1/d_e
+        b += sR * (3 * nc);                 // z0, za, zh
+        b += sR * (ne + nc);                // G, H
+        b += 4 * ne;                        // packed local byte offsets of (c1, c2)
+        b += 2 * TILE_NE2P * ne;            // edgesOnEdge byte offsets, padded
+        b += 2 * TILE_NCEP * nc;            // edgesOnCell byte offsets, padded
+        b += 64 * 16;                       // alignment slack
         best = std::max(best, b);
     }
     return best;

@@ -7,6 +7,10 @@
 
 namespace sse {
 
+// padded per-entry strides of the tiled sub-cycle's local connectivity
+constexpr int TILE_NE2P = 12;  // edgesOnEdge per edge (<= 10 used)
+constexpr int TILE_NCEP = 8;   // edgesOnCell per cell (<= 8 used)
+
 // host copy of the connectivity and coefficients the plan needs
 struct HostMesh {
     int C = 0, E = 0, maxE = 0, maxE2 = 0;
@@ -24,12 +28,12 @@ struct TilePatch {
     std::vector<int> cell_gid, edge_gid;   // local -> global (owned first)
     std::vector<int32_t> c12;              // [ne] local c1 | c2 << 16
     std::vector<int16_t> n2;               // [ne]
-    std::vector<int16_t> eoe;              // [maxE2][ne] local (dummy = ne)
-    std::vector<double> cfc;               // [maxE2][ne]
+    std::vector<int16_t> eoe;              // [ne][maxE2] local (dummy = ne)
+    std::vector<double> cfc;               // [ne][maxE2]
     std::vector<double> invdc;             // [ne]
     std::vector<int16_t> nce;              // [nc]
-    std::vector<int16_t> ce;               // [maxE][nc] local edges (dummy = ne)
-    std::vector<double> divc;              // [maxE][nc]
+    std::vector<int16_t> ce;               // [nc][maxE] local edges (dummy = ne)
+    std::vector<double> divc;              // [nc][maxE]
     std::vector<double> H;                 // [nc + 1]
 };
 
