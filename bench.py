@@ -57,8 +57,13 @@ def kernel_bytes(cls, C, E, V, L, nT, sR, stage_has_old=True, mixed=False):
     if cls == "transport":
         return 8 * CL + 2 * EL * sR + 2 * E * sR + 3 * 8 * E + EL * sR
     if cls == "thickness":
-        return (EL * sR + 8 * CL + nT * CL * sR + 8 * CL + nT * CL * sR +
-                8 * CL + (4 * CL if mixed else 0) + nT * CL * sR + 8 * C)
+        # flux, column flux, h_s (+ its FP32 copy), tracers; h^n, its copy and
+        # tracers^n only in stages that combine with the old level; writes h
+        # (+ copy), tracers, zeta
+        h_words = 8 * CL + (sR * CL if mixed else 0)
+        old = (h_words + nT * CL * sR) if stage_has_old else 0
+        return (EL * sR + 8 * E + h_words + nT * CL * sR + old +
+                h_words + nT * CL * sR + 8 * C)
     if cls == "combine":
         return 4 * E * sR
     return 0
@@ -76,6 +81,49 @@ def step_bytes_per_cell_layer(mixed: bool, nT: int = 1) -> float:
     h_words = 3 + 2 + 3 + 3
     total_words = (7 + nT) + 2 * (10 + nT) + (5 + 2 * nT) + 2 * (6 + 3 * nT)
     return 8.0 * h_words + 4.0 * (total_words - h_words)
+
+
+# ncu summaries under profiles/ per kernel class (mixed form, this workload);
+# each records DRAM traffic per launch and the hashes of the sources it was
+# captured from, so a figure taken from an older kernel is not reported
+PROFILE_OF = {"btr": "btr_tiled_channel_1km.md", "bcl_edge": "bcl_edge_channel_1km.md",
+              "thickness": "thickness_channel_1km.md"}
+KERNEL_SOURCES = ("paper_2105_13484_gb300/csrc/btr_kernel.cu",
+                  "paper_2105_13484_gb300/csrc/stage_kernels.cu",
+                  "paper_2105_13484_gb300/csrc/sse_internal.cuh")
+
+
+def source_hashes():
+    import hashlib
+    out = {}
+    for rel in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, rel), "rb") as f:
+            out[os.path.basename(rel)] = hashlib.sha256(f.read()).hexdigest()[:16]
+    return out
+
+
+def ncu_traffic(cls, mixed):
+    """DRAM bytes per launch from the committed ncu capture of `cls`, or
+    (None, reason) when there is none or the kernel sources have changed."""
+    name = PROFILE_OF.get(cls)
+    if not mixed or name is None:
+        return None, "no ncu capture of this kernel/form"
+    path = os.path.join(ROOT, "profiles", name)
+    if not os.path.exists(path):
+        return None, "no ncu capture of this kernel/form"
+    traffic, hashes = None, {}
+    with open(path) as f:
+        for line in f:
+            if line.startswith("| DRAM bytes read + written"):
+                traffic = float(line.split("|")[2].split()[0]) * 1e6
+            if line.startswith("- source sha256 "):
+                k, v = line[len("- source sha256 "):].strip().split(": ")
+                hashes[k] = v
+    if traffic is None or not hashes:
+        return None, "capture summary incomplete"
+    if hashes != source_hashes():
+        return None, "kernel sources changed since the ncu capture"
+    return traffic, f"profiles/{name}"
 
 
 def measured_peaks():
@@ -139,6 +187,20 @@ class ClockSampler:
         busy = [s for s in sm if s > 0.5 * max(sm)] or sm
         return {"sm_mhz": float(np.median(busy)), "sm_max_mhz": float(max(smax)),
                 "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def max_over_ranks(torch, dist, value, device):
+    """Max of a per-rank float over all ranks (identity without a process group)."""
+    if dist is None or not dist.is_initialized():
+        return float(value)
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_throughput(units_per_rank, world, max_ms):
+    """Whole-job throughput of `world` independent replicas timed together."""
+    return world * units_per_rank / (max_ms / 1e3)
 
 
 def build_workload(seed=0, scale=None):
@@ -289,28 +351,29 @@ def run_ours(args):
         dist.barrier()
     torch.cuda.synchronize()
     sampler = ClockSampler(local)
-    for prec in ("mixed", "fp64"):
+    todo = ("mixed", "fp64") if args.forms == "both" else (args.forms,)
+    if args.precision not in todo:
+        todo = todo + (args.precision,)
+    for prec in todo:
         forms[prec] = measure_form(torch, binding, dm, m, L, p, state0, run, prec, args.steps,
                                    args.warmup, stream, flush,
                                    sampler if prec == args.precision else None)
     head = forms[args.precision]
     units = m.nCells * L * args.steps
-    t_max = head["device_ms"]
-    if dist:
-        t = torch.tensor([t_max], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_max = float(t.item())
-    value = world * units / (t_max / 1e3)
+    t_max = max_over_ranks(torch, dist, head["device_ms"], "cuda")
+    value = replica_throughput(units, world, t_max)
 
     # error of the mixed form against the FP64 form at the horizon (per field)
-    fu, fh, ft = forms["fp64"]["final"]
-    mu, mh, mt = forms["mixed"]["final"]
+    mixed_err = None
+    if "fp64" in forms and "mixed" in forms:
+        fu, fh, ft = forms["fp64"]["final"]
+        mu, mh, mt = forms["mixed"]["final"]
 
-    def rel(a, b):
-        return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
-    mixed_err = {"u": rel(mu, fu), "h": rel(mh, fh), "zeta": rel(mh.sum(1) - m.bottomDepth,
-                                                                 fh.sum(1) - m.bottomDepth),
-                 "T": rel(mt, ft)}
+        def rel(a, b):
+            return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+        mixed_err = {"u": rel(mu, fu), "h": rel(mh, fh),
+                     "zeta": rel(mh.sum(1) - m.bottomDepth, fh.sum(1) - m.bottomDepth),
+                     "T": rel(mt, ft)}
 
     # roofline of the dominant kernel class (by summed device time)
     peaks, peak_kind = measured_peaks()
@@ -321,15 +384,18 @@ def run_ours(args):
     nlaunch = prof[dom][1]
     per_launch_ms = prof[dom][0] / max(nlaunch, 1)
     nT = int(p.get("nTracers", 1))
-    if dom == "bcl_edge":
-        # 1 of 3 launches per step has no utilde^n input
+    if dom in ("bcl_edge", "thickness"):
+        # the first stage of a step has no old-level input (utilde^n, h^n)
         b = (kernel_bytes(dom, m.nCells, m.nEdges, m.nVertices, L, nT, sR, False, mixed) +
-             2 * kernel_bytes(dom, m.nCells, m.nEdges, m.nVertices, L, nT, sR, True, mixed)) / 3
+             (order - 1) * kernel_bytes(dom, m.nCells, m.nEdges, m.nVertices, L, nT, sR, True,
+                                        mixed)) / order
     else:
         b = kernel_bytes(dom, m.nCells, m.nEdges, m.nVertices, L, nT, sR, True, mixed)
     achieved = b / (per_launch_ms / 1e3) / 1e9
+    traffic, traffic_src = ncu_traffic(dom, mixed)
     roof = {"kernel": dom, "bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"],
-            "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"], "traffic": None,
+            "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"], "traffic": traffic,
+            "traffic_source": traffic_src,
             "peak_source": f"{peak_kind} hbm_gbs (copy)", "bytes_per_launch": b,
             "ms_per_launch": per_launch_ms}
     step_b = step_bytes_per_cell_layer(mixed, nT) * m.nCells * L
@@ -339,10 +405,15 @@ def run_ours(args):
     kernels = {k: {"ms_per_step": v[0] / args.steps, "share": v[0] / max(head["device_ms"], 1e-9),
                    "launches_per_step": v[1] / args.steps} for k, v in prof.items()}
 
-    e2e_steps = min(args.steps, 20)
-    e2e_ms, nbytes = measure_e2e(torch, binding, dm, p, state0, run, args.precision, e2e_steps,
-                                 stream)
-    e2e_val = world * m.nCells * L * e2e_steps / (e2e_ms / 1e3)
+    e2e = None
+    if not args.no_e2e:
+        e2e_steps = min(args.steps, 20)
+        e2e_ms, nbytes = measure_e2e(torch, binding, dm, p, state0, run, args.precision,
+                                     e2e_steps, stream)
+        e2e_val = replica_throughput(m.nCells * L * e2e_steps, world,
+                                     max_over_ranks(torch, dist, e2e_ms, "cuda"))
+        e2e = {"value": e2e_val, "unit": METRIC, "h2d_bytes_per_step": nbytes,
+               "d2h_bytes_per_step": nbytes}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
@@ -366,8 +437,7 @@ def run_ours(args):
                       "volume_rel_change": abs(v["diag"]["volume"] - vol0) / vol0}
                   for k, v in forms.items()},
         "mixed_vs_fp64_rel_l2": mixed_err,
-        "e2e": {"value": e2e_val, "unit": METRIC, "h2d_bytes_per_step": nbytes,
-                "d2h_bytes_per_step": nbytes},
+        "e2e": e2e,
         "gpu_launches": head["kernels_per_step"] * args.steps,
         "clocks": head["clocks"],
         "cpu_baseline": cpu,
@@ -389,6 +459,9 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
+    ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end leg")
+    ap.add_argument("--forms", default="both", choices=["both", "mixed", "fp64"],
+                    help="precision forms to measure (the headline form is always measured)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -223,6 +223,7 @@ extern "C" int sse_mesh_create(const sse_mesh_desc *d, sse_mesh **out) {
     dm.neoc = A.upload(neoc); dm.eoc = A.upload(eoc); dm.ooc = A.upload(ooc);
     dm.neoe = A.upload(neoe); dm.eoe = A.upload(eoe); dm.eov = A.upload(eov);
     dm.cov = A.upload(cov); dm.H = A.upload(H); dm.sfrac = A.upload(sfrac);
+    dm.sfrac_f = A.upload(tof(sfrac));
     dm.divc_d = A.upload(divc); dm.area = A.upload(area); dm.ld2 = A.upload(ld2);
     dm.d.divc = dm.divc_d; dm.d.kec = A.upload(kec); dm.d.wl = A.upload(wl);
     dm.d.cfc = A.upload(cfc); dm.d.curlc = A.upload(curlc); dm.d.kw = A.upload(kw);
@@ -337,7 +338,8 @@ struct Engine : EngineBase {
     unsigned int *barwords;
     int *barerr;
     double *stage;   // staging for host transfers
-    double *wind;
+    double *wind, *wind_d;
+    float *wind_f;
     double *dpart, *dout;
     int dparts = 0;
     int btr_blocks = 1;
@@ -465,7 +467,9 @@ struct Engine : EngineBase {
         p.kappa_h = prm->kappa_h; p.kappa_v = prm->kappa_v; p.c_drag = prm->c_drag;
         p.alpha = prm->eos_alpha; p.beta = prm->eos_beta; p.T_ref = prm->eos_T_ref;
         p.S_ref = prm->eos_S_ref; p.zcoef = prm->g * (1.0 - prm->eos_rho_ref / prm->rho0);
-        p.nT = prm->nTracers; p.recon = prm->recon; p.wind = nullptr;
+        p.nT = prm->nTracers; p.recon = prm->recon; p.wind = nullptr; p.wind_f = nullptr;
+        fill_phys(p.pd);
+        fill_phys(p.pf);
         const size_t EL = (size_t)m.L * m.Ep, CL = (size_t)m.L * m.Cp, VL = (size_t)m.L * m.Vp;
         const int nT = p.nT;
         ubar_n = A.alloc<R>(m.Ep); ut_n = A.alloc<R>(EL);
@@ -498,6 +502,8 @@ struct Engine : EngineBase {
         barerr = A.alloc<int>(1);
         stage = A.alloc<double>((size_t)std::max(m.Ep, m.Cp) * m.L);
         wind = A.alloc<double>(m.Ep);
+        wind_d = A.alloc<double>(m.Ep);
+        wind_f = A.alloc<float>(m.Ep);
         dparts = 256;
         dpart = A.alloc<double>((size_t)dparts * 9);
         dout = A.alloc<double>(9);
@@ -524,6 +530,13 @@ struct Engine : EngineBase {
     }
 
     Barrier bar() const { return Barrier{barwords, barwords + 1, barerr}; }
+
+    template <class T> void fill_phys(PhysR<T> &q) const {
+        q.g = (T)p.g; q.inv_rho0 = (T)(1.0 / p.rho0); q.nu_h = (T)p.nu_h; q.nu_v = (T)p.nu_v;
+        q.kappa_h = (T)p.kappa_h; q.kappa_v = (T)p.kappa_v; q.c_drag = (T)p.c_drag;
+        q.alpha = (T)p.alpha; q.beta = (T)p.beta; q.T_ref = (T)p.T_ref; q.S_ref = (T)p.S_ref;
+        q.zcoef = (T)p.zcoef;
+    }
 
     int check_launch() {
         cudaError_t e = cudaGetLastError();
@@ -565,7 +578,9 @@ struct Engine : EngineBase {
         }
         case SSE_FIELD_WIND:
             CK(cudaMemcpyAsync(wind, host, sizeof(double) * m.E, cudaMemcpyHostToDevice, s));
-            p.wind = wind;
+            launch_scale(wind, 1.0 / p.rho0, wind_d, wind_f, m.E, s);
+            p.wind = wind_d;
+            p.wind_f = wind_f;
             break;
         default:
             return SSE_ERR_INVALID_ARG;
@@ -691,7 +706,8 @@ struct Engine : EngineBase {
     void thickness(const double *h_s, const R *hR_s, const R *tr_s, double a, double b, double dt,
                    double *h_out, R *hR_out, R *tr_out, double *zeta_out) {
         ThickArgs<R> t{};
-        t.flux = flux; t.Fcol = Fcol; t.h_s = h_s; t.hR_s = hR_s; t.tr_s = tr_s; t.h_n = h_n; t.tr_n = tr_n;
+        t.flux = flux; t.Fcol = Fcol; t.h_s = h_s; t.hR_s = hR_s; t.tr_s = tr_s; t.h_n = h_n;
+        t.hR_n = hR_n; t.tr_n = tr_n;
         t.a = a; t.b = b; t.dt = dt; t.h_out = h_out; t.hR_out = mixed ? hR_out : nullptr;
         t.tr_out = tr_out; t.zeta_out = zeta_out;
         pbeg(SSE_K_THICKNESS);

@@ -41,6 +41,7 @@ struct DMesh {
     const int *cov;     // [3][Vp] (land -> 0, with zero weight)
     const double *H;    // [Cp] resting depth
     const double *sfrac;  // [L] z-star fractions
+    const float *sfrac_f; // [L] the same in FP32
     const double *divc_d; // [maxE][Cp] divergence coefficients in FP64
     const double *area;   // [Cp]
     const double *ld2;    // [Ep] l_e d_e / 2 (energy weight)
@@ -52,13 +53,30 @@ template <class R> __host__ __device__ inline const Coef<R> &coef(const DMesh &m
 template <> __host__ __device__ inline const Coef<double> &coef<double>(const DMesh &m) { return m.d; }
 template <> __host__ __device__ inline const Coef<float> &coef<float>(const DMesh &m) { return m.f; }
 
+// physical constants in one precision (converted once on the host)
+template <class R> struct PhysR {
+    R g, inv_rho0, nu_h, nu_v, kappa_h, kappa_v, c_drag;
+    R alpha, beta, T_ref, S_ref;  // rho' = rho - rho_ref = -alpha (T - T_ref) + beta (S - S_ref)
+    R zcoef;                      // g (1 - rho_ref / rho0)
+};
+
 struct DParams {
     double g, rho0, nu_h, nu_v, kappa_h, kappa_v, c_drag;
-    double alpha, beta, T_ref, S_ref;  // rho' = rho - rho_ref
+    double alpha, beta, T_ref, S_ref;
     double zcoef;                      // g (1 - rho_ref / rho0)
     int nT, recon;
-    const double *wind;  // [Ep] or nullptr
+    const double *wind;                // [Ep] wind stress / rho0, or nullptr
+    const float *wind_f;               // the same in FP32
+    PhysR<double> pd;
+    PhysR<float> pf;
 };
+
+template <class R> __host__ __device__ inline const PhysR<R> &phys(const DParams &p);
+template <> __host__ __device__ inline const PhysR<double> &phys<double>(const DParams &p) { return p.pd; }
+template <> __host__ __device__ inline const PhysR<float> &phys<float>(const DParams &p) { return p.pf; }
+template <class R> __device__ inline const R *wind_over_rho0(const DParams &p);
+template <> __device__ inline const double *wind_over_rho0<double>(const DParams &p) { return p.wind; }
+template <> __device__ inline const float *wind_over_rho0<float>(const DParams &p) { return p.wind_f; }
 
 // Grid barrier words of the persistent sub-cycle kernel.
 struct Barrier {
@@ -157,6 +175,7 @@ template <class R> struct ThickArgs {
     const R *hR_s;            // stage thickness in the tendency precision
     const R *tr_s;            // stage tracers [nT][L][Cp]
     const double *h_n;        // h^n (convex combination)
+    const R *hR_n;            // h^n in the tendency precision
     const R *tr_n;
     double a, b, dt;          // out = a * (h^n) + b * (FE result)
     double *h_out;
@@ -175,6 +194,7 @@ void launch_from_device(const R *src, double *dst, int n, int L, int np, cudaStr
 template <class R>
 void launch_add_bar(const R *ubar, const R *ut, double *dst, int E, int L, int Ep, cudaStream_t s);
 void launch_h_to_float(const double *h, float *hf, int n, cudaStream_t s);
+void launch_scale(const double *src, double scale, double *dst_d, float *dst_f, int n, cudaStream_t s);
 void launch_ssh(const DMesh &m, const double *h, double *zeta, cudaStream_t s);
 
 template <class R>

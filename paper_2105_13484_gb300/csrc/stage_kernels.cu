@@ -21,10 +21,14 @@ namespace sse {
 
 template <class R> __device__ __forceinline__ R ld(const R *p) { return __ldg(p); }
 
+template <class R> __device__ __forceinline__ const R *sfrac_of(const DMesh &m);
+template <> __device__ __forceinline__ const double *sfrac_of<double>(const DMesh &m) { return m.sfrac; }
+template <> __device__ __forceinline__ const float *sfrac_of<float>(const DMesh &m) { return m.sfrac_f; }
+
 // ---------------------------------------------------------------------------
 // cell diagnostics
 // ---------------------------------------------------------------------------
-template <class R>
+template <class R, int NCE>
 __global__ void __launch_bounds__(128) k_cell_diag(DMesh m, DParams p, const R *__restrict__ ubar,
                                                    const R *__restrict__ ut,
                                                    const R *__restrict__ hR,
@@ -34,10 +38,10 @@ __global__ void __launch_bounds__(128) k_cell_diag(DMesh m, DParams p, const R *
     const Coef<R> &c = coef<R>(m);
     const int Cp = m.Cp, Ep = m.Ep, L = m.L;
     const int ne = m.neoc[i];
-    int es[MAXE], os[MAXE];
-    R dcf[MAXE], kcf[MAXE], ub[MAXE];
+    int es[NCE], os[NCE];
+    R dcf[NCE], kcf[NCE], ub[NCE];
 #pragma unroll
-    for (int j = 0; j < MAXE; j++) {
+    for (int j = 0; j < NCE; j++) {
         if (j < ne) {
             es[j] = m.eoc[j * Cp + i];
             os[j] = m.ooc[j * Cp + i];
@@ -48,14 +52,15 @@ __global__ void __launch_bounds__(128) k_cell_diag(DMesh m, DParams p, const R *
             es[j] = 0; os[j] = i; dcf[j] = R(0); kcf[j] = R(0); ub[j] = R(0);
         }
     }
-    const R g = (R)p.g, alpha = (R)p.alpha, beta = (R)p.beta, Tref = (R)p.T_ref,
-            Sref = (R)p.S_ref;
+    const PhysR<R> &q = phys<R>(p);
+    const R g = q.g, alpha = q.alpha, beta = q.beta, Tref = q.T_ref, Sref = q.S_ref;
+    const R *sfr = sfrac_of<R>(m);
     R accp = R(0), divsum = R(0);
     for (int k = 0; k < L; k++) {
         const R hk = ld(hR + k * Cp + i);
         R ke = R(0), dl = R(0), dv = R(0);
 #pragma unroll
-        for (int j = 0; j < MAXE; j++) {
+        for (int j = 0; j < NCE; j++) {
             if (j < ne) {
                 const R uk = ub[j] + ld(ut + k * Ep + es[j]);
                 const R he = R(0.5) * (hk + ld(hR + k * Cp + os[j]));
@@ -84,7 +89,7 @@ __global__ void __launch_bounds__(128) k_cell_diag(DMesh m, DParams p, const R *
         const R hk = ld(hR + x);
         b.zm[x] = -Hi + below + R(0.5) * hk;
         below += hk;
-        const R wk = (k == 0) ? R(0) : wk1 - b.w[x] + (R)m.sfrac[k] * divsum;
+        const R wk = (k == 0) ? R(0) : wk1 - b.w[x] + sfr[k] * divsum;
         b.w[x] = wk;
         wk1 = wk;
     }
@@ -174,7 +179,7 @@ __global__ void __launch_bounds__(128) k_edge_pre(DMesh m, R *__restrict__ ubar,
 // - (grad p' + g rho'_e grad z) / rho0.
 // ---------------------------------------------------------------------------
 template <class R, int NE2>
-__global__ void __launch_bounds__(128) k_bcl_edge(DMesh m, DParams p, const R *__restrict__ ubar,
+__global__ void __launch_bounds__(128, 8) k_bcl_edge(DMesh m, DParams p, const R *__restrict__ ubar,
                                                   const R *__restrict__ ut,
                                                   const R *__restrict__ hR,
                                                   const double *__restrict__ zeta, DiagBufs<R> b,
@@ -202,10 +207,12 @@ __global__ void __launch_bounds__(128) k_bcl_edge(DMesh m, DParams p, const R *_
     }
     const R invdc = c.invdc[e], invdv = c.invdv[e];
     const R ub = ubar[e];
-    const R gzeta = (R)(p.zcoef * (zeta[c2] - zeta[c1])) * invdc;
-    const R g = (R)p.g, inv_rho0 = (R)(1.0 / p.rho0), nu_h = (R)p.nu_h, nu_v = (R)p.nu_v;
-    const R cdrag = (R)p.c_drag;
-    const R wind = p.wind ? (R)(p.wind[e] / p.rho0) : R(0);
+    const PhysR<R> &q = phys<R>(p);
+    const R gzeta = q.zcoef * (R)(zeta[c2] - zeta[c1]) * invdc;
+    const R g = q.g, inv_rho0 = q.inv_rho0, nu_h = q.nu_h, nu_v = q.nu_v;
+    const R cdrag = q.c_drag;
+    const R *wnd = wind_over_rho0<R>(p);
+    const R wind = wnd ? wnd[e] : R(0);
 
     R ut_cur = ut[e];
     R u_cur = ub + ut_cur;
@@ -323,18 +330,18 @@ __global__ void __launch_bounds__(128) k_transport(DMesh m, TransportArgs<R> a) 
 // (FP64, from k_transport); the per-layer flux feeds w and the tracers in the
 // tendency precision.
 // ---------------------------------------------------------------------------
-template <class R>
-__global__ void __launch_bounds__(128) k_thickness(DMesh m, DParams p, ThickArgs<R> a) {
+template <class R, int NCE>
+__global__ void __launch_bounds__(128, 6) k_thickness(DMesh m, DParams p, ThickArgs<R> a) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= m.C) return;
     const Coef<R> &c = coef<R>(m);
     const int Cp = m.Cp, Ep = m.Ep, L = m.L;
     const int ne = m.neoc[i];
-    int es[MAXE], os[MAXE];
-    R dcf[MAXE], idc[MAXE];
+    int es[NCE], os[NCE];
+    R dcf[NCE], idc[NCE];
     double D = 0.0;
 #pragma unroll
-    for (int j = 0; j < MAXE; j++) {
+    for (int j = 0; j < NCE; j++) {
         if (j < ne) {
             es[j] = m.eoc[j * Cp + i];
             os[j] = m.ooc[j * Cp + i];
@@ -346,42 +353,49 @@ __global__ void __launch_bounds__(128) k_thickness(DMesh m, DParams p, ThickArgs
         }
     }
     const R Dr = (R)D;
-    // per-layer flux divergence (tendency precision) and w at interfaces
-    R divF[LMAX];
-    for (int k = 0; k < L; k++) {
-        R sdiv = R(0);
-#pragma unroll
-        for (int j = 0; j < MAXE; j++)
-            if (j < ne) sdiv += dcf[j] * ld(a.flux + k * Ep + es[j]);
-        divF[k] = sdiv;
-    }
-    R w[LMAX + 1];
-    w[L] = R(0);
-    for (int k = L - 1; k >= 1; k--) w[k] = w[k + 1] - divF[k] + (R)m.sfrac[k] * Dr;
-    w[0] = R(0);
+    const double dtD = a.dt * D;
+    const PhysR<R> &q = phys<R>(p);
+    const R *sfr = sfrac_of<R>(m);
+    const R dtR = (R)a.dt, aR = (R)a.a, bR = (R)a.b, kh = q.kappa_h, kv = q.kappa_v;
+    const bool comb = a.a != 0.0;
+    const bool khz = p.kappa_h != 0.0;
+    const int nT = p.nT;
     double hsum = 0.0;
-    const double dt = a.dt;
-    const R dtR = (R)dt, aR = (R)a.a, bR = (R)a.b, kh = (R)p.kappa_h, kv = (R)p.kappa_v;
+    // one pass from the top: w_0 = 0 and w_{k+1} = w_k + div_k - s_k D (the
+    // z-star relation read downward, D = sum_l div_l), so w_k and w_{k+1} are
+    // both at hand when layer k is updated
+    R wk = R(0);
+    R hs_prev = R(0), hs_cur = ld(a.hR_s + i);
     for (int k = 0; k < L; k++) {
         const int x = k * Cp + i;
-        const double h1 = a.h_s[x] - dt * m.sfrac[k] * D;
-        // h_out may alias h_n: read h^n before the store
-        const double hn = (a.a != 0.0) ? a.h_n[x] : 0.0;
-        const double hout = (a.a != 0.0) ? a.a * hn + a.b * h1 : a.b * h1;
-        const R h1r = (R)h1, houtr = (R)hout, hnr = (R)hn;
-        const R hsx = ld(a.hR_s + x);
-        for (int t = 0; t < p.nT; t++) {
+        R divk = R(0);
+#pragma unroll
+        for (int j = 0; j < NCE; j++)
+            if (j < ne) divk += dcf[j] * ld(a.flux + k * Ep + es[j]);
+        const R sk = sfr[k];
+        const R wk1 = (k + 1 < L) ? wk + divk - sk * Dr : R(0);
+        const R hs_next = (k + 1 < L) ? ld(a.hR_s + x + Cp) : R(0);
+        // thickness in FP64 from the column-integrated flux (volume conservation);
+        // h_out may alias h_n, so h^n is read before the store
+        const double h1 = a.h_s[x] - m.sfrac[k] * dtD;
+        const double hn = comb ? a.h_n[x] : 0.0;
+        const double hout = comb ? a.a * hn + a.b * h1 : h1;
+        // the tracer arithmetic uses the tendency precision
+        const R h1r = hs_cur - sk * (dtR * Dr);
+        const R hnr = comb ? ld(a.hR_n + x) : R(0);
+        const R houtr = comb ? aR * hnr + bR * h1r : h1r;
+        for (int t = 0; t < nT; t++) {
             const R *phi = a.tr_s + t * L * Cp;
             const R ph = ld(phi + x);
             R adv = R(0), dif = R(0);
 #pragma unroll
-            for (int j = 0; j < MAXE; j++) {
+            for (int j = 0; j < NCE; j++) {
                 if (j < ne) {
                     const R po = ld(phi + k * Cp + os[j]);
                     adv += dcf[j] * (ld(a.flux + k * Ep + es[j]) * (R(0.5) * (ph + po)));
-                    if (p.kappa_h != 0.0) {
+                    if (khz) {
                         // n_{e,i} grad_e(phi) = (phi_other - phi_i) / d_e for either orientation
-                        const R he = R(0.5) * (hsx + ld(a.hR_s + k * Cp + os[j]));
+                        const R he = R(0.5) * (hs_cur + ld(a.hR_s + k * Cp + os[j]));
                         dif += fabs(dcf[j]) * he * kh * (po - ph) * idc[j];
                     }
                 }
@@ -389,18 +403,18 @@ __global__ void __launch_bounds__(128) k_thickness(DMesh m, DParams p, ThickArgs
             R ftop = R(0), fbot = R(0), dtop = R(0), dbot = R(0);
             if (k >= 1) {
                 const R pu = ld(phi + x - Cp);
-                ftop = R(0.5) * (pu + ph) * w[k];
-                dtop = (pu - ph) / (R(0.5) * (ld(a.hR_s + x - Cp) + hsx));
+                ftop = R(0.5) * (pu + ph) * wk;
+                dtop = (pu - ph) / (R(0.5) * (hs_prev + hs_cur));
             }
             if (k + 1 <= L - 1) {
                 const R pd = ld(phi + x + Cp);
-                fbot = R(0.5) * (ph + pd) * w[k + 1];
-                dbot = (ph - pd) / (R(0.5) * (hsx + ld(a.hR_s + x + Cp)));
+                fbot = R(0.5) * (ph + pd) * wk1;
+                dbot = (ph - pd) / (R(0.5) * (hs_cur + hs_next));
             }
-            const R hphi = hsx * ph + dtR * (-adv - (ftop - fbot) + dif + kv * (dtop - dbot));
+            const R hphi = hs_cur * ph + dtR * (-adv - (ftop - fbot) + dif + kv * (dtop - dbot));
             const R phi1 = hphi / h1r;
             R out;
-            if (a.a != 0.0)
+            if (comb)
                 out = (aR * hnr * a.tr_n[t * L * Cp + x] + bR * h1r * phi1) / houtr;
             else
                 out = phi1;
@@ -409,6 +423,9 @@ __global__ void __launch_bounds__(128) k_thickness(DMesh m, DParams p, ThickArgs
         a.h_out[x] = hout;
         if (a.hR_out) a.hR_out[x] = houtr;
         hsum += hout;
+        wk = wk1;
+        hs_prev = hs_cur;
+        hs_cur = hs_next;
     }
     a.zeta_out[i] = hsum - m.H[i];
 }
@@ -443,6 +460,14 @@ __global__ void k_add_bar(const R *__restrict__ ubar, const R *__restrict__ ut,
 __global__ void k_h_to_float(const double *__restrict__ h, float *__restrict__ hf, int n) {
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t < n) hf[t] = (float)h[t];
+}
+__global__ void k_scale(const double *__restrict__ src, double scale, double *__restrict__ dd,
+                        float *__restrict__ df, int n) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < n) {
+        dd[t] = src[t] * scale;
+        df[t] = (float)dd[t];
+    }
 }
 __global__ void k_ssh(DMesh m, const double *__restrict__ h, double *__restrict__ zeta) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -531,7 +556,10 @@ static inline int nblk(long long n, int t) { return (int)((n + t - 1) / t); }
 template <class R>
 void launch_cell_diag(const DMesh &m, const DParams &p, const R *ubar, const R *ut, const R *hR,
                       const R *tr, const DiagBufs<R> &b, cudaStream_t s) {
-    k_cell_diag<R><<<nblk(m.C, 128), 128, 0, s>>>(m, p, ubar, ut, hR, tr, b);
+    if (m.maxE <= 6)
+        k_cell_diag<R, 6><<<nblk(m.C, 128), 128, 0, s>>>(m, p, ubar, ut, hR, tr, b);
+    else
+        k_cell_diag<R, MAXE><<<nblk(m.C, 128), 128, 0, s>>>(m, p, ubar, ut, hR, tr, b);
 }
 template <class R>
 void launch_vertex(const DMesh &m, const R *ubar, const R *ut, const R *hR, const DiagBufs<R> &b,
@@ -560,7 +588,10 @@ void launch_transport(const DMesh &m, const TransportArgs<R> &a, cudaStream_t s)
 }
 template <class R>
 void launch_thickness(const DMesh &m, const DParams &p, const ThickArgs<R> &a, cudaStream_t s) {
-    k_thickness<R><<<nblk(m.C, 128), 128, 0, s>>>(m, p, a);
+    if (m.maxE <= 6)
+        k_thickness<R, 6><<<nblk(m.C, 128), 128, 0, s>>>(m, p, a);
+    else
+        k_thickness<R, MAXE><<<nblk(m.C, 128), 128, 0, s>>>(m, p, a);
 }
 template <class R>
 void launch_to_device(const double *src, R *dst, int n, int L, int np, cudaStream_t s) {
@@ -576,6 +607,10 @@ void launch_add_bar(const R *ubar, const R *ut, double *dst, int E, int L, int E
 }
 void launch_h_to_float(const double *h, float *hf, int n, cudaStream_t s) {
     k_h_to_float<<<nblk(n, 256), 256, 0, s>>>(h, hf, n);
+}
+void launch_scale(const double *src, double scale, double *dst_d, float *dst_f, int n,
+                  cudaStream_t s) {
+    k_scale<<<nblk(n, 256), 256, 0, s>>>(src, scale, dst_d, dst_f, n);
 }
 void launch_ssh(const DMesh &m, const double *h, double *zeta, cudaStream_t s) {
     k_ssh<<<nblk(m.C, 128), 128, 0, s>>>(m, h, zeta);
