@@ -9,10 +9,14 @@ step: three baroclinic stages, three sub-cycles and three thickness stages.
 
 Metric: cell-layer-steps/s = cells x layers x steps / device time.  The
 headline form is the mixed-precision path; the FP64 path is measured in the
-same run and reported under "forms".  L2 is flushed (a 512 MB write) between
-timed steps and the flush is excluded from the per-step CUDA-event times.
+same run and reported under "forms", with per-step p50/p99 latency.  L2 is
+flushed (a 512 MB write) between timed steps and the flush is excluded from
+the per-step CUDA-event times.  The same run also measures the largest single
+mesh, the level-7 icosahedral sphere with 60 layers (114,689 ocean cells, T
+and S, wind stress; SSPRK3-SE, dt = 600 s, M = 40), mixed form, under "also".
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                    [--workload channel_1km|sphere_l7] [--no-sphere]
 
 Under torchrun with N > 1 every rank runs an independent replica (the method
 has no cross-replica exchange): value = N x per-replica units / max time.
@@ -203,12 +207,12 @@ def replica_throughput(units_per_rank, world, max_ms):
     return world * units_per_rank / (max_ms / 1e3)
 
 
-def build_workload(seed=0, scale=None):
+def build_workload(seed=0, scale=None, name=WORKLOAD):
     from paper_2105_13484_gb300 import inputs
     over = {}
     if scale is not None:
         over = dict(nx=scale[0], ny=scale[1])
-    m, L, p, st, run = inputs.workload(WORKLOAD, seed=seed, perturb=True, **over)
+    m, L, p, st, run = inputs.workload(name, seed=seed, perturb=True, **over)
     return m, L, p, st, run
 
 
@@ -282,9 +286,11 @@ def measure_form(torch, binding, dm, m, L, p, state0, run, precision, steps, war
     clocks = sampler.stop() if sampler else None
     prof = st.profile_read()
     st.profile(False)
-    ms = sum(a.elapsed_time(b) for a, b in ev)
+    per = np.array([a.elapsed_time(b) for a, b in ev])
+    ms = float(per.sum())
     d = st.diagnostics(check=False)
     res = {"device_ms": ms, "ms_per_step": ms / steps, "wall_s": t_wall, "prof": prof,
+           "latency_ms": {"p50": float(np.percentile(per, 50)), "p99": float(np.percentile(per, 99))},
            "clocks": clocks, "diag": d, "kernels_per_step": st.kernels_per_step(order)}
     gu, gh, gt = st.read_state()
     res["final"] = (gu, gh, gt)
@@ -297,32 +303,121 @@ def measure_e2e(torch, binding, dm, p, state0, run, precision, steps, stream):
     (u, h, T), one large step, D2H of (u, h, T)."""
     u, h, tr = state0
     st = binding.State(dm, p, precision, stream=stream.cuda_stream)
-    hu = torch.from_numpy(np.ascontiguousarray(u)).pin_memory()
-    hh = torch.from_numpy(np.ascontiguousarray(h)).pin_memory()
-    ht = torch.from_numpy(np.ascontiguousarray(tr[0])).pin_memory()
-    ou, oh, ot = (torch.empty_like(x).pin_memory() for x in (hu, hh, ht))
+    fields = [("u", u), ("h", h)] + [(f"tracer{k}", tr[k]) for k in range(tr.shape[0])]
+    hin = [(n, torch.from_numpy(np.ascontiguousarray(x)).pin_memory()) for n, x in fields]
+    hout = [(n, torch.empty_like(x).pin_memory()) for n, x in hin]
     order, dt, M = run["order"], run["dt"], run["M"]
-    st.set_ptr("u", hu.data_ptr())
-    st.set_ptr("h", hh.data_ptr())
-    st.set_ptr("tracer0", ht.data_ptr())
+    for n, x in hin:
+        st.set_ptr(n, x.data_ptr())
     st.step(order, dt, M, 1)
     torch.cuda.synchronize()
     a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     a.record(stream)
     for _ in range(steps):
-        st.set_ptr("u", hu.data_ptr())
-        st.set_ptr("h", hh.data_ptr())
-        st.set_ptr("tracer0", ht.data_ptr())
+        for n, x in hin:
+            st.set_ptr(n, x.data_ptr())
         st.step(order, dt, M, 1)
-        st.get_ptr("u", ou.data_ptr())
-        st.get_ptr("h", oh.data_ptr())
-        st.get_ptr("tracer0", ot.data_ptr())
+        for n, x in hout:
+            st.get_ptr(n, x.data_ptr())
     b.record(stream)
     torch.cuda.synchronize()
     ms = a.elapsed_time(b)
-    nbytes = (hu.numel() + hh.numel() + ht.numel()) * 8
+    nbytes = sum(x.numel() for _, x in hin) * 8
     st.close()
     return ms, nbytes
+
+
+def roofline_of(prof, m, L, nT, mixed, order, steps, ms_per_step):
+    """Dominant kernel class against the HBM copy peak, and the whole step."""
+    peaks, peak_kind = measured_peaks()
+    sR = 4 if mixed else 8
+    dom = max(prof, key=lambda k: prof[k][0])
+    nlaunch = prof[dom][1]
+    per_launch_ms = prof[dom][0] / max(nlaunch, 1)
+    C, E, V = m.nCells, m.nEdges, m.nVertices
+    if dom in ("bcl_edge", "thickness"):
+        # the first stage of a step has no old-level input (utilde^n, h^n)
+        b = (kernel_bytes(dom, C, E, V, L, nT, sR, False, mixed) +
+             (order - 1) * kernel_bytes(dom, C, E, V, L, nT, sR, True, mixed)) / order
+    else:
+        b = kernel_bytes(dom, C, E, V, L, nT, sR, True, mixed)
+    achieved = b / (per_launch_ms / 1e3) / 1e9
+    return {"kernel": dom, "bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"],
+            "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"],
+            "peak_source": f"{peak_kind} hbm_gbs (copy)", "bytes_per_launch": b,
+            "ms_per_launch": per_launch_ms}
+
+
+def step_roofline_of(m, L, nT, mixed, ms_per_step):
+    peaks, _ = measured_peaks()
+    step_b = step_bytes_per_cell_layer(mixed, nT) * m.nCells * L
+    gbs = step_b / (ms_per_step / 1e3) / 1e9
+    return {"bytes_per_step": step_b, "achieved_gbs": gbs, "frac_of_hbm": gbs / peaks["hbm_gbs"]}
+
+
+def measure_workload(torch, binding, name, forms_todo, headline, steps, warmup, rank, stream,
+                     flush, sampler=None, e2e=True, world=1, dist=None):
+    """Every requested precision form of one named workload on this GPU."""
+    m, L, p, state0, run = build_workload(seed=rank, name=name)
+    nT = int(p.get("nTracers", 1))
+    dm = binding.Mesh(m, L)
+    forms = {}
+    for prec in forms_todo:
+        forms[prec] = measure_form(torch, binding, dm, m, L, p, state0, run, prec, steps, warmup,
+                                   stream, flush, sampler if prec == headline else None)
+    head = forms[headline]
+    mixed = headline == "mixed"
+    out = {"mesh": m, "L": L, "p": p, "run": run, "nT": nT, "forms": forms, "head": head}
+    out["t_max"] = max_over_ranks(torch, dist, head["device_ms"], "cuda")
+    out["value"] = replica_throughput(m.nCells * L * steps, world, out["t_max"])
+    # error of the mixed form against the FP64 form at the horizon (per field)
+    out["mixed_err"] = None
+    if "fp64" in forms and "mixed" in forms:
+        fu, fh, ft = forms["fp64"]["final"]
+        mu, mh, mt = forms["mixed"]["final"]
+
+        def rel(a, b):
+            return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+        err = {"u": rel(mu, fu), "h": rel(mh, fh),
+               "zeta": rel(mh.sum(1) - m.bottomDepth, fh.sum(1) - m.bottomDepth)}
+        for k, nm in zip(range(nT), ("T", "S")):
+            err[nm] = rel(mt[k], ft[k])
+        out["mixed_err"] = err
+    prof = head["prof"]
+    roof = roofline_of(prof, m, L, nT, mixed, run["order"], steps, head["ms_per_step"])
+    traffic, traffic_src = ncu_traffic(roof["kernel"], mixed) if name == WORKLOAD else \
+        (None, "no ncu capture of this workload")
+    roof["traffic"], roof["traffic_source"] = traffic, traffic_src
+    out["roofline"] = roof
+    out["step_roofline"] = step_roofline_of(m, L, nT, mixed, head["ms_per_step"])
+    out["kernels"] = {k: {"ms_per_step": v[0] / steps, "share": v[0] / max(head["device_ms"], 1e-9),
+                          "launches_per_step": v[1] / steps} for k, v in prof.items()}
+    vol0 = float(m.areaCell @ state0[1].sum(1))
+    out["forms_summary"] = {
+        k: {"value": world * m.nCells * L * steps / (v["device_ms"] / 1e3),
+            "ms_per_step": v["ms_per_step"], "latency_ms": v["latency_ms"],
+            "volume_rel_change": abs(v["diag"]["volume"] - vol0) / vol0}
+        for k, v in forms.items()}
+    out["e2e"] = None
+    if e2e:
+        e2e_steps = min(steps, 20)
+        e2e_ms, nbytes = measure_e2e(torch, binding, dm, p, state0, run, headline, e2e_steps,
+                                     stream)
+        e2e_val = replica_throughput(m.nCells * L * e2e_steps, world,
+                                     max_over_ranks(torch, dist, e2e_ms, "cuda"))
+        out["e2e"] = {"value": e2e_val, "unit": METRIC, "h2d_bytes_per_step": nbytes,
+                      "d2h_bytes_per_step": nbytes}
+    dm.close()
+    return out
+
+
+def config_of(name, w, precision, world):
+    m, L, run, p = w["mesh"], w["L"], w["run"], w["p"]
+    return {"workload": name, "cells": m.nCells, "edges": m.nEdges, "layers": L,
+            "tracers": w["nT"], "scheme": f"SSPRK{run['order']}-SE", "dt": run["dt"],
+            "M": run["M"], "recon": p.get("recon"), "precision": precision,
+            "l2": "flushed (512 MB write) between timed steps, flush excluded",
+            "parallelism": f"replicas x{world}"}
 
 
 def run_ours(args):
@@ -341,12 +436,8 @@ def run_ours(args):
         dist.init_process_group("nccl")
     build.build()
     binding.load()
-    m, L, p, state0, run = build_workload(seed=rank)
-    dm = binding.Mesh(m, L)
     stream = torch.cuda.Stream()
     flush = torch.empty(512 * 2 ** 20 // 4, dtype=torch.float32, device="cuda")
-    forms = {}
-    order = run["order"]
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
@@ -354,93 +445,42 @@ def run_ours(args):
     todo = ("mixed", "fp64") if args.forms == "both" else (args.forms,)
     if args.precision not in todo:
         todo = todo + (args.precision,)
-    for prec in todo:
-        forms[prec] = measure_form(torch, binding, dm, m, L, p, state0, run, prec, args.steps,
-                                   args.warmup, stream, flush,
-                                   sampler if prec == args.precision else None)
-    head = forms[args.precision]
-    units = m.nCells * L * args.steps
-    t_max = max_over_ranks(torch, dist, head["device_ms"], "cuda")
-    value = replica_throughput(units, world, t_max)
-
-    # error of the mixed form against the FP64 form at the horizon (per field)
-    mixed_err = None
-    if "fp64" in forms and "mixed" in forms:
-        fu, fh, ft = forms["fp64"]["final"]
-        mu, mh, mt = forms["mixed"]["final"]
-
-        def rel(a, b):
-            return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
-        mixed_err = {"u": rel(mu, fu), "h": rel(mh, fh),
-                     "zeta": rel(mh.sum(1) - m.bottomDepth, fh.sum(1) - m.bottomDepth),
-                     "T": rel(mt, ft)}
-
-    # roofline of the dominant kernel class (by summed device time)
-    peaks, peak_kind = measured_peaks()
-    mixed = args.precision == "mixed"
-    sR = 4 if mixed else 8
-    prof = head["prof"]
-    dom = max(prof, key=lambda k: prof[k][0])
-    nlaunch = prof[dom][1]
-    per_launch_ms = prof[dom][0] / max(nlaunch, 1)
-    nT = int(p.get("nTracers", 1))
-    if dom in ("bcl_edge", "thickness"):
-        # the first stage of a step has no old-level input (utilde^n, h^n)
-        b = (kernel_bytes(dom, m.nCells, m.nEdges, m.nVertices, L, nT, sR, False, mixed) +
-             (order - 1) * kernel_bytes(dom, m.nCells, m.nEdges, m.nVertices, L, nT, sR, True,
-                                        mixed)) / order
-    else:
-        b = kernel_bytes(dom, m.nCells, m.nEdges, m.nVertices, L, nT, sR, True, mixed)
-    achieved = b / (per_launch_ms / 1e3) / 1e9
-    traffic, traffic_src = ncu_traffic(dom, mixed)
-    roof = {"kernel": dom, "bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"],
-            "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"], "traffic": traffic,
-            "traffic_source": traffic_src,
-            "peak_source": f"{peak_kind} hbm_gbs (copy)", "bytes_per_launch": b,
-            "ms_per_launch": per_launch_ms}
-    step_b = step_bytes_per_cell_layer(mixed, nT) * m.nCells * L
-    step_roof = {"bytes_per_step": step_b,
-                 "achieved_gbs": step_b / (head["ms_per_step"] / 1e3) / 1e9,
-                 "frac_of_hbm": step_b / (head["ms_per_step"] / 1e3) / 1e9 / peaks["hbm_gbs"]}
-    kernels = {k: {"ms_per_step": v[0] / args.steps, "share": v[0] / max(head["device_ms"], 1e-9),
-                   "launches_per_step": v[1] / args.steps} for k, v in prof.items()}
-
-    e2e = None
-    if not args.no_e2e:
-        e2e_steps = min(args.steps, 20)
-        e2e_ms, nbytes = measure_e2e(torch, binding, dm, p, state0, run, args.precision,
-                                     e2e_steps, stream)
-        e2e_val = replica_throughput(m.nCells * L * e2e_steps, world,
-                                     max_over_ranks(torch, dist, e2e_ms, "cuda"))
-        e2e = {"value": e2e_val, "unit": METRIC, "h2d_bytes_per_step": nbytes,
-               "d2h_bytes_per_step": nbytes}
+    w = measure_workload(torch, binding, args.workload, todo, args.precision, args.steps,
+                         args.warmup, rank, stream, flush, sampler, not args.no_e2e, world, dist)
+    head = w["head"]
+    also = {}
+    if args.workload == WORKLOAD and not args.no_sphere:
+        # the largest single mesh: the 60-layer level-7 sphere, mixed form
+        ns = min(args.steps, 144)
+        s7 = measure_workload(torch, binding, "sphere_l7", ("mixed",), "mixed", ns, args.warmup,
+                              rank, stream, flush, None, False, world, dist)
+        also["sphere_l7"] = {
+            "value": s7["value"], "unit": METRIC, "steps": ns,
+            "ms_per_step": s7["t_max"] / ns, "latency_ms": s7["head"]["latency_ms"],
+            "config": config_of("sphere_l7", s7, "mixed", world), "roofline": s7["roofline"],
+            "step_roofline": s7["step_roofline"], "kernels": s7["kernels"],
+            "volume_rel_change": s7["forms_summary"]["mixed"]["volume_rel_change"]}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
         v, ms, sample = time_oracle(2, 0, sample=(160, 578))
         cpu = {"value": v, "unit": METRIC, "cores": 1, "kind": "oracle", "sample": sample}
 
-    vol0 = float(m.areaCell @ state0[1].sum(1))
     line = {
-        "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": world,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_max / args.steps,
+        "metric": METRIC, "value": w["value"], "unit": METRIC, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": w["t_max"] / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "f32+f64" if mixed else "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "cells": m.nCells, "edges": m.nEdges, "layers": L,
-                   "scheme": f"SSPRK{order}-SE", "dt": run["dt"], "M": run["M"],
-                   "recon": p.get("recon"), "precision": args.precision,
-                   "l2": "flushed (512 MB write) between timed steps, flush excluded",
-                   "parallelism": f"replicas x{world}"},
-        "roofline": roof, "step_roofline": step_roof, "kernels": kernels,
-        "forms": {k: {"value": world * units / (v["device_ms"] / 1e3),
-                      "ms_per_step": v["ms_per_step"],
-                      "volume_rel_change": abs(v["diag"]["volume"] - vol0) / vol0}
-                  for k, v in forms.items()},
-        "mixed_vs_fp64_rel_l2": mixed_err,
-        "e2e": e2e,
+        "dtype": "f32+f64" if args.precision == "mixed" else "f64", "data": "synthetic",
+        "config": config_of(args.workload, w, args.precision, world),
+        "roofline": w["roofline"], "step_roofline": w["step_roofline"], "kernels": w["kernels"],
+        "latency_ms": head["latency_ms"],
+        "forms": w["forms_summary"],
+        "mixed_vs_fp64_rel_l2": w["mixed_err"],
+        "e2e": w["e2e"],
         "gpu_launches": head["kernels_per_step"] * args.steps,
         "clocks": head["clocks"],
         "cpu_baseline": cpu,
+        "also": also or None,
     }
     if dist:
         dist.barrier()
@@ -462,6 +502,10 @@ def main():
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end leg")
     ap.add_argument("--forms", default="both", choices=["both", "mixed", "fp64"],
                     help="precision forms to measure (the headline form is always measured)")
+    ap.add_argument("--workload", default=WORKLOAD, choices=[WORKLOAD, "sphere_l7"],
+                    help="headline workload (default: the 92,480-cell channel)")
+    ap.add_argument("--no-sphere", action="store_true",
+                    help="skip the extra level-7 sphere measurement")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

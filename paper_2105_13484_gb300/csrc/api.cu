@@ -364,13 +364,18 @@ struct Engine : EngineBase {
                 if (verbose) fprintf(stderr, "libsse: tile plan k=%d: 16-bit local index overflow\n", k);
                 continue;
             }
-            bool small = true;  // 16-bit byte offsets; <= 2 entries of each kind per thread
-            for (const TilePatch &t : plan.patches)
-                if ((size_t)(t.ne + 1) * sizeof(R) >= 65536 || (size_t)(t.nc + 1) * sizeof(R) >= 65536 ||
-                    t.n_own_e > 2 * nthreads || t.ne - t.n_own_e > 2 * nthreads ||
-                    t.n_own_c > 2 * nthreads || t.nc - t.n_own_c > 2 * nthreads)
+            // 16-bit byte offsets; at most 3 entries of each kind per thread
+            int own = 0;
+            bool small = true;
+            for (const TilePatch &t : plan.patches) {
+                if ((size_t)(t.ne + 1) * sizeof(R) >= 65536 || (size_t)(t.nc + 1) * sizeof(R) >= 65536)
                     small = false;
-            if (!small) {
+                const int most = std::max(std::max(t.n_own_e, t.ne - t.n_own_e),
+                                          std::max(t.n_own_c, t.nc - t.n_own_c));
+                own = std::max(own, (most + nthreads - 1) / nthreads);
+            }
+            own = std::max(own, 2);
+            if (!small || own > 3) {
                 if (verbose) fprintf(stderr, "libsse: tile plan k=%d: patch too large\n", k);
                 continue;
             }
@@ -383,10 +388,10 @@ struct Engine : EngineBase {
             }
 
             for (int o = 2; o <= 3; o++)
-                CK(cudaFuncSetAttribute(btr_tiled_kernel_ptr<R>(o),
+                CK(cudaFuncSetAttribute(btr_tiled_kernel_ptr<R>(o, own),
                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
             int occ = 0;
-            CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, btr_tiled_kernel_ptr<R>(3),
+            CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, btr_tiled_kernel_ptr<R>(3, own),
                                                              nthreads, smem));
             if (occ * nsm < P) {
                 if (verbose)
@@ -401,16 +406,16 @@ struct Engine : EngineBase {
                     mne = std::max(mne, t.ne); mnc = std::max(mnc, t.nc);
                     moe = std::max(moe, t.n_own_e); tne += t.ne; tnc += t.nc;
                 }
-                fprintf(stderr, "libsse: tiled sub-cycle P=%d smem=%zu max(ne,nc,own_e)=(%d,%d,%d) "
-                        "halo overhead edges %.2f cells %.2f\n", P, smem, mne, mnc, moe,
+                fprintf(stderr, "libsse: tiled sub-cycle P=%d own=%d smem=%zu max(ne,nc,own_e)=(%d,%d,%d) "
+                        "halo overhead edges %.2f cells %.2f\n", P, own, smem, mne, mnc, moe,
                         (double)tne / m.E, (double)tnc / m.C);
             }
-            return upload_tiles(plan, nthreads, smem);
+            return upload_tiles(plan, nthreads, own, smem);
         }
         return SSE_OK;  // no plan fits: the global-memory sub-cycle is used
     }
 
-    int upload_tiles(const TilePlan &plan, int nthreads, size_t smem) {
+    int upload_tiles(const TilePlan &plan, int nthreads, int own, size_t smem) {
         const unsigned int sR = sizeof(R);
         std::vector<int> noc, noe, cg, eg, c12;
         std::vector<unsigned short> eo, ce;
@@ -442,7 +447,7 @@ struct Engine : EngineBase {
             for (double x : t.H) Hh.push_back((R)x);
         }
         DTiles<R> &t = tiles;
-        t.P = plan.P; t.nthreads = nthreads; t.smem = smem;
+        t.P = plan.P; t.nthreads = nthreads; t.own = own; t.smem = smem;
         t.cell_off = A.upload(plan.cell_off); t.edge_off = A.upload(plan.edge_off);
         t.n_own_c = A.upload(noc); t.n_own_e = A.upload(noe);
         t.cell_gid = A.upload(cg); t.edge_gid = A.upload(eg); t.c12 = A.upload(c12);

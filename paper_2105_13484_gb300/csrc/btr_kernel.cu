@@ -289,11 +289,12 @@ template <class R> __device__ __forceinline__ R at(const R *base, unsigned int o
     return *(const R *)((const char *)base + off);
 }
 
-// the coefficients of one edge (TILE_NE2P) or one cell (TILE_NCEP) with 128-bit loads
+// the coefficients of one edge (TILE_NE2P) or one cell (TILE_NCEP) with paired
+// loads (rows are 8-byte aligned in FP32 and 16-byte aligned in FP64)
 __device__ __forceinline__ void ldc(const float *p, float *c, int n) {
-    for (int i = 0; i < n / 4; i++) {
-        const float4 v = __ldg((const float4 *)p + i);
-        c[4 * i] = v.x; c[4 * i + 1] = v.y; c[4 * i + 2] = v.z; c[4 * i + 3] = v.w;
+    for (int i = 0; i < n / 2; i++) {
+        const float2 v = __ldg((const float2 *)p + i);
+        c[2 * i] = v.x; c[2 * i + 1] = v.y;
     }
 }
 __device__ __forceinline__ void ldc(const double *p, double *c, int n) {
@@ -309,13 +310,12 @@ __device__ __forceinline__ R tile_fe_edge(const TileSmem<R> &S, const R *__restr
                                           const R *u, const R *z, R tau, R g, R &flux) {
     R cf[TILE_NE2P];
     ldc(cfc + (size_t)l * TILE_NE2P, cf, TILE_NE2P);
-    const uint2 *eo = (const uint2 *)(S.eoe + (size_t)l * TILE_NE2P);
+    const unsigned int *eo = (const unsigned int *)(S.eoe + (size_t)l * TILE_NE2P);
     unsigned int o[TILE_NE2P];
 #pragma unroll
-    for (int i = 0; i < TILE_NE2P / 4; i++) {
-        const uint2 v = eo[i];
-        o[4 * i] = v.x & 0xffffu; o[4 * i + 1] = v.x >> 16;
-        o[4 * i + 2] = v.y & 0xffffu; o[4 * i + 3] = v.y >> 16;
+    for (int i = 0; i < TILE_NE2P / 2; i++) {
+        const unsigned int v = eo[i];
+        o[2 * i] = v & 0xffffu; o[2 * i + 1] = v >> 16;
     }
     R acc = R(0);
 #pragma unroll
@@ -333,21 +333,23 @@ __device__ __forceinline__ R tile_fe_cell(const TileSmem<R> &S, const R *__restr
                                           const R *z, R tau) {
     R dc[TILE_NCEP];
     ldc(dvc + (size_t)l * TILE_NCEP, dc, TILE_NCEP);
-    const uint4 v = *(const uint4 *)(S.ce + (size_t)l * TILE_NCEP);
-    const unsigned int o[8] = {v.x & 0xffffu, v.x >> 16, v.y & 0xffffu, v.y >> 16,
-                               v.z & 0xffffu, v.z >> 16, v.w & 0xffffu, v.w >> 16};
+    const unsigned int *co = (const unsigned int *)(S.ce + (size_t)l * TILE_NCEP);
+    unsigned int o[TILE_NCEP];
+#pragma unroll
+    for (int i = 0; i < TILE_NCEP / 2; i++) {
+        const unsigned int v = co[i];
+        o[2 * i] = v & 0xffffu; o[2 * i + 1] = v >> 16;
+    }
     R dv = R(0);
 #pragma unroll
     for (int j = 0; j < TILE_NCEP; j++) dv += dc[j] * at(S.fl, o[j]);
     return z[l] - tau * dv;
 }
 
-// Each thread owns at most TILE_OWN owned edges, halo edges, owned cells and
-// halo cells of its patch (the plan checks this); their global indices, the
+// Each thread owns at most OWN owned edges, halo edges, owned cells and halo
+// cells of its patch (the plan checks this); their global indices, the
 // sub-step's partial F^zeta and the FP64 accumulators stay in registers.
-constexpr int TILE_OWN = 2;
-
-template <class R, int ORDER>
+template <class R, int ORDER, int OWN>
 __global__ void __launch_bounds__(TILE_THREADS, 1) k_btr_tiled(DTiles<R> t, BtrArgs<R> a,
                                                                Barrier bar) {
     extern __shared__ __align__(16) char smem_raw[];
@@ -363,9 +365,9 @@ __global__ void __launch_bounds__(TILE_THREADS, 1) k_btr_tiled(DTiles<R> t, BtrA
     unsigned int gen = 0;
 
     // global indices of this thread's owned and halo entries
-    int oe[TILE_OWN], he[TILE_OWN], oc[TILE_OWN], hc[TILE_OWN];
+    int oe[OWN], he[OWN], oc[OWN], hc[OWN];
 #pragma unroll
-    for (int k = 0; k < TILE_OWN; k++) {
+    for (int k = 0; k < OWN; k++) {
         const int lo = tid + k * nt, lh = noe + tid + k * nt;
         const int co = tid + k * nt, ch = noc + tid + k * nt;
         oe[k] = lo < noe ? t.edge_gid[eoff + lo] : -1;
@@ -389,12 +391,12 @@ __global__ void __launch_bounds__(TILE_THREADS, 1) k_btr_tiled(DTiles<R> t, BtrA
         S.ua[l] = R(0); S.uh[l] = R(0); S.fl[l] = R(0);
     }
     {
-        // rows are TILE_NE2P * 2 = 24 bytes: copy in 8-byte words (every row and the
-        // patch base edge_off * 24 bytes are 8-byte aligned)
-        const uint2 *src = (const uint2 *)(t.eoe + (size_t)eoff * TILE_NE2P);
-        uint2 *dst = (uint2 *)S.eoe;
-        const int n8 = ne * (TILE_NE2P * 2 / 8);
-        for (int x = tid; x < n8; x += nt) dst[x] = src[x];
+        // rows are TILE_NE2P * 2 = 20 bytes: copy in 4-byte words (every row and the
+        // patch base edge_off * 20 bytes are 4-byte aligned)
+        const unsigned int *src = (const unsigned int *)(t.eoe + (size_t)eoff * TILE_NE2P);
+        unsigned int *dst = (unsigned int *)S.eoe;
+        const int n4 = ne * (TILE_NE2P / 2);
+        for (int x = tid; x < n4; x += nt) dst[x] = src[x];
         if (tid < TILE_NE2P) S.eoe[(size_t)ne * TILE_NE2P + tid] = (unsigned short)(ne * sizeof(R));
     }
     for (int l = tid; l <= nc; l += nt) {
@@ -403,14 +405,16 @@ __global__ void __launch_bounds__(TILE_THREADS, 1) k_btr_tiled(DTiles<R> t, BtrA
         S.H[l] = t.H[coff + p + l];
     }
     {
-        const uint4 *src = (const uint4 *)(t.ce + (size_t)coff * TILE_NCEP);
-        uint4 *dst = (uint4 *)S.ce;
-        for (int x = tid; x < nc; x += nt) dst[x] = src[x];
+        // rows of TILE_NCEP * 2 = 12 bytes, copied in 4-byte words
+        const unsigned int *src = (const unsigned int *)(t.ce + (size_t)coff * TILE_NCEP);
+        unsigned int *dst = (unsigned int *)S.ce;
+        const int n4 = nc * (TILE_NCEP / 2);
+        for (int x = tid; x < n4; x += nt) dst[x] = src[x];
     }
-    R Fs[TILE_OWN];
-    double Fz[TILE_OWN];
+    R Fs[OWN];
+    double Fz[OWN];
 #pragma unroll
-    for (int k = 0; k < TILE_OWN; k++) { Fs[k] = R(0); Fz[k] = 0.0; }
+    for (int k = 0; k < OWN; k++) { Fs[k] = R(0); Fz[k] = 0.0; }
     __syncthreads();
 
     const R wAB = (ORDER == 2) ? R(0.5) : R(1.0 / 6.0);
@@ -420,7 +424,7 @@ __global__ void __launch_bounds__(TILE_THREADS, 1) k_btr_tiled(DTiles<R> t, BtrA
     for (int j = 0; j < a.M; j++) {
         // ---- stage a: (ua, za) = FE(u0, z0)
 #pragma unroll
-        for (int k = 0; k < TILE_OWN; k++) {
+        for (int k = 0; k < OWN; k++) {
             const int l = tid + k * nt;
             if (l < noe) {
                 R f;
@@ -439,7 +443,7 @@ __global__ void __launch_bounds__(TILE_THREADS, 1) k_btr_tiled(DTiles<R> t, BtrA
         __syncthreads();
         // ---- stage b: FE(ua, za), first convex combination
 #pragma unroll
-        for (int k = 0; k < TILE_OWN; k++) {
+        for (int k = 0; k < OWN; k++) {
             const int l = tid + k * nt;
             if (l < noe) {
                 R f;
@@ -467,7 +471,7 @@ __global__ void __launch_bounds__(TILE_THREADS, 1) k_btr_tiled(DTiles<R> t, BtrA
         if (ORDER == 3) {
             // ---- stage c: FE(uh, zh), second convex combination
 #pragma unroll
-            for (int k = 0; k < TILE_OWN; k++) {
+            for (int k = 0; k < OWN; k++) {
                 const int l = tid + k * nt;
                 if (l < noe) {
                     R f;
@@ -491,18 +495,18 @@ __global__ void __launch_bounds__(TILE_THREADS, 1) k_btr_tiled(DTiles<R> t, BtrA
             __syncthreads();
         }
 #pragma unroll
-        for (int k = 0; k < TILE_OWN; k++) Fz[k] += invM * (double)Fs[k];
+        for (int k = 0; k < OWN; k++) Fz[k] += invM * (double)Fs[k];
         if (j + 1 == a.M) break;
         // ---- exchange the owned values, refresh the halo
         R *xu = t.xu[buf], *xz = t.xz[buf];
 #pragma unroll
-        for (int k = 0; k < TILE_OWN; k++) {
+        for (int k = 0; k < OWN; k++) {
             if (oe[k] >= 0) xu[oe[k]] = S.u0[tid + k * nt];
             if (oc[k] >= 0) xz[oc[k]] = S.z0[tid + k * nt];
         }
         if (!grid_barrier(bar, gen, gridDim.x)) return;
 #pragma unroll
-        for (int k = 0; k < TILE_OWN; k++) {
+        for (int k = 0; k < OWN; k++) {
             if (he[k] >= 0) S.u0[noe + tid + k * nt] = __ldcg(xu + he[k]);
             if (hc[k] >= 0) S.z0[noc + tid + k * nt] = __ldcg(xz + hc[k]);
         }
@@ -511,7 +515,7 @@ __global__ void __launch_bounds__(TILE_THREADS, 1) k_btr_tiled(DTiles<R> t, BtrA
     }
     // ---- outputs for the owned edges and cells
 #pragma unroll
-    for (int k = 0; k < TILE_OWN; k++) {
+    for (int k = 0; k < OWN; k++) {
         if (oe[k] >= 0) {
             const R u0 = S.u0[tid + k * nt];
             a.Fz[oe[k]] = Fz[k];
@@ -521,8 +525,10 @@ __global__ void __launch_bounds__(TILE_THREADS, 1) k_btr_tiled(DTiles<R> t, BtrA
     }
 }
 
-template <class R> const void *btr_tiled_kernel_ptr(int order) {
-    return order == 2 ? (const void *)k_btr_tiled<R, 2> : (const void *)k_btr_tiled<R, 3>;
+template <class R> const void *btr_tiled_kernel_ptr(int order, int own) {
+    if (own == 2)
+        return order == 2 ? (const void *)k_btr_tiled<R, 2, 2> : (const void *)k_btr_tiled<R, 3, 2>;
+    return order == 2 ? (const void *)k_btr_tiled<R, 2, 3> : (const void *)k_btr_tiled<R, 3, 3>;
 }
 
 template <class R>
@@ -542,11 +548,11 @@ cudaError_t launch_btr_tiled(const DTiles<R> &t, const BtrArgs<R> &a, const Barr
     attr[0].val.cooperative = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    return cudaLaunchKernelExC(&cfg, btr_tiled_kernel_ptr<R>(a.order), args);
+    return cudaLaunchKernelExC(&cfg, btr_tiled_kernel_ptr<R>(a.order, t.own), args);
 }
 
-template const void *btr_tiled_kernel_ptr<double>(int);
-template const void *btr_tiled_kernel_ptr<float>(int);
+template const void *btr_tiled_kernel_ptr<double>(int, int);
+template const void *btr_tiled_kernel_ptr<float>(int, int);
 template cudaError_t launch_btr_tiled<double>(const DTiles<double> &, const BtrArgs<double> &,
                                               const Barrier &, cudaStream_t);
 template cudaError_t launch_btr_tiled<float>(const DTiles<float> &, const BtrArgs<float> &,

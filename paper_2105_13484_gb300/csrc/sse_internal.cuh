@@ -132,7 +132,7 @@ int btr_max_items_per_thread();
 // Device copy of the tiled sub-cycle plan (see tiles.h): per-patch arrays
 // flattened with the offsets cell_off / edge_off.
 template <class R> struct DTiles {
-    int P, nthreads;
+    int P, nthreads, own;            // patches, threads per patch, entries per thread
     const int *cell_off, *edge_off;  // [P + 1]
     const int *n_own_c, *n_own_e;    // [P]
     const int *cell_gid, *edge_gid;  // local -> global
@@ -150,7 +150,7 @@ template <class R> struct DTiles {
 template <class R>
 cudaError_t launch_btr_tiled(const DTiles<R> &t, const BtrArgs<R> &a, const Barrier &bar,
                              cudaStream_t s);
-template <class R> const void *btr_tiled_kernel_ptr(int order);
+template <class R> const void *btr_tiled_kernel_ptr(int order, int own);
 
 template <class R> struct TransportArgs {
     const R *hR;              // stage thickness [L][Cp] in the tendency precision

@@ -8,8 +8,8 @@
 namespace sse {
 
 // padded per-entry strides of the tiled sub-cycle's local connectivity
-constexpr int TILE_NE2P = 12;  // edgesOnEdge per edge (<= 10 used)
-constexpr int TILE_NCEP = 8;   // edgesOnCell per cell (<= 8 used)
+constexpr int TILE_NE2P = 10;  // edgesOnEdge per edge (hexagon/pentagon meshes: <= 10)
+constexpr int TILE_NCEP = 6;   // edgesOnCell per cell (<= 6)
 
 // host copy of the connectivity and coefficients the plan needs
 struct HostMesh {

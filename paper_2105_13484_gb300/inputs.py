@@ -14,9 +14,11 @@ stand in for them):
   SSPRK2-SE, dt = 300 s, M = 20, 10 steps.
 * ``channel_1km``   160 x 578 cells at 1 km (160 km x 500 km, 92,480 cells),
   20 layers x 50 m, beta plane, same front.  SSPRK3-SE, dt = 60 s, M = 30.
-* ``sphere_l7``     icosahedral geodesic sphere (163,842 cells), 60 z-star
-  layers, seeded bathymetry, ~30 % land, T and S, wind stress.
-  SSPRK3-SE, dt = 600 s, M = 40.
+* ``sphere_l7``     icosahedral geodesic sphere at level 7 (163,842 cells before
+  the land mask), 60 z-star layers, seeded bathymetry 100-5000 m, ~30 % land,
+  T and S with the linear EOS, f = 2 Omega sin(lat), seeded zonal wind stress.
+  SSPRK3-SE, dt = 600 s, M = 40, 144 steps.  ``sphere_l4`` is the same
+  recipe at level 4 (2,562 cells) with 12 layers for parity tests.
 """
 from __future__ import annotations
 
@@ -95,11 +97,80 @@ def channel_case(nx, ny, dc, L, *, depth=1000.0, f0=1.2e-4, beta=0.0, seed=0, pe
     return m, L, p, (u, h, tr)
 
 
+def _low_degree_field(rng, deg=4):
+    """Seeded smooth field on the unit sphere: a random polynomial of degree
+    <= deg in (x, y, z), i.e. a combination of spherical harmonics of degree
+    <= deg, returned as a function of unit vectors [n, 3]."""
+    terms = [(a, b, c) for a in range(deg + 1) for b in range(deg + 1 - a)
+             for c in range(deg + 1 - a - b)]
+    coef = rng.standard_normal(len(terms)) / (1.0 + np.array([sum(t) for t in terms]))
+
+    def field(p):
+        x, y, z = p[:, 0], p[:, 1], p[:, 2]
+        return sum(k * x ** a * y ** b * z ** c for k, (a, b, c) in zip(coef, terms))
+    return field
+
+
+def sphere_case(level, L, *, seed=0, land_frac=0.3, dmin=100.0, dmax=5000.0, nTracers=2,
+                wind=0.1, perturb=False, **params):
+    """(mesh, L, params, (u, h, tr)) for the global-ocean-like sphere.
+
+    Land: the cells where a seeded low-degree field is below its land_frac
+    quantile (largest ocean basin kept).  Bathymetry: a second seeded field
+    mapped linearly onto [dmin, dmax] over the ocean.  T decreases with
+    latitude and depth (about 25 C at the equator surface to 5 C at depth), S
+    between 34 and 36; u = 0 and zeta = 0 at rest (``perturb`` adds a seeded
+    smooth SSH bump).  Wind stress: zonal, amplitude ``wind`` N m^-2, a seeded
+    mix of cos(2 lat)-type bands, projected on the edge normals.
+    """
+    rng = np.random.default_rng(seed)
+    f_land, f_dep = _low_degree_field(rng), _low_degree_field(rng)
+
+    def land(p):
+        v = f_land(p)
+        return v < np.quantile(v, land_frac)
+
+    def depth(p):
+        v = f_dep(p)
+        v = (v - v.min()) / max(v.max() - v.min(), 1e-300)
+        return dmin + (dmax - dmin) * v
+
+    m = _mesh.geodesic_sphere(level, land=land, depth=depth)
+    R = float(np.linalg.norm(m.xCell[0]))
+    lat = m.latCell
+    s = np.full(L, 1.0 / L)
+    zfrac = -(np.cumsum(s) - 0.5 * s)            # 0 at the surface, -1 at the bottom
+    dz = m.bottomDepth[:, None] * zfrac[None, :]  # mid-layer depth (negative), m
+    zeta = np.zeros(m.nCells)
+    if perturb:
+        c0 = m.xCell[rng.integers(m.nCells)] / R
+        zeta = 0.5 * np.exp(-((1.0 - m.xCell @ c0 / R) / 0.02))
+    h = (m.bottomDepth + zeta)[:, None] * s[None, :]
+    T = 5.0 + 20.0 * (np.cos(lat) ** 2)[:, None] * np.exp(dz / 800.0)
+    S = 34.0 + 2.0 * (np.cos(lat) ** 2)[:, None] * np.exp(dz / 1500.0)
+    tr = np.stack([T, S][:nTracers])
+    u = np.zeros((m.nEdges, L))
+    xe = m.xEdge / R
+    late = np.arcsin(np.clip(xe[:, 2], -1, 1))
+    east = np.cross(np.array([0.0, 0.0, 1.0]), xe)
+    east /= np.maximum(np.linalg.norm(east, axis=1, keepdims=True), 1e-300)
+    a1, a2 = rng.uniform(0.5, 1.0, 2)
+    prof = -a1 * np.cos(3.0 * late) + a2 * np.cos(5.0 * late) * np.cos(late)
+    tau = wind * prof / np.abs(prof).max() * np.sum(east * m.normalEdge, axis=1)
+    p = dict(PHYS)
+    p.update(nTracers=nTracers, recon="consistent", nu_h=1.0e3, nu_v=1e-4, kappa_h=0.0,
+             kappa_v=0.0, c_drag=1e-3, windStress=tau)
+    p.update(params)
+    return m, L, p, (u, h, tr)
+
+
 WORKLOADS = {
     "channel_10km": dict(nx=16, ny=32, dc=10e3, L=10, depth=1000.0, f0=1.2e-4, beta=0.0,
                          order=2, dt=300.0, M=20, steps=10),
     "channel_1km": dict(nx=160, ny=578, dc=1e3, L=20, depth=1000.0, f0=1.2e-4, beta=1.6e-11,
                         order=3, dt=60.0, M=30, steps=200),
+    "sphere_l7": dict(kind="sphere", level=7, L=60, order=3, dt=600.0, M=40, steps=144),
+    "sphere_l4": dict(kind="sphere", level=4, L=12, order=3, dt=600.0, M=40, steps=10),
 }
 
 
@@ -108,6 +179,9 @@ def workload(name, *, seed=0, perturb=False, **override):
     w = dict(WORKLOADS[name])
     w.update(override)
     run = {k: w.pop(k) for k in ("order", "dt", "M", "steps")}
-    m, L, p, st = channel_case(w.pop("nx"), w.pop("ny"), w.pop("dc"), w.pop("L"), seed=seed,
-                               perturb=perturb, **w)
+    if w.pop("kind", "channel") == "sphere":
+        m, L, p, st = sphere_case(w.pop("level"), w.pop("L"), seed=seed, perturb=perturb, **w)
+    else:
+        m, L, p, st = channel_case(w.pop("nx"), w.pop("ny"), w.pop("dc"), w.pop("L"), seed=seed,
+                                   perturb=perturb, **w)
     return m, L, p, st, run

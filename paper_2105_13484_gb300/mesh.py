@@ -154,30 +154,36 @@ def _build(geo, cell_pos, vert_pos, cell_verts, n_on_cell):
     """
     C = cell_pos.shape[0]
     maxE = cell_verts.shape[1]
-    # --- edges: one per unordered vertex pair on a cell boundary
-    pairs = {}
-    edge_cells = []
-    edge_verts = []
-    edgesOnCell = -np.ones((C, maxE), dtype=np.int64)
-    for i in range(C):
-        n = n_on_cell[i]
-        for j in range(n):
-            a, b = cell_verts[i, j], cell_verts[i, (j + 1) % n]
-            key = (a, b) if a < b else (b, a)
-            e = pairs.get(key)
-            if e is None:
-                e = len(edge_cells)
-                pairs[key] = e
-                edge_cells.append([i, -1])
-                edge_verts.append([a, b])
-            else:
-                edge_cells[e][1] = i
-            edgesOnCell[i, j] = e
-    cellsOnEdge = np.array(edge_cells, dtype=np.int64)
-    vpair = np.array(edge_verts, dtype=np.int64)
-    E = cellsOnEdge.shape[0]
-    assert (cellsOnEdge[:, 1] >= 0).all(), "mesh is not closed"
     V = vert_pos.shape[0]
+    # --- edges: one per unordered vertex pair on a cell boundary, numbered in
+    # order of first appearance (cell-major); the first cell seen is c1
+    jj = np.arange(maxE)[None, :]
+    valid = jj < n_on_cell[:, None]
+    nn = np.maximum(n_on_cell, 1)[:, None]
+    va = cell_verts
+    vb = np.take_along_axis(cell_verts, (jj + 1) % nn, axis=1)
+    ci, cj = np.nonzero(valid)                      # cell-major order
+    a, b = va[ci, cj].astype(np.int64), vb[ci, cj].astype(np.int64)
+    key = np.minimum(a, b) * V + np.maximum(a, b)
+    uk, first, inv = np.unique(key, return_index=True, return_inverse=True)
+    rank = np.empty(uk.size, dtype=np.int64)
+    rank[np.argsort(first, kind="stable")] = np.arange(uk.size)
+    eid = rank[inv]
+    E = uk.size
+    edgesOnCell = -np.ones((C, maxE), dtype=np.int64)
+    edgesOnCell[ci, cj] = eid
+    cellsOnEdge = -np.ones((E, 2), dtype=np.int64)
+    vpair = np.zeros((E, 2), dtype=np.int64)
+    is_first = np.zeros(eid.size, dtype=bool)
+    is_first[first] = True
+    cellsOnEdge[eid[is_first], 0] = ci[is_first]
+    vpair[eid[is_first]] = np.stack([a[is_first], b[is_first]], axis=1)
+    cellsOnEdge[eid[~is_first], 1] = ci[~is_first]
+    assert (cellsOnEdge[:, 1] >= 0).all(), "mesh is not closed"
+    # position of each edge in the edge list of its c1 and of its c2
+    pos = np.zeros((E, 2), dtype=np.int64)
+    pos[eid[is_first], 0] = cj[is_first]
+    pos[eid[~is_first], 1] = cj[~is_first]
 
     xc1 = cell_pos[cellsOnEdge[:, 0]]
     xc2 = cell_pos[cellsOnEdge[:, 1]]
@@ -208,25 +214,25 @@ def _build(geo, cell_pos, vert_pos, cell_verts, n_on_cell):
         kite[idx, j] = geo.tri_area(xc, mb, xv) + geo.tri_area(xc, xv, ma)
     areaCell = kite.sum(axis=1)
 
-    # --- vertices: 3 cells, 3 edges each
+    # --- vertices: 3 cells, 3 edges each (cells in cell-major order of
+    # appearance, edges in edge order)
+    vv = cell_verts[ci, cj].astype(np.int64)
+    order = np.argsort(vv, kind="stable")
+    cnt = np.bincount(vv, minlength=V)
+    assert (cnt == 3).all(), "every vertex must touch 3 cells"
+    slot = np.arange(vv.size) - np.repeat(np.cumsum(cnt) - cnt, cnt)
     cellsOnVertex = -np.ones((V, 3), dtype=np.int64)
     kiteAreasOnVertex = np.zeros((V, 3))
-    cnt = np.zeros(V, dtype=np.int64)
-    for i in range(C):
-        for j in range(n_on_cell[i]):
-            v = cell_verts[i, j]
-            cellsOnVertex[v, cnt[v]] = i
-            kiteAreasOnVertex[v, cnt[v]] = kite[i, j]
-            cnt[v] += 1
-    assert (cnt == 3).all(), "every vertex must touch 3 cells"
+    cellsOnVertex[vv[order], slot] = ci[order]
+    kiteAreasOnVertex[vv[order], slot] = kite[ci[order], cj[order]]
     areaTriangle = kiteAreasOnVertex.sum(axis=1)
-    edgesOnVertex = -np.ones((V, 3), dtype=np.int64)
-    cnt[:] = 0
-    for e in range(E):
-        for v in verticesOnEdge[e]:
-            edgesOnVertex[v, cnt[v]] = e
-            cnt[v] += 1
+    ve = verticesOnEdge.ravel()
+    order = np.argsort(ve, kind="stable")
+    cnt = np.bincount(ve, minlength=V)
     assert (cnt == 3).all()
+    slot = np.arange(ve.size) - np.repeat(np.cumsum(cnt) - cnt, cnt)
+    edgesOnVertex = -np.ones((V, 3), dtype=np.int64)
+    edgesOnVertex[ve[order], slot] = (np.arange(ve.size) // 2)[order]
 
     # --- TRiSK weights (Thuburn et al. 2009): walk each cell of e counter-
     # clockwise starting after e; the weight of the m-th edge is
@@ -235,27 +241,24 @@ def _build(geo, cell_pos, vert_pos, cell_verts, n_on_cell):
     maxE2 = 2 * (maxE - 1)
     edgesOnEdge = -np.ones((E, maxE2), dtype=np.int64)
     weightsOnEdge = np.zeros((E, maxE2))
-    nEdgesOnEdge = np.zeros(E, dtype=np.int64)
-    pos = {}
-    for i in range(C):
-        for j in range(n_on_cell[i]):
-            pos[(i, edgesOnCell[i, j])] = j
-    for e in range(E):
-        c1, c2 = cellsOnEdge[e]
-        cnt_e = 0
-        for i, s in ((c1, -1.0), (c2, 1.0)):
-            n = n_on_cell[i]
-            j0 = pos[(i, e)]
-            racc = 0.0
-            for m in range(1, n):
-                jv = (j0 + m) % n          # vertex v_m sits at the start of edge j0+m
-                racc += kite[i, jv] / areaCell[i]
-                ep = edgesOnCell[i, (j0 + m) % n]
-                nsign = 1.0 if cellsOnEdge[ep, 0] == i else -1.0
-                edgesOnEdge[e, cnt_e] = ep
-                weightsOnEdge[e, cnt_e] = s * (racc - 0.5) * nsign
-                cnt_e += 1
-        nEdgesOnEdge[e] = cnt_e
+    ee = np.arange(E)
+    col0 = np.zeros(E, dtype=np.int64)
+    for side, sgn in ((0, -1.0), (1, 1.0)):
+        i = cellsOnEdge[:, side]
+        n = n_on_cell[i].astype(np.int64)
+        j0 = pos[:, side]
+        racc = np.zeros(E)
+        for mm in range(1, maxE):
+            ok = mm < n
+            jv = (j0 + mm) % np.maximum(n, 1)   # vertex v_m sits at the start of edge j0+m
+            racc = np.where(ok, racc + kite[i, jv] / areaCell[i], racc)
+            ep = edgesOnCell[i, jv]
+            nsign = np.where(cellsOnEdge[np.maximum(ep, 0), 0] == i, 1.0, -1.0)
+            col = col0 + mm - 1
+            edgesOnEdge[ee[ok], col[ok]] = ep[ok]
+            weightsOnEdge[ee[ok], col[ok]] = (sgn * (racc - 0.5) * nsign)[ok]
+        col0 = col0 + n - 1
+    nEdgesOnEdge = col0
 
     return dict(
         cellsOnEdge=cellsOnEdge, verticesOnEdge=verticesOnEdge, edgesOnCell=edgesOnCell,
@@ -389,3 +392,118 @@ def planar_hex(nx: int, ny: int, dc: float, *, land_rows: int = 2, depth=1000.0,
     dep = depth(cell_pos[:, 0], cell_pos[:, 1]) if callable(depth) else np.full(C, float(depth))
     name = f"planar_hex_{nx}x{ny}_dc{dc:g}"
     return _cull(full, land, cell_pos, vert_pos, fE, fV, dep, "planar", name)
+
+
+# ----------------------------------------------------------------------------
+# icosahedral geodesic sphere
+# ----------------------------------------------------------------------------
+def _icosahedron():
+    t = (1.0 + math.sqrt(5.0)) / 2.0
+    p = np.array([[-1, t, 0], [1, t, 0], [-1, -t, 0], [1, -t, 0], [0, -1, t], [0, 1, t],
+                  [0, -1, -t], [0, 1, -t], [t, 0, -1], [t, 0, 1], [-t, 0, -1], [-t, 0, 1]],
+                 dtype=F64)
+    f = np.array([[0, 11, 5], [0, 5, 1], [0, 1, 7], [0, 7, 10], [0, 10, 11], [1, 5, 9],
+                  [5, 11, 4], [11, 10, 2], [10, 7, 6], [7, 1, 8], [3, 9, 4], [3, 4, 2],
+                  [3, 2, 6], [3, 6, 8], [3, 8, 9], [4, 9, 5], [2, 4, 11], [6, 2, 10],
+                  [8, 6, 7], [9, 8, 1]], dtype=np.int64)
+    return p / np.linalg.norm(p, axis=1, keepdims=True), f
+
+
+def _orient_outward(p, f):
+    a, b, c = p[f[:, 0]], p[f[:, 1]], p[f[:, 2]]
+    out = np.sum(np.cross(b - a, c - a) * (a + b + c), axis=1) < 0
+    f = f.copy()
+    f[out] = f[out][:, [0, 2, 1]]
+    return f
+
+
+def _subdivide(p, f):
+    """Split every triangle into four; new points on the unit sphere."""
+    nP = p.shape[0]
+    e = np.concatenate([f[:, [0, 1]], f[:, [1, 2]], f[:, [2, 0]]])
+    key = np.minimum(e[:, 0], e[:, 1]) * nP + np.maximum(e[:, 0], e[:, 1])
+    uk, first, inv = np.unique(key, return_index=True, return_inverse=True)
+    mid = p[e[first, 0]] + p[e[first, 1]]
+    mid /= np.linalg.norm(mid, axis=1, keepdims=True)
+    m = nP + inv.reshape(3, -1)          # midpoint ids of (01, 12, 20) per face
+    a, b, c = f[:, 0], f[:, 1], f[:, 2]
+    m01, m12, m20 = m[0], m[1], m[2]
+    nf = np.concatenate([np.stack([a, m01, m20], 1), np.stack([b, m12, m01], 1),
+                         np.stack([c, m20, m12], 1), np.stack([m01, m12, m20], 1)])
+    return np.concatenate([p, mid]), nf
+
+
+def _largest_component(cellsOnEdge, ocean):
+    """Mask of the largest connected set of ocean cells (edges between ocean cells)."""
+    C = ocean.size
+    c1, c2 = cellsOnEdge[:, 0], cellsOnEdge[:, 1]
+    keep = ocean[c1] & ocean[c2]
+    parent = np.arange(C)
+
+    def find(x):
+        while parent[x] != x:
+            parent[x] = parent[parent[x]]
+            x = parent[x]
+        return x
+
+    for a, b in zip(c1[keep], c2[keep]):
+        ra, rb = find(a), find(b)
+        if ra != rb:
+            parent[max(ra, rb)] = min(ra, rb)
+    roots = np.array([find(i) for i in range(C)])
+    roots[~ocean] = -1
+    vals, counts = np.unique(roots[ocean], return_counts=True)
+    return roots == vals[np.argmax(counts)]
+
+
+def geodesic_sphere(level: int, *, R: float = 6.371e6, omega: float = 7.292e-5, land=None,
+                    depth=4000.0) -> Mesh:
+    """Voronoi (hexagon/pentagon) C-grid on the icosahedral geodesic grid.
+
+    Cells are the 10 * 4**level + 2 points of the recursively bisected
+    icosahedron; vertices are the circumcentres of its triangles.  Coriolis
+    f = 2 Omega sin(latitude).  ``land`` is None or a function of the unit
+    cell-centre vectors [C, 3] returning a boolean mask; only the largest
+    connected ocean basin is kept.  ``depth`` is a constant or a function of
+    the unit vectors.
+    """
+    p, f = _icosahedron()
+    f = _orient_outward(p, f)
+    for _ in range(level):
+        p, f = _subdivide(p, f)
+    C = p.shape[0]
+    a, b, c = p[f[:, 0]], p[f[:, 1]], p[f[:, 2]]
+    cc = np.cross(b - a, c - a)
+    cc /= np.linalg.norm(cc, axis=1, keepdims=True)
+    # incident triangles of each cell, counter-clockwise seen from outside
+    tri = np.repeat(np.arange(f.shape[0]), 3)
+    cel = f.ravel()
+    order = np.argsort(cel, kind="stable")
+    tri, cel = tri[order], cel[order]
+    cnt = np.bincount(cel, minlength=C)
+    assert set(np.unique(cnt)) <= {5, 6}
+    ref = np.where(np.abs(p[:, 2:3]) < 0.9, np.array([[0.0, 0.0, 1.0]]), np.array([[1.0, 0.0, 0.0]]))
+    e1 = np.cross(ref, p)
+    e1 /= np.linalg.norm(e1, axis=1, keepdims=True)
+    e2 = np.cross(p, e1)
+    d = cc[tri] - p[cel]
+    ang = np.arctan2(np.sum(d * e2[cel], 1), np.sum(d * e1[cel], 1))
+    order = np.lexsort((ang, cel))
+    tri, cel = tri[order], cel[order]
+    slot = np.arange(tri.size) - np.repeat(np.cumsum(cnt) - cnt, cnt)
+    cv = -np.ones((C, 6), dtype=np.int64)
+    cv[cel, slot] = tri
+    geo = _Sphere(R)
+    cell_pos, vert_pos = R * p, R * cc
+    full = _build(geo, cell_pos, vert_pos, cv, cnt.astype(np.int64))
+    fE = 2.0 * omega * full["xEdge"][:, 2] / R
+    fV = 2.0 * omega * cc[:, 2]
+    ocean = np.ones(C, dtype=bool)
+    if land is not None:
+        ocean = ~np.asarray(land(p), dtype=bool)
+        ocean = _largest_component(full["cellsOnEdge"], ocean)
+    dep = depth(p) if callable(depth) else np.full(C, float(depth))
+    lat = np.arcsin(np.clip(p[:, 2], -1, 1))
+    lon = np.arctan2(p[:, 1], p[:, 0])
+    return _cull(full, ~ocean, cell_pos, vert_pos, fE, fV, dep, "sphere",
+                 f"geodesic_l{level}", extra={"latCell": lat, "lonCell": lon})

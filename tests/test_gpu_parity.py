@@ -207,3 +207,108 @@ def test_tiled_subcycle_matches_global_kernel(precision, order, monkeypatch):
     tol = 1e-5 if precision == "mixed" else 1e-13
     for a, b in zip(out["tiled"], out["global"]):
         assert rel(a, b) < tol
+
+
+@pytest.mark.parametrize("order", [2, 3])
+def test_full_step_sphere(order):
+    """Icosahedral sphere at level 4 with ~30 % land, bathymetry 100-5000 m,
+    12 layers, T and S, wind stress, pentagons: 3 steps, FP64."""
+    m, L, p, (u, h, tr), run = inputs.workload("sphere_l4", perturb=True)
+    o = oracle.Oracle(m, L, p)
+    ref = o.step(order, run["dt"], run["M"], u, h, tr, n_steps=3)
+    dm, st = _gpu(m, L, p, u, h, tr)
+    st.step(order, run["dt"], run["M"], 3)
+    _compare(st.read_state(), ref, TOL64)
+
+
+def test_mixed_precision_sphere():
+    m, L, p, (u, h, tr), run = inputs.workload("sphere_l4", perturb=True)
+    o = oracle.Oracle(m, L, p)
+    ref = o.step(3, run["dt"], run["M"], u, h, tr, n_steps=6)
+    dm, st = _gpu(m, L, p, u, h, tr, "mixed")
+    d0 = st.diagnostics()
+    st.step(3, run["dt"], run["M"], 6)
+    d1 = st.diagnostics()
+    gu, gh, gt = st.read_state()
+    # the barotropic pair (ubar, zeta) is advanced in FP32 in the mixed form, so
+    # the SSH carries the velocity's relative error; under z-star every layer
+    # thickness is s_k (H + zeta), so h follows zeta
+    H = m.bottomDepth
+    errs = {"u": rel(gu, ref[0]), "zeta": rel(gh.sum(1) - H, ref[1].sum(1) - H),
+            "T": rel(gt[0], ref[2][0]), "S": rel(gt[1], ref[2][1])}
+    assert errs["u"] < 1e-4 and errs["zeta"] < 1e-4, errs
+    assert errs["T"] < 1e-6 and errs["S"] < 1e-6, errs
+    assert np.abs(gh - (gh.sum(1, keepdims=True) / L)).max() < 1e-10 * H.max()
+    assert abs(d1["volume"] - d0["volume"]) / d0["volume"] < 1e-13
+
+
+@pytest.mark.parametrize("precision", ["mixed", "fp64"])
+def test_tiled_subcycle_sphere(precision, monkeypatch):
+    """Tiled against global sub-cycle on the level-7 sphere (mixed: patches of
+    up to 3 owned entries per thread) and the level-4 sphere (FP64)."""
+    name = "sphere_l7" if precision == "mixed" else "sphere_l4"
+    m, L, p, (u, h, tr), run = inputs.workload(name, perturb=True, L=4)
+    rng = np.random.default_rng(4)
+    ubar = 0.05 * rng.standard_normal(m.nEdges)
+    G = 1e-6 * rng.standard_normal(m.nEdges)
+    out = {}
+    for kern in ("global", "tiled"):
+        if kern == "global":
+            monkeypatch.setenv("SSE_BTR_KERNEL", "global")
+        else:
+            monkeypatch.delenv("SSE_BTR_KERNEL", raising=False)
+        dm, st = _gpu(m, L, p, u, h, tr, precision)
+        st.set("ubar", ubar)
+        st.set("G", G)
+        st.barotropic_substep(3, run["dt"], run["M"])
+        out[kern] = (st.get("ubar"), st.get("Fzeta"), st.get("zeta_sub"))
+        st.close()
+        dm.close()
+    tol = 1e-5 if precision == "mixed" else 1e-13
+    for a, b in zip(out["tiled"], out["global"]):
+        assert rel(a, b) < tol
+
+
+def _pgf_rounding(m, p, h, tr):
+    """L2 norm of the rounding of the layer pressure gradient as the oracle
+    writes it, (grad p + g rho_e grad z_mid) / rho0: two terms of size
+    g |grad z| that cancel over bathymetry.  Estimated against the same
+    quantity in anomaly form, (rho_ref/rho0) g grad zeta + (grad p' +
+    g rho'_e grad z) / rho0, whose terms are ~300 times smaller."""
+    g, rho0, rref = p["g"], p["rho0"], p["eos_rho_ref"]
+    rho = rref - p["eos_alpha"] * (tr[0] - p["eos_T_ref"]) + p["eos_beta"] * (tr[1] - p["eos_S_ref"])
+    c1, c2 = m.cellsOnEdge[:, 0], m.cellsOnEdge[:, 1]
+
+    def grad(x):
+        return (x[c2] - x[c1]) / m.dcEdge[:, None]
+
+    def pres(r):
+        rh = r * h
+        return g * (np.cumsum(rh, 1) - 0.5 * rh)
+    zmid = -m.bottomDepth[:, None] + np.cumsum(h[:, ::-1], 1)[:, ::-1] - 0.5 * h
+    zeta = (h.sum(1) - m.bottomDepth)[:, None]
+    full = (grad(pres(rho)) + g * 0.5 * (rho[c1] + rho[c2]) * grad(zmid)) / rho0
+    ra = rho - rref
+    anom = rref / rho0 * g * grad(zeta) + (grad(pres(ra)) + g * 0.5 * (ra[c1] + ra[c2]) * grad(zmid)) / rho0
+    return float(np.linalg.norm(full - anom))
+
+
+@pytest.mark.slow
+def test_sphere_l7_full_size_one_step():
+    """The level-7 sphere, 60 layers, one SSPRK3-SE step, whole fields, FP64.
+
+    h and the tracers match to 1e-11.  For u the bar is the oracle's own
+    rounding: over 100-5000 m bathymetry its full-form pressure gradient
+    rounds at ~1e-16 m s^-2 while u after one step is only ~5e-4 m s^-1, so
+    the comparison allows twice the PGF rounding integrated over the three
+    stages of the step (the CUDA path uses the anomaly form)."""
+    m, L, p, (u, h, tr), run = inputs.workload("sphere_l7", perturb=True)
+    o = oracle.Oracle(m, L, p)
+    ref = o.step(run["order"], run["dt"], run["M"], u, h, tr, n_steps=1)
+    dm, st = _gpu(m, L, p, u, h, tr)
+    st.step(run["order"], run["dt"], run["M"], 1)
+    gu, gh, gt = st.read_state()
+    assert rel(gh, ref[1]) < TOL64 and rel(gt, ref[2]) < TOL64
+    bound = 2.0 * 3 * run["dt"] * _pgf_rounding(m, p, ref[1], ref[2])
+    assert np.linalg.norm(gu - ref[0]) < bound, (np.linalg.norm(gu - ref[0]), bound)
+    assert rel(gu, ref[0]) < 1e-8
