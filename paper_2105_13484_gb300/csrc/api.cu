@@ -417,11 +417,14 @@ struct Engine : EngineBase {
 
     int upload_tiles(const TilePlan &plan, int nthreads, int own, size_t smem) {
         const unsigned int sR = sizeof(R);
-        std::vector<int> noc, noe, cg, eg, c12;
+        std::vector<int> noc, noe, cg, eg, c12, nel, ncl;
         std::vector<unsigned short> eo, ce;
         std::vector<R> cf, idc, dv, Hh;
         for (const TilePatch &t : plan.patches) {
             noc.push_back(t.n_own_c); noe.push_back(t.n_own_e);
+            // sub-stage s of a sub-step needs edges of ring <= K - s and cells of
+            // ring <= K - 1 - s (K = 3): the later sub-stages skip the outer rings
+            for (int r = 2; r >= 0; r--) { nel.push_back(t.ne_ring[r]); ncl.push_back(t.nc_ring[r]); }
             cg.insert(cg.end(), t.cell_gid.begin(), t.cell_gid.end());
             eg.insert(eg.end(), t.edge_gid.begin(), t.edge_gid.end());
             for (int32_t x : t.c12) {
@@ -450,6 +453,7 @@ struct Engine : EngineBase {
         t.P = plan.P; t.nthreads = nthreads; t.own = own; t.smem = smem;
         t.cell_off = A.upload(plan.cell_off); t.edge_off = A.upload(plan.edge_off);
         t.n_own_c = A.upload(noc); t.n_own_e = A.upload(noe);
+        t.ne_lim = A.upload(nel); t.nc_lim = A.upload(ncl);
         t.cell_gid = A.upload(cg); t.edge_gid = A.upload(eg); t.c12 = A.upload(c12);
         t.eoe = A.upload(eo); t.cfc = A.upload(cf); t.invdc = A.upload(idc);
         t.ce = A.upload(ce); t.divc = A.upload(dv); t.H = A.upload(Hh);

@@ -357,6 +357,10 @@ __global__ void __launch_bounds__(TILE_THREADS, 1) k_btr_tiled(DTiles<R> t, BtrA
     const int coff = t.cell_off[p], eoff = t.edge_off[p];
     const int nc = t.cell_off[p + 1] - coff, ne = t.edge_off[p + 1] - eoff;
     const int noc = t.n_own_c[p], noe = t.n_own_e[p];
+    // sub-stage s only needs the edges and cells still exact after it (the
+    // outer rings of the halo drop out one per sub-stage)
+    const int neA = t.ne_lim[3 * p], neB = t.ne_lim[3 * p + 1], neC = t.ne_lim[3 * p + 2];
+    const int ncA = t.nc_lim[3 * p], ncB = t.nc_lim[3 * p + 1], ncC = t.nc_lim[3 * p + 2];
     const TileSmem<R> S = carve<R>(smem_raw, ne, nc);
     const R *cfc = t.cfc + (size_t)eoff * TILE_NE2P;
     const R *dvc = t.divc + (size_t)coff * TILE_NCEP;
@@ -433,13 +437,13 @@ __global__ void __launch_bounds__(TILE_THREADS, 1) k_btr_tiled(DTiles<R> t, BtrA
                 Fs[k] = wAB * f;
             }
         }
-        for (int l = noe + tid; l < ne; l += nt) {
+        for (int l = noe + tid; l < neA; l += nt) {
             R f;
             S.ua[l] = tile_fe_edge<R>(S, cfc, l, S.u0, S.z0, tau, g, f);
             S.fl[l] = f;
         }
         __syncthreads();
-        for (int l = tid; l < nc; l += nt) S.za[l] = tile_fe_cell<R>(S, dvc, l, S.z0, tau);
+        for (int l = tid; l < ncA; l += nt) S.za[l] = tile_fe_cell<R>(S, dvc, l, S.z0, tau);
         __syncthreads();
         // ---- stage b: FE(ua, za), first convex combination
 #pragma unroll
@@ -454,7 +458,7 @@ __global__ void __launch_bounds__(TILE_THREADS, 1) k_btr_tiled(DTiles<R> t, BtrA
                 else S.uh[l] = R(0.75) * S.u0[l] + R(0.25) * ub;
             }
         }
-        for (int l = noe + tid; l < ne; l += nt) {
+        for (int l = noe + tid; l < neB; l += nt) {
             R f;
             const R ub = tile_fe_edge<R>(S, cfc, l, S.ua, S.za, tau, g, f);
             S.fl[l] = f;
@@ -462,7 +466,7 @@ __global__ void __launch_bounds__(TILE_THREADS, 1) k_btr_tiled(DTiles<R> t, BtrA
             else S.uh[l] = R(0.75) * S.u0[l] + R(0.25) * ub;
         }
         __syncthreads();
-        for (int l = tid; l < nc; l += nt) {
+        for (int l = tid; l < ncB; l += nt) {
             const R zb = tile_fe_cell<R>(S, dvc, l, S.za, tau);
             if (ORDER == 2) S.z0[l] = R(0.5) * (S.z0[l] + zb);
             else S.zh[l] = R(0.75) * S.z0[l] + R(0.25) * zb;
@@ -481,14 +485,14 @@ __global__ void __launch_bounds__(TILE_THREADS, 1) k_btr_tiled(DTiles<R> t, BtrA
                     S.u0[l] = third * S.u0[l] + two_thirds * uc;
                 }
             }
-            for (int l = noe + tid; l < ne; l += nt) {
+            for (int l = noe + tid; l < neC; l += nt) {
                 R f;
                 const R uc = tile_fe_edge<R>(S, cfc, l, S.uh, S.zh, tau, g, f);
                 S.fl[l] = f;
                 S.u0[l] = third * S.u0[l] + two_thirds * uc;
             }
             __syncthreads();
-            for (int l = tid; l < nc; l += nt) {
+            for (int l = tid; l < ncC; l += nt) {
                 const R zc = tile_fe_cell<R>(S, dvc, l, S.zh, tau);
                 S.z0[l] = third * S.z0[l] + two_thirds * zc;
             }

@@ -135,6 +135,7 @@ template <class R> struct DTiles {
     int P, nthreads, own;            // patches, threads per patch, entries per thread
     const int *cell_off, *edge_off;  // [P + 1]
     const int *n_own_c, *n_own_e;    // [P]
+    const int *ne_lim, *nc_lim;      // [P][3] local edges / cells exact after 0, 1, 2 sub-stages
     const int *cell_gid, *edge_gid;  // local -> global
     const int *c12;                  // [sum ne] byte offsets of local (c1, c2): c1 | c2 << 16
     const unsigned short *eoe;       // [sum ne][TILE_NE2P] byte offsets of local edgesOnEdge

@@ -130,8 +130,16 @@ bool build_tile_plan(const HostMesh &hm, int P, int K, TilePlan &plan) {
                 le[e] = 0;
                 (owner[hm.c1[e]] == p ? Eo : Eh).push_back(e);
             }
+        // ring of an edge: the larger ring of its cells (outside the patch: K+1)
+        auto ering = [&](int e) {
+            const int a = dist[hm.c1[e]], b = dist[hm.c2[e]];
+            return std::max(a == INT_MAX ? K + 1 : a, b == INT_MAX ? K + 1 : b);
+        };
         std::sort(Eo.begin(), Eo.end());
-        std::sort(Eh.begin(), Eh.end());
+        std::sort(Eh.begin(), Eh.end(), [&](int a, int b) {
+            const int ra = ering(a), rb = ering(b);
+            return ra != rb ? ra < rb : a < b;
+        });
         std::vector<int> Ed = Eo;
         Ed.insert(Ed.end(), Eh.begin(), Eh.end());
         const int ne = (int)Ed.size();
@@ -182,6 +190,15 @@ bool build_tile_plan(const HostMesh &hm, int P, int K, TilePlan &plan) {
             }
         }
         tp.H[nc] = 1.0;  // dummy cell: finite depth
+        // prefix counts by ring (owned edges have ring 0 or 1)
+        for (int r = 0; r < 3; r++) {
+            int n = tp.n_own_e;
+            for (int e : Eh) n += ering(e) <= r + 1;
+            tp.ne_ring[r] = n;
+            int c = 0;
+            for (int x : X) c += dist[x] <= r;
+            tp.nc_ring[r] = c;
+        }
         plan.patches.push_back(std::move(tp));
         plan.cell_off.push_back(plan.cell_off.back() + nc);
         plan.edge_off.push_back(plan.edge_off.back() + ne);

@@ -35,6 +35,10 @@ struct TilePatch {
     std::vector<int16_t> ce;               // [nc][maxE] local edges (dummy = ne)
     std::vector<double> divc;              // [nc][maxE]
     std::vector<double> H;                 // [nc + 1]
+    // prefix counts by halo ring: local edges with ring <= r+1 (r = 0..2; an
+    // edge's ring is the larger ring of its two cells, cells outside the patch
+    // count K+1) and local cells with ring <= r (r = 0..2)
+    int ne_ring[3] = {0, 0, 0}, nc_ring[3] = {0, 0, 0};
 };
 
 struct TilePlan {
@@ -44,7 +48,8 @@ struct TilePlan {
 };
 
 // Partition into P patches with halos of K rings; false if a patch would
-// need more than 32766 local entries.
+// need more than 32766 local entries.  Local order: owned cells, then halo
+// cells by ring; owned edges (first cell owned), then halo edges by ring.
 bool build_tile_plan(const HostMesh &hm, int P, int K, TilePlan &plan);
 // Dynamic shared memory of the largest patch for element size sR.
 size_t tile_smem_bytes(const TilePlan &plan, int maxE, int maxE2, size_t sR);
