@@ -207,11 +207,10 @@ def replica_throughput(units_per_rank, world, max_ms):
     return world * units_per_rank / (max_ms / 1e3)
 
 
-def build_workload(seed=0, scale=None, name=WORKLOAD):
+def build_workload(seed=0, scale=None, name=WORKLOAD, **over):
     from paper_2105_13484_gb300 import inputs
-    over = {}
     if scale is not None:
-        over = dict(nx=scale[0], ny=scale[1])
+        over = dict(over, nx=scale[0], ny=scale[1])
     m, L, p, st, run = inputs.workload(name, seed=seed, perturb=True, **over)
     return m, L, p, st, run
 
@@ -356,9 +355,9 @@ def step_roofline_of(m, L, nT, mixed, ms_per_step):
 
 
 def measure_workload(torch, binding, name, forms_todo, headline, steps, warmup, rank, stream,
-                     flush, sampler=None, e2e=True, world=1, dist=None):
+                     flush, sampler=None, e2e=True, world=1, dist=None, **over):
     """Every requested precision form of one named workload on this GPU."""
-    m, L, p, state0, run = build_workload(seed=rank, name=name)
+    m, L, p, state0, run = build_workload(seed=rank, name=name, **over)
     nT = int(p.get("nTracers", 1))
     dm = binding.Mesh(m, L)
     forms = {}
@@ -460,6 +459,18 @@ def run_ours(args):
             "config": config_of("sphere_l7", s7, "mixed", world), "roofline": s7["roofline"],
             "step_roofline": s7["step_roofline"], "kernels": s7["kernels"],
             "volume_rel_change": s7["forms_summary"]["mixed"]["volume_rel_change"]}
+
+    if args.workload == WORKLOAD and not args.no_sphere:
+        # the same channel with Algorithm 2 (implicit vertical mixing) in every stage
+        vm = measure_workload(torch, binding, WORKLOAD, ("mixed",), "mixed", args.steps,
+                              args.warmup, rank, stream, flush, None, False, world, dist,
+                              vmix=True)
+        also["channel_1km_vmix"] = {
+            "value": vm["value"], "unit": METRIC, "steps": args.steps,
+            "ms_per_step": vm["t_max"] / args.steps, "latency_ms": vm["head"]["latency_ms"],
+            "config": dict(config_of(WORKLOAD, vm, "mixed", world), baroclinic="Algorithm 2"),
+            "kernels": vm["kernels"],
+            "volume_rel_change": vm["forms_summary"]["mixed"]["volume_rel_change"]}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:

@@ -99,13 +99,20 @@ typedef struct {
     const double *restThicknessFrac; /* [nLayers] z-star fractions, sum 1  */
 } sse_mesh_desc;
 
+/* SSE_OPT_VMIX: every baroclinic stage uses Algorithm 2
+ * (Baroclinic_FEuler_Mixing) instead of Algorithm 1: D^u leaves the explicit
+ * tendency and (I - dt D^u) u1 = ut1 + ubar is solved down every edge column
+ * (tridiagonal), wind stress explicit at the top, bottom drag linearised about
+ * the speed of the stage's input velocity; then ut1 = u1 - ubar. */
+#define SSE_OPT_VMIX 1
+
 /* Physics and numerics.  Linear equation of state (Eq. eqstate):
  *   rho = eos_rho_ref - eos_alpha (T - eos_T_ref) + eos_beta (S - eos_S_ref). */
 typedef struct {
     int32_t precision;  /* SSE_FP64 or SSE_MIXED                             */
     int32_t recon;      /* SSE_RECON_*                                        */
     int32_t nTracers;   /* 1 (T) or 2 (T, S)                                  */
-    int32_t reserved;   /* must be 0                                          */
+    int32_t options;    /* bit set of SSE_OPT_* (other bits: SSE_ERR_INVALID_ARG) */
     double g, rho0;     /* gravity (m s^-2), reference density (kg m^-3)      */
     double nu_h, nu_v;  /* horizontal / vertical viscosity (m^2 s^-1)         */
     double kappa_h, kappa_v; /* tracer diffusivities (m^2 s^-1)               */

@@ -51,7 +51,7 @@ class _Params(ct.Structure):
     _fields_ = [("nTracers", ct.c_int), ("recon", ct.c_int)] + [
         (n, ct.c_double) for n in ("g", "rho0", "nu_h", "nu_v", "kappa_h", "kappa_v", "c_drag",
                                    "eos_rho_ref", "eos_alpha", "eos_beta", "eos_T_ref",
-                                   "eos_S_ref")] + [("windStress", _dp)]
+                                   "eos_S_ref")] + [("windStress", _dp), ("vmix", ct.c_int)]
 
 
 class _Aux(ct.Structure):
@@ -63,7 +63,7 @@ RECON = {"off": 0, "paper": 1, "consistent": 2}
 
 DEFAULT_PARAMS = dict(nTracers=1, recon="consistent", g=9.80616, rho0=1000.0, nu_h=0.0, nu_v=0.0,
                       kappa_h=0.0, kappa_v=0.0, c_drag=0.0, eos_rho_ref=1000.0, eos_alpha=0.2,
-                      eos_beta=0.8, eos_T_ref=10.0, eos_S_ref=35.0, windStress=None)
+                      eos_beta=0.8, eos_T_ref=10.0, eos_S_ref=35.0, windStress=None, vmix=0)
 
 
 def _d(a):
@@ -119,7 +119,7 @@ class Oracle:
             wsp = None
         self.p = _Params(self.nT, recon, *[float(q[n]) for n in (
             "g", "rho0", "nu_h", "nu_v", "kappa_h", "kappa_v", "c_drag", "eos_rho_ref",
-            "eos_alpha", "eos_beta", "eos_T_ref", "eos_S_ref")], wsp)
+            "eos_alpha", "eos_beta", "eos_T_ref", "eos_S_ref")], wsp, int(bool(q.get("vmix", 0))))
 
     def _sig(self):
         L = self.lib
@@ -237,6 +237,24 @@ class Oracle:
         G = np.zeros(self.E)
         self.lib.om_baroclinic_feuler(ct.byref(self.m), ct.byref(self.p), _d(u), _d(ut),
                                       _d(zeta), _d(h), _d(tr), ct.c_double(dt), _d(ut1), _d(G))
+        return ut1, G
+
+    def vertical_mixing_solve(self, u_drag, h, r, dt):
+        """(I - dt D^u) x = r per edge column (the solve of Algorithm 2)."""
+        u_drag, h, r = map(self._f, (u_drag, h, r))
+        x = np.zeros((self.E, self.L))
+        self.lib.om_vertical_mixing_solve(ct.byref(self.m), ct.byref(self.p), _d(u_drag), _d(h),
+                                          _d(r), ct.c_double(dt), _d(x))
+        return x
+
+    def baroclinic_feuler_mixing(self, u, ut, ubar, zeta, h, tr, dt):
+        """Algorithm 2: returns (ut1 [E, L], G [E])."""
+        u, ut, ubar, zeta, h, tr = map(self._f, (u, ut, ubar, zeta, h, tr))
+        ut1 = np.zeros((self.E, self.L))
+        G = np.zeros(self.E)
+        self.lib.om_baroclinic_feuler_mixing(ct.byref(self.m), ct.byref(self.p), _d(u), _d(ut),
+                                             _d(ubar), _d(zeta), _d(h), _d(tr), ct.c_double(dt),
+                                             _d(ut1), _d(G))
         return ut1, G
 
     def barotropic_fe(self, ubar, zeta, G, tau):

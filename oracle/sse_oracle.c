@@ -297,8 +297,19 @@ void om_split(const om_mesh *m, const double *u, const double *h, double *ubar, 
  *   D^u = D_zm(nu_v D_zt u) with wind stress tau/rho0 at the surface and
  *                           bottom drag c_drag |u| u at the bottom (Sec. 5)
  */
+static void baroclinic_rhs(const om_mesh *m, const om_params *p, const double *u,
+                           const double *ut, const double *zeta, const double *h,
+                           const double *tr, double *rhs, int with_vvisc);
+
 void om_baroclinic_rhs(const om_mesh *m, const om_params *p, const double *u, const double *ut,
                        const double *zeta, const double *h, const double *tr, double *rhs) {
+    baroclinic_rhs(m, p, u, ut, zeta, h, tr, rhs, 1);
+}
+
+/* with_vvisc = 0 leaves out D^u (Algorithm 2 treats it implicitly) */
+static void baroclinic_rhs(const om_mesh *m, const om_params *p, const double *u,
+                           const double *ut, const double *zeta, const double *h,
+                           const double *tr, double *rhs, int with_vvisc) {
     int L = m->nLayers;
     size_t EL = (size_t)m->nEdges * L, CL = (size_t)m->nCells * L;
     double *Q = vec(EL), *Cu = vec(EL), *Cut = vec(EL), *K = vec(CL), *gK = vec(EL);
@@ -349,7 +360,7 @@ void om_baroclinic_rhs(const om_mesh *m, const om_params *p, const double *u, co
             } else {
                 Xbot = p->nu_v * Dk1;
             }
-            double vvisc = (Xtop - Xbot) / hee[k];
+            double vvisc = with_vvisc ? (Xtop - Xbot) / hee[k] : 0.0;
             double rho_e = 0.5 * (rho[(size_t)c1 * L + k] + rho[(size_t)c2 * L + k]);
             double pgf = (gp[x] + p->g * rho_e * gz[x]) / p->rho0;
             rhs[x] = Cut[x] + (Q[x] - Cu[x]) - gK[x] - pgf - vadv + p->nu_h * lap[x] + vvisc +
@@ -381,6 +392,98 @@ void om_baroclinic_feuler(const om_mesh *m, const om_params *p, const double *u,
     }
     free(rhs);
     free(he);
+}
+
+/* Implicit vertical diffusion, the solve of Algorithm 2:
+ *   x_k - dt D^u(x)_k = r_k,  D^u(x)_k = (X_k - X_{k+1}) / h_e,k,
+ *   X_k = nu_v (x_{k-1} - x_k) / ((h_e,k-1 + h_e,k)/2) at interior interfaces,
+ *   X_0 = tau_e / rho0 (wind stress, known), X_L = c_drag |u_drag| x_{L-1}
+ * (bottom drag with the speed of u_drag, |u| = sqrt(u^2 + u_t^2) of the
+ * bottom layer).  One tridiagonal system per edge column, solved by forward
+ * elimination and back substitution (Thomas algorithm). */
+void om_vertical_mixing_solve(const om_mesh *m, const om_params *p, const double *u_drag,
+                              const double *h, const double *r, double dt, double *x) {
+    int L = m->nLayers;
+    size_t EL = (size_t)m->nEdges * L;
+    double *he = vec(EL), *utan = vec(EL);
+    double *lo = vec(L), *di = vec(L), *up = vec(L), *rr = vec(L), *cp = vec(L), *dp = vec(L);
+    om_edge_thickness(m, L, h, he);
+    om_tangential(m, L, u_drag, utan);
+    for (int e = 0; e < m->nEdges; e++) {
+        const double *hk = he + (size_t)e * L;
+        /* the matrix: lo_k x_{k-1} + di_k x_k + up_k x_{k+1} = rr_k */
+        for (int k = 0; k < L; k++) {
+            double a = 0.0, c = 0.0;
+            if (k >= 1) a = dt * p->nu_v / (hk[k] * 0.5 * (hk[k - 1] + hk[k]));
+            if (k + 1 <= L - 1) c = dt * p->nu_v / (hk[k] * 0.5 * (hk[k] + hk[k + 1]));
+            lo[k] = -a;
+            up[k] = -c;
+            di[k] = 1.0 + a + c;
+            rr[k] = r[(size_t)e * L + k];
+        }
+        if (p->windStress) rr[0] += dt * p->windStress[e] / p->rho0 / hk[0];
+        {
+            size_t xb = (size_t)e * L + (L - 1);
+            double speed = sqrt(u_drag[xb] * u_drag[xb] + utan[xb] * utan[xb]);
+            di[L - 1] += dt * p->c_drag * speed / hk[L - 1];
+        }
+        /* forward elimination */
+        cp[0] = up[0] / di[0];
+        dp[0] = rr[0] / di[0];
+        for (int k = 1; k < L; k++) {
+            double den = di[k] - lo[k] * cp[k - 1];
+            cp[k] = up[k] / den;
+            dp[k] = (rr[k] - lo[k] * dp[k - 1]) / den;
+        }
+        /* back substitution */
+        x[(size_t)e * L + L - 1] = dp[L - 1];
+        for (int k = L - 2; k >= 0; k--)
+            x[(size_t)e * L + k] = dp[k] - cp[k] * x[(size_t)e * L + k + 1];
+    }
+    free(he); free(utan); free(lo); free(di); free(up); free(rr); free(cp); free(dp);
+}
+
+/* Algorithm 2, Baroclinic_FEuler_Mixing(u, ut, ubar, zeta, h, dt) -> (ut1, G):
+ * the explicit stage of Algorithm 1 without D^u, G from it, then the
+ * vertical diffusion solve on the whole velocity ut1 + ubar, and ut1 = u1 -
+ * ubar (ubar: the stage's input barotropic velocity). */
+void om_baroclinic_feuler_mixing(const om_mesh *m, const om_params *p, const double *u,
+                                 const double *ut, const double *ubar, const double *zeta,
+                                 const double *h, const double *tr, double dt, double *ut1,
+                                 double *G) {
+    int L = m->nLayers;
+    size_t EL = (size_t)m->nEdges * L;
+    double *rhs = vec(EL), *he = vec(EL), *r = vec(EL), *u1 = vec(EL);
+    baroclinic_rhs(m, p, u, ut, zeta, h, tr, rhs, 0);
+    om_edge_thickness(m, L, h, he);
+    for (size_t x = 0; x < EL; x++) ut1[x] = ut[x] + dt * rhs[x];
+    for (int e = 0; e < m->nEdges; e++) {
+        double num = 0.0, den = 0.0;
+        for (int k = 0; k < L; k++) {
+            num += he[(size_t)e * L + k] * ut1[(size_t)e * L + k];
+            den += he[(size_t)e * L + k];
+        }
+        G[e] = num / den / dt;
+        for (int k = 0; k < L; k++) {
+            ut1[(size_t)e * L + k] -= dt * G[e];
+            r[(size_t)e * L + k] = ut1[(size_t)e * L + k] + ubar[e];
+        }
+    }
+    om_vertical_mixing_solve(m, p, u, h, r, dt, u1);
+    for (int e = 0; e < m->nEdges; e++)
+        for (int k = 0; k < L; k++)
+            ut1[(size_t)e * L + k] = u1[(size_t)e * L + k] - ubar[e];
+    free(rhs); free(he); free(r); free(u1);
+}
+
+/* the baroclinic stage of the step: Algorithm 1, or Algorithm 2 when mixing */
+static void bcl_stage(const om_mesh *m, const om_params *p, const double *u, const double *ut,
+                      const double *ubar, const double *zeta, const double *h, const double *tr,
+                      double dt, double *ut1, double *G) {
+    if (p->vmix)
+        om_baroclinic_feuler_mixing(m, p, u, ut, ubar, zeta, h, tr, dt, ut1, G);
+    else
+        om_baroclinic_feuler(m, p, u, ut, zeta, h, tr, dt, ut1, G);
 }
 
 /* One forward-Euler stage of the barotropic mode, Eq. (eqtropic):
@@ -586,7 +689,7 @@ int om_sse_step(const om_mesh *m, const om_params *p, int order, double dt, int 
 
     if (order == 2) {
         /* Stage 1 of SSPRK2-SE */
-        om_baroclinic_feuler(m, p, u, ut_n, zeta_n, h, tr, dt, ut1, G0);
+        bcl_stage(m, p, u, ut_n, ubar_n, zeta_n, h, tr, dt, ut1, G0);
         om_barotropic_substep(m, p, 2, ubar_n, zeta_n, G0, dt, M, ubar1, Fz1, NULL);
         for (int e = 0; e < E; e++)
             for (int k = 0; k < L; k++) u1[(size_t)e * L + k] = ubar1[e] + ut1[(size_t)e * L + k];
@@ -596,7 +699,7 @@ int om_sse_step(const om_mesh *m, const om_params *p, int order, double dt, int 
         om_thickness_tracer_fe(m, p, h, tr, v, dt, h1, tr1);
         om_ssh(m, h1, zeta1);
         /* Stage 2 (baroclinic) */
-        om_baroclinic_feuler(m, p, u1, ut1, zeta1, h1, tr1, dt, ut2, G1);
+        bcl_stage(m, p, u1, ut1, ubar1, zeta1, h1, tr1, dt, ut2, G1);
         comb(EL, 0.5, ut_n, 0.5, ut2, utn1);
         /* Step 2: corrector with Interp_2(G0, G1), Eq. (force2) */
         comb(E, 0.5, G0, 0.5, G1, Gi);
@@ -625,7 +728,7 @@ int om_sse_step(const om_mesh *m, const om_params *p, int order, double dt, int 
         }
     } else {
         /* Stage 1 of SSPRK3-SE */
-        om_baroclinic_feuler(m, p, u, ut_n, zeta_n, h, tr, dt, ut1, G0);
+        bcl_stage(m, p, u, ut_n, ubar_n, zeta_n, h, tr, dt, ut1, G0);
         om_barotropic_substep(m, p, 3, ubar_n, zeta_n, G0, dt, M, ubar1, Fz1, NULL);
         for (int e = 0; e < E; e++)
             for (int k = 0; k < L; k++) u1[(size_t)e * L + k] = ubar1[e] + ut1[(size_t)e * L + k];
@@ -635,7 +738,7 @@ int om_sse_step(const om_mesh *m, const om_params *p, int order, double dt, int 
         om_thickness_tracer_fe(m, p, h, tr, v, dt, h1, tr1);
         om_ssh(m, h1, zeta1);
         /* Stage 2 */
-        om_baroclinic_feuler(m, p, u1, ut1, zeta1, h1, tr1, dt, ut2, G1);
+        bcl_stage(m, p, u1, ut1, ubar1, zeta1, h1, tr1, dt, ut2, G1);
         comb(EL, 0.75, ut_n, 0.25, ut2, uth);
         om_barotropic_substep(m, p, 3, ubar1, zeta1, G1, dt, M, ubar2, Fz2, NULL);
         comb(E, 0.75, ubar_n, 0.25, ubar2, ubarh);
@@ -649,7 +752,7 @@ int om_sse_step(const om_mesh *m, const om_params *p, int order, double dt, int 
         comb_tracer(CL, nT, 0.75, h, tr, 0.25, h2, tr2, hh, trh);
         om_ssh(m, hh, zetah);
         /* Stage 3 (baroclinic) */
-        om_baroclinic_feuler(m, p, uh, uth, zetah, hh, trh, dt, ut3, G2);
+        bcl_stage(m, p, uh, uth, ubarh, zetah, hh, trh, dt, ut3, G2);
         comb(EL, 1.0 / 3.0, ut_n, 2.0 / 3.0, ut3, utn1);
         /* Step 2: corrector with Interp_3(G0, G1, G_{1/2}), Eq. (force3) */
         for (int e = 0; e < E; e++) Gi[e] = G0[e] / 6.0 + G1[e] / 6.0 + 2.0 * G2[e] / 3.0;

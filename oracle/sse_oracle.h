@@ -43,6 +43,7 @@ typedef struct {
     double g, rho0, nu_h, nu_v, kappa_h, kappa_v, c_drag;
     double eos_rho_ref, eos_alpha, eos_beta, eos_T_ref, eos_S_ref;
     const double *windStress; /* [E] normal wind stress (N m^-2) or NULL */
+    int vmix;              /* 1: Algorithm 2 (implicit vertical mixing) in every stage */
 } om_params;
 
 /* optional per-step records for the tests (NULL members are skipped) */
@@ -78,6 +79,15 @@ void om_baroclinic_rhs(const om_mesh *m, const om_params *p, const double *u, co
 void om_baroclinic_feuler(const om_mesh *m, const om_params *p, const double *u,
                           const double *ut, const double *zeta, const double *h,
                           const double *tr, double dt, double *ut1, double *G);
+/* implicit vertical diffusion (I - dt D^u) x = r per edge column, D^u with the
+ * wind stress at the surface (explicit) and the bottom drag linearised about
+ * the speed of u_drag (implicit) */
+void om_vertical_mixing_solve(const om_mesh *m, const om_params *p, const double *u_drag,
+                              const double *h, const double *r, double dt, double *x);
+void om_baroclinic_feuler_mixing(const om_mesh *m, const om_params *p, const double *u,
+                                 const double *ut, const double *ubar, const double *zeta,
+                                 const double *h, const double *tr, double dt, double *ut1,
+                                 double *G);
 void om_barotropic_fe(const om_mesh *m, const om_params *p, const double *ubar,
                       const double *zeta, const double *G, double tau, double *ubar1,
                       double *zeta1, double *flux);

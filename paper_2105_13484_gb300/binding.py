@@ -18,6 +18,7 @@ SSE_OK = 0
 ERRORS = {-1: "INVALID_ARG", -2: "BAD_MESH", -3: "OOM", -4: "CUDA", -5: "NONFINITE",
           -6: "SYNC_TIMEOUT", -7: "UNSUPPORTED"}
 FP64, MIXED = 0, 1
+OPT_VMIX = 1          # SSE_OPT_VMIX: Algorithm 2 (implicit vertical mixing)
 RECON = {"off": 0, "paper": 1, "consistent": 2}
 FIELD = {"u": 0, "h": 1, "tracer0": 2, "tracer1": 3, "wind": 4, "zeta": 5, "ubar": 6,
          "utilde": 7, "G": 8, "Fzeta": 9, "zeta_sub": 10}
@@ -45,7 +46,7 @@ class MeshDesc(ct.Structure):
 
 class Params(ct.Structure):
     _fields_ = [("precision", ct.c_int32), ("recon", ct.c_int32), ("nTracers", ct.c_int32),
-                ("reserved", ct.c_int32)] + [
+                ("options", ct.c_int32)] + [
         (n, ct.c_double) for n in ("g", "rho0", "nu_h", "nu_v", "kappa_h", "kappa_v", "c_drag",
                                    "eos_rho_ref", "eos_alpha", "eos_beta", "eos_T_ref",
                                    "eos_S_ref")]
@@ -174,7 +175,8 @@ def make_params(params: dict, precision="fp64") -> Params:
     recon = RECON[recon] if isinstance(recon, str) else int(recon)
     prec = {"fp64": FP64, "mixed": MIXED}[precision] if isinstance(precision, str) else int(
         precision)
-    return Params(prec, recon, int(q.get("nTracers", 1)), 0, *[float(q.get(n, d)) for n, d in (
+    options = OPT_VMIX if q.get("vmix") else 0
+    return Params(prec, recon, int(q.get("nTracers", 1)), options, *[float(q.get(n, d)) for n, d in (
         ("g", 9.80616), ("rho0", 1000.0), ("nu_h", 0.0), ("nu_v", 0.0), ("kappa_h", 0.0),
         ("kappa_v", 0.0), ("c_drag", 0.0), ("eos_rho_ref", 1000.0), ("eos_alpha", 0.2),
         ("eos_beta", 0.8), ("eos_T_ref", 10.0), ("eos_S_ref", 35.0))])

@@ -319,6 +319,7 @@ struct Engine : EngineBase {
     DParams p{};
     int recon = SSE_RECON_CONSISTENT;
     bool mixed = false;
+    bool vmix = false;   // Algorithm 2 in every baroclinic stage
     cudaStream_t s = nullptr;
     DevArena A;
     // state
@@ -472,6 +473,7 @@ struct Engine : EngineBase {
         ps = st;
         mixed = (prm->precision == SSE_MIXED);
         recon = prm->recon;
+        vmix = (prm->options & SSE_OPT_VMIX) != 0;
         p.g = prm->g; p.rho0 = prm->rho0; p.nu_h = prm->nu_h; p.nu_v = prm->nu_v;
         p.kappa_h = prm->kappa_h; p.kappa_v = prm->kappa_v; p.c_drag = prm->c_drag;
         p.alpha = prm->eos_alpha; p.beta = prm->eos_beta; p.T_ref = prm->eos_T_ref;
@@ -677,7 +679,10 @@ struct Engine : EngineBase {
         launch_edge_pre<R>(m, ubar, ut, hR, db, split, s);
         pend();
         pbeg(SSE_K_BCL_EDGE);
-        launch_bcl_edge<R>(m, p, ubar, ut, hR, zeta, db, utn, a, b, dt, out, G, s);
+        // Algorithm 2 keeps its modified super-diagonal in `flux`, which is
+        // free until the stage's transport kernel writes it
+        launch_bcl_edge<R>(m, p, ubar, ut, hR, zeta, db, utn, a, b, dt, out, G,
+                           vmix ? flux : nullptr, s);
         pend();
     }
 
@@ -841,7 +846,7 @@ extern "C" int sse_state_create(const sse_mesh *mesh, const sse_params *prm, voi
     if (!mesh || !prm || !out) return SSE_ERR_INVALID_ARG;
     *out = nullptr;
     if ((prm->precision != SSE_FP64 && prm->precision != SSE_MIXED) || prm->recon < 0 ||
-        prm->recon > 2 || prm->nTracers < 1 || prm->nTracers > 2 || prm->reserved != 0 ||
+        prm->recon > 2 || prm->nTracers < 1 || prm->nTracers > 2 || (prm->options & ~SSE_OPT_VMIX) != 0 ||
         !(prm->g > 0) || !(prm->rho0 > 0) || !(prm->nu_h >= 0) || !(prm->nu_v >= 0) ||
         !(prm->kappa_h >= 0) || !(prm->kappa_v >= 0) || !(prm->c_drag >= 0) ||
         !isfinite(prm->eos_rho_ref) || !isfinite(prm->eos_alpha) || !isfinite(prm->eos_beta) ||

@@ -106,7 +106,8 @@ void launch_edge_pre(const DMesh &m, R *ubar, R *ut, const R *hR, const DiagBufs
 template <class R>
 void launch_bcl_edge(const DMesh &m, const DParams &p, const R *ubar, const R *ut,
                      const R *hR, const double *zeta, const DiagBufs<R> &b, const R *ut_n,
-                     double a, double bcoef, double dt, R *ut_out, R *G, cudaStream_t s);
+                     double a, double bcoef, double dt, R *ut_out, R *G, R *vmc,
+                     cudaStream_t s);
 
 template <class R> struct BtrArgs {
     const R *ub_start;     // [Ep]

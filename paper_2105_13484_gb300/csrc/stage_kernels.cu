@@ -178,13 +178,19 @@ __global__ void __launch_bounds__(128) k_edge_pre(DMesh m, R *__restrict__ ubar,
 // + g rho'_e grad z, so -PGF + g grad zeta = g (1 - rho_ref/rho0) grad zeta
 // - (grad p' + g rho'_e grad z) / rho0.
 // ---------------------------------------------------------------------------
-template <class R, int NE2>
+// VMIX = false: Algorithm 1.  VMIX = true: Algorithm 2 -- the explicit stage
+// without D^u, G, then (I - dt D^u) u1 = ut1 + ubar solved down each edge
+// column (Thomas; the modified super-diagonal goes to the scratch vmc), with
+// the wind explicit at the top and the bottom drag linearised about the speed
+// of the stage's input velocity; ut1 = u1 - ubar.
+template <class R, int NE2, bool VMIX>
 __global__ void __launch_bounds__(128, 8) k_bcl_edge(DMesh m, DParams p, const R *__restrict__ ubar,
                                                   const R *__restrict__ ut,
                                                   const R *__restrict__ hR,
                                                   const double *__restrict__ zeta, DiagBufs<R> b,
                                                   const R *__restrict__ ut_n, R a, R bc, R dt,
-                                                  R *__restrict__ ut_out, R *__restrict__ Gout) {
+                                                  R *__restrict__ ut_out, R *__restrict__ Gout,
+                                                  R *__restrict__ vmc) {
     const int e = blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= m.E) return;
     const Coef<R> &c = coef<R>(m);
@@ -218,7 +224,7 @@ __global__ void __launch_bounds__(128, 8) k_bcl_edge(DMesh m, DParams p, const R
     R u_cur = ub + ut_cur;
     R he_cur = R(0.5) * (ld(hR + c1) + ld(hR + c2));
     R u_prev = R(0), he_prev = R(0);
-    R num = R(0), den = R(0);
+    R num = R(0), den = R(0), speed_b = R(0);
     for (int k = 0; k < L; k++) {
         const int xe = k * Ep + e;
         R ut_next = R(0), u_next = R(0), he_next = R(0);
@@ -256,12 +262,12 @@ __global__ void __launch_bounds__(128, 8) k_bcl_edge(DMesh m, DParams p, const R
 #pragma unroll
             for (int j = 0; j < NE2; j++)
                 if (j < n2) utan += wl[j] * (ld(ubar + eo[j]) + ut[k * Ep + eo[j]]);
-            const R speed = sqrt(u_cur * u_cur + utan * utan);
-            Xbot = cdrag * speed * u_cur;
+            speed_b = sqrt(u_cur * u_cur + utan * utan);
+            Xbot = cdrag * speed_b * u_cur;
         } else {
             Xbot = nu_v * Dk1;
         }
-        const R vvisc = (Xtop - Xbot) / he_cur;
+        const R vvisc = VMIX ? R(0) : (Xtop - Xbot) / he_cur;
         const R lap = (b.delta[x2] - b.delta[x1]) * invdc -
                       (b.omega[k * Vp + v2] - b.omega[k * Vp + v1]) * invdv;
         const R rhs = (Q - cbar) - gradK - pgf - vadv + nu_h * lap + vvisc + gzeta;
@@ -274,10 +280,45 @@ __global__ void __launch_bounds__(128, 8) k_bcl_edge(DMesh m, DParams p, const R
     }
     const R G = num / den / dt;
     Gout[e] = G;
+    if (!VMIX) {
+        for (int k = 0; k < L; k++) {
+            const int xe = k * Ep + e;
+            const R x = ut_out[xe] - dt * G;
+            ut_out[xe] = ut_n ? a * ut_n[xe] + bc * x : bc * x;
+        }
+        return;
+    }
+    // forward elimination down the column: row k is
+    //   -lo x_{k-1} + (1 + lo + up [+ dt c_d |u| / h]) x_k - up x_{k+1} = r_k
+    R cprev = R(0), dprev = R(0), hprev = R(0);
+    R hk = R(0.5) * (ld(hR + c1) + ld(hR + c2));
     for (int k = 0; k < L; k++) {
         const int xe = k * Ep + e;
-        const R x = ut_out[xe] - dt * G;
-        ut_out[xe] = ut_n ? a * ut_n[xe] + bc * x : bc * x;
+        const R hnext = (k + 1 < L)
+            ? R(0.5) * (ld(hR + (k + 1) * Cp + c1) + ld(hR + (k + 1) * Cp + c2)) : R(0);
+        const R lo = (k > 0) ? dt * nu_v / (hk * (R(0.5) * (hprev + hk))) : R(0);
+        const R up = (k + 1 < L) ? dt * nu_v / (hk * (R(0.5) * (hk + hnext))) : R(0);
+        R di = R(1) + lo + up;
+        if (k == L - 1) di += dt * cdrag * speed_b / hk;
+        R r = ut_out[xe] - dt * G + ub;
+        if (k == 0) r += dt * wind / hk;
+        // sub-diagonal -lo, super-diagonal -up: pivot di - (-lo) c'_{k-1}
+        const R dn = di + lo * cprev;
+        cprev = -up / dn;
+        dprev = (r + lo * dprev) / dn;
+        vmc[xe] = cprev;
+        ut_out[xe] = dprev;
+        hprev = hk;
+        hk = hnext;
+    }
+    // back substitution up the column, then the convex combination
+    R xnext = R(0);
+    for (int k = L - 1; k >= 0; k--) {
+        const int xe = k * Ep + e;
+        const R x = ut_out[xe] - vmc[xe] * xnext;
+        xnext = x;
+        const R u1 = x - ub;
+        ut_out[xe] = ut_n ? a * ut_n[xe] + bc * u1 : bc * u1;
     }
 }
 
@@ -574,13 +615,24 @@ void launch_edge_pre(const DMesh &m, R *ubar, R *ut, const R *hR, const DiagBufs
 template <class R>
 void launch_bcl_edge(const DMesh &m, const DParams &p, const R *ubar, const R *ut, const R *hR,
                      const double *zeta, const DiagBufs<R> &b, const R *ut_n, double a,
-                     double bcoef, double dt, R *ut_out, R *G, cudaStream_t s) {
-    if (m.maxE2 <= 10)
-        k_bcl_edge<R, 10><<<nblk(m.E, 128), 128, 0, s>>>(m, p, ubar, ut, hR, zeta, b, ut_n, (R)a,
-                                                         (R)bcoef, (R)dt, ut_out, G);
-    else
-        k_bcl_edge<R, MAXE2><<<nblk(m.E, 128), 128, 0, s>>>(m, p, ubar, ut, hR, zeta, b, ut_n,
-                                                            (R)a, (R)bcoef, (R)dt, ut_out, G);
+                     double bcoef, double dt, R *ut_out, R *G, R *vmc, cudaStream_t s) {
+    const int nb = nblk(m.E, 128);
+    const R ra = (R)a, rb = (R)bcoef, rdt = (R)dt;
+    if (m.maxE2 <= 10) {
+        if (vmc)
+            k_bcl_edge<R, 10, true><<<nb, 128, 0, s>>>(m, p, ubar, ut, hR, zeta, b, ut_n, ra, rb,
+                                                       rdt, ut_out, G, vmc);
+        else
+            k_bcl_edge<R, 10, false><<<nb, 128, 0, s>>>(m, p, ubar, ut, hR, zeta, b, ut_n, ra, rb,
+                                                        rdt, ut_out, G, vmc);
+    } else {
+        if (vmc)
+            k_bcl_edge<R, MAXE2, true><<<nb, 128, 0, s>>>(m, p, ubar, ut, hR, zeta, b, ut_n, ra,
+                                                          rb, rdt, ut_out, G, vmc);
+        else
+            k_bcl_edge<R, MAXE2, false><<<nb, 128, 0, s>>>(m, p, ubar, ut, hR, zeta, b, ut_n, ra,
+                                                           rb, rdt, ut_out, G, vmc);
+    }
 }
 template <class R>
 void launch_transport(const DMesh &m, const TransportArgs<R> &a, cudaStream_t s) {
@@ -631,7 +683,7 @@ void launch_diag(const DMesh &m, const R *ubar, const R *ut, const double *h, co
                                      bool, cudaStream_t);                                        \
     template void launch_bcl_edge<R>(const DMesh &, const DParams &, const R *, const R *,       \
                                      const R *, const double *, const DiagBufs<R> &, const R *,  \
-                                     double, double, double, R *, R *, cudaStream_t);            \
+                                     double, double, double, R *, R *, R *, cudaStream_t);       \
     template void launch_transport<R>(const DMesh &, const TransportArgs<R> &, cudaStream_t);    \
     template void launch_thickness<R>(const DMesh &, const DParams &, const ThickArgs<R> &,      \
                                       cudaStream_t);                                             \

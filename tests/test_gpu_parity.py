@@ -312,3 +312,39 @@ def test_sphere_l7_full_size_one_step():
     bound = 2.0 * 3 * run["dt"] * _pgf_rounding(m, p, ref[1], ref[2])
     assert np.linalg.norm(gu - ref[0]) < bound, (np.linalg.norm(gu - ref[0]), bound)
     assert rel(gu, ref[0]) < 1e-8
+
+
+def _vmix_case():
+    # 10 m layers and nu_v = 0.5: nu_v dt / dz^2 = 1.5, beyond explicit stability
+    return inputs.channel_case(10, 12, 10e3, 10, depth=100.0, perturb=True, nTracers=2,
+                               nu_v=0.5, c_drag=2e-3, vmix=True)
+
+
+def test_alg2_baroclinic_feuler_mixing():
+    m, L, p, (u, h, tr) = _vmix_case()
+    p["windStress"] = 0.1 * np.cos(m.xEdge[:, 1] / 30e3) * m.normalEdge[:, 0]
+    o = oracle.Oracle(m, L, p)
+    ubar, ut = o.split(u, h)
+    zeta = o.ssh(h)
+    ut1, G = o.baroclinic_feuler_mixing(u, ut, ubar, zeta, h, tr, 300.0)
+    dm, st = _gpu(m, L, p, u, h, tr)
+    st.set("ubar", ubar)
+    st.set("utilde", ut)
+    st.baroclinic_feuler(300.0)
+    assert rel(st.get("utilde"), ut1) < TOL64
+    assert rel(st.get("G"), G) < TOL64
+
+
+@pytest.mark.parametrize("order", [2, 3])
+def test_full_step_vertical_mixing(order):
+    m, L, p, (u, h, tr) = _vmix_case()
+    p["windStress"] = 0.1 * np.cos(m.xEdge[:, 1] / 30e3) * m.normalEdge[:, 0]
+    o = oracle.Oracle(m, L, p)
+    ref = o.step(order, 300.0, 10, u, h, tr, n_steps=5)
+    dm, st = _gpu(m, L, p, u, h, tr)
+    st.step(order, 300.0, 10, 5)
+    _compare(st.read_state(), ref, TOL64)
+    dm, st = _gpu(m, L, p, u, h, tr, "mixed")
+    st.step(order, 300.0, 10, 5)
+    gu, gh, gt = st.read_state()
+    assert rel(gu, ref[0]) < 1e-4 and rel(gt, ref[2]) < 1e-6
