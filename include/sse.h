@@ -39,6 +39,8 @@ extern "C" {
 #define SSE_ERR_NONFINITE (-5)     /* NaN/Inf found by sse_diagnostics          */
 #define SSE_ERR_SYNC_TIMEOUT (-6)  /* a grid barrier of the sub-cycle timed out */
 #define SSE_ERR_UNSUPPORTED (-7)   /* size beyond a compiled limit              */
+#define SSE_ERR_TIMEOUT (-8)       /* sse_server_wait: the request is not done  */
+#define SSE_ERR_CANCELLED (-9)     /* request dropped when its server stopped   */
 
 /* ---- precision of the device arithmetic ---- */
 #define SSE_FP64 0   /* everything in FP64                                       */
@@ -225,6 +227,66 @@ int sse_barotropic_substep_noalloc(const sse_mesh *mesh, int order, double dt, i
                                    double g, const double *ubar_in, const double *zeta_in,
                                    const double *G, double *ubar_out, double *Fzeta_out,
                                    double *zeta_out, void *cuda_stream);
+
+/* Device bytes a state of this mesh and parameter set would allocate
+ * (everything sse_state_create allocates; nothing is allocated here). */
+int sse_state_footprint(const sse_mesh *mesh, const sse_params *params, size_t *bytes);
+
+/* dims = {nCells, nEdges, nVertices, nLayers} of a mesh. */
+int sse_mesh_dims(const sse_mesh *mesh, int32_t dims[4]);
+
+/* ---------------------------------------------------------------------------
+ * Request runtime: continuous batching of independent solves on one GPU.
+ *
+ * A request is one solve: an initial state (u [nEdges][nLayers], h
+ * [nCells][nLayers], tracers [nTracers][nCells][nLayers], host, FP64,
+ * layer-fastest; copied at submission) advanced n_steps SSPRK{order}-SE steps
+ * of dt with n_substeps barotropic sub-steps (Sec. 3.2 / 3.3).  A worker
+ * thread admits requests in arrival order while the sum of their
+ * sse_state_footprint stays within hbm_budget_bytes and at most max_active
+ * run; each admitted request gets its own stream and a device-resident state
+ * and is advanced steps_per_launch steps at a time, its work overlapping with
+ * that of the other active requests.  When it reaches its horizon the final
+ * (u, h, tracers) are written to the caller's output buffers (same layouts;
+ * they must stay valid until the request is done) and its memory is released,
+ * so waiting requests are admitted as slots and memory free up.  The mesh
+ * must outlive every request that uses it.  Results do not depend on what else
+ * runs: each request's arithmetic is exactly that of sse_step on its state. */
+typedef struct sse_server sse_server;
+
+#define SSE_REQ_DONE 0       /* finished; outputs written                       */
+#define SSE_REQ_PENDING 1    /* waiting for admission                           */
+#define SSE_REQ_ACTIVE 2     /* admitted, stepping (negative: failed, SSE_ERR_*) */
+
+typedef struct {
+    int64_t id;
+    int32_t status;          /* SSE_REQ_* or a negative SSE_ERR_* code        */
+    int32_t steps_done;
+    double t_submit, t_admit, t_done;   /* seconds since the server started     */
+    size_t footprint;        /* device bytes the request holds while active   */
+} sse_request_info;
+
+typedef struct {
+    int32_t pending, active, max_active_seen, reserved;
+    size_t used_bytes, peak_bytes, budget_bytes;
+} sse_server_info;
+
+int sse_server_create(int device, size_t hbm_budget_bytes, int max_active,
+                      int steps_per_launch, sse_server **out);
+/* Queue a request; *id_out identifies it.  SSE_ERR_OOM if it alone exceeds
+ * the budget. */
+int sse_server_submit(sse_server *server, const sse_mesh *mesh, const sse_params *params,
+                      const double *u, const double *h, const double *tracers, int order,
+                      double dt, int n_substeps, int n_steps, double *u_out, double *h_out,
+                      double *tracers_out, int64_t *id_out);
+int sse_server_query(sse_server *server, int64_t id, sse_request_info *info);
+/* Block until the request is done or failed (SSE_OK) or timeout_s passes
+ * (SSE_ERR_TIMEOUT; timeout_s < 0 waits forever). */
+int sse_server_wait(sse_server *server, int64_t id, double timeout_s, sse_request_info *info);
+int sse_server_stats(sse_server *server, sse_server_info *info);
+/* Cancel the requests still waiting (SSE_ERR_CANCELLED), let the admitted ones
+ * finish, stop the worker and free everything. */
+void sse_server_destroy(sse_server *server);
 
 const char *sse_strerror(int code);
 

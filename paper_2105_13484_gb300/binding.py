@@ -52,6 +52,19 @@ class Params(ct.Structure):
                                    "eos_S_ref")]
 
 
+class RequestInfo(ct.Structure):
+    _fields_ = [("id", ct.c_int64), ("status", ct.c_int32), ("steps_done", ct.c_int32),
+                ("t_submit", ct.c_double), ("t_admit", ct.c_double), ("t_done", ct.c_double),
+                ("footprint", ct.c_size_t)]
+
+
+class ServerInfo(ct.Structure):
+    _fields_ = [("pending", ct.c_int32), ("active", ct.c_int32),
+                ("max_active_seen", ct.c_int32), ("reserved", ct.c_int32),
+                ("used_bytes", ct.c_size_t), ("peak_bytes", ct.c_size_t),
+                ("budget_bytes", ct.c_size_t)]
+
+
 class Diag(ct.Structure):
     _fields_ = [("volume", ct.c_double), ("tracer_content", ct.c_double * 2),
                 ("kinetic_energy", ct.c_double), ("max_speed", ct.c_double),
@@ -63,7 +76,9 @@ class Diag(ct.Structure):
 EXPORTS = ["sse_mesh_create", "sse_mesh_destroy", "sse_state_create", "sse_state_destroy",
            "sse_state_set", "sse_state_get", "sse_step", "sse_baroclinic_feuler",
            "sse_barotropic_substep", "sse_diagnostics", "sse_kernels_per_step", "sse_profile",
-           "sse_profile_read", "sse_barotropic_substep_noalloc", "sse_strerror"]
+           "sse_profile_read", "sse_barotropic_substep_noalloc", "sse_state_footprint",
+           "sse_mesh_dims", "sse_server_create", "sse_server_submit", "sse_server_query",
+           "sse_server_wait", "sse_server_stats", "sse_server_destroy", "sse_strerror"]
 KERNEL_CLASSES = ["cell_diag", "vertex", "edge_pre", "bcl_edge", "btr", "transport", "thickness",
                   "combine"]
 
@@ -97,6 +112,20 @@ def load(path: str = LIB_PATH):
     lib.sse_barotropic_substep_noalloc.argtypes = [
         ct.c_void_p, ct.c_int, ct.c_double, ct.c_int, ct.c_double, ct.c_void_p, ct.c_void_p,
         ct.c_void_p, ct.c_void_p, ct.c_void_p, ct.c_void_p, ct.c_void_p]
+    lib.sse_state_footprint.argtypes = [ct.c_void_p, ct.POINTER(Params), ct.POINTER(ct.c_size_t)]
+    lib.sse_mesh_dims.argtypes = [ct.c_void_p, ct.POINTER(ct.c_int32)]
+    lib.sse_server_create.argtypes = [ct.c_int, ct.c_size_t, ct.c_int, ct.c_int,
+                                      ct.POINTER(ct.c_void_p)]
+    lib.sse_server_submit.argtypes = [ct.c_void_p, ct.c_void_p, ct.POINTER(Params), ct.c_void_p,
+                                      ct.c_void_p, ct.c_void_p, ct.c_int, ct.c_double, ct.c_int,
+                                      ct.c_int, ct.c_void_p, ct.c_void_p, ct.c_void_p,
+                                      ct.POINTER(ct.c_int64)]
+    lib.sse_server_query.argtypes = [ct.c_void_p, ct.c_int64, ct.POINTER(RequestInfo)]
+    lib.sse_server_wait.argtypes = [ct.c_void_p, ct.c_int64, ct.c_double,
+                                    ct.POINTER(RequestInfo)]
+    lib.sse_server_stats.argtypes = [ct.c_void_p, ct.POINTER(ServerInfo)]
+    lib.sse_server_destroy.argtypes = [ct.c_void_p]
+    lib.sse_server_destroy.restype = None
     lib.sse_strerror.argtypes = [ct.c_int]
     lib.sse_strerror.restype = ct.c_char_p
     _lib = lib
@@ -275,6 +304,101 @@ class State:
         if self.handle:
             self.lib.sse_state_destroy(self.handle)
             self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def footprint(mesh: Mesh, params: dict, precision="fp64") -> int:
+    """Device bytes sse_state_create would allocate for this mesh and parameters."""
+    lib = load()
+    prm = make_params(params, precision)
+    out = ct.c_size_t()
+    _check(lib.sse_state_footprint(mesh.handle, ct.byref(prm), ct.byref(out)),
+           "sse_state_footprint")
+    return int(out.value)
+
+
+STATUS = {0: "done", 1: "pending", 2: "active"}
+
+
+class Request:
+    """A submitted solve: the output arrays fill in when it is done."""
+
+    def __init__(self, server, rid, u_out, h_out, tr_out, keep):
+        self.server, self.id = server, rid
+        self.u, self.h, self.tr = u_out, h_out, tr_out
+        self._keep = keep
+
+    def info(self) -> dict:
+        inf = RequestInfo()
+        _check(self.server.lib.sse_server_query(self.server.handle, self.id, ct.byref(inf)),
+               "sse_server_query")
+        return _info(inf)
+
+    def wait(self, timeout: float = -1.0) -> dict:
+        inf = RequestInfo()
+        rc = self.server.lib.sse_server_wait(self.server.handle, self.id, float(timeout),
+                                             ct.byref(inf))
+        if rc not in (0, -8):
+            _check(rc, "sse_server_wait")
+        out = _info(inf)
+        if out["status"] not in ("pending", "active"):
+            self.server._bufs.pop(self.id, None)
+        return out
+
+
+def _info(inf) -> dict:
+    st = int(inf.status)
+    return {"id": int(inf.id), "status": STATUS.get(st, st), "steps_done": int(inf.steps_done),
+            "t_submit": inf.t_submit, "t_admit": inf.t_admit, "t_done": inf.t_done,
+            "footprint": int(inf.footprint)}
+
+
+class Server:
+    """Continuous-batching request runtime (sse_server_*): requests are admitted
+    in arrival order while their footprint fits `hbm_budget` bytes and at most
+    `max_active` run; their steps overlap on the device."""
+
+    def __init__(self, hbm_budget: int, max_active: int = 64, steps_per_launch: int = 1,
+                 device: int = 0):
+        self.lib = load()
+        h = ct.c_void_p()
+        _check(self.lib.sse_server_create(int(device), int(hbm_budget), int(max_active),
+                                          int(steps_per_launch), ct.byref(h)), "sse_server_create")
+        self.handle = h
+        self._bufs = {}   # output arrays the worker may still write, by request id
+
+    def submit(self, mesh: Mesh, params: dict, precision, u, h, tr, order: int, dt: float,
+               M: int, n_steps: int) -> Request:
+        prm = make_params(params, precision)
+        u = np.ascontiguousarray(u, dtype=np.float64)
+        h = np.ascontiguousarray(h, dtype=np.float64)
+        tr = np.ascontiguousarray(tr, dtype=np.float64)
+        uo, ho, to = np.empty_like(u), np.empty_like(h), np.empty_like(tr)
+        rid = ct.c_int64()
+        _check(self.lib.sse_server_submit(self.handle, mesh.handle, ct.byref(prm),
+                                          u.ctypes.data, h.ctypes.data, tr.ctypes.data,
+                                          int(order), float(dt), int(M), int(n_steps),
+                                          uo.ctypes.data, ho.ctypes.data, to.ctypes.data,
+                                          ct.byref(rid)), "sse_server_submit")
+        self._bufs[int(rid.value)] = (uo, ho, to, mesh)
+        return Request(self, int(rid.value), uo, ho, to, (mesh,))
+
+    def stats(self) -> dict:
+        inf = ServerInfo()
+        _check(self.lib.sse_server_stats(self.handle, ct.byref(inf)), "sse_server_stats")
+        return {k: int(getattr(inf, k)) for k in ("pending", "active", "max_active_seen",
+                                                  "used_bytes", "peak_bytes", "budget_bytes")}
+
+    def close(self):
+        if self.handle:
+            self.lib.sse_server_destroy(self.handle)   # admitted requests finish first
+            self.handle = None
+            self._bufs.clear()
 
     def __del__(self):
         try:

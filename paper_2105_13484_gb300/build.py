@@ -1,6 +1,6 @@
 """Build libsse.so (CUDA, sm_103a) in-tree with nvcc.
 
-The three translation units are compiled in parallel and linked into
+The translation units are compiled in parallel and linked into
 ``paper_2105_13484_gb300/_lib/libsse.so``.  No torch or cmake involved.
 """
 from __future__ import annotations
@@ -15,7 +15,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_lib")
 LIB = os.path.join(OUT_DIR, "libsse.so")
-SOURCES = ["api.cu", "stage_kernels.cu", "btr_kernel.cu", "tiles.cu"]
+SOURCES = ["api.cu", "stage_kernels.cu", "btr_kernel.cu", "tiles.cu", "server.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -11,7 +11,9 @@
 #include <string.h>
 
 #include <algorithm>
+#include <map>
 #include <memory>
+#include <mutex>
 #include <new>
 #include <vector>
 
@@ -26,30 +28,48 @@ namespace {
 constexpr int kAlign = 32;
 inline int pad(int n) { return (n + kAlign - 1) / kAlign * kAlign; }
 
-// RAII list of device allocations
+// RAII list of device allocations.  Meshes allocate with cudaMalloc; states
+// allocate stream-ordered on their own stream (cudaMallocAsync / cudaFreeAsync)
+// so that creating or destroying one state never synchronises the device
+// while others run.  In counting mode nothing is allocated: the arena only
+// sums the sizes (the footprint of a state before it is made).
 struct DevArena {
     std::vector<void *> ptrs;
     bool failed = false;
+    bool async = false;
+    bool count_only = false;
+    cudaStream_t stream = nullptr;
+    size_t bytes = 0;
     template <class T> T *alloc(size_t n) {
+        const size_t nb = std::max<size_t>(n, 1) * sizeof(T);
+        bytes += (nb + 255) / 256 * 256;
+        if (count_only) return reinterpret_cast<T *>((uintptr_t)256);  // never dereferenced
         void *p = nullptr;
-        if (cudaMalloc(&p, std::max<size_t>(n, 1) * sizeof(T)) != cudaSuccess) {
+        const cudaError_t e = async ? cudaMallocAsync(&p, nb, stream) : cudaMalloc(&p, nb);
+        if (e != cudaSuccess) {
             failed = true;
             cudaGetLastError();
             return nullptr;
         }
-        cudaMemset(p, 0, std::max<size_t>(n, 1) * sizeof(T));
+        if (async) cudaMemsetAsync(p, 0, nb, stream);
+        else cudaMemset(p, 0, nb);
         ptrs.push_back(p);
         return (T *)p;
     }
     template <class T> T *upload(const std::vector<T> &v) {
         T *d = alloc<T>(v.size());
-        if (d && !v.empty() &&
-            cudaMemcpy(d, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice) != cudaSuccess)
-            failed = true;
+        if (count_only || !d || v.empty()) return d;
+        const cudaError_t e =
+            async ? cudaMemcpyAsync(d, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice, stream)
+                  : cudaMemcpy(d, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) failed = true;
         return d;
     }
     ~DevArena() {
-        for (void *p : ptrs) cudaFree(p);
+        for (void *p : ptrs) {
+            if (async) cudaFreeAsync(p, stream);
+            else cudaFree(p);
+        }
     }
 };
 
@@ -60,6 +80,10 @@ struct sse_mesh {
     DevArena arena;
     int device = 0;
     HostMesh host;  // connectivity kept for the tiled sub-cycle plan
+    // tile plans already built for this mesh, by patch count (host data only;
+    // every state uploads its own copy)
+    std::mutex plan_mu;
+    std::map<int, std::shared_ptr<const TilePlan>> plans;
 };
 
 // ---------------------------------------------------------------------------
@@ -359,12 +383,26 @@ struct Engine : EngineBase {
         for (int k = 1; k <= 1; k++) {
             const int P = std::max(1, std::min(nsm * k, m.C / 64));
             const int nthreads = 1024;
-            TilePlan plan;
             const bool verbose = getenv("SSE_VERBOSE") != nullptr;
-            if (!build_tile_plan(mesh->host, P, 3, plan)) {
+            std::shared_ptr<const TilePlan> cached;
+            {
+                sse_mesh *mm = const_cast<sse_mesh *>(mesh);
+                std::lock_guard<std::mutex> lk(mm->plan_mu);
+                auto it = mm->plans.find(P);
+                if (it != mm->plans.end()) {
+                    cached = it->second;
+                } else {
+                    auto fresh = std::make_shared<TilePlan>();
+                    if (!build_tile_plan(mesh->host, P, 3, *fresh)) fresh.reset();
+                    mm->plans[P] = fresh;
+                    cached = fresh;
+                }
+            }
+            if (!cached) {
                 if (verbose) fprintf(stderr, "libsse: tile plan k=%d: 16-bit local index overflow\n", k);
                 continue;
             }
+            const TilePlan &plan = *cached;
             // 16-bit byte offsets; at most 3 entries of each kind per thread
             int own = 0;
             bool small = true;
@@ -388,9 +426,16 @@ struct Engine : EngineBase {
                 continue;
             }
 
-            for (int o = 2; o <= 3; o++)
+            // the attribute belongs to the kernel, not to this state: allow the
+            // device's whole opt-in size so that states of other meshes, whose
+            // plans need less or more, never lower it under each other
+            for (int o = 2; o <= 3; o++) {
+                cudaFuncAttributes fa;
+                CK(cudaFuncGetAttributes(&fa, btr_tiled_kernel_ptr<R>(o, own)));
                 CK(cudaFuncSetAttribute(btr_tiled_kernel_ptr<R>(o, own),
-                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+                                        cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        smem_block - (int)fa.sharedSizeBytes));
+            }
             int occ = 0;
             CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, btr_tiled_kernel_ptr<R>(3, own),
                                                              nthreads, smem));
@@ -467,10 +512,14 @@ struct Engine : EngineBase {
         return SSE_OK;
     }
 
-    int init(const sse_mesh *mesh, const sse_params *prm, cudaStream_t st) {
+    int init(const sse_mesh *mesh, const sse_params *prm, cudaStream_t st,
+             bool count_only = false) {
         m = mesh->dm;
         s = st;
         ps = st;
+        A.async = true;
+        A.stream = st;
+        A.count_only = count_only;
         mixed = (prm->precision == SSE_MIXED);
         recon = prm->recon;
         vmix = (prm->options & SSE_OPT_VMIX) != 0;
@@ -841,37 +890,62 @@ struct sse_state {
     int device = 0;
 };
 
-extern "C" int sse_state_create(const sse_mesh *mesh, const sse_params *prm, void *stream,
-                                sse_state **out) {
-    if (!mesh || !prm || !out) return SSE_ERR_INVALID_ARG;
-    *out = nullptr;
-    if ((prm->precision != SSE_FP64 && prm->precision != SSE_MIXED) || prm->recon < 0 ||
-        prm->recon > 2 || prm->nTracers < 1 || prm->nTracers > 2 || (prm->options & ~SSE_OPT_VMIX) != 0 ||
-        !(prm->g > 0) || !(prm->rho0 > 0) || !(prm->nu_h >= 0) || !(prm->nu_v >= 0) ||
-        !(prm->kappa_h >= 0) || !(prm->kappa_v >= 0) || !(prm->c_drag >= 0) ||
-        !isfinite(prm->eos_rho_ref) || !isfinite(prm->eos_alpha) || !isfinite(prm->eos_beta) ||
-        !isfinite(prm->eos_T_ref) || !isfinite(prm->eos_S_ref))
-        return SSE_ERR_INVALID_ARG;
+static bool params_ok(const sse_params *prm) {
+    return !((prm->precision != SSE_FP64 && prm->precision != SSE_MIXED) || prm->recon < 0 ||
+             prm->recon > 2 || prm->nTracers < 1 || prm->nTracers > 2 ||
+             (prm->options & ~SSE_OPT_VMIX) != 0 || !(prm->g > 0) || !(prm->rho0 > 0) ||
+             !(prm->nu_h >= 0) || !(prm->nu_v >= 0) || !(prm->kappa_h >= 0) ||
+             !(prm->kappa_v >= 0) || !(prm->c_drag >= 0) || !isfinite(prm->eos_rho_ref) ||
+             !isfinite(prm->eos_alpha) || !isfinite(prm->eos_beta) || !isfinite(prm->eos_T_ref) ||
+             !isfinite(prm->eos_S_ref));
+}
+
+static int make_state(const sse_mesh *mesh, const sse_params *prm, void *stream,
+                      bool count_only, sse_state **out, size_t *bytes) {
     sse_state *st = new (std::nothrow) sse_state();
     if (!st) return SSE_ERR_OOM;
     int rc;
+    size_t b = 0;
     if (prm->precision == SSE_FP64) {
         auto *e = new (std::nothrow) Engine<double>();
         if (!e) { delete st; return SSE_ERR_OOM; }
         st->eng.reset(e);
-        rc = e->init(mesh, prm, (cudaStream_t)stream);
+        rc = e->init(mesh, prm, (cudaStream_t)stream, count_only);
+        b = e->A.bytes;
     } else {
         auto *e = new (std::nothrow) Engine<float>();
         if (!e) { delete st; return SSE_ERR_OOM; }
         st->eng.reset(e);
-        rc = e->init(mesh, prm, (cudaStream_t)stream);
+        rc = e->init(mesh, prm, (cudaStream_t)stream, count_only);
+        b = e->A.bytes;
     }
-    if (rc != SSE_OK) {
+    if (bytes) *bytes = b;
+    if (rc != SSE_OK || count_only) {
         delete st;
         return rc;
     }
     *out = st;
     return SSE_OK;
+}
+
+extern "C" int sse_state_create(const sse_mesh *mesh, const sse_params *prm, void *stream,
+                                sse_state **out) {
+    if (!mesh || !prm || !out) return SSE_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (!params_ok(prm)) return SSE_ERR_INVALID_ARG;
+    return make_state(mesh, prm, stream, false, out, nullptr);
+}
+
+extern "C" int sse_mesh_dims(const sse_mesh *mesh, int32_t dims[4]) {
+    if (!mesh || !dims) return SSE_ERR_INVALID_ARG;
+    dims[0] = mesh->dm.C; dims[1] = mesh->dm.E; dims[2] = mesh->dm.V; dims[3] = mesh->dm.L;
+    return SSE_OK;
+}
+
+extern "C" int sse_state_footprint(const sse_mesh *mesh, const sse_params *prm, size_t *bytes) {
+    if (!mesh || !prm || !bytes) return SSE_ERR_INVALID_ARG;
+    if (!params_ok(prm)) return SSE_ERR_INVALID_ARG;
+    return make_state(mesh, prm, nullptr, true, nullptr, bytes);
 }
 
 extern "C" void sse_state_destroy(sse_state *st) { delete st; }
@@ -941,6 +1015,8 @@ extern "C" const char *sse_strerror(int code) {
     case SSE_ERR_NONFINITE: return "non-finite value in the state";
     case SSE_ERR_SYNC_TIMEOUT: return "grid barrier of the barotropic sub-cycle timed out";
     case SSE_ERR_UNSUPPORTED: return "size beyond a compiled limit";
+    case SSE_ERR_TIMEOUT: return "request not finished within the timeout";
+    case SSE_ERR_CANCELLED: return "request cancelled when its server stopped";
     default: return "unknown error";
     }
 }
