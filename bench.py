@@ -11,9 +11,13 @@ Metric: cell-layer-steps/s = cells x layers x steps / device time.  The
 headline form is the mixed-precision path; the FP64 path is measured in the
 same run and reported under "forms", with per-step p50/p99 latency.  L2 is
 flushed (a 512 MB write) between timed steps and the flush is excluded from
-the per-step CUDA-event times.  The same run also measures the largest single
-mesh, the level-7 icosahedral sphere with 60 layers (114,689 ocean cells, T
-and S, wind stress; SSPRK3-SE, dt = 600 s, M = 40), mixed form, under "also".
+the per-step CUDA-event times.  The same run also measures, under "also":
+the largest single mesh, the level-7 icosahedral sphere with 60 layers
+(114,689 ocean cells, T and S, wind stress; SSPRK3-SE, dt = 600 s, M = 40);
+the channel with Algorithm 2 (implicit vertical mixing); a 64-member uneven
+ensemble batched through the request runtime against one member at a time;
+and a seeded Poisson request stream, mixed precision with continuous
+batching against FP64 one request at a time (p50/p99 time-to-horizon).
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
                     [--workload channel_1km|sphere_l7] [--no-sphere]
@@ -410,6 +414,90 @@ def measure_workload(torch, binding, name, forms_todo, headline, steps, warmup, 
     return out
 
 
+def _build_requests(binding, specs):
+    """Meshes (shared where the spec repeats) and initial states of request specs."""
+    from paper_2105_13484_gb300 import inputs
+    cache, out = {}, []
+    for sp in specs:
+        key = (sp["kind"], sp.get("level"), sp.get("nx"), sp.get("ny"), sp["L"],
+               sp["seed"] % 7 if sp["kind"] == "sphere" else sp["seed"])
+        if key not in cache:
+            m, L, p, st = inputs.build_spec(sp)
+            dm = binding.Mesh(m, L)
+            for prec in ("mixed", "fp64"):      # plans and tuning before the clock runs
+                for obj in ("latency", "throughput"):
+                    binding.footprint(dm, p, prec, binding.tune(dm, p, prec, obj))
+            cache[key] = (m, L, p, st, dm)
+        out.append(cache[key])
+    return out
+
+
+def run_stream(binding, specs, built, precision, max_active, budget, chunk, realtime=True,
+               tune="throughput"):
+    """Submit the specs (at their arrival times when realtime) to one server;
+    returns per-request (latency, units) and the makespan."""
+    srv = binding.Server(hbm_budget=budget, max_active=max_active, steps_per_launch=chunk,
+                         tune=tune)
+    t0 = time.perf_counter()
+    handles = []
+    for sp, (m, L, p, (u, h, tr), dm) in zip(specs, built):
+        if realtime:
+            wait = t0 + sp.get("arrival", 0.0) - time.perf_counter()
+            if wait > 0:
+                time.sleep(wait)
+        handles.append((srv.submit(dm, p, precision, u, h, tr, sp["order"], sp["dt"], sp["M"],
+                                   sp["steps"]), m.nCells * L * sp["steps"]))
+    lat, units = [], 0
+    for hd, un in handles:
+        inf = hd.wait(-1)
+        if inf["status"] != "done":
+            raise RuntimeError(f"request {inf['id']} ended with {inf['status']}")
+        lat.append(inf["t_done"] - inf["t_submit"])
+        units += un
+    makespan = time.perf_counter() - t0
+    st = srv.stats()
+    srv.close()
+    lat = np.array(lat)
+    return {"requests": len(specs), "makespan_s": makespan, "value": units / makespan,
+            "unit": METRIC, "p50_s": float(np.percentile(lat, 50)),
+            "p99_s": float(np.percentile(lat, 99)), "max_active_seen": st["max_active_seen"],
+            "peak_bytes": st["peak_bytes"]}
+
+
+def measure_ensemble(binding, seed=0):
+    """64 uneven channel members (SSPRK3-SE, mixed, 100 steps each) batched
+    through the request runtime against the same members one at a time."""
+    from paper_2105_13484_gb300 import inputs
+    specs = inputs.ensemble_members(seed=seed)
+    built = _build_requests(binding, specs)
+    batched = run_stream(binding, specs, built, "mixed", 64, 200 << 30, 10, realtime=False,
+                         tune="throughput")
+    single = run_stream(binding, specs, built, "mixed", 1, 200 << 30, 10, realtime=False,
+                        tune="latency")
+    tuned = sorted({(b[0].nCells, binding.tune(b[4], b[2], "mixed", "throughput")) for b in built})
+    return {"members": len(specs), "cells": sorted({b[0].nCells for b in built}),
+            "patch_cells_throughput": tuned,
+            "layers": [int(min(b[1] for b in built)), int(max(b[1] for b in built))],
+            "batched": batched, "one_at_a_time": single,
+            "speedup": single["makespan_s"] / batched["makespan_s"]}
+
+
+def measure_serving(binding, seed=0):
+    """A seeded Poisson stream (20 requests/s) of SSPRK2/3-SE solves on planar
+    channels and geodesic spheres: mixed precision with continuous batching
+    against the FP64 path one request at a time, same arrival times."""
+    from paper_2105_13484_gb300 import inputs
+    specs = inputs.serving_requests(seed=seed)
+    built = _build_requests(binding, specs)
+    mixed = run_stream(binding, specs, built, "mixed", 64, 200 << 30, 4, tune="throughput")
+    fp64 = run_stream(binding, specs, built, "fp64", 1, 200 << 30, 4, tune="latency")
+    return {"requests": len(specs), "rate_per_s": 20.0,
+            "mix": "planar 2k-60k cells and geodesic levels 5-6, 10-60 layers, 20-100 steps",
+            "mixed_batched": mixed, "fp64_one_at_a_time": fp64,
+            "throughput_ratio": mixed["value"] / fp64["value"],
+            "p99_ratio": fp64["p99_s"] / mixed["p99_s"]}
+
+
 def config_of(name, w, precision, world):
     m, L, run, p = w["mesh"], w["L"], w["run"], w["p"]
     return {"workload": name, "cells": m.nCells, "edges": m.nEdges, "layers": L,
@@ -472,6 +560,10 @@ def run_ours(args):
             "kernels": vm["kernels"],
             "volume_rel_change": vm["forms_summary"]["mixed"]["volume_rel_change"]}
 
+    if args.workload == WORKLOAD and not args.no_serving:
+        also["ensemble"] = measure_ensemble(binding, seed=rank)
+        also["serving"] = measure_serving(binding, seed=rank)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
         v, ms, sample = time_oracle(2, 0, sample=(160, 578))
@@ -516,7 +608,9 @@ def main():
     ap.add_argument("--workload", default=WORKLOAD, choices=[WORKLOAD, "sphere_l7"],
                     help="headline workload (default: the 92,480-cell channel)")
     ap.add_argument("--no-sphere", action="store_true",
-                    help="skip the extra level-7 sphere measurement")
+                    help="skip the extra level-7 sphere and Algorithm 2 measurements")
+    ap.add_argument("--no-serving", action="store_true",
+                    help="skip the batched-ensemble and request-stream measurements")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -228,9 +228,35 @@ int sse_barotropic_substep_noalloc(const sse_mesh *mesh, int order, double dt, i
                                    const double *G, double *ubar_out, double *Fzeta_out,
                                    double *zeta_out, void *cuda_stream);
 
+/* Launch-shape choices of a state.  patch_cells: target cells per patch of
+ * the tiled barotropic sub-cycle (one patch per SM, at most one per SM in
+ * total; 0 = 64, i.e. as many patches as the mesh allows).  Larger patches
+ * use fewer SMs for longer, which lets the sub-cycles of several states run
+ * side by side. */
+typedef struct {
+    int32_t patch_cells;
+    int32_t reserved[7];     /* must be 0 */
+} sse_tuning;
+
+#define SSE_TUNE_LATENCY 0     /* the fastest sub-cycle                          */
+#define SSE_TUNE_THROUGHPUT 1  /* the least SM-time (duration x patches) within
+                                  twice the fastest                             */
+
+int sse_state_create_ex(const sse_mesh *mesh, const sse_params *params,
+                        const sse_tuning *tuning, void *cuda_stream, sse_state **out);
+/* Patches of the state's tiled sub-cycle (0: the global-memory sub-cycle). */
+int sse_state_patches(const sse_state *state, int *patches);
+/* Autotuner: times the Algorithm 3/4 sub-cycle (M = 20) of a zero state of
+ * this mesh for each candidate patch size and returns the best one for the
+ * objective (SSE_TUNE_*).  Runs GPU work on a private stream; the result is
+ * cached in the mesh. */
+int sse_tune(const sse_mesh *mesh, const sse_params *params, int objective, sse_tuning *out);
+
 /* Device bytes a state of this mesh and parameter set would allocate
  * (everything sse_state_create allocates; nothing is allocated here). */
 int sse_state_footprint(const sse_mesh *mesh, const sse_params *params, size_t *bytes);
+int sse_state_footprint_ex(const sse_mesh *mesh, const sse_params *params,
+                           const sse_tuning *tuning, size_t *bytes);
 
 /* dims = {nCells, nEdges, nVertices, nLayers} of a mesh. */
 int sse_mesh_dims(const sse_mesh *mesh, int32_t dims[4]);
@@ -240,7 +266,8 @@ int sse_mesh_dims(const sse_mesh *mesh, int32_t dims[4]);
  *
  * A request is one solve: an initial state (u [nEdges][nLayers], h
  * [nCells][nLayers], tracers [nTracers][nCells][nLayers], host, FP64,
- * layer-fastest; copied at submission) advanced n_steps SSPRK{order}-SE steps
+ * layer-fastest; copied at submission; wind_stress [nEdges] or NULL, as
+ * SSE_FIELD_WIND) advanced n_steps SSPRK{order}-SE steps
  * of dt with n_substeps barotropic sub-steps (Sec. 3.2 / 3.3).  A worker
  * thread admits requests in arrival order while the sum of their
  * sse_state_footprint stays within hbm_budget_bytes and at most max_active
@@ -271,14 +298,17 @@ typedef struct {
     size_t used_bytes, peak_bytes, budget_bytes;
 } sse_server_info;
 
+/* tune_objective: -1 = default launch shapes, else SSE_TUNE_* (sse_tune is
+ * run once per mesh and precision, at the first submission that uses it). */
 int sse_server_create(int device, size_t hbm_budget_bytes, int max_active,
-                      int steps_per_launch, sse_server **out);
+                      int steps_per_launch, int tune_objective, sse_server **out);
 /* Queue a request; *id_out identifies it.  SSE_ERR_OOM if it alone exceeds
  * the budget. */
 int sse_server_submit(sse_server *server, const sse_mesh *mesh, const sse_params *params,
-                      const double *u, const double *h, const double *tracers, int order,
-                      double dt, int n_substeps, int n_steps, double *u_out, double *h_out,
-                      double *tracers_out, int64_t *id_out);
+                      const double *u, const double *h, const double *tracers,
+                      const double *wind_stress, int order, double dt, int n_substeps,
+                      int n_steps, double *u_out, double *h_out, double *tracers_out,
+                      int64_t *id_out);
 int sse_server_query(sse_server *server, int64_t id, sse_request_info *info);
 /* Block until the request is done or failed (SSE_OK) or timeout_s passes
  * (SSE_ERR_TIMEOUT; timeout_s < 0 waits forever). */

@@ -52,6 +52,13 @@ class Params(ct.Structure):
                                    "eos_S_ref")]
 
 
+class Tuning(ct.Structure):
+    _fields_ = [("patch_cells", ct.c_int32), ("reserved", ct.c_int32 * 7)]
+
+
+TUNE = {"latency": 0, "throughput": 1}
+
+
 class RequestInfo(ct.Structure):
     _fields_ = [("id", ct.c_int64), ("status", ct.c_int32), ("steps_done", ct.c_int32),
                 ("t_submit", ct.c_double), ("t_admit", ct.c_double), ("t_done", ct.c_double),
@@ -77,6 +84,7 @@ EXPORTS = ["sse_mesh_create", "sse_mesh_destroy", "sse_state_create", "sse_state
            "sse_state_set", "sse_state_get", "sse_step", "sse_baroclinic_feuler",
            "sse_barotropic_substep", "sse_diagnostics", "sse_kernels_per_step", "sse_profile",
            "sse_profile_read", "sse_barotropic_substep_noalloc", "sse_state_footprint",
+           "sse_state_footprint_ex", "sse_state_create_ex", "sse_state_patches", "sse_tune",
            "sse_mesh_dims", "sse_server_create", "sse_server_submit", "sse_server_query",
            "sse_server_wait", "sse_server_stats", "sse_server_destroy", "sse_strerror"]
 KERNEL_CLASSES = ["cell_diag", "vertex", "edge_pre", "bcl_edge", "btr", "transport", "thickness",
@@ -114,12 +122,18 @@ def load(path: str = LIB_PATH):
         ct.c_void_p, ct.c_void_p, ct.c_void_p, ct.c_void_p, ct.c_void_p]
     lib.sse_state_footprint.argtypes = [ct.c_void_p, ct.POINTER(Params), ct.POINTER(ct.c_size_t)]
     lib.sse_mesh_dims.argtypes = [ct.c_void_p, ct.POINTER(ct.c_int32)]
-    lib.sse_server_create.argtypes = [ct.c_int, ct.c_size_t, ct.c_int, ct.c_int,
+    lib.sse_server_create.argtypes = [ct.c_int, ct.c_size_t, ct.c_int, ct.c_int, ct.c_int,
                                       ct.POINTER(ct.c_void_p)]
+    lib.sse_state_create_ex.argtypes = [ct.c_void_p, ct.POINTER(Params), ct.POINTER(Tuning),
+                                        ct.c_void_p, ct.POINTER(ct.c_void_p)]
+    lib.sse_state_footprint_ex.argtypes = [ct.c_void_p, ct.POINTER(Params), ct.POINTER(Tuning),
+                                           ct.POINTER(ct.c_size_t)]
+    lib.sse_state_patches.argtypes = [ct.c_void_p, ct.POINTER(ct.c_int)]
+    lib.sse_tune.argtypes = [ct.c_void_p, ct.POINTER(Params), ct.c_int, ct.POINTER(Tuning)]
     lib.sse_server_submit.argtypes = [ct.c_void_p, ct.c_void_p, ct.POINTER(Params), ct.c_void_p,
-                                      ct.c_void_p, ct.c_void_p, ct.c_int, ct.c_double, ct.c_int,
-                                      ct.c_int, ct.c_void_p, ct.c_void_p, ct.c_void_p,
-                                      ct.POINTER(ct.c_int64)]
+                                      ct.c_void_p, ct.c_void_p, ct.c_void_p, ct.c_int,
+                                      ct.c_double, ct.c_int, ct.c_int, ct.c_void_p, ct.c_void_p,
+                                      ct.c_void_p, ct.POINTER(ct.c_int64)]
     lib.sse_server_query.argtypes = [ct.c_void_p, ct.c_int64, ct.POINTER(RequestInfo)]
     lib.sse_server_wait.argtypes = [ct.c_void_p, ct.c_int64, ct.c_double,
                                     ct.POINTER(RequestInfo)]
@@ -214,15 +228,17 @@ def make_params(params: dict, precision="fp64") -> Params:
 class State:
     """A model state on the GPU (the library owns its device memory)."""
 
-    def __init__(self, mesh: Mesh, params: dict, precision="fp64", stream=None):
+    def __init__(self, mesh: Mesh, params: dict, precision="fp64", stream=None,
+                 patch_cells: int = 0):
         self.lib = load()
         self.mesh = mesh
         self.params = make_params(params, precision)
         self.nT = self.params.nTracers
         h = ct.c_void_p()
-        _check(self.lib.sse_state_create(mesh.handle, ct.byref(self.params),
-                                          ct.c_void_p(stream or 0), ct.byref(h)),
-               "sse_state_create")
+        t = Tuning(int(patch_cells))
+        _check(self.lib.sse_state_create_ex(mesh.handle, ct.byref(self.params), ct.byref(t),
+                                             ct.c_void_p(stream or 0), ct.byref(h)),
+               "sse_state_create_ex")
         self.handle = h
         ws = params.get("windStress")
         if ws is not None:
@@ -297,6 +313,11 @@ class State:
                "sse_profile_read")
         return {k: (float(ms[i]), int(n[i])) for i, k in enumerate(KERNEL_CLASSES)}
 
+    def patches(self) -> int:
+        n = ct.c_int()
+        _check(self.lib.sse_state_patches(self.handle, ct.byref(n)), "sse_state_patches")
+        return int(n.value)
+
     def kernels_per_step(self, order: int) -> int:
         return int(self.lib.sse_kernels_per_step(self.handle, int(order)))
 
@@ -312,14 +333,24 @@ class State:
             pass
 
 
-def footprint(mesh: Mesh, params: dict, precision="fp64") -> int:
+def footprint(mesh: Mesh, params: dict, precision="fp64", patch_cells: int = 0) -> int:
     """Device bytes sse_state_create would allocate for this mesh and parameters."""
     lib = load()
     prm = make_params(params, precision)
     out = ct.c_size_t()
-    _check(lib.sse_state_footprint(mesh.handle, ct.byref(prm), ct.byref(out)),
-           "sse_state_footprint")
+    t = Tuning(int(patch_cells))
+    _check(lib.sse_state_footprint_ex(mesh.handle, ct.byref(prm), ct.byref(t), ct.byref(out)),
+           "sse_state_footprint_ex")
     return int(out.value)
+
+
+def tune(mesh: Mesh, params: dict, precision="mixed", objective="throughput") -> int:
+    """Autotuned patch size of the tiled sub-cycle (sse_tune)."""
+    lib = load()
+    prm = make_params(params, precision)
+    t = Tuning()
+    _check(lib.sse_tune(mesh.handle, ct.byref(prm), TUNE[objective], ct.byref(t)), "sse_tune")
+    return int(t.patch_cells)
 
 
 STATUS = {0: "done", 1: "pending", 2: "active"}
@@ -364,11 +395,13 @@ class Server:
     `max_active` run; their steps overlap on the device."""
 
     def __init__(self, hbm_budget: int, max_active: int = 64, steps_per_launch: int = 1,
-                 device: int = 0):
+                 device: int = 0, tune=None):
         self.lib = load()
         h = ct.c_void_p()
+        obj = -1 if tune is None else TUNE[tune]
         _check(self.lib.sse_server_create(int(device), int(hbm_budget), int(max_active),
-                                          int(steps_per_launch), ct.byref(h)), "sse_server_create")
+                                          int(steps_per_launch), obj, ct.byref(h)),
+               "sse_server_create")
         self.handle = h
         self._bufs = {}   # output arrays the worker may still write, by request id
 
@@ -379,9 +412,12 @@ class Server:
         h = np.ascontiguousarray(h, dtype=np.float64)
         tr = np.ascontiguousarray(tr, dtype=np.float64)
         uo, ho, to = np.empty_like(u), np.empty_like(h), np.empty_like(tr)
+        ws = params.get("windStress")
+        ws = None if ws is None else np.ascontiguousarray(ws, dtype=np.float64)
         rid = ct.c_int64()
         _check(self.lib.sse_server_submit(self.handle, mesh.handle, ct.byref(prm),
                                           u.ctypes.data, h.ctypes.data, tr.ctypes.data,
+                                          None if ws is None else ws.ctypes.data,
                                           int(order), float(dt), int(M), int(n_steps),
                                           uo.ctypes.data, ho.ctypes.data, to.ctypes.data,
                                           ct.byref(rid)), "sse_server_submit")

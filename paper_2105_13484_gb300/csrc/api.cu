@@ -84,6 +84,7 @@ struct sse_mesh {
     // every state uploads its own copy)
     std::mutex plan_mu;
     std::map<int, std::shared_ptr<const TilePlan>> plans;
+    std::map<int, int> tuned;   // autotuned patch size by (precision, objective)
 };
 
 // ---------------------------------------------------------------------------
@@ -278,6 +279,7 @@ struct EngineBase {
     virtual int step(int order, double dt, int M) = 0;
     virtual int bcl_feuler(double dt) = 0;
     virtual int btr_substep(int order, double dt, int M) = 0;
+    virtual int patches() const = 0;       // tiled sub-cycle patches (0: global kernel)
     virtual int diagnostics(sse_diag *out) = 0;
     long long steps = 0;
 
@@ -344,6 +346,7 @@ struct Engine : EngineBase {
     int recon = SSE_RECON_CONSISTENT;
     bool mixed = false;
     bool vmix = false;   // Algorithm 2 in every baroclinic stage
+    int patch_cells = 64;  // target cells per sub-cycle patch (sse_tuning)
     cudaStream_t s = nullptr;
     DevArena A;
     // state
@@ -380,8 +383,11 @@ struct Engine : EngineBase {
         CK(cudaDeviceGetAttribute(&smem_block, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
         CK(cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev));
         if (m.maxE2 > 10 || m.maxE > TILE_NCEP) return SSE_OK;
-        for (int k = 1; k <= 1; k++) {
-            const int P = std::max(1, std::min(nsm * k, m.C / 64));
+        // patches of about patch_cells cells, at most one per SM; a plan whose
+        // patches are too large for one SM is retried with more patches
+        int P0 = std::max(1, std::min(nsm, m.C / std::max(patch_cells, 1)));
+        for (int k = 1, P = P0; P > 0;
+             k++, P = (P >= nsm) ? 0 : std::min(nsm, std::max(P + 1, P * 5 / 4))) {
             const int nthreads = 1024;
             const bool verbose = getenv("SSE_VERBOSE") != nullptr;
             std::shared_ptr<const TilePlan> cached;
@@ -419,7 +425,7 @@ struct Engine : EngineBase {
                 continue;
             }
             const size_t smem = tile_smem_bytes(plan, m.maxE, m.maxE2, sizeof(R));
-            if (smem > (size_t)smem_block || smem * k > (size_t)smem_sm - 1024 * k) {
+            if (smem > (size_t)smem_block || smem > (size_t)smem_sm - 1024) {   // one CTA per SM
                 if (verbose)
                     fprintf(stderr, "libsse: tile plan k=%d P=%d: smem %zu > limits %d/%d\n", k, P,
                             smem, smem_block, smem_sm);
@@ -839,6 +845,8 @@ struct Engine : EngineBase {
         return check_launch();
     }
 
+    int patches() const override { return tiled ? tiles.P : 0; }
+
     int btr_substep(int order, double dt, int M) override {
         launch_ssh(m, h_n, zeta_n, s);
         CK(btr(order, ubar_n, zeta_n, G0, dt, M, nullptr, 0, 1, ubar_1, Fz1, zeta_sub));
@@ -900,22 +908,33 @@ static bool params_ok(const sse_params *prm) {
              !isfinite(prm->eos_S_ref));
 }
 
-static int make_state(const sse_mesh *mesh, const sse_params *prm, void *stream,
-                      bool count_only, sse_state **out, size_t *bytes) {
+static bool tuning_ok(const sse_tuning *t) {
+    if (!t) return true;
+    if (t->patch_cells < 0) return false;
+    for (int k = 0; k < 7; k++)
+        if (t->reserved[k] != 0) return false;
+    return true;
+}
+
+static int make_state(const sse_mesh *mesh, const sse_params *prm, const sse_tuning *tun,
+                      void *stream, bool count_only, sse_state **out, size_t *bytes) {
     sse_state *st = new (std::nothrow) sse_state();
     if (!st) return SSE_ERR_OOM;
+    const int pc = (tun && tun->patch_cells > 0) ? tun->patch_cells : 64;
     int rc;
     size_t b = 0;
     if (prm->precision == SSE_FP64) {
         auto *e = new (std::nothrow) Engine<double>();
         if (!e) { delete st; return SSE_ERR_OOM; }
         st->eng.reset(e);
+        e->patch_cells = pc;
         rc = e->init(mesh, prm, (cudaStream_t)stream, count_only);
         b = e->A.bytes;
     } else {
         auto *e = new (std::nothrow) Engine<float>();
         if (!e) { delete st; return SSE_ERR_OOM; }
         st->eng.reset(e);
+        e->patch_cells = pc;
         rc = e->init(mesh, prm, (cudaStream_t)stream, count_only);
         b = e->A.bytes;
     }
@@ -930,10 +949,26 @@ static int make_state(const sse_mesh *mesh, const sse_params *prm, void *stream,
 
 extern "C" int sse_state_create(const sse_mesh *mesh, const sse_params *prm, void *stream,
                                 sse_state **out) {
+    return sse_state_create_ex(mesh, prm, nullptr, stream, out);
+}
+
+extern "C" int sse_state_create_ex(const sse_mesh *mesh, const sse_params *prm,
+                                   const sse_tuning *tuning, void *stream, sse_state **out) {
     if (!mesh || !prm || !out) return SSE_ERR_INVALID_ARG;
     *out = nullptr;
-    if (!params_ok(prm)) return SSE_ERR_INVALID_ARG;
-    return make_state(mesh, prm, stream, false, out, nullptr);
+    if (!params_ok(prm) || !tuning_ok(tuning)) return SSE_ERR_INVALID_ARG;
+    return make_state(mesh, prm, tuning, stream, false, out, nullptr);
+}
+
+extern "C" int sse_state_footprint(const sse_mesh *mesh, const sse_params *prm, size_t *bytes) {
+    return sse_state_footprint_ex(mesh, prm, nullptr, bytes);
+}
+
+extern "C" int sse_state_footprint_ex(const sse_mesh *mesh, const sse_params *prm,
+                                      const sse_tuning *tuning, size_t *bytes) {
+    if (!mesh || !prm || !bytes) return SSE_ERR_INVALID_ARG;
+    if (!params_ok(prm) || !tuning_ok(tuning)) return SSE_ERR_INVALID_ARG;
+    return make_state(mesh, prm, tuning, nullptr, true, nullptr, bytes);
 }
 
 extern "C" int sse_mesh_dims(const sse_mesh *mesh, int32_t dims[4]) {
@@ -942,10 +977,99 @@ extern "C" int sse_mesh_dims(const sse_mesh *mesh, int32_t dims[4]) {
     return SSE_OK;
 }
 
-extern "C" int sse_state_footprint(const sse_mesh *mesh, const sse_params *prm, size_t *bytes) {
-    if (!mesh || !prm || !bytes) return SSE_ERR_INVALID_ARG;
+extern "C" int sse_state_patches(const sse_state *st, int *patches) {
+    if (!st || !patches) return SSE_ERR_INVALID_ARG;
+    *patches = st->eng->patches();
+    return SSE_OK;
+}
+
+// Measured choice of the sub-cycle patch size: the Algorithm 3/4 sub-cycle
+// (M = 20 sub-steps, the kernel every large step calls two or three times)
+// is timed with CUDA events for each candidate patch size on a zero state of
+// this mesh; LATENCY keeps the fastest, THROUGHPUT the one with the least
+// SM-time (duration x patches, one SM each), among those within twice the
+// fastest.  Results are cached per mesh, precision and objective.
+extern "C" int sse_tune(const sse_mesh *mesh, const sse_params *prm, int objective,
+                        sse_tuning *out) {
+    if (!mesh || !prm || !out || (objective != SSE_TUNE_LATENCY &&
+                                  objective != SSE_TUNE_THROUGHPUT))
+        return SSE_ERR_INVALID_ARG;
     if (!params_ok(prm)) return SSE_ERR_INVALID_ARG;
-    return make_state(mesh, prm, nullptr, true, nullptr, bytes);
+    sse_mesh *mm = const_cast<sse_mesh *>(mesh);
+    const int key = -(1 + prm->precision * 2 + objective);   // negative: not a patch count
+    {
+        std::lock_guard<std::mutex> lk(mm->plan_mu);
+        auto it = mm->tuned.find(key);
+        if (it != mm->tuned.end()) {
+            memset(out, 0, sizeof(*out));
+            out->patch_cells = it->second;
+            return SSE_OK;
+        }
+    }
+    cudaStream_t s = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) return SSE_ERR_CUDA;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    const int C = mesh->dm.C;
+    const int cands[] = {64, 128, 256, 384, 512, 768, 1024, 1536};
+    std::vector<std::pair<int, std::pair<float, int>>> res;   // (cells, (ms, patches))
+    int last_P = -1, rc = SSE_OK;
+    for (int pc : cands) {
+        if (pc > 64 && C / pc < 1) break;
+        sse_tuning t{};
+        t.patch_cells = pc;
+        sse_state *st = nullptr;
+        rc = make_state(mesh, prm, &t, s, false, &st, nullptr);
+        if (rc) break;
+        int P = st->eng->patches();
+        if (P == 0 || P == last_P) {     // no tiled plan, or the same plan again
+            delete st;
+            if (P == 0) break;
+            continue;
+        }
+        last_P = P;
+        float best = 1e30f;
+        for (int rep = 0; rep < 4 && !rc; rep++) {
+            cudaEventRecord(e0, s);
+            rc = st->eng->btr_substep(3, 600.0, 20);
+            cudaEventRecord(e1, s);
+            cudaEventSynchronize(e1);
+            float ms = 0;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (rep > 0) best = std::min(best, ms);   // the first run warms up
+        }
+        delete st;
+        if (rc) break;
+        res.push_back({pc, {best, P}});
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaStreamSynchronize(s);
+    cudaStreamDestroy(s);
+    if (rc) return rc;
+    int choice = 64;
+    if (!res.empty()) {
+        float fastest = 1e30f;
+        for (auto &r : res) fastest = std::min(fastest, r.second.first);
+        double best_cost = 1e300;
+        for (auto &r : res) {
+            const double cost = objective == SSE_TUNE_LATENCY
+                                    ? r.second.first
+                                    : (double)r.second.first * r.second.second;
+            if (r.second.first <= 2.0f * fastest && cost < best_cost) {
+                best_cost = cost;
+                choice = r.first;
+            }
+        }
+    }
+    {
+        std::lock_guard<std::mutex> lk(mm->plan_mu);
+        mm->tuned[key] = choice;
+    }
+    memset(out, 0, sizeof(*out));
+    out->patch_cells = choice;
+    return SSE_OK;
 }
 
 extern "C" void sse_state_destroy(sse_state *st) { delete st; }

@@ -36,9 +36,10 @@ struct Req {
     int order = 3, M = 1, n_steps = 0;
     double dt = 0.0;
     int nE = 0, nC = 0, L = 0;
-    std::vector<double> u, h, tr;        // host copies of the inputs
+    std::vector<double> u, h, tr, wind;  // host copies of the inputs
     double *u_out = nullptr, *h_out = nullptr, *tr_out = nullptr;
     size_t footprint = 0;
+    sse_tuning tun{};
     int steps_done = 0, inflight = 0;
     sse_state *st = nullptr;
     cudaStream_t s = nullptr;
@@ -56,7 +57,7 @@ double now_s(std::chrono::steady_clock::time_point t0) {
 struct sse_server {
     int device = 0;
     size_t budget = 0, used = 0, peak = 0;
-    int max_active = 1, chunk = 1;
+    int max_active = 1, chunk = 1, tune = -1;
     std::chrono::steady_clock::time_point t0;
     std::mutex mu;
     std::condition_variable cv_work, cv_done;
@@ -101,16 +102,18 @@ int start(sse_server *S, Req *r) {
     } else if (cudaEventCreateWithFlags(&r->ev, cudaEventDisableTiming) != cudaSuccess) {
         return SSE_ERR_CUDA;
     }
-    int rc = sse_state_create(r->mesh, &r->prm, r->s, &r->st);
+    int rc = sse_state_create_ex(r->mesh, &r->prm, &r->tun, r->s, &r->st);
     if (rc) return rc;
     rc = sse_state_set(r->st, SSE_FIELD_U, r->u.data());
     if (!rc) rc = sse_state_set(r->st, SSE_FIELD_H, r->h.data());
     for (int t = 0; !rc && t < r->prm.nTracers; t++)
         rc = sse_state_set(r->st, SSE_FIELD_TRACER0 + t, r->tr.data() + (size_t)t * r->nC * r->L);
+    if (!rc && !r->wind.empty()) rc = sse_state_set(r->st, SSE_FIELD_WIND, r->wind.data());
     // the inputs are on the device now
     std::vector<double>().swap(r->u);
     std::vector<double>().swap(r->h);
     std::vector<double>().swap(r->tr);
+    std::vector<double>().swap(r->wind);
     return rc;
 }
 
@@ -212,8 +215,9 @@ void worker_loop(sse_server *S) {
 }  // namespace
 
 extern "C" int sse_server_create(int device, size_t hbm_budget_bytes, int max_active,
-                                 int steps_per_launch, sse_server **out) {
-    if (!out || max_active < 1 || steps_per_launch < 1 || hbm_budget_bytes == 0)
+                                 int steps_per_launch, int tune_objective, sse_server **out) {
+    if (!out || max_active < 1 || steps_per_launch < 1 || hbm_budget_bytes == 0 ||
+        tune_objective < -1 || tune_objective > SSE_TUNE_THROUGHPUT)
         return SSE_ERR_INVALID_ARG;
     *out = nullptr;
     int ndev = 0;
@@ -225,6 +229,7 @@ extern "C" int sse_server_create(int device, size_t hbm_budget_bytes, int max_ac
     S->budget = hbm_budget_bytes;
     S->max_active = max_active;
     S->chunk = steps_per_launch;
+    S->tune = tune_objective;
     S->t0 = std::chrono::steady_clock::now();
     // keep freed state memory in the device's pool for the next request
     cudaMemPool_t pool;
@@ -245,8 +250,8 @@ extern "C" int sse_server_create(int device, size_t hbm_budget_bytes, int max_ac
 
 extern "C" int sse_server_submit(sse_server *S, const sse_mesh *mesh, const sse_params *params,
                                  const double *u, const double *h, const double *tracers,
-                                 int order, double dt, int n_substeps, int n_steps,
-                                 double *u_out, double *h_out, double *tracers_out,
+                                 const double *wind_stress, int order, double dt, int n_substeps,
+                                 int n_steps, double *u_out, double *h_out, double *tracers_out,
                                  int64_t *id_out) {
     if (!S || !mesh || !params || !u || !h || !tracers || !u_out || !h_out || !tracers_out ||
         !id_out || n_steps < 0 || (order != 2 && order != 3) || !(dt > 0.0) || n_substeps < 1 ||
@@ -256,8 +261,13 @@ extern "C" int sse_server_submit(sse_server *S, const sse_mesh *mesh, const sse_
     int rc = sse_mesh_dims(mesh, dims);
     if (rc) return rc;
     const int nCells = dims[0], nEdges = dims[1], nLayers = dims[3];
+    sse_tuning tun{};
+    if (S->tune >= 0) {
+        rc = sse_tune(mesh, params, S->tune, &tun);
+        if (rc) return rc;
+    }
     size_t fp = 0;
-    rc = sse_state_footprint(mesh, params, &fp);
+    rc = sse_state_footprint_ex(mesh, params, &tun, &fp);
     if (rc) return rc;
     if (fp > S->budget) return SSE_ERR_OOM;
     Req *r = new (std::nothrow) Req();
@@ -272,11 +282,13 @@ extern "C" int sse_server_submit(sse_server *S, const sse_mesh *mesh, const sse_
     r->nC = nCells;
     r->L = nLayers;
     r->footprint = fp;
+    r->tun = tun;
     const size_t EL = (size_t)nEdges * nLayers, CL = (size_t)nCells * nLayers;
     try {
         r->u.assign(u, u + EL);
         r->h.assign(h, h + CL);
         r->tr.assign(tracers, tracers + CL * params->nTracers);
+        if (wind_stress) r->wind.assign(wind_stress, wind_stress + nEdges);
     } catch (...) {
         delete r;
         return SSE_ERR_OOM;

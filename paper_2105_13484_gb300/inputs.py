@@ -185,3 +185,70 @@ def workload(name, *, seed=0, perturb=False, **override):
         m, L, p, st = channel_case(w.pop("nx"), w.pop("ny"), w.pop("dc"), w.pop("L"), seed=seed,
                                    perturb=perturb, **w)
     return m, L, p, st, run
+
+
+# ----------------------------------------------------------------------------
+# ensembles and request streams (specifications only; meshes and states are
+# built from them with the generators above)
+# ----------------------------------------------------------------------------
+def planar_shape(n_cells, rng):
+    """(nx, ny) of a channel with about n_cells ocean cells, ny even."""
+    aspect = rng.uniform(0.5, 2.0)
+    nx = max(8, int(round(math.sqrt(n_cells * aspect))))
+    ny = max(8, int(round(n_cells / nx)))
+    ny += ny % 2
+    return nx, ny
+
+
+def ensemble_members(n=64, seed=0, size_classes=8, cells=(2000, 60000), layers=(10, 40),
+                     substeps=(20, 40), steps=100):
+    """Batched-ensemble members: planar channels with seeded sizes (log-uniform
+    in `cells`, drawn once per size class and shared by the members of the
+    class), seeded layer counts, fronts, dt and sub-step counts; SSPRK3-SE,
+    mixed precision, `steps` large steps each."""
+    rng = np.random.default_rng(seed)
+    shapes = [planar_shape(int(math.exp(rng.uniform(math.log(cells[0]), math.log(cells[1])))), rng)
+              for _ in range(size_classes)]
+    out = []
+    for k in range(n):
+        nx, ny = shapes[k % size_classes]
+        out.append(dict(kind="planar", nx=nx, ny=ny, dc=5e3,
+                        L=int(rng.integers(layers[0], layers[1] + 1)),
+                        order=3, dt=float(rng.choice([90.0, 120.0, 150.0])),
+                        M=int(rng.integers(substeps[0], substeps[1] + 1)), steps=steps,
+                        seed=int(rng.integers(1 << 30))))
+    return out
+
+
+def serving_requests(n=16, seed=0, rate=20.0, cells=(2000, 60000), levels=(5, 6),
+                     layers=(10, 60), horizon=(20, 100)):
+    """A Poisson stream of solves: arrival times with mean rate `rate` per
+    second, each an SSPRK2-SE or SSPRK3-SE solve on a planar channel (cells
+    log-uniform in `cells`) or a geodesic sphere of a level in `levels`, with
+    a seeded layer count and horizon."""
+    rng = np.random.default_rng(seed)
+    t = 0.0
+    out = []
+    for _ in range(n):
+        t += float(rng.exponential(1.0 / rate))
+        order = int(rng.choice([2, 3]))
+        L = int(rng.integers(layers[0], layers[1] + 1))
+        steps = int(rng.integers(horizon[0], horizon[1] + 1))
+        if rng.random() < 0.5:
+            nx, ny = planar_shape(int(math.exp(rng.uniform(math.log(cells[0]),
+                                                           math.log(cells[1])))), rng)
+            spec = dict(kind="planar", nx=nx, ny=ny, dc=5e3, dt=120.0, M=20)
+        else:
+            lev = int(rng.integers(levels[0], levels[1] + 1))
+            spec = dict(kind="sphere", level=lev, dt=1200.0 / 2 ** (lev - 5), M=40)
+        spec.update(L=L, order=order, steps=steps, arrival=t, seed=int(rng.integers(1 << 30)))
+        out.append(spec)
+    return out
+
+
+def build_spec(spec):
+    """(mesh, L, params, (u, h, tr)) for an ensemble member or request spec."""
+    if spec["kind"] == "sphere":
+        return sphere_case(spec["level"], spec["L"], seed=spec["seed"] % 7, perturb=True)
+    return channel_case(spec["nx"], spec["ny"], spec["dc"], spec["L"], beta=1.6e-11,
+                        seed=spec["seed"], perturb=True)

@@ -129,3 +129,43 @@ def test_concurrent_small_requests_overlap():
     makespan(4)                                           # warm up
     t1, t8 = makespan(1), makespan(8)
     assert t8 < t1 / 1.3, (t1, t8)
+
+
+def _rel(a, b):
+    return np.linalg.norm(a - b) / np.linalg.norm(b)
+
+
+def test_patch_size_keeps_results_within_rounding_and_the_tuner_picks_a_candidate():
+    """The partition of the tiled sub-cycle only changes which code path (an
+    owned or a halo copy of an edge) rounds a value first, so results with 2,
+    7 or 28 patches agree to the mixed form's rounding, far inside its error
+    bounds against the oracle (u 1e-4, h 1e-9, tracers 1e-6)."""
+    m, L, p, (u, h, tr), run = inputs.workload("sphere_l4", perturb=True)
+    dm = binding.Mesh(m, L)
+    outs, patches = [], []
+    for pc in (0, 256, 2000):
+        st = binding.State(dm, p, "mixed", patch_cells=pc)
+        patches.append(st.patches())
+        st.load_state(u, h, tr)
+        st.step(3, run["dt"], run["M"], 3)
+        outs.append(st.read_state())
+        st.close()
+    assert len(set(patches)) == 3 and min(patches) >= 1
+    for o in outs[1:]:
+        assert _rel(o[0], outs[0][0]) < 1e-5
+        assert _rel(o[1], outs[0][1]) < 1e-10
+        assert _rel(o[2], outs[0][2]) < 1e-7
+    for obj in ("latency", "throughput"):
+        pc = binding.tune(dm, p, "mixed", obj)
+        assert pc in (64, 128, 256, 384, 512, 768, 1024, 1536)
+    # a server that tunes for throughput: bit-identical to a state with its patch size
+    pc = binding.tune(dm, p, "mixed", "throughput")
+    srv = binding.Server(hbm_budget=4 << 30, max_active=4, tune="throughput")
+    r = srv.submit(dm, p, "mixed", u, h, tr, 3, run["dt"], run["M"], 3)
+    assert r.wait(120)["status"] == "done"
+    srv.close()
+    st = binding.State(dm, p, "mixed", patch_cells=pc)
+    st.load_state(u, h, tr)
+    st.step(3, run["dt"], run["M"], 3)
+    for a, b in zip(st.read_state(), (r.u, r.h, r.tr)):
+        assert np.array_equal(a, b)
