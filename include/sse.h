@@ -120,6 +120,8 @@ typedef struct {
     double kappa_h, kappa_v; /* tracer diffusivities (m^2 s^-1)               */
     double c_drag;      /* quadratic bottom-drag coefficient                  */
     double eos_rho_ref, eos_alpha, eos_beta, eos_T_ref, eos_S_ref;
+    double nu_4;        /* biharmonic viscosity (m^4 s^-1): -nu_4 del^4 u in T^u, the
+                           hyperviscosity of the paper's global setup (Sec. 2)  */
 } sse_params;
 
 /* Global diagnostics, reduced on the device in a fixed order (FP64). */
@@ -190,7 +192,8 @@ int sse_kernels_per_step(const sse_state *state, int order);
 #define SSE_K_TRANSPORT 5   /* Sec. 3.4 adjustment and edge mass flux         */
 #define SSE_K_THICKNESS 6   /* thickness and tracer stage                     */
 #define SSE_K_COMBINE 7     /* Interp_2 / Interp_3 forcing combination        */
-#define SSE_K_NCLASS 8
+#define SSE_K_DEL4 8        /* div and curl of del^2 u (biharmonic viscosity)  */
+#define SSE_K_NCLASS 9
 /* enable != 0 starts recording an event pair around every launch of sse_step
  * (and clears earlier records); enable == 0 stops recording. */
 int sse_profile(sse_state *state, int enable);

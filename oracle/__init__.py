@@ -51,7 +51,8 @@ class _Params(ct.Structure):
     _fields_ = [("nTracers", ct.c_int), ("recon", ct.c_int)] + [
         (n, ct.c_double) for n in ("g", "rho0", "nu_h", "nu_v", "kappa_h", "kappa_v", "c_drag",
                                    "eos_rho_ref", "eos_alpha", "eos_beta", "eos_T_ref",
-                                   "eos_S_ref")] + [("windStress", _dp), ("vmix", ct.c_int)]
+                                   "eos_S_ref")] + [("windStress", _dp), ("vmix", ct.c_int),
+                                                     ("nu_4", ct.c_double)]
 
 
 class _Aux(ct.Structure):
@@ -63,7 +64,7 @@ RECON = {"off": 0, "paper": 1, "consistent": 2}
 
 DEFAULT_PARAMS = dict(nTracers=1, recon="consistent", g=9.80616, rho0=1000.0, nu_h=0.0, nu_v=0.0,
                       kappa_h=0.0, kappa_v=0.0, c_drag=0.0, eos_rho_ref=1000.0, eos_alpha=0.2,
-                      eos_beta=0.8, eos_T_ref=10.0, eos_S_ref=35.0, windStress=None, vmix=0)
+                      eos_beta=0.8, eos_T_ref=10.0, eos_S_ref=35.0, windStress=None, vmix=0, nu_4=0.0)
 
 
 def _d(a):
@@ -119,12 +120,14 @@ class Oracle:
             wsp = None
         self.p = _Params(self.nT, recon, *[float(q[n]) for n in (
             "g", "rho0", "nu_h", "nu_v", "kappa_h", "kappa_v", "c_drag", "eos_rho_ref",
-            "eos_alpha", "eos_beta", "eos_T_ref", "eos_S_ref")], wsp, int(bool(q.get("vmix", 0))))
+            "eos_alpha", "eos_beta", "eos_T_ref", "eos_S_ref")], wsp, int(bool(q.get("vmix", 0))),
+            float(q.get("nu_4", 0.0)))
 
     def _sig(self):
         L = self.lib
         for n in ("om_div", "om_grad", "om_curl", "om_tangential", "om_kinetic_energy",
-                  "om_laplacian", "om_coriolis", "om_edge_thickness", "om_vertex_thickness"):
+                  "om_laplacian", "om_biharmonic", "om_coriolis", "om_edge_thickness",
+                  "om_vertex_thickness"):
             getattr(L, n).argtypes = [ct.c_void_p, ct.c_int, _dp, _dp]
         L.om_pv_flux.argtypes = [ct.c_void_p, ct.c_int, _dp, _dp, _dp]
         L.om_sse_step.restype = ct.c_int
@@ -169,6 +172,9 @@ class Oracle:
 
     def laplacian(self, u):
         return self._wrap("om_laplacian", u, self.E)
+
+    def biharmonic(self, u):
+        return self._wrap("om_biharmonic", u, self.E)
 
     def coriolis(self, x):
         return self._wrap("om_coriolis", x, self.E)

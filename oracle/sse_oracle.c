@@ -122,6 +122,16 @@ void om_laplacian(const om_mesh *m, int L, const double *u, double *out) {
     free(omega);
 }
 
+/* del^4 u: the vector Laplacian applied twice (the hyperviscosity that
+ * replaces nu_h del^2 u in the global setup, Sec. 2 remark on horizontal
+ * dissipation) */
+void om_biharmonic(const om_mesh *m, int L, const double *u, double *out) {
+    double *l1 = vec((size_t)m->nEdges * L);
+    om_laplacian(m, L, u, l1);
+    om_laplacian(m, L, l1, out);
+    free(l1);
+}
+
 /* Coriolis tendency of a velocity x: normal component of -f k x x, in the
  * energy-neutral TRiSK form C_f(x)_e = (1/d_e) sum_{e'} w l_{e'} x_{e'} (f_e+f_{e'})/2 */
 void om_coriolis(const om_mesh *m, int L, const double *x, double *out) {
@@ -315,7 +325,7 @@ static void baroclinic_rhs(const om_mesh *m, const om_params *p, const double *u
     double *Q = vec(EL), *Cu = vec(EL), *Cut = vec(EL), *K = vec(CL), *gK = vec(EL);
     double *rho = vec(CL), *pres = vec(CL), *zmid = vec(CL), *gp = vec(EL), *gz = vec(EL);
     double *lap = vec(EL), *he = vec(EL), *w = vec((size_t)m->nCells * (L + 1));
-    double *utan = vec(EL), *gzeta = vec(m->nEdges);
+    double *utan = vec(EL), *gzeta = vec(m->nEdges), *del4 = vec(EL);
 
     om_pv_flux(m, L, u, h, Q);
     om_coriolis(m, L, u, Cu);
@@ -327,6 +337,7 @@ static void baroclinic_rhs(const om_mesh *m, const om_params *p, const double *u
     om_grad(m, L, pres, gp);
     om_grad(m, L, zmid, gz);
     om_laplacian(m, L, u, lap);
+    if (p->nu_4 != 0.0) om_biharmonic(m, L, u, del4);
     om_edge_thickness(m, L, h, he);
     om_vertical_velocity(m, h, u, w);
     om_tangential(m, L, u, utan);
@@ -364,11 +375,11 @@ static void baroclinic_rhs(const om_mesh *m, const om_params *p, const double *u
             double rho_e = 0.5 * (rho[(size_t)c1 * L + k] + rho[(size_t)c2 * L + k]);
             double pgf = (gp[x] + p->g * rho_e * gz[x]) / p->rho0;
             rhs[x] = Cut[x] + (Q[x] - Cu[x]) - gK[x] - pgf - vadv + p->nu_h * lap[x] + vvisc +
-                     p->g * gzeta[e];
+                     p->g * gzeta[e] - p->nu_4 * del4[x];
         }
     }
     free(Q); free(Cu); free(Cut); free(K); free(gK); free(rho); free(pres); free(zmid);
-    free(gp); free(gz); free(lap); free(he); free(w); free(utan); free(gzeta);
+    free(gp); free(gz); free(lap); free(he); free(w); free(utan); free(gzeta); free(del4);
 }
 
 /* Algorithm 1, Baroclinic_FEuler(u, ut, zeta, h, dt) -> (ut1, G) */

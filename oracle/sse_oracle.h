@@ -44,6 +44,7 @@ typedef struct {
     double eos_rho_ref, eos_alpha, eos_beta, eos_T_ref, eos_S_ref;
     const double *windStress; /* [E] normal wind stress (N m^-2) or NULL */
     int vmix;              /* 1: Algorithm 2 (implicit vertical mixing) in every stage */
+    double nu_4;           /* biharmonic viscosity: -nu_4 del^4 u in T^u (m^4 s^-1) */
 } om_params;
 
 /* optional per-step records for the tests (NULL members are skipped) */
@@ -61,6 +62,8 @@ void om_curl(const om_mesh *m, int L, const double *u, double *out);
 void om_tangential(const om_mesh *m, int L, const double *u, double *out);
 void om_kinetic_energy(const om_mesh *m, int L, const double *u, double *out);
 void om_laplacian(const om_mesh *m, int L, const double *u, double *out);
+/* del^4 u = Laplacian of the Laplacian (the hyperviscosity operator) */
+void om_biharmonic(const om_mesh *m, int L, const double *u, double *out);
 void om_coriolis(const om_mesh *m, int L, const double *x, double *out);
 void om_edge_thickness(const om_mesh *m, int L, const double *h, double *out);
 void om_vertex_thickness(const om_mesh *m, int L, const double *h, double *out);

@@ -49,7 +49,7 @@ class Params(ct.Structure):
                 ("options", ct.c_int32)] + [
         (n, ct.c_double) for n in ("g", "rho0", "nu_h", "nu_v", "kappa_h", "kappa_v", "c_drag",
                                    "eos_rho_ref", "eos_alpha", "eos_beta", "eos_T_ref",
-                                   "eos_S_ref")]
+                                   "eos_S_ref", "nu_4")]
 
 
 class Tuning(ct.Structure):
@@ -88,7 +88,7 @@ EXPORTS = ["sse_mesh_create", "sse_mesh_destroy", "sse_state_create", "sse_state
            "sse_mesh_dims", "sse_server_create", "sse_server_submit", "sse_server_query",
            "sse_server_wait", "sse_server_stats", "sse_server_destroy", "sse_strerror"]
 KERNEL_CLASSES = ["cell_diag", "vertex", "edge_pre", "bcl_edge", "btr", "transport", "thickness",
-                  "combine"]
+                  "combine", "del4"]
 
 _lib = None
 
@@ -222,7 +222,7 @@ def make_params(params: dict, precision="fp64") -> Params:
     return Params(prec, recon, int(q.get("nTracers", 1)), options, *[float(q.get(n, d)) for n, d in (
         ("g", 9.80616), ("rho0", 1000.0), ("nu_h", 0.0), ("nu_v", 0.0), ("kappa_h", 0.0),
         ("kappa_v", 0.0), ("c_drag", 0.0), ("eos_rho_ref", 1000.0), ("eos_alpha", 0.2),
-        ("eos_beta", 0.8), ("eos_T_ref", 10.0), ("eos_S_ref", 35.0))])
+        ("eos_beta", 0.8), ("eos_T_ref", 10.0), ("eos_S_ref", 35.0), ("nu_4", 0.0))])
 
 
 class State:

@@ -280,6 +280,7 @@ struct EngineBase {
     virtual int bcl_feuler(double dt) = 0;
     virtual int btr_substep(int order, double dt, int M) = 0;
     virtual int patches() const = 0;       // tiled sub-cycle patches (0: global kernel)
+    virtual bool has_del4() const = 0;     // biharmonic viscosity on
     virtual int diagnostics(sse_diag *out) = 0;
     long long steps = 0;
 
@@ -531,6 +532,7 @@ struct Engine : EngineBase {
         vmix = (prm->options & SSE_OPT_VMIX) != 0;
         p.g = prm->g; p.rho0 = prm->rho0; p.nu_h = prm->nu_h; p.nu_v = prm->nu_v;
         p.kappa_h = prm->kappa_h; p.kappa_v = prm->kappa_v; p.c_drag = prm->c_drag;
+        p.nu_4 = prm->nu_4;
         p.alpha = prm->eos_alpha; p.beta = prm->eos_beta; p.T_ref = prm->eos_T_ref;
         p.S_ref = prm->eos_S_ref; p.zcoef = prm->g * (1.0 - prm->eos_rho_ref / prm->rho0);
         p.nT = prm->nTracers; p.recon = prm->recon; p.wind = nullptr; p.wind_f = nullptr;
@@ -562,6 +564,10 @@ struct Engine : EngineBase {
         db.pp = A.alloc<R>(CL); db.zm = A.alloc<R>(CL); db.w = A.alloc<R>(CL);
         db.omega = A.alloc<R>(VL); db.q = A.alloc<R>(VL);
         db.hu = A.alloc<R>(EL); db.qe = A.alloc<R>(EL);
+        db.del2 = db.delta2 = db.omega2 = nullptr;
+        if (p.nu_4 > 0.0) {
+            db.del2 = A.alloc<R>(EL); db.delta2 = A.alloc<R>(CL); db.omega2 = A.alloc<R>(VL);
+        }
         bu0 = A.alloc<R>(m.Ep); bua = A.alloc<R>(m.Ep); buh = A.alloc<R>(m.Ep);
         bz0 = A.alloc<R>(m.Cp); bza = A.alloc<R>(m.Cp); bzh = A.alloc<R>(m.Cp);
         barwords = A.alloc<unsigned int>(2);
@@ -600,6 +606,7 @@ struct Engine : EngineBase {
     template <class T> void fill_phys(PhysR<T> &q) const {
         q.g = (T)p.g; q.inv_rho0 = (T)(1.0 / p.rho0); q.nu_h = (T)p.nu_h; q.nu_v = (T)p.nu_v;
         q.kappa_h = (T)p.kappa_h; q.kappa_v = (T)p.kappa_v; q.c_drag = (T)p.c_drag;
+        q.nu_4 = (T)p.nu_4;
         q.alpha = (T)p.alpha; q.beta = (T)p.beta; q.T_ref = (T)p.T_ref; q.S_ref = (T)p.S_ref;
         q.zcoef = (T)p.zcoef;
     }
@@ -733,6 +740,11 @@ struct Engine : EngineBase {
         pbeg(SSE_K_EDGE_PRE);
         launch_edge_pre<R>(m, ubar, ut, hR, db, split, s);
         pend();
+        if (db.del2) {
+            pbeg(SSE_K_DEL4);
+            launch_del2_divcurl<R>(m, db, s);
+            pend();
+        }
         pbeg(SSE_K_BCL_EDGE);
         // Algorithm 2 keeps its modified super-diagonal in `flux`, which is
         // free until the stage's transport kernel writes it
@@ -846,6 +858,7 @@ struct Engine : EngineBase {
     }
 
     int patches() const override { return tiled ? tiles.P : 0; }
+    bool has_del4() const override { return db.del2 != nullptr; }
 
     int btr_substep(int order, double dt, int M) override {
         launch_ssh(m, h_n, zeta_n, s);
@@ -903,7 +916,8 @@ static bool params_ok(const sse_params *prm) {
              prm->recon > 2 || prm->nTracers < 1 || prm->nTracers > 2 ||
              (prm->options & ~SSE_OPT_VMIX) != 0 || !(prm->g > 0) || !(prm->rho0 > 0) ||
              !(prm->nu_h >= 0) || !(prm->nu_v >= 0) || !(prm->kappa_h >= 0) ||
-             !(prm->kappa_v >= 0) || !(prm->c_drag >= 0) || !isfinite(prm->eos_rho_ref) ||
+             !(prm->kappa_v >= 0) || !(prm->c_drag >= 0) || !(prm->nu_4 >= 0) ||
+             !isfinite(prm->nu_4) || !isfinite(prm->eos_rho_ref) ||
              !isfinite(prm->eos_alpha) || !isfinite(prm->eos_beta) || !isfinite(prm->eos_T_ref) ||
              !isfinite(prm->eos_S_ref));
 }
@@ -1113,8 +1127,10 @@ extern "C" int sse_diagnostics(sse_state *st, sse_diag *out) {
 
 extern "C" int sse_kernels_per_step(const sse_state *st, int order) {
     if (!st) return SSE_ERR_INVALID_ARG;
-    // 4 per baroclinic stage, 1 per sub-cycle, 2 per thickness stage, 1 forcing combination
-    return order == 2 ? 2 * 4 + 2 + 2 * 2 + 1 : 3 * 4 + 3 + 3 * 2 + 1;
+    // 4 per baroclinic stage (5 with biharmonic viscosity), 1 per sub-cycle,
+    // 2 per thickness stage, 1 forcing combination
+    const int bcl = 4 + (st->eng->has_del4() ? 1 : 0);
+    return order == 2 ? 2 * bcl + 2 + 2 * 2 + 1 : 3 * bcl + 3 + 3 * 2 + 1;
 }
 
 extern "C" int sse_profile(sse_state *st, int enable) {

@@ -55,13 +55,13 @@ template <> __host__ __device__ inline const Coef<float> &coef<float>(const DMes
 
 // physical constants in one precision (converted once on the host)
 template <class R> struct PhysR {
-    R g, inv_rho0, nu_h, nu_v, kappa_h, kappa_v, c_drag;
+    R g, inv_rho0, nu_h, nu_v, kappa_h, kappa_v, c_drag, nu_4;
     R alpha, beta, T_ref, S_ref;  // rho' = rho - rho_ref = -alpha (T - T_ref) + beta (S - S_ref)
     R zcoef;                      // g (1 - rho_ref / rho0)
 };
 
 struct DParams {
-    double g, rho0, nu_h, nu_v, kappa_h, kappa_v, c_drag;
+    double g, rho0, nu_h, nu_v, kappa_h, kappa_v, c_drag, nu_4;
     double alpha, beta, T_ref, S_ref;
     double zcoef;                      // g (1 - rho_ref / rho0)
     int nT, recon;
@@ -90,6 +90,9 @@ template <class R> struct DiagBufs {
     R *ke, *delta, *rhop, *pp, *zm, *w;  // [L][Cp]
     R *omega, *q;                        // [L][Vp]
     R *hu, *qe;                          // [L][Ep]
+    // biharmonic viscosity only (nullptr otherwise): del^2 u on edges, its
+    // divergence on cells and its curl on vertices
+    R *del2, *delta2, *omega2;
 };
 
 // hR is the stage thickness in the tendency precision (the FP64 array itself
@@ -100,6 +103,8 @@ void launch_cell_diag(const DMesh &m, const DParams &p, const R *ubar, const R *
 template <class R>
 void launch_vertex(const DMesh &m, const R *ubar, const R *ut, const R *hR,
                    const DiagBufs<R> &b, cudaStream_t s);
+template <class R>
+void launch_del2_divcurl(const DMesh &m, const DiagBufs<R> &b, cudaStream_t s);
 template <class R>
 void launch_edge_pre(const DMesh &m, R *ubar, R *ut, const R *hR, const DiagBufs<R> &b,
                      bool split, cudaStream_t s);

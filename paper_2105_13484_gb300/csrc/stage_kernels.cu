@@ -140,6 +140,8 @@ __global__ void __launch_bounds__(128) k_edge_pre(DMesh m, R *__restrict__ ubar,
     if (e >= m.E) return;
     const int Ep = m.Ep, Cp = m.Cp, Vp = m.Vp;
     const int2 cc = m.coe[e], vv = m.voe[e];
+    const Coef<R> &c = coef<R>(m);
+    const R invdc = c.invdc[e], invdv = c.invdv[e];
     R ub = ubar[e];
     R mean = R(0);
     if (split) {
@@ -163,6 +165,50 @@ __global__ void __launch_bounds__(128) k_edge_pre(DMesh m, R *__restrict__ ubar,
         const R he = R(0.5) * (ld(hR + k * Cp + cc.x) + ld(hR + k * Cp + cc.y));
         b.hu[x] = he * (ub + utk);
         b.qe[x] = R(0.5) * (b.q[k * Vp + vv.x] + b.q[k * Vp + vv.y]);
+        if (b.del2)   // del^2 u = grad(div u) - k x grad(curl u), normal component
+            b.del2[x] = (b.delta[k * Cp + cc.y] - b.delta[k * Cp + cc.x]) * invdc -
+                        (b.omega[k * Vp + vv.y] - b.omega[k * Vp + vv.x]) * invdv;
+    }
+}
+
+// Divergence (cells, items [0, C)) and curl (vertices, items [C, C + V)) of
+// del^2 u, the inputs of del^4 u = del^2(del^2 u) in the baroclinic kernel.
+template <class R, int NCE>
+__global__ void __launch_bounds__(128) k_del2_divcurl(DMesh m, DiagBufs<R> b) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    const Coef<R> &c = coef<R>(m);
+    const int Cp = m.Cp, Ep = m.Ep, Vp = m.Vp, L = m.L;
+    if (t < m.C) {
+        const int i = t, ne = m.neoc[i];
+        int es[NCE];
+        R dcf[NCE];
+#pragma unroll
+        for (int j = 0; j < NCE; j++) {
+            es[j] = j < ne ? m.eoc[j * Cp + i] : 0;
+            dcf[j] = j < ne ? c.divc[j * Cp + i] : R(0);
+        }
+        for (int k = 0; k < L; k++) {
+            R d = R(0);
+#pragma unroll
+            for (int j = 0; j < NCE; j++)
+                if (j < ne) d += dcf[j] * ld(b.del2 + k * Ep + es[j]);
+            b.delta2[k * Cp + i] = d;
+        }
+    } else if (t < m.C + m.V) {
+        const int v = t - m.C;
+        int e[3];
+        R cc[3];
+#pragma unroll
+        for (int j = 0; j < 3; j++) {
+            e[j] = m.eov[j * Vp + v];
+            cc[j] = c.curlc[j * Vp + v];
+        }
+        for (int k = 0; k < L; k++) {
+            R om = R(0);
+#pragma unroll
+            for (int j = 0; j < 3; j++) om += cc[j] * ld(b.del2 + k * Ep + e[j]);
+            b.omega2[k * Vp + v] = om;
+        }
     }
 }
 
@@ -215,7 +261,7 @@ __global__ void __launch_bounds__(128, 8) k_bcl_edge(DMesh m, DParams p, const R
     const R ub = ubar[e];
     const PhysR<R> &q = phys<R>(p);
     const R gzeta = q.zcoef * (R)(zeta[c2] - zeta[c1]) * invdc;
-    const R g = q.g, inv_rho0 = q.inv_rho0, nu_h = q.nu_h, nu_v = q.nu_v;
+    const R g = q.g, inv_rho0 = q.inv_rho0, nu_h = q.nu_h, nu_v = q.nu_v, nu_4 = q.nu_4;
     const R cdrag = q.c_drag;
     const R *wnd = wind_over_rho0<R>(p);
     const R wind = wnd ? wnd[e] : R(0);
@@ -270,7 +316,10 @@ __global__ void __launch_bounds__(128, 8) k_bcl_edge(DMesh m, DParams p, const R
         const R vvisc = VMIX ? R(0) : (Xtop - Xbot) / he_cur;
         const R lap = (b.delta[x2] - b.delta[x1]) * invdc -
                       (b.omega[k * Vp + v2] - b.omega[k * Vp + v1]) * invdv;
-        const R rhs = (Q - cbar) - gradK - pgf - vadv + nu_h * lap + vvisc + gzeta;
+        R rhs = (Q - cbar) - gradK - pgf - vadv + nu_h * lap + vvisc + gzeta;
+        if (b.del2)
+            rhs -= nu_4 * ((b.delta2[x2] - b.delta2[x1]) * invdc -
+                           (b.omega2[k * Vp + v2] - b.omega2[k * Vp + v1]) * invdv);
         const R ut1 = ut_cur + dt * rhs;
         num += he_cur * ut1;
         den += he_cur;
@@ -608,6 +657,13 @@ void launch_vertex(const DMesh &m, const R *ubar, const R *ut, const R *hR, cons
     k_vertex<R><<<nblk(m.V, 128), 128, 0, s>>>(m, ubar, ut, hR, b);
 }
 template <class R>
+void launch_del2_divcurl(const DMesh &m, const DiagBufs<R> &b, cudaStream_t s) {
+    if (m.maxE <= 6)
+        k_del2_divcurl<R, 6><<<nblk(m.C + m.V, 128), 128, 0, s>>>(m, b);
+    else
+        k_del2_divcurl<R, MAXE><<<nblk(m.C + m.V, 128), 128, 0, s>>>(m, b);
+}
+template <class R>
 void launch_edge_pre(const DMesh &m, R *ubar, R *ut, const R *hR, const DiagBufs<R> &b,
                      bool split, cudaStream_t s) {
     k_edge_pre<R><<<nblk(m.E, 128), 128, 0, s>>>(m, ubar, ut, hR, b, split ? 1 : 0);
@@ -679,6 +735,7 @@ void launch_diag(const DMesh &m, const R *ubar, const R *ut, const double *h, co
                                       const R *, const R *, const DiagBufs<R> &, cudaStream_t);  \
     template void launch_vertex<R>(const DMesh &, const R *, const R *, const R *,               \
                                    const DiagBufs<R> &, cudaStream_t);                           \
+    template void launch_del2_divcurl<R>(const DMesh &, const DiagBufs<R> &, cudaStream_t);      \
     template void launch_edge_pre<R>(const DMesh &, R *, R *, const R *, const DiagBufs<R> &,    \
                                      bool, cudaStream_t);                                        \
     template void launch_bcl_edge<R>(const DMesh &, const DParams &, const R *, const R *,       \

@@ -137,8 +137,9 @@ class DenseScheme:
         speed = np.sqrt(u[:, -1] ** 2 + (self.Perp @ u[:, -1]) ** 2)
         X[:, L] = p["c_drag"] * speed * u[:, -1]
         vvisc = (X[:, :L] - X[:, 1:]) / he
+        bih = self.Lap @ (self.Lap @ u)                       # del^4 u
         return (Cut + (Q - Cu) - self.Grad @ K - pgf - vadv + p["nu_h"] * (self.Lap @ u) + vvisc
-                + g * (self.Grad @ zeta)[:, None])
+                + g * (self.Grad @ zeta)[:, None] - p.get("nu_4", 0.0) * bih)
 
     def alg1(self, u, ut, zeta, h, tr, dt):
         ut1 = ut + dt * self.rhs(u, ut, zeta, h, tr)

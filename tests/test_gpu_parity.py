@@ -348,3 +348,22 @@ def test_full_step_vertical_mixing(order):
     st.step(order, 300.0, 10, 5)
     gu, gh, gt = st.read_state()
     assert rel(gu, ref[0]) < 1e-4 and rel(gt, ref[2]) < 1e-6
+
+
+@pytest.mark.parametrize("order", [2, 3])
+def test_full_step_biharmonic_viscosity(order):
+    """-nu_4 del^4 u (with Laplacian viscosity and walls) on a 12 x 14 channel."""
+    m, L, p, (u, h, tr) = inputs.channel_case(12, 14, 10e3, 6, perturb=True, beta=2e-11,
+                                              nu_h=20.0, nu_4=2e10)
+    o = oracle.Oracle(m, L, p)
+    ref = o.step(order, 200.0, 10, u, h, tr, n_steps=4)
+    ref0 = oracle.Oracle(m, L, dict(p, nu_4=0.0)).step(order, 200.0, 10, u, h, tr, n_steps=4)
+    assert rel(ref[0], ref0[0]) > 1e-4          # the term matters at this nu_4
+    dm, st = _gpu(m, L, p, u, h, tr)
+    assert st.kernels_per_step(order) == (17 if order == 2 else 25)   # + 1 per stage
+    st.step(order, 200.0, 10, 4)
+    _compare(st.read_state(), ref, TOL64)
+    dm, st = _gpu(m, L, p, u, h, tr, "mixed")
+    st.step(order, 200.0, 10, 4)
+    gu, gh, gt = st.read_state()
+    assert rel(gu, ref[0]) < 1e-4 and rel(gt, ref[2]) < 1e-6

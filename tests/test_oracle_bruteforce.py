@@ -3,7 +3,8 @@ SSPRK3-SE steps equal a second FP64 implementation written with dense
 operator matrices (tests/dense_scheme.py), which shares no code with it.
 
 Every term is switched on (beta plane, bathymetry, walls, T and S, wind
-stress, bottom drag, horizontal and vertical viscosity and diffusion), so a
+stress, bottom drag, horizontal, biharmonic and vertical viscosity and
+diffusion), so a
 dropped term, a wrong sign, a wrong index or a transposed operand in either
 implementation shows up as a mismatch far above rounding.
 """
@@ -36,7 +37,7 @@ def tiny_case(kind, L, seed):
     S = 35 + 0.5 * rng.standard_normal((C, L))
     p = dict(inputs.PHYS)
     p.update(nTracers=2, nu_h=40.0, nu_v=1e-2, kappa_h=30.0, kappa_v=5e-3, c_drag=2e-3,
-             windStress=0.1 * rng.standard_normal(E))
+             nu_4=1e12, windStress=0.1 * rng.standard_normal(E))
     return m, L, p, (u, h, np.stack([T, S]))
 
 

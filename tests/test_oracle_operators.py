@@ -160,3 +160,34 @@ def test_vertex_thickness_uniform(channel):
     o = oracle.Oracle(m, 2)
     h = np.full((m.nCells, 2), 37.5)
     assert np.allclose(o.vertex_thickness(h), 37.5, rtol=1e-15)
+
+
+def test_biharmonic_of_gradient_mode_is_lambda_squared(torus):
+    """del^4 (grad phi) = lambda^2 grad phi for a hex Fourier mode phi: the
+    vector Laplacian of a gradient field is grad(div), and div(grad phi) =
+    lambda phi exactly (closed form above)."""
+    m, o = torus
+    d = 5e3
+    Lx, Ly = 12 * d, 10 * d * np.sqrt(3) / 2
+    r = d * np.array([[np.cos(a), np.sin(a)] for a in np.arange(6) * np.pi / 3])
+    for kx, ky in ((2 * np.pi / Lx, 0.0), (4 * np.pi / Lx, 2 * np.pi / Ly)):
+        k = np.array([kx, ky])
+        phi = np.cos(m.xCell @ k)
+        lam = 2.0 / (3 * d * d) * np.sum(np.cos(r @ k) - 1.0)
+        u = o.grad(phi)
+        got = o.biharmonic(u)
+        assert np.abs(got - lam * lam * u).max() < 1e-11 * lam * lam * np.abs(u).max()
+
+
+def test_biharmonic_is_self_adjoint_and_dissipative(torus):
+    """<u, del^4 u> = <del^2 u, del^2 u> >= 0 in the l d inner product, for
+    any u (the Laplacian is symmetric there, so -nu_4 del^4 removes energy)."""
+    m, o = torus
+    rng = np.random.default_rng(7)
+    W = m.dvEdge * m.dcEdge
+    for _ in range(3):
+        u = rng.standard_normal(m.nEdges)
+        a = np.sum(W * u * o.biharmonic(u))
+        lu = o.laplacian(u)
+        b = np.sum(W * lu * lu)
+        assert b > 0 and abs(a - b) < 1e-12 * b
