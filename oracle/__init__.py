@@ -44,7 +44,8 @@ class _Mesh(ct.Structure):
                 ("nEdgesOnEdge", _ip), ("edgesOnEdge", _ip), ("weightsOnEdge", _dp),
                 ("dcEdge", _dp), ("dvEdge", _dp), ("areaCell", _dp), ("areaTriangle", _dp),
                 ("kiteAreasOnVertex", _dp), ("fEdge", _dp), ("fVertex", _dp),
-                ("bottomDepth", _dp), ("restThicknessFrac", _dp)]
+                ("bottomDepth", _dp), ("restThicknessFrac", _dp), ("maxLevelCell", _ip),
+                ("restThickness", _dp)]
 
 
 class _Params(ct.Structure):
@@ -74,7 +75,10 @@ def _d(a):
 class Oracle:
     """FP64 oracle bound to one mesh, layer count and parameter set."""
 
-    def __init__(self, mesh, nLayers: int, params: dict | None = None, rest_frac=None):
+    def __init__(self, mesh, nLayers: int, params: dict | None = None, rest_frac=None,
+                 max_level=None, rest_thickness=None):
+        """max_level [C] / rest_thickness [C, L]: partial bottom cells (both or
+        neither; without them every column has all layers)."""
         self.lib = ct.CDLL(build())
         self._sig()
         self.L = int(nLayers)
@@ -101,7 +105,9 @@ class Oracle:
                        ia(mesh.nEdgesOnEdge), ia(mesh.edgesOnEdge), da(mesh.weightsOnEdge),
                        da(mesh.dcEdge), da(mesh.dvEdge), da(mesh.areaCell), da(mesh.areaTriangle),
                        da(mesh.kiteAreasOnVertex), da(mesh.fEdge), da(mesh.fVertex),
-                       da(mesh.bottomDepth), da(self.rest_frac))
+                       da(mesh.bottomDepth), da(self.rest_frac),
+                       None if max_level is None else ia(max_level),
+                       None if rest_thickness is None else da(rest_thickness))
         self.set_params(params or {})
 
     def set_params(self, params: dict):

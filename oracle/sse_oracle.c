@@ -35,6 +35,20 @@
 
 static double *vec(size_t n) { return (double *)calloc(n ? n : 1, sizeof(double)); }
 
+/* Partial bottom cells: a column i has kc(i) active layers; an edge is active
+ * in the layers both its cells have (maxLevelEdgeTop in MPAS); the z-star
+ * stretching of layer k of column i is its share of the column's rest
+ * thickness.  Inactive layers hold h = 0, u = 0 and no tracer. */
+static int kc(const om_mesh *m, int i) { return m->maxLevelCell ? m->maxLevelCell[i] : m->nLayers; }
+static int ke(const om_mesh *m, int e) {
+    int a = kc(m, C1(e)), b = kc(m, C2(e));
+    return a < b ? a : b;
+}
+static double sfr(const om_mesh *m, int i, int k) {
+    if (m->restThickness) return m->restThickness[(size_t)i * m->nLayers + k] / m->bottomDepth[i];
+    return m->restThicknessFrac[k];
+}
+
 /* ======================================================================== */
 /* TRiSK horizontal operators                                               */
 /* ======================================================================== */
@@ -147,14 +161,19 @@ void om_coriolis(const om_mesh *m, int L, const double *x, double *out) {
         }
 }
 
-/* centred edge thickness h_e = (h_c1 + h_c2)/2 */
+/* centred edge thickness h_e = (h_c1 + h_c2)/2, 0 in layers where the edge is
+ * not active (partial bottom cells) */
 void om_edge_thickness(const om_mesh *m, int L, const double *h, double *out) {
-    for (int e = 0; e < m->nEdges; e++)
+    for (int e = 0; e < m->nEdges; e++) {
+        int K = (L == m->nLayers) ? ke(m, e) : L;
         for (int k = 0; k < L; k++)
-            out[(size_t)e * L + k] = 0.5 * (h[(size_t)C1(e) * L + k] + h[(size_t)C2(e) * L + k]);
+            out[(size_t)e * L + k] =
+                k < K ? 0.5 * (h[(size_t)C1(e) * L + k] + h[(size_t)C2(e) * L + k]) : 0.0;
+    }
 }
 
-/* kite-area-weighted vertex thickness over the ocean cells of the vertex */
+/* kite-area-weighted vertex thickness over the ocean cells of the vertex that
+ * are active in the layer (0 where none is) */
 void om_vertex_thickness(const om_mesh *m, int L, const double *h, double *out) {
     for (int v = 0; v < m->nVertices; v++)
         for (int k = 0; k < L; k++) {
@@ -162,10 +181,11 @@ void om_vertex_thickness(const om_mesh *m, int L, const double *h, double *out) 
             for (int j = 0; j < 3; j++) {
                 int c = m->cellsOnVertex[3 * v + j];
                 if (c < 0) continue;
+                if (L == m->nLayers && k >= kc(m, c)) continue;
                 s += m->kiteAreasOnVertex[3 * v + j] * h[(size_t)c * L + k];
                 a += m->kiteAreasOnVertex[3 * v + j];
             }
-            out[(size_t)v * L + k] = s / a;
+            out[(size_t)v * L + k] = a > 0.0 ? s / a : 0.0;
         }
 }
 
@@ -182,8 +202,9 @@ void om_pv_flux(const om_mesh *m, int L, const double *u, const double *h, doubl
     for (int e = 0; e < m->nEdges; e++)
         for (int k = 0; k < L; k++) {
             int a = V1(e), b = V2(e);
-            double qa = (omega[(size_t)a * L + k] + m->fVertex[a]) / hv[(size_t)a * L + k];
-            double qb = (omega[(size_t)b * L + k] + m->fVertex[b]) / hv[(size_t)b * L + k];
+            double ha = hv[(size_t)a * L + k], hb = hv[(size_t)b * L + k];
+            double qa = ha > 0.0 ? (omega[(size_t)a * L + k] + m->fVertex[a]) / ha : 0.0;
+            double qb = hb > 0.0 ? (omega[(size_t)b * L + k] + m->fVertex[b]) / hb : 0.0;
             qe[(size_t)e * L + k] = 0.5 * (qa + qb);
         }
     for (int e = 0; e < m->nEdges; e++)
@@ -208,9 +229,10 @@ void om_pv_flux(const om_mesh *m, int L, const double *u, const double *h, doubl
 /* ======================================================================== */
 
 /* z-star vertical velocity at interfaces, w[i*(L+1) + k] (k = 0 surface,
- * k = L bottom), from the thickness equation (layerthickness) with
- * dh_k/dt = s_k * d(sum_l h_l)/dt, s_k = rest-thickness fraction:
- *   w_L = 0,  w_k = w_{k+1} - div(h_e v)_k + s_k sum_l div(h_e v)_l,  w_0 = 0. */
+ * k = K_i the column's bottom), from the thickness equation (layerthickness)
+ * with dh_k/dt = s_k * d(sum_l h_l)/dt, s_k = rest-thickness fraction:
+ *   w_K = 0,  w_k = w_{k+1} - div(h_e v)_k + s_k sum_l div(h_e v)_l,  w_0 = 0
+ * (w = 0 below the bottom). */
 void om_vertical_velocity(const om_mesh *m, const double *h, const double *v, double *w) {
     int L = m->nLayers;
     size_t EL = (size_t)m->nEdges * L, CL = (size_t)m->nCells * L;
@@ -219,12 +241,13 @@ void om_vertical_velocity(const om_mesh *m, const double *h, const double *v, do
     for (size_t x = 0; x < EL; x++) F[x] = he[x] * v[x];
     om_div(m, L, F, dv);
     for (int i = 0; i < m->nCells; i++) {
+        int K = kc(m, i);
         double tot = 0.0;
-        for (int k = 0; k < L; k++) tot += dv[(size_t)i * L + k];
+        for (int k = 0; k < K; k++) tot += dv[(size_t)i * L + k];
         double *wi = w + (size_t)i * (L + 1);
-        wi[L] = 0.0;
-        for (int k = L - 1; k >= 1; k--)
-            wi[k] = wi[k + 1] - dv[(size_t)i * L + k] + m->restThicknessFrac[k] * tot;
+        for (int k = K; k <= L; k++) wi[k] = 0.0;   /* the column's bottom and below */
+        for (int k = K - 1; k >= 1; k--)
+            wi[k] = wi[k + 1] - dv[(size_t)i * L + k] + sfr(m, i, k) * tot;
         wi[0] = 0.0;
     }
     free(he);
@@ -290,7 +313,8 @@ void om_split(const om_mesh *m, const double *u, const double *h, double *ubar, 
             den += he[(size_t)e * L + k];
         }
         ubar[e] = num / den;
-        for (int k = 0; k < L; k++) ut[(size_t)e * L + k] = u[(size_t)e * L + k] - ubar[e];
+        int K = ke(m, e);
+        for (int k = 0; k < L; k++) ut[(size_t)e * L + k] = k < K ? u[(size_t)e * L + k] - ubar[e] : 0.0;
     }
     free(he);
 }
@@ -344,17 +368,18 @@ static void baroclinic_rhs(const om_mesh *m, const om_params *p, const double *u
     om_grad(m, 1, zeta, gzeta);
 
     for (int e = 0; e < m->nEdges; e++) {
-        int c1 = C1(e), c2 = C2(e);
+        int c1 = C1(e), c2 = C2(e), K = ke(m, e);
         const double *ue = u + (size_t)e * L, *hee = he + (size_t)e * L;
-        /* interface values: D_zt(u)_k and w_k at the edge, k = 0..L */
-        for (int k = 0; k < L; k++) {
+        for (int k = K; k < L; k++) rhs[(size_t)e * L + k] = 0.0;   /* below the edge's bottom */
+        /* interface values: D_zt(u)_k and w_k at the edge, k = 0..K */
+        for (int k = 0; k < K; k++) {
             size_t x = (size_t)e * L + k;
             double Dk = 0.0, Dk1 = 0.0, wk = 0.0, wk1 = 0.0;
             if (k >= 1) {
                 Dk = (ue[k - 1] - ue[k]) / (0.5 * (hee[k - 1] + hee[k]));
                 wk = 0.5 * (w[(size_t)c1 * (L + 1) + k] + w[(size_t)c2 * (L + 1) + k]);
             }
-            if (k + 1 <= L - 1) {
+            if (k + 1 <= K - 1) {
                 Dk1 = (ue[k] - ue[k + 1]) / (0.5 * (hee[k] + hee[k + 1]));
                 wk1 = 0.5 * (w[(size_t)c1 * (L + 1) + k + 1] + w[(size_t)c2 * (L + 1) + k + 1]);
             }
@@ -365,7 +390,7 @@ static void baroclinic_rhs(const om_mesh *m, const om_params *p, const double *u
                 Xtop = p->windStress ? p->windStress[e] / p->rho0 : 0.0;
             else
                 Xtop = p->nu_v * Dk;
-            if (k == L - 1) {
+            if (k == K - 1) {
                 double speed = sqrt(ue[k] * ue[k] + utan[x] * utan[x]);
                 Xbot = p->c_drag * speed * ue[k];
             } else {
@@ -399,7 +424,8 @@ void om_baroclinic_feuler(const om_mesh *m, const om_params *p, const double *u,
             den += he[(size_t)e * L + k];
         }
         G[e] = num / den / dt;
-        for (int k = 0; k < L; k++) ut1[(size_t)e * L + k] -= dt * G[e];
+        int K = ke(m, e);
+        for (int k = 0; k < K; k++) ut1[(size_t)e * L + k] -= dt * G[e];
     }
     free(rhs);
     free(he);
@@ -422,11 +448,13 @@ void om_vertical_mixing_solve(const om_mesh *m, const om_params *p, const double
     om_tangential(m, L, u_drag, utan);
     for (int e = 0; e < m->nEdges; e++) {
         const double *hk = he + (size_t)e * L;
+        const int K = ke(m, e);   /* the edge's active layers */
+        for (int k = K; k < L; k++) x[(size_t)e * L + k] = 0.0;
         /* the matrix: lo_k x_{k-1} + di_k x_k + up_k x_{k+1} = rr_k */
-        for (int k = 0; k < L; k++) {
+        for (int k = 0; k < K; k++) {
             double a = 0.0, c = 0.0;
             if (k >= 1) a = dt * p->nu_v / (hk[k] * 0.5 * (hk[k - 1] + hk[k]));
-            if (k + 1 <= L - 1) c = dt * p->nu_v / (hk[k] * 0.5 * (hk[k] + hk[k + 1]));
+            if (k + 1 <= K - 1) c = dt * p->nu_v / (hk[k] * 0.5 * (hk[k] + hk[k + 1]));
             lo[k] = -a;
             up[k] = -c;
             di[k] = 1.0 + a + c;
@@ -434,21 +462,21 @@ void om_vertical_mixing_solve(const om_mesh *m, const om_params *p, const double
         }
         if (p->windStress) rr[0] += dt * p->windStress[e] / p->rho0 / hk[0];
         {
-            size_t xb = (size_t)e * L + (L - 1);
+            size_t xb = (size_t)e * L + (K - 1);
             double speed = sqrt(u_drag[xb] * u_drag[xb] + utan[xb] * utan[xb]);
-            di[L - 1] += dt * p->c_drag * speed / hk[L - 1];
+            di[K - 1] += dt * p->c_drag * speed / hk[K - 1];
         }
         /* forward elimination */
         cp[0] = up[0] / di[0];
         dp[0] = rr[0] / di[0];
-        for (int k = 1; k < L; k++) {
+        for (int k = 1; k < K; k++) {
             double den = di[k] - lo[k] * cp[k - 1];
             cp[k] = up[k] / den;
             dp[k] = (rr[k] - lo[k] * dp[k - 1]) / den;
         }
         /* back substitution */
-        x[(size_t)e * L + L - 1] = dp[L - 1];
-        for (int k = L - 2; k >= 0; k--)
+        x[(size_t)e * L + K - 1] = dp[K - 1];
+        for (int k = K - 2; k >= 0; k--)
             x[(size_t)e * L + k] = dp[k] - cp[k] * x[(size_t)e * L + k + 1];
     }
     free(he); free(utan); free(lo); free(di); free(up); free(rr); free(cp); free(dp);
@@ -475,7 +503,7 @@ void om_baroclinic_feuler_mixing(const om_mesh *m, const om_params *p, const dou
             den += he[(size_t)e * L + k];
         }
         G[e] = num / den / dt;
-        for (int k = 0; k < L; k++) {
+        for (int k = 0; k < ke(m, e); k++) {
             ut1[(size_t)e * L + k] -= dt * G[e];
             r[(size_t)e * L + k] = ut1[(size_t)e * L + k] + ubar[e];
         }
@@ -483,7 +511,7 @@ void om_baroclinic_feuler_mixing(const om_mesh *m, const om_params *p, const dou
     om_vertical_mixing_solve(m, p, u, h, r, dt, u1);
     for (int e = 0; e < m->nEdges; e++)
         for (int k = 0; k < L; k++)
-            ut1[(size_t)e * L + k] = u1[(size_t)e * L + k] - ubar[e];
+            ut1[(size_t)e * L + k] = k < ke(m, e) ? u1[(size_t)e * L + k] - ubar[e] : 0.0;
     free(rhs); free(he); free(r); free(u1);
 }
 
@@ -603,14 +631,16 @@ void om_thickness_tracer_fe(const om_mesh *m, const om_params *p, const double *
         for (int i = 0; i < m->nCells; i++) {
             const double *ph = phi + (size_t)i * L, *hi = h + (size_t)i * L;
             const double *wi = w + (size_t)i * (L + 1);
-            for (int k = 0; k < L; k++) {
+            const int K = kc(m, i);
+            for (int k = K; k < L; k++) phi1[(size_t)i * L + k] = 0.0;   /* no water */
+            for (int k = 0; k < K; k++) {
                 size_t x = (size_t)i * L + k;
                 double ftop = 0.0, fbot = 0.0, dtop = 0.0, dbot = 0.0;
                 if (k >= 1) {
                     ftop = 0.5 * (ph[k - 1] + ph[k]) * wi[k];
                     dtop = (ph[k - 1] - ph[k]) / (0.5 * (hi[k - 1] + hi[k]));
                 }
-                if (k + 1 <= L - 1) {
+                if (k + 1 <= K - 1) {
                     fbot = 0.5 * (ph[k] + ph[k + 1]) * wi[k + 1];
                     dbot = (ph[k] - ph[k + 1]) / (0.5 * (hi[k] + hi[k + 1]));
                 }
@@ -640,7 +670,7 @@ static void comb_tracer(size_t CL, int nT, double a, const double *h1, const dou
     for (int t = 0; t < nT; t++)
         for (size_t x = 0; x < CL; x++) {
             size_t y = (size_t)t * CL + x;
-            phi[y] = (a * h1[x] * p1[y] + b * h2[x] * p2[y]) / h[x];
+            phi[y] = h[x] > 0.0 ? (a * h1[x] * p1[y] + b * h2[x] * p2[y]) / h[x] : 0.0;
         }
 }
 
@@ -668,7 +698,8 @@ static void transport(const om_mesh *m, int recon, const double *u, const double
     int L = m->nLayers;
     for (int e = 0; e < m->nEdges; e++) {
         double uA = recon ? c * D[e] / hs[e] : 0.0;
-        for (int k = 0; k < L; k++) v[(size_t)e * L + k] = u[(size_t)e * L + k] + uA;
+        int K = ke(m, e);
+        for (int k = 0; k < L; k++) v[(size_t)e * L + k] = k < K ? u[(size_t)e * L + k] + uA : 0.0;
     }
 }
 
@@ -703,7 +734,7 @@ int om_sse_step(const om_mesh *m, const om_params *p, int order, double dt, int 
         bcl_stage(m, p, u, ut_n, ubar_n, zeta_n, h, tr, dt, ut1, G0);
         om_barotropic_substep(m, p, 2, ubar_n, zeta_n, G0, dt, M, ubar1, Fz1, NULL);
         for (int e = 0; e < E; e++)
-            for (int k = 0; k < L; k++) u1[(size_t)e * L + k] = ubar1[e] + ut1[(size_t)e * L + k];
+            for (int k = 0; k < L; k++) u1[(size_t)e * L + k] = k < ke(m, e) ? ubar1[e] + ut1[(size_t)e * L + k] : 0.0;
         layer_flux(m, u, h, Fh1, hs_n);
         for (int e = 0; e < E; e++) D1[e] = Fz1[e] - Fh1[e];
         transport(m, p->recon, u, D1, hs_n, 1.0, v);
@@ -717,7 +748,7 @@ int om_sse_step(const om_mesh *m, const om_params *p, int order, double dt, int 
         om_barotropic_substep(m, p, 2, ubar_n, zeta_n, Gi, dt, M, ubarn1, Fz2, zsub);
         for (int e = 0; e < E; e++)
             for (int k = 0; k < L; k++)
-                un1[(size_t)e * L + k] = ubarn1[e] + utn1[(size_t)e * L + k];
+                un1[(size_t)e * L + k] = k < ke(m, e) ? ubarn1[e] + utn1[(size_t)e * L + k] : 0.0;
         /* Step 3: thickness stage 2 with reconciliation, F^h_2 of Sec. 3.4 */
         layer_flux(m, un1, h1, Fh2, hs_1);
         for (int e = 0; e < E; e++) {
@@ -742,7 +773,7 @@ int om_sse_step(const om_mesh *m, const om_params *p, int order, double dt, int 
         bcl_stage(m, p, u, ut_n, ubar_n, zeta_n, h, tr, dt, ut1, G0);
         om_barotropic_substep(m, p, 3, ubar_n, zeta_n, G0, dt, M, ubar1, Fz1, NULL);
         for (int e = 0; e < E; e++)
-            for (int k = 0; k < L; k++) u1[(size_t)e * L + k] = ubar1[e] + ut1[(size_t)e * L + k];
+            for (int k = 0; k < L; k++) u1[(size_t)e * L + k] = k < ke(m, e) ? ubar1[e] + ut1[(size_t)e * L + k] : 0.0;
         layer_flux(m, u, h, Fh1, hs_n);
         for (int e = 0; e < E; e++) D1[e] = Fz1[e] - Fh1[e];
         transport(m, p->recon, u, D1, hs_n, 1.0, v);
@@ -754,7 +785,7 @@ int om_sse_step(const om_mesh *m, const om_params *p, int order, double dt, int 
         om_barotropic_substep(m, p, 3, ubar1, zeta1, G1, dt, M, ubar2, Fz2, NULL);
         comb(E, 0.75, ubar_n, 0.25, ubar2, ubarh);
         for (int e = 0; e < E; e++)
-            for (int k = 0; k < L; k++) uh[(size_t)e * L + k] = ubarh[e] + uth[(size_t)e * L + k];
+            for (int k = 0; k < L; k++) uh[(size_t)e * L + k] = k < ke(m, e) ? ubarh[e] + uth[(size_t)e * L + k] : 0.0;
         layer_flux(m, u1, h1, Fh2, hs_1);
         for (int e = 0; e < E; e++) D2[e] = Fz2[e] - Fh2[e];
         transport(m, p->recon, u1, D2, hs_1, 1.0, v);
@@ -770,7 +801,7 @@ int om_sse_step(const om_mesh *m, const om_params *p, int order, double dt, int 
         om_barotropic_substep(m, p, 3, ubar_n, zeta_n, Gi, dt, M, ubarn1, Fz3, zsub);
         for (int e = 0; e < E; e++)
             for (int k = 0; k < L; k++)
-                un1[(size_t)e * L + k] = ubarn1[e] + utn1[(size_t)e * L + k];
+                un1[(size_t)e * L + k] = k < ke(m, e) ? ubarn1[e] + utn1[(size_t)e * L + k] : 0.0;
         /* Step 3: F^h_3 of Sec. 3.4, layer by layer */
         om_edge_thickness(m, L, h, he_n);
         om_edge_thickness(m, L, h1, he_1);
@@ -792,7 +823,8 @@ int om_sse_step(const om_mesh *m, const om_params *p, int order, double dt, int 
         for (int e = 0; e < E; e++)
             for (int k = 0; k < L; k++) {
                 size_t x = (size_t)e * L + k;
-                v[x] = 0.5 * (u[x] + un1[x]) + (p->recon ? 1.5 * D3[e] / hs_h[e] : 0.0);
+                v[x] = k < ke(m, e) ? 0.5 * (u[x] + un1[x]) + (p->recon ? 1.5 * D3[e] / hs_h[e] : 0.0)
+                                    : 0.0;
             }
         om_thickness_tracer_fe(m, p, hh, trh, v, dt, h3, tr3);
         double *hn1 = h2; /* reuse */

@@ -35,6 +35,11 @@ typedef struct {
     const double *kiteAreasOnVertex; /* [V][3] */
     const double *fEdge, *fVertex, *bottomDepth;
     const double *restThicknessFrac; /* [L], sums to 1 */
+    /* partial bottom cells (both NULL: every column has all L layers with the
+     * fractions above): active layers per cell, and the rest thickness of
+     * each cell's layers ([C][L], 0 below maxLevelCell, summing to H) */
+    const int *maxLevelCell;
+    const double *restThickness;
 } om_mesh;
 
 typedef struct {

@@ -252,3 +252,45 @@ def build_spec(spec):
         return sphere_case(spec["level"], spec["L"], seed=spec["seed"] % 7, perturb=True)
     return channel_case(spec["nx"], spec["ny"], spec["dc"], spec["L"], beta=1.6e-11,
                         seed=spec["seed"], perturb=True)
+
+
+def partial_bottom(m, L, min_frac=0.25):
+    """Partial bottom cells for the depths of mesh m on a uniform reference
+    grid of L layers reaching the deepest cell: cell i keeps the K_i layers
+    that reach its depth, the last one cut to the depth (merged into the layer
+    above when thinner than min_frac of a layer).  Returns (maxLevelCell [C]
+    int32, restThickness [C, L], 0 below maxLevelCell)."""
+    H = np.asarray(m.bottomDepth, dtype=np.float64)
+    dz = H.max() / L
+    K = np.minimum(np.ceil(H / dz - 1e-12).astype(np.int64), L)
+    K = np.maximum(K, 1)
+    rest = np.zeros((m.nCells, L))
+    for i in range(m.nCells):
+        k = int(K[i])
+        bottom = H[i] - (k - 1) * dz
+        if k > 1 and bottom < min_frac * dz:
+            k -= 1
+            bottom += dz
+        K[i] = k
+        rest[i, :k - 1] = dz
+        rest[i, k - 1] = H[i] - (k - 1) * dz
+    return K.astype(np.int32), rest
+
+
+def partial_case(nx, ny, dc, L, *, depth, seed=0, perturb=True, nTracers=1, **params):
+    """A channel over the bathymetry `depth(x, y)` with partial bottom cells:
+    (mesh, L, params, (u, h, tr), (maxLevelCell, restThickness)).  The state is
+    the channel state remapped to z-star layers proportional to the rest
+    thickness (h_k = rest_k (H + zeta) / H); inactive layers hold h = 0, u = 0
+    and tracer 0."""
+    m, L, p, (u, h, tr) = channel_case(nx, ny, dc, L, depth=depth, seed=seed, perturb=perturb,
+                                       nTracers=nTracers, **params)
+    K, rest = partial_bottom(m, L)
+    H = m.bottomDepth
+    zeta = h.sum(1) - H
+    h = rest * ((H + zeta) / H)[:, None]
+    active = np.arange(L)[None, :] < K[:, None]
+    tr = np.where(active[None], tr, 0.0)
+    Ke = np.minimum(K[m.cellsOnEdge[:, 0]], K[m.cellsOnEdge[:, 1]])
+    u = np.where(np.arange(L)[None, :] < Ke[:, None], u, 0.0)
+    return m, L, p, (u, h, tr), (K, rest)

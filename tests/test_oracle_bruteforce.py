@@ -75,3 +75,41 @@ def test_dense_matrices_pin_operator_identities():
     # the Coriolis operator does no work: l d * Cor is antisymmetric
     W = (m.dvEdge * m.dcEdge)[:, None] * d.Cor
     assert np.abs(W + W.T).max() < 1e-12 * np.abs(W).max()
+
+
+@pytest.mark.parametrize("order", [2, 3])
+@pytest.mark.parametrize("vmix", [0, 1])
+def test_oracle_equals_dense_with_partial_bottom_cells(order, vmix):
+    """Partial bottom cells (1 to 4 active layers, cut bottom layers) with every
+    term on, Algorithm 1 and Algorithm 2: the oracle against the dense-matrix
+    implementation."""
+    rng = np.random.default_rng(21 + order)
+    m = meshmod.planar_hex(4, 4, 20e3, land_rows=2, f0=1e-4, beta=2e-10,
+                           depth=lambda x, y: 120.0 + 700.0 * (0.5 + 0.5 * np.sin(x / 9e3 + y / 7e3)))
+    L = 4
+    K, rest = inputs.partial_bottom(m, L)
+    assert K.min() < K.max()
+    C, E = m.nCells, m.nEdges
+    zeta = 0.3 * rng.standard_normal(C)
+    h = rest * ((m.bottomDepth + zeta) / m.bottomDepth)[:, None]
+    Ke = np.minimum(K[m.cellsOnEdge[:, 0]], K[m.cellsOnEdge[:, 1]])
+    u = np.where(np.arange(L)[None, :] < Ke[:, None], 0.2 * rng.standard_normal((E, L)), 0.0)
+    act = np.arange(L)[None, :] < K[:, None]
+    tr = np.stack([np.where(act, 15 + 3 * rng.standard_normal((C, L)), 0.0),
+                   np.where(act, 35 + 0.5 * rng.standard_normal((C, L)), 0.0)])
+    p = dict(inputs.PHYS)
+    p.update(nTracers=2, nu_h=40.0, nu_v=1e-2, kappa_h=30.0, kappa_v=5e-3, c_drag=2e-3,
+             nu_4=1e12, windStress=0.1 * rng.standard_normal(E), vmix=vmix, recon="consistent")
+    o = oracle.Oracle(m, L, p, max_level=K, rest_thickness=rest)
+    uo, ho, to = o.step(order, 120.0, 4, u.copy(), h.copy(), tr.copy(), n_steps=2)
+    d = DenseScheme(m, L, p, max_level=K, rest_thickness=rest)
+    ud, hd, td = u.copy(), h.copy(), tr.copy()
+    for _ in range(2):
+        ud, hd, td = d.step(order, 120.0, 4, ud, hd, td)
+    assert rel(ud, u) > 1e-3
+    assert rel(uo, ud) < 1e-12
+    assert rel(ho, hd) < 1e-14
+    assert rel(to, td) < 1e-13
+    # inactive layers stay empty
+    assert np.abs(ho[~act]).max() == 0 and np.abs(to[:, ~act]).max() == 0
+    assert np.abs(uo[np.arange(L)[None, :] >= Ke[:, None]]).max() == 0
