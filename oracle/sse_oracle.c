@@ -142,6 +142,10 @@ void om_laplacian(const om_mesh *m, int L, const double *u, double *out) {
 void om_biharmonic(const om_mesh *m, int L, const double *u, double *out) {
     double *l1 = vec((size_t)m->nEdges * L);
     om_laplacian(m, L, u, l1);
+    /* del^2 u lives on the edge layers that exist (partial bottom cells) */
+    if (L == m->nLayers)
+        for (int e = 0; e < m->nEdges; e++)
+            for (int k = ke(m, e); k < L; k++) l1[(size_t)e * L + k] = 0.0;
     om_laplacian(m, L, l1, out);
     free(l1);
 }

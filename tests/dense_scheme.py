@@ -164,7 +164,7 @@ class DenseScheme:
         speed = np.sqrt(ubot ** 2 + (self.Perp @ u)[ee, kb] ** 2)
         X[ee, self.Ke] = p["c_drag"] * speed * ubot
         vvisc = (X[:, :L] - X[:, 1:]) / np.where(he > 0, he, 1.0) if vvisc_on else 0.0
-        bih = self.Lap @ (self.Lap @ u)                       # del^4 u
+        bih = self.Lap @ ((self.Lap @ u) * self.me)          # del^4 u (del^2 u on edge layers)
         return self.me * (Cut + (Q - Cu) - self.Grad @ K - pgf - vadv + p["nu_h"] * (self.Lap @ u) + vvisc
                 + g * (self.Grad @ zeta)[:, None] - p.get("nu_4", 0.0) * bih)
 
