@@ -99,6 +99,16 @@ typedef struct {
     const double *fVertex;           /* [nVertices]                        */
     const double *bottomDepth;       /* [nCells] resting depth H (m) > 0   */
     const double *restThicknessFrac; /* [nLayers] z-star fractions, sum 1  */
+    /* Partial bottom cells (both NULL: every column has all nLayers layers
+     * with thicknesses restThicknessFrac x bottomDepth).  maxLevelCell[i] in
+     * 1..nLayers is the number of layers of column i; restThickness[i][k] > 0
+     * for k < maxLevelCell[i], 0 below, sums to bottomDepth[i] (relative
+     * 1e-10); the z-star stretching of layer k of column i is
+     * restThickness[i][k] / bottomDepth[i].  An edge has the layers both its
+     * cells have.  State values in missing layers are ignored and read back
+     * as 0. */
+    const int32_t *maxLevelCell;     /* [nCells] or NULL                   */
+    const double *restThickness;     /* [nCells][nLayers] or NULL          */
 } sse_mesh_desc;
 
 /* SSE_OPT_VMIX: every baroclinic stage uses Algorithm 2

@@ -41,7 +41,8 @@ class MeshDesc(ct.Structure):
                 ("nEdgesOnEdge", _ip), ("edgesOnEdge", _ip), ("weightsOnEdge", _dp),
                 ("dcEdge", _dp), ("dvEdge", _dp), ("areaCell", _dp), ("areaTriangle", _dp),
                 ("kiteAreasOnVertex", _dp), ("fEdge", _dp), ("fVertex", _dp),
-                ("bottomDepth", _dp), ("restThicknessFrac", _dp)]
+                ("bottomDepth", _dp), ("restThicknessFrac", _dp), ("maxLevelCell", _ip),
+                ("restThickness", _dp)]
 
 
 class Params(ct.Structure):
@@ -154,7 +155,8 @@ def _check(rc, what):
 class Mesh:
     """Device copy of a TRiSK mesh (any object with the mesh.Mesh attributes)."""
 
-    def __init__(self, mesh, nLayers: int, rest_frac=None):
+    def __init__(self, mesh, nLayers: int, rest_frac=None, max_level=None, rest_thickness=None):
+        """max_level [C] / rest_thickness [C, L]: partial bottom cells."""
         self.lib = load()
         self.L = int(nLayers)
         self.nCells, self.nEdges, self.nVertices = int(mesh.nCells), int(mesh.nEdges), int(
@@ -180,7 +182,9 @@ class Mesh:
                              ia(mesh.edgesOnEdge), da(mesh.weightsOnEdge), da(mesh.dcEdge),
                              da(mesh.dvEdge), da(mesh.areaCell), da(mesh.areaTriangle),
                              da(mesh.kiteAreasOnVertex), da(mesh.fEdge), da(mesh.fVertex),
-                             da(mesh.bottomDepth), da(rf))
+                             da(mesh.bottomDepth), da(rf),
+                             None if max_level is None else ia(max_level),
+                             None if rest_thickness is None else da(rest_thickness))
         self._keep = keep
         h = ct.c_void_p()
         _check(self.lib.sse_mesh_create(ct.byref(self.desc), ct.byref(h)), "sse_mesh_create")

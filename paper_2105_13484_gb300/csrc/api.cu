@@ -153,6 +153,20 @@ extern "C" int sse_mesh_create(const sse_mesh_desc *d, sse_mesh **out) {
         }
         if (fabs(s - 1.0) > 1e-12) return SSE_ERR_BAD_MESH;
     }
+    const bool partial = d->maxLevelCell != nullptr;
+    if (partial != (d->restThickness != nullptr)) return SSE_ERR_INVALID_ARG;
+    if (partial)
+        for (int i = 0; i < C; i++) {
+            const int K = d->maxLevelCell[i];
+            if (K < 1 || K > L) return SSE_ERR_BAD_MESH;
+            double s = 0.0;
+            for (int k = 0; k < L; k++) {
+                const double r = d->restThickness[(size_t)i * L + k];
+                if (k < K ? !(r > 0) : r != 0.0) return SSE_ERR_BAD_MESH;
+                s += r;
+            }
+            if (!(fabs(s - d->bottomDepth[i]) <= 1e-10 * d->bottomDepth[i])) return SSE_ERR_BAD_MESH;
+        }
 
     // ---- derived, padded, layer-major arrays
     const int Cp = pad(C), Ep = pad(E), Vp = pad(V);
@@ -258,6 +272,20 @@ extern "C" int sse_mesh_create(const sse_mesh_desc *d, sse_mesh **out) {
     dm.f.cfc = A.upload(tof(cfc)); dm.f.curlc = A.upload(tof(curlc)); dm.f.kw = A.upload(tof(kw));
     dm.f.invdc = A.upload(tof(invdc)); dm.f.invdv = A.upload(tof(invdv));
     dm.f.fV = A.upload(tof(fV));
+    dm.partial = partial ? 1 : 0;
+    dm.kc = nullptr; dm.ke = nullptr; dm.sfc = nullptr; dm.sfc_f = nullptr;
+    if (partial) {
+        std::vector<int> kc(Cp, L), ke(Ep, L);
+        std::vector<double> sfc((size_t)L * Cp, 0.0);
+        for (int i = 0; i < C; i++) {
+            kc[i] = d->maxLevelCell[i];
+            for (int k = 0; k < L; k++)
+                sfc[(size_t)k * Cp + i] = d->restThickness[(size_t)i * L + k] / d->bottomDepth[i];
+        }
+        for (int e = 0; e < E; e++) ke[e] = std::min(kc[coe[e].x], kc[coe[e].y]);
+        dm.kc = A.upload(kc); dm.ke = A.upload(ke);
+        dm.sfc = A.upload(sfc); dm.sfc_f = A.upload(tof(sfc));
+    }
     if (A.failed) {
         delete m;
         return SSE_ERR_OOM;
@@ -628,6 +656,7 @@ struct Engine : EngineBase {
         case SSE_FIELD_UTILDE:
             CK(cudaMemcpyAsync(stage, host, sizeof(double) * m.E * L, cudaMemcpyHostToDevice, s));
             launch_to_device<R>(stage, ut_n, m.E, L, m.Ep, s);
+            if (m.partial) launch_mask_layers<R>(ut_n, m.E, L, m.Ep, m.ke, s);
             if (field == SSE_FIELD_U) CK(cudaMemsetAsync(ubar_n, 0, sizeof(R) * m.Ep, s));
             break;
         case SSE_FIELD_UBAR:
@@ -638,6 +667,7 @@ struct Engine : EngineBase {
         case SSE_FIELD_H:
             CK(cudaMemcpyAsync(stage, host, sizeof(double) * m.C * L, cudaMemcpyHostToDevice, s));
             launch_to_device<double>(stage, h_n, m.C, L, m.Cp, s);
+            if (m.partial) launch_mask_layers<double>(h_n, m.C, L, m.Cp, m.kc, s);
             if (mixed) launch_h_to_float(h_n, (float *)hR_n, L * m.Cp, s);
             launch_ssh(m, h_n, zeta_n, s);
             break;
@@ -647,6 +677,7 @@ struct Engine : EngineBase {
             if (t >= p.nT) return SSE_ERR_INVALID_ARG;
             CK(cudaMemcpyAsync(stage, host, sizeof(double) * m.C * L, cudaMemcpyHostToDevice, s));
             launch_to_device<R>(stage, tr_n + (size_t)t * L * m.Cp, m.C, L, m.Cp, s);
+            if (m.partial) launch_mask_layers<R>(tr_n + (size_t)t * L * m.Cp, m.C, L, m.Cp, m.kc, s);
             break;
         }
         case SSE_FIELD_WIND:
@@ -671,7 +702,7 @@ struct Engine : EngineBase {
         size_t n = 0;
         switch (field) {
         case SSE_FIELD_U:
-            launch_add_bar<R>(ubar_n, ut_n, stage, m.E, L, m.Ep, s);
+            launch_add_bar<R>(ubar_n, ut_n, stage, m.E, L, m.Ep, m.partial ? m.ke : nullptr, s);
             n = (size_t)m.E * L;
             break;
         case SSE_FIELD_UTILDE:

@@ -42,6 +42,13 @@ struct DMesh {
     const double *H;    // [Cp] resting depth
     const double *sfrac;  // [L] z-star fractions
     const float *sfrac_f; // [L] the same in FP32
+    // partial bottom cells (partial = 1): layers per cell and per edge, and the
+    // per-column z-star shares [L][Cp] (0 below the column's bottom)
+    int partial;
+    const int *kc;        // [Cp]
+    const int *ke;        // [Ep]
+    const double *sfc;    // [L][Cp]
+    const float *sfc_f;   // [L][Cp]
     const double *divc_d; // [maxE][Cp] divergence coefficients in FP64
     const double *area;   // [Cp]
     const double *ld2;    // [Ep] l_e d_e / 2 (energy weight)
@@ -199,7 +206,10 @@ void launch_to_device(const double *src, R *dst, int n, int L, int np, cudaStrea
 template <class R>
 void launch_from_device(const R *src, double *dst, int n, int L, int np, cudaStream_t s);
 template <class R>
-void launch_add_bar(const R *ubar, const R *ut, double *dst, int E, int L, int Ep, cudaStream_t s);
+void launch_add_bar(const R *ubar, const R *ut, double *dst, int E, int L, int Ep,
+                    const int *kmax, cudaStream_t s);
+template <class R>
+void launch_mask_layers(R *x, int n, int L, int np, const int *kmax, cudaStream_t s);
 void launch_h_to_float(const double *h, float *hf, int n, cudaStream_t s);
 void launch_scale(const double *src, double scale, double *dst_d, float *dst_f, int n, cudaStream_t s);
 void launch_ssh(const DMesh &m, const double *h, double *zeta, cudaStream_t s);

@@ -24,11 +24,17 @@ template <class R> __device__ __forceinline__ R ld(const R *p) { return __ldg(p)
 template <class R> __device__ __forceinline__ const R *sfrac_of(const DMesh &m);
 template <> __device__ __forceinline__ const double *sfrac_of<double>(const DMesh &m) { return m.sfrac; }
 template <> __device__ __forceinline__ const float *sfrac_of<float>(const DMesh &m) { return m.sfrac_f; }
+// per-column shares (partial bottom cells), [L][Cp]
+template <class R> __device__ __forceinline__ const R *sfc_of(const DMesh &m);
+template <> __device__ __forceinline__ const double *sfc_of<double>(const DMesh &m) { return m.sfc; }
+template <> __device__ __forceinline__ const float *sfc_of<float>(const DMesh &m) { return m.sfc_f; }
 
 // ---------------------------------------------------------------------------
 // cell diagnostics
 // ---------------------------------------------------------------------------
-template <class R, int NCE>
+// PB: partial bottom cells -- the column's own layer count K and per-edge
+// layer counts; u is 0 on edge layers that do not exist.
+template <class R, int NCE, bool PB>
 __global__ void __launch_bounds__(128) k_cell_diag(DMesh m, DParams p, const R *__restrict__ ubar,
                                                    const R *__restrict__ ut,
                                                    const R *__restrict__ hR,
@@ -38,7 +44,8 @@ __global__ void __launch_bounds__(128) k_cell_diag(DMesh m, DParams p, const R *
     const Coef<R> &c = coef<R>(m);
     const int Cp = m.Cp, Ep = m.Ep, L = m.L;
     const int ne = m.neoc[i];
-    int es[NCE], os[NCE];
+    const int K = PB ? m.kc[i] : L;
+    int es[NCE], os[NCE], kej[NCE];
     R dcf[NCE], kcf[NCE], ub[NCE];
 #pragma unroll
     for (int j = 0; j < NCE; j++) {
@@ -48,20 +55,22 @@ __global__ void __launch_bounds__(128) k_cell_diag(DMesh m, DParams p, const R *
             dcf[j] = c.divc[j * Cp + i];
             kcf[j] = c.kec[j * Cp + i];
             ub[j] = ld(ubar + es[j]);
+            kej[j] = PB ? m.ke[es[j]] : L;
         } else {
-            es[j] = 0; os[j] = i; dcf[j] = R(0); kcf[j] = R(0); ub[j] = R(0);
+            es[j] = 0; os[j] = i; dcf[j] = R(0); kcf[j] = R(0); ub[j] = R(0); kej[j] = 0;
         }
     }
     const PhysR<R> &q = phys<R>(p);
     const R g = q.g, alpha = q.alpha, beta = q.beta, Tref = q.T_ref, Sref = q.S_ref;
     const R *sfr = sfrac_of<R>(m);
+    const R *sfc = sfc_of<R>(m);
     R accp = R(0), divsum = R(0);
-    for (int k = 0; k < L; k++) {
+    for (int k = 0; k < K; k++) {
         const R hk = ld(hR + k * Cp + i);
         R ke = R(0), dl = R(0), dv = R(0);
 #pragma unroll
         for (int j = 0; j < NCE; j++) {
-            if (j < ne) {
+            if (j < ne && (!PB || k < kej[j])) {
                 const R uk = ub[j] + ld(ut + k * Ep + es[j]);
                 const R he = R(0.5) * (hk + ld(hR + k * Cp + os[j]));
                 ke += kcf[j] * uk * uk;
@@ -84,12 +93,13 @@ __global__ void __launch_bounds__(128) k_cell_diag(DMesh m, DParams p, const R *
     // mid-layer height z_k = -H + sum_{l>k} h_l + h_k / 2
     R wk1 = R(0), below = R(0);
     const R Hi = (R)m.H[i];
-    for (int k = L - 1; k >= 0; k--) {
+    for (int k = K - 1; k >= 0; k--) {
         const int x = k * Cp + i;
         const R hk = ld(hR + x);
         b.zm[x] = -Hi + below + R(0.5) * hk;
         below += hk;
-        const R wk = (k == 0) ? R(0) : wk1 - b.w[x] + sfr[k] * divsum;
+        const R sk = PB ? sfc[x] : sfr[k];
+        const R wk = (k == 0) ? R(0) : wk1 - b.w[x] + sk * divsum;
         b.w[x] = wk;
         wk1 = wk;
     }
@@ -98,15 +108,15 @@ __global__ void __launch_bounds__(128) k_cell_diag(DMesh m, DParams p, const R *
 // ---------------------------------------------------------------------------
 // vertex vorticity and potential vorticity
 // ---------------------------------------------------------------------------
-template <class R>
+template <class R, bool PB>
 __global__ void __launch_bounds__(128) k_vertex(DMesh m, const R *__restrict__ ubar,
                                                 const R *__restrict__ ut,
                                                 const R *__restrict__ hR, DiagBufs<R> b) {
     const int v = blockIdx.x * blockDim.x + threadIdx.x;
     if (v >= m.V) return;
     const Coef<R> &c = coef<R>(m);
-    const int Vp = m.Vp, Ep = m.Ep, Cp = m.Cp;
-    int e[3], ce[3];
+    const int Vp = m.Vp, Ep = m.Ep, Cp = m.Cp, L = m.L;
+    int e[3], ce[3], kej[3], kcj[3];
     R cc[3], kw[3], ub[3];
 #pragma unroll
     for (int j = 0; j < 3; j++) {
@@ -115,24 +125,33 @@ __global__ void __launch_bounds__(128) k_vertex(DMesh m, const R *__restrict__ u
         cc[j] = c.curlc[j * Vp + v];
         kw[j] = c.kw[j * Vp + v];
         ub[j] = ld(ubar + e[j]);
+        kej[j] = PB ? m.ke[e[j]] : L;
+        kcj[j] = PB ? m.kc[ce[j]] : L;
     }
     const R fv = c.fV[v];
-    for (int k = 0; k < m.L; k++) {
-        R om = R(0), hv = R(0);
+    for (int k = 0; k < L; k++) {
+        R om = R(0), hv = R(0), ws = R(0);
 #pragma unroll
         for (int j = 0; j < 3; j++) {
-            om += cc[j] * (ub[j] + ld(ut + k * Ep + e[j]));
+            if (!PB || k < kej[j]) om += cc[j] * (ub[j] + ld(ut + k * Ep + e[j]));
             hv += kw[j] * ld(hR + k * Cp + ce[j]);
+            if (PB && k < kcj[j]) ws += kw[j];
         }
         b.omega[k * Vp + v] = om;
-        b.q[k * Vp + v] = (om + fv) / hv;
+        if (PB) {
+            // kite average over the cells that have this layer; none: q = 0
+            hv = ws > R(0) ? hv / ws : R(0);
+            b.q[k * Vp + v] = hv > R(0) ? (om + fv) / hv : R(0);
+        } else {
+            b.q[k * Vp + v] = (om + fv) / hv;
+        }
     }
 }
 
 // ---------------------------------------------------------------------------
 // edge pre-pass: h_e u, q_e; optional barotropic/baroclinic split (Eq. BBspl)
 // ---------------------------------------------------------------------------
-template <class R>
+template <class R, bool PB>
 __global__ void __launch_bounds__(128) k_edge_pre(DMesh m, R *__restrict__ ubar, R *__restrict__ ut,
                                                   const R *__restrict__ hR, DiagBufs<R> b,
                                                   int split) {
@@ -144,9 +163,13 @@ __global__ void __launch_bounds__(128) k_edge_pre(DMesh m, R *__restrict__ ubar,
     const R invdc = c.invdc[e], invdv = c.invdv[e];
     R ub = ubar[e];
     R mean = R(0);
+    // the edge's own layers; the rest of its column stays 0 (u, h_e u, del^2 u)
+    const int K = PB ? m.ke[e] : m.L;
+    if (PB && split)
+        for (int k = K; k < m.L; k++) ut[k * Ep + e] = R(0);
     if (split) {
         R num = R(0), den = R(0);
-        for (int k = 0; k < m.L; k++) {
+        for (int k = 0; k < K; k++) {
             const R he = R(0.5) * (ld(hR + k * Cp + cc.x) + ld(hR + k * Cp + cc.y));
             num += he * ut[k * Ep + e];
             den += he;
@@ -155,7 +178,7 @@ __global__ void __launch_bounds__(128) k_edge_pre(DMesh m, R *__restrict__ ubar,
         ub += mean;
         ubar[e] = ub;
     }
-    for (int k = 0; k < m.L; k++) {
+    for (int k = 0; k < K; k++) {
         const int x = k * Ep + e;
         R utk = ut[x];
         if (split) {
@@ -229,7 +252,7 @@ __global__ void __launch_bounds__(128) k_del2_divcurl(DMesh m, DiagBufs<R> b) {
 // column (Thomas; the modified super-diagonal goes to the scratch vmc), with
 // the wind explicit at the top and the bottom drag linearised about the speed
 // of the stage's input velocity; ut1 = u1 - ubar.
-template <class R, int NE2, bool VMIX>
+template <class R, int NE2, bool VMIX, bool PB>
 __global__ void __launch_bounds__(128, 8) k_bcl_edge(DMesh m, DParams p, const R *__restrict__ ubar,
                                                   const R *__restrict__ ut,
                                                   const R *__restrict__ hR,
@@ -266,15 +289,17 @@ __global__ void __launch_bounds__(128, 8) k_bcl_edge(DMesh m, DParams p, const R
     const R *wnd = wind_over_rho0<R>(p);
     const R wind = wnd ? wnd[e] : R(0);
 
+    // the edge's own layers (partial bottom cells); below them nothing is written
+    const int K = PB ? m.ke[e] : L;
     R ut_cur = ut[e];
     R u_cur = ub + ut_cur;
     R he_cur = R(0.5) * (ld(hR + c1) + ld(hR + c2));
     R u_prev = R(0), he_prev = R(0);
     R num = R(0), den = R(0), speed_b = R(0);
-    for (int k = 0; k < L; k++) {
+    for (int k = 0; k < K; k++) {
         const int xe = k * Ep + e;
         R ut_next = R(0), u_next = R(0), he_next = R(0);
-        if (k + 1 < L) {
+        if (k + 1 < K) {
             ut_next = ut[xe + Ep];
             u_next = ub + ut_next;
             he_next = R(0.5) * (ld(hR + (k + 1) * Cp + c1) + ld(hR + (k + 1) * Cp + c2));
@@ -296,18 +321,19 @@ __global__ void __launch_bounds__(128, 8) k_bcl_edge(DMesh m, DParams p, const R
             Dk = (u_prev - u_cur) / (R(0.5) * (he_prev + he_cur));
             wk = R(0.5) * (b.w[x1] + b.w[x2]);
         }
-        if (k + 1 < L) {
+        if (k + 1 < K) {
             Dk1 = (u_cur - u_next) / (R(0.5) * (he_cur + he_next));
             wk1 = R(0.5) * (b.w[x1 + Cp] + b.w[x2 + Cp]);
         }
         const R vadv = R(0.5) * (wk * Dk + wk1 * Dk1);
         const R Xtop = (k == 0) ? wind : nu_v * Dk;
         R Xbot;
-        if (k == L - 1) {
+        if (k == K - 1) {
             R utan = R(0);
 #pragma unroll
             for (int j = 0; j < NE2; j++)
-                if (j < n2) utan += wl[j] * (ld(ubar + eo[j]) + ut[k * Ep + eo[j]]);
+                if (j < n2 && (!PB || k < m.ke[eo[j]]))
+                    utan += wl[j] * (ld(ubar + eo[j]) + ut[k * Ep + eo[j]]);
             speed_b = sqrt(u_cur * u_cur + utan * utan);
             Xbot = cdrag * speed_b * u_cur;
         } else {
@@ -316,7 +342,15 @@ __global__ void __launch_bounds__(128, 8) k_bcl_edge(DMesh m, DParams p, const R
         const R vvisc = VMIX ? R(0) : (Xtop - Xbot) / he_cur;
         const R lap = (b.delta[x2] - b.delta[x1]) * invdc -
                       (b.omega[k * Vp + v2] - b.omega[k * Vp + v1]) * invdv;
-        R rhs = (Q - cbar) - gradK - pgf - vadv + nu_h * lap + vvisc + gzeta;
+        // C_f(u_k) - C_f(ut_k) = C_f(ubar) over the neighbours that have layer k
+        R cb = cbar;
+        if (PB) {
+            cb = R(0);
+#pragma unroll
+            for (int j = 0; j < NE2; j++)
+                if (j < n2 && k < m.ke[eo[j]]) cb += c.cfc[j * Ep + e] * ld(ubar + eo[j]);
+        }
+        R rhs = (Q - cb) - gradK - pgf - vadv + nu_h * lap + vvisc + gzeta;
         if (b.del2)
             rhs -= nu_4 * ((b.delta2[x2] - b.delta2[x1]) * invdc -
                            (b.omega2[k * Vp + v2] - b.omega2[k * Vp + v1]) * invdv);
@@ -330,7 +364,7 @@ __global__ void __launch_bounds__(128, 8) k_bcl_edge(DMesh m, DParams p, const R
     const R G = num / den / dt;
     Gout[e] = G;
     if (!VMIX) {
-        for (int k = 0; k < L; k++) {
+        for (int k = 0; k < K; k++) {
             const int xe = k * Ep + e;
             const R x = ut_out[xe] - dt * G;
             ut_out[xe] = ut_n ? a * ut_n[xe] + bc * x : bc * x;
@@ -341,14 +375,14 @@ __global__ void __launch_bounds__(128, 8) k_bcl_edge(DMesh m, DParams p, const R
     //   -lo x_{k-1} + (1 + lo + up [+ dt c_d |u| / h]) x_k - up x_{k+1} = r_k
     R cprev = R(0), dprev = R(0), hprev = R(0);
     R hk = R(0.5) * (ld(hR + c1) + ld(hR + c2));
-    for (int k = 0; k < L; k++) {
+    for (int k = 0; k < K; k++) {
         const int xe = k * Ep + e;
-        const R hnext = (k + 1 < L)
+        const R hnext = (k + 1 < K)
             ? R(0.5) * (ld(hR + (k + 1) * Cp + c1) + ld(hR + (k + 1) * Cp + c2)) : R(0);
         const R lo = (k > 0) ? dt * nu_v / (hk * (R(0.5) * (hprev + hk))) : R(0);
-        const R up = (k + 1 < L) ? dt * nu_v / (hk * (R(0.5) * (hk + hnext))) : R(0);
+        const R up = (k + 1 < K) ? dt * nu_v / (hk * (R(0.5) * (hk + hnext))) : R(0);
         R di = R(1) + lo + up;
-        if (k == L - 1) di += dt * cdrag * speed_b / hk;
+        if (k == K - 1) di += dt * cdrag * speed_b / hk;
         R r = ut_out[xe] - dt * G + ub;
         if (k == 0) r += dt * wind / hk;
         // sub-diagonal -lo, super-diagonal -up: pivot di - (-lo) c'_{k-1}
@@ -362,7 +396,7 @@ __global__ void __launch_bounds__(128, 8) k_bcl_edge(DMesh m, DParams p, const R
     }
     // back substitution up the column, then the convex combination
     R xnext = R(0);
-    for (int k = L - 1; k >= 0; k--) {
+    for (int k = K - 1; k >= 0; k--) {
         const int xe = k * Ep + e;
         const R x = ut_out[xe] - vmc[xe] * xnext;
         xnext = x;
@@ -379,7 +413,7 @@ __global__ void __launch_bounds__(128, 8) k_bcl_edge(DMesh m, DParams p, const R
 // accumulated in FP64; sum_k h_e,k = ((zeta+H)_c1 + (zeta+H)_c2) / 2 because
 // zeta = sum h - H.  The per-layer flux is stored in the tendency precision.
 // ---------------------------------------------------------------------------
-template <class R>
+template <class R, bool PB>
 __global__ void __launch_bounds__(128) k_transport(DMesh m, TransportArgs<R> a) {
     const int e = blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= m.E) return;
@@ -389,13 +423,17 @@ __global__ void __launch_bounds__(128) k_transport(DMesh m, TransportArgs<R> a) 
     const R ubB = a.ubB ? a.ubB[e] : R(0);
     const R wA = (R)a.wA, wB = (R)a.wB;
     const bool twoB = a.utB != nullptr;
-    const double hs = 0.5 * ((a.zeta[cc.x] + m.H[cc.x]) + (a.zeta[cc.y] + m.H[cc.y]));
+    // with full columns the edge's total thickness is (zeta + H)_e; with partial
+    // bottom cells it is the sum over the layers the edge has
+    const int K = PB ? m.ke[e] : L;
+    double hs = PB ? 0.0 : 0.5 * ((a.zeta[cc.x] + m.H[cc.x]) + (a.zeta[cc.y] + m.H[cc.y]));
     double S = 0.0;
-    for (int k = 0; k < L; k++) {
+    for (int k = 0; k < K; k++) {
         const R he = R(0.5) * (ld(a.hR + k * Cp + cc.x) + ld(a.hR + k * Cp + cc.y));
         R v = wA * (ubA + a.utA[k * Ep + e]);
         if (twoB) v += wB * (ubB + a.utB[k * Ep + e]);
         S += (double)(v * he);
+        if (PB) hs += (double)he;
     }
     double Fh = a.cF * S;
     if (a.ex1) Fh += a.cE * a.ex1[e];
@@ -404,7 +442,7 @@ __global__ void __launch_bounds__(128) k_transport(DMesh m, TransportArgs<R> a) 
     if (a.S_out) a.S_out[e] = S;
     a.Fcol[e] = S + uA * hs;
     const R uAr = (R)uA;
-    for (int k = 0; k < L; k++) {
+    for (int k = 0; k < K; k++) {
         const R he = R(0.5) * (ld(a.hR + k * Cp + cc.x) + ld(a.hR + k * Cp + cc.y));
         R v = wA * (ubA + a.utA[k * Ep + e]);
         if (twoB) v += wB * (ubB + a.utB[k * Ep + e]);
@@ -420,14 +458,15 @@ __global__ void __launch_bounds__(128) k_transport(DMesh m, TransportArgs<R> a) 
 // (FP64, from k_transport); the per-layer flux feeds w and the tracers in the
 // tendency precision.
 // ---------------------------------------------------------------------------
-template <class R, int NCE>
+template <class R, int NCE, bool PB>
 __global__ void __launch_bounds__(128, 6) k_thickness(DMesh m, DParams p, ThickArgs<R> a) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= m.C) return;
     const Coef<R> &c = coef<R>(m);
     const int Cp = m.Cp, Ep = m.Ep, L = m.L;
     const int ne = m.neoc[i];
-    int es[NCE], os[NCE];
+    const int K = PB ? m.kc[i] : L;     // the column's layers; below them nothing is written
+    int es[NCE], os[NCE], kej[NCE];
     R dcf[NCE], idc[NCE];
     double D = 0.0;
 #pragma unroll
@@ -438,14 +477,16 @@ __global__ void __launch_bounds__(128, 6) k_thickness(DMesh m, DParams p, ThickA
             dcf[j] = c.divc[j * Cp + i];
             idc[j] = c.invdc[es[j]];
             D += m.divc_d[j * Cp + i] * a.Fcol[es[j]];
+            kej[j] = PB ? m.ke[es[j]] : L;
         } else {
-            es[j] = 0; os[j] = i; dcf[j] = R(0); idc[j] = R(0);
+            es[j] = 0; os[j] = i; dcf[j] = R(0); idc[j] = R(0); kej[j] = 0;
         }
     }
     const R Dr = (R)D;
     const double dtD = a.dt * D;
     const PhysR<R> &q = phys<R>(p);
     const R *sfr = sfrac_of<R>(m);
+    const R *sfcR = sfc_of<R>(m);
     const R dtR = (R)a.dt, aR = (R)a.a, bR = (R)a.b, kh = q.kappa_h, kv = q.kappa_v;
     const bool comb = a.a != 0.0;
     const bool khz = p.kappa_h != 0.0;
@@ -456,18 +497,18 @@ __global__ void __launch_bounds__(128, 6) k_thickness(DMesh m, DParams p, ThickA
     // both at hand when layer k is updated
     R wk = R(0);
     R hs_prev = R(0), hs_cur = ld(a.hR_s + i);
-    for (int k = 0; k < L; k++) {
+    for (int k = 0; k < K; k++) {
         const int x = k * Cp + i;
         R divk = R(0);
 #pragma unroll
         for (int j = 0; j < NCE; j++)
             if (j < ne) divk += dcf[j] * ld(a.flux + k * Ep + es[j]);
-        const R sk = sfr[k];
-        const R wk1 = (k + 1 < L) ? wk + divk - sk * Dr : R(0);
-        const R hs_next = (k + 1 < L) ? ld(a.hR_s + x + Cp) : R(0);
+        const R sk = PB ? sfcR[x] : sfr[k];
+        const R wk1 = (k + 1 < K) ? wk + divk - sk * Dr : R(0);
+        const R hs_next = (k + 1 < K) ? ld(a.hR_s + x + Cp) : R(0);
         // thickness in FP64 from the column-integrated flux (volume conservation);
         // h_out may alias h_n, so h^n is read before the store
-        const double h1 = a.h_s[x] - m.sfrac[k] * dtD;
+        const double h1 = a.h_s[x] - (PB ? m.sfc[x] : m.sfrac[k]) * dtD;
         const double hn = comb ? a.h_n[x] : 0.0;
         const double hout = comb ? a.a * hn + a.b * h1 : h1;
         // the tracer arithmetic uses the tendency precision
@@ -480,7 +521,7 @@ __global__ void __launch_bounds__(128, 6) k_thickness(DMesh m, DParams p, ThickA
             R adv = R(0), dif = R(0);
 #pragma unroll
             for (int j = 0; j < NCE; j++) {
-                if (j < ne) {
+                if (j < ne && (!PB || k < kej[j])) {
                     const R po = ld(phi + k * Cp + os[j]);
                     adv += dcf[j] * (ld(a.flux + k * Ep + es[j]) * (R(0.5) * (ph + po)));
                     if (khz) {
@@ -496,7 +537,7 @@ __global__ void __launch_bounds__(128, 6) k_thickness(DMesh m, DParams p, ThickA
                 ftop = R(0.5) * (pu + ph) * wk;
                 dtop = (pu - ph) / (R(0.5) * (hs_prev + hs_cur));
             }
-            if (k + 1 <= L - 1) {
+            if (k + 1 <= K - 1) {
                 const R pd = ld(phi + x + Cp);
                 fbot = R(0.5) * (ph + pd) * wk1;
                 dbot = (ph - pd) / (R(0.5) * (hs_cur + hs_next));
@@ -541,11 +582,20 @@ __global__ void k_from_device(const R *__restrict__ src, double *__restrict__ ds
 }
 template <class R>
 __global__ void k_add_bar(const R *__restrict__ ubar, const R *__restrict__ ut,
-                          double *__restrict__ dst, int E, int L, int Ep) {
+                          double *__restrict__ dst, int E, int L, int Ep,
+                          const int *__restrict__ kmax) {
     const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= (long long)E * L) return;
     const int e = (int)(t / L), k = (int)(t % L);
-    dst[t] = (double)ubar[e] + (double)ut[(long long)k * Ep + e];
+    dst[t] = (kmax && k >= kmax[e]) ? 0.0 : (double)ubar[e] + (double)ut[(long long)k * Ep + e];
+}
+// zero the layers a column (or edge) does not have: x[k * np + i], k >= kmax[i]
+template <class R>
+__global__ void k_mask_layers(R *__restrict__ x, int n, int L, int np, const int *__restrict__ kmax) {
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= (long long)n * L) return;
+    const int i = (int)(t % n), k = (int)(t / n);
+    if (k >= kmax[i]) x[(long long)k * np + i] = R(0);
 }
 __global__ void k_h_to_float(const double *__restrict__ h, float *__restrict__ hf, int n) {
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
@@ -582,7 +632,8 @@ __global__ void k_diag_partial(DMesh m, const R *__restrict__ ubar, const R *__r
     const int L = m.L, Cp = m.Cp, Ep = m.Ep;
     for (int i = blockIdx.x * blockDim.x + tid; i < m.C; i += gridDim.x * blockDim.x) {
         double hs = 0.0, t0 = 0.0, t1 = 0.0;
-        for (int k = 0; k < L; k++) {
+        const int K = m.partial ? m.kc[i] : L;    // layers of the column
+        for (int k = 0; k < K; k++) {
             const double hk = h[k * Cp + i];
             hs += hk;
             t0 += hk * (double)tr[k * Cp + i];
@@ -599,7 +650,8 @@ __global__ void k_diag_partial(DMesh m, const R *__restrict__ ubar, const R *__r
     for (int e = blockIdx.x * blockDim.x + tid; e < m.E; e += gridDim.x * blockDim.x) {
         const int2 cc = m.coe[e];
         double ke = 0.0;
-        for (int k = 0; k < L; k++) {
+        const int K = m.partial ? m.ke[e] : L;    // layers of the edge
+        for (int k = 0; k < K; k++) {
             const double u = (double)ubar[e] + (double)ut[k * Ep + e];
             const double he = 0.5 * (h[k * Cp + cc.x] + h[k * Cp + cc.y]);
             ke += he * u * u;
@@ -646,15 +698,20 @@ static inline int nblk(long long n, int t) { return (int)((n + t - 1) / t); }
 template <class R>
 void launch_cell_diag(const DMesh &m, const DParams &p, const R *ubar, const R *ut, const R *hR,
                       const R *tr, const DiagBufs<R> &b, cudaStream_t s) {
-    if (m.maxE <= 6)
-        k_cell_diag<R, 6><<<nblk(m.C, 128), 128, 0, s>>>(m, p, ubar, ut, hR, tr, b);
-    else
-        k_cell_diag<R, MAXE><<<nblk(m.C, 128), 128, 0, s>>>(m, p, ubar, ut, hR, tr, b);
+    const int nb = nblk(m.C, 128);
+    if (m.partial) {
+        if (m.maxE <= 6) k_cell_diag<R, 6, true><<<nb, 128, 0, s>>>(m, p, ubar, ut, hR, tr, b);
+        else k_cell_diag<R, MAXE, true><<<nb, 128, 0, s>>>(m, p, ubar, ut, hR, tr, b);
+    } else {
+        if (m.maxE <= 6) k_cell_diag<R, 6, false><<<nb, 128, 0, s>>>(m, p, ubar, ut, hR, tr, b);
+        else k_cell_diag<R, MAXE, false><<<nb, 128, 0, s>>>(m, p, ubar, ut, hR, tr, b);
+    }
 }
 template <class R>
 void launch_vertex(const DMesh &m, const R *ubar, const R *ut, const R *hR, const DiagBufs<R> &b,
                    cudaStream_t s) {
-    k_vertex<R><<<nblk(m.V, 128), 128, 0, s>>>(m, ubar, ut, hR, b);
+    if (m.partial) k_vertex<R, true><<<nblk(m.V, 128), 128, 0, s>>>(m, ubar, ut, hR, b);
+    else k_vertex<R, false><<<nblk(m.V, 128), 128, 0, s>>>(m, ubar, ut, hR, b);
 }
 template <class R>
 void launch_del2_divcurl(const DMesh &m, const DiagBufs<R> &b, cudaStream_t s) {
@@ -666,7 +723,10 @@ void launch_del2_divcurl(const DMesh &m, const DiagBufs<R> &b, cudaStream_t s) {
 template <class R>
 void launch_edge_pre(const DMesh &m, R *ubar, R *ut, const R *hR, const DiagBufs<R> &b,
                      bool split, cudaStream_t s) {
-    k_edge_pre<R><<<nblk(m.E, 128), 128, 0, s>>>(m, ubar, ut, hR, b, split ? 1 : 0);
+    if (m.partial)
+        k_edge_pre<R, true><<<nblk(m.E, 128), 128, 0, s>>>(m, ubar, ut, hR, b, split ? 1 : 0);
+    else
+        k_edge_pre<R, false><<<nblk(m.E, 128), 128, 0, s>>>(m, ubar, ut, hR, b, split ? 1 : 0);
 }
 template <class R>
 void launch_bcl_edge(const DMesh &m, const DParams &p, const R *ubar, const R *ut, const R *hR,
@@ -674,32 +734,34 @@ void launch_bcl_edge(const DMesh &m, const DParams &p, const R *ubar, const R *u
                      double bcoef, double dt, R *ut_out, R *G, R *vmc, cudaStream_t s) {
     const int nb = nblk(m.E, 128);
     const R ra = (R)a, rb = (R)bcoef, rdt = (R)dt;
+#define SSE_BCL(NE2, VM, PB)                                                                   \
+    k_bcl_edge<R, NE2, VM, PB><<<nb, 128, 0, s>>>(m, p, ubar, ut, hR, zeta, b, ut_n, ra, rb, rdt, \
+                                                  ut_out, G, vmc)
+    const bool vm = vmc != nullptr, pb = m.partial != 0;
     if (m.maxE2 <= 10) {
-        if (vmc)
-            k_bcl_edge<R, 10, true><<<nb, 128, 0, s>>>(m, p, ubar, ut, hR, zeta, b, ut_n, ra, rb,
-                                                       rdt, ut_out, G, vmc);
-        else
-            k_bcl_edge<R, 10, false><<<nb, 128, 0, s>>>(m, p, ubar, ut, hR, zeta, b, ut_n, ra, rb,
-                                                        rdt, ut_out, G, vmc);
+        if (vm) { if (pb) SSE_BCL(10, true, true); else SSE_BCL(10, true, false); }
+        else { if (pb) SSE_BCL(10, false, true); else SSE_BCL(10, false, false); }
     } else {
-        if (vmc)
-            k_bcl_edge<R, MAXE2, true><<<nb, 128, 0, s>>>(m, p, ubar, ut, hR, zeta, b, ut_n, ra,
-                                                          rb, rdt, ut_out, G, vmc);
-        else
-            k_bcl_edge<R, MAXE2, false><<<nb, 128, 0, s>>>(m, p, ubar, ut, hR, zeta, b, ut_n, ra,
-                                                           rb, rdt, ut_out, G, vmc);
+        if (vm) { if (pb) SSE_BCL(MAXE2, true, true); else SSE_BCL(MAXE2, true, false); }
+        else { if (pb) SSE_BCL(MAXE2, false, true); else SSE_BCL(MAXE2, false, false); }
     }
+#undef SSE_BCL
 }
 template <class R>
 void launch_transport(const DMesh &m, const TransportArgs<R> &a, cudaStream_t s) {
-    k_transport<R><<<nblk(m.E, 128), 128, 0, s>>>(m, a);
+    if (m.partial) k_transport<R, true><<<nblk(m.E, 128), 128, 0, s>>>(m, a);
+    else k_transport<R, false><<<nblk(m.E, 128), 128, 0, s>>>(m, a);
 }
 template <class R>
 void launch_thickness(const DMesh &m, const DParams &p, const ThickArgs<R> &a, cudaStream_t s) {
-    if (m.maxE <= 6)
-        k_thickness<R, 6><<<nblk(m.C, 128), 128, 0, s>>>(m, p, a);
-    else
-        k_thickness<R, MAXE><<<nblk(m.C, 128), 128, 0, s>>>(m, p, a);
+    const int nb = nblk(m.C, 128);
+    if (m.partial) {
+        if (m.maxE <= 6) k_thickness<R, 6, true><<<nb, 128, 0, s>>>(m, p, a);
+        else k_thickness<R, MAXE, true><<<nb, 128, 0, s>>>(m, p, a);
+    } else {
+        if (m.maxE <= 6) k_thickness<R, 6, false><<<nb, 128, 0, s>>>(m, p, a);
+        else k_thickness<R, MAXE, false><<<nb, 128, 0, s>>>(m, p, a);
+    }
 }
 template <class R>
 void launch_to_device(const double *src, R *dst, int n, int L, int np, cudaStream_t s) {
@@ -710,8 +772,13 @@ void launch_from_device(const R *src, double *dst, int n, int L, int np, cudaStr
     k_from_device<R><<<nblk((long long)n * L, 256), 256, 0, s>>>(src, dst, n, L, np);
 }
 template <class R>
-void launch_add_bar(const R *ubar, const R *ut, double *dst, int E, int L, int Ep, cudaStream_t s) {
-    k_add_bar<R><<<nblk((long long)E * L, 256), 256, 0, s>>>(ubar, ut, dst, E, L, Ep);
+void launch_add_bar(const R *ubar, const R *ut, double *dst, int E, int L, int Ep,
+                    const int *kmax, cudaStream_t s) {
+    k_add_bar<R><<<nblk((long long)E * L, 256), 256, 0, s>>>(ubar, ut, dst, E, L, Ep, kmax);
+}
+template <class R>
+void launch_mask_layers(R *x, int n, int L, int np, const int *kmax, cudaStream_t s) {
+    k_mask_layers<R><<<nblk((long long)n * L, 256), 256, 0, s>>>(x, n, L, np, kmax);
 }
 void launch_h_to_float(const double *h, float *hf, int n, cudaStream_t s) {
     k_h_to_float<<<nblk(n, 256), 256, 0, s>>>(h, hf, n);
@@ -746,7 +813,9 @@ void launch_diag(const DMesh &m, const R *ubar, const R *ut, const double *h, co
                                       cudaStream_t);                                             \
     template void launch_to_device<R>(const double *, R *, int, int, int, cudaStream_t);         \
     template void launch_from_device<R>(const R *, double *, int, int, int, cudaStream_t);       \
-    template void launch_add_bar<R>(const R *, const R *, double *, int, int, int, cudaStream_t); \
+    template void launch_add_bar<R>(const R *, const R *, double *, int, int, int, const int *,   \
+                                    cudaStream_t);                                               \
+    template void launch_mask_layers<R>(R *, int, int, int, const int *, cudaStream_t);          \
     template void launch_diag<R>(const DMesh &, const R *, const R *, const double *, const R *, \
                                  int, const double *, double *, int, double *, cudaStream_t);
 INST(double)

@@ -104,3 +104,40 @@ def test_rest_fractions_must_sum_to_one(lib):
     desc.restThicknessFrac = rf.ctypes.data_as(ct.POINTER(ct.c_double))
     out = ct.c_void_p()
     assert lib.sse_mesh_create(ct.byref(desc), ct.byref(out)) == -2
+
+
+def test_partial_bottom_arrays_are_validated(lib):
+    """maxLevelCell and restThickness come together, K in 1..L, thickness > 0
+    above the column's bottom and 0 below it, summing to bottomDepth."""
+    from paper_2105_13484_gb300 import inputs
+    m = meshgen.planar_hex(6, 8, 1e4, depth=lambda x, y: 300.0 + 600.0 * y / y.max())
+    L = 4
+    K, rest = inputs.partial_bottom(m, L)
+    out = ct.c_void_p()
+
+    def try_with(Kx, rx):
+        desc, keep = _desc(m, L)
+        if Kx is not None:
+            Kx = np.ascontiguousarray(Kx, dtype=np.int32)
+            keep.append(Kx)
+            desc.maxLevelCell = Kx.ctypes.data_as(ct.POINTER(ct.c_int32))
+        if rx is not None:
+            rx = np.ascontiguousarray(rx, dtype=np.float64)
+            keep.append(rx)
+            desc.restThickness = rx.ctypes.data_as(ct.POINTER(ct.c_double))
+        return lib.sse_mesh_create(ct.byref(desc), ct.byref(out))
+
+    assert try_with(K, None) == -1
+    assert try_with(None, rest) == -1
+    bad = K.copy(); bad[3] = L + 1
+    assert try_with(bad, rest) == -2
+    bad = K.copy(); bad[3] = 0
+    assert try_with(bad, rest) == -2
+    r2 = rest.copy(); r2[5, K[5] - 1] *= 1.01            # no longer sums to the depth
+    assert try_with(K, r2) == -2
+    r2 = rest.copy(); r2[5, K[5] - 1] = 0.0; r2[5, 0] += rest[5, K[5] - 1]   # empty active layer
+    assert try_with(K, r2) == -2
+    if K.min() < L:
+        i = int(np.argmin(K))
+        r2 = rest.copy(); r2[i, L - 1] = 1.0; r2[i, 0] -= 1.0     # water below the bottom
+        assert try_with(K, r2) == -2
