@@ -270,12 +270,14 @@ __global__ void __launch_bounds__(128, 8) k_bcl_edge(DMesh m, DParams p, const R
     int eo[NE2];
     R wl[NE2];
     R cbar = R(0);
+    int kmin = L;   // the first layer some neighbour lacks (partial bottom cells)
 #pragma unroll
     for (int j = 0; j < NE2; j++) {
         if (j < n2) {
             eo[j] = m.eoe[j * Ep + e];
             wl[j] = c.wl[j * Ep + e];
             cbar += c.cfc[j * Ep + e] * ld(ubar + eo[j]);
+            if (PB) kmin = min(kmin, m.ke[eo[j]]);
         } else {
             eo[j] = e; wl[j] = R(0);
         }
@@ -344,7 +346,7 @@ __global__ void __launch_bounds__(128, 8) k_bcl_edge(DMesh m, DParams p, const R
                       (b.omega[k * Vp + v2] - b.omega[k * Vp + v1]) * invdv;
         // C_f(u_k) - C_f(ut_k) = C_f(ubar) over the neighbours that have layer k
         R cb = cbar;
-        if (PB) {
+        if (PB && k >= kmin) {
             cb = R(0);
 #pragma unroll
             for (int j = 0; j < NE2; j++)

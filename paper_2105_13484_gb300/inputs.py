@@ -179,11 +179,25 @@ def workload(name, *, seed=0, perturb=False, **override):
     w = dict(WORKLOADS[name])
     w.update(override)
     run = {k: w.pop(k) for k in ("order", "dt", "M", "steps")}
+    partial = w.pop("partial", False)
     if w.pop("kind", "channel") == "sphere":
         m, L, p, st = sphere_case(w.pop("level"), w.pop("L"), seed=seed, perturb=perturb, **w)
     else:
         m, L, p, st = channel_case(w.pop("nx"), w.pop("ny"), w.pop("dc"), w.pop("L"), seed=seed,
                                    perturb=perturb, **w)
+    if partial:
+        # partial bottom cells: the state remapped to each column's own layers;
+        # the layer data travel in params (maxLevelCell, restThickness)
+        u, h, tr = st
+        K, rest = partial_bottom(m, L)
+        H = m.bottomDepth
+        h = rest * (h.sum(1) / H)[:, None]
+        act = np.arange(L)[None, :] < K[:, None]
+        tr = np.where(act[None], tr, 0.0)
+        Ke = np.minimum(K[m.cellsOnEdge[:, 0]], K[m.cellsOnEdge[:, 1]])
+        u = np.where(np.arange(L)[None, :] < Ke[:, None], u, 0.0)
+        st = (u, h, tr)
+        p = dict(p, maxLevelCell=K, restThickness=rest)
     return m, L, p, st, run
 
 
