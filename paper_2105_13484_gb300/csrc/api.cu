@@ -588,10 +588,9 @@ struct Engine : EngineBase {
         tr_1 = A.alloc<R>(nT * CL); tr_h = A.alloc<R>(nT * CL);
         flux = A.alloc<R>(EL);
         Fcol = A.alloc<double>(m.Ep);
-        db.ke = A.alloc<R>(CL); db.delta = A.alloc<R>(CL); db.rhop = A.alloc<R>(CL);
-        db.pp = A.alloc<R>(CL); db.zm = A.alloc<R>(CL); db.w = A.alloc<R>(CL);
+        db.delta = A.alloc<R>(CL); db.w = A.alloc<R>(CL); db.cq = A.alloc<V4<R>>(CL);
         db.omega = A.alloc<R>(VL); db.q = A.alloc<R>(VL);
-        db.hu = A.alloc<R>(EL); db.qe = A.alloc<R>(EL);
+        db.hq = A.alloc<V2<R>>(EL);
         db.del2 = db.delta2 = db.omega2 = nullptr;
         if (p.nu_4 > 0.0) {
             db.del2 = A.alloc<R>(EL); db.delta2 = A.alloc<R>(CL); db.omega2 = A.alloc<R>(VL);

@@ -93,10 +93,19 @@ struct Barrier {
 };
 
 // ---- stage kernels (layer-major), launched by the driver -----------------
+// two and four values of one precision stored together, loaded as one vector
+struct __align__(32) double4x { double x, y, z, w; };
+template <class R> struct VecT;
+template <> struct VecT<float> { using V2 = float2; using V4 = float4; };
+template <> struct VecT<double> { using V2 = double2; using V4 = double4x; };
+template <class R> using V2 = typename VecT<R>::V2;
+template <class R> using V4 = typename VecT<R>::V4;
+
 template <class R> struct DiagBufs {
-    R *ke, *delta, *rhop, *pp, *zm, *w;  // [L][Cp]
+    R *delta, *w;                        // [L][Cp] div u; div(h_e u), then w at the top of k
+    V4<R> *cq;                           // [L][Cp] (K, p', rho', z_mid), gathered as one
     R *omega, *q;                        // [L][Vp]
-    R *hu, *qe;                          // [L][Ep]
+    V2<R> *hq;                           // [L][Ep] (h_e u, q_e), gathered as one
     // biharmonic viscosity only (nullptr otherwise): del^2 u on edges, its
     // divergence on cells and its curl on vertices
     R *del2, *delta2, *omega2;

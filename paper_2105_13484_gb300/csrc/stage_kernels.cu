@@ -81,10 +81,13 @@ __global__ void __launch_bounds__(128) k_cell_diag(DMesh m, DParams p, const R *
         R rp = -alpha * (ld(tr + k * Cp + i) - Tref);
         if (p.nT > 1) rp += beta * (ld(tr + (L + k) * Cp + i) - Sref);
         const int x = k * Cp + i;
-        b.ke[x] = ke;
+        V4<R> cq;
+        cq.x = ke;
+        cq.y = g * (accp + R(0.5) * rp * hk);
+        cq.z = rp;
+        cq.w = R(0);    // z_mid, filled in on the way up
+        b.cq[x] = cq;
         b.delta[x] = dl;
-        b.rhop[x] = rp;
-        b.pp[x] = g * (accp + R(0.5) * rp * hk);
         accp += rp * hk;
         b.w[x] = dv;  // divergence of h_e u, finalised below
         divsum += dv;
@@ -96,7 +99,7 @@ __global__ void __launch_bounds__(128) k_cell_diag(DMesh m, DParams p, const R *
     for (int k = K - 1; k >= 0; k--) {
         const int x = k * Cp + i;
         const R hk = ld(hR + x);
-        b.zm[x] = -Hi + below + R(0.5) * hk;
+        b.cq[x].w = -Hi + below + R(0.5) * hk;
         below += hk;
         const R sk = PB ? sfc[x] : sfr[k];
         const R wk = (k == 0) ? R(0) : wk1 - b.w[x] + sk * divsum;
@@ -186,8 +189,10 @@ __global__ void __launch_bounds__(128) k_edge_pre(DMesh m, R *__restrict__ ubar,
             ut[x] = utk;
         }
         const R he = R(0.5) * (ld(hR + k * Cp + cc.x) + ld(hR + k * Cp + cc.y));
-        b.hu[x] = he * (ub + utk);
-        b.qe[x] = R(0.5) * (b.q[k * Vp + vv.x] + b.q[k * Vp + vv.y]);
+        V2<R> hq;
+        hq.x = he * (ub + utk);
+        hq.y = R(0.5) * (b.q[k * Vp + vv.x] + b.q[k * Vp + vv.y]);
+        b.hq[x] = hq;
         if (b.del2)   // del^2 u = grad(div u) - k x grad(curl u), normal component
             b.del2[x] = (b.delta[k * Cp + cc.y] - b.delta[k * Cp + cc.x]) * invdc -
                         (b.omega[k * Vp + vv.y] - b.omega[k * Vp + vv.x]) * invdv;
@@ -252,8 +257,12 @@ __global__ void __launch_bounds__(128) k_del2_divcurl(DMesh m, DiagBufs<R> b) {
 // column (Thomas; the modified super-diagonal goes to the scratch vmc), with
 // the wind explicit at the top and the bottom drag linearised about the speed
 // of the stage's input velocity; ut1 = u1 - ubar.
-template <class R, int NE2, bool VMIX, bool PB>
-__global__ void __launch_bounds__(128, 8) k_bcl_edge(DMesh m, DParams p, const R *__restrict__ ubar,
+// MINB: resident blocks per SM the kernel is compiled for (registers 65536 /
+// (128 x MINB)): 8 for short columns; 6 for deep ones, whose longer sliding
+// window over the layers would otherwise spill (measured on the 20-layer
+// channel and the 60-layer sphere).
+template <class R, int NE2, bool VMIX, bool PB, int MINB>
+__global__ void __launch_bounds__(128, MINB) k_bcl_edge(DMesh m, DParams p, const R *__restrict__ ubar,
                                                   const R *__restrict__ ut,
                                                   const R *__restrict__ hR,
                                                   const double *__restrict__ zeta, DiagBufs<R> b,
@@ -307,16 +316,18 @@ __global__ void __launch_bounds__(128, 8) k_bcl_edge(DMesh m, DParams p, const R
             he_next = R(0.5) * (ld(hR + (k + 1) * Cp + c1) + ld(hR + (k + 1) * Cp + c2));
         }
         // potential-vorticity flux
-        const R qk = b.qe[xe];
+        const R qk = b.hq[xe].y;
         R Q = R(0);
 #pragma unroll
         for (int j = 0; j < NE2; j++)
-            if (j < n2) Q += wl[j] * b.hu[k * Ep + eo[j]] * (R(0.5) * (qk + b.qe[k * Ep + eo[j]]));
+            if (j < n2) {
+                const V2<R> nb = b.hq[k * Ep + eo[j]];
+                Q += wl[j] * nb.x * (R(0.5) * (qk + nb.y));
+            }
         const int x1 = k * Cp + c1, x2 = k * Cp + c2;
-        const R gradK = (b.ke[x2] - b.ke[x1]) * invdc;
-        const R pgf = ((b.pp[x2] - b.pp[x1]) +
-                       g * (R(0.5) * (b.rhop[x1] + b.rhop[x2])) * (b.zm[x2] - b.zm[x1])) *
-                      invdc * inv_rho0;
+        const V4<R> A = b.cq[x1], B = b.cq[x2];    // (K, p', rho', z_mid) of both cells
+        const R gradK = (B.x - A.x) * invdc;
+        const R pgf = ((B.y - A.y) + g * (R(0.5) * (A.z + B.z)) * (B.w - A.w)) * invdc * inv_rho0;
         // vertical advection and viscosity at the top (k) and bottom (k+1) interfaces
         R Dk = R(0), wk = R(0), Dk1 = R(0), wk1 = R(0);
         if (k > 0) {
@@ -737,8 +748,14 @@ void launch_bcl_edge(const DMesh &m, const DParams &p, const R *ubar, const R *u
     const int nb = nblk(m.E, 128);
     const R ra = (R)a, rb = (R)bcoef, rdt = (R)dt;
 #define SSE_BCL(NE2, VM, PB)                                                                   \
-    k_bcl_edge<R, NE2, VM, PB><<<nb, 128, 0, s>>>(m, p, ubar, ut, hR, zeta, b, ut_n, ra, rb, rdt, \
-                                                  ut_out, G, vmc)
+    do {                                                                                       \
+        if (m.L >= 40)                                                                         \
+            k_bcl_edge<R, NE2, VM, PB, 6><<<nb, 128, 0, s>>>(m, p, ubar, ut, hR, zeta, b, ut_n,  \
+                                                             ra, rb, rdt, ut_out, G, vmc);     \
+        else                                                                                   \
+            k_bcl_edge<R, NE2, VM, PB, 8><<<nb, 128, 0, s>>>(m, p, ubar, ut, hR, zeta, b, ut_n,  \
+                                                             ra, rb, rdt, ut_out, G, vmc);     \
+    } while (0)
     const bool vm = vmc != nullptr, pb = m.partial != 0;
     if (m.maxE2 <= 10) {
         if (vm) { if (pb) SSE_BCL(10, true, true); else SSE_BCL(10, true, false); }
