@@ -14,7 +14,8 @@ flushed (a 512 MB write) between timed steps and the flush is excluded from
 the per-step CUDA-event times.  The same run also measures, under "also":
 the largest single mesh, the level-7 icosahedral sphere with 60 layers
 (114,689 ocean cells, T and S, wind stress; SSPRK3-SE, dt = 600 s, M = 40);
-the channel with Algorithm 2 (implicit vertical mixing); a 64-member uneven
+the channel with Algorithm 2 (implicit vertical mixing); the dt-refinement
+sweep of the channel (dt 60, 30, 15 s against 3.75 s, FP64 and mixed); a 64-member uneven
 ensemble batched through the request runtime against one member at a time;
 and a seeded Poisson request stream, mixed precision with continuous
 batching against FP64 one request at a time (p50/p99 time-to-horizon).
@@ -452,6 +453,7 @@ def run_stream(binding, specs, built, precision, max_active, budget, chunk, real
         inf = hd.wait(-1)
         if inf["status"] != "done":
             raise RuntimeError(f"request {inf['id']} ended with {inf['status']}")
+        hd.release()
         lat.append(inf["t_done"] - inf["t_submit"])
         units += un
     makespan = time.perf_counter() - t0
@@ -496,6 +498,38 @@ def measure_serving(binding, seed=0):
             "mixed_batched": mixed, "fp64_one_at_a_time": fp64,
             "throughput_ratio": mixed["value"] / fp64["value"],
             "p99_ratio": fp64["p99_s"] / mixed["p99_s"]}
+
+
+def measure_convergence(binding, T=960.0, n_list=(16, 32, 64), n_ref=256):
+    """The dt-refinement sweep of the 1 km channel: SSPRK3-SE with M = 30 held
+    fixed (dt and the sub-step shrink together), the paper's relative l2 error
+    of the top-layer velocity u_1 and thickness h_1 at time T against a run
+    with T / n_ref, on the GPU, FP64 and the mixed form."""
+    m, L, p, (u, h, tr), run = build_workload()
+    dm = binding.Mesh(m, L)
+    M = run["M"]
+
+    def solve(prec, n):
+        st = binding.State(dm, p, prec)
+        st.load_state(u, h, tr)
+        st.step(3, T / n, M, n)
+        gu, gh, _ = st.read_state()
+        st.close()
+        return gu[:, 0], gh[:, 0]
+
+    ru, rh = solve("fp64", n_ref)
+    out = {"T_s": T, "M": M, "dt_s": [T / n for n in n_list], "reference_dt_s": T / n_ref}
+    for prec in ("fp64", "mixed"):
+        eu, eh = [], []
+        for n in n_list:
+            a, b = solve(prec, n)
+            eu.append(float(np.linalg.norm(a - ru) / np.linalg.norm(ru)))
+            eh.append(float(np.linalg.norm(b - rh) / np.linalg.norm(rh)))
+        out[prec] = {"err_u1": eu, "err_h1": eh,
+                     "rate_u1": [float(np.log2(eu[i] / eu[i + 1])) for i in range(len(eu) - 1)],
+                     "rate_h1": [float(np.log2(eh[i] / eh[i + 1])) for i in range(len(eh) - 1)]}
+    dm.close()
+    return out
 
 
 def config_of(name, w, precision, world):
@@ -575,6 +609,8 @@ def run_ours(args):
             "kernels": vm["kernels"],
             "volume_rel_change": vm["forms_summary"]["mixed"]["volume_rel_change"]}
 
+    if args.workload == WORKLOAD and not args.no_sphere:
+        also["convergence"] = measure_convergence(binding)
     if args.workload == WORKLOAD and not args.no_serving:
         also["ensemble"] = measure_ensemble(binding, seed=rank)
         also["serving"] = measure_serving(binding, seed=rank)

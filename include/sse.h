@@ -327,6 +327,10 @@ int sse_server_query(sse_server *server, int64_t id, sse_request_info *info);
  * (SSE_ERR_TIMEOUT; timeout_s < 0 waits forever). */
 int sse_server_wait(sse_server *server, int64_t id, double timeout_s, sse_request_info *info);
 int sse_server_stats(sse_server *server, sse_server_info *info);
+/* Forget a finished (or failed, or cancelled) request's record so that a
+ * long-running server does not accumulate them; SSE_ERR_INVALID_ARG if the
+ * request is still waiting or running or the id is unknown. */
+int sse_server_release(sse_server *server, int64_t id);
 /* Cancel the requests still waiting (SSE_ERR_CANCELLED), let the admitted ones
  * finish, stop the worker and free everything. */
 void sse_server_destroy(sse_server *server);

@@ -87,7 +87,8 @@ EXPORTS = ["sse_mesh_create", "sse_mesh_destroy", "sse_state_create", "sse_state
            "sse_profile_read", "sse_barotropic_substep_noalloc", "sse_state_footprint",
            "sse_state_footprint_ex", "sse_state_create_ex", "sse_state_patches", "sse_tune",
            "sse_mesh_dims", "sse_server_create", "sse_server_submit", "sse_server_query",
-           "sse_server_wait", "sse_server_stats", "sse_server_destroy", "sse_strerror"]
+           "sse_server_wait", "sse_server_stats", "sse_server_release", "sse_server_destroy",
+           "sse_strerror"]
 KERNEL_CLASSES = ["cell_diag", "vertex", "edge_pre", "bcl_edge", "btr", "transport", "thickness",
                   "combine", "del4"]
 
@@ -139,6 +140,7 @@ def load(path: str = LIB_PATH):
     lib.sse_server_wait.argtypes = [ct.c_void_p, ct.c_int64, ct.c_double,
                                     ct.POINTER(RequestInfo)]
     lib.sse_server_stats.argtypes = [ct.c_void_p, ct.POINTER(ServerInfo)]
+    lib.sse_server_release.argtypes = [ct.c_void_p, ct.c_int64]
     lib.sse_server_destroy.argtypes = [ct.c_void_p]
     lib.sse_server_destroy.restype = None
     lib.sse_strerror.argtypes = [ct.c_int]
@@ -384,6 +386,11 @@ class Request:
         if out["status"] not in ("pending", "active"):
             self.server._bufs.pop(self.id, None)
         return out
+
+    def release(self):
+        """Drop the finished request's record in the server."""
+        _check(self.server.lib.sse_server_release(self.server.handle, self.id),
+               "sse_server_release")
 
 
 def _info(inf) -> dict:

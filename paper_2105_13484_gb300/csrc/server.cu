@@ -349,6 +349,18 @@ extern "C" int sse_server_wait(sse_server *S, int64_t id, double timeout_s,
                                                                             : SSE_OK;
 }
 
+extern "C" int sse_server_release(sse_server *S, int64_t id) {
+    if (!S) return SSE_ERR_INVALID_ARG;
+    std::lock_guard<std::mutex> lk(S->mu);
+    auto it = S->reqs.find(id);
+    if (it == S->reqs.end()) return SSE_ERR_INVALID_ARG;
+    Req *r = it->second;
+    if (r->status == SSE_REQ_PENDING || r->status == SSE_REQ_ACTIVE) return SSE_ERR_INVALID_ARG;
+    S->reqs.erase(it);
+    delete r;
+    return SSE_OK;
+}
+
 extern "C" int sse_server_stats(sse_server *S, sse_server_info *info) {
     if (!S || !info) return SSE_ERR_INVALID_ARG;
     std::lock_guard<std::mutex> lk(S->mu);

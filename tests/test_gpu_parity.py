@@ -433,3 +433,32 @@ def test_partial_bottom_sphere_fp64():
     me = (np.arange(L)[None, :] < Ke[:, None]).astype(float)
     bound = 2.0 * 3 * 2 * run["dt"] * _pgf_rounding(m, p, ref[1], ref[2], me)
     assert np.linalg.norm(gu - ref[0]) < bound, (np.linalg.norm(gu - ref[0]), bound)
+
+
+@pytest.mark.parametrize("order", [2, 3])
+def test_gpu_temporal_convergence_fp64(order):
+    """The GPU path's own dt-refinement sweep (M fixed): the paper's relative
+    l2 error of u_1 and h_1 against a run with dt/8 of the finest falls at
+    rate 2, like the oracle's."""
+    m, L, p, (u, h, tr) = inputs.channel_case(12, 16, 10e3, 6, perturb=True)
+    dm = binding.Mesh(m, L)
+    T, M = 1920.0, 8
+
+    def solve(n):
+        st = binding.State(dm, p, "fp64")
+        st.load_state(u, h, tr)
+        st.step(order, T / n, M, n)
+        out = st.read_state()
+        st.close()
+        return out
+
+    ref = solve(512)
+    eu, eh = [], []
+    for n in (16, 32, 64):
+        r = solve(n)
+        eu.append(rel(r[0][:, 0], ref[0][:, 0]))
+        eh.append(rel(r[1][:, 0], ref[1][:, 0]))
+    ru = np.log2(np.array(eu[:-1]) / np.array(eu[1:]))
+    rh = np.log2(np.array(eh[:-1]) / np.array(eh[1:]))
+    assert np.all(ru > 1.75) and np.all(rh > 1.75), (ru, rh)
+    assert np.all(ru < 2.6) and np.all(rh < 2.6), (ru, rh)

@@ -86,6 +86,9 @@ def test_admission_budget_order_and_backfill():
     reqs = [srv.submit(dm, p, "mixed", u, h, tr, 3, 200.0, 10, 5 + k) for k in range(7)]
     infos = [q.wait(300) for q in reqs]
     st = srv.stats()
+    reqs[0].release()                                    # the record is gone afterwards
+    with pytest.raises(binding.SSEError):
+        reqs[0].info()
     srv.close()
     assert all(i["status"] == "done" for i in infos)
     assert all(i["footprint"] == fp for i in infos)
