@@ -15,7 +15,7 @@ the per-step CUDA-event times.  The same run also measures, under "also":
 the largest single mesh, the level-7 icosahedral sphere with 60 layers
 (114,689 ocean cells, T and S, wind stress; SSPRK3-SE, dt = 600 s, M = 40);
 the channel with Algorithm 2 (implicit vertical mixing); the dt-refinement
-sweep of the channel (dt 60, 30, 15 s against 3.75 s, FP64 and mixed); a 64-member uneven
+sweep of the channel (dt 60 to 3.75 s against 0.47 s, FP64 and mixed); a 64-member uneven
 ensemble batched through the request runtime against one member at a time;
 and a seeded Poisson request stream, mixed precision with continuous
 batching against FP64 one request at a time (p50/p99 time-to-horizon).
@@ -500,7 +500,7 @@ def measure_serving(binding, seed=0):
             "p99_ratio": fp64["p99_s"] / mixed["p99_s"]}
 
 
-def measure_convergence(binding, T=960.0, n_list=(16, 32, 64), n_ref=256):
+def measure_convergence(binding, T=960.0, n_list=(16, 32, 64, 128, 256), n_ref=2048):
     """The dt-refinement sweep of the 1 km channel: SSPRK3-SE with M = 30 held
     fixed (dt and the sub-step shrink together), the paper's relative l2 error
     of the top-layer velocity u_1 and thickness h_1 at time T against a run
