@@ -305,7 +305,9 @@ __global__ void __launch_bounds__(128, MINB) k_bcl_edge(DMesh m, DParams p, cons
     R ut_cur = ut[e];
     R u_cur = ub + ut_cur;
     R he_cur = R(0.5) * (ld(hR + c1) + ld(hR + c2));
-    R u_prev = R(0), he_prev = R(0);
+    // the top interface of layer k is the bottom interface of layer k - 1: its
+    // shear D_zt(u) and edge w carry over from the previous layer (0 at k = 0)
+    R Dk = R(0), wk = R(0);
     R num = R(0), den = R(0), speed_b = R(0);
     for (int k = 0; k < K; k++) {
         const int xe = k * Ep + e;
@@ -329,11 +331,7 @@ __global__ void __launch_bounds__(128, MINB) k_bcl_edge(DMesh m, DParams p, cons
         const R gradK = (B.x - A.x) * invdc;
         const R pgf = ((B.y - A.y) + g * (R(0.5) * (A.z + B.z)) * (B.w - A.w)) * invdc * inv_rho0;
         // vertical advection and viscosity at the top (k) and bottom (k+1) interfaces
-        R Dk = R(0), wk = R(0), Dk1 = R(0), wk1 = R(0);
-        if (k > 0) {
-            Dk = (u_prev - u_cur) / (R(0.5) * (he_prev + he_cur));
-            wk = R(0.5) * (b.w[x1] + b.w[x2]);
-        }
+        R Dk1 = R(0), wk1 = R(0);
         if (k + 1 < K) {
             Dk1 = (u_cur - u_next) / (R(0.5) * (he_cur + he_next));
             wk1 = R(0.5) * (b.w[x1 + Cp] + b.w[x2 + Cp]);
@@ -371,7 +369,7 @@ __global__ void __launch_bounds__(128, MINB) k_bcl_edge(DMesh m, DParams p, cons
         num += he_cur * ut1;
         den += he_cur;
         ut_out[xe] = ut1;
-        u_prev = u_cur; he_prev = he_cur;
+        Dk = Dk1; wk = wk1;
         ut_cur = ut_next; u_cur = u_next; he_cur = he_next;
     }
     const R G = num / den / dt;
