@@ -242,18 +242,21 @@ int sse_barotropic_substep_noalloc(const sse_mesh *mesh, int order, double dt, i
                                    double *zeta_out, void *cuda_stream);
 
 /* Launch-shape choices of a state.  patch_cells: target cells per patch of
- * the tiled barotropic sub-cycle (one patch per SM, at most one per SM in
- * total; 0 = 64, i.e. as many patches as the mesh allows).  Larger patches
- * use fewer SMs for longer, which lets the sub-cycles of several states run
- * side by side. */
+ * the tiled barotropic sub-cycle.  0 (the default): one patch per SM, at most
+ * one patch per 64 cells.  A positive value asks for about that many cells per
+ * patch, up to two patches per SM (more than one patch per SM run as 512-thread
+ * blocks holding at most half an SM's shared memory each).  Larger patches use
+ * fewer SMs for longer, which lets the sub-cycles of several states run side
+ * by side. */
 typedef struct {
     int32_t patch_cells;
     int32_t reserved[7];     /* must be 0 */
 } sse_tuning;
 
 #define SSE_TUNE_LATENCY 0     /* the fastest sub-cycle                          */
-#define SSE_TUNE_THROUGHPUT 1  /* the least SM-time (duration x patches) within
-                                  twice the fastest                             */
+#define SSE_TUNE_THROUGHPUT 1  /* the least SM-time (duration x SMs held: one
+                                  per 1024-thread patch, half per 512-thread
+                                  patch) within twice the fastest              */
 
 int sse_state_create_ex(const sse_mesh *mesh, const sse_params *params,
                         const sse_tuning *tuning, void *cuda_stream, sse_state **out);

@@ -308,6 +308,7 @@ struct EngineBase {
     virtual int bcl_feuler(double dt) = 0;
     virtual int btr_substep(int order, double dt, int M) = 0;
     virtual int patches() const = 0;       // tiled sub-cycle patches (0: global kernel)
+    virtual int patch_threads() const = 0; // threads per patch of the tiled sub-cycle
     virtual bool has_del4() const = 0;     // biharmonic viscosity on
     virtual int diagnostics(sse_diag *out) = 0;
     long long steps = 0;
@@ -375,7 +376,7 @@ struct Engine : EngineBase {
     int recon = SSE_RECON_CONSISTENT;
     bool mixed = false;
     bool vmix = false;   // Algorithm 2 in every baroclinic stage
-    int patch_cells = 64;  // target cells per sub-cycle patch (sse_tuning)
+    int patch_cells = 0;   // target cells per sub-cycle patch (sse_tuning; 0: default)
     cudaStream_t s = nullptr;
     DevArena A;
     // state
@@ -403,8 +404,14 @@ struct Engine : EngineBase {
     bool tiled = false;
     DTiles<R> tiles{};
 
-    // Plan the tiled sub-cycle: patches of >= 64 owned cells, one or two
-    // blocks per SM, halo of 3 rings (one SSPRK3 sub-step per exchange).
+    // Plan the tiled sub-cycle: patches of about patch_cells owned cells, halo
+    // of 3 rings (one SSPRK3 sub-step per exchange).  The default (0) is one
+    // patch per SM (at most nSM patches of >= 64 cells) in 1024-thread
+    // blocks.  An explicit patch size may ask for up to two patches per SM:
+    // those run as 512-thread blocks holding at most half an SM's shared
+    // memory each.  Patches small enough that 512 threads do the same work
+    // per thread as 1024 (at most 512 entries of each kind) also take
+    // 512-thread blocks, so that the sub-cycles of two states can share an SM.
     int plan_tiles(const sse_mesh *mesh, int dev, int nsm) {
         const char *env = getenv("SSE_BTR_KERNEL");
         if (env && strcmp(env, "global") == 0) return SSE_OK;
@@ -412,12 +419,14 @@ struct Engine : EngineBase {
         CK(cudaDeviceGetAttribute(&smem_block, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
         CK(cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev));
         if (m.maxE2 > 10 || m.maxE > TILE_NCEP) return SSE_OK;
-        // patches of about patch_cells cells, at most one per SM; a plan whose
-        // patches are too large for one SM is retried with more patches
-        int P0 = std::max(1, std::min(nsm, m.C / std::max(patch_cells, 1)));
+        if (!tile_stencil_ok(mesh->host)) return SSE_OK;   // the global sub-cycle is exact for any stencil
+        // a plan whose patches are too large for their block is retried with
+        // more patches
+        const int Pmax = patch_cells > 0 ? 2 * nsm : nsm;
+        const int pc = patch_cells > 0 ? patch_cells : 64;
+        int P0 = std::max(1, std::min(Pmax, m.C / pc));
         for (int k = 1, P = P0; P > 0;
-             k++, P = (P >= nsm) ? 0 : std::min(nsm, std::max(P + 1, P * 5 / 4))) {
-            const int nthreads = 1024;
+             k++, P = (P >= Pmax) ? 0 : std::min(Pmax, std::max(P + 1, P * 5 / 4))) {
             const bool verbose = getenv("SSE_VERBOSE") != nullptr;
             std::shared_ptr<const TilePlan> cached;
             {
@@ -439,41 +448,44 @@ struct Engine : EngineBase {
             }
             const TilePlan &plan = *cached;
             // 16-bit byte offsets; at most 3 entries of each kind per thread
-            int own = 0;
+            int most = 0;
             bool small = true;
             for (const TilePatch &t : plan.patches) {
                 if ((size_t)(t.ne + 1) * sizeof(R) >= 65536 || (size_t)(t.nc + 1) * sizeof(R) >= 65536)
                     small = false;
-                const int most = std::max(std::max(t.n_own_e, t.ne - t.n_own_e),
-                                          std::max(t.n_own_c, t.nc - t.n_own_c));
-                own = std::max(own, (most + nthreads - 1) / nthreads);
-            }
-            own = std::max(own, 2);
-            if (!small || own > 3) {
-                if (verbose) fprintf(stderr, "libsse: tile plan k=%d: patch too large\n", k);
-                continue;
+                most = std::max(most, std::max(std::max(t.n_own_e, t.ne - t.n_own_e),
+                                               std::max(t.n_own_c, t.nc - t.n_own_c)));
             }
             const size_t smem = tile_smem_bytes(plan, m.maxE, m.maxE2, sizeof(R));
-            if (smem > (size_t)smem_block || smem > (size_t)smem_sm - 1024) {   // one CTA per SM
+            // the runtime reserves 1 KB of shared memory per block
+            const bool half_sm = most <= 3 * 512 && smem <= (size_t)smem_block &&
+                                 2 * (smem + 1024) <= (size_t)smem_sm;
+            const bool whole_sm = P <= nsm && most <= 3 * 1024 && smem <= (size_t)smem_block &&
+                                  smem + 1024 <= (size_t)smem_sm;
+            int nthreads = 0;
+            if (half_sm && (P > nsm || most <= 512)) nthreads = 512;
+            else if (whole_sm) nthreads = 1024;
+            if (!small || nthreads == 0) {
                 if (verbose)
-                    fprintf(stderr, "libsse: tile plan k=%d P=%d: smem %zu > limits %d/%d\n", k, P,
-                            smem, smem_block, smem_sm);
+                    fprintf(stderr, "libsse: tile plan k=%d P=%d: patch too large (%d entries, "
+                            "smem %zu, limits %d/%d)\n", k, P, most, smem, smem_block, smem_sm);
                 continue;
             }
+            const int own = std::max(2, (most + nthreads - 1) / nthreads);
 
             // the attribute belongs to the kernel, not to this state: allow the
             // device's whole opt-in size so that states of other meshes, whose
             // plans need less or more, never lower it under each other
             for (int o = 2; o <= 3; o++) {
                 cudaFuncAttributes fa;
-                CK(cudaFuncGetAttributes(&fa, btr_tiled_kernel_ptr<R>(o, own)));
-                CK(cudaFuncSetAttribute(btr_tiled_kernel_ptr<R>(o, own),
+                CK(cudaFuncGetAttributes(&fa, btr_tiled_kernel_ptr<R>(o, own, nthreads)));
+                CK(cudaFuncSetAttribute(btr_tiled_kernel_ptr<R>(o, own, nthreads),
                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
                                         smem_block - (int)fa.sharedSizeBytes));
             }
             int occ = 0;
-            CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, btr_tiled_kernel_ptr<R>(3, own),
-                                                             nthreads, smem));
+            CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+                &occ, btr_tiled_kernel_ptr<R>(3, own, nthreads), nthreads, smem));
             if (occ * nsm < P) {
                 if (verbose)
                     fprintf(stderr, "libsse: tile plan k=%d P=%d: occupancy %d x %d SMs\n", k, P,
@@ -487,8 +499,9 @@ struct Engine : EngineBase {
                     mne = std::max(mne, t.ne); mnc = std::max(mnc, t.nc);
                     moe = std::max(moe, t.n_own_e); tne += t.ne; tnc += t.nc;
                 }
-                fprintf(stderr, "libsse: tiled sub-cycle P=%d own=%d smem=%zu max(ne,nc,own_e)=(%d,%d,%d) "
-                        "halo overhead edges %.2f cells %.2f\n", P, own, smem, mne, mnc, moe,
+                fprintf(stderr, "libsse: tiled sub-cycle P=%d threads=%d own=%d smem=%zu "
+                        "max(ne,nc,own_e)=(%d,%d,%d) halo overhead edges %.2f cells %.2f\n", P,
+                        nthreads, own, smem, mne, mnc, moe,
                         (double)tne / m.E, (double)tnc / m.C);
             }
             return upload_tiles(plan, nthreads, own, smem);
@@ -498,11 +511,11 @@ struct Engine : EngineBase {
 
     int upload_tiles(const TilePlan &plan, int nthreads, int own, size_t smem) {
         const unsigned int sR = sizeof(R);
-        std::vector<int> noc, noe, cg, eg, c12, nel, ncl;
+        std::vector<int> noc, noe, nie, cg, eg, c12, nel, ncl;
         std::vector<unsigned short> eo, ce;
         std::vector<R> cf, idc, dv, Hh;
         for (const TilePatch &t : plan.patches) {
-            noc.push_back(t.n_own_c); noe.push_back(t.n_own_e);
+            noc.push_back(t.n_own_c); noe.push_back(t.n_own_e); nie.push_back(t.n_int_e);
             // sub-stage s of a sub-step needs edges of ring <= K - s and cells of
             // ring <= K - 1 - s (K = 3): the later sub-stages skip the outer rings
             for (int r = 2; r >= 0; r--) { nel.push_back(t.ne_ring[r]); ncl.push_back(t.nc_ring[r]); }
@@ -512,12 +525,18 @@ struct Engine : EngineBase {
                 const unsigned int a = (unsigned int)x & 0xffffu, b = (unsigned int)x >> 16;
                 c12.push_back((int)((a * sR) | ((b * sR) << 16)));
             }
+            // connectivity per entry (rows, copied to shared memory); coefficients
+            // term-major within the patch ([j][ne], [j][nc]) so that a warp's
+            // load of term j of 32 consecutive entries is one contiguous segment
+            const size_t cf0 = cf.size(), dv0 = dv.size();
+            cf.resize(cf0 + (size_t)t.ne * TILE_NE2P, R(0));
+            dv.resize(dv0 + (size_t)t.nc * TILE_NCEP, R(0));
             for (int k = 0; k < t.ne; k++) {
                 for (int j = 0; j < TILE_NE2P; j++) {
                     const bool on = j < t.n2[k];
                     const int le = on ? t.eoe[(size_t)k * m.maxE2 + j] : t.ne;
                     eo.push_back((unsigned short)(le * sR));
-                    cf.push_back(on ? (R)t.cfc[(size_t)k * m.maxE2 + j] : R(0));
+                    if (on) cf[cf0 + (size_t)j * t.ne + k] = (R)t.cfc[(size_t)k * m.maxE2 + j];
                 }
                 idc.push_back((R)t.invdc[k]);
             }
@@ -526,14 +545,14 @@ struct Engine : EngineBase {
                     const bool on = j < t.nce[k];
                     const int le = on ? t.ce[(size_t)k * m.maxE + j] : t.ne;
                     ce.push_back((unsigned short)(le * sR));
-                    dv.push_back(on ? (R)t.divc[(size_t)k * m.maxE + j] : R(0));
+                    if (on) dv[dv0 + (size_t)j * t.nc + k] = (R)t.divc[(size_t)k * m.maxE + j];
                 }
             for (double x : t.H) Hh.push_back((R)x);
         }
         DTiles<R> &t = tiles;
         t.P = plan.P; t.nthreads = nthreads; t.own = own; t.smem = smem;
         t.cell_off = A.upload(plan.cell_off); t.edge_off = A.upload(plan.edge_off);
-        t.n_own_c = A.upload(noc); t.n_own_e = A.upload(noe);
+        t.n_own_c = A.upload(noc); t.n_own_e = A.upload(noe); t.n_int_e = A.upload(nie);
         t.ne_lim = A.upload(nel); t.nc_lim = A.upload(ncl);
         t.cell_gid = A.upload(cg); t.edge_gid = A.upload(eg); t.c12 = A.upload(c12);
         t.eoe = A.upload(eo); t.cfc = A.upload(cf); t.invdc = A.upload(idc);
@@ -888,6 +907,7 @@ struct Engine : EngineBase {
     }
 
     int patches() const override { return tiled ? tiles.P : 0; }
+    int patch_threads() const override { return tiled ? tiles.nthreads : 0; }
     bool has_del4() const override { return db.del2 != nullptr; }
 
     int btr_substep(int order, double dt, int M) override {
@@ -964,7 +984,7 @@ static int make_state(const sse_mesh *mesh, const sse_params *prm, const sse_tun
                       void *stream, bool count_only, sse_state **out, size_t *bytes) {
     sse_state *st = new (std::nothrow) sse_state();
     if (!st) return SSE_ERR_OOM;
-    const int pc = (tun && tun->patch_cells > 0) ? tun->patch_cells : 64;
+    const int pc = (tun && tun->patch_cells > 0) ? tun->patch_cells : 0;
     int rc;
     size_t b = 0;
     if (prm->precision == SSE_FP64) {
@@ -1031,8 +1051,9 @@ extern "C" int sse_state_patches(const sse_state *st, int *patches) {
 // (M = 20 sub-steps, the kernel every large step calls two or three times)
 // is timed with CUDA events for each candidate patch size on a zero state of
 // this mesh; LATENCY keeps the fastest, THROUGHPUT the one with the least
-// SM-time (duration x patches, one SM each), among those within twice the
-// fastest.  Results are cached per mesh, precision and objective.
+// SM-time (duration x the SMs the patches hold: one per 1024-thread patch,
+// half per 512-thread patch), among those within twice the fastest.  Results
+// are cached per mesh, precision and objective.
 extern "C" int sse_tune(const sse_mesh *mesh, const sse_params *prm, int objective,
                         sse_tuning *out) {
     if (!mesh || !prm || !out || (objective != SSE_TUNE_LATENCY &&
@@ -1057,7 +1078,7 @@ extern "C" int sse_tune(const sse_mesh *mesh, const sse_params *prm, int objecti
     cudaEventCreate(&e1);
     const int C = mesh->dm.C;
     const int cands[] = {64, 128, 256, 384, 512, 768, 1024, 1536};
-    std::vector<std::pair<int, std::pair<float, int>>> res;   // (cells, (ms, patches))
+    std::vector<std::pair<int, std::pair<float, double>>> res;   // (cells, (ms, SMs held))
     int last_P = -1, rc = SSE_OK;
     for (int pc : cands) {
         if (pc > 64 && C / pc < 1) break;
@@ -1066,7 +1087,8 @@ extern "C" int sse_tune(const sse_mesh *mesh, const sse_params *prm, int objecti
         sse_state *st = nullptr;
         rc = make_state(mesh, prm, &t, s, false, &st, nullptr);
         if (rc) break;
-        int P = st->eng->patches();
+        const int P = st->eng->patches();
+        const double sms = P * (st->eng->patch_threads() / 1024.0);
         if (P == 0 || P == last_P) {     // no tiled plan, or the same plan again
             delete st;
             if (P == 0) break;
@@ -1085,14 +1107,14 @@ extern "C" int sse_tune(const sse_mesh *mesh, const sse_params *prm, int objecti
         }
         delete st;
         if (rc) break;
-        res.push_back({pc, {best, P}});
+        res.push_back({pc, {best, sms}});
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     cudaStreamSynchronize(s);
     cudaStreamDestroy(s);
     if (rc) return rc;
-    int choice = 64;
+    int choice = 0;
     if (!res.empty()) {
         float fastest = 1e30f;
         for (auto &r : res) fastest = std::min(fastest, r.second.first);

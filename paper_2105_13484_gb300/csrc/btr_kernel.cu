@@ -82,6 +82,40 @@ __device__ __forceinline__ bool grid_barrier(const Barrier &bar, unsigned int &g
     return s_ok != 0;
 }
 
+// Split-phase grid barrier over the same count word: grid_arrive releases
+// this block's earlier writes and adds one arrival without waiting for the
+// reply; grid_wait returns once `target` arrivals are in (acquire), so a block
+// can do work that needs no other block's data in between.  Both are called
+// by every thread of the block; grid_wait returns false, after setting *err,
+// if the wait exceeded its budget.
+__device__ __forceinline__ void grid_arrive(const Barrier &bar) {
+    __syncthreads();
+    if (threadIdx.x == 0)
+        asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(bar.count) : "memory");
+}
+__device__ __forceinline__ bool grid_wait(const Barrier &bar, unsigned int target) {
+    __shared__ int s_ok;
+    if (threadIdx.x == 0) {
+        int ok = 1;
+        const unsigned long long t0 = gtimer();
+        unsigned int spins = 0;
+        while (ld_acquire(bar.count) < target) {
+            if ((++spins & 255u) == 0) {
+                if (ld_acquire((const unsigned int *)bar.err) ||
+                    gtimer() - t0 > (unsigned long long)BARRIER_SPIN_NS) {
+                    atomicExch(bar.err, 1);
+                    ok = 0;
+                    break;
+                }
+            }
+            __nanosleep(20);
+        }
+        s_ok = ok;
+    }
+    __syncthreads();
+    return s_ok != 0;
+}
+
 constexpr int BTR_NIT = 8;    // edges (and cells) owned per thread, at most
 constexpr int BTR_NE2 = 10;   // edgesOnEdge handled by the unrolled gather
 
@@ -255,7 +289,8 @@ __global__ void __launch_bounds__(BTR_THREADS) k_btr(DMesh m, BtrArgs<R> a, Barr
 // through a double-buffered exchange array and one grid barrier refreshes the
 // halo.  M grid barriers per call instead of 2M or 3M.
 // ---------------------------------------------------------------------------
-constexpr int TILE_THREADS = 1024;
+// threads per patch: one 1024-thread block per SM, or two 512-thread blocks
+// (two patches) per SM whose block barriers overlap each other's work
 constexpr int TILE_NE2 = 10;  // edgesOnEdge terms evaluated per edge (padding -> dummy, 0)
 
 template <class R> struct TileSmem {
@@ -289,27 +324,15 @@ template <class R> __device__ __forceinline__ R at(const R *base, unsigned int o
     return *(const R *)((const char *)base + off);
 }
 
-// the coefficients of one edge (TILE_NE2P) or one cell (TILE_NCEP) with paired
-// loads (rows are 8-byte aligned in FP32 and 16-byte aligned in FP64)
-__device__ __forceinline__ void ldc(const float *p, float *c, int n) {
-    for (int i = 0; i < n / 2; i++) {
-        const float2 v = __ldg((const float2 *)p + i);
-        c[2 * i] = v.x; c[2 * i + 1] = v.y;
-    }
-}
-__device__ __forceinline__ void ldc(const double *p, double *c, int n) {
-    for (int i = 0; i < n / 2; i++) {
-        const double2 v = __ldg((const double2 *)p + i);
-        c[2 * i] = v.x; c[2 * i + 1] = v.y;
-    }
-}
-
-// forward-Euler edge update on the patch: returns the new ubar, sets the flux
+// forward-Euler edge update on the patch: returns the new ubar, sets the flux.
+// The patch's Coriolis coefficients are term-major: term j of edge l at
+// cfc[j * ne + l].
 template <class R>
-__device__ __forceinline__ R tile_fe_edge(const TileSmem<R> &S, const R *__restrict__ cfc, int l,
-                                          const R *u, const R *z, R tau, R g, R &flux) {
+__device__ __forceinline__ R tile_fe_edge(const TileSmem<R> &S, const R *__restrict__ cfc, int ne,
+                                          int l, const R *u, const R *z, R tau, R g, R &flux) {
     R cf[TILE_NE2P];
-    ldc(cfc + (size_t)l * TILE_NE2P, cf, TILE_NE2P);
+#pragma unroll
+    for (int j = 0; j < TILE_NE2P; j++) cf[j] = __ldg(cfc + (size_t)j * ne + l);
     const unsigned int *eo = (const unsigned int *)(S.eoe + (size_t)l * TILE_NE2P);
     unsigned int o[TILE_NE2P];
 #pragma unroll
@@ -328,11 +351,13 @@ __device__ __forceinline__ R tile_fe_edge(const TileSmem<R> &S, const R *__restr
     return ue + tau * (acc - g * (zb - za) * S.idc[l] + S.G[l]);
 }
 
+// term j of cell l's divergence coefficients at dvc[j * nc + l]
 template <class R>
-__device__ __forceinline__ R tile_fe_cell(const TileSmem<R> &S, const R *__restrict__ dvc, int l,
-                                          const R *z, R tau) {
+__device__ __forceinline__ R tile_fe_cell(const TileSmem<R> &S, const R *__restrict__ dvc, int nc,
+                                          int l, const R *z, R tau) {
     R dc[TILE_NCEP];
-    ldc(dvc + (size_t)l * TILE_NCEP, dc, TILE_NCEP);
+#pragma unroll
+    for (int j = 0; j < TILE_NCEP; j++) dc[j] = __ldg(dvc + (size_t)j * nc + l);
     const unsigned int *co = (const unsigned int *)(S.ce + (size_t)l * TILE_NCEP);
     unsigned int o[TILE_NCEP];
 #pragma unroll
@@ -349,14 +374,14 @@ __device__ __forceinline__ R tile_fe_cell(const TileSmem<R> &S, const R *__restr
 // Each thread owns at most OWN owned edges, halo edges, owned cells and halo
 // cells of its patch (the plan checks this); their global indices, the
 // sub-step's partial F^zeta and the FP64 accumulators stay in registers.
-template <class R, int ORDER, int OWN>
-__global__ void __launch_bounds__(TILE_THREADS, 1) k_btr_tiled(DTiles<R> t, BtrArgs<R> a,
-                                                               Barrier bar) {
+template <class R, int ORDER, int OWN, int NT>
+__global__ void __launch_bounds__(NT, 1024 / NT) k_btr_tiled(DTiles<R> t, BtrArgs<R> a,
+                                                             Barrier bar) {
     extern __shared__ __align__(16) char smem_raw[];
     const int p = blockIdx.x, tid = threadIdx.x, nt = blockDim.x;
     const int coff = t.cell_off[p], eoff = t.edge_off[p];
     const int nc = t.cell_off[p + 1] - coff, ne = t.edge_off[p + 1] - eoff;
-    const int noc = t.n_own_c[p], noe = t.n_own_e[p];
+    const int noc = t.n_own_c[p], noe = t.n_own_e[p], nint = t.n_int_e[p];
     // sub-stage s only needs the edges and cells still exact after it (the
     // outer rings of the halo drop out one per sub-stage)
     const int neA = t.ne_lim[3 * p], neB = t.ne_lim[3 * p + 1], neC = t.ne_lim[3 * p + 2];
@@ -366,8 +391,6 @@ __global__ void __launch_bounds__(TILE_THREADS, 1) k_btr_tiled(DTiles<R> t, BtrA
     const R *dvc = t.divc + (size_t)coff * TILE_NCEP;
     const R tau = (R)a.tau, g = (R)a.g;
     const R third = R(1.0 / 3.0), two_thirds = R(2.0 / 3.0);
-    unsigned int gen = 0;
-
     // global indices of this thread's owned and halo entries
     int oe[OWN], he[OWN], oc[OWN], hc[OWN];
 #pragma unroll
@@ -426,24 +449,26 @@ __global__ void __launch_bounds__(TILE_THREADS, 1) k_btr_tiled(DTiles<R> t, BtrA
     const double invM = 1.0 / a.M;
     int buf = 0;
     for (int j = 0; j < a.M; j++) {
-        // ---- stage a: (ua, za) = FE(u0, z0)
+        // ---- stage a: (ua, za) = FE(u0, z0); after the first sub-step the owned
+        // edges below nint were already done while the halo exchange was in flight
+        const int lo = j == 0 ? 0 : nint;
 #pragma unroll
         for (int k = 0; k < OWN; k++) {
             const int l = tid + k * nt;
-            if (l < noe) {
+            if (l >= lo && l < noe) {
                 R f;
-                S.ua[l] = tile_fe_edge<R>(S, cfc, l, S.u0, S.z0, tau, g, f);
+                S.ua[l] = tile_fe_edge<R>(S, cfc, ne, l, S.u0, S.z0, tau, g, f);
                 S.fl[l] = f;
                 Fs[k] = wAB * f;
             }
         }
         for (int l = noe + tid; l < neA; l += nt) {
             R f;
-            S.ua[l] = tile_fe_edge<R>(S, cfc, l, S.u0, S.z0, tau, g, f);
+            S.ua[l] = tile_fe_edge<R>(S, cfc, ne, l, S.u0, S.z0, tau, g, f);
             S.fl[l] = f;
         }
         __syncthreads();
-        for (int l = tid; l < ncA; l += nt) S.za[l] = tile_fe_cell<R>(S, dvc, l, S.z0, tau);
+        for (int l = tid; l < ncA; l += nt) S.za[l] = tile_fe_cell<R>(S, dvc, nc, l, S.z0, tau);
         __syncthreads();
         // ---- stage b: FE(ua, za), first convex combination
 #pragma unroll
@@ -451,7 +476,7 @@ __global__ void __launch_bounds__(TILE_THREADS, 1) k_btr_tiled(DTiles<R> t, BtrA
             const int l = tid + k * nt;
             if (l < noe) {
                 R f;
-                const R ub = tile_fe_edge<R>(S, cfc, l, S.ua, S.za, tau, g, f);
+                const R ub = tile_fe_edge<R>(S, cfc, ne, l, S.ua, S.za, tau, g, f);
                 S.fl[l] = f;
                 Fs[k] += wAB * f;
                 if (ORDER == 2) S.u0[l] = R(0.5) * (S.u0[l] + ub);
@@ -460,14 +485,14 @@ __global__ void __launch_bounds__(TILE_THREADS, 1) k_btr_tiled(DTiles<R> t, BtrA
         }
         for (int l = noe + tid; l < neB; l += nt) {
             R f;
-            const R ub = tile_fe_edge<R>(S, cfc, l, S.ua, S.za, tau, g, f);
+            const R ub = tile_fe_edge<R>(S, cfc, ne, l, S.ua, S.za, tau, g, f);
             S.fl[l] = f;
             if (ORDER == 2) S.u0[l] = R(0.5) * (S.u0[l] + ub);
             else S.uh[l] = R(0.75) * S.u0[l] + R(0.25) * ub;
         }
         __syncthreads();
         for (int l = tid; l < ncB; l += nt) {
-            const R zb = tile_fe_cell<R>(S, dvc, l, S.za, tau);
+            const R zb = tile_fe_cell<R>(S, dvc, nc, l, S.za, tau);
             if (ORDER == 2) S.z0[l] = R(0.5) * (S.z0[l] + zb);
             else S.zh[l] = R(0.75) * S.z0[l] + R(0.25) * zb;
         }
@@ -479,7 +504,7 @@ __global__ void __launch_bounds__(TILE_THREADS, 1) k_btr_tiled(DTiles<R> t, BtrA
                 const int l = tid + k * nt;
                 if (l < noe) {
                     R f;
-                    const R uc = tile_fe_edge<R>(S, cfc, l, S.uh, S.zh, tau, g, f);
+                    const R uc = tile_fe_edge<R>(S, cfc, ne, l, S.uh, S.zh, tau, g, f);
                     S.fl[l] = f;
                     Fs[k] += wC * f;
                     S.u0[l] = third * S.u0[l] + two_thirds * uc;
@@ -487,13 +512,13 @@ __global__ void __launch_bounds__(TILE_THREADS, 1) k_btr_tiled(DTiles<R> t, BtrA
             }
             for (int l = noe + tid; l < neC; l += nt) {
                 R f;
-                const R uc = tile_fe_edge<R>(S, cfc, l, S.uh, S.zh, tau, g, f);
+                const R uc = tile_fe_edge<R>(S, cfc, ne, l, S.uh, S.zh, tau, g, f);
                 S.fl[l] = f;
                 S.u0[l] = third * S.u0[l] + two_thirds * uc;
             }
             __syncthreads();
             for (int l = tid; l < ncC; l += nt) {
-                const R zc = tile_fe_cell<R>(S, dvc, l, S.zh, tau);
+                const R zc = tile_fe_cell<R>(S, dvc, nc, l, S.zh, tau);
                 S.z0[l] = third * S.z0[l] + two_thirds * zc;
             }
             __syncthreads();
@@ -508,7 +533,22 @@ __global__ void __launch_bounds__(TILE_THREADS, 1) k_btr_tiled(DTiles<R> t, BtrA
             if (oe[k] >= 0) xu[oe[k]] = S.u0[tid + k * nt];
             if (oc[k] >= 0) xz[oc[k]] = S.z0[tid + k * nt];
         }
-        if (!grid_barrier(bar, gen, gridDim.x)) return;
+        grid_arrive(bar);
+        // Stage a of the next sub-step on the owned edges with both cells owned
+        // (l < nint): it reads zeta at owned cells and ubar at edges of owned
+        // cells (ring <= 1), all exact after this sub-step's last stage, and
+        // writes only ua and the flux, which the refresh does not touch.
+#pragma unroll
+        for (int k = 0; k < OWN; k++) {
+            const int l = tid + k * nt;
+            if (l < nint) {
+                R f;
+                S.ua[l] = tile_fe_edge<R>(S, cfc, ne, l, S.u0, S.z0, tau, g, f);
+                S.fl[l] = f;
+                Fs[k] = wAB * f;
+            }
+        }
+        if (!grid_wait(bar, (unsigned int)(j + 1) * gridDim.x)) return;
 #pragma unroll
         for (int k = 0; k < OWN; k++) {
             if (he[k] >= 0) S.u0[noe + tid + k * nt] = __ldcg(xu + he[k]);
@@ -529,10 +569,17 @@ __global__ void __launch_bounds__(TILE_THREADS, 1) k_btr_tiled(DTiles<R> t, BtrA
     }
 }
 
-template <class R> const void *btr_tiled_kernel_ptr(int order, int own) {
+template <class R, int NT> const void *btr_tiled_kernel_ptr_nt(int order, int own) {
     if (own == 2)
-        return order == 2 ? (const void *)k_btr_tiled<R, 2, 2> : (const void *)k_btr_tiled<R, 3, 2>;
-    return order == 2 ? (const void *)k_btr_tiled<R, 2, 3> : (const void *)k_btr_tiled<R, 3, 3>;
+        return order == 2 ? (const void *)k_btr_tiled<R, 2, 2, NT>
+                          : (const void *)k_btr_tiled<R, 3, 2, NT>;
+    return order == 2 ? (const void *)k_btr_tiled<R, 2, 3, NT>
+                      : (const void *)k_btr_tiled<R, 3, 3, NT>;
+}
+template <class R> const void *btr_tiled_kernel_ptr(int order, int own, int nthreads) {
+    if (nthreads == 512) return btr_tiled_kernel_ptr_nt<R, 512>(order, own);
+    if (nthreads == 1024) return btr_tiled_kernel_ptr_nt<R, 1024>(order, own);
+    return nullptr;
 }
 
 template <class R>
@@ -552,11 +599,13 @@ cudaError_t launch_btr_tiled(const DTiles<R> &t, const BtrArgs<R> &a, const Barr
     attr[0].val.cooperative = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    return cudaLaunchKernelExC(&cfg, btr_tiled_kernel_ptr<R>(a.order, t.own), args);
+    const void *fn = btr_tiled_kernel_ptr<R>(a.order, t.own, t.nthreads);
+    if (!fn) return cudaErrorInvalidConfiguration;
+    return cudaLaunchKernelExC(&cfg, fn, args);
 }
 
-template const void *btr_tiled_kernel_ptr<double>(int, int);
-template const void *btr_tiled_kernel_ptr<float>(int, int);
+template const void *btr_tiled_kernel_ptr<double>(int, int, int);
+template const void *btr_tiled_kernel_ptr<float>(int, int, int);
 template cudaError_t launch_btr_tiled<double>(const DTiles<double> &, const BtrArgs<double> &,
                                               const Barrier &, cudaStream_t);
 template cudaError_t launch_btr_tiled<float>(const DTiles<float> &, const BtrArgs<float> &,

@@ -157,14 +157,15 @@ template <class R> struct DTiles {
     int P, nthreads, own;            // patches, threads per patch, entries per thread
     const int *cell_off, *edge_off;  // [P + 1]
     const int *n_own_c, *n_own_e;    // [P]
+    const int *n_int_e;              // [P] owned edges with both cells owned (local 0..)
     const int *ne_lim, *nc_lim;      // [P][3] local edges / cells exact after 0, 1, 2 sub-stages
     const int *cell_gid, *edge_gid;  // local -> global
     const int *c12;                  // [sum ne] byte offsets of local (c1, c2): c1 | c2 << 16
     const unsigned short *eoe;       // [sum ne][TILE_NE2P] byte offsets of local edgesOnEdge
-    const R *cfc;                    // [sum ne][TILE_NE2P] Coriolis coefficients (0 on padding)
+    const R *cfc;                    // per patch [TILE_NE2P][ne] Coriolis coefficients (0 on padding)
     const R *invdc;                  // [sum ne]
     const unsigned short *ce;        // [sum nc][TILE_NCEP] byte offsets of local edgesOnCell
-    const R *divc;                   // [sum nc][TILE_NCEP] divergence coefficients
+    const R *divc;                   // per patch [TILE_NCEP][nc] divergence coefficients
     const R *H;                      // patch p at cell_off[p] + p: [nc_p + 1]
     R *xu[2];                        // [Ep] exchange of owned ubar, double-buffered
     R *xz[2];                        // [Cp] exchange of owned zeta
@@ -173,7 +174,9 @@ template <class R> struct DTiles {
 template <class R>
 cudaError_t launch_btr_tiled(const DTiles<R> &t, const BtrArgs<R> &a, const Barrier &bar,
                              cudaStream_t s);
-template <class R> const void *btr_tiled_kernel_ptr(int order, int own);
+// kernel of the tiled sub-cycle for (order, entries per thread, threads per
+// patch: 512 or 1024); null for another thread count
+template <class R> const void *btr_tiled_kernel_ptr(int order, int own, int nthreads);
 
 template <class R> struct TransportArgs {
     const R *hR;              // stage thickness [L][Cp] in the tendency precision

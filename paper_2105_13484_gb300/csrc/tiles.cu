@@ -80,6 +80,16 @@ void bisect(const std::vector<std::vector<int>> &adj, std::vector<int> cells, in
 
 }  // namespace
 
+bool tile_stencil_ok(const HostMesh &hm) {
+    for (int e = 0; e < hm.E; e++)
+        for (int j = 0; j < hm.neoe[e]; j++) {
+            const int ep = hm.eoe[(size_t)e * hm.maxE2 + j];
+            const int a = hm.c1[ep], b = hm.c2[ep];
+            if (a != hm.c1[e] && a != hm.c2[e] && b != hm.c1[e] && b != hm.c2[e]) return false;
+        }
+    return true;
+}
+
 bool build_tile_plan(const HostMesh &hm, int P, int K, TilePlan &plan) {
     const int C = hm.C, E = hm.E;
     // cell adjacency through edges
@@ -135,7 +145,12 @@ bool build_tile_plan(const HostMesh &hm, int P, int K, TilePlan &plan) {
             const int a = dist[hm.c1[e]], b = dist[hm.c2[e]];
             return std::max(a == INT_MAX ? K + 1 : a, b == INT_MAX ? K + 1 : b);
         };
-        std::sort(Eo.begin(), Eo.end());
+        // owned edges of ring 0 (both cells owned) first: their next forward-Euler
+        // stage reads only values that are exact before the halo is refreshed
+        std::sort(Eo.begin(), Eo.end(), [&](int a, int b) {
+            const int ra = ering(a), rb = ering(b);
+            return ra != rb ? ra < rb : a < b;
+        });
         std::sort(Eh.begin(), Eh.end(), [&](int a, int b) {
             const int ra = ering(a), rb = ering(b);
             return ra != rb ? ra < rb : a < b;
@@ -155,6 +170,8 @@ bool build_tile_plan(const HostMesh &hm, int P, int K, TilePlan &plan) {
         tp.nc = nc; tp.ne = ne;
         tp.n_own_c = (int)own[p].size();
         tp.n_own_e = (int)Eo.size();
+        tp.n_int_e = 0;
+        for (int e : Eo) tp.n_int_e += ering(e) == 0;
         tp.cell_gid = X;
         tp.edge_gid = Ed;
         tp.c12.resize(ne);

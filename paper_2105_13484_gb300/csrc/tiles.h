@@ -25,6 +25,7 @@ struct HostMesh {
 
 struct TilePatch {
     int nc = 0, ne = 0, n_own_c = 0, n_own_e = 0;
+    int n_int_e = 0;                       // owned edges with both cells owned (first)
     std::vector<int> cell_gid, edge_gid;   // local -> global (owned first)
     std::vector<int32_t> c12;              // [ne] local c1 | c2 << 16
     std::vector<int16_t> n2;               // [ne]
@@ -49,8 +50,13 @@ struct TilePlan {
 
 // Partition into P patches with halos of K rings; false if a patch would
 // need more than 32766 local entries.  Local order: owned cells, then halo
-// cells by ring; owned edges (first cell owned), then halo edges by ring.
+// cells by ring; owned edges (first cell owned: those with both cells owned,
+// then the others), then halo edges by ring.
 bool build_tile_plan(const HostMesh &hm, int P, int K, TilePlan &plan);
+// True if every edgesOnEdge entry of an edge is an edge of one of its two
+// cells (the TRiSK stencil): the ring counts of a plan, which decide which
+// halo values are exact after each sub-stage, rely on it.
+bool tile_stencil_ok(const HostMesh &hm);
 // Dynamic shared memory of the largest patch for element size sR.
 size_t tile_smem_bytes(const TilePlan &plan, int maxE, int maxE2, size_t sR);
 

@@ -140,9 +140,10 @@ def _rel(a, b):
 
 def test_patch_size_keeps_results_within_rounding_and_the_tuner_picks_a_candidate():
     """The partition of the tiled sub-cycle only changes which code path (an
-    owned or a halo copy of an edge) rounds a value first, so results with 2,
-    7 or 28 patches agree to the mixed form's rounding, far inside its error
-    bounds against the oracle (u 1e-4, h 1e-9, tracers 1e-6)."""
+    owned or a halo copy of an edge) rounds a value first, so results with
+    three different patch counts (and 512- or 1024-thread patches) agree to the
+    mixed form's rounding, far inside its error bounds against the oracle
+    (u 1e-4, h 1e-9, tracers 1e-6)."""
     m, L, p, (u, h, tr), run = inputs.workload("sphere_l4", perturb=True)
     dm = binding.Mesh(m, L)
     outs, patches = [], []
