@@ -86,16 +86,17 @@ __device__ __forceinline__ bool grid_barrier(const Barrier &bar, unsigned int &g
 // this block's earlier writes and adds one arrival without waiting for the
 // reply; grid_wait returns once `target` arrivals are in (acquire), so a block
 // can do work that needs no other block's data in between.  Both are called
-// by every thread of the block; grid_wait returns false, after setting *err,
-// if the wait exceeded its budget.
+// by every thread of the block; the block's last thread arrives and polls.
+// grid_wait returns false, after setting *err, if the wait exceeded its
+// budget.
 __device__ __forceinline__ void grid_arrive(const Barrier &bar) {
     __syncthreads();
-    if (threadIdx.x == 0)
+    if (threadIdx.x == blockDim.x - 1)
         asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(bar.count) : "memory");
 }
 __device__ __forceinline__ bool grid_wait(const Barrier &bar, unsigned int target) {
     __shared__ int s_ok;
-    if (threadIdx.x == 0) {
+    if (threadIdx.x == blockDim.x - 1) {
         int ok = 1;
         const unsigned long long t0 = gtimer();
         unsigned int spins = 0;
@@ -371,6 +372,31 @@ __device__ __forceinline__ R tile_fe_cell(const TileSmem<R> &S, const R *__restr
     return z[l] - tau * dv;
 }
 
+// Accumulator of F^zeta = (1/M) sum_j (sub-step flux sum) for one owned
+// edge.  FP64 form: a double.  Mixed form: the sub-step sums are FP32 and are
+// added into an unevaluated pair of floats (hi, lo) with Knuth's TwoSum, which
+// yields the exact rounding error of each addition; the pair carries about
+// 48 significant bits, and FP64 is needed only once, at the end.  (FP64 adds
+// run at a small fraction of the FP32 rate on this GPU; one per owned edge
+// and sub-step costs more than a sub-stage's cell update.)
+template <class R> struct FzAcc;
+template <> struct FzAcc<float> {
+    float hi = 0.f, lo = 0.f;
+    __device__ __forceinline__ void add(float x, double) {
+        const float s = hi + x, bp = s - hi;
+        lo += (hi - (s - bp)) + (x - bp);
+        hi = s;
+    }
+    __device__ __forceinline__ double value(double invM) const {
+        return invM * ((double)hi + (double)lo);
+    }
+};
+template <> struct FzAcc<double> {
+    double s = 0.0;
+    __device__ __forceinline__ void add(double x, double invM) { s += invM * x; }
+    __device__ __forceinline__ double value(double) const { return s; }
+};
+
 // Each thread owns at most OWN owned edges, halo edges, owned cells and halo
 // cells of its patch (the plan checks this); their global indices, the
 // sub-step's partial F^zeta and the FP64 accumulators stay in registers.
@@ -382,6 +408,7 @@ __global__ void __launch_bounds__(NT, 1024 / NT) k_btr_tiled(DTiles<R> t, BtrArg
     const int coff = t.cell_off[p], eoff = t.edge_off[p];
     const int nc = t.cell_off[p + 1] - coff, ne = t.edge_off[p + 1] - eoff;
     const int noc = t.n_own_c[p], noe = t.n_own_e[p], nint = t.n_int_e[p];
+    const bool arriver = (tid >> 5) == ((nt - 1) >> 5);   // the warp of grid_arrive / grid_wait
     // sub-stage s only needs the edges and cells still exact after it (the
     // outer rings of the halo drop out one per sub-stage)
     const int neA = t.ne_lim[3 * p], neB = t.ne_lim[3 * p + 1], neC = t.ne_lim[3 * p + 2];
@@ -439,9 +466,9 @@ __global__ void __launch_bounds__(NT, 1024 / NT) k_btr_tiled(DTiles<R> t, BtrArg
         for (int x = tid; x < n4; x += nt) dst[x] = src[x];
     }
     R Fs[OWN];
-    double Fz[OWN];
+    FzAcc<R> Fz[OWN];
 #pragma unroll
-    for (int k = 0; k < OWN; k++) { Fs[k] = R(0); Fz[k] = 0.0; }
+    for (int k = 0; k < OWN; k++) Fs[k] = R(0);
     __syncthreads();
 
     const R wAB = (ORDER == 2) ? R(0.5) : R(1.0 / 6.0);
@@ -450,8 +477,9 @@ __global__ void __launch_bounds__(NT, 1024 / NT) k_btr_tiled(DTiles<R> t, BtrArg
     int buf = 0;
     for (int j = 0; j < a.M; j++) {
         // ---- stage a: (ua, za) = FE(u0, z0); after the first sub-step the owned
-        // edges below nint were already done while the halo exchange was in flight
-        const int lo = j == 0 ? 0 : nint;
+        // edges below nint were already done while the halo exchange was in
+        // flight, except by the arriving warp
+        const int lo = (j == 0 || arriver) ? 0 : nint;
 #pragma unroll
         for (int k = 0; k < OWN; k++) {
             const int l = tid + k * nt;
@@ -524,7 +552,7 @@ __global__ void __launch_bounds__(NT, 1024 / NT) k_btr_tiled(DTiles<R> t, BtrArg
             __syncthreads();
         }
 #pragma unroll
-        for (int k = 0; k < OWN; k++) Fz[k] += invM * (double)Fs[k];
+        for (int k = 0; k < OWN; k++) Fz[k].add(Fs[k], invM);
         if (j + 1 == a.M) break;
         // ---- exchange the owned values, refresh the halo
         R *xu = t.xu[buf], *xz = t.xz[buf];
@@ -537,11 +565,13 @@ __global__ void __launch_bounds__(NT, 1024 / NT) k_btr_tiled(DTiles<R> t, BtrArg
         // Stage a of the next sub-step on the owned edges with both cells owned
         // (l < nint): it reads zeta at owned cells and ubar at edges of owned
         // cells (ring <= 1), all exact after this sub-step's last stage, and
-        // writes only ua and the flux, which the refresh does not touch.
+        // writes only ua and the flux, which the refresh does not touch.  The
+        // arriving warp, which waits for its release first, leaves its share
+        // to the main stage a.
 #pragma unroll
         for (int k = 0; k < OWN; k++) {
             const int l = tid + k * nt;
-            if (l < nint) {
+            if (!arriver && l < nint) {
                 R f;
                 S.ua[l] = tile_fe_edge<R>(S, cfc, ne, l, S.u0, S.z0, tau, g, f);
                 S.fl[l] = f;
@@ -562,7 +592,7 @@ __global__ void __launch_bounds__(NT, 1024 / NT) k_btr_tiled(DTiles<R> t, BtrArg
     for (int k = 0; k < OWN; k++) {
         if (oe[k] >= 0) {
             const R u0 = S.u0[tid + k * nt];
-            a.Fz[oe[k]] = Fz[k];
+            a.Fz[oe[k]] = Fz[k].value(invM);
             a.ub_out[oe[k]] = a.X ? (R)(a.alpha * (double)a.X[oe[k]] + a.beta * (double)u0) : u0;
         }
         if (a.z_out && oc[k] >= 0) a.z_out[oc[k]] = (double)S.z0[tid + k * nt];
