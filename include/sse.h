@@ -262,6 +262,17 @@ int sse_state_create_ex(const sse_mesh *mesh, const sse_params *params,
                         const sse_tuning *tuning, void *cuda_stream, sse_state **out);
 /* Patches of the state's tiled sub-cycle (0: the global-memory sub-cycle). */
 int sse_state_patches(const sse_state *state, int *patches);
+
+/* Test hook for the failure path of the sub-cycle's grid barriers (no
+ * counterpart in the paper).  With SSE_INJECT_BARRIER_STALL set to 1, every
+ * grid-barrier wait of the state's sub-cycle waits for one arrival more than
+ * its grid provides, so that the wait runs out its bounded budget (2 s), the
+ * kernel sets the state's error word and returns: the next sse_state_get or
+ * sse_diagnostics returns SSE_ERR_SYNC_TIMEOUT and the CUDA context stays
+ * usable.  Set it back to 0 and re-set the state (sse_state_set) to continue.
+ * Returns SSE_ERR_INVALID_ARG for another `what` or a value other than 0/1. */
+#define SSE_INJECT_BARRIER_STALL 1
+int sse_state_inject(sse_state *state, int what, int value);
 /* Autotuner: times the Algorithm 3/4 sub-cycle (M = 20) of a zero state of
  * this mesh for each candidate patch size and returns the best one for the
  * objective (SSE_TUNE_*).  Runs GPU work on a private stream; the result is

@@ -85,7 +85,8 @@ EXPORTS = ["sse_mesh_create", "sse_mesh_destroy", "sse_state_create", "sse_state
            "sse_state_set", "sse_state_get", "sse_step", "sse_baroclinic_feuler",
            "sse_barotropic_substep", "sse_diagnostics", "sse_kernels_per_step", "sse_profile",
            "sse_profile_read", "sse_barotropic_substep_noalloc", "sse_state_footprint",
-           "sse_state_footprint_ex", "sse_state_create_ex", "sse_state_patches", "sse_tune",
+           "sse_state_footprint_ex", "sse_state_create_ex", "sse_state_patches", "sse_state_inject",
+           "sse_tune",
            "sse_mesh_dims", "sse_server_create", "sse_server_submit", "sse_server_query",
            "sse_server_wait", "sse_server_stats", "sse_server_release", "sse_server_destroy",
            "sse_strerror"]
@@ -131,6 +132,7 @@ def load(path: str = LIB_PATH):
     lib.sse_state_footprint_ex.argtypes = [ct.c_void_p, ct.POINTER(Params), ct.POINTER(Tuning),
                                            ct.POINTER(ct.c_size_t)]
     lib.sse_state_patches.argtypes = [ct.c_void_p, ct.POINTER(ct.c_int)]
+    lib.sse_state_inject.argtypes = [ct.c_void_p, ct.c_int, ct.c_int]
     lib.sse_tune.argtypes = [ct.c_void_p, ct.POINTER(Params), ct.c_int, ct.POINTER(Tuning)]
     lib.sse_server_submit.argtypes = [ct.c_void_p, ct.c_void_p, ct.POINTER(Params), ct.c_void_p,
                                       ct.c_void_p, ct.c_void_p, ct.c_void_p, ct.c_int,
@@ -323,6 +325,11 @@ class State:
         n = ct.c_int()
         _check(self.lib.sse_state_patches(self.handle, ct.byref(n)), "sse_state_patches")
         return int(n.value)
+
+    def inject_barrier_stall(self, on: bool):
+        """Test hook: every grid-barrier wait of the sub-cycle runs out its
+        bounded budget while on (sse_state_inject)."""
+        _check(self.lib.sse_state_inject(self.handle, 1, 1 if on else 0), "sse_state_inject")
 
     def kernels_per_step(self, order: int) -> int:
         return int(self.lib.sse_kernels_per_step(self.handle, int(order)))

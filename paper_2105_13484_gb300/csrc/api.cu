@@ -309,6 +309,7 @@ struct EngineBase {
     virtual int btr_substep(int order, double dt, int M) = 0;
     virtual int patches() const = 0;       // tiled sub-cycle patches (0: global kernel)
     virtual int patch_threads() const = 0; // threads per patch of the tiled sub-cycle
+    unsigned int inject_stall = 0;         // sse_state_inject(SSE_INJECT_BARRIER_STALL)
     virtual bool has_del4() const = 0;     // biharmonic viscosity on
     virtual int diagnostics(sse_diag *out) = 0;
     long long steps = 0;
@@ -809,7 +810,7 @@ struct Engine : EngineBase {
         a.ub_start = ub_start; a.z_start = z_start; a.G = Ga; a.X = X; a.alpha = al;
         a.beta = be; a.ub_out = ub_out; a.Fz = Fz; a.z_out = z_out;
         a.u0 = bu0; a.ua = bua; a.uh = buh; a.z0 = bz0; a.za = bza; a.zh = bzh;
-        a.tau = tau_dt / M; a.g = p.g; a.M = M; a.order = order;
+        a.tau = tau_dt / M; a.g = p.g; a.M = M; a.order = order; a.stall = inject_stall;
         last_Fz = Fz;
         // the barrier reset (a memset) sits outside the timed pair
         cudaError_t me = cudaMemsetAsync(barwords, 0, 2 * sizeof(unsigned int), s);
@@ -1038,6 +1039,13 @@ extern "C" int sse_state_footprint_ex(const sse_mesh *mesh, const sse_params *pr
 extern "C" int sse_mesh_dims(const sse_mesh *mesh, int32_t dims[4]) {
     if (!mesh || !dims) return SSE_ERR_INVALID_ARG;
     dims[0] = mesh->dm.C; dims[1] = mesh->dm.E; dims[2] = mesh->dm.V; dims[3] = mesh->dm.L;
+    return SSE_OK;
+}
+
+extern "C" int sse_state_inject(sse_state *st, int what, int value) {
+    if (!st || what != SSE_INJECT_BARRIER_STALL || (value != 0 && value != 1))
+        return SSE_ERR_INVALID_ARG;
+    st->eng->inject_stall = (unsigned int)value;
     return SSE_OK;
 }
 

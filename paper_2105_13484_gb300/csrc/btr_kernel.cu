@@ -170,7 +170,7 @@ __device__ __forceinline__ R fe_cell(const DMesh &m, const Coef<R> &c, int i, co
 template <class R, int ORDER, int NE2>
 __global__ void __launch_bounds__(BTR_THREADS) k_btr(DMesh m, BtrArgs<R> a, Barrier bar) {
     const Coef<R> &c = coef<R>(m);
-    const unsigned int nb = gridDim.x;
+    const unsigned int nb = gridDim.x + a.stall;   // arrivals a barrier waits for
     const int T = gridDim.x * blockDim.x;
     const int t0 = blockIdx.x * blockDim.x + threadIdx.x;
     const int nit = ((m.E > m.C ? m.E : m.C) + T - 1) / T;  // <= BTR_NIT (host checks)
@@ -578,7 +578,7 @@ __global__ void __launch_bounds__(NT, 1024 / NT) k_btr_tiled(DTiles<R> t, BtrArg
                 Fs[k] = wAB * f;
             }
         }
-        if (!grid_wait(bar, (unsigned int)(j + 1) * gridDim.x)) return;
+        if (!grid_wait(bar, (unsigned int)(j + 1) * gridDim.x + a.stall)) return;
 #pragma unroll
         for (int k = 0; k < OWN; k++) {
             if (he[k] >= 0) S.u0[noe + tid + k * nt] = __ldcg(xu + he[k]);

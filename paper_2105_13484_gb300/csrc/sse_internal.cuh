@@ -143,6 +143,7 @@ template <class R> struct BtrArgs {
     R *z0, *za, *zh;       // work [Cp]
     double tau, g;
     int M, order;
+    unsigned int stall;    // test hook: arrivals every grid barrier waits for beyond the grid (0)
 };
 template <class R>
 cudaError_t launch_btr(const DMesh &m, const BtrArgs<R> &a, const Barrier &bar, int nblocks,
