@@ -101,6 +101,28 @@ template <> struct VecT<double> { using V2 = double2; using V4 = double4x; };
 template <class R> using V2 = typename VecT<R>::V2;
 template <class R> using V4 = typename VecT<R>::V4;
 
+// Sum of tendency-precision terms, read out in FP64.  FP32 terms go into an
+// unevaluated pair of floats with Knuth's TwoSum, which carries the rounding
+// error of every addition exactly in the low part (about 48 significant bits
+// in all), so no FP64 instruction runs per term: GB300 runs FP64 and the
+// f32->f64 conversion at about 1/67 of the FP32 rate.  FP64 terms are summed
+// in a double.
+template <class R> struct PairSum;
+template <> struct PairSum<float> {
+    float hi = 0.f, lo = 0.f;
+    __device__ __forceinline__ void add(float x) {
+        const float s = hi + x, bp = s - hi;
+        lo += (hi - (s - bp)) + (x - bp);
+        hi = s;
+    }
+    __device__ __forceinline__ double value() const { return (double)hi + (double)lo; }
+};
+template <> struct PairSum<double> {
+    double s = 0.0;
+    __device__ __forceinline__ void add(double x) { s += x; }
+    __device__ __forceinline__ double value() const { return s; }
+};
+
 template <class R> struct DiagBufs {
     R *delta, *w;                        // [L][Cp] div u; div(h_e u), then w at the top of k
     V4<R> *cq;                           // [L][Cp] (K, p', rho', z_mid), gathered as one

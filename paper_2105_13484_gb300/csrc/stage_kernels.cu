@@ -421,8 +421,9 @@ __global__ void __launch_bounds__(128, MINB) k_bcl_edge(DMesh m, DParams p, cons
 //   F^h = cF * sum_k v_k h_e,k + cE * (extra terms), D = F^zeta - F^h,
 //   u^A = cA * D / sum_k h_e,k,  flux_k = h_e,k (v_k + u^A)
 // The column sums that decide D, u^A and the column-integrated flux F_col are
-// accumulated in FP64; sum_k h_e,k = ((zeta+H)_c1 + (zeta+H)_c2) / 2 because
-// zeta = sum h - H.  The per-layer flux is stored in the tendency precision.
+// read out in FP64 (PairSum: a float pair in the mixed form);
+// sum_k h_e,k = ((zeta+H)_c1 + (zeta+H)_c2) / 2 because zeta = sum h - H.  The
+// per-layer flux is stored in the tendency precision.
 // ---------------------------------------------------------------------------
 template <class R, bool PB>
 __global__ void __launch_bounds__(128) k_transport(DMesh m, TransportArgs<R> a) {
@@ -437,15 +438,17 @@ __global__ void __launch_bounds__(128) k_transport(DMesh m, TransportArgs<R> a) 
     // with full columns the edge's total thickness is (zeta + H)_e; with partial
     // bottom cells it is the sum over the layers the edge has
     const int K = PB ? m.ke[e] : L;
-    double hs = PB ? 0.0 : 0.5 * ((a.zeta[cc.x] + m.H[cc.x]) + (a.zeta[cc.y] + m.H[cc.y]));
-    double S = 0.0;
+    PairSum<R> Sacc, hacc;
     for (int k = 0; k < K; k++) {
         const R he = R(0.5) * (ld(a.hR + k * Cp + cc.x) + ld(a.hR + k * Cp + cc.y));
         R v = wA * (ubA + a.utA[k * Ep + e]);
         if (twoB) v += wB * (ubB + a.utB[k * Ep + e]);
-        S += (double)(v * he);
-        if (PB) hs += (double)he;
+        Sacc.add(v * he);
+        if (PB) hacc.add(he);
     }
+    const double S = Sacc.value();
+    const double hs =
+        PB ? hacc.value() : 0.5 * ((a.zeta[cc.x] + m.H[cc.x]) + (a.zeta[cc.y] + m.H[cc.y]));
     double Fh = a.cF * S;
     if (a.ex1) Fh += a.cE * a.ex1[e];
     if (a.ex2) Fh += a.cE * a.ex2[e];
