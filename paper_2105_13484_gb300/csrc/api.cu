@@ -299,6 +299,23 @@ extern "C" void sse_mesh_destroy(sse_mesh *m) { delete m; }
 const sse::DMesh *sse_internal_dmesh(const sse_mesh *m) { return &m->dm; }
 
 // ---------------------------------------------------------------------------
+// Device address of page-locked host memory (cudaHostAlloc, cudaHostRegister)
+// mapped for the current device, or null for any other pointer.  The state's
+// set/get kernels then read or write such host buffers directly, which saves
+// the staging copy through device memory.
+static void *host_alias(const void *p) {
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess || at.type != cudaMemoryTypeHost ||
+        at.device != dev || !at.devicePointer)
+        return nullptr;
+    return at.devicePointer;
+}
+
 // state: a precision-specific engine behind a small virtual interface
 // ---------------------------------------------------------------------------
 struct EngineBase {
@@ -670,22 +687,25 @@ struct Engine : EngineBase {
     // ---- host <-> device
     int set(int field, const double *host) override {
         const int L = m.L;
+        // page-locked host buffers are read by the conversion kernels directly
+        const double *direct = (const double *)host_alias(host);
+        const double *in = direct ? direct : stage;
         switch (field) {
         case SSE_FIELD_U:
         case SSE_FIELD_UTILDE:
-            CK(cudaMemcpyAsync(stage, host, sizeof(double) * m.E * L, cudaMemcpyHostToDevice, s));
-            launch_to_device<R>(stage, ut_n, m.E, L, m.Ep, s);
+            if (!direct) CK(cudaMemcpyAsync(stage, host, sizeof(double) * m.E * L, cudaMemcpyHostToDevice, s));
+            launch_to_device<R>(in, ut_n, m.E, L, m.Ep, s);
             if (m.partial) launch_mask_layers<R>(ut_n, m.E, L, m.Ep, m.ke, s);
             if (field == SSE_FIELD_U) CK(cudaMemsetAsync(ubar_n, 0, sizeof(R) * m.Ep, s));
             break;
         case SSE_FIELD_UBAR:
         case SSE_FIELD_G:
-            CK(cudaMemcpyAsync(stage, host, sizeof(double) * m.E, cudaMemcpyHostToDevice, s));
-            launch_to_device<R>(stage, field == SSE_FIELD_UBAR ? ubar_n : G0, m.E, 1, m.Ep, s);
+            if (!direct) CK(cudaMemcpyAsync(stage, host, sizeof(double) * m.E, cudaMemcpyHostToDevice, s));
+            launch_to_device<R>(in, field == SSE_FIELD_UBAR ? ubar_n : G0, m.E, 1, m.Ep, s);
             break;
         case SSE_FIELD_H:
-            CK(cudaMemcpyAsync(stage, host, sizeof(double) * m.C * L, cudaMemcpyHostToDevice, s));
-            launch_to_device<double>(stage, h_n, m.C, L, m.Cp, s);
+            if (!direct) CK(cudaMemcpyAsync(stage, host, sizeof(double) * m.C * L, cudaMemcpyHostToDevice, s));
+            launch_to_device<double>(in, h_n, m.C, L, m.Cp, s);
             if (m.partial) launch_mask_layers<double>(h_n, m.C, L, m.Cp, m.kc, s);
             if (mixed) launch_h_to_float(h_n, (float *)hR_n, L * m.Cp, s);
             launch_ssh(m, h_n, zeta_n, s);
@@ -694,8 +714,8 @@ struct Engine : EngineBase {
         case SSE_FIELD_TRACER1: {
             const int t = field - SSE_FIELD_TRACER0;
             if (t >= p.nT) return SSE_ERR_INVALID_ARG;
-            CK(cudaMemcpyAsync(stage, host, sizeof(double) * m.C * L, cudaMemcpyHostToDevice, s));
-            launch_to_device<R>(stage, tr_n + (size_t)t * L * m.Cp, m.C, L, m.Cp, s);
+            if (!direct) CK(cudaMemcpyAsync(stage, host, sizeof(double) * m.C * L, cudaMemcpyHostToDevice, s));
+            launch_to_device<R>(in, tr_n + (size_t)t * L * m.Cp, m.C, L, m.Cp, s);
             if (m.partial) launch_mask_layers<R>(tr_n + (size_t)t * L * m.Cp, m.C, L, m.Cp, m.kc, s);
             break;
         }
@@ -719,46 +739,49 @@ struct Engine : EngineBase {
     int get(int field, double *host) override {
         const int L = m.L;
         size_t n = 0;
+        // the conversion kernels write page-locked host buffers directly
+        double *direct = (double *)host_alias(host);
+        double *out = direct ? direct : stage;
         switch (field) {
         case SSE_FIELD_U:
-            launch_add_bar<R>(ubar_n, ut_n, stage, m.E, L, m.Ep, m.partial ? m.ke : nullptr, s);
+            launch_add_bar<R>(ubar_n, ut_n, out, m.E, L, m.Ep, m.partial ? m.ke : nullptr, s);
             n = (size_t)m.E * L;
             break;
         case SSE_FIELD_UTILDE:
-            launch_from_device<R>(ut_n, stage, m.E, L, m.Ep, s);
+            launch_from_device<R>(ut_n, out, m.E, L, m.Ep, s);
             n = (size_t)m.E * L;
             break;
         case SSE_FIELD_UBAR:
         case SSE_FIELD_G:
-            launch_from_device<R>(field == SSE_FIELD_UBAR ? ubar_n : G0, stage, m.E, 1, m.Ep, s);
+            launch_from_device<R>(field == SSE_FIELD_UBAR ? ubar_n : G0, out, m.E, 1, m.Ep, s);
             n = m.E;
             break;
         case SSE_FIELD_H:
-            launch_from_device<double>(h_n, stage, m.C, L, m.Cp, s);
+            launch_from_device<double>(h_n, out, m.C, L, m.Cp, s);
             n = (size_t)m.C * L;
             break;
         case SSE_FIELD_TRACER0:
         case SSE_FIELD_TRACER1: {
             const int t = field - SSE_FIELD_TRACER0;
             if (t >= p.nT) return SSE_ERR_INVALID_ARG;
-            launch_from_device<R>(tr_n + (size_t)t * L * m.Cp, stage, m.C, L, m.Cp, s);
+            launch_from_device<R>(tr_n + (size_t)t * L * m.Cp, out, m.C, L, m.Cp, s);
             n = (size_t)m.C * L;
             break;
         }
         case SSE_FIELD_ZETA:
-            CK(cudaMemcpyAsync(stage, zeta_n, sizeof(double) * m.C, cudaMemcpyDeviceToDevice, s));
+            CK(cudaMemcpyAsync(out, zeta_n, sizeof(double) * m.C, cudaMemcpyDefault, s));
             n = m.C;
             break;
         case SSE_FIELD_ZETA_SUB:
-            CK(cudaMemcpyAsync(stage, zeta_sub, sizeof(double) * m.C, cudaMemcpyDeviceToDevice, s));
+            CK(cudaMemcpyAsync(out, zeta_sub, sizeof(double) * m.C, cudaMemcpyDefault, s));
             n = m.C;
             break;
         case SSE_FIELD_FZETA:
-            CK(cudaMemcpyAsync(stage, last_Fz, sizeof(double) * m.E, cudaMemcpyDeviceToDevice, s));
+            CK(cudaMemcpyAsync(out, last_Fz, sizeof(double) * m.E, cudaMemcpyDefault, s));
             n = m.E;
             break;
         case SSE_FIELD_WIND:
-            CK(cudaMemcpyAsync(stage, wind, sizeof(double) * m.E, cudaMemcpyDeviceToDevice, s));
+            CK(cudaMemcpyAsync(out, wind, sizeof(double) * m.E, cudaMemcpyDefault, s));
             n = m.E;
             break;
         default:
@@ -766,7 +789,7 @@ struct Engine : EngineBase {
         }
         int rc = check_launch();
         if (rc) return rc;
-        CK(cudaMemcpyAsync(host, stage, sizeof(double) * n, cudaMemcpyDeviceToHost, s));
+        if (!direct) CK(cudaMemcpyAsync(host, stage, sizeof(double) * n, cudaMemcpyDeviceToHost, s));
         CK(cudaStreamSynchronize(s));
         return barrier_status();
     }
