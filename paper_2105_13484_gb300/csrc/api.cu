@@ -11,6 +11,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <numeric>
 #include <map>
 #include <memory>
 #include <mutex>
@@ -178,9 +179,27 @@ extern "C" int sse_mesh_create(const sse_mesh_desc *d, sse_mesh **out) {
     std::vector<double> wl((size_t)mE2 * Ep, 0.0), cfc((size_t)mE2 * Ep, 0.0);
     std::vector<double> curlc(3 * Vp, 0.0), kw(3 * Vp, 0.0), invdc(Ep, 1.0), invdv(Ep, 1.0);
     std::vector<double> fV(Vp, 0.0), area(Cp, 0.0), ld2(Ep, 0.0);
+    // Vertices are numbered internally in the order of their lowest cell, so that
+    // a warp of consecutive vertices gathers from nearby cells and edges (the
+    // caller's numbering may be arbitrary; vertex data never crosses the API).
+    std::vector<int> vold(V), vnew(V);
+    {
+        std::vector<long long> key(V);
+        for (int v = 0; v < V; v++) {
+            int lo = C;
+            for (int j = 0; j < 3; j++) {
+                const int c = d->cellsOnVertex[3 * v + j];
+                if (c >= 0 && c < lo) lo = c;
+            }
+            key[v] = (long long)lo * V + v;   // ties keep the caller's order
+        }
+        std::iota(vold.begin(), vold.end(), 0);
+        std::sort(vold.begin(), vold.end(), [&](int a, int b) { return key[a] < key[b]; });
+        for (int nv = 0; nv < V; nv++) vnew[vold[nv]] = nv;
+    }
     for (int e = 0; e < E; e++) {
         coe[e] = make_int2(d->cellsOnEdge[2 * e], d->cellsOnEdge[2 * e + 1]);
-        voe[e] = make_int2(d->verticesOnEdge[2 * e], d->verticesOnEdge[2 * e + 1]);
+        voe[e] = make_int2(vnew[d->verticesOnEdge[2 * e]], vnew[d->verticesOnEdge[2 * e + 1]]);
         invdc[e] = 1.0 / d->dcEdge[e];
         invdv[e] = 1.0 / d->dvEdge[e];
         ld2[e] = 0.5 * d->dvEdge[e] * d->dcEdge[e];
@@ -206,21 +225,22 @@ extern "C" int sse_mesh_create(const sse_mesh_desc *d, sse_mesh **out) {
             kec[(size_t)j * Cp + i] = 0.25 * d->dvEdge[e] * d->dcEdge[e] / d->areaCell[i];
         }
     }
-    for (int v = 0; v < V; v++) {
-        fV[v] = d->fVertex[v];
+    for (int nv = 0; nv < V; nv++) {
+        const int v = vold[nv];   // the caller's index
+        fV[nv] = d->fVertex[v];
         double ksum = 0.0;
         for (int j = 0; j < 3; j++)
             if (d->cellsOnVertex[3 * v + j] >= 0) ksum += d->kiteAreasOnVertex[3 * v + j];
         for (int j = 0; j < 3; j++) {
             int e = d->edgesOnVertex[3 * v + j], c = d->cellsOnVertex[3 * v + j];
             if (e >= 0) {
-                eov[(size_t)j * Vp + v] = e;
+                eov[(size_t)j * Vp + nv] = e;
                 double sign = (d->verticesOnEdge[2 * e + 1] == v) ? 1.0 : -1.0;
-                curlc[(size_t)j * Vp + v] = sign * d->dcEdge[e] / d->areaTriangle[v];
+                curlc[(size_t)j * Vp + nv] = sign * d->dcEdge[e] / d->areaTriangle[v];
             }
             if (c >= 0) {
-                cov[(size_t)j * Vp + v] = c;
-                kw[(size_t)j * Vp + v] = d->kiteAreasOnVertex[3 * v + j] / ksum;
+                cov[(size_t)j * Vp + nv] = c;
+                kw[(size_t)j * Vp + nv] = d->kiteAreasOnVertex[3 * v + j] / ksum;
             }
         }
     }
