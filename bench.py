@@ -304,31 +304,44 @@ def measure_form(torch, binding, dm, m, L, p, state0, run, precision, steps, war
 
 def measure_e2e(torch, binding, dm, p, state0, run, precision, steps, stream):
     """Through the public C ABI with pinned host buffers: per step, H2D of
-    (u, h, T), one large step, D2H of (u, h, T)."""
+    (u, h, T), one large step, D2H of (u, h, T).  Each field crosses in the
+    precision the state holds it in: FP32 u and T for the mixed form
+    (sse_state_set_f32/get_f32), FP64 h always, FP64 everything for the FP64
+    form."""
     u, h, tr = state0
     st = binding.State(dm, p, precision, stream=stream.cuda_stream)
     fields = [("u", u), ("h", h)] + [(f"tracer{k}", tr[k]) for k in range(tr.shape[0])]
-    hin = [(n, torch.from_numpy(np.ascontiguousarray(x)).pin_memory()) for n, x in fields]
+    f32 = {n: precision == "mixed" and n != "h" for n, _ in fields}
+    hin = [(n, torch.from_numpy(np.ascontiguousarray(
+        x, dtype=np.float32 if f32[n] else np.float64)).pin_memory()) for n, x in fields]
     hout = [(n, torch.empty_like(x).pin_memory()) for n, x in hin]
     order, dt, M = run["order"], run["dt"], run["M"]
+
+    def put(n, x):
+        (st.set_ptr_f32 if f32[n] else st.set_ptr)(n, x.data_ptr())
+
+    def take(n, x):
+        (st.get_ptr_f32 if f32[n] else st.get_ptr)(n, x.data_ptr())
+
     for n, x in hin:
-        st.set_ptr(n, x.data_ptr())
+        put(n, x)
     st.step(order, dt, M, 1)
     torch.cuda.synchronize()
     a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     a.record(stream)
     for _ in range(steps):
         for n, x in hin:
-            st.set_ptr(n, x.data_ptr())
+            put(n, x)
         st.step(order, dt, M, 1)
         for n, x in hout:
-            st.get_ptr(n, x.data_ptr())
+            take(n, x)
     b.record(stream)
     torch.cuda.synchronize()
     ms = a.elapsed_time(b)
-    nbytes = sum(x.numel() for _, x in hin) * 8
+    nbytes = sum(x.numel() * x.element_size() for _, x in hin)
+    dtypes = {n: ("f32" if f32[n] else "f64") for n, _ in fields}
     st.close()
-    return ms, nbytes
+    return ms, nbytes, dtypes
 
 
 def roofline_of(prof, m, L, nT, mixed, order, steps, ms_per_step):
@@ -405,12 +418,12 @@ def measure_workload(torch, binding, name, forms_todo, headline, steps, warmup, 
     out["e2e"] = None
     if e2e:
         e2e_steps = min(steps, 20)
-        e2e_ms, nbytes = measure_e2e(torch, binding, dm, p, state0, run, headline, e2e_steps,
-                                     stream)
+        e2e_ms, nbytes, dtypes = measure_e2e(torch, binding, dm, p, state0, run, headline,
+                                             e2e_steps, stream)
         e2e_val = replica_throughput(m.nCells * L * e2e_steps, world,
                                      max_over_ranks(torch, dist, e2e_ms, "cuda"))
         out["e2e"] = {"value": e2e_val, "unit": METRIC, "h2d_bytes_per_step": nbytes,
-                      "d2h_bytes_per_step": nbytes}
+                      "d2h_bytes_per_step": nbytes, "host_dtypes": dtypes}
     dm.close()
     return out
 

@@ -168,6 +168,16 @@ void sse_state_destroy(sse_state *state);
 int sse_state_set(sse_state *state, int field, const double *host);
 /* Device -> host copy of one field as FP64; synchronises the stream. */
 int sse_state_get(sse_state *state, int field, double *host_out);
+/* The same transfers with FP32 host arrays, for the fields a state holds in
+ * its tendency precision: U, UTILDE, UBAR, G, TRACER0/1 (FP32 in the mixed
+ * form, so nothing is rounded there; the FP64 form rounds on the way out and
+ * widens on the way in).  H, ZETA, ZETA_SUB, FZETA and WIND are FP64 state in
+ * both forms: SSE_ERR_INVALID_ARG.  Both calls return once the host array has
+ * been read or written.  With page-locked host memory (cudaHostAlloc,
+ * cudaHostRegister) the conversion kernels access the host array directly,
+ * for sse_state_set/get as well; the array must then hold the whole field. */
+int sse_state_set_f32(sse_state *state, int field, const float *host);
+int sse_state_get_f32(sse_state *state, int field, float *host_out);
 
 /* Advance n_steps large steps of SSPRK{order}-SE (order 2: Sec. 3.2 with
  * Algorithm 3; order 3: Sec. 3.3 with Algorithm 4), time step dt (s) and

@@ -86,6 +86,7 @@ EXPORTS = ["sse_mesh_create", "sse_mesh_destroy", "sse_state_create", "sse_state
            "sse_barotropic_substep", "sse_diagnostics", "sse_kernels_per_step", "sse_profile",
            "sse_profile_read", "sse_barotropic_substep_noalloc", "sse_state_footprint",
            "sse_state_footprint_ex", "sse_state_create_ex", "sse_state_patches", "sse_state_inject",
+           "sse_state_set_f32", "sse_state_get_f32",
            "sse_tune",
            "sse_mesh_dims", "sse_server_create", "sse_server_submit", "sse_server_query",
            "sse_server_wait", "sse_server_stats", "sse_server_release", "sse_server_destroy",
@@ -133,6 +134,8 @@ def load(path: str = LIB_PATH):
                                            ct.POINTER(ct.c_size_t)]
     lib.sse_state_patches.argtypes = [ct.c_void_p, ct.POINTER(ct.c_int)]
     lib.sse_state_inject.argtypes = [ct.c_void_p, ct.c_int, ct.c_int]
+    lib.sse_state_set_f32.argtypes = [ct.c_void_p, ct.c_int, ct.c_void_p]
+    lib.sse_state_get_f32.argtypes = [ct.c_void_p, ct.c_int, ct.c_void_p]
     lib.sse_tune.argtypes = [ct.c_void_p, ct.POINTER(Params), ct.c_int, ct.POINTER(Tuning)]
     lib.sse_server_submit.argtypes = [ct.c_void_p, ct.c_void_p, ct.POINTER(Params), ct.c_void_p,
                                       ct.c_void_p, ct.c_void_p, ct.c_void_p, ct.c_int,
@@ -278,6 +281,29 @@ class State:
     def get_ptr(self, field: str, ptr: int):
         _check(self.lib.sse_state_get(self.handle, FIELD[field], ct.c_void_p(ptr)),
                f"get {field}")
+
+    def set_f32(self, field: str, x):
+        """FP32 host transfer (u, utilde, ubar, G, tracers only)."""
+        a = np.ascontiguousarray(x, dtype=np.float32)
+        if a.size != int(np.prod(self._shape(field))):
+            raise ValueError(f"{field}: expected shape {self._shape(field)}, got {a.shape}")
+        _check(self.lib.sse_state_set_f32(self.handle, FIELD[field], a.ctypes.data),
+               f"set_f32 {field}")
+
+    def get_f32(self, field: str, out=None) -> np.ndarray:
+        if out is None:
+            out = np.empty(self._shape(field), dtype=np.float32)
+        _check(self.lib.sse_state_get_f32(self.handle, FIELD[field], out.ctypes.data),
+               f"get_f32 {field}")
+        return out
+
+    def set_ptr_f32(self, field: str, ptr: int):
+        _check(self.lib.sse_state_set_f32(self.handle, FIELD[field], ct.c_void_p(ptr)),
+               f"set_f32 {field}")
+
+    def get_ptr_f32(self, field: str, ptr: int):
+        _check(self.lib.sse_state_get_f32(self.handle, FIELD[field], ct.c_void_p(ptr)),
+               f"get_f32 {field}")
 
     def load_state(self, u, h, tr):
         self.set("u", u)

@@ -12,6 +12,7 @@
 
 #include <algorithm>
 #include <numeric>
+#include <type_traits>
 #include <map>
 #include <memory>
 #include <mutex>
@@ -341,6 +342,8 @@ static void *host_alias(const void *p) {
 struct EngineBase {
     virtual int set(int field, const double *host) = 0;
     virtual int get(int field, double *host) = 0;
+    virtual int set_f32(int field, const float *host) = 0;
+    virtual int get_f32(int field, float *host) = 0;
     virtual int step(int order, double dt, int M) = 0;
     virtual int bcl_feuler(double dt) = 0;
     virtual int btr_substep(int order, double dt, int M) = 0;
@@ -705,46 +708,64 @@ struct Engine : EngineBase {
     }
 
     // ---- host <-> device
-    int set(int field, const double *host) override {
+    int set(int field, const double *host) override { return set_t<double>(field, host); }
+    int get(int field, double *host) override { return get_t<double>(field, host); }
+    int set_f32(int field, const float *host) override { return set_t<float>(field, host); }
+    int get_f32(int field, float *host) override { return get_t<float>(field, host); }
+
+    // Host transfers in precision H: FP64 for every field; FP32 for the fields
+    // held in the tendency precision (u, utilde, ubar, G, tracers).
+    template <class H> int set_t(int field, const H *host) {
+        constexpr bool f64 = std::is_same<H, double>::value;
         const int L = m.L;
         // page-locked host buffers are read by the conversion kernels directly
-        const double *direct = (const double *)host_alias(host);
-        const double *in = direct ? direct : stage;
+        const H *direct = (const H *)host_alias(host);
+        const H *in = direct ? direct : (const H *)stage;
         switch (field) {
         case SSE_FIELD_U:
         case SSE_FIELD_UTILDE:
-            if (!direct) CK(cudaMemcpyAsync(stage, host, sizeof(double) * m.E * L, cudaMemcpyHostToDevice, s));
+            if (!direct) CK(cudaMemcpyAsync(stage, host, sizeof(H) * m.E * L, cudaMemcpyHostToDevice, s));
             launch_to_device<R>(in, ut_n, m.E, L, m.Ep, s);
             if (m.partial) launch_mask_layers<R>(ut_n, m.E, L, m.Ep, m.ke, s);
             if (field == SSE_FIELD_U) CK(cudaMemsetAsync(ubar_n, 0, sizeof(R) * m.Ep, s));
             break;
         case SSE_FIELD_UBAR:
         case SSE_FIELD_G:
-            if (!direct) CK(cudaMemcpyAsync(stage, host, sizeof(double) * m.E, cudaMemcpyHostToDevice, s));
+            if (!direct) CK(cudaMemcpyAsync(stage, host, sizeof(H) * m.E, cudaMemcpyHostToDevice, s));
             launch_to_device<R>(in, field == SSE_FIELD_UBAR ? ubar_n : G0, m.E, 1, m.Ep, s);
             break;
         case SSE_FIELD_H:
-            if (!direct) CK(cudaMemcpyAsync(stage, host, sizeof(double) * m.C * L, cudaMemcpyHostToDevice, s));
-            launch_to_device<double>(in, h_n, m.C, L, m.Cp, s);
-            if (m.partial) launch_mask_layers<double>(h_n, m.C, L, m.Cp, m.kc, s);
-            if (mixed) launch_h_to_float(h_n, (float *)hR_n, L * m.Cp, s);
-            launch_ssh(m, h_n, zeta_n, s);
-            break;
+            if constexpr (f64) {
+                if (!direct)
+                    CK(cudaMemcpyAsync(stage, host, sizeof(double) * m.C * L,
+                                       cudaMemcpyHostToDevice, s));
+                launch_to_device<double>(in, h_n, m.C, L, m.Cp, s);
+                if (m.partial) launch_mask_layers<double>(h_n, m.C, L, m.Cp, m.kc, s);
+                if (mixed) launch_h_to_float(h_n, (float *)hR_n, L * m.Cp, s);
+                launch_ssh(m, h_n, zeta_n, s);
+                break;
+            } else {
+                return SSE_ERR_INVALID_ARG;   // h is FP64 state in both forms
+            }
         case SSE_FIELD_TRACER0:
         case SSE_FIELD_TRACER1: {
             const int t = field - SSE_FIELD_TRACER0;
             if (t >= p.nT) return SSE_ERR_INVALID_ARG;
-            if (!direct) CK(cudaMemcpyAsync(stage, host, sizeof(double) * m.C * L, cudaMemcpyHostToDevice, s));
+            if (!direct) CK(cudaMemcpyAsync(stage, host, sizeof(H) * m.C * L, cudaMemcpyHostToDevice, s));
             launch_to_device<R>(in, tr_n + (size_t)t * L * m.Cp, m.C, L, m.Cp, s);
             if (m.partial) launch_mask_layers<R>(tr_n + (size_t)t * L * m.Cp, m.C, L, m.Cp, m.kc, s);
             break;
         }
         case SSE_FIELD_WIND:
-            CK(cudaMemcpyAsync(wind, host, sizeof(double) * m.E, cudaMemcpyHostToDevice, s));
-            launch_scale(wind, 1.0 / p.rho0, wind_d, wind_f, m.E, s);
-            p.wind = wind_d;
-            p.wind_f = wind_f;
-            break;
+            if constexpr (f64) {
+                CK(cudaMemcpyAsync(wind, host, sizeof(double) * m.E, cudaMemcpyHostToDevice, s));
+                launch_scale(wind, 1.0 / p.rho0, wind_d, wind_f, m.E, s);
+                p.wind = wind_d;
+                p.wind_f = wind_f;
+                break;
+            } else {
+                return SSE_ERR_INVALID_ARG;
+            }
         default:
             return SSE_ERR_INVALID_ARG;
         }
@@ -756,12 +777,17 @@ struct Engine : EngineBase {
         return SSE_OK;
     }
 
-    int get(int field, double *host) override {
+    template <class H> int get_t(int field, H *host) {
+        constexpr bool f64 = std::is_same<H, double>::value;
         const int L = m.L;
         size_t n = 0;
         // the conversion kernels write page-locked host buffers directly
-        double *direct = (double *)host_alias(host);
-        double *out = direct ? direct : stage;
+        H *direct = (H *)host_alias(host);
+        H *out = direct ? direct : (H *)stage;
+        if (!f64 && (field == SSE_FIELD_H || field == SSE_FIELD_ZETA ||
+                     field == SSE_FIELD_ZETA_SUB || field == SSE_FIELD_FZETA ||
+                     field == SSE_FIELD_WIND))
+            return SSE_ERR_INVALID_ARG;   // FP64 state in both forms
         switch (field) {
         case SSE_FIELD_U:
             launch_add_bar<R>(ubar_n, ut_n, out, m.E, L, m.Ep, m.partial ? m.ke : nullptr, s);
@@ -777,7 +803,7 @@ struct Engine : EngineBase {
             n = m.E;
             break;
         case SSE_FIELD_H:
-            launch_from_device<double>(h_n, out, m.C, L, m.Cp, s);
+            if constexpr (f64) launch_from_device<double>(h_n, out, m.C, L, m.Cp, s);
             n = (size_t)m.C * L;
             break;
         case SSE_FIELD_TRACER0:
@@ -789,19 +815,19 @@ struct Engine : EngineBase {
             break;
         }
         case SSE_FIELD_ZETA:
-            CK(cudaMemcpyAsync(out, zeta_n, sizeof(double) * m.C, cudaMemcpyDefault, s));
+            if constexpr (f64) CK(cudaMemcpyAsync(out, zeta_n, sizeof(double) * m.C, cudaMemcpyDefault, s));
             n = m.C;
             break;
         case SSE_FIELD_ZETA_SUB:
-            CK(cudaMemcpyAsync(out, zeta_sub, sizeof(double) * m.C, cudaMemcpyDefault, s));
+            if constexpr (f64) CK(cudaMemcpyAsync(out, zeta_sub, sizeof(double) * m.C, cudaMemcpyDefault, s));
             n = m.C;
             break;
         case SSE_FIELD_FZETA:
-            CK(cudaMemcpyAsync(out, last_Fz, sizeof(double) * m.E, cudaMemcpyDefault, s));
+            if constexpr (f64) CK(cudaMemcpyAsync(out, last_Fz, sizeof(double) * m.E, cudaMemcpyDefault, s));
             n = m.E;
             break;
         case SSE_FIELD_WIND:
-            CK(cudaMemcpyAsync(out, wind, sizeof(double) * m.E, cudaMemcpyDefault, s));
+            if constexpr (f64) CK(cudaMemcpyAsync(out, wind, sizeof(double) * m.E, cudaMemcpyDefault, s));
             n = m.E;
             break;
         default:
@@ -809,7 +835,7 @@ struct Engine : EngineBase {
         }
         int rc = check_launch();
         if (rc) return rc;
-        if (!direct) CK(cudaMemcpyAsync(host, stage, sizeof(double) * n, cudaMemcpyDeviceToHost, s));
+        if (!direct) CK(cudaMemcpyAsync(host, stage, sizeof(H) * n, cudaMemcpyDeviceToHost, s));
         CK(cudaStreamSynchronize(s));
         return barrier_status();
     }
@@ -1199,6 +1225,16 @@ extern "C" int sse_state_set(sse_state *st, int field, const double *host) {
 extern "C" int sse_state_get(sse_state *st, int field, double *host) {
     if (!st || !host) return SSE_ERR_INVALID_ARG;
     return st->eng->get(field, host);
+}
+
+extern "C" int sse_state_set_f32(sse_state *st, int field, const float *host) {
+    if (!st || !host) return SSE_ERR_INVALID_ARG;
+    return st->eng->set_f32(field, host);
+}
+
+extern "C" int sse_state_get_f32(sse_state *st, int field, float *host) {
+    if (!st || !host) return SSE_ERR_INVALID_ARG;
+    return st->eng->get_f32(field, host);
 }
 
 extern "C" int sse_step(sse_state *st, int order, double dt, int n_substeps, int n_steps) {

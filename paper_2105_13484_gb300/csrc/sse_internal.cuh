@@ -235,13 +235,14 @@ template <class R> struct ThickArgs {
 template <class R>
 void launch_thickness(const DMesh &m, const DParams &p, const ThickArgs<R> &a, cudaStream_t s);
 
-// layout conversion: host-order FP64 [n][L] <-> device layer-major R [L][np]
-template <class R>
-void launch_to_device(const double *src, R *dst, int n, int L, int np, cudaStream_t s);
-template <class R>
-void launch_from_device(const R *src, double *dst, int n, int L, int np, cudaStream_t s);
-template <class R>
-void launch_add_bar(const R *ubar, const R *ut, double *dst, int E, int L, int Ep,
+// layout conversion: host-order [n][L] in precision H (FP64 or FP32) <->
+// device layer-major R [L][np]
+template <class R, class H>
+void launch_to_device(const H *src, R *dst, int n, int L, int np, cudaStream_t s);
+template <class R, class H>
+void launch_from_device(const R *src, H *dst, int n, int L, int np, cudaStream_t s);
+template <class R, class H>
+void launch_add_bar(const R *ubar, const R *ut, H *dst, int E, int L, int Ep,
                     const int *kmax, cudaStream_t s);
 template <class R>
 void launch_mask_layers(R *x, int n, int L, int np, const int *kmax, cudaStream_t s);

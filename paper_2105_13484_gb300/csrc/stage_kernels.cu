@@ -578,30 +578,33 @@ __global__ void __launch_bounds__(128, 6) k_thickness(DMesh m, DParams p, ThickA
 // ---------------------------------------------------------------------------
 // small helpers: layout conversion, SSH
 // ---------------------------------------------------------------------------
-template <class R>
-__global__ void k_to_device(const double *__restrict__ src, R *__restrict__ dst, int n, int L,
+// host order [n][L] in precision H <-> device layer-major [L][np] in precision R
+template <class H, class R>
+__global__ void k_to_device(const H *__restrict__ src, R *__restrict__ dst, int n, int L,
                             int np) {
     const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= (long long)n * L) return;
     const int i = (int)(t / L), k = (int)(t % L);
     dst[(long long)k * np + i] = (R)src[t];
 }
-template <class R>
-__global__ void k_from_device(const R *__restrict__ src, double *__restrict__ dst, int n, int L,
+template <class R, class H>
+__global__ void k_from_device(const R *__restrict__ src, H *__restrict__ dst, int n, int L,
                               int np) {
     const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= (long long)n * L) return;
     const int i = (int)(t / L), k = (int)(t % L);
-    dst[t] = (double)src[(long long)k * np + i];
+    dst[t] = (H)src[(long long)k * np + i];
 }
-template <class R>
+// u = ubar + utilde, summed in FP64 and rounded once to H
+template <class R, class H>
 __global__ void k_add_bar(const R *__restrict__ ubar, const R *__restrict__ ut,
-                          double *__restrict__ dst, int E, int L, int Ep,
+                          H *__restrict__ dst, int E, int L, int Ep,
                           const int *__restrict__ kmax) {
     const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= (long long)E * L) return;
     const int e = (int)(t / L), k = (int)(t % L);
-    dst[t] = (kmax && k >= kmax[e]) ? 0.0 : (double)ubar[e] + (double)ut[(long long)k * Ep + e];
+    dst[t] = (kmax && k >= kmax[e]) ? H(0)
+                                    : (H)((double)ubar[e] + (double)ut[(long long)k * Ep + e]);
 }
 // zero the layers a column (or edge) does not have: x[k * np + i], k >= kmax[i]
 template <class R>
@@ -783,18 +786,18 @@ void launch_thickness(const DMesh &m, const DParams &p, const ThickArgs<R> &a, c
         else k_thickness<R, MAXE, false><<<nb, 128, 0, s>>>(m, p, a);
     }
 }
-template <class R>
-void launch_to_device(const double *src, R *dst, int n, int L, int np, cudaStream_t s) {
-    k_to_device<R><<<nblk((long long)n * L, 256), 256, 0, s>>>(src, dst, n, L, np);
+template <class R, class H>
+void launch_to_device(const H *src, R *dst, int n, int L, int np, cudaStream_t s) {
+    k_to_device<H, R><<<nblk((long long)n * L, 256), 256, 0, s>>>(src, dst, n, L, np);
 }
-template <class R>
-void launch_from_device(const R *src, double *dst, int n, int L, int np, cudaStream_t s) {
-    k_from_device<R><<<nblk((long long)n * L, 256), 256, 0, s>>>(src, dst, n, L, np);
+template <class R, class H>
+void launch_from_device(const R *src, H *dst, int n, int L, int np, cudaStream_t s) {
+    k_from_device<R, H><<<nblk((long long)n * L, 256), 256, 0, s>>>(src, dst, n, L, np);
 }
-template <class R>
-void launch_add_bar(const R *ubar, const R *ut, double *dst, int E, int L, int Ep,
+template <class R, class H>
+void launch_add_bar(const R *ubar, const R *ut, H *dst, int E, int L, int Ep,
                     const int *kmax, cudaStream_t s) {
-    k_add_bar<R><<<nblk((long long)E * L, 256), 256, 0, s>>>(ubar, ut, dst, E, L, Ep, kmax);
+    k_add_bar<R, H><<<nblk((long long)E * L, 256), 256, 0, s>>>(ubar, ut, dst, E, L, Ep, kmax);
 }
 template <class R>
 void launch_mask_layers(R *x, int n, int L, int np, const int *kmax, cudaStream_t s) {
@@ -831,10 +834,15 @@ void launch_diag(const DMesh &m, const R *ubar, const R *ut, const double *h, co
     template void launch_transport<R>(const DMesh &, const TransportArgs<R> &, cudaStream_t);    \
     template void launch_thickness<R>(const DMesh &, const DParams &, const ThickArgs<R> &,      \
                                       cudaStream_t);                                             \
-    template void launch_to_device<R>(const double *, R *, int, int, int, cudaStream_t);         \
-    template void launch_from_device<R>(const R *, double *, int, int, int, cudaStream_t);       \
-    template void launch_add_bar<R>(const R *, const R *, double *, int, int, int, const int *,   \
-                                    cudaStream_t);                                               \
+    template void launch_to_device<R, double>(const double *, R *, int, int, int, cudaStream_t); \
+    template void launch_to_device<R, float>(const float *, R *, int, int, int, cudaStream_t);   \
+    template void launch_from_device<R, double>(const R *, double *, int, int, int,              \
+                                                cudaStream_t);                                   \
+    template void launch_from_device<R, float>(const R *, float *, int, int, int, cudaStream_t); \
+    template void launch_add_bar<R, double>(const R *, const R *, double *, int, int, int,       \
+                                            const int *, cudaStream_t);                          \
+    template void launch_add_bar<R, float>(const R *, const R *, float *, int, int, int,         \
+                                           const int *, cudaStream_t);                           \
     template void launch_mask_layers<R>(R *, int, int, int, const int *, cudaStream_t);          \
     template void launch_diag<R>(const DMesh &, const R *, const R *, const double *, const R *, \
                                  int, const double *, double *, int, double *, cudaStream_t);

@@ -43,6 +43,8 @@ def test_null_arguments(lib):
     assert lib.sse_step(None, 3, 60.0, 10, 1) == -1
     assert lib.sse_state_create(None, None, None, ct.byref(out)) == -1
     assert lib.sse_state_inject(None, 1, 1) == -1
+    assert lib.sse_state_set_f32(None, 0, None) == -1
+    assert lib.sse_state_get_f32(None, 0, None) == -1
 
 
 def _desc(m, L):

@@ -30,3 +30,41 @@ def test_pinned_and_pageable_host_buffers_agree(precision):
         assert np.array_equal(out.numpy().reshape(want.shape), want), n
     a.close()
     b.close()
+
+
+@pytest.mark.parametrize("precision", ["mixed", "fp64"])
+def test_fp32_transfers_match_the_fp64_ones(precision):
+    """sse_state_set_f32/get_f32 move the same values as the FP64 calls for the
+    fields held in the tendency precision; h and the other FP64 fields refuse
+    them."""
+    torch = pytest.importorskip("torch")
+    m, L, p, (u, h, tr), run = inputs.workload("channel_10km", perturb=True)
+    dm = binding.Mesh(m, L)
+    u32, t32 = u.astype(np.float32), tr[0].astype(np.float32)
+    a = binding.State(dm, p, precision)
+    b = binding.State(dm, p, precision)
+    a.set("u", u32.astype(np.float64))
+    a.set("h", h)
+    a.set("tracer0", t32.astype(np.float64))
+    b.set_f32("u", u32)                                             # pageable
+    b.set("h", h)
+    pin = torch.from_numpy(t32.copy()).pin_memory()
+    b.set_ptr_f32("tracer0", pin.data_ptr())                        # page-locked
+    for st in (a, b):
+        st.step(run["order"], run["dt"], run["M"], 2)
+    for n in ("u", "tracer0"):
+        want = a.get(n)
+        assert np.array_equal(b.get(n), want), n
+        assert np.array_equal(b.get_f32(n), want.astype(np.float32)), n
+        out = torch.empty(want.size, dtype=torch.float32).pin_memory()
+        b.get_ptr_f32(n, out.data_ptr())
+        assert np.array_equal(out.numpy().reshape(want.shape), want.astype(np.float32)), n
+    assert np.array_equal(b.get("h"), a.get("h"))
+    for n in ("h", "zeta", "Fzeta"):
+        with pytest.raises(binding.SSEError) as e:
+            b.get_f32(n)
+        assert e.value.code == -1
+    with pytest.raises(binding.SSEError):
+        b.set_f32("h", h.astype(np.float32))
+    a.close()
+    b.close()
