@@ -113,3 +113,19 @@ def test_oracle_equals_dense_with_partial_bottom_cells(order, vmix):
     # inactive layers stay empty
     assert np.abs(ho[~act]).max() == 0 and np.abs(to[:, ~act]).max() == 0
     assert np.abs(uo[np.arange(L)[None, :] >= Ke[:, None]]).max() == 0
+
+
+def test_every_term_is_exercised_by_the_brute_force_case():
+    """The brute-force comparison pins a term only if the case exercises it:
+    removing any one physics term moves the two-step result by orders of
+    magnitude more than the comparison's tolerance."""
+    m, L, p, (u, h, tr) = tiny_case("walls", 3, seed=14)
+    base = oracle.Oracle(m, L, p).step(3, 120.0, 4, u.copy(), h.copy(), tr.copy(), n_steps=2)
+    for term, off, field, least in [("c_drag", 0.0, 0, 1e-5), ("windStress", None, 0, 1e-6),
+                                    ("nu_h", 0.0, 0, 1e-6), ("nu_v", 0.0, 0, 1e-7),
+                                    ("nu_4", 0.0, 0, 1e-4), ("kappa_h", 0.0, 2, 1e-7),
+                                    ("kappa_v", 0.0, 2, 1e-7)]:
+        q = dict(p)
+        q[term] = off
+        out = oracle.Oracle(m, L, q).step(3, 120.0, 4, u.copy(), h.copy(), tr.copy(), n_steps=2)
+        assert rel(out[field], base[field]) > least, term
