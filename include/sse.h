@@ -272,6 +272,14 @@ int sse_state_create_ex(const sse_mesh *mesh, const sse_params *params,
                         const sse_tuning *tuning, void *cuda_stream, sse_state **out);
 /* Patches of the state's tiled sub-cycle (0: the global-memory sub-cycle). */
 int sse_state_patches(const sse_state *state, int *patches);
+/* CUDA graphs the state holds.  sse_step with n_steps >= 2 runs the steps in
+ * pairs, each pair replayed from a graph captured (once per order, dt,
+ * n_substeps and buffer assignment) from the launches a single step makes;
+ * an odd last step runs launch by launch.  Graphs are not used while
+ * profiling is on or the test hook below is set, and not at all on the
+ * legacy default stream (a NULL cuda_stream), which cannot be captured.
+ * Results are the same bits either way. */
+int sse_state_graphs(const sse_state *state, int *graphs);
 
 /* Test hook for the failure path of the sub-cycle's grid barriers (no
  * counterpart in the paper).  With SSE_INJECT_BARRIER_STALL set to 1, every

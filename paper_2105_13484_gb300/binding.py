@@ -86,7 +86,7 @@ EXPORTS = ["sse_mesh_create", "sse_mesh_destroy", "sse_state_create", "sse_state
            "sse_barotropic_substep", "sse_diagnostics", "sse_kernels_per_step", "sse_profile",
            "sse_profile_read", "sse_barotropic_substep_noalloc", "sse_state_footprint",
            "sse_state_footprint_ex", "sse_state_create_ex", "sse_state_patches", "sse_state_inject",
-           "sse_state_set_f32", "sse_state_get_f32",
+           "sse_state_set_f32", "sse_state_get_f32", "sse_state_graphs",
            "sse_tune",
            "sse_mesh_dims", "sse_server_create", "sse_server_submit", "sse_server_query",
            "sse_server_wait", "sse_server_stats", "sse_server_release", "sse_server_destroy",
@@ -133,6 +133,7 @@ def load(path: str = LIB_PATH):
     lib.sse_state_footprint_ex.argtypes = [ct.c_void_p, ct.POINTER(Params), ct.POINTER(Tuning),
                                            ct.POINTER(ct.c_size_t)]
     lib.sse_state_patches.argtypes = [ct.c_void_p, ct.POINTER(ct.c_int)]
+    lib.sse_state_graphs.argtypes = [ct.c_void_p, ct.POINTER(ct.c_int)]
     lib.sse_state_inject.argtypes = [ct.c_void_p, ct.c_int, ct.c_int]
     lib.sse_state_set_f32.argtypes = [ct.c_void_p, ct.c_int, ct.c_void_p]
     lib.sse_state_get_f32.argtypes = [ct.c_void_p, ct.c_int, ct.c_void_p]
@@ -356,6 +357,11 @@ class State:
         """Test hook: every grid-barrier wait of the sub-cycle runs out its
         bounded budget while on (sse_state_inject)."""
         _check(self.lib.sse_state_inject(self.handle, 1, 1 if on else 0), "sse_state_inject")
+
+    def graphs(self) -> int:
+        n = ct.c_int()
+        _check(self.lib.sse_state_graphs(self.handle, ct.byref(n)), "sse_state_graphs")
+        return int(n.value)
 
     def kernels_per_step(self, order: int) -> int:
         return int(self.lib.sse_kernels_per_step(self.handle, int(order)))

@@ -345,6 +345,8 @@ struct EngineBase {
     virtual int set_f32(int field, const float *host) = 0;
     virtual int get_f32(int field, float *host) = 0;
     virtual int step(int order, double dt, int M) = 0;
+    virtual int step2(int order, double dt, int M) = 0;   // two steps, replayed from a graph
+    virtual int graph_count() const = 0;                  // step-pair graphs held
     virtual int bcl_feuler(double dt) = 0;
     virtual int btr_substep(int order, double dt, int M) = 0;
     virtual int patches() const = 0;       // tiled sub-cycle patches (0: global kernel)
@@ -762,6 +764,7 @@ struct Engine : EngineBase {
                 launch_scale(wind, 1.0 / p.rho0, wind_d, wind_f, m.E, s);
                 p.wind = wind_d;
                 p.wind_f = wind_f;
+                graphs_clear();   // the step's kernel arguments changed
                 break;
             } else {
                 return SSE_ERR_INVALID_ARG;
@@ -936,8 +939,6 @@ struct Engine : EngineBase {
             transport(hR_1, zeta_1, ubar_np1, ut_c, 1.0, nullptr, nullptr, 0.0, Fz2,
                       consistent ? Fz1 : S1, nullptr, 0.5, 0.5, 2.0, nullptr);
             thickness(h_1, hR_1, tr_1, 0.5, 0.5, dt, h_n, hR_n, tr_n, zeta_n);
-            std::swap(ut_n, ut_c);
-            std::swap(ubar_n, ubar_np1);
         } else {
             // Stage 1 (Sec. 3.3)
             bcl_stage(ubar_n, ut_n, hR_n, tr_n, zeta_n, true, nullptr, 0.0, 1.0, dt, ut_1, G0);
@@ -962,10 +963,83 @@ struct Engine : EngineBase {
                       consistent ? Fz1 : S1, consistent ? Fz2 : S2, 2.0 / 3.0, 1.0 / 6.0, 1.5,
                       nullptr);
             thickness(h_h, hR_h, tr_h, 1.0 / 3.0, 2.0 / 3.0, dt, h_n, hR_n, tr_n, zeta_n);
-            std::swap(ut_n, ut_3);
-            std::swap(ubar_n, ubar_np1);
         }
+        advance(order);
+        return check_launch();
+    }
+
+    // The host side of the end of a step: the new levels become level n.
+    void advance(int order) {
+        std::swap(ut_n, order == 2 ? ut_c : ut_3);
+        std::swap(ubar_n, ubar_np1);
         steps++;
+    }
+
+    // ---- CUDA graphs of two large steps (sse_step with n_steps >= 2): the
+    // launches of step() twice, captured once per (order, dt, M) and buffer
+    // assignment (two steps bring the rotating buffers back), then replayed
+    // with one cudaGraphLaunch.  Not used while profiling or with the barrier
+    // stall hook on; given up for good if a capture fails (the legacy default
+    // stream cannot be captured), in which case the steps run launch by launch.
+    struct StepGraph {
+        int order, M;
+        double dt;
+        const void *key[5];
+        cudaGraphExec_t exec;
+    };
+    std::vector<StepGraph> graphs;
+    bool graphs_ok = true;
+    void graphs_clear() {
+        for (auto &g : graphs) cudaGraphExecDestroy(g.exec);
+        graphs.clear();
+    }
+    ~Engine() override { graphs_clear(); }
+    int graph_count() const override { return (int)graphs.size(); }
+
+    int step2(int order, double dt, int M) override {
+        if (!graphs_ok || prof || inject_stall) {
+            int rc = step(order, dt, M);
+            return rc ? rc : step(order, dt, M);
+        }
+        const void *key[5] = {ut_n, ut_c, ut_3, ubar_n, ubar_np1};
+        for (auto &g : graphs)
+            if (g.order == order && g.dt == dt && g.M == M &&
+                std::equal(key, key + 5, g.key)) {
+                CK(cudaGraphLaunch(g.exec, s));
+                advance(order);
+                advance(order);
+                return check_launch();
+            }
+        R *k_ut_n = ut_n, *k_ut_c = ut_c, *k_ut_3 = ut_3, *k_ub = ubar_n, *k_ubp = ubar_np1;
+        const long long steps0 = steps;
+        if (cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+            cudaGetLastError();
+            graphs_ok = false;
+            return step2(order, dt, M);
+        }
+        int rc = step(order, dt, M);
+        if (!rc) rc = step(order, dt, M);
+        cudaGraph_t g = nullptr;
+        cudaError_t e = cudaStreamEndCapture(s, &g);
+        cudaGraphExec_t x = nullptr;
+        if (!rc && e == cudaSuccess && g) e = cudaGraphInstantiate(&x, g, 0);
+        if (g) cudaGraphDestroy(g);
+        // capturing ran the host side of the two steps: undo it; the launch redoes it
+        ut_n = k_ut_n; ut_c = k_ut_c; ut_3 = k_ut_3; ubar_n = k_ub; ubar_np1 = k_ubp;
+        steps = steps0;
+        if (rc || e != cudaSuccess || !x) {
+            if (x) cudaGraphExecDestroy(x);
+            cudaGetLastError();
+            graphs_ok = false;
+            return step2(order, dt, M);
+        }
+        if (graphs.size() >= 8) graphs_clear();
+        StepGraph sg{order, M, dt, {}, x};
+        std::copy(key, key + 5, sg.key);
+        graphs.push_back(sg);
+        CK(cudaGraphLaunch(x, s));
+        advance(order);
+        advance(order);
         return check_launch();
     }
 
@@ -1118,6 +1192,12 @@ extern "C" int sse_state_inject(sse_state *st, int what, int value) {
     return SSE_OK;
 }
 
+extern "C" int sse_state_graphs(const sse_state *st, int *graphs) {
+    if (!st || !graphs) return SSE_ERR_INVALID_ARG;
+    *graphs = st->eng->graph_count();
+    return SSE_OK;
+}
+
 extern "C" int sse_state_patches(const sse_state *st, int *patches) {
     if (!st || !patches) return SSE_ERR_INVALID_ARG;
     *patches = st->eng->patches();
@@ -1241,7 +1321,12 @@ extern "C" int sse_step(sse_state *st, int order, double dt, int n_substeps, int
     if (!st || (order != 2 && order != 3) || !(dt > 0) || !isfinite(dt) || n_substeps < 1 ||
         n_steps < 0)
         return SSE_ERR_INVALID_ARG;
-    for (int i = 0; i < n_steps; i++) {
+    int i = 0;
+    for (; i + 2 <= n_steps; i += 2) {
+        int rc = st->eng->step2(order, dt, n_substeps);
+        if (rc) return rc;
+    }
+    for (; i < n_steps; i++) {
         int rc = st->eng->step(order, dt, n_substeps);
         if (rc) return rc;
     }
