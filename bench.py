@@ -33,6 +33,7 @@ import json
 import os
 import platform
 import subprocess
+import tempfile
 import sys
 import time
 
@@ -153,7 +154,10 @@ class ClockSampler:
     def __init__(self, index):
         self.index = index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
+        # the raw samples go to SSE_CLOCKS_DIR (default: the system temp folder);
+        # the JSON line carries their summary
+        d = os.environ.get("SSE_CLOCKS_DIR") or tempfile.gettempdir()
+        self.path = os.path.join(d, f"clocks_{os.getpid()}.csv")
 
     def start(self):
         try:
