@@ -278,7 +278,11 @@ int sse_state_patches(const sse_state *state, int *patches);
  * an odd last step runs launch by launch.  Graphs are not used while
  * profiling is on or the test hook below is set, and not at all on the
  * legacy default stream (a NULL cuda_stream), which cannot be captured.
- * Results are the same bits either way. */
+ * Results are the same bits either way.  While a capture is in progress,
+ * work that another thread puts on the legacy default stream would have to
+ * wait for the state's stream; give a state stepped in pairs a stream created
+ * with cudaStreamNonBlocking (the request runtime's streams are) when other
+ * threads use the legacy default stream. */
 int sse_state_graphs(const sse_state *state, int *graphs);
 
 /* Test hook for the failure path of the sub-cycle's grid barriers (no
