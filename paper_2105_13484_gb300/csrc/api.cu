@@ -499,27 +499,19 @@ struct Engine : EngineBase {
                 most = std::max(most, std::max(std::max(t.n_own_e, t.ne - t.n_own_e),
                                                std::max(t.n_own_c, t.nc - t.n_own_c)));
             }
-            // the runtime reserves 1 KB of shared memory per block; a patch keeps
-            // G and 1/d_e in shared memory when they fit, else in global memory
-            const size_t smem_g = tile_smem_bytes(plan, m.maxE, m.maxE2, sizeof(R), true);
-            const size_t smem_n = tile_smem_bytes(plan, m.maxE, m.maxE2, sizeof(R), false);
-            auto fits = [&](size_t b, int per_sm) {
-                return b <= (size_t)smem_block && (size_t)per_sm * (b + 1024) <= (size_t)smem_sm;
-            };
+            const size_t smem = tile_smem_bytes(plan, m.maxE, m.maxE2, sizeof(R));
+            // the runtime reserves 1 KB of shared memory per block
+            const bool half_sm = most <= 3 * 512 && smem <= (size_t)smem_block &&
+                                 2 * (smem + 1024) <= (size_t)smem_sm;
+            const bool whole_sm = P <= nsm && most <= 3 * 1024 && smem <= (size_t)smem_block &&
+                                  smem + 1024 <= (size_t)smem_sm;
             int nthreads = 0;
-            bool gsm = true;
-            if (most <= 3 * 512 && (P > nsm || most <= 512) && (fits(smem_g, 2) || fits(smem_n, 2))) {
-                nthreads = 512;
-                gsm = fits(smem_g, 2);
-            } else if (P <= nsm && most <= 3 * 1024 && (fits(smem_g, 1) || fits(smem_n, 1))) {
-                nthreads = 1024;
-                gsm = fits(smem_g, 1);
-            }
-            const size_t smem = gsm ? smem_g : smem_n;
+            if (half_sm && (P > nsm || most <= 512)) nthreads = 512;
+            else if (whole_sm) nthreads = 1024;
             if (!small || nthreads == 0) {
                 if (verbose)
                     fprintf(stderr, "libsse: tile plan k=%d P=%d: patch too large (%d entries, "
-                            "smem %zu, limits %d/%d)\n", k, P, most, smem_n, smem_block, smem_sm);
+                            "smem %zu, limits %d/%d)\n", k, P, most, smem, smem_block, smem_sm);
                 continue;
             }
             const int own = std::max(2, (most + nthreads - 1) / nthreads);
@@ -529,14 +521,14 @@ struct Engine : EngineBase {
             // plans need less or more, never lower it under each other
             for (int o = 2; o <= 3; o++) {
                 cudaFuncAttributes fa;
-                CK(cudaFuncGetAttributes(&fa, btr_tiled_kernel_ptr<R>(o, own, nthreads, gsm)));
-                CK(cudaFuncSetAttribute(btr_tiled_kernel_ptr<R>(o, own, nthreads, gsm),
+                CK(cudaFuncGetAttributes(&fa, btr_tiled_kernel_ptr<R>(o, own, nthreads)));
+                CK(cudaFuncSetAttribute(btr_tiled_kernel_ptr<R>(o, own, nthreads),
                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
                                         smem_block - (int)fa.sharedSizeBytes));
             }
             int occ = 0;
             CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-                &occ, btr_tiled_kernel_ptr<R>(3, own, nthreads, gsm), nthreads, smem));
+                &occ, btr_tiled_kernel_ptr<R>(3, own, nthreads), nthreads, smem));
             if (occ * nsm < P) {
                 if (verbose)
                     fprintf(stderr, "libsse: tile plan k=%d P=%d: occupancy %d x %d SMs\n", k, P,
@@ -550,17 +542,17 @@ struct Engine : EngineBase {
                     mne = std::max(mne, t.ne); mnc = std::max(mnc, t.nc);
                     moe = std::max(moe, t.n_own_e); tne += t.ne; tnc += t.nc;
                 }
-                fprintf(stderr, "libsse: tiled sub-cycle P=%d threads=%d own=%d smem=%zu gsm=%d "
+                fprintf(stderr, "libsse: tiled sub-cycle P=%d threads=%d own=%d smem=%zu "
                         "max(ne,nc,own_e)=(%d,%d,%d) halo overhead edges %.2f cells %.2f\n", P,
-                        nthreads, own, smem, (int)gsm, mne, mnc, moe,
+                        nthreads, own, smem, mne, mnc, moe,
                         (double)tne / m.E, (double)tnc / m.C);
             }
-            return upload_tiles(plan, nthreads, own, smem, gsm);
+            return upload_tiles(plan, nthreads, own, smem);
         }
         return SSE_OK;  // no plan fits: the global-memory sub-cycle is used
     }
 
-    int upload_tiles(const TilePlan &plan, int nthreads, int own, size_t smem, bool gsm) {
+    int upload_tiles(const TilePlan &plan, int nthreads, int own, size_t smem) {
         const unsigned int sR = sizeof(R);
         std::vector<int> noc, noe, nie, cg, eg, c12, nel, ncl;
         std::vector<unsigned short> eo, ce;
@@ -601,14 +593,13 @@ struct Engine : EngineBase {
             for (double x : t.H) Hh.push_back((R)x);
         }
         DTiles<R> &t = tiles;
-        t.P = plan.P; t.nthreads = nthreads; t.own = own; t.smem = smem; t.gsm = gsm ? 1 : 0;
+        t.P = plan.P; t.nthreads = nthreads; t.own = own; t.smem = smem;
         t.cell_off = A.upload(plan.cell_off); t.edge_off = A.upload(plan.edge_off);
         t.n_own_c = A.upload(noc); t.n_own_e = A.upload(noe); t.n_int_e = A.upload(nie);
         t.ne_lim = A.upload(nel); t.nc_lim = A.upload(ncl);
         t.cell_gid = A.upload(cg); t.edge_gid = A.upload(eg); t.c12 = A.upload(c12);
         t.eoe = A.upload(eo); t.cfc = A.upload(cf); t.invdc = A.upload(idc);
         t.ce = A.upload(ce); t.divc = A.upload(dv); t.H = A.upload(Hh);
-        t.Gl = A.alloc<R>((size_t)plan.edge_off[plan.P] + 1);
         for (int b = 0; b < 2; b++) {
             t.xu[b] = A.alloc<R>(m.Ep);
             t.xz[b] = A.alloc<R>(m.Cp);

@@ -305,9 +305,7 @@ __device__ __forceinline__ char *align16(char *p) {
     return (char *)(((uintptr_t)p + 15) & ~(uintptr_t)15);
 }
 
-// shared-memory layout of a patch; without GSM the forcing G and 1/d_e are
-// left to the caller (global memory)
-template <class R, bool GSM>
+template <class R>
 __device__ __forceinline__ TileSmem<R> carve(char *base, int ne, int nc) {
     TileSmem<R> s;
     char *c = align16(base);
@@ -315,9 +313,7 @@ __device__ __forceinline__ TileSmem<R> carve(char *base, int ne, int nc) {
     R *r = (R *)c;
     s.u0 = r; r += ne1; s.ua = r; r += ne1; s.uh = r; r += ne1; s.fl = r; r += ne1;
     s.z0 = r; r += nc1; s.za = r; r += nc1; s.zh = r; r += nc1;
-    s.H = r; r += nc1;
-    s.G = nullptr; s.idc = nullptr;
-    if (GSM) { s.G = r; r += ne1; s.idc = r; r += ne1; }
+    s.G = r; r += ne1; s.H = r; r += nc1; s.idc = r; r += ne1;
     c = align16((char *)r);
     s.c12 = (unsigned int *)c; c = align16(c + 4 * ne1);
     s.eoe = (unsigned short *)c; c = align16(c + 2 * TILE_NE2P * (size_t)ne1);
@@ -404,7 +400,7 @@ template <> struct FzAcc<double> {
 // Each thread owns at most OWN owned edges, halo edges, owned cells and halo
 // cells of its patch (the plan checks this); their global indices, the
 // sub-step's partial F^zeta and the FP64 accumulators stay in registers.
-template <class R, int ORDER, int OWN, int NT, bool GSM>
+template <class R, int ORDER, int OWN, int NT>
 __global__ void __launch_bounds__(NT, 1024 / NT) k_btr_tiled(DTiles<R> t, BtrArgs<R> a,
                                                              Barrier bar) {
     extern __shared__ __align__(16) char smem_raw[];
@@ -417,8 +413,7 @@ __global__ void __launch_bounds__(NT, 1024 / NT) k_btr_tiled(DTiles<R> t, BtrArg
     // outer rings of the halo drop out one per sub-stage)
     const int neA = t.ne_lim[3 * p], neB = t.ne_lim[3 * p + 1], neC = t.ne_lim[3 * p + 2];
     const int ncA = t.nc_lim[3 * p], ncB = t.nc_lim[3 * p + 1], ncC = t.nc_lim[3 * p + 2];
-    TileSmem<R> S = carve<R, GSM>(smem_raw, ne, nc);
-    if (!GSM) { S.G = t.Gl + eoff; S.idc = (R *)t.invdc + eoff; }   // read-only here
+    const TileSmem<R> S = carve<R>(smem_raw, ne, nc);
     const R *cfc = t.cfc + (size_t)eoff * TILE_NE2P;
     const R *dvc = t.divc + (size_t)coff * TILE_NCEP;
     const R tau = (R)a.tau, g = (R)a.g;
@@ -446,9 +441,7 @@ __global__ void __launch_bounds__(NT, 1024 / NT) k_btr_tiled(DTiles<R> t, BtrArg
             d = t.invdc[eoff + l];
             cc = (unsigned int)t.c12[eoff + l];
         }
-        S.u0[l] = u; S.c12[l] = cc;
-        if (GSM) { S.G[l] = G; S.idc[l] = d; }
-        else if (l < ne) t.Gl[eoff + l] = G;   // read back by this block only
+        S.u0[l] = u; S.G[l] = G; S.idc[l] = d; S.c12[l] = cc;
         S.ua[l] = R(0); S.uh[l] = R(0); S.fl[l] = R(0);
     }
     {
@@ -606,21 +599,16 @@ __global__ void __launch_bounds__(NT, 1024 / NT) k_btr_tiled(DTiles<R> t, BtrArg
     }
 }
 
-template <class R, int NT, bool GSM> const void *btr_tiled_kernel_ptr_nt(int order, int own) {
+template <class R, int NT> const void *btr_tiled_kernel_ptr_nt(int order, int own) {
     if (own == 2)
-        return order == 2 ? (const void *)k_btr_tiled<R, 2, 2, NT, GSM>
-                          : (const void *)k_btr_tiled<R, 3, 2, NT, GSM>;
-    return order == 2 ? (const void *)k_btr_tiled<R, 2, 3, NT, GSM>
-                      : (const void *)k_btr_tiled<R, 3, 3, NT, GSM>;
+        return order == 2 ? (const void *)k_btr_tiled<R, 2, 2, NT>
+                          : (const void *)k_btr_tiled<R, 3, 2, NT>;
+    return order == 2 ? (const void *)k_btr_tiled<R, 2, 3, NT>
+                      : (const void *)k_btr_tiled<R, 3, 3, NT>;
 }
-template <class R>
-const void *btr_tiled_kernel_ptr(int order, int own, int nthreads, bool gsm) {
-    if (nthreads == 512)
-        return gsm ? btr_tiled_kernel_ptr_nt<R, 512, true>(order, own)
-                   : btr_tiled_kernel_ptr_nt<R, 512, false>(order, own);
-    if (nthreads == 1024)
-        return gsm ? btr_tiled_kernel_ptr_nt<R, 1024, true>(order, own)
-                   : btr_tiled_kernel_ptr_nt<R, 1024, false>(order, own);
+template <class R> const void *btr_tiled_kernel_ptr(int order, int own, int nthreads) {
+    if (nthreads == 512) return btr_tiled_kernel_ptr_nt<R, 512>(order, own);
+    if (nthreads == 1024) return btr_tiled_kernel_ptr_nt<R, 1024>(order, own);
     return nullptr;
 }
 
@@ -641,13 +629,13 @@ cudaError_t launch_btr_tiled(const DTiles<R> &t, const BtrArgs<R> &a, const Barr
     attr[0].val.cooperative = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    const void *fn = btr_tiled_kernel_ptr<R>(a.order, t.own, t.nthreads, t.gsm != 0);
+    const void *fn = btr_tiled_kernel_ptr<R>(a.order, t.own, t.nthreads);
     if (!fn) return cudaErrorInvalidConfiguration;
     return cudaLaunchKernelExC(&cfg, fn, args);
 }
 
-template const void *btr_tiled_kernel_ptr<double>(int, int, int, bool);
-template const void *btr_tiled_kernel_ptr<float>(int, int, int, bool);
+template const void *btr_tiled_kernel_ptr<double>(int, int, int);
+template const void *btr_tiled_kernel_ptr<float>(int, int, int);
 template cudaError_t launch_btr_tiled<double>(const DTiles<double> &, const BtrArgs<double> &,
                                               const Barrier &, cudaStream_t);
 template cudaError_t launch_btr_tiled<float>(const DTiles<float> &, const BtrArgs<float> &,

@@ -178,7 +178,6 @@ int btr_max_items_per_thread();
 // flattened with the offsets cell_off / edge_off.
 template <class R> struct DTiles {
     int P, nthreads, own;            // patches, threads per patch, entries per thread
-    int gsm;                         // G and 1/d_e in shared memory (else read from Gl, invdc)
     const int *cell_off, *edge_off;  // [P + 1]
     const int *n_own_c, *n_own_e;    // [P]
     const int *n_int_e;              // [P] owned edges with both cells owned (local 0..)
@@ -188,7 +187,6 @@ template <class R> struct DTiles {
     const unsigned short *eoe;       // [sum ne][TILE_NE2P] byte offsets of local edgesOnEdge
     const R *cfc;                    // per patch [TILE_NE2P][ne] Coriolis coefficients (0 on padding)
     const R *invdc;                  // [sum ne]
-    R *Gl;                           // [sum ne] the launch's forcing G in local order (gsm 0)
     const unsigned short *ce;        // [sum nc][TILE_NCEP] byte offsets of local edgesOnCell
     const R *divc;                   // per patch [TILE_NCEP][nc] divergence coefficients
     const R *H;                      // patch p at cell_off[p] + p: [nc_p + 1]
@@ -200,8 +198,8 @@ template <class R>
 cudaError_t launch_btr_tiled(const DTiles<R> &t, const BtrArgs<R> &a, const Barrier &bar,
                              cudaStream_t s);
 // kernel of the tiled sub-cycle for (order, entries per thread, threads per
-// patch: 512 or 1024, G and 1/d_e in shared memory); null for another thread count
-template <class R> const void *btr_tiled_kernel_ptr(int order, int own, int nthreads, bool gsm);
+// patch: 512 or 1024); null for another thread count
+template <class R> const void *btr_tiled_kernel_ptr(int order, int own, int nthreads);
 
 template <class R> struct TransportArgs {
     const R *hR;              // stage thickness [L][Cp] in the tendency precision

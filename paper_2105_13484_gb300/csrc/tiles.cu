@@ -225,7 +225,7 @@ bool build_tile_plan(const HostMesh &hm, int P, int K, TilePlan &plan) {
     return true;
 }
 
-size_t tile_smem_bytes(const TilePlan &plan, int maxE, int maxE2, size_t sR, bool gd_smem) {
+size_t tile_smem_bytes(const TilePlan &plan, int maxE, int maxE2, size_t sR) {
     (void)maxE;
     (void)maxE2;
     size_t best = 0;
@@ -233,9 +233,9 @@ size_t tile_smem_bytes(const TilePlan &plan, int maxE, int maxE2, size_t sR, boo
         const size_t ne = t.ne + 1, nc = t.nc + 1;
         size_t b = 0;
         b += sR * (4 * ne);                 // u0, ua, uh, flux
-        if (gd_smem) b += 2 * sR * ne;      // G, 1/d_e
+        b += sR * ne;                       // 1/d_e
         b += sR * (3 * nc);                 // z0, za, zh
-        b += sR * nc;                       // H
+        b += sR * (ne + nc);                // G, H
         b += 4 * ne;                        // packed local byte offsets of (c1, c2)
         b += 2 * TILE_NE2P * ne;            // edgesOnEdge byte offsets, padded
         b += 2 * TILE_NCEP * nc;            // edgesOnCell byte offsets, padded

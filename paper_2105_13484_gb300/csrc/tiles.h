@@ -57,8 +57,7 @@ bool build_tile_plan(const HostMesh &hm, int P, int K, TilePlan &plan);
 // cells (the TRiSK stencil): the ring counts of a plan, which decide which
 // halo values are exact after each sub-stage, rely on it.
 bool tile_stencil_ok(const HostMesh &hm);
-// Dynamic shared memory of the largest patch for element size sR; with
-// gd_smem false the per-edge forcing G and 1/d_e stay in global memory.
-size_t tile_smem_bytes(const TilePlan &plan, int maxE, int maxE2, size_t sR, bool gd_smem);
+// Dynamic shared memory of the largest patch for element size sR.
+size_t tile_smem_bytes(const TilePlan &plan, int maxE, int maxE2, size_t sR);
 
 }  // namespace sse
