@@ -96,8 +96,11 @@ def step_bytes_per_cell_layer(mixed: bool, nT: int = 1) -> float:
 # ncu summaries under profiles/ per kernel class (mixed form, this workload);
 # each records DRAM traffic per launch and the hashes of the sources it was
 # captured from, so a figure taken from an older kernel is not reported
-PROFILE_OF = {"btr": "btr_tiled_channel_1km.md", "bcl_edge": "bcl_edge_channel_1km.md",
-              "thickness": "thickness_channel_1km.md"}
+PROFILE_OF = {  # committed ncu summaries by workload and kernel class (mixed form)
+    "channel_1km": {"btr": "btr_tiled_channel_1km.md", "bcl_edge": "bcl_edge_channel_1km.md",
+                    "thickness": "thickness_channel_1km.md"},
+    "sphere_l7": {"btr": "btr_tiled_sphere_l7.md"},
+}
 KERNEL_SOURCES = ("paper_2105_13484_gb300/csrc/btr_kernel.cu",
                   "paper_2105_13484_gb300/csrc/stage_kernels.cu",
                   "paper_2105_13484_gb300/csrc/sse_internal.cuh")
@@ -112,12 +115,12 @@ def source_hashes():
     return out
 
 
-def ncu_traffic(cls, mixed):
+def ncu_traffic(cls, mixed, workload):
     """DRAM bytes per launch from the committed ncu capture of `cls`, or
     (None, reason) when there is none or the kernel sources have changed."""
-    name = PROFILE_OF.get(cls)
+    name = PROFILE_OF.get(workload, {}).get(cls)
     if not mixed or name is None:
-        return None, "no ncu capture of this kernel/form"
+        return None, "no ncu capture of this kernel/form/workload"
     path = os.path.join(ROOT, "profiles", name)
     if not os.path.exists(path):
         return None, "no ncu capture of this kernel/form"
@@ -406,8 +409,8 @@ def measure_workload(torch, binding, name, forms_todo, headline, steps, warmup, 
         out["mixed_err"] = err
     prof = head["prof"]
     roof = roofline_of(prof, m, L, nT, mixed, run["order"], steps, head["ms_per_step"])
-    traffic, traffic_src = ncu_traffic(roof["kernel"], mixed) if name == WORKLOAD else \
-        (None, "no ncu capture of this workload")
+    traffic, traffic_src = ncu_traffic(roof["kernel"], mixed, name) if not over else \
+        (None, "no ncu capture of this variant of the workload")
     roof["traffic"], roof["traffic_source"] = traffic, traffic_src
     out["roofline"] = roof
     out["step_roofline"] = step_roofline_of(m, L, nT, mixed, head["ms_per_step"])
