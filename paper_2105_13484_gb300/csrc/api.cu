@@ -13,6 +13,8 @@
 #include <algorithm>
 #include <numeric>
 #include <type_traits>
+
+#include <nvtx3/nvToolsExt.h>
 #include <map>
 #include <memory>
 #include <mutex>
@@ -372,13 +374,20 @@ struct EngineBase {
         cudaEventCreate(&e);
         return e;
     }
+    // An NVTX range per kernel class (visible to nsys and other NVTX tools,
+    // no-ops otherwise); with profiling on, CUDA events around the launch.
     void pbeg(int cls) {
+        static const char *const names[SSE_K_NCLASS] = {
+            "sse cell_diag", "sse vertex", "sse edge_pre", "sse bcl_edge", "sse btr",
+            "sse transport", "sse thickness", "sse combine", "sse del4"};
+        nvtxRangePushA(names[cls]);
         if (!prof) return;
         Rec r{cls, take(), take()};
         cudaEventRecord(r.a, ps);
         recs.push_back(r);
     }
     void pend() {
+        nvtxRangePop();
         if (!prof || recs.empty()) return;
         cudaEventRecord(recs.back().b, ps);
     }
@@ -1321,16 +1330,12 @@ extern "C" int sse_step(sse_state *st, int order, double dt, int n_substeps, int
     if (!st || (order != 2 && order != 3) || !(dt > 0) || !isfinite(dt) || n_substeps < 1 ||
         n_steps < 0)
         return SSE_ERR_INVALID_ARG;
-    int i = 0;
-    for (; i + 2 <= n_steps; i += 2) {
-        int rc = st->eng->step2(order, dt, n_substeps);
-        if (rc) return rc;
-    }
-    for (; i < n_steps; i++) {
-        int rc = st->eng->step(order, dt, n_substeps);
-        if (rc) return rc;
-    }
-    return SSE_OK;
+    nvtxRangePushA("sse_step");
+    int i = 0, rc = SSE_OK;
+    for (; !rc && i + 2 <= n_steps; i += 2) rc = st->eng->step2(order, dt, n_substeps);
+    for (; !rc && i < n_steps; i++) rc = st->eng->step(order, dt, n_substeps);
+    nvtxRangePop();
+    return rc;
 }
 
 extern "C" int sse_baroclinic_feuler(sse_state *st, double dt) {
