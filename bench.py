@@ -311,10 +311,11 @@ def measure_form(torch, binding, dm, m, L, p, state0, run, precision, steps, war
 
 def measure_e2e(torch, binding, dm, p, state0, run, precision, steps, stream):
     """Through the public C ABI with pinned host buffers: per step, H2D of
-    (u, h, T), one large step, D2H of (u, h, T).  Each field crosses in the
-    precision the state holds it in: FP32 u and T for the mixed form
-    (sse_state_set_f32/get_f32), FP64 h always, FP64 everything for the FP64
-    form."""
+    (u, h, T), one large step, D2H of (u, h, T), queued in stream order
+    (sse_state_transfer with SSE_XFER_ASYNC) and one sse_state_sync, after
+    which the step's result is in host memory.  Each field crosses in the
+    precision the state holds it in: FP32 u and T for the mixed form, FP64 h
+    always, FP64 everything for the FP64 form."""
     u, h, tr = state0
     st = binding.State(dm, p, precision, stream=stream.cuda_stream)
     fields = [("u", u), ("h", h)] + [(f"tracer{k}", tr[k]) for k in range(tr.shape[0])]
@@ -325,14 +326,15 @@ def measure_e2e(torch, binding, dm, p, state0, run, precision, steps, stream):
     order, dt, M = run["order"], run["dt"], run["M"]
 
     def put(n, x):
-        (st.set_ptr_f32 if f32[n] else st.set_ptr)(n, x.data_ptr())
+        st.transfer_ptr(n, x.data_ptr(), get=False, f32=f32[n], asynchronous=True)
 
     def take(n, x):
-        (st.get_ptr_f32 if f32[n] else st.get_ptr)(n, x.data_ptr())
+        st.transfer_ptr(n, x.data_ptr(), get=True, f32=f32[n], asynchronous=True)
 
     for n, x in hin:
         put(n, x)
     st.step(order, dt, M, 1)
+    st.sync()
     torch.cuda.synchronize()
     a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     a.record(stream)
@@ -342,6 +344,7 @@ def measure_e2e(torch, binding, dm, p, state0, run, precision, steps, stream):
         st.step(order, dt, M, 1)
         for n, x in hout:
             take(n, x)
+        st.sync()   # the step's result is in host memory
     b.record(stream)
     torch.cuda.synchronize()
     ms = a.elapsed_time(b)

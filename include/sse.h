@@ -179,6 +179,25 @@ int sse_state_get(sse_state *state, int field, double *host_out);
 int sse_state_set_f32(sse_state *state, int field, const float *host);
 int sse_state_get_f32(sse_state *state, int field, float *host_out);
 
+/* One entry point for all four transfers, with a stream-ordered option.
+ * flags: SSE_XFER_GET (device -> host; else host -> device), SSE_XFER_F32
+ * (an FP32 host array, same fields as sse_state_set_f32; else FP64) and
+ * SSE_XFER_ASYNC: the call returns without synchronising the state's
+ * stream.  Then the host array is read or written when the stream reaches
+ * the transfer: it must stay valid, and unchanged for a set, until then, and
+ * its contents after a get are defined only once the stream has passed it
+ * (sse_state_sync).  A pageable host array makes the copy synchronous all the
+ * same (the CUDA copy semantics of pageable memory); page-locked memory does
+ * not.  A barrier timeout is reported by the next synchronising call.
+ * SSE_ERR_INVALID_ARG for unknown flags or a field the precision excludes. */
+#define SSE_XFER_GET 1
+#define SSE_XFER_F32 2
+#define SSE_XFER_ASYNC 4
+int sse_state_transfer(sse_state *state, int field, void *host, int flags);
+/* Synchronise the state's stream; returns SSE_ERR_SYNC_TIMEOUT if a grid
+ * barrier of the sub-cycle timed out since the state was last set. */
+int sse_state_sync(sse_state *state);
+
 /* Advance n_steps large steps of SSPRK{order}-SE (order 2: Sec. 3.2 with
  * Algorithm 3; order 3: Sec. 3.3 with Algorithm 4), time step dt (s) and
  * n_substeps barotropic sub-steps of dt/n_substeps, with the reconciliation

@@ -86,7 +86,8 @@ EXPORTS = ["sse_mesh_create", "sse_mesh_destroy", "sse_state_create", "sse_state
            "sse_barotropic_substep", "sse_diagnostics", "sse_kernels_per_step", "sse_profile",
            "sse_profile_read", "sse_barotropic_substep_noalloc", "sse_state_footprint",
            "sse_state_footprint_ex", "sse_state_create_ex", "sse_state_patches", "sse_state_inject",
-           "sse_state_set_f32", "sse_state_get_f32", "sse_state_graphs",
+           "sse_state_set_f32", "sse_state_get_f32", "sse_state_graphs", "sse_state_transfer",
+           "sse_state_sync",
            "sse_tune",
            "sse_mesh_dims", "sse_server_create", "sse_server_submit", "sse_server_query",
            "sse_server_wait", "sse_server_stats", "sse_server_release", "sse_server_destroy",
@@ -134,6 +135,8 @@ def load(path: str = LIB_PATH):
                                            ct.POINTER(ct.c_size_t)]
     lib.sse_state_patches.argtypes = [ct.c_void_p, ct.POINTER(ct.c_int)]
     lib.sse_state_graphs.argtypes = [ct.c_void_p, ct.POINTER(ct.c_int)]
+    lib.sse_state_transfer.argtypes = [ct.c_void_p, ct.c_int, ct.c_void_p, ct.c_int]
+    lib.sse_state_sync.argtypes = [ct.c_void_p]
     lib.sse_state_inject.argtypes = [ct.c_void_p, ct.c_int, ct.c_int]
     lib.sse_state_set_f32.argtypes = [ct.c_void_p, ct.c_int, ct.c_void_p]
     lib.sse_state_get_f32.argtypes = [ct.c_void_p, ct.c_int, ct.c_void_p]
@@ -305,6 +308,17 @@ class State:
     def get_ptr_f32(self, field: str, ptr: int):
         _check(self.lib.sse_state_get_f32(self.handle, FIELD[field], ct.c_void_p(ptr)),
                f"get_f32 {field}")
+
+    def transfer_ptr(self, field: str, ptr: int, get: bool, f32: bool = False,
+                     asynchronous: bool = False):
+        """sse_state_transfer on a host pointer; with asynchronous=True the
+        array is read or written in stream order (see sync())."""
+        flags = (1 if get else 0) | (2 if f32 else 0) | (4 if asynchronous else 0)
+        _check(self.lib.sse_state_transfer(self.handle, FIELD[field], ct.c_void_p(ptr), flags),
+               f"transfer {field}")
+
+    def sync(self):
+        _check(self.lib.sse_state_sync(self.handle), "sse_state_sync")
 
     def load_state(self, u, h, tr):
         self.set("u", u)

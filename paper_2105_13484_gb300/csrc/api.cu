@@ -346,6 +346,8 @@ struct EngineBase {
     virtual int get(int field, double *host) = 0;
     virtual int set_f32(int field, const float *host) = 0;
     virtual int get_f32(int field, float *host) = 0;
+    virtual int transfer(int field, void *host, int flags) = 0;   // sse_state_transfer
+    virtual int sync() = 0;                                       // sse_state_sync
     virtual int step(int order, double dt, int M) = 0;
     virtual int step2(int order, double dt, int M) = 0;   // two steps, replayed from a graph
     virtual int graph_count() const = 0;                  // step-pair graphs held
@@ -723,10 +725,22 @@ struct Engine : EngineBase {
     int get(int field, double *host) override { return get_t<double>(field, host); }
     int set_f32(int field, const float *host) override { return set_t<float>(field, host); }
     int get_f32(int field, float *host) override { return get_t<float>(field, host); }
+    int transfer(int field, void *host, int flags) override {
+        const bool get = flags & SSE_XFER_GET, sync = !(flags & SSE_XFER_ASYNC);
+        if (flags & SSE_XFER_F32)
+            return get ? get_t<float>(field, (float *)host, sync)
+                       : set_t<float>(field, (const float *)host, sync);
+        return get ? get_t<double>(field, (double *)host, sync)
+                   : set_t<double>(field, (const double *)host, sync);
+    }
+    int sync() override {
+        CK(cudaStreamSynchronize(s));
+        return barrier_status();
+    }
 
     // Host transfers in precision H: FP64 for every field; FP32 for the fields
     // held in the tendency precision (u, utilde, ubar, G, tracers).
-    template <class H> int set_t(int field, const H *host) {
+    template <class H> int set_t(int field, const H *host, bool sync = true) {
         constexpr bool f64 = std::is_same<H, double>::value;
         const int L = m.L;
         // page-locked host buffers are read by the conversion kernels directly
@@ -785,11 +799,11 @@ struct Engine : EngineBase {
         steps = 0;
         int rc = check_launch();
         if (rc) return rc;
-        CK(cudaStreamSynchronize(s));
+        if (sync) CK(cudaStreamSynchronize(s));
         return SSE_OK;
     }
 
-    template <class H> int get_t(int field, H *host) {
+    template <class H> int get_t(int field, H *host, bool sync = true) {
         constexpr bool f64 = std::is_same<H, double>::value;
         const int L = m.L;
         size_t n = 0;
@@ -848,6 +862,7 @@ struct Engine : EngineBase {
         int rc = check_launch();
         if (rc) return rc;
         if (!direct) CK(cudaMemcpyAsync(host, stage, sizeof(H) * n, cudaMemcpyDeviceToHost, s));
+        if (!sync) return SSE_OK;
         CK(cudaStreamSynchronize(s));
         return barrier_status();
     }
@@ -1314,6 +1329,17 @@ extern "C" int sse_state_set(sse_state *st, int field, const double *host) {
 extern "C" int sse_state_get(sse_state *st, int field, double *host) {
     if (!st || !host) return SSE_ERR_INVALID_ARG;
     return st->eng->get(field, host);
+}
+
+extern "C" int sse_state_transfer(sse_state *st, int field, void *host, int flags) {
+    if (!st || !host || (flags & ~(SSE_XFER_GET | SSE_XFER_F32 | SSE_XFER_ASYNC)) != 0)
+        return SSE_ERR_INVALID_ARG;
+    return st->eng->transfer(field, host, flags);
+}
+
+extern "C" int sse_state_sync(sse_state *st) {
+    if (!st) return SSE_ERR_INVALID_ARG;
+    return st->eng->sync();
 }
 
 extern "C" int sse_state_set_f32(sse_state *st, int field, const float *host) {

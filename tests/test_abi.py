@@ -46,6 +46,8 @@ def test_null_arguments(lib):
     assert lib.sse_state_set_f32(None, 0, None) == -1
     assert lib.sse_state_get_f32(None, 0, None) == -1
     assert lib.sse_state_graphs(None, None) == -1
+    assert lib.sse_state_transfer(None, 0, None, 0) == -1
+    assert lib.sse_state_sync(None) == -1
 
 
 def _desc(m, L):

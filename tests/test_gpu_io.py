@@ -68,3 +68,39 @@ def test_fp32_transfers_match_the_fp64_ones(precision):
         b.set_f32("h", h.astype(np.float32))
     a.close()
     b.close()
+
+
+def test_stream_ordered_transfers_match_the_synchronous_ones():
+    """sse_state_transfer with SSE_XFER_ASYNC: sets, steps and gets queued in
+    stream order without a synchronisation give the same bits as the
+    synchronous calls once sse_state_sync returns."""
+    torch = pytest.importorskip("torch")
+    m, L, p, (u, h, tr), run = inputs.workload("channel_10km", perturb=True)
+    dm = binding.Mesh(m, L)
+    stream = torch.cuda.Stream()
+    a = binding.State(dm, p, "mixed")
+    b = binding.State(dm, p, "mixed", stream=stream.cuda_stream)
+    a.load_state(u, h, tr)
+    a.step(run["order"], run["dt"], run["M"], 2)
+    want = a.read_state()
+    src = {"u": torch.from_numpy(u.astype(np.float32)).pin_memory(),
+           "h": torch.from_numpy(np.ascontiguousarray(h)).pin_memory(),
+           "tracer0": torch.from_numpy(tr[0].astype(np.float32)).pin_memory()}
+    out = {n: torch.empty_like(x).pin_memory() for n, x in src.items()}
+    for _ in range(2):   # twice in a row from the same buffers
+        for n, x in src.items():
+            b.transfer_ptr(n, x.data_ptr(), get=False, f32=(n != "h"), asynchronous=True)
+        b.step(run["order"], run["dt"], run["M"], 2)
+        for n, x in out.items():
+            b.transfer_ptr(n, x.data_ptr(), get=True, f32=(n != "h"), asynchronous=True)
+        b.sync()
+    # a started from the FP64 u and T; b from their FP32 roundings, which the
+    # mixed form stores anyway: the same state
+    assert np.array_equal(out["u"].numpy(), want[0].astype(np.float32))
+    assert np.array_equal(out["h"].numpy(), want[1])
+    assert np.array_equal(out["tracer0"].numpy(), want[2][0].astype(np.float32))
+    import ctypes
+    lib = binding.load()
+    assert lib.sse_state_transfer(b.handle, 0, ctypes.c_void_p(out["u"].data_ptr()), 8) == -1
+    a.close()
+    b.close()
