@@ -309,7 +309,7 @@ def measure_form(torch, binding, dm, m, L, p, state0, run, precision, steps, war
     return res
 
 
-def measure_e2e(torch, binding, dm, p, state0, run, precision, steps, stream):
+def measure_e2e(torch, binding, dm, p, state0, run, precision, steps, stream, native=True):
     """Through the public C ABI with pinned host buffers: per step, H2D of
     (u, h, T), one large step, D2H of (u, h, T), queued in stream order
     (sse_state_transfer with SSE_XFER_ASYNC) and one sse_state_sync, after
@@ -319,7 +319,8 @@ def measure_e2e(torch, binding, dm, p, state0, run, precision, steps, stream):
     u, h, tr = state0
     st = binding.State(dm, p, precision, stream=stream.cuda_stream)
     fields = [("u", u), ("h", h)] + [(f"tracer{k}", tr[k]) for k in range(tr.shape[0])]
-    f32 = {n: precision == "mixed" and n != "h" for n, _ in fields}
+    # native: each field in the precision the state holds it in; else all FP64
+    f32 = {n: native and precision == "mixed" and n != "h" for n, _ in fields}
     hin = [(n, torch.from_numpy(np.ascontiguousarray(
         x, dtype=np.float32 if f32[n] else np.float64)).pin_memory()) for n, x in fields]
     hout = [(n, torch.empty_like(x).pin_memory()) for n, x in hin]
@@ -434,6 +435,15 @@ def measure_workload(torch, binding, name, forms_todo, headline, steps, warmup, 
                                      max_over_ranks(torch, dist, e2e_ms, "cuda"))
         out["e2e"] = {"value": e2e_val, "unit": METRIC, "h2d_bytes_per_step": nbytes,
                       "d2h_bytes_per_step": nbytes, "host_dtypes": dtypes}
+        if headline == "mixed":
+            # the same loop with every field crossing as FP64 host data
+            ms64, nb64, dt64 = measure_e2e(torch, binding, dm, p, state0, run, headline,
+                                           e2e_steps, stream, native=False)
+            out["e2e_fp64_host"] = {
+                "value": replica_throughput(m.nCells * L * e2e_steps, world,
+                                            max_over_ranks(torch, dist, ms64, "cuda")),
+                "unit": METRIC, "h2d_bytes_per_step": nb64, "d2h_bytes_per_step": nb64,
+                "host_dtypes": dt64}
     dm.close()
     return out
 
@@ -654,6 +664,7 @@ def run_ours(args):
         "forms": w["forms_summary"],
         "mixed_vs_fp64_rel_l2": w["mixed_err"],
         "e2e": w["e2e"],
+        "e2e_fp64_host": w.get("e2e_fp64_host"),
         "gpu_launches": head["kernels_per_step"] * args.steps,
         "clocks": head["clocks"],
         "cpu_baseline": cpu,
