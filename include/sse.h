@@ -24,6 +24,7 @@
 #ifndef SSE_H
 #define SSE_H
 
+#include <stddef.h>
 #include <stdint.h>
 
 #ifdef __cplusplus

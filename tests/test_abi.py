@@ -147,3 +147,20 @@ def test_partial_bottom_arrays_are_validated(lib):
         i = int(np.argmin(K))
         r2 = rest.copy(); r2[i, L - 1] = 1.0; r2[i, 0] -= 1.0     # water below the bottom
         assert try_with(K, r2) == -2
+
+
+@pytest.mark.parametrize("lang,std", [("c", "-std=c99"), ("c++", "-std=c++17")])
+def test_header_compiles_on_its_own(tmp_path, lang, std):
+    """include/sse.h is self-contained for C and C++ callers."""
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc" if lang == "c" else "g++")
+    if cc is None:
+        pytest.skip("no host compiler")
+    src = tmp_path / ("t.c" if lang == "c" else "t.cpp")
+    src.write_text('#include "sse.h"\nint main(void) { return 0; }\n')
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    r = subprocess.run([cc, std, "-Wall", "-Wextra", "-pedantic", "-fsyntax-only",
+                        "-I", os.path.join(root, "include"), str(src)],
+                       capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
