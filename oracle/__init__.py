@@ -20,20 +20,34 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "sse_oracle.c")
 _LIB = os.path.join(_HERE, "libsse_oracle.so")
+_LIB_OMP = os.path.join(_HERE, "libsse_oracle_omp.so")
 
 _dp = ct.POINTER(ct.c_double)
 _ip = ct.POINTER(ct.c_int)
 
 
-def build(force: bool = False) -> str:
-    """Compile the oracle with gcc (plain C99, no FMA contraction)."""
-    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < max(
+def build(force: bool = False, openmp: bool = False) -> str:
+    """Compile the oracle with gcc (plain C99, no FMA contraction).  With
+    ``openmp`` a second library is built from the same source with -fopenmp:
+    its loops over cells, edges and vertices run across threads and give
+    results bit-identical to the serial library (each iteration writes only
+    its own entity's outputs)."""
+    lib = _LIB_OMP if openmp else _LIB
+    if force or not os.path.exists(lib) or os.path.getmtime(lib) < max(
             os.path.getmtime(_SRC), os.path.getmtime(os.path.join(_HERE, "sse_oracle.h"))):
-        tmp = _LIB + f".{os.getpid()}.tmp"
+        tmp = lib + f".{os.getpid()}.tmp"
         subprocess.check_call(["gcc", "-O2", "-std=c99", "-ffp-contract=off", "-shared", "-fPIC",
-                               _SRC, "-o", tmp, "-lm"])
-        os.replace(tmp, _LIB)
-    return _LIB
+                               *(["-fopenmp"] if openmp else []), _SRC, "-o", tmp, "-lm"])
+        os.replace(tmp, lib)
+    return lib
+
+
+def host_threads() -> int:
+    """Host cores this process may run on."""
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
 
 
 class _Mesh(ct.Structure):
@@ -76,11 +90,15 @@ class Oracle:
     """FP64 oracle bound to one mesh, layer count and parameter set."""
 
     def __init__(self, mesh, nLayers: int, params: dict | None = None, rest_frac=None,
-                 max_level=None, rest_thickness=None):
+                 max_level=None, rest_thickness=None, threads: int = 1):
         """max_level [C] / rest_thickness [C, L]: partial bottom cells (both or
-        neither; without them every column has all layers)."""
-        self.lib = ct.CDLL(build())
+        neither; without them every column has all layers).  threads > 1 runs
+        the OpenMP build of the same source on that many host threads."""
+        self.threads = max(1, int(threads))
+        self.lib = ct.CDLL(build(openmp=self.threads > 1))
         self._sig()
+        if self.threads > 1:
+            self.lib.om_set_threads(self.threads)
         self.L = int(nLayers)
         self.C, self.E, self.V = int(mesh.nCells), int(mesh.nEdges), int(mesh.nVertices)
         self._keep = []
@@ -137,6 +155,7 @@ class Oracle:
             getattr(L, n).argtypes = [ct.c_void_p, ct.c_int, _dp, _dp]
         L.om_pv_flux.argtypes = [ct.c_void_p, ct.c_int, _dp, _dp, _dp]
         L.om_sse_step.restype = ct.c_int
+        L.om_set_threads.argtypes = [ct.c_int]
 
     # ---- helpers -------------------------------------------------------
     @staticmethod

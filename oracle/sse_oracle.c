@@ -28,6 +28,26 @@
 #include <stdlib.h>
 #include <string.h>
 
+/* Loops over mesh entities write only the entity's own outputs and read only
+ * inputs, so built with -fopenmp (oracle/__init__.py builds a second library
+ * that way) they run across threads with results bit-identical to the serial
+ * build; without OpenMP the marker expands to nothing. */
+#ifdef _OPENMP
+#include <omp.h>
+#define OMP_FOR _Pragma("omp parallel for schedule(static)")
+#else
+#define OMP_FOR
+#endif
+
+/* threads of the OpenMP build (no effect in the serial build) */
+void om_set_threads(int n) {
+#ifdef _OPENMP
+    if (n > 0) omp_set_num_threads(n);
+#else
+    (void)n;
+#endif
+}
+
 #define C1(e) (m->cellsOnEdge[2 * (e)])
 #define C2(e) (m->cellsOnEdge[2 * (e) + 1])
 #define V1(e) (m->verticesOnEdge[2 * (e)])
@@ -56,6 +76,7 @@ static double sfr(const om_mesh *m, int i, int k) {
 /* div_i(F) = (1/A_i) sum_{e in EC(i)} n_{e,i} l_e F_e, n_{e,i} = +1 if the edge
  * normal points out of cell i. */
 void om_div(const om_mesh *m, int L, const double *F, double *out) {
+    OMP_FOR
     for (int i = 0; i < m->nCells; i++)
         for (int k = 0; k < L; k++) {
             double s = 0.0;
@@ -70,6 +91,7 @@ void om_div(const om_mesh *m, int L, const double *F, double *out) {
 
 /* grad_e(phi) = (phi_c2 - phi_c1) / d_e */
 void om_grad(const om_mesh *m, int L, const double *phi, double *out) {
+    OMP_FOR
     for (int e = 0; e < m->nEdges; e++)
         for (int k = 0; k < L; k++)
             out[(size_t)e * L + k] =
@@ -79,6 +101,7 @@ void om_grad(const om_mesh *m, int L, const double *phi, double *out) {
 /* curl_v(u) = (1/A_v) sum_{e in EV(v)} t_{e,v} d_e u_e, t_{e,v} = +1 when the
  * edge normal circulates counter-clockwise around v (v = v2 of the edge). */
 void om_curl(const om_mesh *m, int L, const double *u, double *out) {
+    OMP_FOR
     for (int v = 0; v < m->nVertices; v++)
         for (int k = 0; k < L; k++) {
             double s = 0.0;
@@ -95,6 +118,7 @@ void om_curl(const om_mesh *m, int L, const double *u, double *out) {
 /* tangential velocity u^t_e = (1/d_e) sum_{e'} w_{e,e'} l_{e'} u_{e'} along
  * t_e = k x n_e */
 void om_tangential(const om_mesh *m, int L, const double *u, double *out) {
+    OMP_FOR
     for (int e = 0; e < m->nEdges; e++)
         for (int k = 0; k < L; k++) {
             double s = 0.0;
@@ -109,6 +133,7 @@ void om_tangential(const om_mesh *m, int L, const double *u, double *out) {
 
 /* K_i = (1/A_i) sum_{e in EC(i)} (l_e d_e / 4) u_e^2 */
 void om_kinetic_energy(const om_mesh *m, int L, const double *u, double *out) {
+    OMP_FOR
     for (int i = 0; i < m->nCells; i++)
         for (int k = 0; k < L; k++) {
             double s = 0.0;
@@ -127,6 +152,7 @@ void om_laplacian(const om_mesh *m, int L, const double *u, double *out) {
     double *delta = vec((size_t)m->nCells * L), *omega = vec((size_t)m->nVertices * L);
     om_div(m, L, u, delta);
     om_curl(m, L, u, omega);
+    OMP_FOR
     for (int e = 0; e < m->nEdges; e++)
         for (int k = 0; k < L; k++)
             out[(size_t)e * L + k] =
@@ -144,6 +170,7 @@ void om_biharmonic(const om_mesh *m, int L, const double *u, double *out) {
     om_laplacian(m, L, u, l1);
     /* del^2 u lives on the edge layers that exist (partial bottom cells) */
     if (L == m->nLayers)
+        OMP_FOR
         for (int e = 0; e < m->nEdges; e++)
             for (int k = ke(m, e); k < L; k++) l1[(size_t)e * L + k] = 0.0;
     om_laplacian(m, L, l1, out);
@@ -153,6 +180,7 @@ void om_biharmonic(const om_mesh *m, int L, const double *u, double *out) {
 /* Coriolis tendency of a velocity x: normal component of -f k x x, in the
  * energy-neutral TRiSK form C_f(x)_e = (1/d_e) sum_{e'} w l_{e'} x_{e'} (f_e+f_{e'})/2 */
 void om_coriolis(const om_mesh *m, int L, const double *x, double *out) {
+    OMP_FOR
     for (int e = 0; e < m->nEdges; e++)
         for (int k = 0; k < L; k++) {
             double s = 0.0;
@@ -168,6 +196,7 @@ void om_coriolis(const om_mesh *m, int L, const double *x, double *out) {
 /* centred edge thickness h_e = (h_c1 + h_c2)/2, 0 in layers where the edge is
  * not active (partial bottom cells) */
 void om_edge_thickness(const om_mesh *m, int L, const double *h, double *out) {
+    OMP_FOR
     for (int e = 0; e < m->nEdges; e++) {
         int K = (L == m->nLayers) ? ke(m, e) : L;
         for (int k = 0; k < L; k++)
@@ -179,6 +208,7 @@ void om_edge_thickness(const om_mesh *m, int L, const double *h, double *out) {
 /* kite-area-weighted vertex thickness over the ocean cells of the vertex that
  * are active in the layer (0 where none is) */
 void om_vertex_thickness(const om_mesh *m, int L, const double *h, double *out) {
+    OMP_FOR
     for (int v = 0; v < m->nVertices; v++)
         for (int k = 0; k < L; k++) {
             double s = 0.0, a = 0.0;
@@ -203,6 +233,7 @@ void om_pv_flux(const om_mesh *m, int L, const double *u, const double *h, doubl
     om_curl(m, L, u, omega);
     om_vertex_thickness(m, L, h, hv);
     om_edge_thickness(m, L, h, he);
+    OMP_FOR
     for (int e = 0; e < m->nEdges; e++)
         for (int k = 0; k < L; k++) {
             int a = V1(e), b = V2(e);
@@ -211,6 +242,7 @@ void om_pv_flux(const om_mesh *m, int L, const double *u, const double *h, doubl
             double qb = hb > 0.0 ? (omega[(size_t)b * L + k] + m->fVertex[b]) / hb : 0.0;
             qe[(size_t)e * L + k] = 0.5 * (qa + qb);
         }
+    OMP_FOR
     for (int e = 0; e < m->nEdges; e++)
         for (int k = 0; k < L; k++) {
             double s = 0.0;
@@ -242,8 +274,10 @@ void om_vertical_velocity(const om_mesh *m, const double *h, const double *v, do
     size_t EL = (size_t)m->nEdges * L, CL = (size_t)m->nCells * L;
     double *he = vec(EL), *F = vec(EL), *dv = vec(CL);
     om_edge_thickness(m, L, h, he);
+    OMP_FOR
     for (size_t x = 0; x < EL; x++) F[x] = he[x] * v[x];
     om_div(m, L, F, dv);
+    OMP_FOR
     for (int i = 0; i < m->nCells; i++) {
         int K = kc(m, i);
         double tot = 0.0;
@@ -263,6 +297,7 @@ void om_vertical_velocity(const om_mesh *m, const double *h, const double *v, do
  * + beta (S - S_ref); tracers are [nT][C][L] with T first, S second. */
 void om_density(const om_mesh *m, const om_params *p, const double *tr, double *rho) {
     size_t CL = (size_t)m->nCells * m->nLayers;
+    OMP_FOR
     for (size_t x = 0; x < CL; x++) {
         double r = p->eos_rho_ref - p->eos_alpha * (tr[x] - p->eos_T_ref);
         if (p->nTracers >= 2) r += p->eos_beta * (tr[CL + x] - p->eos_S_ref);
@@ -276,6 +311,7 @@ void om_density(const om_mesh *m, const om_params *p, const double *tr, double *
 void om_pressure(const om_mesh *m, const om_params *p, const double *h, const double *rho,
                  double *pres, double *zmid) {
     int L = m->nLayers;
+    OMP_FOR
     for (int i = 0; i < m->nCells; i++) {
         const double *hi = h + (size_t)i * L, *ri = rho + (size_t)i * L;
         double acc = 0.0;
@@ -294,6 +330,7 @@ void om_pressure(const om_mesh *m, const om_params *p, const double *h, const do
 /* SSH from the layer thicknesses: zeta = sum_k h_k - H */
 void om_ssh(const om_mesh *m, const double *h, double *zeta) {
     int L = m->nLayers;
+    OMP_FOR
     for (int i = 0; i < m->nCells; i++) {
         double s = 0.0;
         for (int k = 0; k < L; k++) s += h[(size_t)i * L + k];
@@ -310,6 +347,7 @@ void om_split(const om_mesh *m, const double *u, const double *h, double *ubar, 
     int L = m->nLayers;
     double *he = vec((size_t)m->nEdges * L);
     om_edge_thickness(m, L, h, he);
+    OMP_FOR
     for (int e = 0; e < m->nEdges; e++) {
         double num = 0.0, den = 0.0;
         for (int k = 0; k < L; k++) {
@@ -371,6 +409,7 @@ static void baroclinic_rhs(const om_mesh *m, const om_params *p, const double *u
     om_tangential(m, L, u, utan);
     om_grad(m, 1, zeta, gzeta);
 
+    OMP_FOR
     for (int e = 0; e < m->nEdges; e++) {
         int c1 = C1(e), c2 = C2(e), K = ke(m, e);
         const double *ue = u + (size_t)e * L, *hee = he + (size_t)e * L;
@@ -420,7 +459,9 @@ void om_baroclinic_feuler(const om_mesh *m, const om_params *p, const double *u,
     double *rhs = vec(EL), *he = vec(EL);
     om_baroclinic_rhs(m, p, u, ut, zeta, h, tr, rhs);
     om_edge_thickness(m, L, h, he);
+    OMP_FOR
     for (size_t x = 0; x < EL; x++) ut1[x] = ut[x] + dt * rhs[x];
+    OMP_FOR
     for (int e = 0; e < m->nEdges; e++) {
         double num = 0.0, den = 0.0;
         for (int k = 0; k < L; k++) {
@@ -499,7 +540,9 @@ void om_baroclinic_feuler_mixing(const om_mesh *m, const om_params *p, const dou
     double *rhs = vec(EL), *he = vec(EL), *r = vec(EL), *u1 = vec(EL);
     baroclinic_rhs(m, p, u, ut, zeta, h, tr, rhs, 0);
     om_edge_thickness(m, L, h, he);
+    OMP_FOR
     for (size_t x = 0; x < EL; x++) ut1[x] = ut[x] + dt * rhs[x];
+    OMP_FOR
     for (int e = 0; e < m->nEdges; e++) {
         double num = 0.0, den = 0.0;
         for (int k = 0; k < L; k++) {
@@ -513,6 +556,7 @@ void om_baroclinic_feuler_mixing(const om_mesh *m, const om_params *p, const dou
         }
     }
     om_vertical_mixing_solve(m, p, u, h, r, dt, u1);
+    OMP_FOR
     for (int e = 0; e < m->nEdges; e++)
         for (int k = 0; k < L; k++)
             ut1[(size_t)e * L + k] = k < ke(m, e) ? u1[(size_t)e * L + k] - ubar[e] : 0.0;
@@ -540,13 +584,16 @@ void om_barotropic_fe(const om_mesh *m, const om_params *p, const double *ubar,
     double *cf = vec(E), *gz = vec(E), *dv = vec(C);
     om_coriolis(m, 1, ubar, cf);
     om_grad(m, 1, zeta, gz);
+    OMP_FOR
     for (int e = 0; e < E; e++) {
         double Hc1 = zeta[C1(e)] + m->bottomDepth[C1(e)];
         double Hc2 = zeta[C2(e)] + m->bottomDepth[C2(e)];
         flux[e] = ubar[e] * 0.5 * (Hc1 + Hc2);
     }
     om_div(m, 1, flux, dv);
+    OMP_FOR
     for (int e = 0; e < E; e++) ubar1[e] = ubar[e] + tau * (cf[e] - p->g * gz[e] + G[e]);
+    OMP_FOR
     for (int i = 0; i < C; i++) zeta1[i] = zeta[i] - tau * dv[i];
     free(cf);
     free(gz);
@@ -573,21 +620,27 @@ void om_barotropic_substep(const om_mesh *m, const om_params *p, int order,
         /* hat{ubar}^{(j+1)/M}, hat{zeta}^{(j+1)/M} */
         om_barotropic_fe(m, p, ua, za, G, tau, ub, zb, Fb);
         if (order == 2) {
+            OMP_FOR
             for (int e = 0; e < E; e++) {
                 u0[e] = 0.5 * (u0[e] + ub[e]);
                 Fzeta[e] += (Fa[e] + Fb[e]) / (2.0 * M);
             }
+            OMP_FOR
             for (int i = 0; i < C; i++) z0[i] = 0.5 * (z0[i] + zb[i]);
         } else {
             /* hat{ubar}^{(j-1/2)/M} = 3/4 ubar^{(j-1)/M} + 1/4 hat{ubar}^{(j+1)/M} */
+            OMP_FOR
             for (int e = 0; e < E; e++) uh[e] = 0.75 * u0[e] + 0.25 * ub[e];
+            OMP_FOR
             for (int i = 0; i < C; i++) zh[i] = 0.75 * z0[i] + 0.25 * zb[i];
             /* hat{ubar}^{(j+1/2)/M} */
             om_barotropic_fe(m, p, uh, zh, G, tau, uc, zc, Fc);
+            OMP_FOR
             for (int e = 0; e < E; e++) {
                 u0[e] = u0[e] / 3.0 + 2.0 * uc[e] / 3.0;
                 Fzeta[e] += (Fa[e] + Fb[e]) / (6.0 * M) + 2.0 * Fc[e] / (3.0 * M);
             }
+            OMP_FOR
             for (int i = 0; i < C; i++) z0[i] = z0[i] / 3.0 + 2.0 * zc[i] / 3.0;
         }
     }
@@ -610,9 +663,11 @@ void om_thickness_tracer_fe(const om_mesh *m, const om_params *p, const double *
     double *he = vec(EL), *F = vec(EL), *divF = vec(CL), *w = vec((size_t)m->nCells * (L + 1));
     double *Ft = vec(EL), *divFt = vec(CL), *gphi = vec(EL), *Fd = vec(EL), *divFd = vec(CL);
     om_edge_thickness(m, L, h, he);
+    OMP_FOR
     for (size_t x = 0; x < EL; x++) F[x] = he[x] * v[x];
     om_div(m, L, F, divF);
     om_vertical_velocity(m, h, v, w);
+    OMP_FOR
     for (int i = 0; i < m->nCells; i++)
         for (int k = 0; k < L; k++) {
             size_t x = (size_t)i * L + k;
@@ -622,6 +677,7 @@ void om_thickness_tracer_fe(const om_mesh *m, const om_params *p, const double *
     for (int t = 0; t < p->nTracers; t++) {
         const double *phi = tr + (size_t)t * CL;
         double *phi1 = tr1 + (size_t)t * CL;
+        OMP_FOR
         for (int e = 0; e < m->nEdges; e++)
             for (int k = 0; k < L; k++) {
                 size_t x = (size_t)e * L + k;
@@ -630,8 +686,10 @@ void om_thickness_tracer_fe(const om_mesh *m, const om_params *p, const double *
             }
         om_div(m, L, Ft, divFt);
         om_grad(m, L, phi, gphi);
+        OMP_FOR
         for (size_t x = 0; x < EL; x++) Fd[x] = he[x] * p->kappa_h * gphi[x];
         om_div(m, L, Fd, divFd);
+        OMP_FOR
         for (int i = 0; i < m->nCells; i++) {
             const double *ph = phi + (size_t)i * L, *hi = h + (size_t)i * L;
             const double *wi = w + (size_t)i * (L + 1);
@@ -664,6 +722,7 @@ void om_thickness_tracer_fe(const om_mesh *m, const om_params *p, const double *
 
 /* x = a*x1 + b*x2, elementwise */
 static void comb(size_t n, double a, const double *x1, double b, const double *x2, double *x) {
+    OMP_FOR
     for (size_t i = 0; i < n; i++) x[i] = a * x1[i] + b * x2[i];
 }
 
@@ -672,6 +731,7 @@ static void comb(size_t n, double a, const double *x1, double b, const double *x
 static void comb_tracer(size_t CL, int nT, double a, const double *h1, const double *p1, double b,
                         const double *h2, const double *p2, const double *h, double *phi) {
     for (int t = 0; t < nT; t++)
+        OMP_FOR
         for (size_t x = 0; x < CL; x++) {
             size_t y = (size_t)t * CL + x;
             phi[y] = h[x] > 0.0 ? (a * h1[x] * p1[y] + b * h2[x] * p2[y]) / h[x] : 0.0;
@@ -684,6 +744,7 @@ static void layer_flux(const om_mesh *m, const double *u, const double *h, doubl
     int L = m->nLayers;
     double *he = vec((size_t)m->nEdges * L);
     om_edge_thickness(m, L, h, he);
+    OMP_FOR
     for (int e = 0; e < m->nEdges; e++) {
         double f = 0.0, s = 0.0;
         for (int k = 0; k < L; k++) {
@@ -700,6 +761,7 @@ static void layer_flux(const om_mesh *m, const double *u, const double *h, doubl
 static void transport(const om_mesh *m, int recon, const double *u, const double *D,
                       const double *hs, double c, double *v) {
     int L = m->nLayers;
+    OMP_FOR
     for (int e = 0; e < m->nEdges; e++) {
         double uA = recon ? c * D[e] / hs[e] : 0.0;
         int K = ke(m, e);
@@ -737,6 +799,7 @@ int om_sse_step(const om_mesh *m, const om_params *p, int order, double dt, int 
         /* Stage 1 of SSPRK2-SE */
         bcl_stage(m, p, u, ut_n, ubar_n, zeta_n, h, tr, dt, ut1, G0);
         om_barotropic_substep(m, p, 2, ubar_n, zeta_n, G0, dt, M, ubar1, Fz1, NULL);
+        OMP_FOR
         for (int e = 0; e < E; e++)
             for (int k = 0; k < L; k++) u1[(size_t)e * L + k] = k < ke(m, e) ? ubar1[e] + ut1[(size_t)e * L + k] : 0.0;
         layer_flux(m, u, h, Fh1, hs_n);
@@ -750,6 +813,7 @@ int om_sse_step(const om_mesh *m, const om_params *p, int order, double dt, int 
         /* Step 2: corrector with Interp_2(G0, G1), Eq. (force2) */
         comb(E, 0.5, G0, 0.5, G1, Gi);
         om_barotropic_substep(m, p, 2, ubar_n, zeta_n, Gi, dt, M, ubarn1, Fz2, zsub);
+        OMP_FOR
         for (int e = 0; e < E; e++)
             for (int k = 0; k < L; k++)
                 un1[(size_t)e * L + k] = k < ke(m, e) ? ubarn1[e] + utn1[(size_t)e * L + k] : 0.0;
@@ -776,6 +840,7 @@ int om_sse_step(const om_mesh *m, const om_params *p, int order, double dt, int 
         /* Stage 1 of SSPRK3-SE */
         bcl_stage(m, p, u, ut_n, ubar_n, zeta_n, h, tr, dt, ut1, G0);
         om_barotropic_substep(m, p, 3, ubar_n, zeta_n, G0, dt, M, ubar1, Fz1, NULL);
+        OMP_FOR
         for (int e = 0; e < E; e++)
             for (int k = 0; k < L; k++) u1[(size_t)e * L + k] = k < ke(m, e) ? ubar1[e] + ut1[(size_t)e * L + k] : 0.0;
         layer_flux(m, u, h, Fh1, hs_n);
@@ -788,6 +853,7 @@ int om_sse_step(const om_mesh *m, const om_params *p, int order, double dt, int 
         comb(EL, 0.75, ut_n, 0.25, ut2, uth);
         om_barotropic_substep(m, p, 3, ubar1, zeta1, G1, dt, M, ubar2, Fz2, NULL);
         comb(E, 0.75, ubar_n, 0.25, ubar2, ubarh);
+        OMP_FOR
         for (int e = 0; e < E; e++)
             for (int k = 0; k < L; k++) uh[(size_t)e * L + k] = k < ke(m, e) ? ubarh[e] + uth[(size_t)e * L + k] : 0.0;
         layer_flux(m, u1, h1, Fh2, hs_1);
@@ -803,6 +869,7 @@ int om_sse_step(const om_mesh *m, const om_params *p, int order, double dt, int 
         /* Step 2: corrector with Interp_3(G0, G1, G_{1/2}), Eq. (force3) */
         for (int e = 0; e < E; e++) Gi[e] = G0[e] / 6.0 + G1[e] / 6.0 + 2.0 * G2[e] / 3.0;
         om_barotropic_substep(m, p, 3, ubar_n, zeta_n, Gi, dt, M, ubarn1, Fz3, zsub);
+        OMP_FOR
         for (int e = 0; e < E; e++)
             for (int k = 0; k < L; k++)
                 un1[(size_t)e * L + k] = k < ke(m, e) ? ubarn1[e] + utn1[(size_t)e * L + k] : 0.0;
@@ -810,6 +877,7 @@ int om_sse_step(const om_mesh *m, const om_params *p, int order, double dt, int 
         om_edge_thickness(m, L, h, he_n);
         om_edge_thickness(m, L, h1, he_1);
         om_edge_thickness(m, L, hh, he_h);
+        OMP_FOR
         for (int e = 0; e < E; e++) {
             double s = 0.0, hs = 0.0;
             for (int k = 0; k < L; k++) {
@@ -824,6 +892,7 @@ int om_sse_step(const om_mesh *m, const om_params *p, int order, double dt, int 
             hs_h[e] = hs;
             D3[e] = Fz3[e] - Fh3[e];
         }
+        OMP_FOR
         for (int e = 0; e < E; e++)
             for (int k = 0; k < L; k++) {
                 size_t x = (size_t)e * L + k;

@@ -111,6 +111,9 @@ void om_ssh(const om_mesh *m, const double *h, double *zeta);
 int om_sse_step(const om_mesh *m, const om_params *p, int order, double dt, int M,
                 double *u, double *h, double *tr, om_aux *aux);
 
+/* threads used by the OpenMP build of the oracle (ignored by the serial one) */
+void om_set_threads(int n);
+
 #ifdef __cplusplus
 }
 #endif
