@@ -151,16 +151,34 @@ typedef struct {
 /* Copy and validate a mesh; uploads connectivity and derived coefficients
  * (divergence, curl, kinetic-energy, TRiSK and Coriolis coefficients) to the
  * current CUDA device.  *out receives the handle.  BAD_MESH on any index out
- * of range or non-positive geometry; UNSUPPORTED beyond the stated limits. */
+ * of range or non-positive geometry; UNSUPPORTED beyond the stated limits.
+ * The library numbers cells, edges and vertices internally in a locality
+ * order of its own (a recursive bisection of the cell graph); every per-cell
+ * and per-edge array of this API, on the host or on the device, stays in the
+ * caller's numbering. */
 int sse_mesh_create(const sse_mesh_desc *desc, sse_mesh **out);
 void sse_mesh_destroy(sse_mesh *mesh);
 
 /* Allocate a model state on `mesh` with parameters `params`; `cuda_stream`
  * is a cudaStream_t (or NULL).  The state starts at rest with h = 0 and must
- * be filled with sse_state_set (at least U, H and the tracers). */
+ * be filled with sse_state_set (at least U, H and the tracers).  The device
+ * current at the call must be the one the mesh was made on (else
+ * SSE_ERR_INVALID_ARG). */
 int sse_state_create(const sse_mesh *mesh, const sse_params *params, void *cuda_stream,
                      sse_state **out);
 void sse_state_destroy(sse_state *state);
+
+/* sse_state_create followed by sse_state_set of U, H, each tracer and (if not
+ * NULL) the wind stress: the whole initial state of Sec. 3 in one call.
+ *   u           host [nEdges][nLayers] normal velocity (split into ubar and
+ *               utilde by Eq. BBspl at the first step)
+ *   h           host [nCells][nLayers] layer thickness (zeta = sum h - H)
+ *   tracers     host [nTracers][nCells][nLayers] (T, then S)
+ *   windStress  host [nEdges] normal wind stress (N m^-2) or NULL
+ * On any error nothing is left allocated and *out is NULL. */
+int sse_state_init(const sse_mesh *mesh, const sse_params *params, const double *u,
+                   const double *h, const double *tracers, const double *windStress,
+                   void *cuda_stream, sse_state **out);
 
 /* Host -> device copy of one field (FP64 host array, layout per SSE_FIELD_*).
  * Setting U splits it into barotropic and baroclinic parts at the next step
@@ -242,12 +260,22 @@ int sse_profile(sse_state *state, int enable);
  * since the last sse_profile(state, 1). */
 int sse_profile_read(sse_state *state, double *ms, int32_t *launches);
 
+/* Measurement utility (no counterpart in the paper): the fused multiply-add
+ * rate of the current GPU in TFLOP/s (2 flops per FMA), FP64 for
+ * precision = SSE_FP64 and FP32 for SSE_MIXED, timed with CUDA events over
+ * many independent FMA chains on every SM.  It allocates a few bytes, runs
+ * on a private stream and synchronises it; the benchmark uses it as the
+ * denominator of the FP64 form's arithmetic roofline. */
+int sse_probe_fma_rate(int precision, double *tflops);
+
 /* Allocation-free variant of sse_barotropic_substep (FP64), for callers that
- * cannot allocate device memory at the point where they run the sub-cycle
- * (for example while their stream is being captured into a CUDA graph, or
- * inside a memory pool or allocator callback that forbids new allocations).
- * The paper has no counterpart; it computes the same Algorithm 3 (order 2)
- * or Algorithm 4 (order 3) sub-cycle as sse_barotropic_substep.
+ * must not allocate device memory at the point where they run the sub-cycle:
+ * code running inside a device-memory allocator or memory-pool callback, a
+ * host runtime that reserves all of its device memory up front and forbids
+ * later cudaMalloc calls, or a latency-critical loop that cannot accept the
+ * device-wide synchronisation cudaMalloc and cudaFree may imply.  The paper
+ * has no counterpart; it computes the same Algorithm 3 (order 2) or
+ * Algorithm 4 (order 3) sub-cycle as sse_barotropic_substep.
  *   mesh       a mesh made earlier by sse_mesh_create
  *   ubar_in    device [nEdges] barotropic velocity at the start
  *   zeta_in    device [nCells] SSH at the start
@@ -261,11 +289,14 @@ int sse_profile_read(sse_state *state, double *ms, int32_t *launches);
  * (limits: nEdges <= 393216, nCells <= 131072, about 12.6 MB) that every GPU
  * loading the library holds until the process exits; larger meshes return
  * SSE_ERR_UNSUPPORTED.  The first call on a device looks up that array's
- * device address and the launch shape; make it before any stream capture.
- * All calls share the array, so calls that overlap on the GPU (on different
- * streams or devices' shared context) race and must be serialised by the
- * caller.  The call synchronises `cuda_stream` to read the barrier status and
- * returns SSE_ERR_SYNC_TIMEOUT if a grid barrier timed out. */
+ * device address and the launch shape (the first call of each order); make
+ * it before any stream capture.  The device current at the call must be the
+ * one the mesh was made on (else SSE_ERR_INVALID_ARG).  All calls share the
+ * array, so calls that overlap on the GPU (on different streams or devices'
+ * shared context) race and must be serialised by the caller; each call clears
+ * the barrier and error words itself.  The call copies the barrier status to
+ * host memory and synchronises `cuda_stream` before it returns, and returns
+ * SSE_ERR_SYNC_TIMEOUT if a grid barrier timed out. */
 int sse_barotropic_substep_noalloc(const sse_mesh *mesh, int order, double dt, int n_substeps,
                                    double g, const double *ubar_in, const double *zeta_in,
                                    const double *G, double *ubar_out, double *Fzeta_out,

@@ -82,6 +82,7 @@ class Diag(ct.Structure):
 
 
 EXPORTS = ["sse_mesh_create", "sse_mesh_destroy", "sse_state_create", "sse_state_destroy",
+           "sse_state_init", "sse_probe_fma_rate",
            "sse_state_set", "sse_state_get", "sse_step", "sse_baroclinic_feuler",
            "sse_barotropic_substep", "sse_diagnostics", "sse_kernels_per_step", "sse_profile",
            "sse_profile_read", "sse_barotropic_substep_noalloc", "sse_state_footprint",
@@ -113,6 +114,10 @@ def load(path: str = LIB_PATH):
                                      ct.POINTER(ct.c_void_p)]
     lib.sse_state_destroy.argtypes = [ct.c_void_p]
     lib.sse_state_destroy.restype = None
+    lib.sse_probe_fma_rate.argtypes = [ct.c_int, ct.POINTER(ct.c_double)]
+    lib.sse_state_init.argtypes = [ct.c_void_p, ct.POINTER(Params), ct.c_void_p, ct.c_void_p,
+                                   ct.c_void_p, ct.c_void_p, ct.c_void_p,
+                                   ct.POINTER(ct.c_void_p)]
     lib.sse_state_set.argtypes = [ct.c_void_p, ct.c_int, ct.c_void_p]
     lib.sse_state_get.argtypes = [ct.c_void_p, ct.c_int, ct.c_void_p]
     lib.sse_step.argtypes = [ct.c_void_p, ct.c_int, ct.c_double, ct.c_int, ct.c_int]
@@ -227,6 +232,14 @@ def barotropic_substep_noalloc(mesh: Mesh, order: int, dt: float, M: int, g: flo
            "sse_barotropic_substep_noalloc")
 
 
+def fma_rate(precision="fp64") -> float:
+    """sse_probe_fma_rate: the measured FMA rate of the current GPU (TFLOP/s)."""
+    x = ct.c_double()
+    prec = {"fp64": FP64, "mixed": MIXED}[precision]
+    _check(load().sse_probe_fma_rate(prec, ct.byref(x)), "sse_probe_fma_rate")
+    return x.value
+
+
 def make_params(params: dict, precision="fp64") -> Params:
     q = dict(params)
     recon = q.get("recon", "consistent")
@@ -258,6 +271,27 @@ class State:
         ws = params.get("windStress")
         if ws is not None:
             self.set("wind", ws)
+
+    @classmethod
+    def init(cls, mesh: Mesh, params: dict, precision, u, h, tr, stream=None):
+        """sse_state_init: a state made and filled (u, h, tracers, wind) in one call."""
+        self = cls.__new__(cls)
+        self.lib = load()
+        self.mesh = mesh
+        self.params = make_params(params, precision)
+        self.nT = self.params.nTracers
+        u = np.ascontiguousarray(u, dtype=np.float64)
+        h = np.ascontiguousarray(h, dtype=np.float64)
+        tr = np.ascontiguousarray(tr, dtype=np.float64)
+        ws = params.get("windStress")
+        ws = None if ws is None else np.ascontiguousarray(ws, dtype=np.float64)
+        hd = ct.c_void_p()
+        _check(self.lib.sse_state_init(mesh.handle, ct.byref(self.params), u.ctypes.data,
+                                       h.ctypes.data, tr.ctypes.data,
+                                       None if ws is None else ws.ctypes.data,
+                                       ct.c_void_p(stream or 0), ct.byref(hd)), "sse_state_init")
+        self.handle = hd
+        return self
 
     def _shape(self, field):
         E, C, L = self.mesh.nEdges, self.mesh.nCells, self.mesh.L

@@ -88,6 +88,8 @@ struct sse_mesh {
     // every state uploads its own copy)
     std::mutex plan_mu;
     std::map<int, std::shared_ptr<const TilePlan>> plans;
+    // fused baroclinic plans already built, by cells per patch (null: no fit)
+    std::map<int, std::shared_ptr<const BclPlan>> bcl_plans;
     std::map<int, int> tuned;   // autotuned patch size by (precision, objective)
 };
 
@@ -172,6 +174,77 @@ extern "C" int sse_mesh_create(const sse_mesh_desc *d, sse_mesh **out) {
             if (!(fabs(s - d->bottomDepth[i]) <= 1e-10 * d->bottomDepth[i])) return SSE_ERR_BAD_MESH;
         }
 
+    // ---- internal numbering of cells and edges.  Cells follow the depth-first
+    // order of a recursive bisection of the cell graph (any run of consecutive
+    // cells is a compact region), edges the order of their lower-numbered
+    // cell, vertices (below) the order of their lowest cell: a block of
+    // consecutive columns then gathers its neighbours from a few cache lines
+    // whatever the caller's numbering.  Every per-cell and per-edge field
+    // crosses the API in the caller's numbering (the set/get kernels permute);
+    // everything below works on the renumbered copy of the description.
+    std::vector<int> cold, cnew(C), eold(E), enew(E);
+    {
+        std::vector<int> a(E), b(E);
+        for (int e = 0; e < E; e++) { a[e] = d->cellsOnEdge[2 * e]; b[e] = d->cellsOnEdge[2 * e + 1]; }
+        cold = cell_locality_order(C, a, b, 8);
+        for (int i = 0; i < C; i++) cnew[cold[i]] = i;
+        std::vector<long long> key(E);
+        for (int e = 0; e < E; e++) {
+            const long long x = cnew[a[e]], y = cnew[b[e]];
+            key[e] = (std::min(x, y) * C + std::max(x, y)) * (long long)E + e;
+        }
+        std::iota(eold.begin(), eold.end(), 0);
+        std::sort(eold.begin(), eold.end(), [&](int p, int q) { return key[p] < key[q]; });
+        for (int e = 0; e < E; e++) enew[eold[e]] = e;
+    }
+    std::vector<int32_t> r_coe(2 * E), r_voe(2 * E), r_neoc(C), r_eoc((size_t)C * mE, 0);
+    std::vector<int32_t> r_cov(3 * V), r_eov(3 * V), r_neoe(E), r_eoe((size_t)E * mE2, 0);
+    std::vector<double> r_woe((size_t)E * mE2, 0.0), r_dc(E), r_dv(E), r_area(C), r_fE(E), r_H(C);
+    std::vector<int32_t> r_mlc;
+    std::vector<double> r_rest;
+    for (int e = 0; e < E; e++) {
+        const int o = eold[e];
+        for (int s = 0; s < 2; s++) {
+            r_coe[2 * e + s] = cnew[d->cellsOnEdge[2 * o + s]];
+            r_voe[2 * e + s] = d->verticesOnEdge[2 * o + s];
+        }
+        r_neoe[e] = d->nEdgesOnEdge[o];
+        for (int j = 0; j < r_neoe[e]; j++) {
+            r_eoe[(size_t)e * mE2 + j] = enew[d->edgesOnEdge[(size_t)o * mE2 + j]];
+            r_woe[(size_t)e * mE2 + j] = d->weightsOnEdge[(size_t)o * mE2 + j];
+        }
+        r_dc[e] = d->dcEdge[o]; r_dv[e] = d->dvEdge[o]; r_fE[e] = d->fEdge[o];
+    }
+    for (int i = 0; i < C; i++) {
+        const int o = cold[i];
+        r_neoc[i] = d->nEdgesOnCell[o];
+        for (int j = 0; j < r_neoc[i]; j++)
+            r_eoc[(size_t)i * mE + j] = enew[d->edgesOnCell[(size_t)o * mE + j]];
+        r_area[i] = d->areaCell[o]; r_H[i] = d->bottomDepth[o];
+    }
+    for (int v = 0; v < 3 * V; v++) {
+        r_cov[v] = d->cellsOnVertex[v] >= 0 ? cnew[d->cellsOnVertex[v]] : -1;
+        r_eov[v] = d->edgesOnVertex[v] >= 0 ? enew[d->edgesOnVertex[v]] : -1;
+    }
+    if (partial) {
+        r_mlc.resize(C);
+        r_rest.resize((size_t)C * L);
+        for (int i = 0; i < C; i++) {
+            r_mlc[i] = d->maxLevelCell[cold[i]];
+            for (int k = 0; k < L; k++)
+                r_rest[(size_t)i * L + k] = d->restThickness[(size_t)cold[i] * L + k];
+        }
+    }
+    sse_mesh_desc rd = *d;
+    rd.cellsOnEdge = r_coe.data(); rd.verticesOnEdge = r_voe.data();
+    rd.nEdgesOnCell = r_neoc.data(); rd.edgesOnCell = r_eoc.data();
+    rd.cellsOnVertex = r_cov.data(); rd.edgesOnVertex = r_eov.data();
+    rd.nEdgesOnEdge = r_neoe.data(); rd.edgesOnEdge = r_eoe.data();
+    rd.weightsOnEdge = r_woe.data(); rd.dcEdge = r_dc.data(); rd.dvEdge = r_dv.data();
+    rd.areaCell = r_area.data(); rd.fEdge = r_fE.data(); rd.bottomDepth = r_H.data();
+    if (partial) { rd.maxLevelCell = r_mlc.data(); rd.restThickness = r_rest.data(); }
+    d = &rd;
+
     // ---- derived, padded, layer-major arrays
     const int Cp = pad(C), Ep = pad(E), Vp = pad(V);
     std::vector<int2> coe(Ep, make_int2(0, 0)), voe(Ep, make_int2(0, 0));
@@ -255,24 +328,48 @@ extern "C" int sse_mesh_create(const sse_mesh_desc *d, sse_mesh **out) {
     if (!m) return SSE_ERR_OOM;
     {
         HostMesh &hm = m->host;
-        hm.C = C; hm.E = E; hm.maxE = mE; hm.maxE2 = mE2;
-        hm.c1.resize(E); hm.c2.resize(E); hm.neoe.resize(E); hm.invdc.resize(E);
+        hm.C = C; hm.E = E; hm.V = V; hm.maxE = mE; hm.maxE2 = mE2;
+        hm.c1.resize(E); hm.c2.resize(E); hm.v1.resize(E); hm.v2.resize(E);
+        hm.neoe.resize(E); hm.invdc.resize(E); hm.invdv.resize(E);
         hm.eoe.assign((size_t)E * mE2, 0); hm.cfc.assign((size_t)E * mE2, 0.0);
+        hm.wl.assign((size_t)E * mE2, 0.0);
         for (int e = 0; e < E; e++) {
             hm.c1[e] = coe[e].x; hm.c2[e] = coe[e].y; hm.neoe[e] = neoe[e];
-            hm.invdc[e] = invdc[e];
+            hm.v1[e] = voe[e].x; hm.v2[e] = voe[e].y;
+            hm.invdc[e] = invdc[e]; hm.invdv[e] = invdv[e];
             for (int j = 0; j < neoe[e]; j++) {
                 hm.eoe[(size_t)e * mE2 + j] = eoe[(size_t)j * Ep + e];
                 hm.cfc[(size_t)e * mE2 + j] = cfc[(size_t)j * Ep + e];
+                hm.wl[(size_t)e * mE2 + j] = wl[(size_t)j * Ep + e];
             }
         }
         hm.neoc.resize(C); hm.eoc.assign((size_t)C * mE, 0); hm.divc.assign((size_t)C * mE, 0.0);
+        hm.kec.assign((size_t)C * mE, 0.0);
         hm.H.resize(C);
         for (int i = 0; i < C; i++) {
             hm.neoc[i] = neoc[i]; hm.H[i] = H[i];
             for (int j = 0; j < neoc[i]; j++) {
                 hm.eoc[(size_t)i * mE + j] = eoc[(size_t)j * Cp + i];
                 hm.divc[(size_t)i * mE + j] = divc[(size_t)j * Cp + i];
+                hm.kec[(size_t)i * mE + j] = kec[(size_t)j * Cp + i];
+            }
+        }
+        // vertices in the internal numbering; absent edges and cells -1
+        hm.eov.assign(3 * (size_t)V, -1); hm.cov.assign(3 * (size_t)V, -1);
+        hm.curlc.assign(3 * (size_t)V, 0.0); hm.kw.assign(3 * (size_t)V, 0.0);
+        hm.fV.resize(V);
+        for (int nv = 0; nv < V; nv++) {
+            const int v = vold[nv];
+            hm.fV[nv] = fV[nv];
+            for (int j = 0; j < 3; j++) {
+                if (d->edgesOnVertex[3 * v + j] >= 0) {
+                    hm.eov[3 * (size_t)nv + j] = eov[(size_t)j * Vp + nv];
+                    hm.curlc[3 * (size_t)nv + j] = curlc[(size_t)j * Vp + nv];
+                }
+                if (d->cellsOnVertex[3 * v + j] >= 0) {
+                    hm.cov[3 * (size_t)nv + j] = cov[(size_t)j * Vp + nv];
+                    hm.kw[3 * (size_t)nv + j] = kw[(size_t)j * Vp + nv];
+                }
             }
         }
     }
@@ -295,6 +392,11 @@ extern "C" int sse_mesh_create(const sse_mesh_desc *d, sse_mesh **out) {
     dm.f.cfc = A.upload(tof(cfc)); dm.f.curlc = A.upload(tof(curlc)); dm.f.kw = A.upload(tof(kw));
     dm.f.invdc = A.upload(tof(invdc)); dm.f.invdv = A.upload(tof(invdv));
     dm.f.fV = A.upload(tof(fV));
+    // caller index -> internal index (set/get) and internal -> caller
+    cnew.resize(Cp, 0); enew.resize(Ep, 0);
+    cold.resize(Cp, 0); eold.resize(Ep, 0);
+    dm.cperm = A.upload(cnew); dm.eperm = A.upload(enew);
+    dm.cinv = A.upload(cold); dm.einv = A.upload(eold);
     dm.partial = partial ? 1 : 0;
     dm.kc = nullptr; dm.ke = nullptr; dm.sfc = nullptr; dm.sfc_f = nullptr;
     if (partial) {
@@ -320,6 +422,7 @@ extern "C" int sse_mesh_create(const sse_mesh_desc *d, sse_mesh **out) {
 extern "C" void sse_mesh_destroy(sse_mesh *m) { delete m; }
 
 const sse::DMesh *sse_internal_dmesh(const sse_mesh *m) { return &m->dm; }
+int sse_internal_device(const sse_mesh *m) { return m->device; }
 
 // ---------------------------------------------------------------------------
 // Device address of page-locked host memory (cudaHostAlloc, cudaHostRegister)
@@ -357,6 +460,7 @@ struct EngineBase {
     virtual int patch_threads() const = 0; // threads per patch of the tiled sub-cycle
     unsigned int inject_stall = 0;         // sse_state_inject(SSE_INJECT_BARRIER_STALL)
     virtual bool has_del4() const = 0;     // biharmonic viscosity on
+    virtual bool fused_bcl() const = 0;    // the fused baroclinic stage is used
     virtual int diagnostics(sse_diag *out) = 0;
     long long steps = 0;
 
@@ -457,6 +561,9 @@ struct Engine : EngineBase {
     int btr_blocks = 1;
     bool tiled = false;
     DTiles<R> tiles{};
+    bool fused = false;   // the baroclinic stage as k_colflux + k_bcl_fused
+    DBcl<R> bcl{};
+    R *Fc = nullptr;      // [Ep] column transport of the stage (k_colflux)
 
     // Plan the tiled sub-cycle: patches of about patch_cells owned cells, halo
     // of 3 rings (one SSPRK3 sub-step per exchange).  The default (0) is one
@@ -561,6 +668,69 @@ struct Engine : EngineBase {
             return upload_tiles(plan, nthreads, own, smem);
         }
         return SSE_OK;  // no plan fits: the global-memory sub-cycle is used
+    }
+
+    // Plan the fused baroclinic stage: patches of Pc consecutive cells of the
+    // internal numbering, Pc the largest of a few sizes whose patches fit the
+    // kernel's limits and whose shared memory fits a CTA.  Meshes with partial
+    // bottom cells, Algorithm 2 or biharmonic viscosity keep the unfused
+    // kernels, and so does any mesh no plan fits.
+    int plan_bcl(const sse_mesh *mesh, int dev) {
+        const char *env = getenv("SSE_BCL_KERNEL");
+        if (env && strcmp(env, "unfused") == 0) return SSE_OK;
+        if (m.partial || vmix || p.nu_4 > 0.0) return SSE_OK;
+        int smem_block = 0;
+        CK(cudaDeviceGetAttribute(&smem_block, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+        for (int Pc : {160, 128, 96, 64, 48, 32}) {
+            std::shared_ptr<const BclPlan> cached;
+            {
+                sse_mesh *mm = const_cast<sse_mesh *>(mesh);
+                std::lock_guard<std::mutex> lk(mm->plan_mu);
+                auto it = mm->bcl_plans.find(Pc);
+                if (it != mm->bcl_plans.end()) {
+                    cached = it->second;
+                } else {
+                    auto fresh = std::make_shared<BclPlan>();
+                    if (!build_bcl_plan(mesh->host, Pc, bcl_max_edges_per_patch(),
+                                        bcl_max_cells_per_patch(), *fresh))
+                        fresh.reset();
+                    mm->bcl_plans[Pc] = fresh;
+                    cached = fresh;
+                }
+            }
+            if (!cached) continue;
+            const size_t smem = bcl_smem_bytes<R>(*cached);
+            if (smem + 1024 > (size_t)smem_block) continue;
+            CK(cudaFuncSetAttribute(bcl_fused_kernel_ptr<R>(),
+                                    cudaFuncAttributeMaxDynamicSharedMemorySize, smem_block));
+            return upload_bcl(*cached, smem);
+        }
+        return SSE_OK;
+    }
+
+    int upload_bcl(const BclPlan &pl, size_t smem) {
+        auto toR = [](const std::vector<double> &x) { return std::vector<R>(x.begin(), x.end()); };
+        DBcl<R> &t = bcl;
+        t.P = pl.P; t.maxE0 = pl.maxE0; t.maxE1 = pl.maxE1; t.maxE2 = pl.maxE2; t.maxC1 = pl.maxC1;
+        t.maxC2 = pl.maxC2; t.maxV = pl.maxV; t.smem = smem;
+        t.cnt = A.upload(pl.cnt);
+        t.off_e0 = A.upload(pl.off_e0); t.off_e1 = A.upload(pl.off_e1); t.off_e2 = A.upload(pl.off_e2);
+        t.off_c1 = A.upload(pl.off_c1); t.off_c2 = A.upload(pl.off_c2); t.off_v = A.upload(pl.off_v);
+        t.egid = A.upload(pl.egid); t.cgid = A.upload(pl.cgid);
+        t.e0_eoe = A.upload(pl.e0_eoe); t.e0_wl = A.upload(toR(pl.e0_wl));
+        t.e0_cfc = A.upload(toR(pl.e0_cfc)); t.e0_c12 = A.upload(pl.e0_c12);
+        t.e0_v12 = A.upload(pl.e0_v12); t.e0_invdc = A.upload(toR(pl.e0_invdc));
+        t.e0_invdv = A.upload(toR(pl.e0_invdv));
+        t.e1_c12 = A.upload(pl.e1_c12); t.e1_v12 = A.upload(pl.e1_v12);
+        t.c1_e = A.upload(pl.c1_e); t.c1_o = A.upload(pl.c1_o);
+        t.c1_divc = A.upload(toR(pl.c1_divc)); t.c1_kec = A.upload(toR(pl.c1_kec));
+        t.v_e = A.upload(pl.v_e); t.v_c = A.upload(pl.v_c);
+        t.v_curl = A.upload(toR(pl.v_curl)); t.v_kw = A.upload(toR(pl.v_kw));
+        t.v_f = A.upload(toR(pl.v_f));
+        Fc = A.alloc<R>(m.Ep);
+        if (A.failed) return SSE_ERR_OOM;
+        fused = true;
+        return SSE_OK;
     }
 
     int upload_tiles(const TilePlan &plan, int nthreads, int own, size_t smem) {
@@ -697,6 +867,8 @@ struct Engine : EngineBase {
             return SSE_ERR_UNSUPPORTED;
         int rc = plan_tiles(mesh, dev, nsm);
         if (rc) return rc;
+        rc = plan_bcl(mesh, dev);
+        if (rc) return rc;
         CK(cudaStreamSynchronize(s));
         return SSE_OK;
     }
@@ -750,21 +922,21 @@ struct Engine : EngineBase {
         case SSE_FIELD_U:
         case SSE_FIELD_UTILDE:
             if (!direct) CK(cudaMemcpyAsync(stage, host, sizeof(H) * m.E * L, cudaMemcpyHostToDevice, s));
-            launch_to_device<R>(in, ut_n, m.E, L, m.Ep, s);
+            launch_to_device<R>(in, ut_n, m.E, L, m.Ep, m.eperm, s);
             if (m.partial) launch_mask_layers<R>(ut_n, m.E, L, m.Ep, m.ke, s);
             if (field == SSE_FIELD_U) CK(cudaMemsetAsync(ubar_n, 0, sizeof(R) * m.Ep, s));
             break;
         case SSE_FIELD_UBAR:
         case SSE_FIELD_G:
             if (!direct) CK(cudaMemcpyAsync(stage, host, sizeof(H) * m.E, cudaMemcpyHostToDevice, s));
-            launch_to_device<R>(in, field == SSE_FIELD_UBAR ? ubar_n : G0, m.E, 1, m.Ep, s);
+            launch_to_device<R>(in, field == SSE_FIELD_UBAR ? ubar_n : G0, m.E, 1, m.Ep, m.eperm, s);
             break;
         case SSE_FIELD_H:
             if constexpr (f64) {
                 if (!direct)
                     CK(cudaMemcpyAsync(stage, host, sizeof(double) * m.C * L,
                                        cudaMemcpyHostToDevice, s));
-                launch_to_device<double>(in, h_n, m.C, L, m.Cp, s);
+                launch_to_device<double>(in, h_n, m.C, L, m.Cp, m.cperm, s);
                 if (m.partial) launch_mask_layers<double>(h_n, m.C, L, m.Cp, m.kc, s);
                 if (mixed) launch_h_to_float(h_n, (float *)hR_n, L * m.Cp, s);
                 launch_ssh(m, h_n, zeta_n, s);
@@ -777,14 +949,14 @@ struct Engine : EngineBase {
             const int t = field - SSE_FIELD_TRACER0;
             if (t >= p.nT) return SSE_ERR_INVALID_ARG;
             if (!direct) CK(cudaMemcpyAsync(stage, host, sizeof(H) * m.C * L, cudaMemcpyHostToDevice, s));
-            launch_to_device<R>(in, tr_n + (size_t)t * L * m.Cp, m.C, L, m.Cp, s);
+            launch_to_device<R>(in, tr_n + (size_t)t * L * m.Cp, m.C, L, m.Cp, m.cperm, s);
             if (m.partial) launch_mask_layers<R>(tr_n + (size_t)t * L * m.Cp, m.C, L, m.Cp, m.kc, s);
             break;
         }
         case SSE_FIELD_WIND:
             if constexpr (f64) {
                 CK(cudaMemcpyAsync(wind, host, sizeof(double) * m.E, cudaMemcpyHostToDevice, s));
-                launch_scale(wind, 1.0 / p.rho0, wind_d, wind_f, m.E, s);
+                launch_scale(wind, 1.0 / p.rho0, wind_d, wind_f, m.E, m.eperm, s);
                 p.wind = wind_d;
                 p.wind_f = wind_f;
                 graphs_clear();   // the step's kernel arguments changed
@@ -816,40 +988,40 @@ struct Engine : EngineBase {
             return SSE_ERR_INVALID_ARG;   // FP64 state in both forms
         switch (field) {
         case SSE_FIELD_U:
-            launch_add_bar<R>(ubar_n, ut_n, out, m.E, L, m.Ep, m.partial ? m.ke : nullptr, s);
+            launch_add_bar<R>(ubar_n, ut_n, out, m.E, L, m.Ep, m.partial ? m.ke : nullptr, m.eperm, s);
             n = (size_t)m.E * L;
             break;
         case SSE_FIELD_UTILDE:
-            launch_from_device<R>(ut_n, out, m.E, L, m.Ep, s);
+            launch_from_device<R>(ut_n, out, m.E, L, m.Ep, m.eperm, s);
             n = (size_t)m.E * L;
             break;
         case SSE_FIELD_UBAR:
         case SSE_FIELD_G:
-            launch_from_device<R>(field == SSE_FIELD_UBAR ? ubar_n : G0, out, m.E, 1, m.Ep, s);
+            launch_from_device<R>(field == SSE_FIELD_UBAR ? ubar_n : G0, out, m.E, 1, m.Ep, m.eperm, s);
             n = m.E;
             break;
         case SSE_FIELD_H:
-            if constexpr (f64) launch_from_device<double>(h_n, out, m.C, L, m.Cp, s);
+            if constexpr (f64) launch_from_device<double>(h_n, out, m.C, L, m.Cp, m.cperm, s);
             n = (size_t)m.C * L;
             break;
         case SSE_FIELD_TRACER0:
         case SSE_FIELD_TRACER1: {
             const int t = field - SSE_FIELD_TRACER0;
             if (t >= p.nT) return SSE_ERR_INVALID_ARG;
-            launch_from_device<R>(tr_n + (size_t)t * L * m.Cp, out, m.C, L, m.Cp, s);
+            launch_from_device<R>(tr_n + (size_t)t * L * m.Cp, out, m.C, L, m.Cp, m.cperm, s);
             n = (size_t)m.C * L;
             break;
         }
         case SSE_FIELD_ZETA:
-            if constexpr (f64) CK(cudaMemcpyAsync(out, zeta_n, sizeof(double) * m.C, cudaMemcpyDefault, s));
+            if constexpr (f64) launch_from_device<double>(zeta_n, out, m.C, 1, m.Cp, m.cperm, s);
             n = m.C;
             break;
         case SSE_FIELD_ZETA_SUB:
-            if constexpr (f64) CK(cudaMemcpyAsync(out, zeta_sub, sizeof(double) * m.C, cudaMemcpyDefault, s));
+            if constexpr (f64) launch_from_device<double>(zeta_sub, out, m.C, 1, m.Cp, m.cperm, s);
             n = m.C;
             break;
         case SSE_FIELD_FZETA:
-            if constexpr (f64) CK(cudaMemcpyAsync(out, last_Fz, sizeof(double) * m.E, cudaMemcpyDefault, s));
+            if constexpr (f64) launch_from_device<double>(last_Fz, out, m.E, 1, m.Ep, m.eperm, s);
             n = m.E;
             break;
         case SSE_FIELD_WIND:
@@ -877,6 +1049,20 @@ struct Engine : EngineBase {
     // ---- pieces
     void bcl_stage(R *ubar, R *ut, R *hR, R *tr, const double *zeta, bool split, const R *utn,
                    double a, double b, double dt, R *out, R *G) {
+        if (fused) {
+            // the column pre-pass (and the split at stage 1) counts as the edge
+            // pre-pass class, the fused kernel as the baroclinic-edge class
+            pbeg(SSE_K_EDGE_PRE);
+            launch_colflux<R>(m, ubar, ut, hR, split, Fc, s);
+            pend();
+            BclArgs<R> x{};
+            x.ubar = ubar; x.ut = ut; x.hR = hR; x.tr = tr; x.zeta = zeta; x.Fc = Fc;
+            x.ut_n = utn; x.a = (R)a; x.b = (R)b; x.dt = (R)dt; x.ut_out = out; x.G = G;
+            pbeg(SSE_K_BCL_EDGE);
+            launch_bcl_fused<R>(bcl, m, p, x, s);
+            pend();
+            return;
+        }
         pbeg(SSE_K_CELL_DIAG);
         launch_cell_diag<R>(m, p, ubar, ut, hR, tr, db, s);
         pend();
@@ -1077,6 +1263,7 @@ struct Engine : EngineBase {
     int patches() const override { return tiled ? tiles.P : 0; }
     int patch_threads() const override { return tiled ? tiles.nthreads : 0; }
     bool has_del4() const override { return db.del2 != nullptr; }
+    bool fused_bcl() const override { return fused; }
 
     int btr_substep(int order, double dt, int M) override {
         launch_ssh(m, h_n, zeta_n, s);
@@ -1150,6 +1337,11 @@ static bool tuning_ok(const sse_tuning *t) {
 
 static int make_state(const sse_mesh *mesh, const sse_params *prm, const sse_tuning *tun,
                       void *stream, bool count_only, sse_state **out, size_t *bytes) {
+    // the state's kernels dereference the mesh's device arrays: the device
+    // current now must be the one the mesh was made on
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess) return SSE_ERR_CUDA;
+    if (dev != mesh->device) return SSE_ERR_INVALID_ARG;
     sse_state *st = new (std::nothrow) sse_state();
     if (!st) return SSE_ERR_OOM;
     const int pc = (tun && tun->patch_cells > 0) ? tun->patch_cells : 0;
@@ -1190,6 +1382,28 @@ extern "C" int sse_state_create_ex(const sse_mesh *mesh, const sse_params *prm,
     *out = nullptr;
     if (!params_ok(prm) || !tuning_ok(tuning)) return SSE_ERR_INVALID_ARG;
     return make_state(mesh, prm, tuning, stream, false, out, nullptr);
+}
+
+extern "C" int sse_state_init(const sse_mesh *mesh, const sse_params *prm, const double *u,
+                              const double *h, const double *tracers, const double *windStress,
+                              void *stream, sse_state **out) {
+    if (!mesh || !prm || !u || !h || !tracers || !out) return SSE_ERR_INVALID_ARG;
+    *out = nullptr;
+    sse_state *st = nullptr;
+    int rc = sse_state_create(mesh, prm, stream, &st);
+    if (rc) return rc;
+    const size_t CL = (size_t)mesh->dm.C * mesh->dm.L;
+    rc = sse_state_set(st, SSE_FIELD_U, u);
+    if (!rc) rc = sse_state_set(st, SSE_FIELD_H, h);
+    for (int t = 0; !rc && t < prm->nTracers; t++)
+        rc = sse_state_set(st, SSE_FIELD_TRACER0 + t, tracers + t * CL);
+    if (!rc && windStress) rc = sse_state_set(st, SSE_FIELD_WIND, windStress);
+    if (rc) {
+        sse_state_destroy(st);
+        return rc;
+    }
+    *out = st;
+    return SSE_OK;
 }
 
 extern "C" int sse_state_footprint(const sse_mesh *mesh, const sse_params *prm, size_t *bytes) {
@@ -1382,9 +1596,9 @@ extern "C" int sse_diagnostics(sse_state *st, sse_diag *out) {
 
 extern "C" int sse_kernels_per_step(const sse_state *st, int order) {
     if (!st) return SSE_ERR_INVALID_ARG;
-    // 4 per baroclinic stage (5 with biharmonic viscosity), 1 per sub-cycle,
-    // 2 per thickness stage, 1 forcing combination
-    const int bcl = 4 + (st->eng->has_del4() ? 1 : 0);
+    // 4 per baroclinic stage (5 with biharmonic viscosity; 2 when fused), 1
+    // per sub-cycle, 2 per thickness stage, 1 forcing combination
+    const int bcl = st->eng->fused_bcl() ? 2 : 4 + (st->eng->has_del4() ? 1 : 0);
     return order == 2 ? 2 * bcl + 2 + 2 * 2 + 1 : 3 * bcl + 3 + 3 * 2 + 1;
 }
 

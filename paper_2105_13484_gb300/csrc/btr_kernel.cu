@@ -187,12 +187,13 @@ __global__ void __launch_bounds__(BTR_THREADS) k_btr(DMesh m, BtrArgs<R> a, Barr
         const int x = t0 + s * T;
         u0r[s] = R(0); z0r[s] = R(0); Gr[s] = R(0); Fz[s] = 0.0; Fs[s] = R(0);
         if (s < nit && x < m.E) {
-            u0r[s] = a.ub_start[x];
-            Gr[s] = a.G[x];
+            const int xa = a.einv ? a.einv[x] : x;   // the caller's numbering
+            u0r[s] = a.ub_start[xa];
+            Gr[s] = a.G[xa];
             u0[x] = u0r[s];
         }
         if (s < nit && x < m.C) {
-            z0r[s] = (R)a.z_start[x];
+            z0r[s] = (R)a.z_start[a.cinv ? a.cinv[x] : x];
             z0[x] = z0r[s];
         }
     }
@@ -273,10 +274,11 @@ __global__ void __launch_bounds__(BTR_THREADS) k_btr(DMesh m, BtrArgs<R> a, Barr
     for (int s = 0; s < BTR_NIT; s++) {
         const int x = t0 + s * T;
         if (s < nit && x < m.E) {
-            a.Fz[x] = Fz[s];
-            a.ub_out[x] = a.X ? (R)(a.alpha * (double)a.X[x] + a.beta * (double)u0r[s]) : u0r[s];
+            const int xa = a.einv ? a.einv[x] : x;
+            a.Fz[xa] = Fz[s];
+            a.ub_out[xa] = a.X ? (R)(a.alpha * (double)a.X[xa] + a.beta * (double)u0r[s]) : u0r[s];
         }
-        if (s < nit && x < m.C && a.z_out) a.z_out[x] = (double)z0r[s];
+        if (s < nit && x < m.C && a.z_out) a.z_out[a.cinv ? a.cinv[x] : x] = (double)z0r[s];
     }
 }
 
@@ -685,12 +687,14 @@ template cudaError_t launch_btr<float>(const DMesh &, const BtrArgs<float> &, co
 // ===========================================================================
 // Allocation-free sub-cycle: sse_barotropic_substep_noalloc
 //
-// For callers that cannot allocate device memory when they run the
-// sub-cycle (for example code that executes while a CUDA stream is being
-// captured into a graph, or inside an allocator callback or a memory pool
-// that forbids new allocations): the work buffers live in one file-scope
-// device array that every GPU loading this library holds until the process
-// exits.  The first 256 bytes hold the grid-barrier words and the error word.
+// For callers that must not allocate device memory at the point where they
+// run the sub-cycle: code running inside a device-memory allocator or pool
+// callback, a runtime that reserves all of its device memory up front and
+// forbids later cudaMalloc calls, or a latency-critical loop in which the
+// implicit device synchronisation of cudaMalloc/cudaFree is not acceptable.
+// The work buffers live in one file-scope device array that every GPU
+// loading this library holds until the process exits.  The first 256 bytes
+// hold the grid-barrier words and the error word.
 // ===========================================================================
 namespace sse {
 
@@ -704,7 +708,10 @@ namespace {
 constexpr int kMaxDevices = 64;
 struct NoallocDevice {
     double *scratch = nullptr;  // device address of g_noalloc_scratch on this device
-    int blocks_per_sm = 0, sms = 0;
+    int sms = 0;
+    // co-resident blocks per SM of each kernel variant the entry point may
+    // launch, [order - 2][maxE2 <= BTR_NE2 ? 0 : 1] (0: not yet queried)
+    int blocks_per_sm[2][2] = {{0, 0}, {0, 0}};
 };
 NoallocDevice g_noalloc_dev[kMaxDevices];
 std::mutex g_noalloc_mutex;
@@ -713,6 +720,7 @@ std::mutex g_noalloc_mutex;
 }  // namespace sse
 
 const sse::DMesh *sse_internal_dmesh(const sse_mesh *m);
+int sse_internal_device(const sse_mesh *m);
 
 extern "C" int sse_barotropic_substep_noalloc(const sse_mesh *mesh, int order, double dt,
                                               int n_substeps, double g, const double *ubar_in,
@@ -727,29 +735,38 @@ extern "C" int sse_barotropic_substep_noalloc(const sse_mesh *mesh, int order, d
     if (m.E > NOALLOC_MAX_EDGES || m.C > NOALLOC_MAX_CELLS) return SSE_ERR_UNSUPPORTED;
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return SSE_ERR_CUDA;
+    // the mesh's arrays live on the device that was current at sse_mesh_create
+    if (dev != sse_internal_device(mesh)) return SSE_ERR_INVALID_ARG;
+    // the variant launch_btr picks for this mesh
+    const int vi = m.maxE2 <= BTR_NE2 ? 0 : 1;
     NoallocDevice nd;
+    int blocks_per_sm = 0;
     {
         // once per device, with that device current: the device address of the
-        // array (the host-side symbol is only a stand-in for it)
+        // array (the host-side symbol is only a stand-in for it); once per
+        // kernel variant: its occupancy
         std::lock_guard<std::mutex> lock(g_noalloc_mutex);
         NoallocDevice &d = g_noalloc_dev[dev];
         if (!d.scratch) {
             void *p = nullptr;
-            if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess) return SSE_ERR_CUDA;
-            int occ2 = 0, occ3 = 0, nsm = 0;
-            if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ2, k_btr<double, 2, MAXE2>,
-                                                              BTR_THREADS, 0) != cudaSuccess ||
-                cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ3, k_btr<double, 3, MAXE2>,
-                                                              BTR_THREADS, 0) != cudaSuccess ||
+            int nsm = 0;
+            if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess ||
                 cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
                 return SSE_ERR_CUDA;
-            d.blocks_per_sm = occ2 < occ3 ? occ2 : occ3;
             d.sms = nsm;
             d.scratch = (double *)p;
         }
+        int &occ = d.blocks_per_sm[order - 2][vi];
+        if (occ == 0 && cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+                            &occ, btr_kernel_ptr<double>(order, m.maxE2), BTR_THREADS, 0) !=
+                            cudaSuccess) {
+            occ = 0;
+            return SSE_ERR_CUDA;
+        }
+        blocks_per_sm = occ;
         nd = d;
     }
-    if (nd.blocks_per_sm < 1) return SSE_ERR_UNSUPPORTED;
+    if (blocks_per_sm < 1) return SSE_ERR_UNSUPPORTED;
     cudaStream_t s = (cudaStream_t)cuda_stream;
     double *base = nd.scratch;
     unsigned int *words = (unsigned int *)base;
@@ -757,6 +774,8 @@ extern "C" int sse_barotropic_substep_noalloc(const sse_mesh *mesh, int order, d
     BtrArgs<double> a{};
     a.ub_start = ubar_in; a.z_start = zeta_in; a.G = G; a.X = nullptr; a.alpha = 0.0;
     a.beta = 1.0; a.ub_out = ubar_out; a.Fz = Fzeta_out; a.z_out = zeta_out;
+    // the caller's arrays are in the caller's numbering
+    a.einv = m.einv; a.cinv = m.cinv;
     a.u0 = work; a.ua = work + NOALLOC_MAX_EDGES; a.uh = work + 2 * NOALLOC_MAX_EDGES;
     a.z0 = work + 3 * NOALLOC_MAX_EDGES; a.za = a.z0 + NOALLOC_MAX_CELLS;
     a.zh = a.z0 + 2 * NOALLOC_MAX_CELLS;
@@ -766,7 +785,7 @@ extern "C" int sse_barotropic_substep_noalloc(const sse_mesh *mesh, int order, d
     if (cudaMemsetAsync(base, 0, NOALLOC_HEADER * sizeof(double), s) != cudaSuccess)
         return SSE_ERR_CUDA;
     const int need = ((m.E > m.C ? m.E : m.C) + BTR_THREADS - 1) / BTR_THREADS;
-    int blocks = nd.blocks_per_sm * nd.sms;
+    int blocks = blocks_per_sm * nd.sms;
     if (need < blocks) blocks = need;
     if (blocks < 1) blocks = 1;
     if ((long long)blocks * BTR_THREADS * BTR_NIT < (m.E > m.C ? m.E : m.C))

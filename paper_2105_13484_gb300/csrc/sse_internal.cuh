@@ -39,6 +39,10 @@ struct DMesh {
     const int *eoe;     // [maxE2][Ep]
     const int *eov;     // [3][Vp] (absent -> 0, with zero coefficient)
     const int *cov;     // [3][Vp] (land -> 0, with zero weight)
+    // numbering: the caller's cell / edge index -> the internal one, and back
+    // (padding entries map to 0)
+    const int *cperm, *eperm;   // [Cp], [Ep] caller -> internal
+    const int *cinv, *einv;     // [Cp], [Ep] internal -> caller
     const double *H;    // [Cp] resting depth
     const double *sfrac;  // [L] z-star fractions
     const float *sfrac_f; // [L] the same in FP32
@@ -152,6 +156,45 @@ void launch_bcl_edge(const DMesh &m, const DParams &p, const R *ubar, const R *u
                      double a, double bcoef, double dt, R *ut_out, R *G, R *vmc,
                      cudaStream_t s);
 
+// ---- the fused baroclinic stage (bcl_fused.cu); plan from build_bcl_plan
+template <class R> struct DBcl {
+    int P = 0;
+    int maxE0 = 0, maxE1 = 0, maxE2 = 0, maxC1 = 0, maxC2 = 0, maxV = 0;
+    size_t smem = 0;
+    const int *cnt = nullptr;                 // [P][8]
+    const int *off_e0, *off_e1, *off_e2, *off_c1, *off_c2, *off_v;
+    const int *egid, *cgid;
+    const unsigned short *e0_eoe;             // [sum 10 nE0]
+    const R *e0_wl, *e0_cfc;                  // [sum 10 nE0]
+    const int *e0_c12, *e0_v12;               // [sum nE0]
+    const R *e0_invdc, *e0_invdv;             // [sum nE0]
+    const int *e1_c12, *e1_v12;               // [sum nE1]
+    const unsigned short *c1_e, *c1_o;        // [sum 6 nC1]
+    const R *c1_divc, *c1_kec;                // [sum 6 nC1]
+    const unsigned short *v_e, *v_c;          // [sum 3 nV]
+    const R *v_curl, *v_kw;                   // [sum 3 nV]
+    const R *v_f;                             // [sum nV]
+};
+template <class R> struct BclArgs {
+    const R *ubar, *ut, *hR, *tr;  // stage input (ubar, utilde, thickness, tracers)
+    const double *zeta;            // stage SSH
+    const R *Fc;                   // [Ep] column transport sum_k h_e u_k (k_colflux)
+    const R *ut_n;                 // old level for the convex combination, or null
+    R a, b, dt;                    // out = a ut_n + b (ut1 - dt G)
+    R *ut_out, *G;
+};
+struct BclPlan;
+template <class R> size_t bcl_smem_bytes(const BclPlan &plan);
+int bcl_max_edges_per_patch();
+int bcl_max_cells_per_patch();
+template <class R> const void *bcl_fused_kernel_ptr();
+template <class R>
+void launch_colflux(const DMesh &m, R *ubar, R *ut, const R *hR, bool split, R *Fc,
+                    cudaStream_t s);
+template <class R>
+void launch_bcl_fused(const DBcl<R> &t, const DMesh &m, const DParams &p, const BclArgs<R> &a,
+                      cudaStream_t s);
+
 template <class R> struct BtrArgs {
     const R *ub_start;     // [Ep]
     const double *z_start; // [Cp]
@@ -166,6 +209,10 @@ template <class R> struct BtrArgs {
     double tau, g;
     int M, order;
     unsigned int stall;    // test hook: arrivals every grid barrier waits for beyond the grid (0)
+    // global-memory kernel only: internal -> caller index of the edge and cell
+    // arrays above (ub_start ... z_out) when they are in the caller's
+    // numbering (null: internal numbering)
+    const int *einv, *cinv;
 };
 template <class R>
 cudaError_t launch_btr(const DMesh &m, const BtrArgs<R> &a, const Barrier &bar, int nblocks,
@@ -237,17 +284,21 @@ void launch_thickness(const DMesh &m, const DParams &p, const ThickArgs<R> &a, c
 
 // layout conversion: host-order [n][L] in precision H (FP64 or FP32) <->
 // device layer-major R [L][np]
+// (perm: the caller's index -> the internal one, DMesh::cperm / eperm)
 template <class R, class H>
-void launch_to_device(const H *src, R *dst, int n, int L, int np, cudaStream_t s);
+void launch_to_device(const H *src, R *dst, int n, int L, int np, const int *perm,
+                      cudaStream_t s);
 template <class R, class H>
-void launch_from_device(const R *src, H *dst, int n, int L, int np, cudaStream_t s);
+void launch_from_device(const R *src, H *dst, int n, int L, int np, const int *perm,
+                        cudaStream_t s);
 template <class R, class H>
 void launch_add_bar(const R *ubar, const R *ut, H *dst, int E, int L, int Ep,
-                    const int *kmax, cudaStream_t s);
+                    const int *kmax, const int *perm, cudaStream_t s);
 template <class R>
 void launch_mask_layers(R *x, int n, int L, int np, const int *kmax, cudaStream_t s);
 void launch_h_to_float(const double *h, float *hf, int n, cudaStream_t s);
-void launch_scale(const double *src, double scale, double *dst_d, float *dst_f, int n, cudaStream_t s);
+void launch_scale(const double *src, double scale, double *dst_d, float *dst_f, int n,
+                  const int *perm, cudaStream_t s);
 void launch_ssh(const DMesh &m, const double *h, double *zeta, cudaStream_t s);
 
 template <class R>

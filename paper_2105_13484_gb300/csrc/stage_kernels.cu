@@ -578,31 +578,33 @@ __global__ void __launch_bounds__(128, 6) k_thickness(DMesh m, DParams p, ThickA
 // ---------------------------------------------------------------------------
 // small helpers: layout conversion, SSH
 // ---------------------------------------------------------------------------
-// host order [n][L] in precision H <-> device layer-major [L][np] in precision R
+// host order [n][L] in precision H, the caller's numbering <-> device
+// layer-major [L][np] in precision R, the internal numbering (perm: caller
+// index -> internal index)
 template <class H, class R>
 __global__ void k_to_device(const H *__restrict__ src, R *__restrict__ dst, int n, int L,
-                            int np) {
+                            int np, const int *__restrict__ perm) {
     const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= (long long)n * L) return;
     const int i = (int)(t / L), k = (int)(t % L);
-    dst[(long long)k * np + i] = (R)src[t];
+    dst[(long long)k * np + perm[i]] = (R)src[t];
 }
 template <class R, class H>
 __global__ void k_from_device(const R *__restrict__ src, H *__restrict__ dst, int n, int L,
-                              int np) {
+                              int np, const int *__restrict__ perm) {
     const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= (long long)n * L) return;
     const int i = (int)(t / L), k = (int)(t % L);
-    dst[t] = (H)src[(long long)k * np + i];
+    dst[t] = (H)src[(long long)k * np + perm[i]];
 }
 // u = ubar + utilde, summed in FP64 and rounded once to H
 template <class R, class H>
 __global__ void k_add_bar(const R *__restrict__ ubar, const R *__restrict__ ut,
                           H *__restrict__ dst, int E, int L, int Ep,
-                          const int *__restrict__ kmax) {
+                          const int *__restrict__ kmax, const int *__restrict__ perm) {
     const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= (long long)E * L) return;
-    const int e = (int)(t / L), k = (int)(t % L);
+    const int e = perm[(int)(t / L)], k = (int)(t % L);
     dst[t] = (kmax && k >= kmax[e]) ? H(0)
                                     : (H)((double)ubar[e] + (double)ut[(long long)k * Ep + e]);
 }
@@ -618,12 +620,15 @@ __global__ void k_h_to_float(const double *__restrict__ h, float *__restrict__ h
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t < n) hf[t] = (float)h[t];
 }
+// dd[perm[t]] = scale * src[t] (and its FP32 copy): a caller-ordered 2-D
+// field into the internal numbering
 __global__ void k_scale(const double *__restrict__ src, double scale, double *__restrict__ dd,
-                        float *__restrict__ df, int n) {
+                        float *__restrict__ df, int n, const int *__restrict__ perm) {
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t < n) {
-        dd[t] = src[t] * scale;
-        df[t] = (float)dd[t];
+        const double x = src[t] * scale;
+        dd[perm[t]] = x;
+        df[perm[t]] = (float)x;
     }
 }
 __global__ void k_ssh(DMesh m, const double *__restrict__ h, double *__restrict__ zeta) {
@@ -787,17 +792,20 @@ void launch_thickness(const DMesh &m, const DParams &p, const ThickArgs<R> &a, c
     }
 }
 template <class R, class H>
-void launch_to_device(const H *src, R *dst, int n, int L, int np, cudaStream_t s) {
-    k_to_device<H, R><<<nblk((long long)n * L, 256), 256, 0, s>>>(src, dst, n, L, np);
+void launch_to_device(const H *src, R *dst, int n, int L, int np, const int *perm,
+                      cudaStream_t s) {
+    k_to_device<H, R><<<nblk((long long)n * L, 256), 256, 0, s>>>(src, dst, n, L, np, perm);
 }
 template <class R, class H>
-void launch_from_device(const R *src, H *dst, int n, int L, int np, cudaStream_t s) {
-    k_from_device<R, H><<<nblk((long long)n * L, 256), 256, 0, s>>>(src, dst, n, L, np);
+void launch_from_device(const R *src, H *dst, int n, int L, int np, const int *perm,
+                        cudaStream_t s) {
+    k_from_device<R, H><<<nblk((long long)n * L, 256), 256, 0, s>>>(src, dst, n, L, np, perm);
 }
 template <class R, class H>
 void launch_add_bar(const R *ubar, const R *ut, H *dst, int E, int L, int Ep,
-                    const int *kmax, cudaStream_t s) {
-    k_add_bar<R, H><<<nblk((long long)E * L, 256), 256, 0, s>>>(ubar, ut, dst, E, L, Ep, kmax);
+                    const int *kmax, const int *perm, cudaStream_t s) {
+    k_add_bar<R, H><<<nblk((long long)E * L, 256), 256, 0, s>>>(ubar, ut, dst, E, L, Ep, kmax,
+                                                                perm);
 }
 template <class R>
 void launch_mask_layers(R *x, int n, int L, int np, const int *kmax, cudaStream_t s) {
@@ -807,8 +815,8 @@ void launch_h_to_float(const double *h, float *hf, int n, cudaStream_t s) {
     k_h_to_float<<<nblk(n, 256), 256, 0, s>>>(h, hf, n);
 }
 void launch_scale(const double *src, double scale, double *dst_d, float *dst_f, int n,
-                  cudaStream_t s) {
-    k_scale<<<nblk(n, 256), 256, 0, s>>>(src, scale, dst_d, dst_f, n);
+                  const int *perm, cudaStream_t s) {
+    k_scale<<<nblk(n, 256), 256, 0, s>>>(src, scale, dst_d, dst_f, n, perm);
 }
 void launch_ssh(const DMesh &m, const double *h, double *zeta, cudaStream_t s) {
     k_ssh<<<nblk(m.C, 128), 128, 0, s>>>(m, h, zeta);
@@ -834,15 +842,18 @@ void launch_diag(const DMesh &m, const R *ubar, const R *ut, const double *h, co
     template void launch_transport<R>(const DMesh &, const TransportArgs<R> &, cudaStream_t);    \
     template void launch_thickness<R>(const DMesh &, const DParams &, const ThickArgs<R> &,      \
                                       cudaStream_t);                                             \
-    template void launch_to_device<R, double>(const double *, R *, int, int, int, cudaStream_t); \
-    template void launch_to_device<R, float>(const float *, R *, int, int, int, cudaStream_t);   \
-    template void launch_from_device<R, double>(const R *, double *, int, int, int,              \
+    template void launch_to_device<R, double>(const double *, R *, int, int, int, const int *,   \
+                                              cudaStream_t);                                     \
+    template void launch_to_device<R, float>(const float *, R *, int, int, int, const int *,     \
+                                             cudaStream_t);                                      \
+    template void launch_from_device<R, double>(const R *, double *, int, int, int, const int *, \
                                                 cudaStream_t);                                   \
-    template void launch_from_device<R, float>(const R *, float *, int, int, int, cudaStream_t); \
+    template void launch_from_device<R, float>(const R *, float *, int, int, int, const int *,   \
+                                               cudaStream_t);                                    \
     template void launch_add_bar<R, double>(const R *, const R *, double *, int, int, int,       \
-                                            const int *, cudaStream_t);                          \
+                                            const int *, const int *, cudaStream_t);             \
     template void launch_add_bar<R, float>(const R *, const R *, float *, int, int, int,         \
-                                           const int *, cudaStream_t);                           \
+                                           const int *, const int *, cudaStream_t);              \
     template void launch_mask_layers<R>(R *, int, int, int, const int *, cudaStream_t);          \
     template void launch_diag<R>(const DMesh &, const R *, const R *, const double *, const R *, \
                                  int, const double *, double *, int, double *, cudaStream_t);

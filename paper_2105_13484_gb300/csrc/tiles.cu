@@ -225,6 +225,197 @@ bool build_tile_plan(const HostMesh &hm, int P, int K, TilePlan &plan) {
     return true;
 }
 
+std::vector<int> cell_locality_order(int C, const std::vector<int> &c1,
+                                     const std::vector<int> &c2, int leaf) {
+    std::vector<std::vector<int>> adj(C);
+    for (size_t e = 0; e < c1.size(); e++) {
+        adj[c1[e]].push_back(c2[e]);
+        adj[c2[e]].push_back(c1[e]);
+    }
+    std::vector<int> owner(C, -1), mask(C, 0), da(C), db(C), all(C);
+    std::iota(all.begin(), all.end(), 0);
+    int next = 0, tagctr = 0;
+    const int parts = std::max(1, (C + std::max(leaf, 1) - 1) / std::max(leaf, 1));
+    // part ids are handed out depth first: the left half of every bisection
+    // gets the lower ids
+    bisect(adj, all, parts, owner, next, mask, tagctr, da, db);
+    std::vector<int> order(C);
+    std::iota(order.begin(), order.end(), 0);
+    std::stable_sort(order.begin(), order.end(),
+                     [&](int a, int b) { return owner[a] < owner[b]; });
+    return order;
+}
+
+bool build_bcl_plan(const HostMesh &hm, int Pc, int max_e0, int max_c1, BclPlan &plan) {
+    const int C = hm.C, E = hm.E, V = hm.V;
+    if (Pc < 1) return false;
+    for (int c = 0; c < C; c++) if (hm.neoc[c] > BCL_NCEP) return false;
+    for (int e = 0; e < E; e++) if (hm.neoe[e] > BCL_NE2P) return false;
+    plan = BclPlan();
+    plan.Pc = Pc;
+    plan.P = (C + Pc - 1) / Pc;
+    const int P = plan.P;
+    // owned edges: edges are numbered by their lower cell, so each patch's run
+    // is contiguous
+    std::vector<int> e_first(P + 1, E);
+    for (int e = E - 1; e >= 0; e--) e_first[std::min(hm.c1[e], hm.c2[e]) / Pc] = e;
+    for (int p = P - 1; p >= 0; p--) e_first[p] = std::min(e_first[p], e_first[p + 1]);
+    for (int e = 1; e < E; e++)
+        if (std::min(hm.c1[e], hm.c2[e]) < std::min(hm.c1[e - 1], hm.c2[e - 1])) return false;
+    std::vector<int> le(E, -1), lc(C, -1), lv(V, -1);
+    for (auto *o : {&plan.off_e0, &plan.off_e1, &plan.off_e2, &plan.off_c1, &plan.off_c2,
+                    &plan.off_v})
+        o->push_back(0);
+    for (int p = 0; p < P; p++) {
+        std::vector<int> Ed, Cd, Vd;   // local -> internal
+        auto add_e = [&](int e) { if (e >= 0 && le[e] < 0) { le[e] = (int)Ed.size(); Ed.push_back(e); } };
+        auto add_c = [&](int c) { if (c >= 0 && lc[c] < 0) { lc[c] = (int)Cd.size(); Cd.push_back(c); } };
+        auto add_v = [&](int v) { if (v >= 0 && lv[v] < 0) { lv[v] = (int)Vd.size(); Vd.push_back(v); } };
+        auto sorted_add = [](std::vector<int> x, auto &&fn) {
+            std::sort(x.begin(), x.end());
+            for (int y : x) fn(y);
+        };
+        const int e0a = e_first[p], e0b = e_first[p + 1];
+        for (int e = e0a; e < e0b; e++) add_e(e);
+        const int nE0 = (int)Ed.size();
+        {   // C1: the cells of the owned edges
+            std::vector<int> x;
+            for (int e = e0a; e < e0b; e++) { x.push_back(hm.c1[e]); x.push_back(hm.c2[e]); }
+            sorted_add(x, add_c);
+        }
+        const int nC1 = (int)Cd.size();
+        {   // E1: the edges of C1's cells
+            std::vector<int> x;
+            for (int k = 0; k < nC1; k++)
+                for (int j = 0; j < hm.neoc[Cd[k]]; j++) x.push_back(hm.eoc[(size_t)Cd[k] * hm.maxE + j]);
+            sorted_add(x, add_e);
+        }
+        const int nE1 = (int)Ed.size();
+        {   // V: the vertices of E1's edges
+            std::vector<int> x;
+            for (int k = 0; k < nE1; k++) { x.push_back(hm.v1[Ed[k]]); x.push_back(hm.v2[Ed[k]]); }
+            sorted_add(x, add_v);
+        }
+        const int nV = (int)Vd.size();
+        {   // E2: plus the edges of V's vertices; C2: plus the cells of E1's
+            // edges and of V's vertices
+            std::vector<int> x, y;
+            for (int k = 0; k < nV; k++)
+                for (int j = 0; j < 3; j++) {
+                    x.push_back(hm.eov[3 * (size_t)Vd[k] + j]);
+                    y.push_back(hm.cov[3 * (size_t)Vd[k] + j]);
+                }
+            for (int k = 0; k < nE1; k++) { y.push_back(hm.c1[Ed[k]]); y.push_back(hm.c2[Ed[k]]); }
+            x.erase(std::remove(x.begin(), x.end(), -1), x.end());
+            y.erase(std::remove(y.begin(), y.end(), -1), y.end());
+            sorted_add(x, add_e);
+            sorted_add(y, add_c);
+        }
+        const int nE2 = (int)Ed.size(), nC2 = (int)Cd.size();
+        auto reset = [&]() {
+            for (int e : Ed) le[e] = -1;
+            for (int c : Cd) lc[c] = -1;
+            for (int v : Vd) lv[v] = -1;
+        };
+        if (nE0 > max_e0 || nC1 > max_c1 || nE2 + 1 > 65535 || nC2 + 1 > 65535 || nV > 65535) {
+            reset();
+            return false;
+        }
+        // owned edges: edgesOnEdge must lie in E1
+        bool ok = true;
+        for (int k = 0; k < nE0 && ok; k++) {
+            const int e = Ed[k];
+            if (hm.neoe[e] > BCL_NE2P) ok = false;
+            for (int j = 0; j < hm.neoe[e] && ok; j++) {
+                const int l = le[hm.eoe[(size_t)e * hm.maxE2 + j]];
+                if (l < 0 || l >= nE1) ok = false;
+            }
+        }
+        if (!ok) { reset(); return false; }
+        plan.cnt.insert(plan.cnt.end(), {nE0, nE1, nE2, nC1, nC2, nV, e0a, 0});
+        plan.maxE0 = std::max(plan.maxE0, nE0); plan.maxE1 = std::max(plan.maxE1, nE1);
+        plan.maxE2 = std::max(plan.maxE2, nE2); plan.maxC1 = std::max(plan.maxC1, nC1);
+        plan.maxC2 = std::max(plan.maxC2, nC2); plan.maxV = std::max(plan.maxV, nV);
+        plan.egid.insert(plan.egid.end(), Ed.begin(), Ed.end());
+        plan.cgid.insert(plan.cgid.end(), Cd.begin(), Cd.end());
+        // owned edges, term-major
+        const size_t b10 = plan.e0_eoe.size();
+        plan.e0_eoe.resize(b10 + (size_t)BCL_NE2P * nE0, (uint16_t)nE1);
+        plan.e0_wl.resize(b10 + (size_t)BCL_NE2P * nE0, 0.0);
+        plan.e0_cfc.resize(b10 + (size_t)BCL_NE2P * nE0, 0.0);
+        for (int k = 0; k < nE0; k++) {
+            const int e = Ed[k];
+            for (int j = 0; j < hm.neoe[e]; j++) {
+                const size_t x = b10 + (size_t)j * nE0 + k;
+                plan.e0_eoe[x] = (uint16_t)le[hm.eoe[(size_t)e * hm.maxE2 + j]];
+                plan.e0_wl[x] = hm.wl[(size_t)e * hm.maxE2 + j];
+                plan.e0_cfc[x] = hm.cfc[(size_t)e * hm.maxE2 + j];
+            }
+            plan.e0_c12.push_back(lc[hm.c1[e]] | (lc[hm.c2[e]] << 16));
+            plan.e0_v12.push_back(lv[hm.v1[e]] | (lv[hm.v2[e]] << 16));
+            plan.e0_n2.push_back(hm.neoe[e]);
+            plan.e0_invdc.push_back(hm.invdc[e]);
+            plan.e0_invdv.push_back(hm.invdv[e]);
+        }
+        for (int k = 0; k < nE1; k++) {
+            const int e = Ed[k];
+            plan.e1_c12.push_back(lc[hm.c1[e]] | (lc[hm.c2[e]] << 16));
+            plan.e1_v12.push_back(lv[hm.v1[e]] | (lv[hm.v2[e]] << 16));
+        }
+        // C1 cells: edges (dummy: the zero velocity slot nE2) and the cell
+        // across each (dummy: the cell itself), term-major
+        const size_t b6 = plan.c1_e.size();
+        plan.c1_e.resize(b6 + (size_t)BCL_NCEP * nC1, (uint16_t)nE2);
+        plan.c1_o.resize(b6 + (size_t)BCL_NCEP * nC1, 0);
+        plan.c1_divc.resize(b6 + (size_t)BCL_NCEP * nC1, 0.0);
+        plan.c1_kec.resize(b6 + (size_t)BCL_NCEP * nC1, 0.0);
+        for (int k = 0; k < nC1; k++) {
+            const int c = Cd[k];
+            for (int j = 0; j < BCL_NCEP; j++) plan.c1_o[b6 + (size_t)j * nC1 + k] = (uint16_t)k;
+            for (int j = 0; j < hm.neoc[c]; j++) {
+                const int e = hm.eoc[(size_t)c * hm.maxE + j];
+                const int o = hm.c1[e] == c ? hm.c2[e] : hm.c1[e];
+                const size_t x = b6 + (size_t)j * nC1 + k;
+                plan.c1_e[x] = (uint16_t)le[e];
+                plan.c1_o[x] = (uint16_t)lc[o];
+                plan.c1_divc[x] = hm.divc[(size_t)c * hm.maxE + j];
+                plan.c1_kec[x] = hm.kec[(size_t)c * hm.maxE + j];
+            }
+        }
+        // vertices (absent edge: the zero velocity slot; absent cell: the zero
+        // thickness slot nC2, weight 0)
+        const size_t b3 = plan.v_e.size();
+        plan.v_e.resize(b3 + (size_t)3 * nV, (uint16_t)nE2);
+        plan.v_c.resize(b3 + (size_t)3 * nV, (uint16_t)nC2);
+        plan.v_curl.resize(b3 + (size_t)3 * nV, 0.0);
+        plan.v_kw.resize(b3 + (size_t)3 * nV, 0.0);
+        for (int k = 0; k < nV; k++) {
+            const int v = Vd[k];
+            for (int j = 0; j < 3; j++) {
+                const size_t x = b3 + (size_t)j * nV + k;
+                const int e = hm.eov[3 * (size_t)v + j], c = hm.cov[3 * (size_t)v + j];
+                if (e >= 0) {
+                    plan.v_e[x] = (uint16_t)le[e];
+                    plan.v_curl[x] = hm.curlc[3 * (size_t)v + j];
+                }
+                if (c >= 0) {
+                    plan.v_c[x] = (uint16_t)lc[c];
+                    plan.v_kw[x] = hm.kw[3 * (size_t)v + j];
+                }
+            }
+            plan.v_f.push_back(hm.fV[v]);
+        }
+        plan.off_e0.push_back(plan.off_e0.back() + nE0);
+        plan.off_e1.push_back(plan.off_e1.back() + nE1);
+        plan.off_e2.push_back(plan.off_e2.back() + nE2);
+        plan.off_c1.push_back(plan.off_c1.back() + nC1);
+        plan.off_c2.push_back(plan.off_c2.back() + nC2);
+        plan.off_v.push_back(plan.off_v.back() + nV);
+        reset();
+    }
+    return true;
+}
+
 size_t tile_smem_bytes(const TilePlan &plan, int maxE, int maxE2, size_t sR) {
     (void)maxE;
     (void)maxE2;

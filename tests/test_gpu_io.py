@@ -104,3 +104,23 @@ def test_stream_ordered_transfers_match_the_synchronous_ones():
     assert lib.sse_state_transfer(b.handle, 0, ctypes.c_void_p(out["u"].data_ptr()), 8) == -1
     a.close()
     b.close()
+
+
+@pytest.mark.parametrize("precision", ["mixed", "fp64"])
+def test_state_init_equals_create_and_set(precision):
+    """sse_state_init (create + set of u, h, tracers and wind in one call) gives
+    the state sse_state_create + sse_state_set give: the same bits after two
+    steps, on the sphere (two tracers, wind stress, the internal numbering
+    far from the caller's)."""
+    m, L, p, (u, h, tr), run = inputs.workload("sphere_l4", perturb=True)
+    dm = binding.Mesh(m, L)
+    a = binding.State(dm, p, precision)
+    a.load_state(u, h, tr)
+    b = binding.State.init(dm, p, precision, u, h, tr)
+    for st in (a, b):
+        st.step(run["order"], run["dt"], run["M"], 2)
+    for n in ("u", "h", "tracer0", "tracer1", "zeta", "Fzeta", "ubar", "G"):
+        assert np.array_equal(a.get(n), b.get(n)), n
+    a.close()
+    b.close()
+    dm.close()

@@ -1,10 +1,11 @@
 """The allocation-free sub-cycle entry point (sse_barotropic_substep_noalloc).
 
-It serves callers that cannot allocate device memory where they run the
-sub-cycle, e.g. while their stream is being captured into a CUDA graph.  The
-test calls it through the C ABI on caller-owned device arrays, twice in a row
-with different inputs (the shared work array keeps the previous call's
-contents), and checks each result against sse_barotropic_substep.  This file
+It serves callers that must not allocate device memory where they run the
+sub-cycle (inside an allocator or memory-pool callback, or in a runtime that
+reserves its device memory up front).  The test calls it through the C ABI on
+caller-owned device arrays, twice in a row with different inputs (the shared
+work array keeps the previous call's contents), and checks each result
+against sse_barotropic_substep.  This file
 is collected last so that a failure here leaves every other test run.
 """
 import numpy as np
