@@ -44,7 +44,7 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 METRIC = "cell-layer-steps/s"
-WORKLOAD = "channel_1km"
+WORKLOAD = "sphere_l7"
 
 # algorithmic HBM bytes per launch of each kernel class (inputs read once,
 # outputs written once); sR = 8 (FP64) or 4 (mixed); h and zeta are FP64
@@ -230,12 +230,40 @@ def build_workload(seed=0, scale=None, name=WORKLOAD, **over):
 # ---------------------------------------------------------------------------
 # the oracle (CPU baseline / reference arm)
 # ---------------------------------------------------------------------------
-def time_oracle(steps, warmup, sample=(40, 200)):
-    """The FP64 C oracle, single thread, on a bounded sample of the workload:
-    the same channel at 1 km cut to sample[0] x sample[1] cells."""
+def host_info():
+    """CPU model and core count of this host (the oracle baseline's machine)."""
     import oracle
-    m, L, p, (u, h, tr), run = build_workload(scale=sample)
-    o = oracle.Oracle(m, L, p)
+    model = platform.processor() or platform.machine()
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                k = line.split(":")[0].strip().lower()
+                if k in ("model name", "cpu model", "hardware"):
+                    model = line.split(":", 1)[1].strip()
+                    break
+            else:
+                f.seek(0)
+                parts = {}
+                for line in f:
+                    if ":" in line:
+                        k, v = line.split(":", 1)
+                        parts.setdefault(k.strip().lower(), v.strip())
+                if "cpu implementer" in parts:
+                    model = (f"{platform.machine()} implementer {parts['cpu implementer']} "
+                             f"part {parts.get('cpu part', '?')}")
+    except OSError:
+        pass
+    return {"cpu_model": model, "nproc": os.cpu_count(), "threads_available": oracle.host_threads(),
+            "machine": platform.machine()}
+
+
+def time_oracle(steps, warmup, name=WORKLOAD, threads=1, **over):
+    """The FP64 C oracle on `threads` host threads (its OpenMP build above 1,
+    bit-identical results), `steps` timed steps of the named workload after
+    `warmup` untimed ones.  Returns (cell-layer-steps/s, ms per step, sample)."""
+    import oracle
+    m, L, p, (u, h, tr), run = build_workload(name=name, **over)
+    o = oracle.Oracle(m, L, p, threads=threads)
     for _ in range(warmup):
         u, h, tr = o.step(run["order"], run["dt"], run["M"], u, h, tr)
     t0 = time.perf_counter()
@@ -243,26 +271,51 @@ def time_oracle(steps, warmup, sample=(40, 200)):
         u, h, tr = o.step(run["order"], run["dt"], run["M"], u, h, tr)
     dt = time.perf_counter() - t0
     units = m.nCells * L * steps
-    return units / dt, dt / steps * 1e3, f"{m.nCells} cells x {L} layers ({sample[0]}x{sample[1]} " \
-        f"of the 160x578 channel), {steps} SSPRK3-SE steps, 1 thread"
+    desc = (f"{name}: {m.nCells} cells x {L} layers, {steps} SSPRK{run['order']}-SE steps "
+            f"(dt {run['dt']} s, M {run['M']}), {threads} thread{'s' if threads > 1 else ''}")
+    return units / dt, dt / steps * 1e3, desc
+
+
+def cpu_baseline_of(name, horizon, omp_steps=3, single_steps=1):
+    """The oracle as it stands on this host's cores: all threads (OpenMP
+    build) and one thread, each on a few steps of the full workload; the
+    time for the configuration's horizon is extrapolated from them."""
+    info = host_info()
+    nt = info["threads_available"]
+    v_all, ms_all, s_all = time_oracle(omp_steps, 0, name=name, threads=nt)
+    v_one, ms_one, s_one = time_oracle(single_steps, 0, name=name, threads=1)
+    return {"value": v_all, "unit": METRIC, "cores": nt, "kind": "oracle", "sample": s_all,
+            "horizon_steps": horizon,
+            "horizon_s_extrapolated": ms_all * horizon / 1e3,
+            "single_thread": {"value": v_one, "unit": METRIC, "cores": 1, "sample": s_one,
+                              "horizon_s_extrapolated": ms_one * horizon / 1e3},
+            **info}
 
 
 def run_reference(args):
+    """The reference arm: the FP64 oracle (the only implementation of the
+    method besides this one) on every host core, on the headline workload;
+    each timed step is one full step of the level-7 sphere when the whole run
+    stays within minutes, else of the same recipe at level 6."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return 0
+    import oracle
     steps, warmup = args.steps, args.warmup
-    value, ms, sample = time_oracle(steps, warmup)
+    nt = oracle.host_threads()
+    over = {} if steps + warmup <= 40 else {"level": 6}
+    value, ms, sample = time_oracle(steps, warmup, name=args.workload, threads=nt, **over)
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": METRIC,
             "n_gpus": args.gpus, "steps": steps, "warmup": warmup, "ms_per_step": ms,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": {"workload": WORKLOAD + " (bounded sample)",
-                                            "sample": sample, "l2": "n/a (CPU)"},
-            "cpu_baseline": {"value": value, "unit": METRIC, "cores": 1, "kind": "oracle",
+            "data": "synthetic",
+            "config": {"workload": args.workload + ("" if not over else " at level 6 (bounded sample)"),
+                       "sample": sample, "l2": "n/a (CPU)"},
+            "cpu_baseline": {"value": value, "unit": METRIC, "cores": nt, "kind": "oracle",
                              "sample": sample},
             "e2e": {"value": value, "unit": METRIC, "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0},
-            "host": platform.machine()}
+            "host": host_info()}
     print(json.dumps(line), flush=True)
     return 0
 
@@ -301,6 +354,7 @@ def measure_form(torch, binding, dm, m, L, p, state0, run, precision, steps, war
     ms = float(per.sum())
     d = st.diagnostics(check=False)
     res = {"device_ms": ms, "ms_per_step": ms / steps, "wall_s": t_wall, "prof": prof,
+           "patches": st.patches(), "fused_bcl": st.kernels_per_step(order) < 20,
            "latency_ms": {"p50": float(np.percentile(per, 50)), "p99": float(np.percentile(per, 99))},
            "clocks": clocks, "diag": d, "kernels_per_step": st.kernels_per_step(order)}
     gu, gh, gt = st.read_state()
@@ -355,8 +409,9 @@ def measure_e2e(torch, binding, dm, p, state0, run, precision, steps, stream, na
     return ms, nbytes, dtypes
 
 
-def roofline_of(prof, m, L, nT, mixed, order, steps, ms_per_step):
-    """Dominant kernel class against the HBM copy peak, and the whole step."""
+def kernel_roofline_of(prof, m, L, nT, mixed, order):
+    """The longest kernel class against the HBM copy peak (its own
+    algorithmic bytes per launch / its average launch time)."""
     peaks, peak_kind = measured_peaks()
     sR = 4 if mixed else 8
     dom = max(prof, key=lambda k: prof[k][0])
@@ -376,15 +431,117 @@ def roofline_of(prof, m, L, nT, mixed, order, steps, ms_per_step):
             "ms_per_launch": per_launch_ms}
 
 
-def step_roofline_of(m, L, nT, mixed, ms_per_step):
-    peaks, _ = measured_peaks()
-    step_b = step_bytes_per_cell_layer(mixed, nT) * m.nCells * L
+def step_roofline_of(m, L, nT, mixed, ms_per_step, workload):
+    """The whole step against the HBM copy peak: the algorithmic bytes of one
+    large step (every 3-D array read or written once per stage) over the
+    step's device time; traffic from the committed launch list with DRAM
+    counters when one exists for this workload and form."""
+    peaks, peak_kind = measured_peaks()
+    per_cl = step_bytes_per_cell_layer(mixed, nT)
+    step_b = per_cl * m.nCells * L
     gbs = step_b / (ms_per_step / 1e3) / 1e9
-    return {"bytes_per_step": step_b, "achieved_gbs": gbs, "frac_of_hbm": gbs / peaks["hbm_gbs"]}
+    traffic, src = step_traffic(workload, mixed)
+    return {"kernel": "step (all launches of one large step)", "bound": "hbm", "achieved": gbs,
+            "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": gbs / peaks["hbm_gbs"],
+            "peak_source": f"{peak_kind} hbm_gbs (copy)", "bytes_per_step": step_b,
+            "bytes_per_cell_layer": per_cl, "ms_per_step": ms_per_step,
+            "traffic": traffic, "traffic_source": src}
+
+
+def step_traffic(workload, mixed):
+    """DRAM bytes (read + write) of one large step from the committed ncu
+    launch list of this workload and form, while the kernel sources match."""
+    name = f"launches_{workload}_{'mixed' if mixed else 'fp64'}.md"
+    path = os.path.join(ROOT, "profiles", name)
+    if not os.path.exists(path):
+        return None, "no ncu launch list with DRAM counters for this workload/form"
+    traffic, hashes = None, {}
+    with open(path) as f:
+        for line in f:
+            if line.startswith("| DRAM bytes per step"):
+                traffic = float(line.split("|")[2].split()[0]) * 1e6
+            if line.startswith("- source sha256 "):
+                k, v = line[len("- source sha256 "):].strip().split(": ")
+                hashes[k] = v
+    if traffic is None or not hashes:
+        return None, "launch list incomplete"
+    if hashes != source_hashes():
+        return None, "kernel sources changed since the ncu capture"
+    return traffic, f"profiles/{name}"
+
+
+def subcycle_of(prof, m, run, steps, tiled_patches, workload, mixed):
+    """The barotropic sub-cycle, which is bound by its grid synchronisations
+    and on-chip latency rather than by HBM: its time per step, grid barriers
+    per step (the tiled kernel: one per sub-step; the global-memory kernel:
+    one per forward-Euler sub-stage), the time per barrier interval, and its
+    L2/DRAM traffic per launch from the committed ncu capture."""
+    order, M = run["order"], run["M"]
+    calls = 3 if order == 3 else 2
+    ms, launches = prof.get("btr", (0.0, 0))
+    ms_step = ms / steps
+    per_call_syncs = M if tiled_patches else order * M
+    syncs = calls * per_call_syncs
+    out = {"ms_per_step": ms_step, "launches_per_step": launches / steps,
+           "substeps_per_step": calls * M, "fe_substages_per_step": calls * order * M,
+           "grid_barriers_per_step": syncs,
+           "us_per_barrier_interval": ms_step * 1e3 / syncs if syncs else None,
+           "kernel": "k_btr_tiled (one patch per SM in shared memory)" if tiled_patches
+           else "k_btr (global memory)", "patches": tiled_patches,
+           "state_bytes_2d": (4 if mixed else 8) * 4 * m.nEdges + 8 * m.nCells}
+    name = PROFILE_OF.get(workload, {}).get("btr")
+    l2 = dram = None
+    src = "no ncu capture of the sub-cycle for this workload/form"
+    if name and mixed and os.path.exists(os.path.join(ROOT, "profiles", name)):
+        hashes = {}
+        with open(os.path.join(ROOT, "profiles", name)) as f:
+            for line in f:
+                if line.startswith("| L2 bytes"):
+                    l2 = float(line.split("|")[2].split()[0]) * 1e6
+                if line.startswith("| DRAM bytes read + written"):
+                    dram = float(line.split("|")[2].split()[0]) * 1e6
+                if line.startswith("- source sha256 "):
+                    k, v = line[len("- source sha256 "):].strip().split(": ")
+                    hashes[k] = v
+        src = f"profiles/{name}"
+        if hashes != source_hashes():
+            l2 = dram = None
+            src = "kernel sources changed since the ncu capture"
+    out.update({"l2_bytes_per_launch": l2, "dram_bytes_per_launch": dram, "traffic_source": src})
+    return out
+
+
+def fp64_alu_of(m, L, ms_per_step, fp64_tflops, workload):
+    """The FP64 form against its arithmetic bound: FP64 operations per
+    cell-layer-step counted by ncu (dadd + dmul + 2 dfma over every launch of
+    one step, committed summary) x cell-layers / step time, against the FMA
+    rate measured by sse_probe_fma_rate."""
+    path = os.path.join(ROOT, "profiles", "fp64_ops_per_cell_layer_step.md")
+    per_cl, src = None, "no committed FP64 operation count"
+    if os.path.exists(path):
+        hashes = {}
+        with open(path) as f:
+            for line in f:
+                if line.startswith("| FP64 flops per cell-layer-step"):
+                    per_cl = float(line.split("|")[2].split()[0])
+                if line.startswith("- source sha256 "):
+                    k, v = line[len("- source sha256 "):].strip().split(": ")
+                    hashes[k] = v
+        src = "profiles/fp64_ops_per_cell_layer_step.md"
+        if hashes != source_hashes():
+            per_cl, src = None, "kernel sources changed since the FP64 operation count"
+    out = {"bound": "alu", "unit": "TFLOP/s", "peak": fp64_tflops,
+           "peak_source": "measured FP64 FMA rate (sse_probe_fma_rate)",
+           "flops_per_cell_layer_step": per_cl, "flops_source": src}
+    if per_cl is not None and fp64_tflops:
+        ach = per_cl * m.nCells * L / (ms_per_step / 1e3) / 1e12
+        out.update({"achieved": ach, "frac": ach / fp64_tflops})
+    return out
 
 
 def measure_workload(torch, binding, name, forms_todo, headline, steps, warmup, rank, stream,
-                     flush, sampler=None, e2e=True, world=1, dist=None, **over):
+                     flush, sampler=None, e2e=True, world=1, dist=None, fp64_tflops=None,
+                     **over):
     """Every requested precision form of one named workload on this GPU."""
     m, L, p, state0, run = build_workload(seed=rank, name=name, **over)
     nT = int(p.get("nTracers", 1))
@@ -412,20 +569,30 @@ def measure_workload(torch, binding, name, forms_todo, headline, steps, warmup, 
             err[nm] = rel(mt[k], ft[k])
         out["mixed_err"] = err
     prof = head["prof"]
-    roof = roofline_of(prof, m, L, nT, mixed, run["order"], steps, head["ms_per_step"])
-    traffic, traffic_src = ncu_traffic(roof["kernel"], mixed, name) if not over else \
+    tag = name if not over else name + " (variant)"
+    kroof = kernel_roofline_of(prof, m, L, nT, mixed, run["order"])
+    traffic, traffic_src = ncu_traffic(kroof["kernel"], mixed, name) if not over else \
         (None, "no ncu capture of this variant of the workload")
-    roof["traffic"], roof["traffic_source"] = traffic, traffic_src
-    out["roofline"] = roof
-    out["step_roofline"] = step_roofline_of(m, L, nT, mixed, head["ms_per_step"])
+    kroof["traffic"], kroof["traffic_source"] = traffic, traffic_src
+    out["kernel_roofline"] = kroof
+    out["roofline"] = step_roofline_of(m, L, nT, mixed, head["ms_per_step"], tag)
+    out["subcycle"] = subcycle_of(prof, m, run, steps, head["patches"], tag, mixed)
     out["kernels"] = {k: {"ms_per_step": v[0] / steps, "share": v[0] / max(head["device_ms"], 1e-9),
-                          "launches_per_step": v[1] / steps} for k, v in prof.items()}
+                          "launches_per_step": v[1] / steps} for k, v in prof.items() if v[1]}
     vol0 = float(m.areaCell @ state0[1].sum(1))
-    out["forms_summary"] = {
-        k: {"value": world * m.nCells * L * steps / (v["device_ms"] / 1e3),
-            "ms_per_step": v["ms_per_step"], "latency_ms": v["latency_ms"],
-            "volume_rel_change": abs(v["diag"]["volume"] - vol0) / vol0}
-        for k, v in forms.items()}
+    out["forms_summary"] = {}
+    for k, v in forms.items():
+        fs = {"value": world * m.nCells * L * steps / (v["device_ms"] / 1e3),
+              "ms_per_step": v["ms_per_step"], "latency_ms": v["latency_ms"],
+              "volume_rel_change": abs(v["diag"]["volume"] - vol0) / vol0,
+              "hbm_roofline": step_roofline_of(m, L, nT, k == "mixed", v["ms_per_step"], tag),
+              "fused_baroclinic": v["fused_bcl"]}
+        if k == "fp64":
+            fs["alu_roofline"] = fp64_alu_of(m, L, v["ms_per_step"], fp64_tflops, tag)
+            fs["kernels"] = {c: {"ms_per_step": x[0] / steps,
+                                 "share": x[0] / max(v["device_ms"], 1e-9)}
+                             for c, x in v["prof"].items() if x[1]}
+        out["forms_summary"][k] = fs
     out["e2e"] = None
     if e2e:
         e2e_steps = min(steps, 20)
@@ -467,11 +634,11 @@ def _build_requests(binding, specs):
 
 
 def run_stream(binding, specs, built, precision, max_active, budget, chunk, realtime=True,
-               tune="throughput"):
-    """Submit the specs (at their arrival times when realtime) to one server;
-    returns per-request (latency, units) and the makespan."""
+               tune="throughput", packed=False):
+    """Submit the specs (at their arrival times when realtime) to one server
+    (packed: SSE_SERVER_PACKED); returns per-request latency and the makespan."""
     srv = binding.Server(hbm_budget=budget, max_active=max_active, steps_per_launch=chunk,
-                         tune=tune)
+                         tune=tune, packed=packed)
     t0 = time.perf_counter()
     handles = []
     for sp, (m, L, p, (u, h, tr), dm) in zip(specs, built):
@@ -496,7 +663,7 @@ def run_stream(binding, specs, built, precision, max_active, budget, chunk, real
     return {"requests": len(specs), "makespan_s": makespan, "value": units / makespan,
             "unit": METRIC, "p50_s": float(np.percentile(lat, 50)),
             "p99_s": float(np.percentile(lat, 99)), "max_active_seen": st["max_active_seen"],
-            "peak_bytes": st["peak_bytes"]}
+            "peak_bytes": st["peak_bytes"], "latencies_s": [float(x) for x in lat]}
 
 
 def measure_ensemble(binding, seed=0):
@@ -505,54 +672,91 @@ def measure_ensemble(binding, seed=0):
     from paper_2105_13484_gb300 import inputs
     specs = inputs.ensemble_members(seed=seed)
     built = _build_requests(binding, specs)
+    packed = run_stream(binding, specs, built, "mixed", 64, 200 << 30, 10, realtime=False,
+                        tune="throughput", packed=True)
     batched = run_stream(binding, specs, built, "mixed", 64, 200 << 30, 10, realtime=False,
                          tune="throughput")
     single = run_stream(binding, specs, built, "mixed", 1, 200 << 30, 10, realtime=False,
                         tune="latency")
     tuned = sorted({(b[0].nCells, binding.tune(b[4], b[2], "mixed", "throughput")) for b in built})
+    for r in (packed, batched, single):
+        r.pop("latencies_s", None)
     return {"members": len(specs), "cells": sorted({b[0].nCells for b in built}),
             "patch_cells_throughput": tuned,
             "layers": [int(min(b[1] for b in built)), int(max(b[1] for b in built))],
-            "batched": batched, "one_at_a_time": single,
+            "packed": packed, "batched": batched, "one_at_a_time": single,
+            "speedup_packed": single["makespan_s"] / packed["makespan_s"],
             "speedup": single["makespan_s"] / batched["makespan_s"]}
 
 
-def measure_serving(binding, seed=0):
-    """A seeded Poisson stream (20 requests/s) of SSPRK2/3-SE solves on planar
-    channels and geodesic spheres: mixed precision with continuous batching
-    against the FP64 path one request at a time, same arrival times."""
+def measure_serving(binding, seed=0, n_fp64=8):
+    """A seeded Poisson stream (20 requests/s, 32 requests) of SSPRK2/3-SE
+    solves on planar channels and geodesic spheres of levels 5-7, 10-60
+    layers, 50-500 steps: mixed precision with continuous batching against
+    the FP64 path one request at a time on the same arrival times.  The FP64
+    arm serves only the first `n_fp64` requests (one at a time it would take
+    minutes); the mixed arm's latencies on those same requests are reported
+    beside it."""
     from paper_2105_13484_gb300 import inputs
     specs = inputs.serving_requests(seed=seed)
     built = _build_requests(binding, specs)
-    mixed = run_stream(binding, specs, built, "mixed", 64, 200 << 30, 4, tune="throughput")
-    fp64 = run_stream(binding, specs, built, "fp64", 1, 200 << 30, 4, tune="latency")
+    mixed = run_stream(binding, specs, built, "mixed", 64, 200 << 30, 4, tune="throughput",
+                       packed=True)
+    streams = run_stream(binding, specs, built, "mixed", 64, 200 << 30, 4, tune="throughput")
+    fp64 = run_stream(binding, specs[:n_fp64], built[:n_fp64], "fp64", 1, 200 << 30, 4,
+                      tune="latency")
+    lat8 = np.array(mixed["latencies_s"][:n_fp64])
+    for r in (mixed, streams, fp64):
+        r.pop("latencies_s", None)
+    mixed_first = {"requests": n_fp64, "p50_s": float(np.percentile(lat8, 50)),
+                   "p99_s": float(np.percentile(lat8, 99))}
+    cells = sorted({b[0].nCells for b in built})
     return {"requests": len(specs), "rate_per_s": 20.0,
-            "mix": "planar 2k-60k cells and geodesic levels 5-6, 10-60 layers, 20-100 steps",
-            "mixed_batched": mixed, "fp64_one_at_a_time": fp64,
+            "mix": "planar 2k-60k cells and geodesic levels 5-7 (up to 163,842 cells), "
+                   "10-60 layers, 50-500 steps, SSPRK2-SE and SSPRK3-SE",
+            "cells": [cells[0], cells[-1]],
+            "mixed_batched": mixed, "mixed_streams": streams, "fp64_one_at_a_time": fp64,
+            "batching": "mixed_batched: SSE_SERVER_PACKED rounds (one 3-D launch per kernel "
+                        "and stage for all active requests); mixed_streams: one stream per "
+                        "request",
+            "fp64_requests": f"the first {n_fp64} of the {len(specs)} (same arrival times)",
+            "mixed_batched_first": mixed_first,
             "throughput_ratio": mixed["value"] / fp64["value"],
-            "p99_ratio": fp64["p99_s"] / mixed["p99_s"]}
+            "p99_ratio_same_requests": fp64["p99_s"] / mixed_first["p99_s"]}
 
 
-def measure_convergence(binding, T=960.0, n_list=(16, 32, 64, 128, 256), n_ref=2048):
-    """The dt-refinement sweep of the 1 km channel: SSPRK3-SE with M = 30 held
-    fixed (dt and the sub-step shrink together), the paper's relative l2 error
-    of the top-layer velocity u_1 and thickness h_1 at time T against a run
-    with T / n_ref, on the GPU, FP64 and the mixed form."""
-    m, L, p, (u, h, tr), run = build_workload()
+def measure_convergence(binding, T=960.0, n_list=(16, 32, 64, 128, 256), n_ref=2048,
+                        hold="M", recon=None, forms=("fp64", "mixed"), M0=None):
+    """The dt-refinement sweep of the 1 km channel: SSPRK3-SE, the paper's
+    relative l2 error of the top-layer velocity u_1 and thickness h_1 at time T
+    against a run with T / n_ref, on the GPU.  hold = "M": the sub-step count
+    is fixed (dt and the sub-step shrink together); hold = "tau": the
+    sub-step length tau = dt / M is fixed (M shrinks with dt).  recon: the
+    reconciliation mode (default: the workload's)."""
+    m, L, p, (u, h, tr), run = build_workload(name="channel_1km")
+    if recon is not None:
+        p = dict(p, recon=recon)
     dm = binding.Mesh(m, L)
-    M = run["M"]
+    M0 = M0 or run["M"]
+    dt0 = T / n_list[0]
+    tau = dt0 / M0
+
+    def M_of(n):
+        return M0 if hold == "M" else max(1, int(round((T / n) / tau)))
 
     def solve(prec, n):
         st = binding.State(dm, p, prec)
         st.load_state(u, h, tr)
-        st.step(3, T / n, M, n)
+        st.step(3, T / n, M_of(n), n)
         gu, gh, _ = st.read_state()
         st.close()
         return gu[:, 0], gh[:, 0]
 
     ru, rh = solve("fp64", n_ref)
-    out = {"T_s": T, "M": M, "dt_s": [T / n for n in n_list], "reference_dt_s": T / n_ref}
-    for prec in ("fp64", "mixed"):
+    out = {"T_s": T, "hold": hold, "recon": p.get("recon"), "dt_s": [T / n for n in n_list],
+           "M": [M_of(n) for n in n_list], "reference_dt_s": T / n_ref,
+           "reference_M": M_of(n_ref)}
+    for prec in forms:
         eu, eh = [], []
         for n in n_list:
             a, b = solve(prec, n)
@@ -563,6 +767,21 @@ def measure_convergence(binding, T=960.0, n_list=(16, 32, 64, 128, 256), n_ref=2
                      "rate_h1": [float(np.log2(eh[i] / eh[i + 1])) for i in range(len(eh) - 1)]}
     dm.close()
     return out
+
+
+def convergence_study(binding):
+    """The longer study of the channel's observed order (run with --study):
+    T = 3840 s (64 steps at dt = 60 s) against dt = 0.9375 s, FP64, with M
+    fixed and with tau fixed, in the consistent and the printed
+    reconciliation."""
+    res = {}
+    n_list, n_ref = (64, 128, 256, 512), 4096
+    for hold in ("M", "tau"):
+        for recon in ("consistent", "paper"):
+            res[f"{hold}_{recon}"] = measure_convergence(binding, T=3840.0, n_list=n_list,
+                                                         n_ref=n_ref, hold=hold, recon=recon,
+                                                         forms=("fp64",))
+    return res
 
 
 def config_of(name, w, precision, world):
@@ -596,20 +815,32 @@ def run_ours(args):
         dist.barrier()
     torch.cuda.synchronize()
     sampler = ClockSampler(local)
+    # measured arithmetic rates (denominators of the FP64 form's ALU roofline)
+    rates = {"fp64_tflops": binding.fma_rate("fp64"), "fp32_tflops": binding.fma_rate("mixed")}
     todo = ("mixed", "fp64") if args.forms == "both" else (args.forms,)
     if args.precision not in todo:
         todo = todo + (args.precision,)
     w = measure_workload(torch, binding, args.workload, todo, args.precision, args.steps,
-                         args.warmup, rank, stream, flush, sampler, not args.no_e2e, world, dist)
+                         args.warmup, rank, stream, flush, sampler, not args.no_e2e, world, dist,
+                         fp64_tflops=rates["fp64_tflops"])
     head = w["head"]
     also = {}
-    if args.workload == WORKLOAD and not args.no_sphere:
-        # the largest single mesh: the 60-layer level-7 sphere, mixed form
-        ns = min(args.steps, 144)
-        s7 = measure_workload(torch, binding, "sphere_l7", ("mixed",), "mixed", ns, args.warmup,
-                              rank, stream, flush, None, False, world, dist)
+    extra = args.workload == WORKLOAD and not args.no_also
+    if extra:
+        # the 92,480-cell channel (SSPRK3-SE, dt 60 s, M 30), both forms
+        nc = min(args.steps, 200)
+        ch = measure_workload(torch, binding, "channel_1km", ("mixed", "fp64"), "mixed", nc,
+                              args.warmup, rank, stream, flush, None, False, world, dist,
+                              fp64_tflops=rates["fp64_tflops"])
+        also["channel_1km"] = {
+            "value": ch["value"], "unit": METRIC, "steps": nc, "ms_per_step": ch["t_max"] / nc,
+            "latency_ms": ch["head"]["latency_ms"],
+            "config": config_of("channel_1km", ch, "mixed", world), "roofline": ch["roofline"],
+            "subcycle": ch["subcycle"], "kernels": ch["kernels"], "forms": ch["forms_summary"],
+            "mixed_vs_fp64_rel_l2": ch["mixed_err"]}
         # the same sphere as a global-ocean setup: partial bottom cells on the
         # 60 reference layers and biharmonic viscosity
+        ns = min(args.steps, 144)
         pb = measure_workload(torch, binding, "sphere_l7", ("mixed",), "mixed", ns, args.warmup,
                               rank, stream, flush, None, False, world, dist, partial=True,
                               nu_4=1e11)
@@ -623,35 +854,24 @@ def run_ours(args):
                            nu_4=1e11),
             "kernels": pb["kernels"],
             "volume_rel_change": pb["forms_summary"]["mixed"]["volume_rel_change"]}
-        also["sphere_l7"] = {
-            "value": s7["value"], "unit": METRIC, "steps": ns,
-            "ms_per_step": s7["t_max"] / ns, "latency_ms": s7["head"]["latency_ms"],
-            "config": config_of("sphere_l7", s7, "mixed", world), "roofline": s7["roofline"],
-            "step_roofline": s7["step_roofline"], "kernels": s7["kernels"],
-            "volume_rel_change": s7["forms_summary"]["mixed"]["volume_rel_change"]}
-
-    if args.workload == WORKLOAD and not args.no_sphere:
-        # the same channel with Algorithm 2 (implicit vertical mixing) in every stage
-        vm = measure_workload(torch, binding, WORKLOAD, ("mixed",), "mixed", args.steps,
+        # the channel with Algorithm 2 (implicit vertical mixing) in every stage
+        vm = measure_workload(torch, binding, "channel_1km", ("mixed",), "mixed", nc,
                               args.warmup, rank, stream, flush, None, False, world, dist,
                               vmix=True)
         also["channel_1km_vmix"] = {
-            "value": vm["value"], "unit": METRIC, "steps": args.steps,
-            "ms_per_step": vm["t_max"] / args.steps, "latency_ms": vm["head"]["latency_ms"],
-            "config": dict(config_of(WORKLOAD, vm, "mixed", world), baroclinic="Algorithm 2"),
+            "value": vm["value"], "unit": METRIC, "steps": nc,
+            "ms_per_step": vm["t_max"] / nc, "latency_ms": vm["head"]["latency_ms"],
+            "config": dict(config_of("channel_1km", vm, "mixed", world), baroclinic="Algorithm 2"),
             "kernels": vm["kernels"],
             "volume_rel_change": vm["forms_summary"]["mixed"]["volume_rel_change"]}
-
-    if args.workload == WORKLOAD and not args.no_sphere:
         also["convergence"] = measure_convergence(binding)
-    if args.workload == WORKLOAD and not args.no_serving:
+    if extra and not args.no_serving:
         also["ensemble"] = measure_ensemble(binding, seed=rank)
         also["serving"] = measure_serving(binding, seed=rank)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
-        v, ms, sample = time_oracle(2, 0, sample=(160, 578))
-        cpu = {"value": v, "unit": METRIC, "cores": 1, "kind": "oracle", "sample": sample}
+        cpu = cpu_baseline_of(args.workload, w["run"]["steps"])
 
     line = {
         "metric": METRIC, "value": w["value"], "unit": METRIC, "n_gpus": world,
@@ -659,10 +879,12 @@ def run_ours(args):
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32+f64" if args.precision == "mixed" else "f64", "data": "synthetic",
         "config": config_of(args.workload, w, args.precision, world),
-        "roofline": w["roofline"], "step_roofline": w["step_roofline"], "kernels": w["kernels"],
+        "roofline": w["roofline"], "kernel_roofline": w["kernel_roofline"],
+        "subcycle": w["subcycle"], "kernels": w["kernels"],
         "latency_ms": head["latency_ms"],
         "forms": w["forms_summary"],
         "mixed_vs_fp64_rel_l2": w["mixed_err"],
+        "measured_rates": rates,
         "e2e": w["e2e"],
         "e2e_fp64_host": w.get("e2e_fp64_host"),
         "gpu_launches": head["kernels_per_step"] * args.steps,
@@ -682,7 +904,7 @@ def run_ours(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--steps", type=int, default=144)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
@@ -690,17 +912,27 @@ def main():
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end leg")
     ap.add_argument("--forms", default="both", choices=["both", "mixed", "fp64"],
                     help="precision forms to measure (the headline form is always measured)")
-    ap.add_argument("--workload", default=WORKLOAD, choices=[WORKLOAD, "sphere_l7"],
-                    help="headline workload (default: the 92,480-cell channel)")
-    ap.add_argument("--no-sphere", action="store_true",
-                    help="skip the extra level-7 sphere and Algorithm 2 measurements")
+    ap.add_argument("--workload", default=WORKLOAD, choices=[WORKLOAD, "channel_1km"],
+                    help="headline workload (default: the level-7 sphere, 60 layers)")
+    ap.add_argument("--no-also", "--no-sphere", dest="no_also", action="store_true",
+                    help="skip the channel, partial-bottom, Algorithm 2 and convergence "
+                         "measurements")
     ap.add_argument("--no-serving", action="store_true",
                     help="skip the batched-ensemble and request-stream measurements")
+    ap.add_argument("--study", choices=["convergence"],
+                    help="run only the named longer study and print its JSON")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":
         return run_reference(args)
+    if args.study == "convergence":
+        from paper_2105_13484_gb300 import binding, build
+        build.build()
+        binding.load()
+        print(json.dumps({"study": "convergence", "channel_1km": convergence_study(binding)}),
+              flush=True)
+        return 0
     return run_ours(args)
 
 

@@ -225,6 +225,21 @@ int sse_state_sync(sse_state *state);
  * n_steps < 0. */
 int sse_step(sse_state *state, int order, double dt, int n_substeps, int n_steps);
 
+/* The same steps for n states at once, in lock-step (Sec. 3.2 / 3.3 per state,
+ * with each state's own dt[i] and n_substeps[i]): the 3-D kernels of all n
+ * states are issued as one launch per kernel and stage on `cuda_stream`, each
+ * state's barotropic sub-cycle (Algorithm 3 / 4) runs on the state's own
+ * stream between events that fork from and join back into `cuda_stream`, and
+ * every state's stream waits for the batch at the end.  Each state's results
+ * are bit-identical to sse_step on it alone.  The states must have been made
+ * on the current device, share the precision, and use the fused baroclinic
+ * and thickness kernels (full columns, Algorithm 1, no biharmonic viscosity)
+ * with profiling and test hooks off; otherwise SSE_ERR_UNSUPPORTED and no
+ * state is stepped.  INVALID_ARG as for sse_step, for n < 1 or for a state
+ * listed twice.  Asynchronous. */
+int sse_step_batch(sse_state *const *states, int n, int order, const double *dt,
+                   const int32_t *n_substeps, int n_steps, void *cuda_stream);
+
 /* Algorithm 1 (Baroclinic_FEuler) alone, on the state's u (= UBAR + UTILDE),
  * UTILDE, h, tracers and zeta = sum h - H: overwrites UTILDE with the
  * output tilde-u^1 and G with the barotropic forcing. */
@@ -402,6 +417,16 @@ typedef struct {
  * run once per mesh and precision, at the first submission that uses it). */
 int sse_server_create(int device, size_t hbm_budget_bytes, int max_active,
                       int steps_per_launch, int tune_objective, sse_server **out);
+/* flags = SSE_SERVER_PACKED: the active requests of one precision and order
+ * advance in rounds of up to steps_per_launch steps, all of them in one
+ * sse_step_batch call (one 3-D launch per kernel and stage for the whole
+ * round); between rounds finished requests retire and waiting ones join.
+ * Requests whose states cannot be packed step alone.  flags = 0 is
+ * sse_server_create: every request steps on its own stream. */
+#define SSE_SERVER_PACKED 1
+int sse_server_create_ex(int device, size_t hbm_budget_bytes, int max_active,
+                         int steps_per_launch, int tune_objective, int flags,
+                         sse_server **out);
 /* Queue a request; *id_out identifies it.  SSE_ERR_OOM if it alone exceeds
  * the budget. */
 int sse_server_submit(sse_server *server, const sse_mesh *mesh, const sse_params *params,

@@ -82,7 +82,7 @@ class Diag(ct.Structure):
 
 
 EXPORTS = ["sse_mesh_create", "sse_mesh_destroy", "sse_state_create", "sse_state_destroy",
-           "sse_state_init", "sse_probe_fma_rate",
+           "sse_state_init", "sse_probe_fma_rate", "sse_step_batch", "sse_server_create_ex",
            "sse_state_set", "sse_state_get", "sse_step", "sse_baroclinic_feuler",
            "sse_barotropic_substep", "sse_diagnostics", "sse_kernels_per_step", "sse_profile",
            "sse_profile_read", "sse_barotropic_substep_noalloc", "sse_state_footprint",
@@ -115,6 +115,9 @@ def load(path: str = LIB_PATH):
     lib.sse_state_destroy.argtypes = [ct.c_void_p]
     lib.sse_state_destroy.restype = None
     lib.sse_probe_fma_rate.argtypes = [ct.c_int, ct.POINTER(ct.c_double)]
+    lib.sse_step_batch.argtypes = [ct.POINTER(ct.c_void_p), ct.c_int, ct.c_int,
+                                   ct.POINTER(ct.c_double), ct.POINTER(ct.c_int32), ct.c_int,
+                                   ct.c_void_p]
     lib.sse_state_init.argtypes = [ct.c_void_p, ct.POINTER(Params), ct.c_void_p, ct.c_void_p,
                                    ct.c_void_p, ct.c_void_p, ct.c_void_p,
                                    ct.POINTER(ct.c_void_p)]
@@ -134,6 +137,8 @@ def load(path: str = LIB_PATH):
     lib.sse_mesh_dims.argtypes = [ct.c_void_p, ct.POINTER(ct.c_int32)]
     lib.sse_server_create.argtypes = [ct.c_int, ct.c_size_t, ct.c_int, ct.c_int, ct.c_int,
                                       ct.POINTER(ct.c_void_p)]
+    lib.sse_server_create_ex.argtypes = [ct.c_int, ct.c_size_t, ct.c_int, ct.c_int, ct.c_int,
+                                         ct.c_int, ct.POINTER(ct.c_void_p)]
     lib.sse_state_create_ex.argtypes = [ct.c_void_p, ct.POINTER(Params), ct.POINTER(Tuning),
                                         ct.c_void_p, ct.POINTER(ct.c_void_p)]
     lib.sse_state_footprint_ex.argtypes = [ct.c_void_p, ct.POINTER(Params), ct.POINTER(Tuning),
@@ -230,6 +235,18 @@ def barotropic_substep_noalloc(mesh: Mesh, order: int, dt: float, M: int, g: flo
                                               ct.c_void_p(zeta_out or 0),
                                               ct.c_void_p(stream or 0)),
            "sse_barotropic_substep_noalloc")
+
+
+def step_batch(states, order: int, dts, Ms, n_steps: int, stream=None):
+    """sse_step_batch: n_steps large steps of every state, in lock-step, the
+    3-D kernels of all states in one launch per kernel and stage on `stream`."""
+    n = len(states)
+    hs = (ct.c_void_p * n)(*[st.handle.value if hasattr(st.handle, "value") else st.handle
+                             for st in states])
+    d = (ct.c_double * n)(*[float(x) for x in dts])
+    m = (ct.c_int32 * n)(*[int(x) for x in Ms])
+    _check(load().sse_step_batch(hs, n, int(order), d, m, int(n_steps), ct.c_void_p(stream or 0)),
+           "sse_step_batch")
 
 
 def fma_rate(precision="fp64") -> float:
@@ -493,13 +510,16 @@ class Server:
     `max_active` run; their steps overlap on the device."""
 
     def __init__(self, hbm_budget: int, max_active: int = 64, steps_per_launch: int = 1,
-                 device: int = 0, tune=None):
+                 device: int = 0, tune=None, packed: bool = False):
+        """packed: the active requests of one precision and order advance in
+        rounds, all of them in one sse_step_batch call (SSE_SERVER_PACKED)."""
         self.lib = load()
         h = ct.c_void_p()
         obj = -1 if tune is None else TUNE[tune]
-        _check(self.lib.sse_server_create(int(device), int(hbm_budget), int(max_active),
-                                          int(steps_per_launch), obj, ct.byref(h)),
-               "sse_server_create")
+        _check(self.lib.sse_server_create_ex(int(device), int(hbm_budget), int(max_active),
+                                             int(steps_per_launch), obj, 1 if packed else 0,
+                                             ct.byref(h)),
+               "sse_server_create_ex")
         self.handle = h
         self._bufs = {}   # output arrays the worker may still write, by request id
 

@@ -15,7 +15,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_lib")
 LIB = os.path.join(OUT_DIR, "libsse.so")
-SOURCES = ["api.cu", "stage_kernels.cu", "bcl_fused.cu", "btr_kernel.cu", "tiles.cu", "server.cu", "probe.cu"]
+SOURCES = ["api.cu", "stage_kernels.cu", "bcl_fused.cu", "thick_fused.cu", "btr_kernel.cu", "tiles.cu", "server.cu", "probe.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

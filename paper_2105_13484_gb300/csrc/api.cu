@@ -90,6 +90,9 @@ struct sse_mesh {
     std::map<int, std::shared_ptr<const TilePlan>> plans;
     // fused baroclinic plans already built, by cells per patch (null: no fit)
     std::map<int, std::shared_ptr<const BclPlan>> bcl_plans;
+    // fused thickness plan (null: no fit), built once
+    std::shared_ptr<const ThickPlan> thick_plan;
+    bool thick_tried = false;
     std::map<int, int> tuned;   // autotuned patch size by (precision, objective)
 };
 
@@ -527,8 +530,32 @@ struct EngineBase {
         }                                                            \
     } while (0)
 
+// One launch of a step, recorded instead of issued (sse_step_batch): the
+// batched driver replays the i-th launch of every state as one grid.
+enum RecClass { REC_COLFLUX, REC_BCL, REC_BTR, REC_TRANSPORT, REC_THICK, REC_COMBINE };
+template <class R> struct CombineJob {
+    const R *a, *b, *c;
+    R *out;
+    double wa, wb, wc;
+    int n, pad_;
+};
+template <class R> struct LaunchRec {
+    int cls = 0;
+    size_t smem = 0;
+    union U {
+        ColfluxJob<R> cf;
+        BclJob<R> bcl;
+        TransportJob<R> tr;
+        ThickJob<R> th;
+        BtrArgs<R> btr;
+        CombineJob<R> cmb;
+        U() {}
+    } u;
+};
+
 template <class R>
 struct Engine : EngineBase {
+    std::vector<LaunchRec<R>> *rec = nullptr;   // set: record launches, do not issue them
     DMesh m;
     DParams p{};
     int recon = SSE_RECON_CONSISTENT;
@@ -564,6 +591,10 @@ struct Engine : EngineBase {
     bool fused = false;   // the baroclinic stage as k_colflux + k_bcl_fused
     DBcl<R> bcl{};
     R *Fc = nullptr;      // [Ep] column transport of the stage (k_colflux)
+    bool fused_th = false;   // the thickness stage as k_transport_cols + k_thick_fused
+    DThick thk{};
+    R *uA_e = nullptr;       // [Ep] transport adjustment u^A of the stage
+    TransportArgs<R> last_ta{};   // the transport velocity the next thickness stage uses
 
     // Plan the tiled sub-cycle: patches of about patch_cells owned cells, halo
     // of 3 rings (one SSPRK3 sub-step per exchange).  The default (0) is one
@@ -679,9 +710,13 @@ struct Engine : EngineBase {
         const char *env = getenv("SSE_BCL_KERNEL");
         if (env && strcmp(env, "unfused") == 0) return SSE_OK;
         if (m.partial || vmix || p.nu_4 > 0.0) return SSE_OK;
-        int smem_block = 0;
+        int smem_block = 0, smem_sm = 0;
         CK(cudaDeviceGetAttribute(&smem_block, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
-        for (int Pc : {160, 128, 96, 64, 48, 32}) {
+        CK(cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev));
+        // the largest patches of which two CTAs fit an SM (the kernel is built for
+        // two per SM); else the largest that fit at all
+        for (int pass = 0; pass < 2; pass++)
+        for (int Pc : {160, 128, 112, 96, 80, 64, 48, 32}) {
             std::shared_ptr<const BclPlan> cached;
             {
                 sse_mesh *mm = const_cast<sse_mesh *>(mesh);
@@ -700,11 +735,60 @@ struct Engine : EngineBase {
             }
             if (!cached) continue;
             const size_t smem = bcl_smem_bytes<R>(*cached);
-            if (smem + 1024 > (size_t)smem_block) continue;
+            if (smem + 1024 + sizeof(BclJob<R>) + 64 > (size_t)smem_block) continue;
+            if (pass == 0 && 2 * (smem + 1024 + sizeof(BclJob<R>)) > (size_t)smem_sm) continue;
+            // both kernels hold a job descriptor in static shared memory
             CK(cudaFuncSetAttribute(bcl_fused_kernel_ptr<R>(),
-                                    cudaFuncAttributeMaxDynamicSharedMemorySize, smem_block));
+                                    cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    smem_block - (int)sizeof(BclJob<R>) - 64));
+            CK(cudaFuncSetAttribute(bcl_fused_batch_kernel_ptr<R>(),
+                                    cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    smem_block - (int)sizeof(BclJob<R>) - 64));
             return upload_bcl(*cached, smem);
         }
+        return SSE_OK;
+    }
+
+    // Plan the fused thickness stage (full columns only): patches of
+    // thick_cells_per_patch() consecutive cells, built once per mesh.
+    int plan_thick(const sse_mesh *mesh, int dev) {
+        const char *env = getenv("SSE_THICK_KERNEL");
+        if (env && strcmp(env, "unfused") == 0) return SSE_OK;
+        if (m.partial) return SSE_OK;
+        std::shared_ptr<const ThickPlan> pl;
+        {
+            sse_mesh *mm = const_cast<sse_mesh *>(mesh);
+            std::lock_guard<std::mutex> lk(mm->plan_mu);
+            if (!mm->thick_tried) {
+                auto fresh = std::make_shared<ThickPlan>();
+                if (!build_thick_plan(mesh->host, thick_cells_per_patch(), *fresh)) fresh.reset();
+                mm->thick_plan = fresh;
+                mm->thick_tried = true;
+            }
+            pl = mm->thick_plan;
+        }
+        if (!pl) return SSE_OK;
+        int smem_block = 0;
+        CK(cudaDeviceGetAttribute(&smem_block, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+        DThick t{};
+        t.P = pl->P; t.Pc = pl->Pc; t.maxEO = pl->maxEO; t.maxC1 = pl->maxC1;
+        if (thick_smem_bytes(t, p.nT, true, true, sizeof(R)) + 1024 + sizeof(ThickJob<R>) + 64 >
+            (size_t)smem_block)
+            return SSE_OK;
+        CK(cudaFuncSetAttribute(thick_fused_kernel_ptr<R>(),
+                                cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                smem_block - (int)sizeof(ThickJob<R>) - 64));
+        CK(cudaFuncSetAttribute(thick_fused_batch_kernel_ptr<R>(),
+                                cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                smem_block - (int)sizeof(ThickJob<R>) - 64));
+        t.cnt = A.upload(pl->cnt);
+        t.off_eo = A.upload(pl->off_eo); t.off_c1 = A.upload(pl->off_c1);
+        t.eogid = A.upload(pl->eogid); t.c1gid = A.upload(pl->c1gid);
+        t.o_e = A.upload(pl->o_e); t.o_o = A.upload(pl->o_o);
+        uA_e = A.alloc<R>(m.Ep);
+        if (A.failed) return SSE_ERR_OOM;
+        thk = t;
+        fused_th = true;
         return SSE_OK;
     }
 
@@ -868,6 +952,8 @@ struct Engine : EngineBase {
         int rc = plan_tiles(mesh, dev, nsm);
         if (rc) return rc;
         rc = plan_bcl(mesh, dev);
+        if (rc) return rc;
+        rc = plan_thick(mesh, dev);
         if (rc) return rc;
         CK(cudaStreamSynchronize(s));
         return SSE_OK;
@@ -1049,6 +1135,21 @@ struct Engine : EngineBase {
     // ---- pieces
     void bcl_stage(R *ubar, R *ut, R *hR, R *tr, const double *zeta, bool split, const R *utn,
                    double a, double b, double dt, R *out, R *G) {
+        if (fused && rec) {
+            LaunchRec<R> r1;
+            r1.cls = REC_COLFLUX;
+            r1.u.cf = ColfluxJob<R>{m, ubar, ut, hR, Fc, split ? 1 : 0, 0};
+            rec->push_back(r1);
+            LaunchRec<R> r2;
+            r2.cls = REC_BCL;
+            r2.smem = bcl.smem;
+            BclArgs<R> x{};
+            x.ubar = ubar; x.ut = ut; x.hR = hR; x.tr = tr; x.zeta = zeta; x.Fc = Fc;
+            x.ut_n = utn; x.a = (R)a; x.b = (R)b; x.dt = (R)dt; x.ut_out = out; x.G = G;
+            r2.u.bcl = BclJob<R>{m, p, bcl, x};
+            rec->push_back(r2);
+            return;
+        }
         if (fused) {
             // the column pre-pass (and the split at stage 1) counts as the edge
             // pre-pass class, the fused kernel as the baroclinic-edge class
@@ -1094,6 +1195,17 @@ struct Engine : EngineBase {
         a.u0 = bu0; a.ua = bua; a.uh = buh; a.z0 = bz0; a.za = bza; a.zh = bzh;
         a.tau = tau_dt / M; a.g = p.g; a.M = M; a.order = order; a.stall = inject_stall;
         last_Fz = Fz;
+        if (rec) {
+            LaunchRec<R> r;
+            r.cls = REC_BTR;
+            r.u.btr = a;
+            rec->push_back(r);
+            return cudaSuccess;
+        }
+        return issue_btr(a);
+    }
+    // the sub-cycle's launch on the state's own stream
+    cudaError_t issue_btr(const BtrArgs<R> &a) {
         // the barrier reset (a memset) sits outside the timed pair
         cudaError_t me = cudaMemsetAsync(barwords, 0, 2 * sizeof(unsigned int), s);
         if (me != cudaSuccess) return me;
@@ -1111,8 +1223,22 @@ struct Engine : EngineBase {
         a.hR = hR; a.zeta = zeta; a.Fcol = Fcol; a.ubA = ubA; a.utA = utA; a.ubB = ubB; a.utB = utB; a.wA = wA; a.wB = wB;
         a.Fz = Fz; a.ex1 = e1; a.ex2 = e2; a.cF = cF; a.cE = cE; a.cA = cA;
         a.recon = (recon != SSE_RECON_OFF); a.S_out = S_out; a.flux = flux;
+        if (fused_th && rec) {
+            LaunchRec<R> r;
+            r.cls = REC_TRANSPORT;
+            r.u.tr = TransportJob<R>{m, a, uA_e};
+            rec->push_back(r);
+            last_ta = a;
+            return;
+        }
         pbeg(SSE_K_TRANSPORT);
-        launch_transport<R>(m, a, s);
+        if (fused_th) {
+            // columns only; the thickness kernel forms the per-layer flux itself
+            launch_transport_cols<R>(m, a, uA_e, s);
+            last_ta = a;
+        } else {
+            launch_transport<R>(m, a, s);
+        }
         pend();
     }
 
@@ -1124,7 +1250,27 @@ struct Engine : EngineBase {
         t.a = a; t.b = b; t.dt = dt; t.h_out = h_out; t.hR_out = mixed ? hR_out : nullptr;
         t.tr_out = tr_out; t.zeta_out = zeta_out;
         pbeg(SSE_K_THICKNESS);
-        launch_thickness<R>(m, p, t, s);
+        if (fused_th) {
+            ThickFArgs<R> f{};
+            f.ubA = last_ta.ubA; f.utA = last_ta.utA; f.ubB = last_ta.ubB; f.utB = last_ta.utB;
+            f.wA = last_ta.wA; f.wB = last_ta.wB; f.uA = uA_e; f.Fcol = Fcol;
+            f.h_s = h_s; f.hR_s = hR_s; f.tr_s = tr_s; f.h_n = h_n; f.hR_n = hR_n; f.tr_n = tr_n;
+            f.a = a; f.b = b; f.dt = dt; f.h_out = h_out; f.hR_out = t.hR_out; f.tr_out = tr_out;
+            f.zeta_out = zeta_out;
+            const size_t smem = thick_smem_bytes(thk, p.nT, f.utB != nullptr, a != 0.0, sizeof(R));
+            if (rec) {
+                pend();
+                LaunchRec<R> r;
+                r.cls = REC_THICK;
+                r.smem = smem;
+                r.u.th = ThickJob<R>{m, p, thk, f};
+                rec->push_back(r);
+                return;
+            }
+            launch_thick_fused<R>(thk, m, p, f, smem, s);
+        } else {
+            launch_thickness<R>(m, p, t, s);
+        }
         pend();
     }
 
@@ -1296,18 +1442,31 @@ struct Engine : EngineBase {
     }
 };
 
-template <class R>
-__global__ void k_combine_G(const R *__restrict__ a, const R *__restrict__ b,
-                            const R *__restrict__ c, R *__restrict__ out, double wa, double wb,
-                            double wc, int n) {
-    const int e = blockIdx.x * blockDim.x + threadIdx.x;
-    if (e >= n) return;
-    out[e] = (R)(wa * (double)a[e] + wb * (double)b[e] + wc * (double)c[e]);
+// the Interp forcing of the corrector, Gw = w0 G0 + w1 G1 + w2 G2; the single
+// and the batched kernel run the same per-edge function on a shared-memory
+// copy of their descriptor (the same bits alone or in a batch)
+template <class R> __device__ __forceinline__ void combine_edge(const CombineJob<R> &J, int e) {
+    if (e >= J.n) return;
+    J.out[e] = (R)(J.wa * (double)J.a[e] + J.wb * (double)J.b[e] + J.wc * (double)J.c[e]);
+}
+template <class R> __global__ void k_combine_G(const CombineJob<R> job) {
+    __shared__ CombineJob<R> J;
+    if (threadIdx.x == 0) J = job;
+    __syncthreads();
+    combine_edge<R>(J, blockIdx.x * blockDim.x + threadIdx.x);
 }
 
 template <class R> void Engine<R>::combine_G(double w0, double w1, double w2) {
+    if (rec) {
+        LaunchRec<R> r;
+        r.cls = REC_COMBINE;
+        r.u.cmb = CombineJob<R>{G0, G1, G2, Gw, w0, w1, w2, m.E, 0};
+        rec->push_back(r);
+        return;
+    }
     pbeg(SSE_K_COMBINE);
-    k_combine_G<R><<<(m.E + 255) / 256, 256, 0, s>>>(G0, G1, G2, Gw, w0, w1, w2, m.E);
+    k_combine_G<R><<<(m.E + 255) / 256, 256, 0, s>>>(CombineJob<R>{G0, G1, G2, Gw, w0, w1, w2,
+                                                                   m.E, 0});
     pend();
 }
 
@@ -1344,6 +1503,7 @@ static int make_state(const sse_mesh *mesh, const sse_params *prm, const sse_tun
     if (dev != mesh->device) return SSE_ERR_INVALID_ARG;
     sse_state *st = new (std::nothrow) sse_state();
     if (!st) return SSE_ERR_OOM;
+    st->device = dev;
     const int pc = (tun && tun->patch_cells > 0) ? tun->patch_cells : 0;
     int rc;
     size_t b = 0;
@@ -1574,6 +1734,251 @@ extern "C" int sse_step(sse_state *st, int order, double dt, int n_substeps, int
     int i = 0, rc = SSE_OK;
     for (; !rc && i + 2 <= n_steps; i += 2) rc = st->eng->step2(order, dt, n_substeps);
     for (; !rc && i < n_steps; i++) rc = st->eng->step(order, dt, n_substeps);
+    nvtxRangePop();
+    return rc;
+}
+
+// ---------------------------------------------------------------------------
+// Batched steps: several states advance in lock-step; the i-th launch of every
+// state's step (recorded by Engine::step with `rec` set) is issued as one grid
+// for the 3-D kernels, and each state's sub-cycle runs on its own stream
+// between fork and join events.  Per-state arithmetic is unchanged.
+// ---------------------------------------------------------------------------
+template <class R>
+__global__ void k_combine_G_batch(const CombineJob<R> *__restrict__ jobs,
+                                  const int *__restrict__ first, int njobs) {
+    int lo = 0, hi = njobs - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (first[mid] <= (int)blockIdx.x) lo = mid; else hi = mid - 1;
+    }
+    __shared__ CombineJob<R> J;
+    if (threadIdx.x == 0) J = jobs[lo];
+    __syncthreads();
+    combine_edge<R>(J, (blockIdx.x - first[lo]) * blockDim.x + threadIdx.x);
+}
+
+namespace {
+// staging of the job descriptors: two regions (steps alternate), pinned host
+// and device, grown on demand; one per (device, stream), used under its mutex.
+// Work on one stream is ordered, so the upload of step s + 2 into a region
+// follows the kernels of step s that read it; batches on other streams have
+// arenas of their own.
+struct BatchArena {
+    std::mutex mu;
+    size_t cap = 0;
+    char *host[2] = {nullptr, nullptr};
+    char *dev[2] = {nullptr, nullptr};
+    cudaEvent_t uploaded[2] = {nullptr, nullptr};
+    cudaEvent_t fork = nullptr;
+    std::vector<cudaEvent_t> join;
+    int reserve(size_t bytes, int n, cudaStream_t ms) {
+        if (!fork && cudaEventCreateWithFlags(&fork, cudaEventDisableTiming) != cudaSuccess)
+            return SSE_ERR_CUDA;
+        while ((int)join.size() < n + 1) {
+            cudaEvent_t e;
+            if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) return SSE_ERR_CUDA;
+            join.push_back(e);
+        }
+        if (bytes <= cap) return SSE_OK;
+        // the old regions may still feed kernels queued on this stream
+        if (cap && cudaStreamSynchronize(ms) != cudaSuccess) return SSE_ERR_CUDA;
+        for (int b = 0; b < 2; b++) {
+            if (uploaded[b]) cudaEventSynchronize(uploaded[b]);
+            if (host[b]) cudaFreeHost(host[b]);
+            if (dev[b]) cudaFree(dev[b]);
+            host[b] = nullptr; dev[b] = nullptr;
+        }
+        cap = 0;
+        for (int b = 0; b < 2; b++) {
+            if (cudaMallocHost(&host[b], bytes) != cudaSuccess || cudaMalloc(&dev[b], bytes) != cudaSuccess)
+                return SSE_ERR_OOM;
+            if (!uploaded[b] && cudaEventCreateWithFlags(&uploaded[b], cudaEventDisableTiming) != cudaSuccess)
+                return SSE_ERR_CUDA;
+        }
+        cap = bytes;
+        return SSE_OK;
+    }
+};
+std::mutex g_arena_mu;
+std::map<std::pair<int, cudaStream_t>, std::unique_ptr<BatchArena>> g_arenas;
+
+size_t align64(size_t x) { return (x + 63) / 64 * 64; }
+
+template <class R> size_t job_size(int cls) {
+    switch (cls) {
+    case REC_COLFLUX: return sizeof(ColfluxJob<R>);
+    case REC_BCL: return sizeof(BclJob<R>);
+    case REC_TRANSPORT: return sizeof(TransportJob<R>);
+    case REC_THICK: return sizeof(ThickJob<R>);
+    case REC_COMBINE: return sizeof(CombineJob<R>);
+    default: return 0;
+    }
+}
+template <class R> const void *job_ptr(const LaunchRec<R> &r) {
+    switch (r.cls) {
+    case REC_COLFLUX: return &r.u.cf;
+    case REC_BCL: return &r.u.bcl;
+    case REC_TRANSPORT: return &r.u.tr;
+    case REC_THICK: return &r.u.th;
+    case REC_COMBINE: return &r.u.cmb;
+    default: return nullptr;
+    }
+}
+// blocks of one state's launch of class cls
+template <class R> int job_blocks(const LaunchRec<R> &r) {
+    switch (r.cls) {
+    case REC_COLFLUX: return colflux_blocks(r.u.cf.m);
+    case REC_BCL: return r.u.bcl.t.P;
+    case REC_TRANSPORT: return (r.u.tr.m.E + 127) / 128;
+    case REC_THICK: return r.u.th.t.P;
+    case REC_COMBINE: return (r.u.cmb.n + 255) / 256;
+    default: return 0;
+    }
+}
+
+template <class R>
+int step_batch_t(std::vector<Engine<R> *> &E, int order, const double *dt, const int32_t *M,
+                 int n_steps, cudaStream_t ms) {
+    const int n = (int)E.size();
+    int dev = 0;
+    CK(cudaGetDevice(&dev));
+    BatchArena *A = nullptr;
+    {
+        std::lock_guard<std::mutex> lk(g_arena_mu);
+        auto &slot = g_arenas[std::make_pair(dev, ms)];
+        if (!slot) slot.reset(new BatchArena());
+        A = slot.get();
+    }
+    std::lock_guard<std::mutex> lk(A->mu);
+    std::vector<std::vector<LaunchRec<R>>> rec(n);
+    for (int st = 0; st < n_steps; st++) {
+        // record the step of every state (this also advances their buffers)
+        for (int i = 0; i < n; i++) {
+            rec[i].clear();
+            E[i]->rec = &rec[i];
+            const int rc = E[i]->step(order, dt[i], M[i]);
+            E[i]->rec = nullptr;
+            if (rc) return rc;
+        }
+        const size_t nl = rec[0].size();
+        for (int i = 1; i < n; i++) {
+            if (rec[i].size() != nl) return SSE_ERR_UNSUPPORTED;
+            for (size_t k = 0; k < nl; k++)
+                if (rec[i][k].cls != rec[0][k].cls) return SSE_ERR_UNSUPPORTED;
+        }
+        // lay out the step's job arrays: per launch, n descriptors and n + 1 block starts
+        std::vector<size_t> off(nl, 0), foff(nl, 0);
+        size_t bytes = 0;
+        for (size_t k = 0; k < nl; k++) {
+            const size_t js = job_size<R>(rec[0][k].cls);
+            if (!js) continue;
+            off[k] = bytes;
+            bytes = align64(bytes + js * n);
+            foff[k] = bytes;
+            bytes = align64(bytes + sizeof(int) * (n + 1));
+        }
+        int rc = A->reserve(std::max<size_t>(bytes, 64), n, ms);
+        if (rc) return rc;
+        const int b = st & 1;
+        // the host region may still feed the upload of two steps ago
+        CK(cudaEventSynchronize(A->uploaded[b]));
+        std::vector<int> blocks(nl, 0);
+        for (size_t k = 0; k < nl; k++) {
+            const size_t js = job_size<R>(rec[0][k].cls);
+            if (!js) continue;
+            int *first = (int *)(A->host[b] + foff[k]);
+            int acc = 0;
+            for (int i = 0; i < n; i++) {
+                memcpy(A->host[b] + off[k] + js * i, job_ptr<R>(rec[i][k]), js);
+                first[i] = acc;
+                acc += job_blocks<R>(rec[i][k]);
+            }
+            first[n] = acc;
+            blocks[k] = acc;
+        }
+        CK(cudaMemcpyAsync(A->dev[b], A->host[b], bytes, cudaMemcpyHostToDevice, ms));
+        CK(cudaEventRecord(A->uploaded[b], ms));
+        for (size_t k = 0; k < nl; k++) {
+            const int cls = rec[0][k].cls;
+            const char *d = A->dev[b];
+            if (cls == REC_BTR) {
+                // fork: every sub-cycle on its own state's stream, then join
+                CK(cudaEventRecord(A->fork, ms));
+                for (int i = 0; i < n; i++) {
+                    CK(cudaStreamWaitEvent(E[i]->s, A->fork, 0));
+                    CK(E[i]->issue_btr(rec[i][k].u.btr));
+                    CK(cudaEventRecord(A->join[i], E[i]->s));
+                }
+                for (int i = 0; i < n; i++) CK(cudaStreamWaitEvent(ms, A->join[i], 0));
+                continue;
+            }
+            const int *first = (const int *)(d + foff[k]);
+            size_t smem = 0;
+            for (int i = 0; i < n; i++) smem = std::max(smem, rec[i][k].smem);
+            switch (cls) {
+            case REC_COLFLUX:
+                launch_colflux_batch<R>((const ColfluxJob<R> *)(d + off[k]), first, n, blocks[k], ms);
+                break;
+            case REC_BCL:
+                launch_bcl_fused_batch<R>((const BclJob<R> *)(d + off[k]), first, n, blocks[k], smem, ms);
+                break;
+            case REC_TRANSPORT:
+                launch_transport_cols_batch<R>((const TransportJob<R> *)(d + off[k]), first, n,
+                                               blocks[k], ms);
+                break;
+            case REC_THICK:
+                launch_thick_fused_batch<R>((const ThickJob<R> *)(d + off[k]), first, n, blocks[k],
+                                            smem, ms);
+                break;
+            case REC_COMBINE:
+                k_combine_G_batch<R><<<blocks[k], 256, 0, ms>>>((const CombineJob<R> *)(d + off[k]),
+                                                                first, n);
+                break;
+            }
+            cudaError_t e = cudaGetLastError();
+            if (e != cudaSuccess) {
+                fprintf(stderr, "libsse: batched launch failed: %s\n", cudaGetErrorString(e));
+                return SSE_ERR_CUDA;
+            }
+        }
+    }
+    // later work on each state's own stream follows the batch
+    CK(cudaEventRecord(A->join[n], ms));
+    for (int i = 0; i < n; i++) CK(cudaStreamWaitEvent(E[i]->s, A->join[n], 0));
+    return SSE_OK;
+}
+}  // namespace
+
+extern "C" int sse_step_batch(sse_state *const *states, int n, int order, const double *dt,
+                              const int32_t *n_substeps, int n_steps, void *cuda_stream) {
+    if (!states || n < 1 || !dt || !n_substeps || (order != 2 && order != 3) || n_steps < 0)
+        return SSE_ERR_INVALID_ARG;
+    for (int i = 0; i < n; i++) {
+        if (!states[i] || !(dt[i] > 0) || !isfinite(dt[i]) || n_substeps[i] < 1)
+            return SSE_ERR_INVALID_ARG;
+        for (int j = 0; j < i; j++)
+            if (states[j] == states[i]) return SSE_ERR_INVALID_ARG;
+    }
+    if (n_steps == 0) return SSE_OK;
+    nvtxRangePushA("sse_step_batch");
+    int rc = SSE_ERR_UNSUPPORTED;
+    auto run = [&](auto *proto) {
+        using Eng = std::remove_pointer_t<decltype(proto)>;
+        std::vector<Eng *> E;
+        for (int i = 0; i < n; i++) {
+            Eng *e = dynamic_cast<Eng *>(states[i]->eng.get());
+            if (!e || !e->fused || !e->fused_th || e->prof || e->inject_stall) return SSE_ERR_UNSUPPORTED;
+            E.push_back(e);
+        }
+        for (int i = 1; i < n; i++)
+            if (states[i]->device != states[0]->device) return SSE_ERR_INVALID_ARG;
+        return step_batch_t(E, order, dt, n_substeps, n_steps, (cudaStream_t)cuda_stream);
+    };
+    if (dynamic_cast<Engine<float> *>(states[0]->eng.get()))
+        rc = run((Engine<float> *)nullptr);
+    else if (dynamic_cast<Engine<double> *>(states[0]->eng.get()))
+        rc = run((Engine<double> *)nullptr);
     nvtxRangePop();
     return rc;
 }

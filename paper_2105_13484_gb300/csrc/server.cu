@@ -17,6 +17,7 @@
 #include <atomic>
 #include <chrono>
 #include <condition_variable>
+#include <algorithm>
 #include <deque>
 #include <mutex>
 #include <thread>
@@ -40,7 +41,7 @@ struct Req {
     double *u_out = nullptr, *h_out = nullptr, *tr_out = nullptr;
     size_t footprint = 0;
     sse_tuning tun{};
-    int steps_done = 0, inflight = 0;
+    int steps_done = 0, inflight = 0, inflight_alone = 0;
     sse_state *st = nullptr;
     cudaStream_t s = nullptr;
     cudaEvent_t ev = nullptr;
@@ -54,10 +55,20 @@ double now_s(std::chrono::steady_clock::time_point t0) {
 
 }  // namespace
 
+// a packed group: the active requests of one precision and order advanced
+// together by sse_step_batch (3-D kernels of all of them in one launch)
+struct PackGroup {
+    cudaStream_t s = nullptr;
+    cudaEvent_t ev = nullptr;
+    std::vector<Req *> members;   // the members of the round in flight
+    int k = 0;                    // steps of the round in flight (0: idle)
+};
+
 struct sse_server {
     int device = 0;
     size_t budget = 0, used = 0, peak = 0;
-    int max_active = 1, chunk = 1, tune = -1;
+    int max_active = 1, chunk = 1, tune = -1, flags = 0;
+    std::unordered_map<int, PackGroup> groups;    // by precision * 4 + order
     std::chrono::steady_clock::time_point t0;
     std::mutex mu;
     std::condition_variable cv_work, cv_done;
@@ -127,6 +138,103 @@ int finish(Req *r) {
     return rc;
 }
 
+// release a finished or failed request's slot
+void retire(sse_server *S, Req *r, int rc) {
+    if (r->st) {
+        sse_state_destroy(r->st);
+        r->st = nullptr;
+    }
+    S->streams.push_back(r->s);
+    S->events.push_back(r->ev);
+    r->s = nullptr;
+    r->ev = nullptr;
+    std::lock_guard<std::mutex> lk(S->mu);
+    S->used -= r->footprint;
+    S->n_active--;
+    r->status = rc ? rc : SSE_REQ_DONE;
+    r->t_done = now_s(S->t0);
+    S->cv_done.notify_all();
+}
+
+// Packed mode: the active requests of each (precision, order) advance in
+// rounds of k steps, all of them in one sse_step_batch call on the group's
+// stream; between rounds finished requests retire and new ones join.
+// Requests whose states cannot be packed step alone, as in the default mode.
+bool packed_round(sse_server *S) {
+    bool progressed = false;
+    // rounds in flight: account for the finished ones
+    for (auto &kv : S->groups) {
+        PackGroup &g = kv.second;
+        if (!g.k) continue;
+        const cudaError_t q = cudaEventQuery(g.ev);
+        if (q == cudaErrorNotReady) continue;
+        for (Req *r : g.members) { r->steps_done += g.k; r->inflight = 0; }
+        g.members.clear();
+        g.k = 0;
+        progressed = true;
+    }
+    // requests stepping alone (not packable) in flight
+    for (Req *r : S->active) {
+        if (r->inflight && r->inflight_alone && cudaEventQuery(r->ev) != cudaErrorNotReady) {
+            r->steps_done += r->inflight;
+            r->inflight = 0;
+            r->inflight_alone = 0;
+            progressed = true;
+        }
+    }
+    // retire the finished
+    for (size_t i = 0; i < S->active.size();) {
+        Req *r = S->active[i];
+        if (r->inflight || r->steps_done < r->n_steps) { i++; continue; }
+        const int rc = finish(r);
+        S->active.erase(S->active.begin() + i);
+        retire(S, r, rc);
+        progressed = true;
+    }
+    // start the next round of every idle group
+    std::unordered_map<int, std::vector<Req *>> ready;
+    for (Req *r : S->active)
+        if (!r->inflight) ready[r->prm.precision * 4 + r->order].push_back(r);
+    for (auto &kv : ready) {
+        PackGroup &g = S->groups[kv.first];
+        if (g.k) continue;   // still running; these requests wait for it
+        if (!g.s && (cudaStreamCreateWithFlags(&g.s, cudaStreamNonBlocking) != cudaSuccess ||
+                     cudaEventCreateWithFlags(&g.ev, cudaEventDisableTiming) != cudaSuccess))
+            continue;
+        std::vector<Req *> &rs = kv.second;
+        int k = S->chunk;
+        for (Req *r : rs) k = std::min(k, r->n_steps - r->steps_done);
+        std::vector<sse_state *> sts;
+        std::vector<double> dts;
+        std::vector<int32_t> Ms;
+        for (Req *r : rs) { sts.push_back(r->st); dts.push_back(r->dt); Ms.push_back(r->M); }
+        int rc = sse_step_batch(sts.data(), (int)sts.size(), rs[0]->order, dts.data(), Ms.data(),
+                                k, g.s);
+        if (rc == SSE_OK && cudaEventRecord(g.ev, g.s) == cudaSuccess) {
+            g.members = rs;
+            g.k = k;
+            for (Req *r : rs) r->inflight = k;
+            progressed = true;
+            continue;
+        }
+        // not packable: each steps alone on its own stream
+        for (Req *r : rs) {
+            const int kk = std::min(S->chunk, r->n_steps - r->steps_done);
+            int rr = sse_step(r->st, r->order, r->dt, r->M, kk);
+            if (!rr && cudaEventRecord(r->ev, r->s) != cudaSuccess) rr = SSE_ERR_CUDA;
+            if (rr) {
+                S->active.erase(std::find(S->active.begin(), S->active.end(), r));
+                retire(S, r, rr);
+            } else {
+                r->inflight = kk;
+                r->inflight_alone = 1;
+            }
+            progressed = true;
+        }
+    }
+    return progressed;
+}
+
 void worker_loop(sse_server *S) {
     cudaSetDevice(S->device);
     for (;;) {
@@ -158,6 +266,14 @@ void worker_loop(sse_server *S) {
             S->active.push_back(r);
         }
         bool progressed = !admit.empty();
+        if (S->flags & SSE_SERVER_PACKED) {
+            progressed = packed_round(S) || progressed;
+            if (!progressed) {
+                std::unique_lock<std::mutex> lk(S->mu);
+                S->cv_work.wait_for(lk, std::chrono::microseconds(50));
+            }
+            continue;
+        }
         for (size_t i = 0; i < S->active.size();) {
             Req *r = S->active[i];
             if (r->inflight) {
@@ -208,16 +324,29 @@ void worker_loop(sse_server *S) {
     }
     for (cudaStream_t s : S->streams) cudaStreamDestroy(s);
     for (cudaEvent_t e : S->events) cudaEventDestroy(e);
+    for (auto &kv : S->groups) {
+        if (kv.second.s) cudaStreamDestroy(kv.second.s);
+        if (kv.second.ev) cudaEventDestroy(kv.second.ev);
+    }
     S->streams.clear();
     S->events.clear();
+    S->groups.clear();
 }
 
 }  // namespace
 
 extern "C" int sse_server_create(int device, size_t hbm_budget_bytes, int max_active,
                                  int steps_per_launch, int tune_objective, sse_server **out) {
+    return sse_server_create_ex(device, hbm_budget_bytes, max_active, steps_per_launch,
+                                tune_objective, 0, out);
+}
+
+extern "C" int sse_server_create_ex(int device, size_t hbm_budget_bytes, int max_active,
+                                    int steps_per_launch, int tune_objective, int flags,
+                                    sse_server **out) {
     if (!out || max_active < 1 || steps_per_launch < 1 || hbm_budget_bytes == 0 ||
-        tune_objective < -1 || tune_objective > SSE_TUNE_THROUGHPUT)
+        tune_objective < -1 || tune_objective > SSE_TUNE_THROUGHPUT ||
+        (flags & ~SSE_SERVER_PACKED))
         return SSE_ERR_INVALID_ARG;
     *out = nullptr;
     int ndev = 0;
@@ -230,6 +359,7 @@ extern "C" int sse_server_create(int device, size_t hbm_budget_bytes, int max_ac
     S->max_active = max_active;
     S->chunk = steps_per_launch;
     S->tune = tune_objective;
+    S->flags = flags;
     S->t0 = std::chrono::steady_clock::now();
     // keep freed state memory in the device's pool for the next request
     cudaMemPool_t pool;

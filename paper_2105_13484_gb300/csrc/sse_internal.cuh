@@ -183,6 +183,23 @@ template <class R> struct BclArgs {
     R a, b, dt;                    // out = a ut_n + b (ut1 - dt G)
     R *ut_out, *G;
 };
+// one state's share of a batched launch
+template <class R> struct BclJob { DMesh m; DParams p; DBcl<R> t; BclArgs<R> a; };
+template <class R> struct ColfluxJob {
+    DMesh m;
+    R *ubar, *ut;
+    const R *hR;
+    R *Fc;
+    int split, pad_;
+};
+template <class R>
+void launch_colflux_batch(const ColfluxJob<R> *jobs, const int *first, int njobs, int blocks,
+                          cudaStream_t s);
+int colflux_blocks(const DMesh &m);
+template <class R>
+void launch_bcl_fused_batch(const BclJob<R> *jobs, const int *first, int njobs, int blocks,
+                            size_t smem, cudaStream_t s);
+template <class R> const void *bcl_fused_batch_kernel_ptr();
 struct BclPlan;
 template <class R> size_t bcl_smem_bytes(const BclPlan &plan);
 int bcl_max_edges_per_patch();
@@ -281,6 +298,49 @@ template <class R> struct ThickArgs {
 };
 template <class R>
 void launch_thickness(const DMesh &m, const DParams &p, const ThickArgs<R> &a, cudaStream_t s);
+
+// ---- the fused thickness/tracer stage (thick_fused.cu); plan from build_thick_plan
+struct DThick {
+    int P = 0, Pc = 0, maxEO = 0, maxC1 = 0;
+    const int *cnt = nullptr;            // [P][4]
+    const int *off_eo, *off_c1;          // [P + 1]
+    const int *eogid, *c1gid;            // local -> internal
+    const unsigned short *o_e, *o_o;     // [P][6][Pc]
+};
+template <class R> struct ThickFArgs {
+    // transport velocity v = wA (ubA + utA) + wB (ubB + utB) + u^A (utB may be null)
+    const R *ubA, *utA, *ubB, *utB;
+    double wA, wB;
+    const R *uA;              // [Ep] from k_transport_cols
+    const double *Fcol;       // [Ep] column-integrated flux (FP64)
+    const double *h_s;        // stage thickness (FP64) and its tendency-precision copy
+    const R *hR_s, *tr_s;
+    const double *h_n;        // h^n for the convex combination (unused when a == 0)
+    const R *hR_n, *tr_n;
+    double a, b, dt;          // out = a (h^n) + b (FE result)
+    double *h_out;
+    R *hR_out;                // tendency-precision copy of h_out (SSE_MIXED) or null
+    R *tr_out;
+    double *zeta_out;
+};
+template <class R> struct ThickJob { DMesh m; DParams p; DThick t; ThickFArgs<R> a; };
+template <class R> struct TransportJob { DMesh m; TransportArgs<R> a; R *uA; };
+template <class R>
+void launch_transport_cols_batch(const TransportJob<R> *jobs, const int *first, int njobs,
+                                 int blocks, cudaStream_t s);
+template <class R>
+void launch_thick_fused_batch(const ThickJob<R> *jobs, const int *first, int njobs, int blocks,
+                              size_t smem, cudaStream_t s);
+template <class R> const void *thick_fused_batch_kernel_ptr();
+size_t thick_smem_bytes(const DThick &plan, int nT, bool twoB, bool comb, size_t sR);
+int thick_cells_per_patch();
+template <class R> const void *thick_fused_kernel_ptr();
+template <class R>
+void launch_transport_cols(const DMesh &m, const TransportArgs<R> &a, R *uA, cudaStream_t s);
+template <class R>
+void launch_thick_fused(const DThick &t, const DMesh &m, const DParams &p, const ThickFArgs<R> &a,
+                        size_t smem, cudaStream_t s);
+
 
 // layout conversion: host-order [n][L] in precision H (FP64 or FP32) <->
 // device layer-major R [L][np]

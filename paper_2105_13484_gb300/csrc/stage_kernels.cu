@@ -294,7 +294,8 @@ __global__ void __launch_bounds__(128, MINB) k_bcl_edge(DMesh m, DParams p, cons
     const R invdc = c.invdc[e], invdv = c.invdv[e];
     const R ub = ubar[e];
     const PhysR<R> &q = phys<R>(p);
-    const R gzeta = q.zcoef * (R)(zeta[c2] - zeta[c1]) * invdc;
+    const R dzeta = (R)(zeta[c2] - zeta[c1]);   // the difference taken in FP64
+    const R gzeta = q.zcoef * dzeta * invdc;
     const R g = q.g, inv_rho0 = q.inv_rho0, nu_h = q.nu_h, nu_v = q.nu_v, nu_4 = q.nu_4;
     const R cdrag = q.c_drag;
     const R *wnd = wind_over_rho0<R>(p);
@@ -304,19 +305,25 @@ __global__ void __launch_bounds__(128, MINB) k_bcl_edge(DMesh m, DParams p, cons
     const int K = PB ? m.ke[e] : L;
     R ut_cur = ut[e];
     R u_cur = ub + ut_cur;
-    R he_cur = R(0.5) * (ld(hR + c1) + ld(hR + c2));
+    R h1_cur = ld(hR + c1), h2_cur = ld(hR + c2);
+    R he_cur = R(0.5) * (h1_cur + h2_cur);
+    // pressure gradient from differences across the edge accumulated down the
+    // column: dA = sum_{l<k} (rho' h)_c2 - (rho' h)_c1, dH = sum_{l<k} h_c2 - h_c1
+    R dA = R(0), dH = R(0);
     // the top interface of layer k is the bottom interface of layer k - 1: its
     // shear D_zt(u) and edge w carry over from the previous layer (0 at k = 0)
     R Dk = R(0), wk = R(0);
     R num = R(0), den = R(0), speed_b = R(0);
     for (int k = 0; k < K; k++) {
         const int xe = k * Ep + e;
-        R ut_next = R(0), u_next = R(0), he_next = R(0);
+        R ut_next = R(0), u_next = R(0), h1_next = R(0), h2_next = R(0);
         if (k + 1 < K) {
             ut_next = ut[xe + Ep];
             u_next = ub + ut_next;
-            he_next = R(0.5) * (ld(hR + (k + 1) * Cp + c1) + ld(hR + (k + 1) * Cp + c2));
+            h1_next = ld(hR + (k + 1) * Cp + c1);
+            h2_next = ld(hR + (k + 1) * Cp + c2);
         }
+        const R he_next = R(0.5) * (h1_next + h2_next);
         // potential-vorticity flux
         const R qk = b.hq[xe].y;
         R Q = R(0);
@@ -329,7 +336,15 @@ __global__ void __launch_bounds__(128, MINB) k_bcl_edge(DMesh m, DParams p, cons
         const int x1 = k * Cp + c1, x2 = k * Cp + c2;
         const V4<R> A = b.cq[x1], B = b.cq[x2];    // (K, p', rho', z_mid) of both cells
         const R gradK = (B.x - A.x) * invdc;
-        const R pgf = ((B.y - A.y) + g * (R(0.5) * (A.z + B.z)) * (B.w - A.w)) * invdc * inv_rho0;
+        // p'_2 - p'_1 and z_2 - z_1 (z = zeta - sum_{l<k} h_l - h_k / 2), the
+        // same quantities as the differences of the two columns' values (Eq.
+        // hydrocon) without cancelling two O(g rho' H) sums
+        const R rh = B.z * h2_cur - A.z * h1_cur;
+        const R dp = g * (dA + R(0.5) * rh);
+        const R dz = dzeta - dH - R(0.5) * (h2_cur - h1_cur);
+        const R pgf = (dp + g * (R(0.5) * (A.z + B.z)) * dz) * invdc * inv_rho0;
+        dA += rh;
+        dH += h2_cur - h1_cur;
         // vertical advection and viscosity at the top (k) and bottom (k+1) interfaces
         R Dk1 = R(0), wk1 = R(0);
         if (k + 1 < K) {
@@ -371,6 +386,7 @@ __global__ void __launch_bounds__(128, MINB) k_bcl_edge(DMesh m, DParams p, cons
         ut_out[xe] = ut1;
         Dk = Dk1; wk = wk1;
         ut_cur = ut_next; u_cur = u_next; he_cur = he_next;
+        h1_cur = h1_next; h2_cur = h2_next;
     }
     const R G = num / den / dt;
     Gout[e] = G;

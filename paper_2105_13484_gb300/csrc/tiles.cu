@@ -80,6 +80,20 @@ void bisect(const std::vector<std::vector<int>> &adj, std::vector<int> cells, in
 
 }  // namespace
 
+std::vector<int> partition_cells(const HostMesh &hm, int P) {
+    const int C = hm.C;
+    std::vector<std::vector<int>> adj(C);
+    for (int e = 0; e < hm.E; e++) {
+        adj[hm.c1[e]].push_back(hm.c2[e]);
+        adj[hm.c2[e]].push_back(hm.c1[e]);
+    }
+    std::vector<int> owner(C, -1), mask(C, 0), da(C), db(C), all(C);
+    std::iota(all.begin(), all.end(), 0);
+    int next = 0, tagctr = 0;
+    bisect(adj, all, P, owner, next, mask, tagctr, da, db);
+    return owner;
+}
+
 bool tile_stencil_ok(const HostMesh &hm) {
     for (int e = 0; e < hm.E; e++)
         for (int j = 0; j < hm.neoe[e]; j++) {
@@ -255,13 +269,11 @@ bool build_bcl_plan(const HostMesh &hm, int Pc, int max_e0, int max_c1, BclPlan 
     plan.Pc = Pc;
     plan.P = (C + Pc - 1) / Pc;
     const int P = plan.P;
-    // owned edges: edges are numbered by their lower cell, so each patch's run
-    // is contiguous
-    std::vector<int> e_first(P + 1, E);
-    for (int e = E - 1; e >= 0; e--) e_first[std::min(hm.c1[e], hm.c2[e]) / Pc] = e;
-    for (int p = P - 1; p >= 0; p--) e_first[p] = std::min(e_first[p], e_first[p + 1]);
-    for (int e = 1; e < E; e++)
-        if (std::min(hm.c1[e], hm.c2[e]) < std::min(hm.c1[e - 1], hm.c2[e - 1])) return false;
+    // compact patches: a recursive bisection of the cell graph into P parts;
+    // an edge belongs to the patch of its lower-numbered cell
+    plan.owner = partition_cells(hm, P);
+    std::vector<std::vector<int>> own_e(P);
+    for (int e = 0; e < E; e++) own_e[plan.owner[std::min(hm.c1[e], hm.c2[e])]].push_back(e);
     std::vector<int> le(E, -1), lc(C, -1), lv(V, -1);
     for (auto *o : {&plan.off_e0, &plan.off_e1, &plan.off_e2, &plan.off_c1, &plan.off_c2,
                     &plan.off_v})
@@ -275,12 +287,11 @@ bool build_bcl_plan(const HostMesh &hm, int Pc, int max_e0, int max_c1, BclPlan 
             std::sort(x.begin(), x.end());
             for (int y : x) fn(y);
         };
-        const int e0a = e_first[p], e0b = e_first[p + 1];
-        for (int e = e0a; e < e0b; e++) add_e(e);
+        for (int e : own_e[p]) add_e(e);
         const int nE0 = (int)Ed.size();
         {   // C1: the cells of the owned edges
             std::vector<int> x;
-            for (int e = e0a; e < e0b; e++) { x.push_back(hm.c1[e]); x.push_back(hm.c2[e]); }
+            for (int e : own_e[p]) { x.push_back(hm.c1[e]); x.push_back(hm.c2[e]); }
             sorted_add(x, add_c);
         }
         const int nC1 = (int)Cd.size();
@@ -332,7 +343,7 @@ bool build_bcl_plan(const HostMesh &hm, int Pc, int max_e0, int max_c1, BclPlan 
             }
         }
         if (!ok) { reset(); return false; }
-        plan.cnt.insert(plan.cnt.end(), {nE0, nE1, nE2, nC1, nC2, nV, e0a, 0});
+        plan.cnt.insert(plan.cnt.end(), {nE0, nE1, nE2, nC1, nC2, nV, 0, 0});
         plan.maxE0 = std::max(plan.maxE0, nE0); plan.maxE1 = std::max(plan.maxE1, nE1);
         plan.maxE2 = std::max(plan.maxE2, nE2); plan.maxC1 = std::max(plan.maxC1, nC1);
         plan.maxC2 = std::max(plan.maxC2, nC2); plan.maxV = std::max(plan.maxV, nV);
@@ -411,6 +422,72 @@ bool build_bcl_plan(const HostMesh &hm, int Pc, int max_e0, int max_c1, BclPlan 
         plan.off_c1.push_back(plan.off_c1.back() + nC1);
         plan.off_c2.push_back(plan.off_c2.back() + nC2);
         plan.off_v.push_back(plan.off_v.back() + nV);
+        reset();
+    }
+    return true;
+}
+
+bool build_thick_plan(const HostMesh &hm, int Pc, ThickPlan &plan) {
+    const int C = hm.C, E = hm.E;
+    if (Pc < 1) return false;
+    for (int c = 0; c < C; c++) if (hm.neoc[c] > BCL_NCEP) return false;
+    plan = ThickPlan();
+    plan.Pc = Pc;
+    // compact patches of at most Pc cells: a recursive bisection into parts
+    // of about 31/32 Pc cells (the bisection balances the parts to within a few
+    // cells)
+    plan.P = (int)(((long long)C * 32 + 31LL * Pc - 1) / (31LL * Pc));
+    plan.owner = partition_cells(hm, plan.P);
+    std::vector<std::vector<int>> own_c(plan.P);
+    for (int c = 0; c < C; c++) own_c[plan.owner[c]].push_back(c);
+    for (const auto &o : own_c) if ((int)o.size() > Pc) return false;
+    std::vector<int> le(E, -1), lc(C, -1);
+    plan.off_eo.push_back(0);
+    plan.off_c1.push_back(0);
+    for (int p = 0; p < plan.P; p++) {
+        const std::vector<int> &own = own_c[p];
+        const int nO = (int)own.size();
+        std::vector<int> Ed, Cd;
+        for (int l = 0; l < nO; l++) { lc[own[l]] = l; Cd.push_back(own[l]); }
+        std::vector<int> x;
+        for (int l = 0; l < nO; l++)
+            for (int j = 0; j < hm.neoc[own[l]]; j++) x.push_back(hm.eoc[(size_t)own[l] * hm.maxE + j]);
+        std::sort(x.begin(), x.end());
+        x.erase(std::unique(x.begin(), x.end()), x.end());
+        for (int e : x) { le[e] = (int)Ed.size(); Ed.push_back(e); }
+        std::vector<int> y;
+        for (int e : Ed) { y.push_back(hm.c1[e]); y.push_back(hm.c2[e]); }
+        std::sort(y.begin(), y.end());
+        y.erase(std::unique(y.begin(), y.end()), y.end());
+        for (int c : y) if (lc[c] < 0) { lc[c] = (int)Cd.size(); Cd.push_back(c); }
+        const int nEO = (int)Ed.size(), nC1 = (int)Cd.size();
+        auto reset = [&]() {
+            for (int e : Ed) le[e] = -1;
+            for (int c : Cd) lc[c] = -1;
+        };
+        if (nEO + 1 > 65535 || nC1 > 65535) { reset(); return false; }
+        plan.cnt.insert(plan.cnt.end(), {nO, nEO, nC1, 0});
+        plan.maxEO = std::max(plan.maxEO, nEO);
+        plan.maxC1 = std::max(plan.maxC1, nC1);
+        plan.eogid.insert(plan.eogid.end(), Ed.begin(), Ed.end());
+        plan.c1gid.insert(plan.c1gid.end(), Cd.begin(), Cd.end());
+        for (int e : Ed) plan.eo_c12.push_back(lc[hm.c1[e]] | (lc[hm.c2[e]] << 16));
+        const size_t b = plan.o_e.size();
+        plan.o_e.resize(b + (size_t)BCL_NCEP * Pc, (uint16_t)nEO);
+        plan.o_o.resize(b + (size_t)BCL_NCEP * Pc, 0);
+        for (int l = 0; l < Pc; l++)
+            for (int j = 0; j < BCL_NCEP; j++) plan.o_o[b + (size_t)j * Pc + l] = (uint16_t)(l < nO ? l : 0);
+        for (int l = 0; l < nO; l++) {
+            const int c = own[l];
+            for (int j = 0; j < hm.neoc[c]; j++) {
+                const int e = hm.eoc[(size_t)c * hm.maxE + j];
+                const int o = hm.c1[e] == c ? hm.c2[e] : hm.c1[e];
+                plan.o_e[b + (size_t)j * Pc + l] = (uint16_t)le[e];
+                plan.o_o[b + (size_t)j * Pc + l] = (uint16_t)lc[o];
+            }
+        }
+        plan.off_eo.push_back(plan.off_eo.back() + nEO);
+        plan.off_c1.push_back(plan.off_c1.back() + nC1);
         reset();
     }
     return true;

@@ -78,9 +78,9 @@ std::vector<int> cell_locality_order(int C, const std::vector<int> &c1,
                                      const std::vector<int> &c2, int leaf);
 
 // Patch plan of the fused baroclinic kernel (one CTA per patch, the stage's
-// cell, vertex and edge diagnostics of a layer in shared memory).  Patch p
-// owns the run of cells [p Pc, (p+1) Pc) of the internal numbering and the
-// edges whose lower-numbered cell it owns (E0, a contiguous run of edges).
+// cell, vertex and edge diagnostics of a layer in shared memory).  The cells
+// are cut into ceil(C / Pc) compact parts by recursive bisection; patch p
+// owns the edges whose lower-numbered cell lies in part p (E0).
 // Local index spaces, each listing its smaller set first:
 //   E0 <= E1 <= E2 (edges): E1 = the edges of C1's cells (edgesOnEdge of E0
 //   lies in E1 for TRiSK stencils), E2 = E1 plus the edges of V's vertices;
@@ -90,10 +90,15 @@ std::vector<int> cell_locality_order(int C, const std::vector<int> &c1,
 // term j of consecutive items reads one contiguous run.  Local indices are
 // 16-bit; a dummy slot after the last entry of E1 (hq), E2 (velocity) and C2
 // (thickness) holds zero and stands in for absent neighbours.
+// Cells into P compact parts (recursive bisection of the cell graph); the
+// part of each cell.
+std::vector<int> partition_cells(const HostMesh &hm, int P);
+
 struct BclPlan {
     int P = 0, Pc = 0;
+    std::vector<int> owner;                        // [C] patch of each cell
     int maxE0 = 0, maxE1 = 0, maxE2 = 0, maxC1 = 0, maxC2 = 0, maxV = 0;
-    std::vector<int> cnt;                          // [P][8]: nE0 nE1 nE2 nC1 nC2 nV e0_first 0
+    std::vector<int> cnt;                          // [P][8]: nE0 nE1 nE2 nC1 nC2 nV 0 0
     std::vector<int> off_e0, off_e1, off_e2;       // [P + 1] prefix sums
     std::vector<int> off_c1, off_c2, off_v;        // [P + 1]
     std::vector<int> egid, cgid;                   // [sum nE2], [sum nC2] local -> internal
@@ -116,5 +121,23 @@ constexpr int BCL_NCEP = 6;    // edgesOnCell slots of the fused kernel
 // bits, a cell has more than 6 edges, an edge more than 10 edgesOnEdge, or
 // edgesOnEdge leaves E1.
 bool build_bcl_plan(const HostMesh &hm, int Pc, int max_e0, int max_c1, BclPlan &plan);
+
+// Patch plan of the fused thickness/tracer kernel (one CTA per patch).  The
+// cells are cut into compact parts of at most Pc cells by recursive
+// bisection; patch p owns part p's cells (local cells 0 .. nO - 1); EO = the
+// edges of the owned cells, C1 = the owned cells followed by the cells across
+// EO's edges.  Per owned cell, term-major ([j][Pc]): its edges
+// (local EO index; a zero slot after EO's last entry for absent ones) and
+// the cell across each (local C1 index; the cell itself for absent ones).
+struct ThickPlan {
+    int P = 0, Pc = 0, maxEO = 0, maxC1 = 0;
+    std::vector<int> owner;                // [C] patch of each cell
+    std::vector<int> cnt;                  // [P][4]: nO nEO nC1 0
+    std::vector<int> off_eo, off_c1;       // [P + 1]
+    std::vector<int> eogid, c1gid;         // [sum nEO], [sum nC1] local -> internal
+    std::vector<int> eo_c12;               // [sum nEO] c1 | c2 << 16 (C1 indices)
+    std::vector<uint16_t> o_e, o_o;        // [P][6][Pc] local edge, local cell across
+};
+bool build_thick_plan(const HostMesh &hm, int Pc, ThickPlan &plan);
 
 }  // namespace sse

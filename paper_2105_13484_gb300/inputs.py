@@ -111,6 +111,11 @@ def _low_degree_field(rng, deg=4):
     return field
 
 
+# meshes already built, by (level, seed, land fraction, depth range): a mesh
+# does not depend on the layer count or on the state drawn after it
+_SPHERE_MESHES = {}
+
+
 def sphere_case(level, L, *, seed=0, land_frac=0.3, dmin=100.0, dmax=5000.0, nTracers=2,
                 wind=0.1, perturb=False, **params):
     """(mesh, L, params, (u, h, tr)) for the global-ocean-like sphere.
@@ -135,7 +140,10 @@ def sphere_case(level, L, *, seed=0, land_frac=0.3, dmin=100.0, dmax=5000.0, nTr
         v = (v - v.min()) / max(v.max() - v.min(), 1e-300)
         return dmin + (dmax - dmin) * v
 
-    m = _mesh.geodesic_sphere(level, land=land, depth=depth)
+    key = (level, seed, land_frac, dmin, dmax)
+    m = _SPHERE_MESHES.get(key)
+    if m is None:
+        m = _SPHERE_MESHES[key] = _mesh.geodesic_sphere(level, land=land, depth=depth)
     R = float(np.linalg.norm(m.xCell[0]))
     lat = m.latCell
     s = np.full(L, 1.0 / L)
@@ -234,8 +242,8 @@ def ensemble_members(n=64, seed=0, size_classes=8, cells=(2000, 60000), layers=(
     return out
 
 
-def serving_requests(n=16, seed=0, rate=20.0, cells=(2000, 60000), levels=(5, 6),
-                     layers=(10, 60), horizon=(20, 100)):
+def serving_requests(n=32, seed=0, rate=20.0, cells=(2000, 60000), levels=(5, 7),
+                     layers=(10, 60), horizon=(50, 500)):
     """A Poisson stream of solves: arrival times with mean rate `rate` per
     second, each an SSPRK2-SE or SSPRK3-SE solve on a planar channel (cells
     log-uniform in `cells`) or a geodesic sphere of a level in `levels`, with

@@ -5,7 +5,9 @@
 // kernel dereferences lies inside its patch's list (or is that list's zero
 // slot); every neighbour an owned edge, a C1 cell, a vertex or an E1 edge
 // reads is the one the global mesh names; the plan's maxima bound every
-// patch.  Usage: bcl_plan_check <mesh dir> <cells per patch>; prints "ok" or
+// patch; and the same for the fused thickness kernel's plan (owned cells
+// contiguous, each cell's edges and neighbours the mesh's, absent ones the zero
+// slot).  Usage: bcl_plan_check <mesh dir> <cells per patch>; prints "ok" or
 // the first violation (exit status 1).
 #include <algorithm>
 #include <cstdio>
@@ -106,6 +108,8 @@ int main(int argc, char **argv) {
     BclPlan pl;
     if (!build_bcl_plan(hm, Pc, 512, 512, pl)) { printf("violation: no plan\n"); return 1; }
     if (pl.P != (C + Pc - 1) / Pc) return fail("patch count", -1, -1);
+    if ((int)pl.owner.size() != C) return fail("owner size", -1, -1);
+    for (int c = 0; c < C; c++) if (pl.owner[c] < 0 || pl.owner[c] >= pl.P) return fail("cell owner", -1, c);
     std::vector<int> owner(E, -1);
     for (int p = 0; p < pl.P; p++) {
         const int *n = &pl.cnt[8 * p];
@@ -122,14 +126,13 @@ int main(int argc, char **argv) {
         const int *eg = &pl.egid[pl.off_e2[p]], *cg = &pl.cgid[pl.off_c2[p]];
         for (int l = 0; l < nE2; l++) if (eg[l] < 0 || eg[l] >= E) return fail("edge gid", p, l);
         for (int l = 0; l < nC2; l++) if (cg[l] < 0 || cg[l] >= C) return fail("cell gid", p, l);
-        // owned edges: a contiguous run starting at cnt[6], owned by the patch
-        // of their lower cell
+        // owned edges: those whose lower cell is in this patch's part
         for (int l = 0; l < nE0; l++) {
             const int e = eg[l];
-            if (e != n[6] + l) return fail("owned edges not contiguous", p, l);
             if (owner[e] != -1) return fail("edge owned twice", p, l);
             owner[e] = p;
-            if (std::min(hm.c1[e], hm.c2[e]) / Pc != p) return fail("edge owner is not its lower cell's patch", p, l);
+            if (pl.owner[std::min(hm.c1[e], hm.c2[e])] != p)
+                return fail("edge owner is not its lower cell's patch", p, l);
         }
         // the lookup of a global vertex in V (by its E1 edges)
         std::vector<int> vg(nV, -1);
@@ -214,6 +217,42 @@ int main(int argc, char **argv) {
         }
     }
     for (int e = 0; e < E; e++) if (owner[e] < 0) return fail("edge not owned", -1, e);
+
+    // the fused thickness kernel's plan (128 cells per patch, as the library uses)
+    ThickPlan tp;
+    const int Tc = 128;
+    if (!build_thick_plan(hm, Tc, tp)) { printf("violation: no thickness plan\n"); return 1; }
+    std::vector<int> towned(C, 0);
+    for (int p = 0; p < tp.P; p++) {
+        const int nO = tp.cnt[4 * p], nEO = tp.cnt[4 * p + 1], nC1 = tp.cnt[4 * p + 2];
+        if (nO > Tc) return fail("thickness patch above the kernel's threads", p, -1);
+        if (nEO > tp.maxEO || nC1 > tp.maxC1 || nO > nC1) return fail("thickness counts", p, -1);
+        if (tp.off_eo[p + 1] - tp.off_eo[p] != nEO || tp.off_c1[p + 1] - tp.off_c1[p] != nC1)
+            return fail("thickness offsets", p, -1);
+        const int *eg = &tp.eogid[tp.off_eo[p]], *cg = &tp.c1gid[tp.off_c1[p]];
+        for (int l = 0; l < nEO; l++) if (eg[l] < 0 || eg[l] >= E) return fail("thickness edge gid", p, l);
+        for (int l = 0; l < nC1; l++) if (cg[l] < 0 || cg[l] >= C) return fail("thickness cell gid", p, l);
+        for (int l = 0; l < nO; l++) {
+            if (tp.owner[cg[l]] != p) return fail("owned cell of another patch", p, l);
+            if (towned[cg[l]]++) return fail("cell owned twice", p, l);
+        }
+        for (int l = 0; l < Tc; l++) {
+            const int c = l < nO ? cg[l] : -1;
+            for (int j = 0; j < BCL_NCEP; j++) {
+                const size_t x = (size_t)BCL_NCEP * Tc * p + (size_t)j * Tc + l;
+                const int le = tp.o_e[x], lo = tp.o_o[x];
+                if (l < nO && j < hm.neoc[c]) {
+                    const int e = hm.eoc[(size_t)c * mE + j];
+                    if (le >= nEO || eg[le] != e) return fail("thickness cell edge", p, l);
+                    if (lo >= nC1 || cg[lo] != (hm.c1[e] == c ? hm.c2[e] : hm.c1[e]))
+                        return fail("thickness cell neighbour", p, l);
+                } else if (le != nEO || lo >= nC1) {
+                    return fail("thickness padding is not the zero slot", p, l);
+                }
+            }
+        }
+    }
+    for (int c = 0; c < C; c++) if (!towned[c]) return fail("cell not owned by a thickness patch", -1, c);
     printf("ok\n");
     return 0;
 }
