@@ -399,6 +399,14 @@ static void baroclinic_rhs(const om_mesh *m, const om_params *p, const double *u
     om_kinetic_energy(m, L, u, K);
     om_grad(m, L, K, gK);
     om_density(m, p, tr, rho);
+    /* pressure-gradient force in the anomaly form: with rho = rho_ref + rho'
+     * and zeta = sum h - H, Eq. (hydrocon) gives p_k = g rho_ref (zeta - z_k)
+     * + p'_k (p' the pressure of rho'), so
+     *   grad p_k + g rho_e grad z_k = g rho_ref grad zeta + grad p'_k + g rho'_e grad z_k.
+     * Both forms are the same quantity; this one avoids cancelling two terms
+     * of size g rho grad z over sloping bathymetry. */
+    OMP_FOR
+    for (size_t x = 0; x < CL; x++) rho[x] -= p->eos_rho_ref;
     om_pressure(m, p, h, rho, pres, zmid);
     om_grad(m, L, pres, gp);
     om_grad(m, L, zmid, gz);
@@ -440,8 +448,8 @@ static void baroclinic_rhs(const om_mesh *m, const om_params *p, const double *u
                 Xbot = p->nu_v * Dk1;
             }
             double vvisc = with_vvisc ? (Xtop - Xbot) / hee[k] : 0.0;
-            double rho_e = 0.5 * (rho[(size_t)c1 * L + k] + rho[(size_t)c2 * L + k]);
-            double pgf = (gp[x] + p->g * rho_e * gz[x]) / p->rho0;
+            double rhoa_e = 0.5 * (rho[(size_t)c1 * L + k] + rho[(size_t)c2 * L + k]);
+            double pgf = (p->g * p->eos_rho_ref * gzeta[e] + gp[x] + p->g * rhoa_e * gz[x]) / p->rho0;
             rhs[x] = Cut[x] + (Q[x] - Cu[x]) - gK[x] - pgf - vadv + p->nu_h * lap[x] + vvisc +
                      p->g * gzeta[e] - p->nu_4 * del4[x];
         }

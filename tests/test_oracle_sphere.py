@@ -97,3 +97,29 @@ def test_sphere_constant_tracer():
     o = oracle.Oracle(m, L, p)
     u1, h1, tr1 = o.step(3, run["dt"], run["M"], u, h, tr, n_steps=4)
     assert np.abs(tr1[1] - 35.0).max() < 1e-12
+
+
+def test_pressure_gradient_forms_agree():
+    """The oracle's pressure-gradient force uses the anomaly form (rho =
+    rho_ref + rho', p = g rho_ref (zeta - z) + p'); over sloping bathymetry it
+    equals the layer form grad p + g rho_e grad z of Eq. (hydrocon) to the
+    layer form's own rounding, i.e. a relative difference ~1e-13 of the terms
+    g rho_e grad z that cancel in it."""
+    import oracle
+    from paper_2105_13484_gb300 import inputs
+    m, L, p, (u, h, tr), run = inputs.workload("sphere_l4", perturb=True)
+    o = oracle.Oracle(m, L, p)
+    g, rho0, rref = p["g"], p["rho0"], p["eos_rho_ref"]
+    zeta = h.sum(1) - m.bottomDepth
+    c1, c2 = m.cellsOnEdge[:, 0], m.cellsOnEdge[:, 1]
+    rho = o.density(tr)
+    pres, z = o.pressure(h, rho)
+    layer = (o.grad(pres) + g * 0.5 * (rho[c1] + rho[c2]) * o.grad(z)) / rho0
+    rhoa = rho - rref
+    presa, za = o.pressure(h, rhoa)
+    anom = (g * rref * o.grad(zeta)[:, None] + o.grad(presa)
+            + g * 0.5 * (rhoa[c1] + rhoa[c2]) * o.grad(za)) / rho0
+    scale = np.abs(g * 0.5 * (rho[c1] + rho[c2]) * o.grad(z) / rho0).max()
+    assert np.abs(layer - anom).max() < 1e-13 * scale
+    # the two differ by far less than either's size, which is not negligible
+    assert np.abs(anom).max() > 1e-9 * scale
