@@ -103,6 +103,8 @@ PROFILE_OF = {  # committed ncu summaries by workload and kernel class (mixed fo
 }
 KERNEL_SOURCES = ("paper_2105_13484_gb300/csrc/btr_kernel.cu",
                   "paper_2105_13484_gb300/csrc/stage_kernels.cu",
+                  "paper_2105_13484_gb300/csrc/bcl_fused.cu",
+                  "paper_2105_13484_gb300/csrc/thick_fused.cu",
                   "paper_2105_13484_gb300/csrc/sse_internal.cuh")
 
 

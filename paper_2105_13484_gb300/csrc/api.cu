@@ -713,8 +713,8 @@ struct Engine : EngineBase {
         int smem_block = 0, smem_sm = 0;
         CK(cudaDeviceGetAttribute(&smem_block, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
         CK(cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev));
-        // the largest patches of which two CTAs fit an SM (the kernel is built for
-        // two per SM); else the largest that fit at all
+        // the largest patches of which as many CTAs fit an SM as the kernel is
+        // built for (two in FP32, one in FP64); else the largest that fit at all
         for (int pass = 0; pass < 2; pass++)
         for (int Pc : {160, 128, 112, 96, 80, 64, 48, 32}) {
             std::shared_ptr<const BclPlan> cached;
@@ -736,7 +736,9 @@ struct Engine : EngineBase {
             if (!cached) continue;
             const size_t smem = bcl_smem_bytes<R>(*cached);
             if (smem + 1024 + sizeof(BclJob<R>) + 64 > (size_t)smem_block) continue;
-            if (pass == 0 && 2 * (smem + 1024 + sizeof(BclJob<R>)) > (size_t)smem_sm) continue;
+            if (pass == 0 && (size_t)bcl_blocks_per_sm<R>() * (smem + 1024 + sizeof(BclJob<R>)) >
+                                 (size_t)smem_sm)
+                continue;
             // both kernels hold a job descriptor in static shared memory
             CK(cudaFuncSetAttribute(bcl_fused_kernel_ptr<R>(),
                                     cudaFuncAttributeMaxDynamicSharedMemorySize,

@@ -5,10 +5,10 @@
 // vorticity, edge pre-pass, edge tendency) that hand every diagnostic
 // (K, p', rho', z_mid, w, div u, omega, q, h_e u, q_e) to the next through
 // HBM.  Here one CTA owns a compact patch of edges (csrc/tiles.cu,
-// build_bcl_plan) and walks the layers from the top: each layer's velocity
-// and thickness over the patch and its halo are copied into shared memory
-// (cp.async into a ring of four layers, two layers ahead of the one being
-// computed), the cell, vertex and edge diagnostics of that layer are
+// build_bcl_plan) and walks the layers from the top, two at a time: each
+// pair's velocity and thickness over the patch and its halo are copied into
+// shared memory (cp.async into a ring of three pairs, one pair ahead of the
+// two in use), the cell, vertex and edge diagnostics of both layers are
 // formed in shared memory, and the owned edges' tendencies follow.  Only the
 // state itself crosses HBM: utilde, h and the tracers in, utilde out.
 //
@@ -49,8 +49,16 @@ __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commi
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::); }
 // wait until at most one committed group is still in flight
 __device__ __forceinline__ void cp_async_wait_1() { asm volatile("cp.async.wait_group 1;\n" ::); }
-// layers staged in shared memory: k and k + 1 in use, k + 2 and k + 3 in flight
-constexpr int NBUF = 4;
+// layer pairs staged in shared memory: p and p + 1 in use, p + 2 in flight
+constexpr int NB2 = 3;
+// CTAs per SM of the fused kernel: two in FP32 (128 registers a thread); one
+// in FP64, whose per-thread column state needs about 250 registers
+template <class R> constexpr int bcl_min_blocks() { return sizeof(R) == 4 ? 2 : 1; }
+// four values of one precision side by side in shared memory, at the 16-byte
+// alignment a carve gives
+struct __align__(16) dbl4s { double x, y, z, w; };
+template <class R> struct Sh4 { using T = float4; };
+template <> struct Sh4<double> { using T = dbl4s; };
 
 template <class R> __device__ __forceinline__ const R *sfrac_R(const DMesh &m);
 template <> __device__ __forceinline__ const double *sfrac_R<double>(const DMesh &m) { return m.sfrac; }
@@ -115,11 +123,20 @@ __device__ __forceinline__ void colflux_edge(const DMesh &m, R *__restrict__ uba
 //   G = (1/dt) sum_k h_e,k ut1_k / sum_k h_e,k,  out_k = a ut_n,k + b (ut1_k - dt G)
 // with the same operators, PGF anomaly form and boundary fluxes as the
 // unfused kernels (stage_kernels.cu).
+//
+// The layers are taken two at a time: shared memory holds each value of a
+// pair of layers (k, k + 1) side by side, so one vector load serves both and
+// every index and coefficient is read once per pair; the column recurrences
+// (w, the pressure-gradient sums, D_zt u, G) then advance through the two
+// layers in order.  A ring of three pair buffers holds pair p (being
+// computed), pair p + 1 (its first layer is the layer below pair p's second)
+// and pair p + 2 (in flight).
 // ---------------------------------------------------------------------------
 template <class R, int NT, int NI>
 __device__ __forceinline__ void bcl_fused_patch(const DMesh &m, const DParams &p, const DBcl<R> &t,
                                                 const BclArgs<R> &a, const int pid) {
     using R2 = V2<R>;
+    using R4 = typename Sh4<R>::T;
     const int tid = threadIdx.x;
     const int *cn = t.cnt + 8 * pid;
     const int nE0 = cn[0], nE1 = cn[1], nE2 = cn[2], nC1 = cn[3], nC2 = cn[4], nV = cn[5];
@@ -127,41 +144,35 @@ __device__ __forceinline__ void bcl_fused_patch(const DMesh &m, const DParams &p
     const int *cg_g = t.cgid + t.off_c2[pid];
     const int oe0 = t.off_e0[pid], oe1 = t.off_e1[pid], oc1 = t.off_c1[pid], ov = t.off_v[pid];
     const int Ep = m.Ep, Cp = m.Cp, L = m.L;
+    const int NP = (L + 1) / 2;   // layer pairs (the second layer of the last is absent if L is odd)
     const PhysR<R> &q = phys<R>(p);
 
     extern __shared__ __align__(16) char smem[];
     char *sp = smem;
-    // three layers of utilde / h (k, k + 1 and k + 2 in flight), of the
-    // tracers at C1 and of the old level at the owned edges
     R *ub_s = carve<R>(sp, t.maxE2 + 1);
     // buffer b of each ring starts at b times its stride (a multiple of 16 bytes)
-    const int sE = pad16<R>(t.maxE2 + 1), sC = pad16<R>(t.maxC2 + 1);
-    const int s1 = pad16<R>(t.maxC1), s0 = pad16<R>(t.maxE0);
-    R *ut_r = carve<R>(sp, NBUF * sE);
-    R *h_r = carve<R>(sp, NBUF * sC);
-    R *T_r = carve<R>(sp, NBUF * s1);
-    R *S_r = carve<R>(sp, NBUF * s1);
-    R *un_r = carve<R>(sp, NBUF * s0);
-    R *q_s = carve<R>(sp, t.maxV);
-    R *om_s = carve<R>(sp, t.maxV);
-    R2 *hq_s = carve<R2>(sp, t.maxE1 + 1);
-    R *cK = carve<R>(sp, t.maxC1);
-    R *cR = carve<R>(sp, t.maxC1);
-    R *cW1 = carve<R>(sp, t.maxC1);
-    R *cD = carve<R>(sp, t.maxC1);
-    // the patch's connectivity and coefficients, read every layer: copied to
-    // shared memory once (term-major, stride = the patch's own count)
+    const int sE = pad16<R2>(t.maxE2 + 1), sC = pad16<R2>(t.maxC2 + 1), s1 = pad16<R2>(t.maxC1);
+    R2 *ut_r = carve<R2>(sp, NB2 * sE);
+    R2 *h_r = carve<R2>(sp, NB2 * sC);
+    R2 *T_r = carve<R2>(sp, NB2 * s1);
+    R2 *S_r = carve<R2>(sp, NB2 * s1);
+    R2 *q_s = carve<R2>(sp, t.maxV);
+    R2 *om_s = carve<R2>(sp, t.maxV);
+    R4 *hq_s = carve<R4>(sp, t.maxE1 + 1);   // (h_e u, q_e) of both layers
+    R2 *cK = carve<R2>(sp, t.maxC1);
+    R2 *cR = carve<R2>(sp, t.maxC1);
+    R2 *cW1 = carve<R2>(sp, t.maxC1);
+    R2 *cD = carve<R2>(sp, t.maxC1);
+    // the patch's connectivity and coefficients, read every pair: copied to
+    // shared memory once (term-major, stride = the patch's own count); index
+    // pairs packed as lo | hi << 16, coefficient pairs side by side
     unsigned short *x_e0i = carve<unsigned short>(sp, BCL_NE2P * t.maxE0);
     R *x_e0w = carve<R>(sp, BCL_NE2P * t.maxE0);
-    unsigned short *x_c1e = carve<unsigned short>(sp, BCL_NCEP * t.maxC1);
-    unsigned short *x_c1o = carve<unsigned short>(sp, BCL_NCEP * t.maxC1);
-    R *x_c1d = carve<R>(sp, BCL_NCEP * t.maxC1);
-    R *x_c1k = carve<R>(sp, BCL_NCEP * t.maxC1);
-    unsigned short *x_ve = carve<unsigned short>(sp, 3 * t.maxV);
-    unsigned short *x_vc = carve<unsigned short>(sp, 3 * t.maxV);
-    R *x_vcu = carve<R>(sp, 3 * t.maxV);
-    R *x_vkw = carve<R>(sp, 3 * t.maxV);
-    R *x_vf = carve<R>(sp, t.maxV);
+    unsigned *x_c1eo = carve<unsigned>(sp, BCL_NCEP * t.maxC1);
+    R2 *x_c1dk = carve<R2>(sp, BCL_NCEP * t.maxC1);
+    unsigned *x_vec = carve<unsigned>(sp, 3 * t.maxV);
+    R2 *x_vck = carve<R2>(sp, 3 * t.maxV);
+    R2 *x_vbf = carve<R2>(sp, t.maxV);   // (curl ubar, curl ubar + f): layer-invariant
     int *x_e1c = carve<int>(sp, t.maxE1);
     int *x_e1v = carve<int>(sp, t.maxE1);
     // the patch's internal edge and cell indices (each layer's copies use them)
@@ -175,78 +186,92 @@ __device__ __forceinline__ void bcl_fused_patch(const DMesh &m, const DParams &p
         x_e0w[j] = ldg(t.e0_wl + BCL_NE2P * oe0 + j);
     }
     for (int j = tid; j < BCL_NCEP * nC1; j += NT) {
-        x_c1e[j] = t.c1_e[BCL_NCEP * oc1 + j];
-        x_c1o[j] = t.c1_o[BCL_NCEP * oc1 + j];
-        x_c1d[j] = ldg(t.c1_divc + BCL_NCEP * oc1 + j);
-        x_c1k[j] = ldg(t.c1_kec + BCL_NCEP * oc1 + j);
+        const int x = BCL_NCEP * oc1 + j;
+        x_c1eo[j] = (unsigned)t.c1_e[x] | ((unsigned)t.c1_o[x] << 16);
+        R2 dk;
+        dk.x = ldg(t.c1_divc + x);
+        dk.y = ldg(t.c1_kec + x);
+        x_c1dk[j] = dk;
     }
     for (int j = tid; j < 3 * nV; j += NT) {
-        x_ve[j] = t.v_e[3 * ov + j];
-        x_vc[j] = t.v_c[3 * ov + j];
-        x_vcu[j] = ldg(t.v_curl + 3 * ov + j);
-        x_vkw[j] = ldg(t.v_kw + 3 * ov + j);
+        const int x = 3 * ov + j;
+        x_vec[j] = (unsigned)t.v_e[x] | ((unsigned)t.v_c[x] << 16);
+        R2 ck;
+        ck.x = ldg(t.v_curl + x);
+        ck.y = ldg(t.v_kw + x);
+        x_vck[j] = ck;
     }
-    for (int j = tid; j < nV; j += NT) x_vf[j] = ldg(t.v_f + ov + j);
     for (int j = tid; j < nE1; j += NT) {
         x_e1c[j] = t.e1_c12[oe1 + j];
         x_e1v[j] = t.e1_v12[oe1 + j];
     }
     const bool two = p.nT > 1;
     const bool comb = a.ut_n != nullptr;
-    // one layer's copies into buffer b
-    auto issue = [&](int k, int b) {
-        const R *un = a.ut + (size_t)k * Ep;
-        const R *hn = a.hR + (size_t)k * Cp;
-        R *ud = ut_r + b * sE, *hd = h_r + b * sC, *Td = T_r + b * s1, *Sd = S_r + b * s1;
-        for (int j = tid; j < nE2; j += NT) cp_async(ud + j, un + eg[j]);
-        for (int j = tid; j < nC2; j += NT) cp_async(hd + j, hn + cg[j]);
-        for (int j = tid; j < nC1; j += NT) {
-            cp_async(Td + j, a.tr + (size_t)k * Cp + cg[j]);
-            if (two) cp_async(Sd + j, a.tr + (size_t)(L + k) * Cp + cg[j]);
+    // one pair's copies into buffer b (the second layer's only if it exists)
+    auto issue = [&](int pp, int b) {
+        const int k0 = 2 * pp;
+        const bool has1 = k0 + 1 < L;
+        R *ud = reinterpret_cast<R *>(ut_r + b * sE), *hd = reinterpret_cast<R *>(h_r + b * sC);
+        R *Td = reinterpret_cast<R *>(T_r + b * s1), *Sd = reinterpret_cast<R *>(S_r + b * s1);
+        const R *u0 = a.ut + (size_t)k0 * Ep, *h0 = a.hR + (size_t)k0 * Cp;
+        const R *T0 = a.tr + (size_t)k0 * Cp, *S0 = a.tr + (size_t)(L + k0) * Cp;
+        for (int j = tid; j < nE2; j += NT) {
+            const int ge = eg[j];
+            cp_async(ud + 2 * j, u0 + ge);
+            if (has1) cp_async(ud + 2 * j + 1, u0 + Ep + ge);
         }
-        if (comb) {
-            R *nd = un_r + b * s0;
-            for (int j = tid; j < nE0; j += NT) cp_async(nd + j, a.ut_n + (size_t)k * Ep + eg[j]);
+        for (int j = tid; j < nC2; j += NT) {
+            const int gc = cg[j];
+            cp_async(hd + 2 * j, h0 + gc);
+            if (has1) cp_async(hd + 2 * j + 1, h0 + Cp + gc);
+        }
+        for (int j = tid; j < nC1; j += NT) {
+            const int gc = cg[j];
+            cp_async(Td + 2 * j, T0 + gc);
+            if (has1) cp_async(Td + 2 * j + 1, T0 + Cp + gc);
+            if (two) {
+                cp_async(Sd + 2 * j, S0 + gc);
+                if (has1) cp_async(Sd + 2 * j + 1, S0 + Cp + gc);
+            }
         }
         cp_async_commit();
     };
 
-    // ---- the layer-invariant 2-D data; layers 0 and 1 in flight
+    // ---- the layer-invariant 2-D data; pairs 0 and 1 in flight
     for (int j = tid; j < nE2; j += NT) ub_s[j] = ldg(a.ubar + eg[j]);
     if (tid == 0) {
+        R2 z2;
+        z2.x = R(0); z2.y = R(0);
         ub_s[nE2] = R(0);
-        for (int b = 0; b < NBUF; b++) { ut_r[b * sE + nE2] = R(0); h_r[b * sC + nC2] = R(0); }
-        R2 z; z.x = R(0); z.y = R(0);
-        hq_s[nE1] = z;
+        for (int b = 0; b < NB2; b++) { ut_r[b * sE + nE2] = z2; h_r[b * sC + nC2] = z2; }
+        R4 z4;
+        z4.x = R(0); z4.y = R(0); z4.z = R(0); z4.w = R(0);
+        hq_s[nE1] = z4;
     }
-    // layers 0, 1 and 2 in flight (one commit group each, empty past the bottom)
-    for (int k = 0; k < NBUF - 1; k++) {
-        if (k < L) issue(k, k);
-        else cp_async_commit();
-    }
+    issue(0, 0);
+    if (NP > 1) issue(1, 1);
+    else cp_async_commit();
 
-    // cells of C1 held by this thread: global index, SSH, depth integral of
-    // div(h_e u) and the running column sums
-    int gc[NI];
+    // cells of C1 held by this thread: the depth integral of div(h_e u) and
+    // the running column sum
     R dsum[NI], W[NI];
 #pragma unroll
     for (int s = 0; s < NI; s++) {
         const int c = tid + s * NT;
-        gc[s] = 0; dsum[s] = R(0); W[s] = R(0);
+        dsum[s] = R(0); W[s] = R(0);
         if (c < nC1) {
-            gc[s] = cg[c];
             R d = R(0);
 #pragma unroll
             for (int j = 0; j < BCL_NCEP; j++) {
-                const int el = t.c1_e[6 * oc1 + j * nC1 + c];
-                if (el < nE2) d += ldg(t.c1_divc + 6 * oc1 + j * nC1 + c) * ldg(a.Fc + eg[el]);
+                const int el = t.c1_e[BCL_NCEP * oc1 + j * nC1 + c];
+                if (el < nE2) d += ldg(t.c1_divc + BCL_NCEP * oc1 + j * nC1 + c) * ldg(a.Fc + eg[el]);
             }
             dsum[s] = d;
         }
     }
     // owned edges held by this thread
     int ge[NI], c12[NI], v12[NI];
-    R cbar[NI], gzeta[NI], wind[NI], idc[NI], idv[NI], Dk[NI], wk[NI], num[NI], den[NI];
+    R cbar[NI], idc[NI], idv[NI], Dk[NI], wk[NI], num[NI], den[NI];
     // pressure gradient from differences across the edge, accumulated down the
     // column: dA = sum_{l<k} (rho' h)_c2 - (rho' h)_c1, dH = sum_{l<k} h_c2 - h_c1
     R dA[NI], dH[NI], dzeta[NI];
@@ -255,7 +280,7 @@ __device__ __forceinline__ void bcl_fused_patch(const DMesh &m, const DParams &p
     for (int s = 0; s < NI; s++) {
         const int e = tid + s * NT;
         ge[s] = 0; c12[s] = 0; v12[s] = 0;
-        gzeta[s] = R(0); wind[s] = R(0); idc[s] = R(0); idv[s] = R(0);
+        idc[s] = R(0); idv[s] = R(0);
         Dk[s] = R(0); wk[s] = R(0); num[s] = R(0); den[s] = R(0); cbar[s] = R(0);
         dA[s] = R(0); dH[s] = R(0); dzeta[s] = R(0);
         if (e < nE0) {
@@ -266,8 +291,6 @@ __device__ __forceinline__ void bcl_fused_patch(const DMesh &m, const DParams &p
             idv[s] = ldg(t.e0_invdv + oe0 + e);
             const int g1 = cg[c12[s] & 0xffff], g2 = cg[c12[s] >> 16];
             dzeta[s] = (R)(a.zeta[g2] - a.zeta[g1]);   // the difference taken in FP64
-            gzeta[s] = q.zcoef * dzeta[s] * idc[s];
-            wind[s] = wnd ? wnd[ge[s]] : R(0);
         }
     }
     __syncthreads();   // ub_s
@@ -285,146 +308,256 @@ __device__ __forceinline__ void bcl_fused_patch(const DMesh &m, const DParams &p
             cbar[s] = cb;
         }
     }
+    // the relative vorticity of ubar at the vertices (every layer's omega is
+    // this plus the curl of its utilde)
+    for (int v = tid; v < nV; v += NT) {
+        R ob = R(0);
+#pragma unroll
+        for (int j = 0; j < 3; j++) {
+            const int x = j * nV + v;
+            ob += x_vck[x].x * ub_s[x_vec[x] & 0xffff];
+        }
+        R2 bf;
+        bf.x = ob;
+        bf.y = ob + ldg(t.v_f + ov + v);
+        x_vbf[v] = bf;
+    }
     const R g = q.g, alpha = q.alpha, beta = q.beta, Tref = q.T_ref, Sref = q.S_ref;
     const R inv_rho0 = q.inv_rho0, nu_h = q.nu_h, nu_v = q.nu_v, cdrag = q.c_drag;
     const R dt = a.dt, ca = a.a, cb = a.b;
     const R *sfr = sfrac_R<R>(m);
     R Sk = R(0);   // sum_{l<k} s_l
 
-    for (int k = 0; k < L; k++) {
-        const int bc = k % NBUF, bn = (k + 1) % NBUF;
-        const R *ut_c = ut_r + bc * sE, *h_c = h_r + bc * sC;
-        const R *ut_nx = ut_r + bn * sE, *h_nx = h_r + bn * sC;
-        const R *T_c = T_r + bc * s1, *S_c = S_r + bc * s1, *un_c = un_r + bc * s0;
-        cp_async_wait_1();
-        __syncthreads();   // layers k and k + 1 in shared memory; layer k - 1's readers done
-        if (k + 3 < L) issue(k + 3, (k + 3) % NBUF);
-        else cp_async_commit();
+    for (int pp = 0; pp < NP; pp++) {
+        const int k0 = 2 * pp;
+        const bool has1 = k0 + 1 < L;
+        const int bc = pp % NB2, bn = (pp + 1) % NB2;
+        const R2 *ut_c = ut_r + bc * sE, *h_c = h_r + bc * sC;
+        const R2 *ut_nx = ut_r + bn * sE, *h_nx = h_r + bn * sC;
+        const R2 *T_c = T_r + bc * s1, *S_c = S_r + bc * s1;
+        cp_async_wait_all();
+        __syncthreads();   // pairs pp and pp + 1 in shared memory; pair pp - 1's readers done
+        if (pp + 2 < NP) issue(pp + 2, (pp + 2) % NB2);
         // ---- vertices: relative vorticity, kite-averaged thickness, PV
         for (int v = tid; v < nV; v += NT) {
-            R om = R(0), hv = R(0);
+            R2 ot, hv;
+            ot.x = R(0); ot.y = R(0); hv.x = R(0); hv.y = R(0);
 #pragma unroll
             for (int j = 0; j < 3; j++) {
                 const int x = j * nV + v;
-                const int el = x_ve[x], cl = x_vc[x];
-                om += x_vcu[x] * (ub_s[el] + ut_c[el]);
-                hv += x_vkw[x] * h_c[cl];
+                const unsigned ec = x_vec[x];
+                const R2 ck = x_vck[x];
+                const R2 u2 = ut_c[ec & 0xffff], h2 = h_c[ec >> 16];
+                ot.x += ck.x * u2.x;
+                ot.y += ck.x * u2.y;
+                hv.x += ck.y * h2.x;
+                hv.y += ck.y * h2.y;
             }
+            const R2 bf = x_vbf[v];
+            R2 om, qv;
+            om.x = bf.x + ot.x;
+            om.y = bf.x + ot.y;
+            qv.x = (bf.y + ot.x) / hv.x;
+            qv.y = (bf.y + ot.y) / hv.y;
             om_s[v] = om;
-            q_s[v] = (om + x_vf[v]) / hv;
+            q_s[v] = qv;
         }
-        // ---- cells of C1: K, div u, div(h_e u), rho', p', z_mid, w
-        const R sk = sfr[k];
+        // ---- cells of C1: K, div u, div(h_e u), rho', w
+        const R sk0 = sfr[k0], sk1 = has1 ? sfr[k0 + 1] : R(0);
 #pragma unroll
         for (int s = 0; s < NI; s++) {
             const int c = tid + s * NT;
             if (c < nC1) {
-                const R hk = h_c[c];
-                R ke = R(0), dl = R(0), dv = R(0);
+                const R2 hk = h_c[c];
+                R2 ke, dl, dv;
+                ke.x = R(0); ke.y = R(0); dl.x = R(0); dl.y = R(0); dv.x = R(0); dv.y = R(0);
 #pragma unroll
                 for (int j = 0; j < BCL_NCEP; j++) {
                     const int x = j * nC1 + c;
-                    const int el = x_c1e[x], ol = x_c1o[x];
-                    const R uk = ub_s[el] + ut_c[el];
-                    const R he = R(0.5) * (hk + h_c[ol]);
-                    const R dc = x_c1d[x];
-                    ke += x_c1k[x] * uk * uk;
-                    dl += dc * uk;
-                    dv += dc * (he * uk);
+                    const unsigned eo = x_c1eo[x];
+                    const int el = eo & 0xffff, ol = eo >> 16;
+                    const R2 dk = x_c1dk[x];
+                    const R ubl = ub_s[el];
+                    const R2 ul = ut_c[el], ho = h_c[ol];
+                    const R u0 = ubl + ul.x, u1 = ubl + ul.y;
+                    const R he0 = R(0.5) * (hk.x + ho.x), he1 = R(0.5) * (hk.y + ho.y);
+                    ke.x += dk.y * u0 * u0;
+                    ke.y += dk.y * u1 * u1;
+                    dl.x += dk.x * u0;
+                    dl.y += dk.x * u1;
+                    dv.x += dk.x * (he0 * u0);
+                    dv.y += dk.x * (he1 * u1);
                 }
-                R rp = -alpha * (T_c[c] - Tref);
-                if (two) rp += beta * (S_c[c] - Sref);
+                const R2 T2 = T_c[c];
+                R2 rp;
+                rp.x = -alpha * (T2.x - Tref);
+                rp.y = -alpha * (T2.y - Tref);
+                if (two) {
+                    const R2 S2 = S_c[c];
+                    rp.x += beta * (S2.x - Sref);
+                    rp.y += beta * (S2.y - Sref);
+                }
                 cK[c] = ke;
                 cR[c] = rp;
                 cD[c] = dl;
-                W[s] += dv;
-                // w at the top of layer k + 1
-                cW1[c] = W[s] - (Sk + sk) * dsum[s];
+                // w at the top of layers k0 + 1 and k0 + 2 (an absent second
+                // layer's value is never read)
+                R2 w1;
+                W[s] += dv.x;
+                w1.x = W[s] - (Sk + sk0) * dsum[s];
+                W[s] += dv.y;
+                w1.y = W[s] - (Sk + sk0 + sk1) * dsum[s];
+                cW1[c] = w1;
             }
         }
         __syncthreads();
-        // ---- edges of E1: (h_e u, q_e)
+        // the old level at the owned edges, read by the owned edges below
+        R un0[NI], un1[NI];
+#pragma unroll
+        for (int s = 0; s < NI; s++) {
+            un0[s] = R(0); un1[s] = R(0);
+            if (comb && tid + s * NT < nE0) {
+                un0[s] = ldg(a.ut_n + (size_t)k0 * Ep + ge[s]);
+                if (has1) un1[s] = ldg(a.ut_n + (size_t)(k0 + 1) * Ep + ge[s]);
+            }
+        }
+        // ---- edges of E1: (h_e u, q_e) of both layers
         for (int e = tid; e < nE1; e += NT) {
             const int cc = x_e1c[e], vv = x_e1v[e];
-            R2 hq;
-            hq.x = R(0.5) * (h_c[cc & 0xffff] + h_c[cc >> 16]) * (ub_s[e] + ut_c[e]);
-            hq.y = R(0.5) * (q_s[vv & 0xffff] + q_s[vv >> 16]);
+            const R2 h1 = h_c[cc & 0xffff], h2 = h_c[cc >> 16];
+            const R2 qa = q_s[vv & 0xffff], qb = q_s[vv >> 16];
+            const R ubl = ub_s[e];
+            const R2 ul = ut_c[e];
+            R4 hq;
+            hq.x = R(0.5) * (h1.x + h2.x) * (ubl + ul.x);
+            hq.y = R(0.5) * (qa.x + qb.x);
+            hq.z = R(0.5) * (h1.y + h2.y) * (ubl + ul.y);
+            hq.w = R(0.5) * (qa.y + qb.y);
             hq_s[e] = hq;
         }
         __syncthreads();
-        // ---- owned edges: the tendency of layer k
+        // ---- owned edges: the tendencies of the pair's layers, in order
 #pragma unroll
         for (int s = 0; s < NI; s++) {
             const int e = tid + s * NT;
             if (e >= nE0) continue;
             const int c1 = c12[s] & 0xffff, c2 = c12[s] >> 16;
             const int v1 = v12[s] & 0xffff, v2 = v12[s] >> 16;
-            const R ut_cur = ut_c[e], u_cur = ub_s[e] + ut_cur;
-            const R he_cur = R(0.5) * (h_c[c1] + h_c[c2]);
-            const R qk = hq_s[e].y;
-            R Q = R(0);
+            const R ube = ub_s[e];
+            const R2 utc = ut_c[e];
+            const R2 h1 = h_c[c1], h2 = h_c[c2];
+            const R4 hqe = hq_s[e];
+            R2 Q;
+            Q.x = R(0); Q.y = R(0);
 #pragma unroll
             for (int j = 0; j < BCL_NE2P; j++) {
                 const int x = j * nE0 + e;
-                const R2 nb = hq_s[x_e0i[x]];
-                Q += x_e0w[x] * nb.x * (R(0.5) * (qk + nb.y));
+                const R w = x_e0w[x];
+                const R4 nb = hq_s[x_e0i[x]];
+                Q.x += w * nb.x * (R(0.5) * (hqe.y + nb.y));
+                Q.y += w * nb.z * (R(0.5) * (hqe.w + nb.w));
             }
-            const R gradK = (cK[c2] - cK[c1]) * idc[s];
-            // p'_2 - p'_1 and z_2 - z_1 (z = zeta - sum_{l<k} h_l - h_k / 2)
-            const R h1 = h_c[c1], h2 = h_c[c2];
-            const R rh = cR[c2] * h2 - cR[c1] * h1;
-            const R dp = g * (dA[s] + R(0.5) * rh);
-            const R dz = dzeta[s] - dH[s] - R(0.5) * (h2 - h1);
-            const R pgf = (dp + g * (R(0.5) * (cR[c1] + cR[c2])) * dz) * idc[s] * inv_rho0;
-            dA[s] += rh;
-            dH[s] += h2 - h1;
-            R Dk1 = R(0), wk1 = R(0);
-            if (k + 1 < L) {
-                const R u_next = ub_s[e] + ut_nx[e];
-                const R he_next = R(0.5) * (h_nx[c1] + h_nx[c2]);
-                Dk1 = (u_cur - u_next) / (R(0.5) * (he_cur + he_next));
-                wk1 = R(0.5) * (cW1[c1] + cW1[c2]);
+            const R2 K1 = cK[c1], K2 = cK[c2], P1 = cR[c1], P2 = cR[c2];
+            const R2 D1 = cD[c1], D2 = cD[c2], o1 = om_s[v1], o2 = om_s[v2];
+            const R2 W1 = cW1[c1], W2 = cW1[c2];
+            // the layer below the pair: the first of the next pair
+            R utn = R(0), h1n = R(0), h2n = R(0);
+            if (k0 + 2 < L) {
+                utn = ut_nx[e].x;
+                h1n = h_nx[c1].x;
+                h2n = h_nx[c2].x;
             }
-            const R vadv = R(0.5) * (wk[s] * Dk[s] + wk1 * Dk1);
-            const R Xtop = (k == 0) ? wind[s] : nu_v * Dk[s];
-            R Xbot;
-            if (k == L - 1) {
-                R utan = R(0);
 #pragma unroll
-                for (int j = 0; j < BCL_NE2P; j++) {
-                    const int x = j * nE0 + e;
-                    const int el = x_e0i[x];
-                    utan += x_e0w[x] * (ub_s[el] + ut_c[el]);
+            for (int i = 0; i < 2; i++) {
+                const int k = k0 + i;
+                if (k >= L) break;
+                const R ut_cur = i ? utc.y : utc.x;
+                const R hh1 = i ? h1.y : h1.x, hh2 = i ? h2.y : h2.x;
+                const R u_cur = ube + ut_cur;
+                const R he_cur = R(0.5) * (hh1 + hh2);
+                const R gradK = ((i ? K2.y : K2.x) - (i ? K1.y : K1.x)) * idc[s];
+                // p'_2 - p'_1 and z_2 - z_1 (z = zeta - sum_{l<k} h_l - h_k / 2)
+                const R r1 = i ? P1.y : P1.x, r2 = i ? P2.y : P2.x;
+                const R rh = r2 * hh2 - r1 * hh1;
+                const R dp = g * (dA[s] + R(0.5) * rh);
+                const R dz = dzeta[s] - dH[s] - R(0.5) * (hh2 - hh1);
+                const R pgf = (dp + g * (R(0.5) * (r1 + r2)) * dz) * idc[s] * inv_rho0;
+                dA[s] += rh;
+                dH[s] += hh2 - hh1;
+                R Dk1 = R(0), wk1 = R(0);
+                if (k + 1 < L) {
+                    const R u_next = ube + (i ? utn : utc.y);
+                    const R he_next = R(0.5) * (i ? h1n + h2n : h1.y + h2.y);
+                    Dk1 = (u_cur - u_next) / (R(0.5) * (he_cur + he_next));
+                    wk1 = R(0.5) * (i ? W1.y + W2.y : W1.x + W2.x);
                 }
-                Xbot = cdrag * sqrt(u_cur * u_cur + utan * utan) * u_cur;
-            } else {
-                Xbot = nu_v * Dk1;
+                const R vadv = R(0.5) * (wk[s] * Dk[s] + wk1 * Dk1);
+                R Xtop = nu_v * Dk[s];
+                if (k == 0) Xtop = wnd ? wnd[ge[s]] : R(0);
+                R Xbot;
+                if (k == L - 1) {
+                    R utan = R(0);
+#pragma unroll
+                    for (int j = 0; j < BCL_NE2P; j++) {
+                        const int x = j * nE0 + e;
+                        const int el = x_e0i[x];
+                        const R2 ul = ut_c[el];
+                        utan += x_e0w[x] * (ub_s[el] + (i ? ul.y : ul.x));
+                    }
+                    Xbot = cdrag * sqrt(u_cur * u_cur + utan * utan) * u_cur;
+                } else {
+                    Xbot = nu_v * Dk1;
+                }
+                const R vvisc = (Xtop - Xbot) / he_cur;
+                const R lap = ((i ? D2.y : D2.x) - (i ? D1.y : D1.x)) * idc[s] -
+                              ((i ? o2.y : o2.x) - (i ? o1.y : o1.x)) * idv[s];
+                const R gzeta = q.zcoef * dzeta[s] * idc[s];
+                const R rhs = ((i ? Q.y : Q.x) - cbar[s]) - gradK - pgf - vadv + nu_h * lap +
+                              vvisc + gzeta;
+                const R ut1 = ut_cur + dt * rhs;
+                num[s] += he_cur * ut1;
+                den[s] += he_cur;
+                const R unk = i ? un1[s] : un0[s];
+                a.ut_out[(size_t)k * Ep + ge[s]] = comb ? ca * unk + cb * ut1 : cb * ut1;
+                Dk[s] = Dk1;
+                wk[s] = wk1;
             }
-            const R vvisc = (Xtop - Xbot) / he_cur;
-            const R lap = (cD[c2] - cD[c1]) * idc[s] - (om_s[v2] - om_s[v1]) * idv[s];
-            const R rhs = (Q - cbar[s]) - gradK - pgf - vadv + nu_h * lap + vvisc + gzeta[s];
-            const R ut1 = ut_cur + dt * rhs;
-            num[s] += he_cur * ut1;
-            den[s] += he_cur;
-            const size_t xo = (size_t)k * Ep + ge[s];
-            a.ut_out[xo] = comb ? ca * un_c[e] + cb * ut1 : cb * ut1;
-            Dk[s] = Dk1;
-            wk[s] = wk1;
         }
-        Sk += sk;
+        Sk = (Sk + sk0) + sk1;
     }
     cp_async_wait_all();
-    // ---- G and the subtraction of dt G over the owned columns
+    // ---- G and the subtraction of dt G over the owned columns.  The loads of
+    // KB layers of both slots are issued before any store, so that a thread
+    // waits for L / KB round trips to global memory instead of NI * L.
+    R corr[NI];
 #pragma unroll
     for (int s = 0; s < NI; s++) {
         const int e = tid + s * NT;
-        if (e >= nE0) continue;
-        const R G = num[s] / den[s] / dt;
-        a.G[ge[s]] = G;
-        const R corr = cb * dt * G;
-        for (int k = 0; k < L; k++) {
-            const size_t xo = (size_t)k * Ep + ge[s];
-            a.ut_out[xo] -= corr;
+        corr[s] = R(0);
+        if (e < nE0) {
+            const R G = num[s] / den[s] / dt;
+            a.G[ge[s]] = G;
+            corr[s] = cb * dt * G;
+        }
+    }
+    constexpr int KB = 4;
+    for (int k0 = 0; k0 < L; k0 += KB) {
+        R v[NI][KB];
+#pragma unroll
+        for (int s = 0; s < NI; s++) {
+#pragma unroll
+            for (int r = 0; r < KB; r++) {
+                if (tid + s * NT < nE0 && k0 + r < L)
+                    v[s][r] = a.ut_out[(size_t)(k0 + r) * Ep + ge[s]];
+            }
+        }
+#pragma unroll
+        for (int s = 0; s < NI; s++) {
+#pragma unroll
+            for (int r = 0; r < KB; r++) {
+                if (tid + s * NT < nE0 && k0 + r < L)
+                    a.ut_out[(size_t)(k0 + r) * Ep + ge[s]] = v[s][r] - corr[s];
+            }
         }
     }
 }
@@ -457,14 +590,14 @@ template <class T> __device__ __forceinline__ void copy_job(T &dst, const T &src
 // the same instructions in both and a state's results are the same bits
 // whether it steps alone or in a batch.
 template <class R, int NT, int NI>
-__global__ void __launch_bounds__(NT, 2) k_bcl_fused(const BclJob<R> job) {
+__global__ void __launch_bounds__(NT, bcl_min_blocks<R>()) k_bcl_fused(const BclJob<R> job) {
     __shared__ BclJob<R> J;
     copy_job(J, job);
     __syncthreads();
     bcl_fused_patch<R, NT, NI>(J.m, J.p, J.t, J.a, blockIdx.x);
 }
 template <class R, int NT, int NI>
-__global__ void __launch_bounds__(NT, 2) k_bcl_fused_batch(const BclJob<R> *__restrict__ jobs,
+__global__ void __launch_bounds__(NT, bcl_min_blocks<R>()) k_bcl_fused_batch(const BclJob<R> *__restrict__ jobs,
                                                            const int *__restrict__ first,
                                                            int njobs) {
     __shared__ BclJob<R> J;
@@ -502,22 +635,25 @@ template <class R> size_t bcl_smem_bytes(const BclPlan &plan) {
     auto a16 = [](size_t b) { return (b + 15) / 16 * 16; };
     const size_t sR = sizeof(R);
     size_t b = 0;
-    b += (1 + NBUF) * a16(sR * (plan.maxE2 + 1));   // ubar, utilde (NBUF layers)
-    b += NBUF * a16(sR * (plan.maxC2 + 1));         // h
-    b += 2 * NBUF * a16(sR * plan.maxC1);           // T, S
-    b += NBUF * a16(sR * plan.maxE0);               // old-level utilde
-    // (each ring is carved as one block of NBUF 16-byte padded strides)
-    b += 2 * a16(sR * plan.maxV);               // q, omega
-    b += a16(2 * sR * (plan.maxE1 + 1));        // (h_e u, q_e)
-    b += 4 * a16(sR * plan.maxC1);              // K, rho', w, div u
+    b += a16(sR * (plan.maxE2 + 1));                   // ubar
+    b += NB2 * a16(2 * sR * (plan.maxE2 + 1));         // utilde (pair ring)
+    b += NB2 * a16(2 * sR * (plan.maxC2 + 1));         // h
+    b += 2 * NB2 * a16(2 * sR * plan.maxC1);           // T, S
+    // (each ring is carved as one block of NB2 16-byte padded strides)
+    b += 2 * a16(2 * sR * plan.maxV);                  // q, omega
+    b += a16(4 * sR * (plan.maxE1 + 1));               // (h_e u, q_e) x 2
+    b += 4 * a16(2 * sR * plan.maxC1);                 // K, rho', w, div u
     // connectivity and coefficients of the patch
     b += a16(2 * BCL_NE2P * plan.maxE0) + a16(sR * BCL_NE2P * plan.maxE0);
-    b += 2 * a16(2 * BCL_NCEP * plan.maxC1) + 2 * a16(sR * BCL_NCEP * plan.maxC1);
-    b += 2 * a16(2 * 3 * plan.maxV) + 2 * a16(sR * 3 * plan.maxV) + a16(sR * plan.maxV);
+    b += a16(4 * BCL_NCEP * plan.maxC1) + a16(2 * sR * BCL_NCEP * plan.maxC1);
+    b += a16(4 * 3 * plan.maxV) + a16(2 * sR * 3 * plan.maxV) + a16(2 * sR * plan.maxV);
     b += 2 * a16(4 * plan.maxE1);
     b += a16(4 * plan.maxE2) + a16(4 * plan.maxC2);   // internal indices
     return b;
 }
+template <class R> int bcl_blocks_per_sm() { return bcl_min_blocks<R>(); }
+template int bcl_blocks_per_sm<float>();
+template int bcl_blocks_per_sm<double>();
 int bcl_max_edges_per_patch() { return BCL_NT * BCL_NI; }
 int bcl_max_cells_per_patch() { return BCL_NT * BCL_NI; }
 template <class R> const void *bcl_fused_kernel_ptr() {

@@ -202,6 +202,8 @@ void launch_bcl_fused_batch(const BclJob<R> *jobs, const int *first, int njobs, 
 template <class R> const void *bcl_fused_batch_kernel_ptr();
 struct BclPlan;
 template <class R> size_t bcl_smem_bytes(const BclPlan &plan);
+// CTAs per SM the fused baroclinic kernel is compiled for (its launch bounds)
+template <class R> int bcl_blocks_per_sm();
 int bcl_max_edges_per_patch();
 int bcl_max_cells_per_patch();
 template <class R> const void *bcl_fused_kernel_ptr();
