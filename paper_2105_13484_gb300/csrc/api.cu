@@ -568,6 +568,7 @@ struct Engine : EngineBase {
     R *ubar_n, *ut_n;
     double *h_n, *zeta_n;
     R *hR_n, *tr_n;
+    double toff[2] = {0.0, 0.0};   // tracer t is held as tracer - toff[t]
     // stage buffers
     R *ut_1, *ut_c, *ut_3, *ubar_1, *ubar_h, *ubar_np1;
     R *G0, *G1, *G2, *Gw;
@@ -734,7 +735,7 @@ struct Engine : EngineBase {
                 }
             }
             if (!cached) continue;
-            const size_t smem = bcl_smem_bytes<R>(*cached);
+            const size_t smem = bcl_smem_bytes<R>(*cached, m.L);
             if (smem + 1024 + sizeof(BclJob<R>) + 64 > (size_t)smem_block) continue;
             if (pass == 0 && (size_t)bcl_blocks_per_sm<R>() * (smem + 1024 + sizeof(BclJob<R>)) >
                                  (size_t)smem_sm)
@@ -823,7 +824,7 @@ struct Engine : EngineBase {
         const unsigned int sR = sizeof(R);
         std::vector<int> noc, noe, nie, cg, eg, c12, nel, ncl;
         std::vector<unsigned short> eo, ce;
-        std::vector<R> cf, idc, dv, Hh;
+        std::vector<R> cf, dv, Hh;
         for (const TilePatch &t : plan.patches) {
             noc.push_back(t.n_own_c); noe.push_back(t.n_own_e); nie.push_back(t.n_int_e);
             // sub-stage s of a sub-step needs edges of ring <= K - s and cells of
@@ -839,7 +840,7 @@ struct Engine : EngineBase {
             // term-major within the patch ([j][ne], [j][nc]) so that a warp's
             // load of term j of 32 consecutive entries is one contiguous segment
             const size_t cf0 = cf.size(), dv0 = dv.size();
-            cf.resize(cf0 + (size_t)t.ne * TILE_NE2P, R(0));
+            cf.resize(cf0 + (size_t)t.ne * TILE_CFR, R(0));
             dv.resize(dv0 + (size_t)t.nc * TILE_NCEP, R(0));
             for (int k = 0; k < t.ne; k++) {
                 for (int j = 0; j < TILE_NE2P; j++) {
@@ -848,7 +849,7 @@ struct Engine : EngineBase {
                     eo.push_back((unsigned short)(le * sR));
                     if (on) cf[cf0 + (size_t)j * t.ne + k] = (R)t.cfc[(size_t)k * m.maxE2 + j];
                 }
-                idc.push_back((R)t.invdc[k]);
+                cf[cf0 + (size_t)TILE_NE2P * t.ne + k] = (R)t.invdc[k];
             }
             for (int k = 0; k < t.nc; k++)
                 for (int j = 0; j < TILE_NCEP; j++) {
@@ -865,7 +866,7 @@ struct Engine : EngineBase {
         t.n_own_c = A.upload(noc); t.n_own_e = A.upload(noe); t.n_int_e = A.upload(nie);
         t.ne_lim = A.upload(nel); t.nc_lim = A.upload(ncl);
         t.cell_gid = A.upload(cg); t.edge_gid = A.upload(eg); t.c12 = A.upload(c12);
-        t.eoe = A.upload(eo); t.cfc = A.upload(cf); t.invdc = A.upload(idc);
+        t.eoe = A.upload(eo); t.cfc = A.upload(cf);
         t.ce = A.upload(ce); t.divc = A.upload(dv); t.H = A.upload(Hh);
         for (int b = 0; b < 2; b++) {
             t.xu[b] = A.alloc<R>(m.Ep);
@@ -890,8 +891,22 @@ struct Engine : EngineBase {
         p.g = prm->g; p.rho0 = prm->rho0; p.nu_h = prm->nu_h; p.nu_v = prm->nu_v;
         p.kappa_h = prm->kappa_h; p.kappa_v = prm->kappa_v; p.c_drag = prm->c_drag;
         p.nu_4 = prm->nu_4;
-        p.alpha = prm->eos_alpha; p.beta = prm->eos_beta; p.T_ref = prm->eos_T_ref;
-        p.S_ref = prm->eos_S_ref; p.zcoef = prm->g * (1.0 - prm->eos_rho_ref / prm->rho0);
+        // The FP32 tracers of the mixed form are held as anomalies from the
+        // EOS reference values (full columns): the density anomaly depends on
+        // differences of T and S between neighbouring columns that are 1e-3 to
+        // 1e-4 of S itself, which an FP32 S of about 35 does not resolve.
+        // Transport, mixing and the stage combinations are linear in the
+        // tracer and conserve it with the same mass fluxes, so the anomaly
+        // obeys the same equations; the kernels' EOS references become the
+        // remainder (zero).
+        toff[0] = toff[1] = 0.0;
+        if (mixed && !m.partial) {
+            toff[0] = prm->eos_T_ref;
+            toff[1] = prm->eos_S_ref;
+        }
+        p.alpha = prm->eos_alpha; p.beta = prm->eos_beta; p.T_ref = prm->eos_T_ref - toff[0];
+        p.S_ref = prm->eos_S_ref - toff[1];
+        p.zcoef = prm->g * (1.0 - prm->eos_rho_ref / prm->rho0);
         p.nT = prm->nTracers; p.recon = prm->recon; p.wind = nullptr; p.wind_f = nullptr;
         fill_phys(p.pd);
         fill_phys(p.pf);
@@ -1037,7 +1052,7 @@ struct Engine : EngineBase {
             const int t = field - SSE_FIELD_TRACER0;
             if (t >= p.nT) return SSE_ERR_INVALID_ARG;
             if (!direct) CK(cudaMemcpyAsync(stage, host, sizeof(H) * m.C * L, cudaMemcpyHostToDevice, s));
-            launch_to_device<R>(in, tr_n + (size_t)t * L * m.Cp, m.C, L, m.Cp, m.cperm, s);
+            launch_to_device<R>(in, tr_n + (size_t)t * L * m.Cp, m.C, L, m.Cp, m.cperm, s, toff[t]);
             if (m.partial) launch_mask_layers<R>(tr_n + (size_t)t * L * m.Cp, m.C, L, m.Cp, m.kc, s);
             break;
         }
@@ -1096,7 +1111,8 @@ struct Engine : EngineBase {
         case SSE_FIELD_TRACER1: {
             const int t = field - SSE_FIELD_TRACER0;
             if (t >= p.nT) return SSE_ERR_INVALID_ARG;
-            launch_from_device<R>(tr_n + (size_t)t * L * m.Cp, out, m.C, L, m.Cp, m.cperm, s);
+            launch_from_device<R>(tr_n + (size_t)t * L * m.Cp, out, m.C, L, m.Cp, m.cperm, s,
+                                  toff[t]);
             n = (size_t)m.C * L;
             break;
         }
@@ -1421,7 +1437,7 @@ struct Engine : EngineBase {
     }
 
     int diagnostics(sse_diag *out) override {
-        launch_diag<R>(m, ubar_n, ut_n, h_n, tr_n, p.nT, zeta_n, dpart, dparts, dout, s);
+        launch_diag<R>(m, ubar_n, ut_n, h_n, tr_n, p.nT, toff, zeta_n, dpart, dparts, dout, s);
         int rc = check_launch();
         if (rc) return rc;
         double v[9];

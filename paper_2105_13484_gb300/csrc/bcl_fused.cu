@@ -7,8 +7,8 @@
 // HBM.  Here one CTA owns a compact patch of edges (csrc/tiles.cu,
 // build_bcl_plan) and walks the layers from the top, two at a time: each
 // pair's velocity and thickness over the patch and its halo are copied into
-// shared memory (cp.async into a ring of three pairs, one pair ahead of the
-// two in use), the cell, vertex and edge diagnostics of both layers are
+// shared memory (cp.async into a ring of NB2 pairs, NB2 - 2 pairs ahead of
+// the two in use), the cell, vertex and edge diagnostics of both layers are
 // formed in shared memory, and the owned edges' tendencies follow.  Only the
 // state itself crosses HBM: utilde, h and the tracers in, utilde out.
 //
@@ -47,9 +47,12 @@ template <class R> __device__ __forceinline__ void cp_async(R *dst, const R *src
 }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::); }
-// wait until at most one committed group is still in flight
-__device__ __forceinline__ void cp_async_wait_1() { asm volatile("cp.async.wait_group 1;\n" ::); }
-// layer pairs staged in shared memory: p and p + 1 in use, p + 2 in flight
+// wait until at most N committed groups are still in flight
+template <int N> __device__ __forceinline__ void cp_async_wait_n() {
+    asm volatile("cp.async.wait_group %0;\n" ::"n"(N));
+}
+// layer pairs staged in shared memory: p and p + 1 in use, p + 2 .. p + NB2 - 1
+// in flight (each pair's copies get NB2 - 2 pairs of compute to land)
 constexpr int NB2 = 3;
 // CTAs per SM of the fused kernel: two in FP32 (128 registers a thread); one
 // in FP64, whose per-thread column state needs about 250 registers
@@ -63,6 +66,13 @@ template <> struct Sh4<double> { using T = dbl4s; };
 template <class R> __device__ __forceinline__ const R *sfrac_R(const DMesh &m);
 template <> __device__ __forceinline__ const double *sfrac_R<double>(const DMesh &m) { return m.sfrac; }
 template <> __device__ __forceinline__ const float *sfrac_R<float>(const DMesh &m) { return m.sfrac_f; }
+
+// a / b for the per-layer quotients: correctly rounded in FP64; in FP32 the
+// reciprocal-multiply form (within 2 ulp for the divisors met here, thicknesses
+// of 1e-3 to 1e4 m), whose error is far below the FP32 form's other rounding
+template <class R> __device__ __forceinline__ R qdiv(R a, R b);
+template <> __device__ __forceinline__ double qdiv<double>(double a, double b) { return a / b; }
+template <> __device__ __forceinline__ float qdiv<float>(float a, float b) { return __fdividef(a, b); }
 
 // elements of R in n rounded up to 16 bytes
 template <class R> __host__ __device__ __forceinline__ int pad16(int n) {
@@ -128,9 +138,9 @@ __device__ __forceinline__ void colflux_edge(const DMesh &m, R *__restrict__ uba
 // pair of layers (k, k + 1) side by side, so one vector load serves both and
 // every index and coefficient is read once per pair; the column recurrences
 // (w, the pressure-gradient sums, D_zt u, G) then advance through the two
-// layers in order.  A ring of three pair buffers holds pair p (being
+// layers in order.  A ring of NB2 pair buffers holds pair p (being
 // computed), pair p + 1 (its first layer is the layer below pair p's second)
-// and pair p + 2 (in flight).
+// and pairs p + 2 .. p + NB2 - 1 (in flight).
 // ---------------------------------------------------------------------------
 template <class R, int NT, int NI>
 __device__ __forceinline__ void bcl_fused_patch(const DMesh &m, const DParams &p, const DBcl<R> &t,
@@ -138,6 +148,9 @@ __device__ __forceinline__ void bcl_fused_patch(const DMesh &m, const DParams &p
     using R2 = V2<R>;
     using R4 = typename Sh4<R>::T;
     const int tid = threadIdx.x;
+    // C1 cells are dealt from the last thread down, so that the threads that
+    // hold a second vertex (the first ones) hold no cell
+    const int ctid = NT - 1 - tid;
     const int *cn = t.cnt + 8 * pid;
     const int nE0 = cn[0], nE1 = cn[1], nE2 = cn[2], nC1 = cn[3], nC2 = cn[4], nV = cn[5];
     const int *eg_g = t.egid + t.off_e2[pid];
@@ -152,10 +165,12 @@ __device__ __forceinline__ void bcl_fused_patch(const DMesh &m, const DParams &p
     R *ub_s = carve<R>(sp, t.maxE2 + 1);
     // buffer b of each ring starts at b times its stride (a multiple of 16 bytes)
     const int sE = pad16<R2>(t.maxE2 + 1), sC = pad16<R2>(t.maxC2 + 1), s1 = pad16<R2>(t.maxC1);
+    const int s0 = pad16<R2>(t.maxE0);
     R2 *ut_r = carve<R2>(sp, NB2 * sE);
     R2 *h_r = carve<R2>(sp, NB2 * sC);
     R2 *T_r = carve<R2>(sp, NB2 * s1);
     R2 *S_r = carve<R2>(sp, NB2 * s1);
+    R2 *un_r = carve<R2>(sp, NB2 * s0);   // the old level at the owned edges
     R2 *q_s = carve<R2>(sp, t.maxV);
     R2 *om_s = carve<R2>(sp, t.maxV);
     R4 *hq_s = carve<R4>(sp, t.maxE1 + 1);   // (h_e u, q_e) of both layers
@@ -178,6 +193,11 @@ __device__ __forceinline__ void bcl_fused_patch(const DMesh &m, const DParams &p
     // the patch's internal edge and cell indices (each layer's copies use them)
     int *eg = carve<int>(sp, t.maxE2);
     int *cg = carve<int>(sp, t.maxC2);
+    R *sf_s = carve<R>(sp, L);   // the layers' z-star stretching fractions s_k
+    {
+        const R *sfr = sfrac_R<R>(m);
+        for (int k = tid; k < L; k += NT) sf_s[k] = sfr[k];
+    }
     for (int j = tid; j < nE2; j += NT) eg[j] = eg_g[j];
     for (int j = tid; j < nC2; j += NT) cg[j] = cg_g[j];
     __syncthreads();
@@ -234,6 +254,15 @@ __device__ __forceinline__ void bcl_fused_patch(const DMesh &m, const DParams &p
                 if (has1) cp_async(Sd + 2 * j + 1, S0 + Cp + gc);
             }
         }
+        if (comb) {
+            R *nd = reinterpret_cast<R *>(un_r + b * s0);
+            const R *n0 = a.ut_n + (size_t)k0 * Ep;
+            for (int j = tid; j < nE0; j += NT) {
+                const int ge = eg[j];
+                cp_async(nd + 2 * j, n0 + ge);
+                if (has1) cp_async(nd + 2 * j + 1, n0 + Ep + ge);
+            }
+        }
         cp_async_commit();
     };
 
@@ -248,16 +277,18 @@ __device__ __forceinline__ void bcl_fused_patch(const DMesh &m, const DParams &p
         z4.x = R(0); z4.y = R(0); z4.z = R(0); z4.w = R(0);
         hq_s[nE1] = z4;
     }
-    issue(0, 0);
-    if (NP > 1) issue(1, 1);
-    else cp_async_commit();
+    // pairs 0 .. NB2 - 2 in flight (one commit group each, empty past the bottom)
+    for (int pp = 0; pp < NB2 - 1; pp++) {
+        if (pp < NP) issue(pp, pp);
+        else cp_async_commit();
+    }
 
     // cells of C1 held by this thread: the depth integral of div(h_e u) and
     // the running column sum
     R dsum[NI], W[NI];
 #pragma unroll
     for (int s = 0; s < NI; s++) {
-        const int c = tid + s * NT;
+        const int c = ctid + s * NT;
         dsum[s] = R(0); W[s] = R(0);
         if (c < nC1) {
             R d = R(0);
@@ -325,7 +356,6 @@ __device__ __forceinline__ void bcl_fused_patch(const DMesh &m, const DParams &p
     const R g = q.g, alpha = q.alpha, beta = q.beta, Tref = q.T_ref, Sref = q.S_ref;
     const R inv_rho0 = q.inv_rho0, nu_h = q.nu_h, nu_v = q.nu_v, cdrag = q.c_drag;
     const R dt = a.dt, ca = a.a, cb = a.b;
-    const R *sfr = sfrac_R<R>(m);
     R Sk = R(0);   // sum_{l<k} s_l
 
     for (int pp = 0; pp < NP; pp++) {
@@ -334,10 +364,11 @@ __device__ __forceinline__ void bcl_fused_patch(const DMesh &m, const DParams &p
         const int bc = pp % NB2, bn = (pp + 1) % NB2;
         const R2 *ut_c = ut_r + bc * sE, *h_c = h_r + bc * sC;
         const R2 *ut_nx = ut_r + bn * sE, *h_nx = h_r + bn * sC;
-        const R2 *T_c = T_r + bc * s1, *S_c = S_r + bc * s1;
-        cp_async_wait_all();
+        const R2 *T_c = T_r + bc * s1, *S_c = S_r + bc * s1, *un_c = un_r + bc * s0;
+        cp_async_wait_n<NB2 - 3>();
         __syncthreads();   // pairs pp and pp + 1 in shared memory; pair pp - 1's readers done
-        if (pp + 2 < NP) issue(pp + 2, (pp + 2) % NB2);
+        if (pp + NB2 - 1 < NP) issue(pp + NB2 - 1, (pp + NB2 - 1) % NB2);
+        else cp_async_commit();
         // ---- vertices: relative vorticity, kite-averaged thickness, PV
         for (int v = tid; v < nV; v += NT) {
             R2 ot, hv;
@@ -357,16 +388,16 @@ __device__ __forceinline__ void bcl_fused_patch(const DMesh &m, const DParams &p
             R2 om, qv;
             om.x = bf.x + ot.x;
             om.y = bf.x + ot.y;
-            qv.x = (bf.y + ot.x) / hv.x;
-            qv.y = (bf.y + ot.y) / hv.y;
+            qv.x = qdiv(bf.y + ot.x, hv.x);
+            qv.y = qdiv(bf.y + ot.y, hv.y);
             om_s[v] = om;
             q_s[v] = qv;
         }
         // ---- cells of C1: K, div u, div(h_e u), rho', w
-        const R sk0 = sfr[k0], sk1 = has1 ? sfr[k0 + 1] : R(0);
+        const R sk0 = sf_s[k0], sk1 = has1 ? sf_s[k0 + 1] : R(0);
 #pragma unroll
         for (int s = 0; s < NI; s++) {
-            const int c = tid + s * NT;
+            const int c = ctid + s * NT;
             if (c < nC1) {
                 const R2 hk = h_c[c];
                 R2 ke, dl, dv;
@@ -411,16 +442,6 @@ __device__ __forceinline__ void bcl_fused_patch(const DMesh &m, const DParams &p
             }
         }
         __syncthreads();
-        // the old level at the owned edges, read by the owned edges below
-        R un0[NI], un1[NI];
-#pragma unroll
-        for (int s = 0; s < NI; s++) {
-            un0[s] = R(0); un1[s] = R(0);
-            if (comb && tid + s * NT < nE0) {
-                un0[s] = ldg(a.ut_n + (size_t)k0 * Ep + ge[s]);
-                if (has1) un1[s] = ldg(a.ut_n + (size_t)(k0 + 1) * Ep + ge[s]);
-            }
-        }
         // ---- edges of E1: (h_e u, q_e) of both layers
         for (int e = tid; e < nE1; e += NT) {
             const int cc = x_e1c[e], vv = x_e1v[e];
@@ -460,6 +481,9 @@ __device__ __forceinline__ void bcl_fused_patch(const DMesh &m, const DParams &p
             const R2 K1 = cK[c1], K2 = cK[c2], P1 = cR[c1], P2 = cR[c2];
             const R2 D1 = cD[c1], D2 = cD[c2], o1 = om_s[v1], o2 = om_s[v2];
             const R2 W1 = cW1[c1], W2 = cW1[c2];
+            R2 un2;
+            un2.x = R(0); un2.y = R(0);
+            if (comb) un2 = un_c[e];
             // the layer below the pair: the first of the next pair
             R utn = R(0), h1n = R(0), h2n = R(0);
             if (k0 + 2 < L) {
@@ -488,7 +512,7 @@ __device__ __forceinline__ void bcl_fused_patch(const DMesh &m, const DParams &p
                 if (k + 1 < L) {
                     const R u_next = ube + (i ? utn : utc.y);
                     const R he_next = R(0.5) * (i ? h1n + h2n : h1.y + h2.y);
-                    Dk1 = (u_cur - u_next) / (R(0.5) * (he_cur + he_next));
+                    Dk1 = qdiv(u_cur - u_next, R(0.5) * (he_cur + he_next));
                     wk1 = R(0.5) * (i ? W1.y + W2.y : W1.x + W2.x);
                 }
                 const R vadv = R(0.5) * (wk[s] * Dk[s] + wk1 * Dk1);
@@ -508,7 +532,7 @@ __device__ __forceinline__ void bcl_fused_patch(const DMesh &m, const DParams &p
                 } else {
                     Xbot = nu_v * Dk1;
                 }
-                const R vvisc = (Xtop - Xbot) / he_cur;
+                const R vvisc = qdiv(Xtop - Xbot, he_cur);
                 const R lap = ((i ? D2.y : D2.x) - (i ? D1.y : D1.x)) * idc[s] -
                               ((i ? o2.y : o2.x) - (i ? o1.y : o1.x)) * idv[s];
                 const R gzeta = q.zcoef * dzeta[s] * idc[s];
@@ -517,7 +541,7 @@ __device__ __forceinline__ void bcl_fused_patch(const DMesh &m, const DParams &p
                 const R ut1 = ut_cur + dt * rhs;
                 num[s] += he_cur * ut1;
                 den[s] += he_cur;
-                const R unk = i ? un1[s] : un0[s];
+                const R unk = i ? un2.y : un2.x;
                 a.ut_out[(size_t)k * Ep + ge[s]] = comb ? ca * unk + cb * ut1 : cb * ut1;
                 Dk[s] = Dk1;
                 wk[s] = wk1;
@@ -631,7 +655,7 @@ __global__ void __launch_bounds__(128) k_colflux_batch(const ColfluxJob<R> *__re
 constexpr int BCL_NT = 256;
 constexpr int BCL_NI = 2;
 
-template <class R> size_t bcl_smem_bytes(const BclPlan &plan) {
+template <class R> size_t bcl_smem_bytes(const BclPlan &plan, int L) {
     auto a16 = [](size_t b) { return (b + 15) / 16 * 16; };
     const size_t sR = sizeof(R);
     size_t b = 0;
@@ -639,6 +663,7 @@ template <class R> size_t bcl_smem_bytes(const BclPlan &plan) {
     b += NB2 * a16(2 * sR * (plan.maxE2 + 1));         // utilde (pair ring)
     b += NB2 * a16(2 * sR * (plan.maxC2 + 1));         // h
     b += 2 * NB2 * a16(2 * sR * plan.maxC1);           // T, S
+    b += NB2 * a16(2 * sR * plan.maxE0);               // old-level utilde
     // (each ring is carved as one block of NB2 16-byte padded strides)
     b += 2 * a16(2 * sR * plan.maxV);                  // q, omega
     b += a16(4 * sR * (plan.maxE1 + 1));               // (h_e u, q_e) x 2
@@ -649,6 +674,7 @@ template <class R> size_t bcl_smem_bytes(const BclPlan &plan) {
     b += a16(4 * 3 * plan.maxV) + a16(2 * sR * 3 * plan.maxV) + a16(2 * sR * plan.maxV);
     b += 2 * a16(4 * plan.maxE1);
     b += a16(4 * plan.maxE2) + a16(4 * plan.maxC2);   // internal indices
+    b += a16(sR * L);                                  // s_k
     return b;
 }
 template <class R> int bcl_blocks_per_sm() { return bcl_min_blocks<R>(); }
@@ -697,8 +723,8 @@ template void launch_bcl_fused_batch<double>(const BclJob<double> *, const int *
                                              size_t, cudaStream_t);
 template const void *bcl_fused_batch_kernel_ptr<float>();
 template const void *bcl_fused_batch_kernel_ptr<double>();
-template size_t bcl_smem_bytes<float>(const BclPlan &);
-template size_t bcl_smem_bytes<double>(const BclPlan &);
+template size_t bcl_smem_bytes<float>(const BclPlan &, int);
+template size_t bcl_smem_bytes<double>(const BclPlan &, int);
 template const void *bcl_fused_kernel_ptr<float>();
 template const void *bcl_fused_kernel_ptr<double>();
 template void launch_colflux<float>(const DMesh &, float *, float *, const float *, bool, float *,

@@ -296,8 +296,19 @@ __global__ void __launch_bounds__(BTR_THREADS) k_btr(DMesh m, BtrArgs<R> a, Barr
 // (two patches) per SM whose block barriers overlap each other's work
 constexpr int TILE_NE2 = 10;  // edgesOnEdge terms evaluated per edge (padding -> dummy, 0)
 
+// The patch carries the sub-cycle as increments from its starting state:
+// u* = ubar - ubar_start and z* = zeta - zeta_start.  The starting state's
+// forcing F0 = C_f(ubar_start) - g grad zeta_start + G is formed once per
+// launch from the FP64 starting SSH, and the starting column depth d0 =
+// zeta_start + H is kept per cell, so that the sub-steps round only the
+// (small) increments: in FP32 the full ubar and zeta would lose the 1e-3 to
+// 1e-2 of themselves that their gradients and changes over a sub-cycle are.
+// Every SSPRK combination has weights summing to one, so it applies to the
+// increments unchanged.  (1/dc is read from global memory with the Coriolis
+// coefficients, as their last row, which keeps the patch's shared memory at
+// its plain size.)
 template <class R> struct TileSmem {
-    R *u0, *ua, *uh, *fl, *z0, *za, *zh, *G, *H, *idc;
+    R *u0, *ua, *uh, *fl, *z0, *za, *zh, *F0, *ub0, *d0;
     unsigned int *c12;                // packed byte offsets of (c1, c2) into the cell arrays
     unsigned short *eoe;              // [ne+1][TILE_NE2P] byte offsets into the edge arrays
     unsigned short *ce;               // [nc+1][TILE_NCEP] byte offsets into fl
@@ -315,7 +326,7 @@ __device__ __forceinline__ TileSmem<R> carve(char *base, int ne, int nc) {
     R *r = (R *)c;
     s.u0 = r; r += ne1; s.ua = r; r += ne1; s.uh = r; r += ne1; s.fl = r; r += ne1;
     s.z0 = r; r += nc1; s.za = r; r += nc1; s.zh = r; r += nc1;
-    s.G = r; r += ne1; s.H = r; r += nc1; s.idc = r; r += ne1;
+    s.F0 = r; r += ne1; s.ub0 = r; r += ne1; s.d0 = r; r += nc1;
     c = align16((char *)r);
     s.c12 = (unsigned int *)c; c = align16(c + 4 * ne1);
     s.eoe = (unsigned short *)c; c = align16(c + 2 * TILE_NE2P * (size_t)ne1);
@@ -327,15 +338,15 @@ template <class R> __device__ __forceinline__ R at(const R *base, unsigned int o
     return *(const R *)((const char *)base + off);
 }
 
-// forward-Euler edge update on the patch: returns the new ubar, sets the flux.
-// The patch's Coriolis coefficients are term-major: term j of edge l at
-// cfc[j * ne + l].
+// forward-Euler edge update on the patch, on the increments u, z: returns the
+// new ubar increment, sets the flux of the full state.  The patch's Coriolis
+// coefficients are term-major: term j of edge l at cfc[j * ne + l].
 template <class R>
 __device__ __forceinline__ R tile_fe_edge(const TileSmem<R> &S, const R *__restrict__ cfc, int ne,
                                           int l, const R *u, const R *z, R tau, R g, R &flux) {
-    R cf[TILE_NE2P];
+    R cf[TILE_CFR];   // the Coriolis coefficients, then 1 / d_e
 #pragma unroll
-    for (int j = 0; j < TILE_NE2P; j++) cf[j] = __ldg(cfc + (size_t)j * ne + l);
+    for (int j = 0; j < TILE_CFR; j++) cf[j] = __ldg(cfc + (size_t)j * ne + l);
     const unsigned int *eo = (const unsigned int *)(S.eoe + (size_t)l * TILE_NE2P);
     unsigned int o[TILE_NE2P];
 #pragma unroll
@@ -350,8 +361,8 @@ __device__ __forceinline__ R tile_fe_edge(const TileSmem<R> &S, const R *__restr
     const unsigned int a = cc & 0xffffu, b = cc >> 16;
     const R za = at(z, a), zb = at(z, b);
     const R ue = u[l];
-    flux = ue * (R(0.5) * ((za + at(S.H, a)) + (zb + at(S.H, b))));
-    return ue + tau * (acc - g * (zb - za) * S.idc[l] + S.G[l]);
+    flux = (S.ub0[l] + ue) * (R(0.5) * ((at(S.d0, a) + at(S.d0, b)) + (za + zb)));
+    return ue + tau * (S.F0[l] + acc - g * (zb - za) * cf[TILE_NE2P]);
 }
 
 // term j of cell l's divergence coefficients at dvc[j * nc + l]
@@ -416,7 +427,7 @@ __global__ void __launch_bounds__(NT, 1024 / NT) k_btr_tiled(DTiles<R> t, BtrArg
     const int neA = t.ne_lim[3 * p], neB = t.ne_lim[3 * p + 1], neC = t.ne_lim[3 * p + 2];
     const int ncA = t.nc_lim[3 * p], ncB = t.nc_lim[3 * p + 1], ncC = t.nc_lim[3 * p + 2];
     const TileSmem<R> S = carve<R>(smem_raw, ne, nc);
-    const R *cfc = t.cfc + (size_t)eoff * TILE_NE2P;
+    const R *cfc = t.cfc + (size_t)eoff * TILE_CFR;
     const R *dvc = t.divc + (size_t)coff * TILE_NCEP;
     const R tau = (R)a.tau, g = (R)a.g;
     const R third = R(1.0 / 3.0), two_thirds = R(2.0 / 3.0);
@@ -432,19 +443,27 @@ __global__ void __launch_bounds__(NT, 1024 / NT) k_btr_tiled(DTiles<R> t, BtrArg
         hc[k] = ch < nc ? t.cell_gid[coff + ch] : -1;
     }
 
-    // ---- load the patch (the extra slot ne / nc is the zero-valued dummy)
+    // ---- load the patch (the extra slot ne / nc is the zero-valued dummy);
+    // the increments start at zero
     for (int l = tid; l <= ne; l += nt) {
-        R u = R(0), G = R(0), d = R(0);
+        R u = R(0), d = R(0);
+        double G = 0.0;
         unsigned int cc = (unsigned int)(nc * sizeof(R)) | ((unsigned int)(nc * sizeof(R)) << 16);
         if (l < ne) {
             const int gid = t.edge_gid[eoff + l];
             u = a.ub_start[gid];
-            G = a.G[gid];
-            d = t.invdc[eoff + l];
+            G = (double)a.G[gid];
+            d = cfc[(size_t)TILE_NE2P * ne + l];
             cc = (unsigned int)t.c12[eoff + l];
         }
-        S.u0[l] = u; S.G[l] = G; S.idc[l] = d; S.c12[l] = cc;
-        S.ua[l] = R(0); S.uh[l] = R(0); S.fl[l] = R(0);
+        // the SSH-gradient part of the starting forcing, from the FP64
+        // starting SSH (the dummy cell: zeta = 0)
+        const int ia = (int)((cc & 0xffffu) / sizeof(R)), ib = (int)((cc >> 16) / sizeof(R));
+        const double za = ia < nc ? a.z_start[t.cell_gid[coff + ia]] : 0.0;
+        const double zb = ib < nc ? a.z_start[t.cell_gid[coff + ib]] : 0.0;
+        S.F0[l] = (R)(G - a.g * (zb - za) * (double)d);
+        S.ub0[l] = u; S.c12[l] = cc;
+        S.u0[l] = R(0); S.ua[l] = R(0); S.uh[l] = R(0); S.fl[l] = R(0);
     }
     {
         // rows are TILE_NE2P * 2 = 20 bytes: copy in 4-byte words (every row and the
@@ -456,9 +475,9 @@ __global__ void __launch_bounds__(NT, 1024 / NT) k_btr_tiled(DTiles<R> t, BtrArg
         if (tid < TILE_NE2P) S.eoe[(size_t)ne * TILE_NE2P + tid] = (unsigned short)(ne * sizeof(R));
     }
     for (int l = tid; l <= nc; l += nt) {
-        const R z = (l < nc) ? (R)a.z_start[t.cell_gid[coff + l]] : R(0);
-        S.z0[l] = z; S.za[l] = z; S.zh[l] = z;
-        S.H[l] = t.H[coff + p + l];
+        const double z = (l < nc) ? a.z_start[t.cell_gid[coff + l]] : 0.0;
+        S.d0[l] = (R)(z + (double)t.H[coff + p + l]);
+        S.z0[l] = R(0); S.za[l] = R(0); S.zh[l] = R(0);
     }
     {
         // rows of TILE_NCEP * 2 = 12 bytes, copied in 4-byte words
@@ -471,6 +490,19 @@ __global__ void __launch_bounds__(NT, 1024 / NT) k_btr_tiled(DTiles<R> t, BtrArg
     FzAcc<R> Fz[OWN];
 #pragma unroll
     for (int k = 0; k < OWN; k++) Fs[k] = R(0);
+    __syncthreads();
+    // the Coriolis term of the starting ubar completes the starting forcing
+    for (int l = tid; l < ne; l += nt) {
+        const unsigned int *eo = (const unsigned int *)(S.eoe + (size_t)l * TILE_NE2P);
+        double cb = 0.0;
+#pragma unroll
+        for (int i = 0; i < TILE_NE2 / 2; i++) {
+            const unsigned int v = eo[i];
+            cb += (double)__ldg(cfc + (size_t)(2 * i) * ne + l) * (double)at(S.ub0, v & 0xffffu);
+            cb += (double)__ldg(cfc + (size_t)(2 * i + 1) * ne + l) * (double)at(S.ub0, v >> 16);
+        }
+        S.F0[l] = (R)((double)S.F0[l] + cb);
+    }
     __syncthreads();
 
     const R wAB = (ORDER == 2) ? R(0.5) : R(1.0 / 6.0);
@@ -589,15 +621,16 @@ __global__ void __launch_bounds__(NT, 1024 / NT) k_btr_tiled(DTiles<R> t, BtrArg
         buf ^= 1;
         __syncthreads();
     }
-    // ---- outputs for the owned edges and cells
+    // ---- outputs for the owned edges and cells: starting state plus increment
 #pragma unroll
     for (int k = 0; k < OWN; k++) {
         if (oe[k] >= 0) {
-            const R u0 = S.u0[tid + k * nt];
+            const double u0 = (double)S.ub0[tid + k * nt] + (double)S.u0[tid + k * nt];
             a.Fz[oe[k]] = Fz[k].value(invM);
-            a.ub_out[oe[k]] = a.X ? (R)(a.alpha * (double)a.X[oe[k]] + a.beta * (double)u0) : u0;
+            a.ub_out[oe[k]] = a.X ? (R)(a.alpha * (double)a.X[oe[k]] + a.beta * u0) : (R)u0;
         }
-        if (a.z_out && oc[k] >= 0) a.z_out[oc[k]] = (double)S.z0[tid + k * nt];
+        if (a.z_out && oc[k] >= 0)
+            a.z_out[oc[k]] = a.z_start[oc[k]] + (double)S.z0[tid + k * nt];
     }
 }
 

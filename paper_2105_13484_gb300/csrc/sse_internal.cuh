@@ -201,7 +201,7 @@ void launch_bcl_fused_batch(const BclJob<R> *jobs, const int *first, int njobs, 
                             size_t smem, cudaStream_t s);
 template <class R> const void *bcl_fused_batch_kernel_ptr();
 struct BclPlan;
-template <class R> size_t bcl_smem_bytes(const BclPlan &plan);
+template <class R> size_t bcl_smem_bytes(const BclPlan &plan, int L);
 // CTAs per SM the fused baroclinic kernel is compiled for (its launch bounds)
 template <class R> int bcl_blocks_per_sm();
 int bcl_max_edges_per_patch();
@@ -251,8 +251,8 @@ template <class R> struct DTiles {
     const int *cell_gid, *edge_gid;  // local -> global
     const int *c12;                  // [sum ne] byte offsets of local (c1, c2): c1 | c2 << 16
     const unsigned short *eoe;       // [sum ne][TILE_NE2P] byte offsets of local edgesOnEdge
-    const R *cfc;                    // per patch [TILE_NE2P][ne] Coriolis coefficients (0 on padding)
-    const R *invdc;                  // [sum ne]
+    const R *cfc;                    // per patch [TILE_CFR][ne]: Coriolis coefficients (0 on
+                                     // padding), then 1 / d_e
     const unsigned short *ce;        // [sum nc][TILE_NCEP] byte offsets of local edgesOnCell
     const R *divc;                   // per patch [TILE_NCEP][nc] divergence coefficients
     const R *H;                      // patch p at cell_off[p] + p: [nc_p + 1]
@@ -346,13 +346,15 @@ void launch_thick_fused(const DThick &t, const DMesh &m, const DParams &p, const
 
 // layout conversion: host-order [n][L] in precision H (FP64 or FP32) <->
 // device layer-major R [L][np]
-// (perm: the caller's index -> the internal one, DMesh::cperm / eperm)
+// (perm: the caller's index -> the internal one, DMesh::cperm / eperm); the
+// device holds the value minus `off` (a tracer's storage offset), the way
+// back adds it
 template <class R, class H>
 void launch_to_device(const H *src, R *dst, int n, int L, int np, const int *perm,
-                      cudaStream_t s);
+                      cudaStream_t s, double off = 0.0);
 template <class R, class H>
 void launch_from_device(const R *src, H *dst, int n, int L, int np, const int *perm,
-                        cudaStream_t s);
+                        cudaStream_t s, double off = 0.0);
 template <class R, class H>
 void launch_add_bar(const R *ubar, const R *ut, H *dst, int E, int L, int Ep,
                     const int *kmax, const int *perm, cudaStream_t s);
@@ -365,7 +367,7 @@ void launch_ssh(const DMesh &m, const double *h, double *zeta, cudaStream_t s);
 
 template <class R>
 void launch_diag(const DMesh &m, const R *ubar, const R *ut, const double *h, const R *tr,
-                 int nT, const double *zeta, double *partials, int nparts, double *out,
-                 cudaStream_t s);
+                 int nT, const double *toff, const double *zeta, double *partials, int nparts,
+                 double *out, cudaStream_t s);
 
 }  // namespace sse

@@ -596,22 +596,23 @@ __global__ void __launch_bounds__(128, 6) k_thickness(DMesh m, DParams p, ThickA
 // ---------------------------------------------------------------------------
 // host order [n][L] in precision H, the caller's numbering <-> device
 // layer-major [L][np] in precision R, the internal numbering (perm: caller
-// index -> internal index)
+// index -> internal index).  The device holds src - off (formed in FP64,
+// rounded once to R); the way back adds off in FP64.
 template <class H, class R>
 __global__ void k_to_device(const H *__restrict__ src, R *__restrict__ dst, int n, int L,
-                            int np, const int *__restrict__ perm) {
+                            int np, const int *__restrict__ perm, double off) {
     const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= (long long)n * L) return;
     const int i = (int)(t / L), k = (int)(t % L);
-    dst[(long long)k * np + perm[i]] = (R)src[t];
+    dst[(long long)k * np + perm[i]] = (R)((double)src[t] - off);
 }
 template <class R, class H>
 __global__ void k_from_device(const R *__restrict__ src, H *__restrict__ dst, int n, int L,
-                              int np, const int *__restrict__ perm) {
+                              int np, const int *__restrict__ perm, double off) {
     const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= (long long)n * L) return;
     const int i = (int)(t / L), k = (int)(t % L);
-    dst[t] = (H)src[(long long)k * np + perm[i]];
+    dst[t] = (H)((double)src[(long long)k * np + perm[i]] + off);
 }
 // u = ubar + utilde, summed in FP64 and rounded once to H
 template <class R, class H>
@@ -663,7 +664,8 @@ constexpr int NDIAG = 9;
 template <class R>
 __global__ void k_diag_partial(DMesh m, const R *__restrict__ ubar, const R *__restrict__ ut,
                                const double *__restrict__ h, const R *__restrict__ tr, int nT,
-                               const double *__restrict__ zeta, double *__restrict__ part) {
+                               double off0, double off1, const double *__restrict__ zeta,
+                               double *__restrict__ part) {
     __shared__ double sh[NDIAG][256];
     const int tid = threadIdx.x;
     double v[NDIAG] = {0, 0, 0, 0, 0, 1e300, 1e300, -1e300, 0};
@@ -674,8 +676,8 @@ __global__ void k_diag_partial(DMesh m, const R *__restrict__ ubar, const R *__r
         for (int k = 0; k < K; k++) {
             const double hk = h[k * Cp + i];
             hs += hk;
-            t0 += hk * (double)tr[k * Cp + i];
-            if (nT > 1) t1 += hk * (double)tr[(L + k) * Cp + i];
+            t0 += hk * ((double)tr[k * Cp + i] + off0);
+            if (nT > 1) t1 += hk * ((double)tr[(L + k) * Cp + i] + off1);
             v[5] = fmin(v[5], hk);
             if (!isfinite(hk) || !isfinite((double)tr[k * Cp + i])) v[8] = 1.0;
         }
@@ -809,13 +811,14 @@ void launch_thickness(const DMesh &m, const DParams &p, const ThickArgs<R> &a, c
 }
 template <class R, class H>
 void launch_to_device(const H *src, R *dst, int n, int L, int np, const int *perm,
-                      cudaStream_t s) {
-    k_to_device<H, R><<<nblk((long long)n * L, 256), 256, 0, s>>>(src, dst, n, L, np, perm);
+                      cudaStream_t s, double off) {
+    k_to_device<H, R><<<nblk((long long)n * L, 256), 256, 0, s>>>(src, dst, n, L, np, perm, off);
 }
 template <class R, class H>
 void launch_from_device(const R *src, H *dst, int n, int L, int np, const int *perm,
-                        cudaStream_t s) {
-    k_from_device<R, H><<<nblk((long long)n * L, 256), 256, 0, s>>>(src, dst, n, L, np, perm);
+                        cudaStream_t s, double off) {
+    k_from_device<R, H><<<nblk((long long)n * L, 256), 256, 0, s>>>(src, dst, n, L, np, perm,
+                                                                    off);
 }
 template <class R, class H>
 void launch_add_bar(const R *ubar, const R *ut, H *dst, int E, int L, int Ep,
@@ -839,8 +842,10 @@ void launch_ssh(const DMesh &m, const double *h, double *zeta, cudaStream_t s) {
 }
 template <class R>
 void launch_diag(const DMesh &m, const R *ubar, const R *ut, const double *h, const R *tr, int nT,
-                 const double *zeta, double *partials, int nparts, double *out, cudaStream_t s) {
-    k_diag_partial<R><<<nparts, 256, 0, s>>>(m, ubar, ut, h, tr, nT, zeta, partials);
+                 const double *toff, const double *zeta, double *partials, int nparts,
+                 double *out, cudaStream_t s) {
+    k_diag_partial<R><<<nparts, 256, 0, s>>>(m, ubar, ut, h, tr, nT, toff[0], toff[1], zeta,
+                                             partials);
     k_diag_final<<<1, 32, 0, s>>>(partials, nparts, out);
 }
 
@@ -859,20 +864,21 @@ void launch_diag(const DMesh &m, const R *ubar, const R *ut, const double *h, co
     template void launch_thickness<R>(const DMesh &, const DParams &, const ThickArgs<R> &,      \
                                       cudaStream_t);                                             \
     template void launch_to_device<R, double>(const double *, R *, int, int, int, const int *,   \
-                                              cudaStream_t);                                     \
+                                              cudaStream_t, double);                             \
     template void launch_to_device<R, float>(const float *, R *, int, int, int, const int *,     \
-                                             cudaStream_t);                                      \
+                                             cudaStream_t, double);                              \
     template void launch_from_device<R, double>(const R *, double *, int, int, int, const int *, \
-                                                cudaStream_t);                                   \
+                                                cudaStream_t, double);                           \
     template void launch_from_device<R, float>(const R *, float *, int, int, int, const int *,   \
-                                               cudaStream_t);                                    \
+                                               cudaStream_t, double);                            \
     template void launch_add_bar<R, double>(const R *, const R *, double *, int, int, int,       \
                                             const int *, const int *, cudaStream_t);             \
     template void launch_add_bar<R, float>(const R *, const R *, float *, int, int, int,         \
                                            const int *, const int *, cudaStream_t);              \
     template void launch_mask_layers<R>(R *, int, int, int, const int *, cudaStream_t);          \
     template void launch_diag<R>(const DMesh &, const R *, const R *, const double *, const R *, \
-                                 int, const double *, double *, int, double *, cudaStream_t);
+                                 int, const double *, const double *, double *, int, double *,  \
+                                 cudaStream_t);
 INST(double)
 INST(float)
 

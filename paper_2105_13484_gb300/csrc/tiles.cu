@@ -500,10 +500,9 @@ size_t tile_smem_bytes(const TilePlan &plan, int maxE, int maxE2, size_t sR) {
     for (const TilePatch &t : plan.patches) {
         const size_t ne = t.ne + 1, nc = t.nc + 1;
         size_t b = 0;
-        b += sR * (4 * ne);                 // u0, ua, uh, flux
-        b += sR * ne;                       // 1/d_e
-        b += sR * (3 * nc);                 // z0, za, zh
-        b += sR * (ne + nc);                // G, H
+        b += sR * (4 * ne);                 // u0, ua, uh, flux (increments)
+        b += sR * (3 * nc);                 // z0, za, zh (increments)
+        b += sR * (2 * ne + nc);            // starting forcing and ubar, starting depth
         b += 4 * ne;                        // packed local byte offsets of (c1, c2)
         b += 2 * TILE_NE2P * ne;            // edgesOnEdge byte offsets, padded
         b += 2 * TILE_NCEP * nc;            // edgesOnCell byte offsets, padded

@@ -9,6 +9,9 @@ namespace sse {
 
 // padded per-entry strides of the tiled sub-cycle's local connectivity
 constexpr int TILE_NE2P = 10;  // edgesOnEdge per edge (hexagon/pentagon meshes: <= 10)
+// rows of a patch's streamed per-edge coefficient block: the TILE_NE2P
+// Coriolis coefficients, then 1 / d_e
+constexpr int TILE_CFR = TILE_NE2P + 1;
 constexpr int TILE_NCEP = 6;   // edgesOnCell per cell (<= 6)
 
 // host copy of the connectivity and coefficients the plans need (the

@@ -5,7 +5,13 @@ initial state for the configuration's whole step count -- the 92,480-cell
 channel: SSPRK3-SE, dt = 60 s, M = 30, 200 steps; the level-7 sphere:
 SSPRK3-SE, dt = 600 s, M = 40, 144 steps -- and a seeded sample of the final
 fields (u, h, zeta, and each tracer) is stored with its indices, next to a
-digest of the inputs, in ``horizon_<workload>.npz``.  The GPU tests step the
+digest of the inputs, in ``horizon_<workload>.npz``.  The oracle also runs
+once more from the same state with every thickness moved by one unit in the
+last place (a seeded sign per entry), and the relative L2 distance between
+the two results over each field's sampled entries is stored as that field's
+spread: how far the FP64 solution itself moves under a rounding-sized change
+of its input, the floor below which no two FP64 evaluation orders can be
+expected to agree.  The GPU tests step the
 same inputs on the device for the same number of steps and compare the
 sampled entries element by element (the full fields are 10^7-10^8 values,
 too large to store).  The digest lets a test refuse to compare results whose
@@ -13,7 +19,7 @@ inputs were generated differently.
 
     python tests/golden/make_horizon.py [channel_1km|sphere_l7 ...] [--threads N] [--out DIR]
 
-Takes minutes per workload on a multi-core host (the OpenMP build of the
+Takes minutes per workload (two runs) on a multi-core host (the OpenMP build of the
 oracle; results are bit-identical to the serial build).
 """
 from __future__ import annotations
@@ -49,6 +55,13 @@ def input_digest(m, L, p, state) -> str:
     return h.hexdigest()
 
 
+def ulp_perturbed(h: np.ndarray, seed: int = 7) -> np.ndarray:
+    """h with every entry moved to its neighbouring double, up or down by a
+    seeded sign."""
+    up = np.random.default_rng(seed).random(h.shape) < 0.5
+    return np.where(up, np.nextafter(h, np.inf), np.nextafter(h, -np.inf))
+
+
 def sample_indices(n: int, seed: int) -> np.ndarray:
     rng = np.random.default_rng(seed)
     return np.sort(rng.choice(n, size=min(NSAMPLE, n), replace=False))
@@ -66,22 +79,29 @@ def make(name: str, threads: int, out_dir: str = HERE) -> None:
     digest = input_digest(m, L, p, (u, h, tr))
     o = oracle.Oracle(m, L, p, threads=threads)
     t0 = time.time()
-    uo, ho, tro = o.step(run["order"], run["dt"], run["M"], u, h, tr, n_steps=run["steps"])
+
+    def fields_of(h0):
+        uo, ho, tro = o.step(run["order"], run["dt"], run["M"], u, h0, tr, n_steps=run["steps"])
+        fl = {"u": uo.ravel(), "h": ho.ravel(), "zeta": ho.sum(1) - m.bottomDepth}
+        for k in range(tro.shape[0]):
+            fl[f"tracer{k}"] = tro[k].ravel()
+        return fl
+
+    fields = fields_of(h)
+    moved = fields_of(ulp_perturbed(h))
     secs = time.time() - t0
-    zeta = ho.sum(1) - m.bottomDepth
     out = {"digest": np.array(digest), "steps": np.array(run["steps"]),
            "order": np.array(run["order"]), "dt": np.array(run["dt"]), "M": np.array(run["M"])}
-    fields = {"u": uo.ravel(), "h": ho.ravel(), "zeta": zeta}
-    for k in range(tro.shape[0]):
-        fields[f"tracer{k}"] = tro[k].ravel()
     for seed, (f, x) in enumerate(fields.items()):
         idx = sample_indices(x.size, seed)
         out[f"{f}_idx"] = idx.astype(np.int64)
         out[f"{f}_val"] = x[idx]
         out[f"{f}_norm"] = np.array(np.linalg.norm(x))   # full-field L2 norm
+        out[f"{f}_spread"] = np.array(np.linalg.norm(moved[f][idx] - x[idx]) / np.linalg.norm(x[idx]))
     np.savez_compressed(path_of(name, out_dir), **out)
-    print(f"{name}: {run['steps']} steps in {secs:.0f} s on {threads} threads -> "
-          f"{path_of(name, out_dir)}", flush=True)
+    print(f"{name}: 2 x {run['steps']} steps in {secs:.0f} s on {threads} threads -> "
+          f"{path_of(name, out_dir)}; spread " +
+          " ".join(f"{f} {float(out[f + '_spread']):.2e}" for f in fields), flush=True)
 
 
 def main() -> None:

@@ -80,12 +80,18 @@ def test_stream_ordered_transfers_match_the_synchronous_ones():
     stream = torch.cuda.Stream()
     a = binding.State(dm, p, "mixed")
     b = binding.State(dm, p, "mixed", stream=stream.cuda_stream)
-    a.load_state(u, h, tr)
+    # b is given FP32 copies of u and T; a starts from the same values in FP64,
+    # so that both hold the same FP32 state (the tracer as its anomaly from
+    # the EOS reference, rounded once)
+    u32, t32 = u.astype(np.float32), tr[0].astype(np.float32)
+    tr_a = tr.copy()
+    tr_a[0] = t32
+    a.load_state(u32.astype(np.float64), h, tr_a)
     a.step(run["order"], run["dt"], run["M"], 2)
     want = a.read_state()
-    src = {"u": torch.from_numpy(u.astype(np.float32)).pin_memory(),
+    src = {"u": torch.from_numpy(u32).pin_memory(),
            "h": torch.from_numpy(np.ascontiguousarray(h)).pin_memory(),
-           "tracer0": torch.from_numpy(tr[0].astype(np.float32)).pin_memory()}
+           "tracer0": torch.from_numpy(t32).pin_memory()}
     out = {n: torch.empty_like(x).pin_memory() for n, x in src.items()}
     for _ in range(2):   # twice in a row from the same buffers
         for n, x in src.items():
@@ -94,8 +100,6 @@ def test_stream_ordered_transfers_match_the_synchronous_ones():
         for n, x in out.items():
             b.transfer_ptr(n, x.data_ptr(), get=True, f32=(n != "h"), asynchronous=True)
         b.sync()
-    # a started from the FP64 u and T; b from their FP32 roundings, which the
-    # mixed form stores anyway: the same state
     assert np.array_equal(out["u"].numpy(), want[0].astype(np.float32))
     assert np.array_equal(out["h"].numpy(), want[1])
     assert np.array_equal(out["tracer0"].numpy(), want[2][0].astype(np.float32))
