@@ -1,27 +1,30 @@
 #!/usr/bin/env python
-"""Throughput of one SSPRK3-SE large step on the 92,480-cell channel.
+"""Throughput of one SSPRK3-SE large step on the level-7 icosahedral sphere.
 
-Workload (the synthetic stand-in for the paper's baroclinic-channel case):
-160 x 578 hexagonal cells at 1 km (160 km x 500 km), 20 z-star layers, beta
-plane, seeded temperature front, SSPRK3-SE with dt = 60 s and M = 30
-barotropic sub-steps, reconciliation "consistent".  A "step" is one large
+Workload (the synthetic stand-in for the paper's global-ocean runs): the
+level-7 geodesic sphere (163,842 cells; 114,689 ocean cells and 343,016
+edges after the seeded land mask), 60 z-star layers over seeded bathymetry
+of 100-5000 m, T and S with a linear EOS, f = 2 Omega sin(lat), seeded zonal
+wind stress; SSPRK3-SE with dt = 600 s and M = 40 barotropic sub-steps,
+reconciliation "consistent", 144 steps (one day).  A "step" is one large
 step: three baroclinic stages, three sub-cycles and three thickness stages.
 
-Metric: cell-layer-steps/s = cells x layers x steps / device time.  The
-headline form is the mixed-precision path; the FP64 path is measured in the
-same run and reported under "forms", with per-step p50/p99 latency.  L2 is
-flushed (a 512 MB write) between timed steps and the flush is excluded from
-the per-step CUDA-event times.  The same run also measures, under "also":
-the largest single mesh, the level-7 icosahedral sphere with 60 layers
-(114,689 ocean cells, T and S, wind stress; SSPRK3-SE, dt = 600 s, M = 40);
-the channel with Algorithm 2 (implicit vertical mixing); the dt-refinement
-sweep of the channel (dt 60 to 3.75 s against 0.47 s, FP64 and mixed); a 64-member uneven
-ensemble batched through the request runtime against one member at a time;
-and a seeded Poisson request stream, mixed precision with continuous
-batching against FP64 one request at a time (p50/p99 time-to-horizon).
+Metric: cell-layer-steps/s = ocean cells x layers x steps / device time.
+The headline form is the mixed-precision path; the FP64 path is measured in
+the same run and reported under "forms", with per-step p50/p99 latency.  L2
+is flushed (a 512 MB write) between timed steps and the flush is excluded
+from the per-step CUDA-event times.  The same run also measures, under
+"also": the 92,480-cell channel (both forms); the sphere with partial bottom
+cells and biharmonic viscosity; the channel with Algorithm 2 (implicit
+vertical mixing); the dt-refinement sweep of the channel (FP64 and mixed); a
+64-member uneven ensemble packed into one launch per kernel and stage
+against one member at a time; and a seeded Poisson request stream, mixed
+precision with continuous batching against FP64 one request at a time
+(p50/p99 time-to-horizon).
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                    [--workload channel_1km|sphere_l7] [--no-sphere]
+                    [--workload sphere_l7|channel_1km] [--no-also] [--no-serving]
+                    [--study convergence]
 
 Under torchrun with N > 1 every rank runs an independent replica (the method
 has no cross-replica exchange): value = N x per-replica units / max time.
@@ -79,6 +82,28 @@ def kernel_bytes(cls, C, E, V, L, nT, sR, stage_has_old=True, mixed=False):
     return 0
 
 
+def fused_stage_bytes(cls, C, E, L, nT, sR, stage_has_old, mixed):
+    """Algorithmic HBM bytes of one launch of a fused 3-D stage kernel: each
+    3-D array the stage needs read once, each it produces written once.
+    Baroclinic stage: utilde in, utilde^n (stages that combine with the old
+    level), h (the FP32 copy in the mixed form), nT tracers; utilde out; the
+    2-D ubar, column transport, G and SSH.  Thickness/tracer stage: the
+    transport velocity's utilde, h and its FP32 copy, nT tracers, and h^n, its
+    copy and nT tracers^n where the stage combines with the old level; h, its
+    copy and nT tracers out; the 2-D u^A, column flux, ubar and SSH."""
+    CL, EL = C * L, E * L
+    hw = 8 * CL + (4 * CL if mixed else 0)          # h (+ the FP32 copy)
+    if cls == "bcl_edge":
+        hr = 4 * CL if mixed else 8 * CL
+        return (2 * EL * sR + (EL * sR if stage_has_old else 0) + hr + nT * CL * sR +
+                3 * E * sR + 8 * C)
+    if cls == "thickness":
+        old = (hw + nT * CL * sR) if stage_has_old else 0
+        return (EL * sR + hw + nT * CL * sR + old + hw + nT * CL * sR +
+                E * (2 * sR + 8) + 8 * C)
+    return None
+
+
 def step_bytes_per_cell_layer(mixed: bool, nT: int = 1) -> float:
     """Algorithmic bytes per cell-layer of one SSPRK3-SE step: every 3-D
     array read or written once per stage (E ~ 3C counts 3 words per cell):
@@ -97,9 +122,8 @@ def step_bytes_per_cell_layer(mixed: bool, nT: int = 1) -> float:
 # each records DRAM traffic per launch and the hashes of the sources it was
 # captured from, so a figure taken from an older kernel is not reported
 PROFILE_OF = {  # committed ncu summaries by workload and kernel class (mixed form)
-    "channel_1km": {"btr": "btr_tiled_channel_1km.md", "bcl_edge": "bcl_edge_channel_1km.md",
-                    "thickness": "thickness_channel_1km.md"},
-    "sphere_l7": {"btr": "btr_tiled_sphere_l7.md"},
+    "sphere_l7": {"btr": "btr_tiled_sphere_l7.md", "bcl_edge": "bcl_fused_sphere_l7.md",
+                  "thickness": "thick_fused_sphere_l7.md"},
 }
 KERNEL_SOURCES = ("paper_2105_13484_gb300/csrc/btr_kernel.cu",
                   "paper_2105_13484_gb300/csrc/stage_kernels.cu",
@@ -411,26 +435,39 @@ def measure_e2e(torch, binding, dm, p, state0, run, precision, steps, stream, na
     return ms, nbytes, dtypes
 
 
-def kernel_roofline_of(prof, m, L, nT, mixed, order):
-    """The longest kernel class against the HBM copy peak (its own
-    algorithmic bytes per launch / its average launch time)."""
+def kernel_roofline_of(prof, m, L, nT, mixed, order, fused):
+    """The dominant kernel of the HBM-bound 3-D phase: the longest kernel
+    class other than the barotropic sub-cycle, whose bound is its grid
+    synchronisations and on-chip latency (reported under "subcycle").  Its
+    algorithmic bytes per launch (averaged over the step's stages; the first
+    stage has no old-level input) over its average launch time, against the
+    measured HBM copy peak."""
     peaks, peak_kind = measured_peaks()
     sR = 4 if mixed else 8
-    dom = max(prof, key=lambda k: prof[k][0])
+    total = sum(v[0] for v in prof.values()) or 1.0
+    overall = max(prof, key=lambda k: prof[k][0])
+    dom = max((k for k in prof if k != "btr" and prof[k][1]), key=lambda k: prof[k][0])
     nlaunch = prof[dom][1]
     per_launch_ms = prof[dom][0] / max(nlaunch, 1)
     C, E, V = m.nCells, m.nEdges, m.nVertices
+
+    def stage_bytes(has_old):
+        b = fused_stage_bytes(dom, C, E, L, nT, sR, has_old, mixed) if fused else None
+        return b if b is not None else kernel_bytes(dom, C, E, V, L, nT, sR, has_old, mixed)
     if dom in ("bcl_edge", "thickness"):
-        # the first stage of a step has no old-level input (utilde^n, h^n)
-        b = (kernel_bytes(dom, C, E, V, L, nT, sR, False, mixed) +
-             (order - 1) * kernel_bytes(dom, C, E, V, L, nT, sR, True, mixed)) / order
+        b = (stage_bytes(False) + (order - 1) * stage_bytes(True)) / order
     else:
         b = kernel_bytes(dom, C, E, V, L, nT, sR, True, mixed)
     achieved = b / (per_launch_ms / 1e3) / 1e9
-    return {"kernel": dom, "bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"],
-            "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"],
-            "peak_source": f"{peak_kind} hbm_gbs (copy)", "bytes_per_launch": b,
-            "ms_per_launch": per_launch_ms}
+    names = {"bcl_edge": "k_bcl_fused" if fused else "k_bcl_edge",
+             "thickness": "k_thick_fused" if fused else "k_thickness"}
+    return {"kernel": names.get(dom, dom), "class": dom, "bound": "hbm", "achieved": achieved,
+            "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"],
+            "peak_source": f"{peak_kind} hbm_gbs (copy), burst", "bytes_per_launch": b,
+            "ms_per_launch": per_launch_ms, "share_of_step": prof[dom][0] / total,
+            "longest_overall": {"class": overall, "share_of_step": prof[overall][0] / total,
+                                "bound": "grid synchronisation and L2 latency (see subcycle)"
+                                if overall == "btr" else "hbm"}}
 
 
 def step_roofline_of(m, L, nT, mixed, ms_per_step, workload):
@@ -572,12 +609,12 @@ def measure_workload(torch, binding, name, forms_todo, headline, steps, warmup, 
         out["mixed_err"] = err
     prof = head["prof"]
     tag = name if not over else name + " (variant)"
-    kroof = kernel_roofline_of(prof, m, L, nT, mixed, run["order"])
-    traffic, traffic_src = ncu_traffic(kroof["kernel"], mixed, name) if not over else \
+    kroof = kernel_roofline_of(prof, m, L, nT, mixed, run["order"], head["fused_bcl"])
+    traffic, traffic_src = ncu_traffic(kroof["class"], mixed, name) if not over else \
         (None, "no ncu capture of this variant of the workload")
     kroof["traffic"], kroof["traffic_source"] = traffic, traffic_src
-    out["kernel_roofline"] = kroof
-    out["roofline"] = step_roofline_of(m, L, nT, mixed, head["ms_per_step"], tag)
+    out["roofline"] = kroof
+    out["step_roofline"] = step_roofline_of(m, L, nT, mixed, head["ms_per_step"], tag)
     out["subcycle"] = subcycle_of(prof, m, run, steps, head["patches"], tag, mixed)
     out["kernels"] = {k: {"ms_per_step": v[0] / steps, "share": v[0] / max(head["device_ms"], 1e-9),
                           "launches_per_step": v[1] / steps} for k, v in prof.items() if v[1]}
@@ -822,12 +859,13 @@ def run_ours(args):
     todo = ("mixed", "fp64") if args.forms == "both" else (args.forms,)
     if args.precision not in todo:
         todo = todo + (args.precision,)
+    over = {"level": args.level} if args.level else {}
     w = measure_workload(torch, binding, args.workload, todo, args.precision, args.steps,
                          args.warmup, rank, stream, flush, sampler, not args.no_e2e, world, dist,
-                         fp64_tflops=rates["fp64_tflops"])
+                         fp64_tflops=rates["fp64_tflops"], **over)
     head = w["head"]
     also = {}
-    extra = args.workload == WORKLOAD and not args.no_also
+    extra = args.workload == WORKLOAD and not args.no_also and not args.level
     if extra:
         # the 92,480-cell channel (SSPRK3-SE, dt 60 s, M 30), both forms
         nc = min(args.steps, 200)
@@ -838,6 +876,7 @@ def run_ours(args):
             "value": ch["value"], "unit": METRIC, "steps": nc, "ms_per_step": ch["t_max"] / nc,
             "latency_ms": ch["head"]["latency_ms"],
             "config": config_of("channel_1km", ch, "mixed", world), "roofline": ch["roofline"],
+            "step_roofline": ch["step_roofline"],
             "subcycle": ch["subcycle"], "kernels": ch["kernels"], "forms": ch["forms_summary"],
             "mixed_vs_fp64_rel_l2": ch["mixed_err"]}
         # the same sphere as a global-ocean setup: partial bottom cells on the
@@ -880,8 +919,9 @@ def run_ours(args):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": w["t_max"] / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32+f64" if args.precision == "mixed" else "f64", "data": "synthetic",
-        "config": config_of(args.workload, w, args.precision, world),
-        "roofline": w["roofline"], "kernel_roofline": w["kernel_roofline"],
+        "config": config_of(args.workload + (f" at level {args.level}" if args.level else ""), w,
+                            args.precision, world),
+        "roofline": w["roofline"], "step_roofline": w["step_roofline"],
         "subcycle": w["subcycle"], "kernels": w["kernels"],
         "latency_ms": head["latency_ms"],
         "forms": w["forms_summary"],
@@ -923,7 +963,12 @@ def main():
                     help="skip the batched-ensemble and request-stream measurements")
     ap.add_argument("--study", choices=["convergence"],
                     help="run only the named longer study and print its JSON")
+    ap.add_argument("--level", type=int, default=0,
+                    help="the sphere recipe at another geodesic level (a smaller case for "
+                         "profiling; not a bench line of the workload)")
     args = ap.parse_args()
+    if args.level and args.workload != WORKLOAD:
+        ap.error("--level applies to the sphere workload")
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":
