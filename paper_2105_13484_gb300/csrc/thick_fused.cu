@@ -74,11 +74,27 @@ __device__ __forceinline__ void transport_cols_edge(const DMesh &m, const Transp
     const R wA = (R)a.wA, wB = (R)a.wB;
     const bool twoB = a.utB != nullptr;
     PairSum<R> Sacc;
-    for (int k = 0; k < L; k++) {
-        const R he = R(0.5) * (ldg(a.hR + k * Cp + cc.x) + ldg(a.hR + k * Cp + cc.y));
-        R v = wA * (ubA + a.utA[k * Ep + e]);
-        if (twoB) v += wB * (ubB + a.utB[k * Ep + e]);
-        Sacc.add(v * he);
+    // layers in chunks of KC, every load of a chunk issued before its sums
+    // (which still run over k in order)
+    constexpr int KC = 4;
+    for (int k0 = 0; k0 < L; k0 += KC) {
+        R h1[KC], h2[KC], xa[KC], xb[KC];
+#pragma unroll
+        for (int j = 0; j < KC; j++) {
+            const int k = k0 + j < L ? k0 + j : L - 1;
+            h1[j] = ldg(a.hR + k * Cp + cc.x);
+            h2[j] = ldg(a.hR + k * Cp + cc.y);
+            xa[j] = ldg(a.utA + k * Ep + e);
+            xb[j] = twoB ? ldg(a.utB + k * Ep + e) : R(0);
+        }
+#pragma unroll
+        for (int j = 0; j < KC; j++) {
+            if (k0 + j >= L) break;
+            const R he = R(0.5) * (h1[j] + h2[j]);
+            R v = wA * (ubA + xa[j]);
+            if (twoB) v += wB * (ubB + xb[j]);
+            Sacc.add(v * he);
+        }
     }
     const double S = Sacc.value();
     const double hs = 0.5 * ((a.zeta[cc.x] + m.H[cc.x]) + (a.zeta[cc.y] + m.H[cc.y]));
