@@ -801,19 +801,16 @@ struct Engine : EngineBase {
         t.P = pl.P; t.maxE0 = pl.maxE0; t.maxE1 = pl.maxE1; t.maxE2 = pl.maxE2; t.maxC1 = pl.maxC1;
         t.maxC2 = pl.maxC2; t.maxV = pl.maxV; t.smem = smem;
         t.cnt = A.upload(pl.cnt);
-        t.off_e0 = A.upload(pl.off_e0); t.off_e1 = A.upload(pl.off_e1); t.off_e2 = A.upload(pl.off_e2);
-        t.off_c1 = A.upload(pl.off_c1); t.off_c2 = A.upload(pl.off_c2); t.off_v = A.upload(pl.off_v);
-        t.egid = A.upload(pl.egid); t.cgid = A.upload(pl.cgid);
-        t.e0_eoe = A.upload(pl.e0_eoe); t.e0_wl = A.upload(toR(pl.e0_wl));
+        t.off_e0 = A.upload(pl.off_e0); t.off_v = A.upload(pl.off_v);
+        t.e0_eoe = A.upload(pl.e0_eoe);
         t.e0_cfc = A.upload(toR(pl.e0_cfc)); t.e0_c12 = A.upload(pl.e0_c12);
         t.e0_v12 = A.upload(pl.e0_v12); t.e0_invdc = A.upload(toR(pl.e0_invdc));
         t.e0_invdv = A.upload(toR(pl.e0_invdv));
-        t.e1_c12 = A.upload(pl.e1_c12); t.e1_v12 = A.upload(pl.e1_v12);
-        t.c1_e = A.upload(pl.c1_e); t.c1_o = A.upload(pl.c1_o);
-        t.c1_divc = A.upload(toR(pl.c1_divc)); t.c1_kec = A.upload(toR(pl.c1_kec));
-        t.v_e = A.upload(pl.v_e); t.v_c = A.upload(pl.v_c);
-        t.v_curl = A.upload(toR(pl.v_curl)); t.v_kw = A.upload(toR(pl.v_kw));
         t.v_f = A.upload(toR(pl.v_f));
+        std::vector<unsigned char> img;
+        std::vector<long long> img_off;
+        t.img_max = bcl_build_image<R>(pl, img, img_off);
+        t.img = A.upload(img); t.img_off = A.upload(img_off);
         Fc = A.alloc<R>(m.Ep);
         if (A.failed) return SSE_ERR_OOM;
         fused = true;

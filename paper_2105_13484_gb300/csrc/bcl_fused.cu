@@ -28,6 +28,10 @@
 // cancelling two O(g rho' H) sums in FP32.  Algorithm 1's G needs the whole
 // column of provisional values: they are written as the layers go, and one
 // pass over the owned columns at the end subtracts dt G.
+#include <algorithm>
+#include <cstring>
+#include <vector>
+
 #include "sse_internal.cuh"
 #include "tiles.h"
 
@@ -44,6 +48,10 @@ __device__ __forceinline__ unsigned smem_addr(const void *p) {
 template <class R> __device__ __forceinline__ void cp_async(R *dst, const R *src) {
     asm volatile("cp.async.ca.shared.global [%0], [%1], %2;\n" ::"r"(smem_addr(dst)), "l"(src),
                  "n"(sizeof(R)));
+}
+// asynchronous 16-byte copy global -> shared, bypassing L1 (both addresses 16-byte aligned)
+__device__ __forceinline__ void cp_async16(void *dst, const void *src) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(smem_addr(dst)), "l"(src));
 }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::); }
@@ -153,9 +161,7 @@ __device__ __forceinline__ void bcl_fused_patch(const DMesh &m, const DParams &p
     const int ctid = NT - 1 - tid;
     const int *cn = t.cnt + 8 * pid;
     const int nE0 = cn[0], nE1 = cn[1], nE2 = cn[2], nC1 = cn[3], nC2 = cn[4], nV = cn[5];
-    const int *eg_g = t.egid + t.off_e2[pid];
-    const int *cg_g = t.cgid + t.off_c2[pid];
-    const int oe0 = t.off_e0[pid], oe1 = t.off_e1[pid], oc1 = t.off_c1[pid], ov = t.off_v[pid];
+    const int oe0 = t.off_e0[pid], ov = t.off_v[pid];
     const int Ep = m.Ep, Cp = m.Cp, L = m.L;
     const int NP = (L + 1) / 2;   // layer pairs (the second layer of the last is absent if L is odd)
     const PhysR<R> &q = phys<R>(p);
@@ -178,53 +184,36 @@ __device__ __forceinline__ void bcl_fused_patch(const DMesh &m, const DParams &p
     R2 *cR = carve<R2>(sp, t.maxC1);
     R2 *cW1 = carve<R2>(sp, t.maxC1);
     R2 *cD = carve<R2>(sp, t.maxC1);
-    // the patch's connectivity and coefficients, read every pair: copied to
-    // shared memory once (term-major, stride = the patch's own count); index
-    // pairs packed as lo | hi << 16, coefficient pairs side by side
-    unsigned short *x_e0i = carve<unsigned short>(sp, BCL_NE2P * t.maxE0);
-    R *x_e0w = carve<R>(sp, BCL_NE2P * t.maxE0);
-    unsigned *x_c1eo = carve<unsigned>(sp, BCL_NCEP * t.maxC1);
-    R2 *x_c1dk = carve<R2>(sp, BCL_NCEP * t.maxC1);
-    unsigned *x_vec = carve<unsigned>(sp, 3 * t.maxV);
-    R2 *x_vck = carve<R2>(sp, 3 * t.maxV);
     R2 *x_vbf = carve<R2>(sp, t.maxV);   // (curl ubar, curl ubar + f): layer-invariant
-    int *x_e1c = carve<int>(sp, t.maxE1);
-    int *x_e1v = carve<int>(sp, t.maxE1);
+    R *sf_s = carve<R>(sp, L);           // the layers' z-star stretching fractions s_k
+    // the patch's connectivity and coefficients, read every pair: the host
+    // packed them per patch in this layout (bcl_build_image), copied here in
+    // 16-byte pieces; term-major with the patch's own counts as strides,
+    // index pairs as lo | hi << 16, coefficient pairs side by side
+    {
+        const unsigned char *src = t.img + t.img_off[pid];
+        const int n16 = (int)((t.img_off[pid + 1] - t.img_off[pid]) / 16);
+        for (int i = tid; i < n16; i += NT) cp_async16(sp + 16 * i, src + 16 * i);
+        cp_async_commit();
+    }
+    char *ip = sp;
+    unsigned short *x_e0i = carve<unsigned short>(ip, BCL_NE2P * nE0);
+    R *x_e0w = carve<R>(ip, BCL_NE2P * nE0);
+    unsigned *x_c1eo = carve<unsigned>(ip, BCL_NCEP * nC1);
+    R2 *x_c1dk = carve<R2>(ip, BCL_NCEP * nC1);
+    unsigned *x_vec = carve<unsigned>(ip, 3 * nV);
+    R2 *x_vck = carve<R2>(ip, 3 * nV);
+    int *x_e1c = carve<int>(ip, nE1);
+    int *x_e1v = carve<int>(ip, nE1);
     // the patch's internal edge and cell indices (each layer's copies use them)
-    int *eg = carve<int>(sp, t.maxE2);
-    int *cg = carve<int>(sp, t.maxC2);
-    R *sf_s = carve<R>(sp, L);   // the layers' z-star stretching fractions s_k
+    int *eg = carve<int>(ip, nE2);
+    int *cg = carve<int>(ip, nC2);
     {
         const R *sfr = sfrac_R<R>(m);
         for (int k = tid; k < L; k += NT) sf_s[k] = sfr[k];
     }
-    for (int j = tid; j < nE2; j += NT) eg[j] = eg_g[j];
-    for (int j = tid; j < nC2; j += NT) cg[j] = cg_g[j];
+    cp_async_wait_all();
     __syncthreads();
-    for (int j = tid; j < BCL_NE2P * nE0; j += NT) {
-        x_e0i[j] = t.e0_eoe[BCL_NE2P * oe0 + j];
-        x_e0w[j] = ldg(t.e0_wl + BCL_NE2P * oe0 + j);
-    }
-    for (int j = tid; j < BCL_NCEP * nC1; j += NT) {
-        const int x = BCL_NCEP * oc1 + j;
-        x_c1eo[j] = (unsigned)t.c1_e[x] | ((unsigned)t.c1_o[x] << 16);
-        R2 dk;
-        dk.x = ldg(t.c1_divc + x);
-        dk.y = ldg(t.c1_kec + x);
-        x_c1dk[j] = dk;
-    }
-    for (int j = tid; j < 3 * nV; j += NT) {
-        const int x = 3 * ov + j;
-        x_vec[j] = (unsigned)t.v_e[x] | ((unsigned)t.v_c[x] << 16);
-        R2 ck;
-        ck.x = ldg(t.v_curl + x);
-        ck.y = ldg(t.v_kw + x);
-        x_vck[j] = ck;
-    }
-    for (int j = tid; j < nE1; j += NT) {
-        x_e1c[j] = t.e1_c12[oe1 + j];
-        x_e1v[j] = t.e1_v12[oe1 + j];
-    }
     const bool two = p.nT > 1;
     const bool comb = a.ut_n != nullptr;
     // one pair's copies into buffer b (the second layer's only if it exists)
@@ -294,8 +283,8 @@ __device__ __forceinline__ void bcl_fused_patch(const DMesh &m, const DParams &p
             R d = R(0);
 #pragma unroll
             for (int j = 0; j < BCL_NCEP; j++) {
-                const int el = t.c1_e[BCL_NCEP * oc1 + j * nC1 + c];
-                if (el < nE2) d += ldg(t.c1_divc + BCL_NCEP * oc1 + j * nC1 + c) * ldg(a.Fc + eg[el]);
+                const int el = x_c1eo[j * nC1 + c] & 0xffff;
+                if (el < nE2) d += x_c1dk[j * nC1 + c].x * ldg(a.Fc + eg[el]);
             }
             dsum[s] = d;
         }
@@ -333,8 +322,7 @@ __device__ __forceinline__ void bcl_fused_patch(const DMesh &m, const DParams &p
             R cb = R(0);
 #pragma unroll
             for (int j = 0; j < BCL_NE2P; j++) {
-                const int x = BCL_NE2P * oe0 + j * nE0 + e;
-                cb += ldg(t.e0_cfc + x) * ub_s[t.e0_eoe[x]];
+                cb += ldg(t.e0_cfc + BCL_NE2P * oe0 + j * nE0 + e) * ub_s[x_e0i[j * nE0 + e]];
             }
             cbar[s] = cb;
         }
@@ -655,6 +643,70 @@ __global__ void __launch_bounds__(128) k_colflux_batch(const ColfluxJob<R> *__re
 constexpr int BCL_NT = 256;
 constexpr int BCL_NI = 2;
 
+// bytes of one patch's shared-memory image: the arrays in the order the kernel
+// carves them, each rounded up to 16 bytes
+template <class R> static size_t image_bytes(int nE0, int nE1, int nE2, int nC1, int nC2, int nV) {
+    auto a16 = [](size_t b) { return (b + 15) / 16 * 16; };
+    const size_t sR = sizeof(R);
+    return a16(2 * BCL_NE2P * (size_t)nE0) + a16(sR * BCL_NE2P * (size_t)nE0) +
+           a16(4 * BCL_NCEP * (size_t)nC1) + a16(2 * sR * BCL_NCEP * (size_t)nC1) +
+           a16(4 * 3 * (size_t)nV) + a16(2 * sR * 3 * (size_t)nV) + 2 * a16(4 * (size_t)nE1) +
+           a16(4 * (size_t)nE2) + a16(4 * (size_t)nC2);
+}
+
+template <class R>
+size_t bcl_build_image(const BclPlan &pl, std::vector<unsigned char> &img,
+                       std::vector<long long> &off) {
+    using R2 = V2<R>;
+    img.clear();
+    off.assign(1, 0);
+    size_t best = 0;
+    for (int p = 0; p < pl.P; p++) {
+        const int *n = &pl.cnt[8 * p];
+        const int nE0 = n[0], nE1 = n[1], nE2 = n[2], nC1 = n[3], nC2 = n[4], nV = n[5];
+        const size_t bytes = image_bytes<R>(nE0, nE1, nE2, nC1, nC2, nV);
+        best = std::max(best, bytes);
+        const size_t base = img.size();
+        img.resize(base + bytes, 0);
+        unsigned char *q = img.data() + base;
+        auto put = [&](const void *src, size_t len) {
+            std::memcpy(q, src, len);
+            q += (len + 15) / 16 * 16;
+        };
+        const int oe0 = pl.off_e0[p], oe1 = pl.off_e1[p], oc1 = pl.off_c1[p], ov = pl.off_v[p];
+        put(&pl.e0_eoe[(size_t)BCL_NE2P * oe0], 2 * (size_t)BCL_NE2P * nE0);
+        std::vector<R> w(pl.e0_wl.begin() + (size_t)BCL_NE2P * oe0,
+                         pl.e0_wl.begin() + (size_t)BCL_NE2P * (oe0 + nE0));
+        put(w.data(), sizeof(R) * w.size());
+        std::vector<uint32_t> eo((size_t)BCL_NCEP * nC1);
+        std::vector<R2> dk((size_t)BCL_NCEP * nC1);
+        for (size_t j = 0; j < eo.size(); j++) {
+            const size_t x = (size_t)BCL_NCEP * oc1 + j;
+            eo[j] = (uint32_t)pl.c1_e[x] | ((uint32_t)pl.c1_o[x] << 16);
+            dk[j].x = (R)pl.c1_divc[x];
+            dk[j].y = (R)pl.c1_kec[x];
+        }
+        put(eo.data(), 4 * eo.size());
+        put(dk.data(), sizeof(R2) * dk.size());
+        std::vector<uint32_t> ec((size_t)3 * nV);
+        std::vector<R2> ck((size_t)3 * nV);
+        for (size_t j = 0; j < ec.size(); j++) {
+            const size_t x = (size_t)3 * ov + j;
+            ec[j] = (uint32_t)pl.v_e[x] | ((uint32_t)pl.v_c[x] << 16);
+            ck[j].x = (R)pl.v_curl[x];
+            ck[j].y = (R)pl.v_kw[x];
+        }
+        put(ec.data(), 4 * ec.size());
+        put(ck.data(), sizeof(R2) * ck.size());
+        put(&pl.e1_c12[oe1], 4 * (size_t)nE1);
+        put(&pl.e1_v12[oe1], 4 * (size_t)nE1);
+        put(&pl.egid[pl.off_e2[p]], 4 * (size_t)nE2);
+        put(&pl.cgid[pl.off_c2[p]], 4 * (size_t)nC2);
+        off.push_back((long long)img.size());
+    }
+    return best;
+}
+
 template <class R> size_t bcl_smem_bytes(const BclPlan &plan, int L) {
     auto a16 = [](size_t b) { return (b + 15) / 16 * 16; };
     const size_t sR = sizeof(R);
@@ -668,14 +720,14 @@ template <class R> size_t bcl_smem_bytes(const BclPlan &plan, int L) {
     b += 2 * a16(2 * sR * plan.maxV);                  // q, omega
     b += a16(4 * sR * (plan.maxE1 + 1));               // (h_e u, q_e) x 2
     b += 4 * a16(2 * sR * plan.maxC1);                 // K, rho', w, div u
-    // connectivity and coefficients of the patch
-    b += a16(2 * BCL_NE2P * plan.maxE0) + a16(sR * BCL_NE2P * plan.maxE0);
-    b += a16(4 * BCL_NCEP * plan.maxC1) + a16(2 * sR * BCL_NCEP * plan.maxC1);
-    b += a16(4 * 3 * plan.maxV) + a16(2 * sR * 3 * plan.maxV) + a16(2 * sR * plan.maxV);
-    b += 2 * a16(4 * plan.maxE1);
-    b += a16(4 * plan.maxE2) + a16(4 * plan.maxC2);   // internal indices
+    b += a16(2 * sR * plan.maxV);                      // curl ubar (+ f)
     b += a16(sR * L);                                  // s_k
-    return b;
+    size_t img = 0;                                    // the largest patch image
+    for (int p = 0; p < plan.P; p++) {
+        const int *n = &plan.cnt[8 * p];
+        img = std::max(img, image_bytes<R>(n[0], n[1], n[2], n[3], n[4], n[5]));
+    }
+    return b + img;
 }
 template <class R> int bcl_blocks_per_sm() { return bcl_min_blocks<R>(); }
 template int bcl_blocks_per_sm<float>();
@@ -725,6 +777,10 @@ template const void *bcl_fused_batch_kernel_ptr<float>();
 template const void *bcl_fused_batch_kernel_ptr<double>();
 template size_t bcl_smem_bytes<float>(const BclPlan &, int);
 template size_t bcl_smem_bytes<double>(const BclPlan &, int);
+template size_t bcl_build_image<float>(const BclPlan &, std::vector<unsigned char> &,
+                                       std::vector<long long> &);
+template size_t bcl_build_image<double>(const BclPlan &, std::vector<unsigned char> &,
+                                        std::vector<long long> &);
 template const void *bcl_fused_kernel_ptr<float>();
 template const void *bcl_fused_kernel_ptr<double>();
 template void launch_colflux<float>(const DMesh &, float *, float *, const float *, bool, float *,

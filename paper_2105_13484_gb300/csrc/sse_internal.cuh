@@ -7,6 +7,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <vector>
+
 namespace sse {
 
 constexpr int MAXE = 8;    // edges per cell
@@ -162,18 +164,17 @@ template <class R> struct DBcl {
     int maxE0 = 0, maxE1 = 0, maxE2 = 0, maxC1 = 0, maxC2 = 0, maxV = 0;
     size_t smem = 0;
     const int *cnt = nullptr;                 // [P][8]
-    const int *off_e0, *off_e1, *off_e2, *off_c1, *off_c2, *off_v;
-    const int *egid, *cgid;
+    const int *off_e0, *off_v;
     const unsigned short *e0_eoe;             // [sum 10 nE0]
-    const R *e0_wl, *e0_cfc;                  // [sum 10 nE0]
+    const R *e0_cfc;                          // [sum 10 nE0]
     const int *e0_c12, *e0_v12;               // [sum nE0]
     const R *e0_invdc, *e0_invdv;             // [sum nE0]
-    const int *e1_c12, *e1_v12;               // [sum nE1]
-    const unsigned short *c1_e, *c1_o;        // [sum 6 nC1]
-    const R *c1_divc, *c1_kec;                // [sum 6 nC1]
-    const unsigned short *v_e, *v_c;          // [sum 3 nV]
-    const R *v_curl, *v_kw;                   // [sum 3 nV]
     const R *v_f;                             // [sum nV]
+    // per patch, the connectivity and coefficients the kernel keeps in shared
+    // memory, packed by the host in the kernel's layout (bcl_build_image)
+    const unsigned char *img;                 // 16-byte aligned blocks
+    const long long *img_off;                 // [P + 1] byte offsets
+    size_t img_max = 0;                       // the largest block
 };
 template <class R> struct BclArgs {
     const R *ubar, *ut, *hR, *tr;  // stage input (ubar, utilde, thickness, tracers)
@@ -202,6 +203,11 @@ void launch_bcl_fused_batch(const BclJob<R> *jobs, const int *first, int njobs, 
 template <class R> const void *bcl_fused_batch_kernel_ptr();
 struct BclPlan;
 template <class R> size_t bcl_smem_bytes(const BclPlan &plan, int L);
+// the per-patch shared-memory images of a plan (byte offsets [P + 1]); the
+// largest image's size is returned
+template <class R>
+size_t bcl_build_image(const BclPlan &plan, std::vector<unsigned char> &img,
+                       std::vector<long long> &off);
 // CTAs per SM the fused baroclinic kernel is compiled for (its launch bounds)
 template <class R> int bcl_blocks_per_sm();
 int bcl_max_edges_per_patch();
