@@ -171,12 +171,10 @@ __device__ __forceinline__ void bcl_fused_patch(const DMesh &m, const DParams &p
     R *ub_s = carve<R>(sp, t.maxE2 + 1);
     // buffer b of each ring starts at b times its stride (a multiple of 16 bytes)
     const int sE = pad16<R2>(t.maxE2 + 1), sC = pad16<R2>(t.maxC2 + 1), s1 = pad16<R2>(t.maxC1);
-    const int s0 = pad16<R2>(t.maxE0);
     R2 *ut_r = carve<R2>(sp, NB2 * sE);
     R2 *h_r = carve<R2>(sp, NB2 * sC);
     R2 *T_r = carve<R2>(sp, NB2 * s1);
     R2 *S_r = carve<R2>(sp, NB2 * s1);
-    R2 *un_r = carve<R2>(sp, NB2 * s0);   // the old level at the owned edges
     R2 *q_s = carve<R2>(sp, t.maxV);
     R2 *om_s = carve<R2>(sp, t.maxV);
     R4 *hq_s = carve<R4>(sp, t.maxE1 + 1);   // (h_e u, q_e) of both layers
@@ -241,15 +239,6 @@ __device__ __forceinline__ void bcl_fused_patch(const DMesh &m, const DParams &p
             if (two) {
                 cp_async(Sd + 2 * j, S0 + gc);
                 if (has1) cp_async(Sd + 2 * j + 1, S0 + Cp + gc);
-            }
-        }
-        if (comb) {
-            R *nd = reinterpret_cast<R *>(un_r + b * s0);
-            const R *n0 = a.ut_n + (size_t)k0 * Ep;
-            for (int j = tid; j < nE0; j += NT) {
-                const int ge = eg[j];
-                cp_async(nd + 2 * j, n0 + ge);
-                if (has1) cp_async(nd + 2 * j + 1, n0 + Ep + ge);
             }
         }
         cp_async_commit();
@@ -352,11 +341,22 @@ __device__ __forceinline__ void bcl_fused_patch(const DMesh &m, const DParams &p
         const int bc = pp % NB2, bn = (pp + 1) % NB2;
         const R2 *ut_c = ut_r + bc * sE, *h_c = h_r + bc * sC;
         const R2 *ut_nx = ut_r + bn * sE, *h_nx = h_r + bn * sC;
-        const R2 *T_c = T_r + bc * s1, *S_c = S_r + bc * s1, *un_c = un_r + bc * s0;
+        const R2 *T_c = T_r + bc * s1, *S_c = S_r + bc * s1;
         cp_async_wait_n<NB2 - 3>();
         __syncthreads();   // pairs pp and pp + 1 in shared memory; pair pp - 1's readers done
         if (pp + NB2 - 1 < NP) issue(pp + NB2 - 1, (pp + NB2 - 1) % NB2);
         else cp_async_commit();
+        // the old level at the owned edges (consecutive, so the loads
+        // coalesce), read by the edge phase two barriers later
+        R2 un2[NI];
+#pragma unroll
+        for (int s = 0; s < NI; s++) {
+            un2[s].x = R(0); un2[s].y = R(0);
+            if (comb && tid + s * NT < nE0) {
+                un2[s].x = ldg(a.ut_n + (size_t)k0 * Ep + ge[s]);
+                if (has1) un2[s].y = ldg(a.ut_n + (size_t)(k0 + 1) * Ep + ge[s]);
+            }
+        }
         // ---- vertices: relative vorticity, kite-averaged thickness, PV
         for (int v = tid; v < nV; v += NT) {
             R2 ot, hv;
@@ -469,9 +469,6 @@ __device__ __forceinline__ void bcl_fused_patch(const DMesh &m, const DParams &p
             const R2 K1 = cK[c1], K2 = cK[c2], P1 = cR[c1], P2 = cR[c2];
             const R2 D1 = cD[c1], D2 = cD[c2], o1 = om_s[v1], o2 = om_s[v2];
             const R2 W1 = cW1[c1], W2 = cW1[c2];
-            R2 un2;
-            un2.x = R(0); un2.y = R(0);
-            if (comb) un2 = un_c[e];
             // the layer below the pair: the first of the next pair
             R utn = R(0), h1n = R(0), h2n = R(0);
             if (k0 + 2 < L) {
@@ -529,7 +526,7 @@ __device__ __forceinline__ void bcl_fused_patch(const DMesh &m, const DParams &p
                 const R ut1 = ut_cur + dt * rhs;
                 num[s] += he_cur * ut1;
                 den[s] += he_cur;
-                const R unk = i ? un2.y : un2.x;
+                const R unk = i ? un2[s].y : un2[s].x;
                 a.ut_out[(size_t)k * Ep + ge[s]] = comb ? ca * unk + cb * ut1 : cb * ut1;
                 Dk[s] = Dk1;
                 wk[s] = wk1;
@@ -715,7 +712,6 @@ template <class R> size_t bcl_smem_bytes(const BclPlan &plan, int L) {
     b += NB2 * a16(2 * sR * (plan.maxE2 + 1));         // utilde (pair ring)
     b += NB2 * a16(2 * sR * (plan.maxC2 + 1));         // h
     b += 2 * NB2 * a16(2 * sR * plan.maxC1);           // T, S
-    b += NB2 * a16(2 * sR * plan.maxE0);               // old-level utilde
     // (each ring is carved as one block of NB2 16-byte padded strides)
     b += 2 * a16(2 * sR * plan.maxV);                  // q, omega
     b += a16(4 * sR * (plan.maxE1 + 1));               // (h_e u, q_e) x 2

@@ -7,10 +7,11 @@
 // one-thread-per-column kernel whose every layer waits on several rounds of
 // gathers.  Here the transport kernel leaves only 2-D results (u^A and the
 // FP64 column flux), and one CTA per patch of consecutive cells walks the
-// layers from the top with each layer's velocities (at the patch's edges),
-// thickness and tracers (at its cells and their neighbours) and its own
-// cells' old level staged in shared memory by cp.async (a ring of four
-// layers, two ahead of the one being computed); the
+// layers from the top with each layer's velocities (at the patch's edges)
+// and thickness and tracers (at its cells and their neighbours) staged in
+// shared memory by cp.async (a ring of four layers, two ahead of the one
+// being computed), and each owned cell's own stage and old levels loaded by
+// its thread (the owned cells are consecutive, so those loads coalesce); the
 // flux is formed in registers from them.  One barrier per layer.
 #include "sse_internal.cuh"
 #include "tiles.h"
@@ -133,17 +134,12 @@ __device__ __forceinline__ void thick_fused_patch(const DMesh &m, const DParams 
 
     extern __shared__ __align__(16) char smem[];
     char *sp = smem;
-    const int sE = pad16<R>(t.maxEO + 1), sC = pad16<R>(t.maxC1), sO = pad16<R>(Pc);
-    const int sO8 = pad16<double>(Pc);
+    const int sE = pad16<R>(t.maxEO + 1), sC = pad16<R>(t.maxC1);
     R *vb_s = carve<R>(sp, t.maxEO + 1);       // wA ubA + wB ubB + u^A per edge (0: zero slot)
     R *uA_r = carve<R>(sp, NBUF * sE);            // utA, NBUF layers
     R *uB_r = carve<R>(sp, twoB ? NBUF * sE : 1); // utB
     R *h_r = carve<R>(sp, NBUF * sC);             // hR_s at C1
     R *tr_r = carve<R>(sp, NBUF * nT * sC);       // tracers at C1, [layer][t][C1]
-    double *hs_r = carve<double>(sp, NBUF * sO8); // h_s of the owned cells (FP64)
-    double *hn_r = carve<double>(sp, comb ? NBUF * sO8 : 1);
-    R *hRn_r = carve<R>(sp, comb ? NBUF * sO : 1);
-    R *trn_r = carve<R>(sp, comb ? NBUF * nT * sO : 1);
     int *eg = carve<int>(sp, t.maxEO);   // the patch's internal indices
     int *cg = carve<int>(sp, t.maxC1);
     for (int j = l; j < nEO; j += NT) eg[j] = eg_g[j];
@@ -159,16 +155,6 @@ __device__ __forceinline__ void thick_fused_patch(const DMesh &m, const DParams 
             cp_async(h_r + b * sC + j, a.hR_s + (size_t)k * Cp + cg[j]);
             for (int tt = 0; tt < nT; tt++)
                 cp_async(tr_r + (b * nT + tt) * sC + j, a.tr_s + ((size_t)tt * L + k) * Cp + cg[j]);
-        }
-        for (int j = l; j < nO; j += NT) {   // the owned cells are C1's first nO
-            const size_t x = (size_t)k * Cp + cg[j];
-            cp_async(hs_r + b * sO8 + j, a.h_s + x);
-            if (comb) {
-                cp_async(hn_r + b * sO8 + j, a.h_n + x);
-                cp_async(hRn_r + b * sO + j, a.hR_n + x);
-                for (int tt = 0; tt < nT; tt++)
-                    cp_async(trn_r + (b * nT + tt) * sO + j, a.tr_n + (size_t)tt * L * Cp + x);
-            }
         }
         cp_async_commit();
     };
@@ -227,6 +213,18 @@ __device__ __forceinline__ void thick_fused_patch(const DMesh &m, const DParams 
         if (k + 3 < L) issue(k + 3, (k + 3) % NBUF);
         else cp_async_commit();
         if (!own) continue;
+        // the owned cell's own stage and old levels: coalesced loads (the
+        // owned cells are consecutive), used after the flux loop below
+        const size_t x = (size_t)k * Cp + i;
+        const double hs_d = a.h_s[x];
+        double hn = 0.0;
+        R hnr = R(0), trn0 = R(0), trn1 = R(0);
+        if (comb) {
+            hn = a.h_n[x];
+            hnr = a.hR_n[x];
+            trn0 = a.tr_n[x];
+            if (nT > 1) trn1 = a.tr_n[(size_t)L * Cp + x];
+        }
         const R *uA_c = uA_r + bc * sE, *uB_c = uB_r + bc * sE, *h_c = h_r + bc * sC;
         const R hs_cur = h_c[l];
         const R hs_next = (k + 1 < L) ? h_r[bn * sC + l] : R(0);
@@ -244,12 +242,9 @@ __device__ __forceinline__ void thick_fused_patch(const DMesh &m, const DParams 
         const R sk = sfr[k];
         const R wk1 = (k + 1 < L) ? wk + divk - sk * Dr : R(0);
         // thickness in FP64 from the column-integrated flux (volume conservation)
-        const size_t x = (size_t)k * Cp + i;
-        const double h1 = hs_r[bc * sO8 + l] - m.sfrac[k] * dtD;
-        const double hn = comb ? hn_r[bc * sO8 + l] : 0.0;
+        const double h1 = hs_d - m.sfrac[k] * dtD;
         const double hout = comb ? a.a * hn + a.b * h1 : h1;
         const R h1r = hs_cur - sk * (dtR * Dr);
-        const R hnr = comb ? hRn_r[bc * sO + l] : R(0);
         const R houtr = comb ? aR * hnr + bR * h1r : h1r;
 #pragma unroll
         for (int tt = 0; tt < 2; tt++) {
@@ -281,7 +276,7 @@ __device__ __forceinline__ void thick_fused_patch(const DMesh &m, const DParams 
             const R phi1 = qdiv(hphi, h1r);
             R out;
             if (comb)
-                out = qdiv(aR * hnr * trn_r[(bc * nT + tt) * sO + l] + bR * h1r * phi1, houtr);
+                out = qdiv(aR * hnr * (tt ? trn1 : trn0) + bR * h1r * phi1, houtr);
             else
                 out = phi1;
             a.tr_out[(size_t)tt * L * Cp + x] = out;
@@ -364,9 +359,9 @@ size_t thick_smem_bytes(const DThick &plan, int nT, bool twoB, bool comb, size_t
     size_t b = a16(sR * (plan.maxEO + 1));
     b += NB * a16(sR * (plan.maxEO + 1)) * (twoB ? 2 : 1) + (twoB ? 0 : 16);
     b += NB * a16(sR * plan.maxC1) * (1 + nT);
-    b += NB * a16(8 * Pc) * (comb ? 2 : 1) + (comb ? 0 : 16);
-    b += comb ? NB * a16(sR * Pc) * (1 + nT) : 32;
     b += a16(4 * (size_t)plan.maxEO) + a16(4 * (size_t)plan.maxC1);
+    (void)Pc;
+    (void)comb;
     return b;
 }
 int thick_cells_per_patch() { return THICK_NT; }
