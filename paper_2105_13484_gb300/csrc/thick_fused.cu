@@ -39,9 +39,10 @@ template <class R> __device__ __forceinline__ const R *sfr_of(const DMesh &m);
 template <> __device__ __forceinline__ const double *sfr_of<double>(const DMesh &m) { return m.sfrac; }
 template <> __device__ __forceinline__ const float *sfr_of<float>(const DMesh &m) { return m.sfrac_f; }
 
-// a / b for the per-layer quotients: correctly rounded in FP64; in FP32 the
-// reciprocal-multiply form (within 2 ulp for the divisors met here,
-// thicknesses of 1e-3 to 1e4 m), far below the FP32 form's other rounding
+// a / b for the vertical-diffusion quotients: correctly rounded in FP64; in
+// FP32 the reciprocal-multiply form (within 2 ulp for the divisors met here,
+// thicknesses of 1e-3 to 1e4 m).  The tracer values themselves keep IEEE
+// division.
 template <class R> __device__ __forceinline__ R qdiv(R a, R b);
 template <> __device__ __forceinline__ double qdiv<double>(double a, double b) { return a / b; }
 template <> __device__ __forceinline__ float qdiv<float>(float a, float b) { return __fdividef(a, b); }
@@ -273,10 +274,12 @@ __device__ __forceinline__ void thick_fused_patch(const DMesh &m, const DParams 
                 dbot = qdiv(ph - pd, R(0.5) * (hs_cur + hs_next));
             }
             const R hphi = hs_cur * ph + dtR * (-adv - (ftop - fbot) + dif + kv * (dtop - dbot));
-            const R phi1 = qdiv(hphi, h1r);
+            // the tracer itself: correctly rounded (a 2-ulp quotient here,
+            // applied every stage, grows into the density and the velocity)
+            const R phi1 = hphi / h1r;
             R out;
             if (comb)
-                out = qdiv(aR * hnr * (tt ? trn1 : trn0) + bR * h1r * phi1, houtr);
+                out = (aR * hnr * (tt ? trn1 : trn0) + bR * h1r * phi1) / houtr;
             else
                 out = phi1;
             a.tr_out[(size_t)tt * L * Cp + x] = out;
