@@ -170,11 +170,9 @@ __device__ __forceinline__ void bcl_fused_patch(const DMesh &m, const DParams &p
     char *sp = smem;
     R *ub_s = carve<R>(sp, t.maxE2 + 1);
     // buffer b of each ring starts at b times its stride (a multiple of 16 bytes)
-    const int sE = pad16<R2>(t.maxE2 + 1), sC = pad16<R2>(t.maxC2 + 1), s1 = pad16<R2>(t.maxC1);
+    const int sE = pad16<R2>(t.maxE2 + 1), sC = pad16<R2>(t.maxC2 + 1);
     R2 *ut_r = carve<R2>(sp, NB2 * sE);
     R2 *h_r = carve<R2>(sp, NB2 * sC);
-    R2 *T_r = carve<R2>(sp, NB2 * s1);
-    R2 *S_r = carve<R2>(sp, NB2 * s1);
     R2 *q_s = carve<R2>(sp, t.maxV);
     R2 *om_s = carve<R2>(sp, t.maxV);
     R4 *hq_s = carve<R4>(sp, t.maxE1 + 1);   // (h_e u, q_e) of both layers
@@ -219,9 +217,7 @@ __device__ __forceinline__ void bcl_fused_patch(const DMesh &m, const DParams &p
         const int k0 = 2 * pp;
         const bool has1 = k0 + 1 < L;
         R *ud = reinterpret_cast<R *>(ut_r + b * sE), *hd = reinterpret_cast<R *>(h_r + b * sC);
-        R *Td = reinterpret_cast<R *>(T_r + b * s1), *Sd = reinterpret_cast<R *>(S_r + b * s1);
         const R *u0 = a.ut + (size_t)k0 * Ep, *h0 = a.hR + (size_t)k0 * Cp;
-        const R *T0 = a.tr + (size_t)k0 * Cp, *S0 = a.tr + (size_t)(L + k0) * Cp;
         for (int j = tid; j < nE2; j += NT) {
             const int ge = eg[j];
             cp_async(ud + 2 * j, u0 + ge);
@@ -231,15 +227,6 @@ __device__ __forceinline__ void bcl_fused_patch(const DMesh &m, const DParams &p
             const int gc = cg[j];
             cp_async(hd + 2 * j, h0 + gc);
             if (has1) cp_async(hd + 2 * j + 1, h0 + Cp + gc);
-        }
-        for (int j = tid; j < nC1; j += NT) {
-            const int gc = cg[j];
-            cp_async(Td + 2 * j, T0 + gc);
-            if (has1) cp_async(Td + 2 * j + 1, T0 + Cp + gc);
-            if (two) {
-                cp_async(Sd + 2 * j, S0 + gc);
-                if (has1) cp_async(Sd + 2 * j + 1, S0 + Cp + gc);
-            }
         }
         cp_async_commit();
     };
@@ -341,7 +328,7 @@ __device__ __forceinline__ void bcl_fused_patch(const DMesh &m, const DParams &p
         const int bc = pp % NB2, bn = (pp + 1) % NB2;
         const R2 *ut_c = ut_r + bc * sE, *h_c = h_r + bc * sC;
         const R2 *ut_nx = ut_r + bn * sE, *h_nx = h_r + bn * sC;
-        const R2 *T_c = T_r + bc * s1, *S_c = S_r + bc * s1;
+
         cp_async_wait_n<NB2 - 3>();
         __syncthreads();   // pairs pp and pp + 1 in shared memory; pair pp - 1's readers done
         if (pp + NB2 - 1 < NP) issue(pp + NB2 - 1, (pp + NB2 - 1) % NB2);
@@ -355,6 +342,24 @@ __device__ __forceinline__ void bcl_fused_patch(const DMesh &m, const DParams &p
             if (comb && tid + s * NT < nE0) {
                 un2[s].x = ldg(a.ut_n + (size_t)k0 * Ep + ge[s]);
                 if (has1) un2[s].y = ldg(a.ut_n + (size_t)(k0 + 1) * Ep + ge[s]);
+            }
+        }
+        // the tracers of this thread's C1 cells, read by the cell phase below
+        // (the owned cells among them are consecutive)
+        R2 T2s[NI], S2s[NI];
+#pragma unroll
+        for (int s = 0; s < NI; s++) {
+            const int c = ctid + s * NT;
+            T2s[s].x = R(0); T2s[s].y = R(0); S2s[s] = T2s[s];
+            if (c < nC1) {
+                const R *T0 = a.tr + (size_t)k0 * Cp + cg[c];
+                T2s[s].x = ldg(T0);
+                if (has1) T2s[s].y = ldg(T0 + Cp);
+                if (two) {
+                    const R *S0 = T0 + (size_t)L * Cp;
+                    S2s[s].x = ldg(S0);
+                    if (has1) S2s[s].y = ldg(S0 + Cp);
+                }
             }
         }
         // ---- vertices: relative vorticity, kite-averaged thickness, PV
@@ -407,12 +412,12 @@ __device__ __forceinline__ void bcl_fused_patch(const DMesh &m, const DParams &p
                     dv.x += dk.x * (he0 * u0);
                     dv.y += dk.x * (he1 * u1);
                 }
-                const R2 T2 = T_c[c];
+                const R2 T2 = T2s[s];
                 R2 rp;
                 rp.x = -alpha * (T2.x - Tref);
                 rp.y = -alpha * (T2.y - Tref);
                 if (two) {
-                    const R2 S2 = S_c[c];
+                    const R2 S2 = S2s[s];
                     rp.x += beta * (S2.x - Sref);
                     rp.y += beta * (S2.y - Sref);
                 }
@@ -711,7 +716,6 @@ template <class R> size_t bcl_smem_bytes(const BclPlan &plan, int L) {
     b += a16(sR * (plan.maxE2 + 1));                   // ubar
     b += NB2 * a16(2 * sR * (plan.maxE2 + 1));         // utilde (pair ring)
     b += NB2 * a16(2 * sR * (plan.maxC2 + 1));         // h
-    b += 2 * NB2 * a16(2 * sR * plan.maxC1);           // T, S
     // (each ring is carved as one block of NB2 16-byte padded strides)
     b += 2 * a16(2 * sR * plan.maxV);                  // q, omega
     b += a16(4 * sR * (plan.maxE1 + 1));               // (h_e u, q_e) x 2
