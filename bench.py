@@ -667,7 +667,8 @@ def _build_requests(binding, specs):
             dm = binding.Mesh(m, L)
             for prec in ("mixed", "fp64"):      # plans and tuning before the clock runs
                 for obj in ("latency", "throughput"):
-                    binding.footprint(dm, p, prec, binding.tune(dm, p, prec, obj))
+                    sh = binding.tune_shapes(dm, p, prec, obj)
+                    binding.footprint(dm, p, prec, sh["patch_cells"], sh["bcl_patch_cells"])
             cache[key] = (m, L, p, st, dm)
         out.append(cache[key])
     return out
@@ -718,11 +719,14 @@ def measure_ensemble(binding, seed=0):
                          tune="throughput")
     single = run_stream(binding, specs, built, "mixed", 1, 200 << 30, 10, realtime=False,
                         tune="latency")
-    tuned = sorted({(b[0].nCells, binding.tune(b[4], b[2], "mixed", "throughput")) for b in built})
+    tuned = sorted({(b[0].nCells, *binding.tune_shapes(b[4], b[2], "mixed", obj).values(), obj)
+                    for b in built for obj in ("throughput", "latency")})
     for r in (packed, batched, single):
         r.pop("latencies_s", None)
     return {"members": len(specs), "cells": sorted({b[0].nCells for b in built}),
-            "patch_cells_throughput": tuned,
+            "tuned_shapes": {"columns": ["cells", "sub-cycle patch cells",
+                                         "baroclinic patch cells", "objective"],
+                             "rows": tuned},
             "layers": [int(min(b[1] for b in built)), int(max(b[1] for b in built))],
             "packed": packed, "batched": batched, "one_at_a_time": single,
             "speedup_packed": single["makespan_s"] / packed["makespan_s"],

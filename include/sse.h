@@ -323,10 +323,17 @@ int sse_barotropic_substep_noalloc(const sse_mesh *mesh, int order, double dt, i
  * patch, up to two patches per SM (more than one patch per SM run as 512-thread
  * blocks holding at most half an SM's shared memory each).  Larger patches use
  * fewer SMs for longer, which lets the sub-cycles of several states run side
- * by side. */
+ * by side.  bcl_patch_cells: cells per patch of the fused baroclinic kernel
+ * (Algorithm 1), one of 160, 128, 112, 96, 80, 64, 48, 32; 0 (the default):
+ * the largest whose patches fit the kernel with as many CTAs per SM as it is
+ * compiled for.  A size whose plan does not fit falls back to the default.
+ * Smaller patches give a small mesh more CTAs (shorter latency when it runs
+ * alone) at the cost of more halo work.  Results are the same bits for every
+ * choice of either size. */
 typedef struct {
     int32_t patch_cells;
-    int32_t reserved[7];     /* must be 0 */
+    int32_t bcl_patch_cells;
+    int32_t reserved[6];     /* must be 0 */
 } sse_tuning;
 
 #define SSE_TUNE_LATENCY 0     /* the fastest sub-cycle                          */
@@ -362,9 +369,12 @@ int sse_state_graphs(const sse_state *state, int *graphs);
 #define SSE_INJECT_BARRIER_STALL 1
 int sse_state_inject(sse_state *state, int what, int value);
 /* Autotuner: times the Algorithm 3/4 sub-cycle (M = 20) of a zero state of
- * this mesh for each candidate patch size and returns the best one for the
- * objective (SSE_TUNE_*).  Runs GPU work on a private stream; the result is
- * cached in the mesh. */
+ * this mesh for each candidate patch size, then Algorithm 1 for each fused
+ * baroclinic patch size whose plan fits, and returns the best of each for the
+ * objective (SSE_TUNE_*: LATENCY the fastest; THROUGHPUT the least SM-time,
+ * duration x the SMs the launch holds, among candidates within twice the
+ * fastest).  Runs GPU work on a private stream; the result is cached in the
+ * mesh. */
 int sse_tune(const sse_mesh *mesh, const sse_params *params, int objective, sse_tuning *out);
 
 /* Device bytes a state of this mesh and parameter set would allocate

@@ -54,7 +54,8 @@ class Params(ct.Structure):
 
 
 class Tuning(ct.Structure):
-    _fields_ = [("patch_cells", ct.c_int32), ("reserved", ct.c_int32 * 7)]
+    _fields_ = [("patch_cells", ct.c_int32), ("bcl_patch_cells", ct.c_int32),
+                ("reserved", ct.c_int32 * 6)]
 
 
 TUNE = {"latency": 0, "throughput": 1}
@@ -274,13 +275,13 @@ class State:
     """A model state on the GPU (the library owns its device memory)."""
 
     def __init__(self, mesh: Mesh, params: dict, precision="fp64", stream=None,
-                 patch_cells: int = 0):
+                 patch_cells: int = 0, bcl_patch_cells: int = 0):
         self.lib = load()
         self.mesh = mesh
         self.params = make_params(params, precision)
         self.nT = self.params.nTracers
         h = ct.c_void_p()
-        t = Tuning(int(patch_cells))
+        t = Tuning(int(patch_cells), int(bcl_patch_cells))
         _check(self.lib.sse_state_create_ex(mesh.handle, ct.byref(self.params), ct.byref(t),
                                              ct.c_void_p(stream or 0), ct.byref(h)),
                "sse_state_create_ex")
@@ -443,24 +444,31 @@ class State:
             pass
 
 
-def footprint(mesh: Mesh, params: dict, precision="fp64", patch_cells: int = 0) -> int:
+def footprint(mesh: Mesh, params: dict, precision="fp64", patch_cells: int = 0,
+              bcl_patch_cells: int = 0) -> int:
     """Device bytes sse_state_create would allocate for this mesh and parameters."""
     lib = load()
     prm = make_params(params, precision)
     out = ct.c_size_t()
-    t = Tuning(int(patch_cells))
+    t = Tuning(int(patch_cells), int(bcl_patch_cells))
     _check(lib.sse_state_footprint_ex(mesh.handle, ct.byref(prm), ct.byref(t), ct.byref(out)),
            "sse_state_footprint_ex")
     return int(out.value)
 
 
-def tune(mesh: Mesh, params: dict, precision="mixed", objective="throughput") -> int:
-    """Autotuned patch size of the tiled sub-cycle (sse_tune)."""
+def tune_shapes(mesh: Mesh, params: dict, precision="mixed", objective="throughput") -> dict:
+    """Autotuned launch shapes (sse_tune): the tiled sub-cycle's and the fused
+    baroclinic kernel's patch sizes."""
     lib = load()
     prm = make_params(params, precision)
     t = Tuning()
     _check(lib.sse_tune(mesh.handle, ct.byref(prm), TUNE[objective], ct.byref(t)), "sse_tune")
-    return int(t.patch_cells)
+    return {"patch_cells": int(t.patch_cells), "bcl_patch_cells": int(t.bcl_patch_cells)}
+
+
+def tune(mesh: Mesh, params: dict, precision="mixed", objective="throughput") -> int:
+    """Autotuned patch size of the tiled sub-cycle (sse_tune)."""
+    return tune_shapes(mesh, params, precision, objective)["patch_cells"]
 
 
 STATUS = {0: "done", 1: "pending", 2: "active"}

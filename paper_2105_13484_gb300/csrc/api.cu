@@ -461,6 +461,8 @@ struct EngineBase {
     virtual int btr_substep(int order, double dt, int M) = 0;
     virtual int patches() const = 0;       // tiled sub-cycle patches (0: global kernel)
     virtual int patch_threads() const = 0; // threads per patch of the tiled sub-cycle
+    virtual int bcl_patch_cells() const = 0;   // cells per fused baroclinic patch (0: unfused)
+    virtual int bcl_patch_count() const = 0;   // fused baroclinic patches (0: unfused)
     unsigned int inject_stall = 0;         // sse_state_inject(SSE_INJECT_BARRIER_STALL)
     virtual bool has_del4() const = 0;     // biharmonic viscosity on
     virtual bool fused_bcl() const = 0;    // the fused baroclinic stage is used
@@ -562,6 +564,10 @@ struct Engine : EngineBase {
     bool mixed = false;
     bool vmix = false;   // Algorithm 2 in every baroclinic stage
     int patch_cells = 0;   // target cells per sub-cycle patch (sse_tuning; 0: default)
+    int bcl_cells = 0;     // cells per fused baroclinic patch (sse_tuning; 0: default)
+    int bcl_pc = 0;        // the patch size the fused baroclinic plan uses (0: unfused)
+    int bcl_patch_cells() const override { return fused ? bcl_pc : 0; }
+    int bcl_patch_count() const override { return fused ? bcl.P : 0; }
     cudaStream_t s = nullptr;
     DevArena A;
     // state
@@ -714,10 +720,12 @@ struct Engine : EngineBase {
         int smem_block = 0, smem_sm = 0;
         CK(cudaDeviceGetAttribute(&smem_block, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
         CK(cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev));
-        // the largest patches of which as many CTAs fit an SM as the kernel is
-        // built for (two in FP32, one in FP64); else the largest that fit at all
-        for (int pass = 0; pass < 2; pass++)
+        // the requested patch size if its plan fits; else the largest patches
+        // of which as many CTAs fit an SM as the kernel is built for (two in
+        // FP32, one in FP64); else the largest that fit at all
+        for (int pass = bcl_cells > 0 ? -1 : 0; pass < 2; pass++)
         for (int Pc : {160, 128, 112, 96, 80, 64, 48, 32}) {
+            if (pass == -1 && Pc != bcl_cells) continue;
             std::shared_ptr<const BclPlan> cached;
             {
                 sse_mesh *mm = const_cast<sse_mesh *>(mesh);
@@ -737,9 +745,10 @@ struct Engine : EngineBase {
             if (!cached) continue;
             const size_t smem = bcl_smem_bytes<R>(*cached, m.L);
             if (smem + 1024 + sizeof(BclJob<R>) + 64 > (size_t)smem_block) continue;
-            if (pass == 0 && (size_t)bcl_blocks_per_sm<R>() * (smem + 1024 + sizeof(BclJob<R>)) >
+            if (pass <= 0 && (size_t)bcl_blocks_per_sm<R>() * (smem + 1024 + sizeof(BclJob<R>)) >
                                  (size_t)smem_sm)
                 continue;
+            bcl_pc = Pc;
             // both kernels hold a job descriptor in static shared memory
             CK(cudaFuncSetAttribute(bcl_fused_kernel_ptr<R>(),
                                     cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -1504,7 +1513,12 @@ static bool params_ok(const sse_params *prm) {
 static bool tuning_ok(const sse_tuning *t) {
     if (!t) return true;
     if (t->patch_cells < 0) return false;
-    for (int k = 0; k < 7; k++)
+    if (t->bcl_patch_cells != 0) {
+        bool known = false;
+        for (int pc : {160, 128, 112, 96, 80, 64, 48, 32}) known = known || t->bcl_patch_cells == pc;
+        if (!known) return false;
+    }
+    for (int k = 0; k < 6; k++)
         if (t->reserved[k] != 0) return false;
     return true;
 }
@@ -1520,6 +1534,7 @@ static int make_state(const sse_mesh *mesh, const sse_params *prm, const sse_tun
     if (!st) return SSE_ERR_OOM;
     st->device = dev;
     const int pc = (tun && tun->patch_cells > 0) ? tun->patch_cells : 0;
+    const int bpc = tun ? tun->bcl_patch_cells : 0;
     int rc;
     size_t b = 0;
     if (prm->precision == SSE_FP64) {
@@ -1527,6 +1542,7 @@ static int make_state(const sse_mesh *mesh, const sse_params *prm, const sse_tun
         if (!e) { delete st; return SSE_ERR_OOM; }
         st->eng.reset(e);
         e->patch_cells = pc;
+        e->bcl_cells = bpc;
         rc = e->init(mesh, prm, (cudaStream_t)stream, count_only);
         b = e->A.bytes;
     } else {
@@ -1534,6 +1550,7 @@ static int make_state(const sse_mesh *mesh, const sse_params *prm, const sse_tun
         if (!e) { delete st; return SSE_ERR_OOM; }
         st->eng.reset(e);
         e->patch_cells = pc;
+        e->bcl_cells = bpc;
         rc = e->init(mesh, prm, (cudaStream_t)stream, count_only);
         b = e->A.bytes;
     }
@@ -1632,12 +1649,14 @@ extern "C" int sse_tune(const sse_mesh *mesh, const sse_params *prm, int objecti
     if (!params_ok(prm)) return SSE_ERR_INVALID_ARG;
     sse_mesh *mm = const_cast<sse_mesh *>(mesh);
     const int key = -(1 + prm->precision * 2 + objective);   // negative: not a patch count
+    const int bkey = key - 100;                                // the baroclinic patch size
     {
         std::lock_guard<std::mutex> lk(mm->plan_mu);
-        auto it = mm->tuned.find(key);
-        if (it != mm->tuned.end()) {
+        auto it = mm->tuned.find(key), jt = mm->tuned.find(bkey);
+        if (it != mm->tuned.end() && jt != mm->tuned.end()) {
             memset(out, 0, sizeof(*out));
             out->patch_cells = it->second;
+            out->bcl_patch_cells = jt->second;
             return SSE_OK;
         }
     }
@@ -1679,32 +1698,74 @@ extern "C" int sse_tune(const sse_mesh *mesh, const sse_params *prm, int objecti
         if (rc) break;
         res.push_back({pc, {best, sms}});
     }
-    cudaEventDestroy(e0);
-    cudaEventDestroy(e1);
-    cudaStreamSynchronize(s);
-    cudaStreamDestroy(s);
-    if (rc) return rc;
-    int choice = 0;
-    if (!res.empty()) {
+    // LATENCY: the fastest; THROUGHPUT: the least SM-time among candidates
+    // within twice the fastest
+    auto pick = [objective](const std::vector<std::pair<int, std::pair<float, double>>> &cand) {
+        int c = 0;
+        if (cand.empty()) return c;
         float fastest = 1e30f;
-        for (auto &r : res) fastest = std::min(fastest, r.second.first);
+        for (auto &r : cand) fastest = std::min(fastest, r.second.first);
         double best_cost = 1e300;
-        for (auto &r : res) {
+        for (auto &r : cand) {
             const double cost = objective == SSE_TUNE_LATENCY
                                     ? r.second.first
                                     : (double)r.second.first * r.second.second;
             if (r.second.first <= 2.0f * fastest && cost < best_cost) {
                 best_cost = cost;
-                choice = r.first;
+                c = r.first;
             }
         }
+        return c;
+    };
+    const int choice = rc ? 0 : pick(res);
+    // the fused baroclinic kernel's patch size: Algorithm 1 of the same zero
+    // state for each size whose plan fits (a size that falls back is skipped)
+    std::vector<std::pair<int, std::pair<float, double>>> bres;
+    int nsm = 1;
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, mesh->device);
+    const int per_sm = prm->precision == SSE_FP64 ? 1 : 2;   // CTAs per SM of the kernel
+    for (int pc : {160, 128, 112, 96, 80, 64, 48, 32}) {
+        if (rc) break;
+        sse_tuning t{};
+        t.patch_cells = choice;
+        t.bcl_patch_cells = pc;
+        sse_state *st = nullptr;
+        rc = make_state(mesh, prm, &t, s, false, &st, nullptr);
+        if (rc) break;
+        if (st->eng->bcl_patch_cells() != pc) {
+            delete st;
+            continue;
+        }
+        const double sms = std::min((double)nsm,
+                                    (double)((st->eng->bcl_patch_count() + per_sm - 1) / per_sm));
+        float best = 1e30f;
+        for (int rep = 0; rep < 4 && !rc; rep++) {
+            cudaEventRecord(e0, s);
+            rc = st->eng->bcl_feuler(600.0);
+            cudaEventRecord(e1, s);
+            cudaEventSynchronize(e1);
+            float ms = 0;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (rep > 0) best = std::min(best, ms);   // the first run warms up
+        }
+        delete st;
+        if (rc) break;
+        bres.push_back({pc, {best, sms}});
     }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaStreamSynchronize(s);
+    cudaStreamDestroy(s);
+    if (rc) return rc;
+    const int bchoice = pick(bres);
     {
         std::lock_guard<std::mutex> lk(mm->plan_mu);
         mm->tuned[key] = choice;
+        mm->tuned[bkey] = bchoice;
     }
     memset(out, 0, sizeof(*out));
     out->patch_cells = choice;
+    out->bcl_patch_cells = bchoice;
     return SSE_OK;
 }
 

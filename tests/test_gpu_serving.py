@@ -175,6 +175,33 @@ def test_patch_size_keeps_results_within_rounding_and_the_tuner_picks_a_candidat
         assert np.array_equal(a, b)
 
 
+@pytest.mark.parametrize("precision", ["mixed", "fp64"])
+def test_baroclinic_patch_size_keeps_the_bits_and_the_tuner_picks_a_candidate(precision):
+    """sse_tuning.bcl_patch_cells sets the fused baroclinic kernel's patch
+    size; every size computes each edge, cell and vertex with the same
+    arithmetic, so the results are the same bits.  sse_tune returns one of the
+    candidate sizes (or 0), and a size the ABI does not know is refused."""
+    m, L, p, (u, h, tr), run = inputs.workload("sphere_l4", perturb=True)
+    dm = binding.Mesh(m, L)
+    outs = []
+    for pc in (0, 32, 64, 160):
+        st = binding.State(dm, p, precision, bcl_patch_cells=pc)
+        st.load_state(u, h, tr)
+        st.step(3, run["dt"], run["M"], 2)
+        outs.append(st.read_state())
+        st.close()
+    for o in outs[1:]:
+        for a, b in zip(o, outs[0]):
+            assert np.array_equal(a, b)
+    for obj in ("latency", "throughput"):
+        shapes = binding.tune_shapes(dm, p, precision, obj)
+        assert shapes["bcl_patch_cells"] in (0, 160, 128, 112, 96, 80, 64, 48, 32)
+        assert shapes["patch_cells"] in (0, 64, 128, 256, 384, 512, 768, 1024, 1536)
+    with pytest.raises(binding.SSEError):
+        binding.State(dm, p, precision, bcl_patch_cells=33)
+    dm.close()
+
+
 def test_packed_mode_same_result_as_alone():
     """SSE_SERVER_PACKED: the active requests of one precision and order run
     in rounds of one sse_step_batch call; each result equals the request run
