@@ -1,6 +1,6 @@
 """bench.py's reference arm (the oracle, timed on the host cores) prints the
-contract's JSON line without any GPU: the driver runs it next to the GPU arm
-on the same box.  A small sample keeps the test to a few seconds."""
+contract's JSON line without any GPU; it runs next to the GPU arm on the
+same box.  A small sample keeps the test to a few seconds."""
 import json
 import os
 import subprocess
