@@ -345,6 +345,14 @@ int sse_state_create_ex(const sse_mesh *mesh, const sse_params *params,
                         const sse_tuning *tuning, void *cuda_stream, sse_state **out);
 /* Patches of the state's tiled sub-cycle (0: the global-memory sub-cycle). */
 int sse_state_patches(const sse_state *state, int *patches);
+/* The tiled sub-cycle's launch shape (Algorithms 3 and 4): threads per patch
+ * (0 without a tiled sub-cycle), and 1 if each thread's edge coefficients and
+ * edgesOnEdge offsets sit in the SM's tensor memory for the whole sub-cycle
+ * (FP32 form, 1024-thread patches of at most 4096 edges; the environment
+ * variable SSE_BTR_TMEM=0, read when the state is created, turns it off),
+ * else 0 (streamed from L2).  Both shapes give the same bits.  Any output
+ * pointer may be null.  SSE_ERR_INVALID_ARG for a null state. */
+int sse_state_subcycle_shape(const sse_state *state, int *threads, int *tmem);
 /* CUDA graphs the state holds.  sse_step with n_steps >= 2 runs the steps in
  * pairs, each pair replayed from a graph captured (once per order, dt,
  * n_substeps and buffer assignment) from the launches a single step makes;

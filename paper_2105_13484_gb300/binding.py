@@ -87,7 +87,8 @@ EXPORTS = ["sse_mesh_create", "sse_mesh_destroy", "sse_state_create", "sse_state
            "sse_state_set", "sse_state_get", "sse_step", "sse_baroclinic_feuler",
            "sse_barotropic_substep", "sse_diagnostics", "sse_kernels_per_step", "sse_profile",
            "sse_profile_read", "sse_barotropic_substep_noalloc", "sse_state_footprint",
-           "sse_state_footprint_ex", "sse_state_create_ex", "sse_state_patches", "sse_state_inject",
+           "sse_state_footprint_ex", "sse_state_create_ex", "sse_state_patches", "sse_state_subcycle_shape",
+           "sse_state_inject",
            "sse_state_set_f32", "sse_state_get_f32", "sse_state_graphs", "sse_state_transfer",
            "sse_state_sync",
            "sse_tune",
@@ -145,6 +146,7 @@ def load(path: str = LIB_PATH):
     lib.sse_state_footprint_ex.argtypes = [ct.c_void_p, ct.POINTER(Params), ct.POINTER(Tuning),
                                            ct.POINTER(ct.c_size_t)]
     lib.sse_state_patches.argtypes = [ct.c_void_p, ct.POINTER(ct.c_int)]
+    lib.sse_state_subcycle_shape.argtypes = [ct.c_void_p, ct.POINTER(ct.c_int), ct.POINTER(ct.c_int)]
     lib.sse_state_graphs.argtypes = [ct.c_void_p, ct.POINTER(ct.c_int)]
     lib.sse_state_transfer.argtypes = [ct.c_void_p, ct.c_int, ct.c_void_p, ct.c_int]
     lib.sse_state_sync.argtypes = [ct.c_void_p]
@@ -418,6 +420,13 @@ class State:
         n = ct.c_int()
         _check(self.lib.sse_state_patches(self.handle, ct.byref(n)), "sse_state_patches")
         return int(n.value)
+
+    def subcycle_shape(self):
+        """(threads per patch, tensor memory used) of the tiled sub-cycle."""
+        th, tm = ct.c_int(), ct.c_int()
+        _check(self.lib.sse_state_subcycle_shape(self.handle, ct.byref(th), ct.byref(tm)),
+               "sse_state_subcycle_shape")
+        return int(th.value), bool(tm.value)
 
     def inject_barrier_stall(self, on: bool):
         """Test hook: every grid-barrier wait of the sub-cycle runs out its

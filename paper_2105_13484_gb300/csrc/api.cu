@@ -461,6 +461,7 @@ struct EngineBase {
     virtual int btr_substep(int order, double dt, int M) = 0;
     virtual int patches() const = 0;       // tiled sub-cycle patches (0: global kernel)
     virtual int patch_threads() const = 0; // threads per patch of the tiled sub-cycle
+    virtual int patch_tmem() const = 0;    // 1: the tiled sub-cycle's edge data in tensor memory
     virtual int bcl_patch_cells() const = 0;   // cells per fused baroclinic patch (0: unfused)
     virtual int bcl_patch_count() const = 0;   // fused baroclinic patches (0: unfused)
     unsigned int inject_stall = 0;         // sse_state_inject(SSE_INJECT_BARRIER_STALL)
@@ -671,20 +672,40 @@ struct Engine : EngineBase {
                 continue;
             }
             const int own = std::max(2, (most + nthreads - 1) / nthreads);
+            // FP32 1024-thread patches keep their edges' constant data in
+            // tensor memory when every patch has at most that variant's slots
+            // of edges per thread (SSE_BTR_TMEM=0 turns it off)
+            const char *tenv = getenv("SSE_BTR_TMEM");
+            int mne = 0;
+            for (const TilePatch &t : plan.patches) mne = std::max(mne, t.ne);
+            const bool tm = sizeof(R) == 4 && nthreads == 1024 && mne <= btr_tiled_tmem_slots() * 1024 &&
+                            !(tenv && strcmp(tenv, "0") == 0);
 
             // the attribute belongs to the kernel, not to this state: allow the
             // device's whole opt-in size so that states of other meshes, whose
             // plans need less or more, never lower it under each other
+            int static_smem = 0;
             for (int o = 2; o <= 3; o++) {
                 cudaFuncAttributes fa;
-                CK(cudaFuncGetAttributes(&fa, btr_tiled_kernel_ptr<R>(o, own, nthreads)));
-                CK(cudaFuncSetAttribute(btr_tiled_kernel_ptr<R>(o, own, nthreads),
+                CK(cudaFuncGetAttributes(&fa, btr_tiled_kernel_ptr<R>(o, own, nthreads, tm)));
+                CK(cudaFuncSetAttribute(btr_tiled_kernel_ptr<R>(o, own, nthreads, tm),
                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
                                         smem_block - (int)fa.sharedSizeBytes));
+                static_smem = std::max(static_smem, (int)fa.sharedSizeBytes);
+            }
+            size_t smem_launch = smem;
+            if (tm) {
+                // The kernel allocates all 512 columns of its SM's tensor
+                // memory, an allocation that would wait for another holder:
+                // asking for more than half the SM's shared memory keeps any
+                // second such CTA off the SM, so the allocation never waits.
+                smem_launch = tile_smem_bytes(plan, m.maxE, m.maxE2, sizeof(R), false);
+                const size_t fixed = (size_t)static_smem + 1024, half = (size_t)smem_sm / 2 + 1;
+                if (smem_launch + fixed < half) smem_launch = half - fixed;
             }
             int occ = 0;
             CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-                &occ, btr_tiled_kernel_ptr<R>(3, own, nthreads), nthreads, smem));
+                &occ, btr_tiled_kernel_ptr<R>(3, own, nthreads, tm), nthreads, smem_launch));
             if (occ * nsm < P) {
                 if (verbose)
                     fprintf(stderr, "libsse: tile plan k=%d P=%d: occupancy %d x %d SMs\n", k, P,
@@ -692,18 +713,18 @@ struct Engine : EngineBase {
                 continue;
             }
             if (verbose) {
-                int mne = 0, mnc = 0, moe = 0;
+                int mnc = 0, moe = 0;
                 long long tne = 0, tnc = 0;
                 for (const TilePatch &t : plan.patches) {
-                    mne = std::max(mne, t.ne); mnc = std::max(mnc, t.nc);
+                    mnc = std::max(mnc, t.nc);
                     moe = std::max(moe, t.n_own_e); tne += t.ne; tnc += t.nc;
                 }
-                fprintf(stderr, "libsse: tiled sub-cycle P=%d threads=%d own=%d smem=%zu "
+                fprintf(stderr, "libsse: tiled sub-cycle P=%d threads=%d own=%d smem=%zu tmem=%d "
                         "max(ne,nc,own_e)=(%d,%d,%d) halo overhead edges %.2f cells %.2f\n", P,
-                        nthreads, own, smem, mne, mnc, moe,
+                        nthreads, own, smem_launch, (int)tm, mne, mnc, moe,
                         (double)tne / m.E, (double)tnc / m.C);
             }
-            return upload_tiles(plan, nthreads, own, smem);
+            return upload_tiles(plan, nthreads, own, smem_launch, tm);
         }
         return SSE_OK;  // no plan fits: the global-memory sub-cycle is used
     }
@@ -826,7 +847,7 @@ struct Engine : EngineBase {
         return SSE_OK;
     }
 
-    int upload_tiles(const TilePlan &plan, int nthreads, int own, size_t smem) {
+    int upload_tiles(const TilePlan &plan, int nthreads, int own, size_t smem, bool tm) {
         const unsigned int sR = sizeof(R);
         std::vector<int> noc, noe, nie, cg, eg, c12, nel, ncl;
         std::vector<unsigned short> eo, ce;
@@ -867,7 +888,7 @@ struct Engine : EngineBase {
             for (double x : t.H) Hh.push_back((R)x);
         }
         DTiles<R> &t = tiles;
-        t.P = plan.P; t.nthreads = nthreads; t.own = own; t.smem = smem;
+        t.P = plan.P; t.nthreads = nthreads; t.own = own; t.smem = smem; t.tm = tm ? 1 : 0;
         t.cell_off = A.upload(plan.cell_off); t.edge_off = A.upload(plan.edge_off);
         t.n_own_c = A.upload(noc); t.n_own_e = A.upload(noe); t.n_int_e = A.upload(nie);
         t.ne_lim = A.upload(nel); t.nc_lim = A.upload(ncl);
@@ -1432,6 +1453,7 @@ struct Engine : EngineBase {
 
     int patches() const override { return tiled ? tiles.P : 0; }
     int patch_threads() const override { return tiled ? tiles.nthreads : 0; }
+    int patch_tmem() const override { return tiled ? tiles.tm : 0; }
     bool has_del4() const override { return db.del2 != nullptr; }
     bool fused_bcl() const override { return fused; }
 
@@ -1631,6 +1653,13 @@ extern "C" int sse_state_graphs(const sse_state *st, int *graphs) {
 extern "C" int sse_state_patches(const sse_state *st, int *patches) {
     if (!st || !patches) return SSE_ERR_INVALID_ARG;
     *patches = st->eng->patches();
+    return SSE_OK;
+}
+
+extern "C" int sse_state_subcycle_shape(const sse_state *st, int *threads, int *tmem) {
+    if (!st) return SSE_ERR_INVALID_ARG;
+    if (threads) *threads = st->eng->patch_threads();
+    if (tmem) *tmem = st->eng->patch_tmem();
     return SSE_OK;
 }
 

@@ -304,13 +304,13 @@ constexpr int TILE_NE2 = 10;  // edgesOnEdge terms evaluated per edge (padding -
 // (small) increments: in FP32 the full ubar and zeta would lose the 1e-3 to
 // 1e-2 of themselves that their gradients and changes over a sub-cycle are.
 // Every SSPRK combination has weights summing to one, so it applies to the
-// increments unchanged.  (1/dc is read from global memory with the Coriolis
-// coefficients, as their last row, which keeps the patch's shared memory at
-// its plain size.)
+// increments unchanged.  (1/dc is stored with the Coriolis coefficients, as
+// their last row, which keeps the patch's shared memory at its plain size.)
 template <class R> struct TileSmem {
     R *u0, *ua, *uh, *fl, *z0, *za, *zh, *F0, *ub0, *d0;
     unsigned int *c12;                // packed byte offsets of (c1, c2) into the cell arrays
     unsigned short *eoe;              // [ne+1][TILE_NE2P] byte offsets into the edge arrays
+                                      // (null when they live in tensor memory)
     unsigned short *ce;               // [nc+1][TILE_NCEP] byte offsets into fl
 };
 
@@ -319,7 +319,7 @@ __device__ __forceinline__ char *align16(char *p) {
 }
 
 template <class R>
-__device__ __forceinline__ TileSmem<R> carve(char *base, int ne, int nc) {
+__device__ __forceinline__ TileSmem<R> carve(char *base, int ne, int nc, bool eoe_smem) {
     TileSmem<R> s;
     char *c = align16(base);
     const int ne1 = ne + 1, nc1 = nc + 1;
@@ -329,7 +329,8 @@ __device__ __forceinline__ TileSmem<R> carve(char *base, int ne, int nc) {
     s.F0 = r; r += ne1; s.ub0 = r; r += ne1; s.d0 = r; r += nc1;
     c = align16((char *)r);
     s.c12 = (unsigned int *)c; c = align16(c + 4 * ne1);
-    s.eoe = (unsigned short *)c; c = align16(c + 2 * TILE_NE2P * (size_t)ne1);
+    s.eoe = nullptr;
+    if (eoe_smem) { s.eoe = (unsigned short *)c; c = align16(c + 2 * TILE_NE2P * (size_t)ne1); }
     s.ce = (unsigned short *)c;
     return s;
 }
@@ -338,31 +339,177 @@ template <class R> __device__ __forceinline__ R at(const R *base, unsigned int o
     return *(const R *)((const char *)base + off);
 }
 
-// forward-Euler edge update on the patch, on the increments u, z: returns the
-// new ubar increment, sets the flux of the full state.  The patch's Coriolis
-// coefficients are term-major: term j of edge l at cfc[j * ne + l].
-template <class R>
-__device__ __forceinline__ R tile_fe_edge(const TileSmem<R> &S, const R *__restrict__ cfc, int ne,
-                                          int l, const R *u, const R *z, R tau, R g, R &flux) {
-    R cf[TILE_CFR];   // the Coriolis coefficients, then 1 / d_e
+// ---- tensor memory as per-thread storage (FP32 form, 1024-thread patches).
+// A thread's edges (l = tid + k * 1024, k < TM_SLOTS) never change during
+// the sub-cycle, and neither do their Coriolis coefficients, 1/d_e and
+// edgesOnEdge offsets: 16 words per edge, read every sub-stage.  Streamed
+// from L2 they cost about a fifth of the sub-cycle (the patch's shared memory
+// leaves L1 no room to keep them); held in tensor memory they are one
+// 32x32b.x16 load per edge.  In that access shape thread i of warp w reads
+// TMEM lane 32 (w % 4) + i, so the eight warps of a lane quadrant take
+// disjoint 64-column ranges (w / 4) * 64 + 16 k: 512 columns in all.
+constexpr int TM_SLOTS = 4;
+constexpr int TM_COLS_SLOT = 16;   // 11 coefficients + 5 words of packed offsets
+constexpr int TM_THREADS = 1024;
+constexpr unsigned int TM_COLS = (TM_THREADS / 128) * TM_SLOTS * TM_COLS_SLOT;   // 512
+static_assert(TILE_CFR + TILE_NE2P / 2 == TM_COLS_SLOT, "one TMEM slot per edge");
+
+// Allocation by one whole warp; the address goes to shared memory.  The
+// launch guarantees that no other CTA using tensor memory shares the SM (its
+// shared memory exceeds half the SM's), so the allocation never waits.
+__device__ __forceinline__ void tmem_alloc(unsigned int *dst, unsigned int ncols) {
+    const unsigned int d = (unsigned int)__cvta_generic_to_shared(dst);
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
+                 ::"r"(d), "r"(ncols) : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_dealloc(unsigned int taddr, unsigned int ncols) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;"
+                 ::"r"(taddr), "r"(ncols) : "memory");
+}
+__device__ __forceinline__ void tmem_fence_before() {
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_fence_after() {
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_st16(unsigned int taddr, const unsigned int (&v)[16]) {
+    asm volatile("tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], "
+                 "{%1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, %16};"
+                 ::"r"(taddr), "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]),
+                 "r"(v[6]), "r"(v[7]), "r"(v[8]), "r"(v[9]), "r"(v[10]), "r"(v[11]), "r"(v[12]),
+                 "r"(v[13]), "r"(v[14]), "r"(v[15]) : "memory");
+}
+__device__ __forceinline__ void tmem_st_wait() {
+    asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+}
+// load and wait; the registers pass through the wait so that no use of them
+// can be scheduled before it
+__device__ __forceinline__ void tmem_ld16(unsigned int taddr, unsigned int (&v)[16]) {
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+                 "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, [%16];"
+                 : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]),
+                   "=r"(v[6]), "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]),
+                   "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
+                 : "r"(taddr) : "memory");
+    asm volatile("tcgen05.wait::ld.sync.aligned;"
+                 : "+r"(v[0]), "+r"(v[1]), "+r"(v[2]), "+r"(v[3]), "+r"(v[4]), "+r"(v[5]),
+                   "+r"(v[6]), "+r"(v[7]), "+r"(v[8]), "+r"(v[9]), "+r"(v[10]), "+r"(v[11]),
+                   "+r"(v[12]), "+r"(v[13]), "+r"(v[14]), "+r"(v[15])
+                 :: "memory");
+}
+
+// An edge's constant data: TILE_CFR coefficients (the Coriolis terms, then
+// 1/d_e) and its TILE_NE2P edgesOnEdge byte offsets.  From tensor memory (a
+// warp-collective load: every lane of the warp calls it) or from the patch's
+// global coefficient block and shared offsets (only for l < ne).
+template <class R, bool TM>
+__device__ __forceinline__ void edge_coefs(const TileSmem<R> &S, const R *__restrict__ cfc,
+                                           int ne, int l, unsigned int taddr,
+                                           R (&cf)[TILE_CFR], unsigned int (&o)[TILE_NE2P]) {
+    if constexpr (TM) {
+        unsigned int v[16];
+        tmem_ld16(taddr, v);
 #pragma unroll
-    for (int j = 0; j < TILE_CFR; j++) cf[j] = __ldg(cfc + (size_t)j * ne + l);
-    const unsigned int *eo = (const unsigned int *)(S.eoe + (size_t)l * TILE_NE2P);
-    unsigned int o[TILE_NE2P];
+        for (int j = 0; j < TILE_CFR; j++) cf[j] = __uint_as_float(v[j]);
 #pragma unroll
-    for (int i = 0; i < TILE_NE2P / 2; i++) {
-        const unsigned int v = eo[i];
-        o[2 * i] = v & 0xffffu; o[2 * i + 1] = v >> 16;
+        for (int i = 0; i < TILE_NE2P / 2; i++) {
+            o[2 * i] = v[TILE_CFR + i] & 0xffffu; o[2 * i + 1] = v[TILE_CFR + i] >> 16;
+        }
+    } else {
+#pragma unroll
+        for (int j = 0; j < TILE_CFR; j++) cf[j] = __ldg(cfc + (size_t)j * ne + l);
+        const unsigned int *eo = (const unsigned int *)(S.eoe + (size_t)l * TILE_NE2P);
+#pragma unroll
+        for (int i = 0; i < TILE_NE2P / 2; i++) {
+            const unsigned int v = eo[i];
+            o[2 * i] = v & 0xffffu; o[2 * i + 1] = v >> 16;
+        }
     }
+}
+
+// The sub-stage arithmetic with every fused multiply-add spelled out: left to
+// the compiler, a*x + b*y may fuse either product, and the choice can differ
+// between the kernel's instantiations and between the owned and halo copies
+// of one expression, which then round differently.  Written out, every code
+// path that evaluates an edge or a cell rounds it the same way.
+__device__ __forceinline__ float fma_r(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ double fma_r(double a, double b, double c) { return __fma_rn(a, b, c); }
+__device__ __forceinline__ float mul_r(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ double mul_r(double a, double b) { return __dmul_rn(a, b); }
+// a x + b y, the second product rounded first
+template <class R> __device__ __forceinline__ R comb(R a, R x, R b, R y) {
+    return fma_r(a, x, mul_r(b, y));
+}
+
+// forward-Euler edge update on the patch, on the increments u, z: returns the
+// new ubar increment, sets the flux of the full state
+template <class R>
+__device__ __forceinline__ R tile_fe_edge(const TileSmem<R> &S, const R (&cf)[TILE_CFR],
+                                          const unsigned int (&o)[TILE_NE2P], int l,
+                                          const R *u, const R *z, R tau, R g, R &flux) {
     R acc = R(0);
 #pragma unroll
-    for (int j = 0; j < TILE_NE2; j++) acc += cf[j] * at(u, o[j]);
+    for (int j = 0; j < TILE_NE2; j++) acc = fma_r(cf[j], at(u, o[j]), acc);
     const unsigned int cc = S.c12[l];
     const unsigned int a = cc & 0xffffu, b = cc >> 16;
     const R za = at(z, a), zb = at(z, b);
     const R ue = u[l];
-    flux = (S.ub0[l] + ue) * (R(0.5) * ((at(S.d0, a) + at(S.d0, b)) + (za + zb)));
-    return ue + tau * (S.F0[l] + acc - g * (zb - za) * cf[TILE_NE2P]);
+    flux = mul_r(S.ub0[l] + ue, mul_r(R(0.5), (at(S.d0, a) + at(S.d0, b)) + (za + zb)));
+    const R rhs = fma_r(-mul_r(g, zb - za), cf[TILE_NE2P], S.F0[l] + acc);
+    return fma_r(tau, rhs, ue);
+}
+
+// One forward-Euler sub-stage over this thread's edges in [lo, hi);
+// fn(k, l, new increment, flux) stores the results, k < OWN for an owned edge
+// in slot k (l = tid + k nt < noe), k = OWN for a halo edge.  With TM every
+// edge has a slot (l = tid + k nt, k < KS): a warp whose 32 edges of slot k
+// all lie outside [lo, hi) skips it, the others load the slot in every lane
+// (the tensor-memory load is warp-collective) and compute only the lanes
+// inside the range.  Without, the owned slots are unrolled and the halo edges
+// (l = noe + tid + i nt) loop.
+template <class R, bool TM, int KS, int OWN, class Fn>
+__device__ __forceinline__ void edge_pass(const TileSmem<R> &S, const R *__restrict__ cfc,
+                                          int ne, int noe, unsigned int tsl, int tid, int nt,
+                                          int lo, int hi, const R *u, const R *z, R tau, R g,
+                                          Fn &&fn) {
+    if constexpr (TM) {
+#pragma unroll
+        for (int k = 0; k < KS; k++) {
+            const int l = tid + k * nt, w0 = (tid & ~31) + k * nt;
+            if (w0 >= hi || w0 + 32 <= lo) continue;
+            R cf[TILE_CFR];
+            unsigned int o[TILE_NE2P];
+            __syncwarp();
+            edge_coefs<R, true>(S, cfc, ne, l, tsl + (unsigned int)(k * TM_COLS_SLOT), cf, o);
+            if (l >= lo && l < hi) {
+                R f;
+                const R r = tile_fe_edge<R>(S, cf, o, l, u, z, tau, g, f);
+                fn(k < OWN && l < noe ? k : OWN, l, r, f);
+            }
+        }
+    } else {
+#pragma unroll
+        for (int k = 0; k < OWN; k++) {
+            const int l = tid + k * nt;
+            if (l >= lo && l < hi && l < noe) {
+                R cf[TILE_CFR];
+                unsigned int o[TILE_NE2P];
+                edge_coefs<R, false>(S, cfc, ne, l, 0u, cf, o);
+                R f;
+                const R r = tile_fe_edge<R>(S, cf, o, l, u, z, tau, g, f);
+                fn(k, l, r, f);
+            }
+        }
+        for (int l = noe + tid; l < hi; l += nt) {
+            R cf[TILE_CFR];
+            unsigned int o[TILE_NE2P];
+            edge_coefs<R, false>(S, cfc, ne, l, 0u, cf, o);
+            R f;
+            const R r = tile_fe_edge<R>(S, cf, o, l, u, z, tau, g, f);
+            fn(OWN, l, r, f);
+        }
+    }
 }
 
 // term j of cell l's divergence coefficients at dvc[j * nc + l]
@@ -381,8 +528,8 @@ __device__ __forceinline__ R tile_fe_cell(const TileSmem<R> &S, const R *__restr
     }
     R dv = R(0);
 #pragma unroll
-    for (int j = 0; j < TILE_NCEP; j++) dv += dc[j] * at(S.fl, o[j]);
-    return z[l] - tau * dv;
+    for (int j = 0; j < TILE_NCEP; j++) dv = fma_r(dc[j], at(S.fl, o[j]), dv);
+    return fma_r(-tau, dv, z[l]);
 }
 
 // Accumulator of F^zeta = (1/M) sum_j (sub-step flux sum) for one owned
@@ -410,14 +557,64 @@ template <> struct FzAcc<double> {
     __device__ __forceinline__ double value(double) const { return s; }
 };
 
+// The Coriolis term of the starting ubar, sum_j cf_j ub0_j, as the FP64 value
+// the starting forcing adds.  FP64 form: FP64 products and sums.  Mixed form:
+// the compensated dot product of Ogita, Rump and Oishi ("Accurate sum and dot
+// product", SIAM J. Sci. Comput. 26, 2005, Algorithm Dot2): each product's
+// rounding error from an FMA, each sum's from Knuth's TwoSum, the errors
+// summed apart, so that the result is as accurate as if computed in twice
+// FP32's precision -- without FP64 arithmetic, ten of whose operations per
+// edge cost more than the whole FP32 evaluation.
+template <class R>
+__device__ __forceinline__ double coriolis_start(const R (&cf)[TILE_CFR],
+                                                 const unsigned int (&o)[TILE_NE2P], const R *ub0) {
+    if constexpr (sizeof(R) == 4) {
+        float s = 0.f, c = 0.f;
+#pragma unroll
+        for (int j = 0; j < TILE_NE2; j++) {
+            const float x = cf[j], y = at(ub0, o[j]);
+            // __fmul_rn / __fadd_rn: never contracted into an FMA, which
+            // would break the error-free transformations
+            const float p = __fmul_rn(x, y), pe = fmaf(x, y, -p);
+            const float t = __fadd_rn(s, p), z = __fsub_rn(t, s);
+            const float se = __fadd_rn(__fsub_rn(s, __fsub_rn(t, z)), __fsub_rn(p, z));
+            s = t;
+            c += pe + se;
+        }
+        return (double)s + (double)c;
+    } else {
+        double cb = 0.0;
+#pragma unroll
+        for (int j = 0; j < TILE_NE2; j++) cb += (double)cf[j] * (double)at(ub0, o[j]);
+        return cb;
+    }
+}
+
 // Each thread owns at most OWN owned edges, halo edges, owned cells and halo
 // cells of its patch (the plan checks this); their global indices, the
-// sub-step's partial F^zeta and the FP64 accumulators stay in registers.
-template <class R, int ORDER, int OWN, int NT>
+// sub-step's partial F^zeta and the FP64 accumulators stay in registers.  The
+// forward-Euler sub-stages take edge l = tid + k nt in slot k, owned edges
+// (l < n_own_e) in the first OWN slots; with TM the slots' constant edge data
+// live in tensor memory (FP32, 1024 threads, at most TM_SLOTS slots).
+template <class R, int ORDER, int OWN, int NT, bool TM>
 __global__ void __launch_bounds__(NT, 1024 / NT) k_btr_tiled(DTiles<R> t, BtrArgs<R> a,
                                                              Barrier bar) {
+    static_assert(!TM || (sizeof(R) == 4 && NT == TM_THREADS), "tensor memory: FP32, 1024 threads");
+    constexpr int KS = TM ? TM_SLOTS : 2 * OWN;   // edge slots per thread
     extern __shared__ __align__(16) char smem_raw[];
+    __shared__ unsigned int s_tmem;
     const int p = blockIdx.x, tid = threadIdx.x, nt = blockDim.x;
+    // tensor memory first, before any exit: warp 0 allocates, every thread
+    // learns the base address, and every path out of the kernel frees it
+    unsigned int tsl = 0;   // this thread's lane and first column
+    if constexpr (TM) {
+        if (tid < 32) tmem_alloc(&s_tmem, TM_COLS);
+        tmem_fence_before();
+        __syncthreads();
+        tmem_fence_after();
+        tsl = s_tmem + ((unsigned int)(32 * ((tid >> 5) & 3)) << 16) +
+              (unsigned int)((tid >> 7) * (TM_SLOTS * TM_COLS_SLOT));
+    }
     const int coff = t.cell_off[p], eoff = t.edge_off[p];
     const int nc = t.cell_off[p + 1] - coff, ne = t.edge_off[p + 1] - eoff;
     const int noc = t.n_own_c[p], noe = t.n_own_e[p], nint = t.n_int_e[p];
@@ -426,9 +623,10 @@ __global__ void __launch_bounds__(NT, 1024 / NT) k_btr_tiled(DTiles<R> t, BtrArg
     // outer rings of the halo drop out one per sub-stage)
     const int neA = t.ne_lim[3 * p], neB = t.ne_lim[3 * p + 1], neC = t.ne_lim[3 * p + 2];
     const int ncA = t.nc_lim[3 * p], ncB = t.nc_lim[3 * p + 1], ncC = t.nc_lim[3 * p + 2];
-    const TileSmem<R> S = carve<R>(smem_raw, ne, nc);
+    const TileSmem<R> S = carve<R>(smem_raw, ne, nc, !TM);
     const R *cfc = t.cfc + (size_t)eoff * TILE_CFR;
     const R *dvc = t.divc + (size_t)coff * TILE_NCEP;
+    const unsigned short *eoe_g = t.eoe + (size_t)eoff * TILE_NE2P;
     const R tau = (R)a.tau, g = (R)a.g;
     const R third = R(1.0 / 3.0), two_thirds = R(2.0 / 3.0);
     // global indices of this thread's owned and halo entries
@@ -465,10 +663,10 @@ __global__ void __launch_bounds__(NT, 1024 / NT) k_btr_tiled(DTiles<R> t, BtrArg
         S.ub0[l] = u; S.c12[l] = cc;
         S.u0[l] = R(0); S.ua[l] = R(0); S.uh[l] = R(0); S.fl[l] = R(0);
     }
-    {
+    if constexpr (!TM) {
         // rows are TILE_NE2P * 2 = 20 bytes: copy in 4-byte words (every row and the
         // patch base edge_off * 20 bytes are 4-byte aligned)
-        const unsigned int *src = (const unsigned int *)(t.eoe + (size_t)eoff * TILE_NE2P);
+        const unsigned int *src = (const unsigned int *)eoe_g;
         unsigned int *dst = (unsigned int *)S.eoe;
         const int n4 = ne * (TILE_NE2P / 2);
         for (int x = tid; x < n4; x += nt) dst[x] = src[x];
@@ -491,97 +689,88 @@ __global__ void __launch_bounds__(NT, 1024 / NT) k_btr_tiled(DTiles<R> t, BtrArg
 #pragma unroll
     for (int k = 0; k < OWN; k++) Fs[k] = R(0);
     __syncthreads();
-    // the Coriolis term of the starting ubar completes the starting forcing
-    for (int l = tid; l < ne; l += nt) {
-        const unsigned int *eo = (const unsigned int *)(S.eoe + (size_t)l * TILE_NE2P);
-        double cb = 0.0;
+    // the Coriolis term of the starting ubar completes the starting forcing;
+    // with TM the same pass moves each slot's constant edge data into tensor
+    // memory (every lane stores every slot: the store is warp-collective)
+#pragma unroll 1
+    for (int k = 0; k < KS; k++) {
+        const int l = tid + k * nt;
+        if (!TM && l >= ne) break;
+        R cf[TILE_CFR];
+        unsigned int o[TILE_NE2P];
+        unsigned int v[16];
 #pragma unroll
-        for (int i = 0; i < TILE_NE2 / 2; i++) {
-            const unsigned int v = eo[i];
-            cb += (double)__ldg(cfc + (size_t)(2 * i) * ne + l) * (double)at(S.ub0, v & 0xffffu);
-            cb += (double)__ldg(cfc + (size_t)(2 * i + 1) * ne + l) * (double)at(S.ub0, v >> 16);
+        for (int i = 0; i < 16; i++) v[i] = 0u;
+        if (l < ne) {
+#pragma unroll
+            for (int j = 0; j < TILE_CFR; j++) cf[j] = __ldg(cfc + (size_t)j * ne + l);
+            const unsigned int *eo = (const unsigned int *)(eoe_g + (size_t)l * TILE_NE2P);
+#pragma unroll
+            for (int i = 0; i < TILE_NE2P / 2; i++) {
+                const unsigned int w = __ldg(eo + i);
+                o[2 * i] = w & 0xffffu; o[2 * i + 1] = w >> 16;
+                v[TILE_CFR + i] = w;
+            }
+            S.F0[l] = (R)((double)S.F0[l] + coriolis_start<R>(cf, o, S.ub0));
+            if constexpr (TM) {
+#pragma unroll
+                for (int j = 0; j < TILE_CFR; j++) v[j] = __float_as_uint(cf[j]);
+            }
         }
-        S.F0[l] = (R)((double)S.F0[l] + cb);
+        if constexpr (TM) {
+            __syncwarp();
+            tmem_st16(tsl + (unsigned int)(k * TM_COLS_SLOT), v);
+        }
     }
+    if constexpr (TM) tmem_st_wait();
     __syncthreads();
 
     const R wAB = (ORDER == 2) ? R(0.5) : R(1.0 / 6.0);
     const R wC = R(2.0 / 3.0);
     const double invM = 1.0 / a.M;
     int buf = 0;
+    bool ok = true;
     for (int j = 0; j < a.M; j++) {
         // ---- stage a: (ua, za) = FE(u0, z0); after the first sub-step the owned
         // edges below nint were already done while the halo exchange was in
         // flight, except by the arriving warp
         const int lo = (j == 0 || arriver) ? 0 : nint;
-#pragma unroll
-        for (int k = 0; k < OWN; k++) {
-            const int l = tid + k * nt;
-            if (l >= lo && l < noe) {
-                R f;
-                S.ua[l] = tile_fe_edge<R>(S, cfc, ne, l, S.u0, S.z0, tau, g, f);
-                S.fl[l] = f;
-                Fs[k] = wAB * f;
-            }
-        }
-        for (int l = noe + tid; l < neA; l += nt) {
-            R f;
-            S.ua[l] = tile_fe_edge<R>(S, cfc, ne, l, S.u0, S.z0, tau, g, f);
-            S.fl[l] = f;
-        }
+        edge_pass<R, TM, KS, OWN>(S, cfc, ne, noe, tsl, tid, nt, lo, neA, S.u0, S.z0, tau, g,
+                             [&](int k, int l, R r, R f) {
+                                 S.ua[l] = r;
+                                 S.fl[l] = f;
+                                 if (k < OWN) Fs[k] = mul_r(wAB, f);
+                             });
         __syncthreads();
         for (int l = tid; l < ncA; l += nt) S.za[l] = tile_fe_cell<R>(S, dvc, nc, l, S.z0, tau);
         __syncthreads();
         // ---- stage b: FE(ua, za), first convex combination
-#pragma unroll
-        for (int k = 0; k < OWN; k++) {
-            const int l = tid + k * nt;
-            if (l < noe) {
-                R f;
-                const R ub = tile_fe_edge<R>(S, cfc, ne, l, S.ua, S.za, tau, g, f);
-                S.fl[l] = f;
-                Fs[k] += wAB * f;
-                if (ORDER == 2) S.u0[l] = R(0.5) * (S.u0[l] + ub);
-                else S.uh[l] = R(0.75) * S.u0[l] + R(0.25) * ub;
-            }
-        }
-        for (int l = noe + tid; l < neB; l += nt) {
-            R f;
-            const R ub = tile_fe_edge<R>(S, cfc, ne, l, S.ua, S.za, tau, g, f);
-            S.fl[l] = f;
-            if (ORDER == 2) S.u0[l] = R(0.5) * (S.u0[l] + ub);
-            else S.uh[l] = R(0.75) * S.u0[l] + R(0.25) * ub;
-        }
+        edge_pass<R, TM, KS, OWN>(S, cfc, ne, noe, tsl, tid, nt, 0, neB, S.ua, S.za, tau, g,
+                             [&](int k, int l, R ub, R f) {
+                                 S.fl[l] = f;
+                                 if (k < OWN) Fs[k] = fma_r(wAB, f, Fs[k]);
+                                 if (ORDER == 2) S.u0[l] = mul_r(R(0.5), S.u0[l] + ub);
+                                 else S.uh[l] = comb(R(0.75), S.u0[l], R(0.25), ub);
+                             });
         __syncthreads();
         for (int l = tid; l < ncB; l += nt) {
             const R zb = tile_fe_cell<R>(S, dvc, nc, l, S.za, tau);
-            if (ORDER == 2) S.z0[l] = R(0.5) * (S.z0[l] + zb);
-            else S.zh[l] = R(0.75) * S.z0[l] + R(0.25) * zb;
+            if (ORDER == 2) S.z0[l] = mul_r(R(0.5), S.z0[l] + zb);
+            else S.zh[l] = comb(R(0.75), S.z0[l], R(0.25), zb);
         }
         __syncthreads();
         if (ORDER == 3) {
             // ---- stage c: FE(uh, zh), second convex combination
-#pragma unroll
-            for (int k = 0; k < OWN; k++) {
-                const int l = tid + k * nt;
-                if (l < noe) {
-                    R f;
-                    const R uc = tile_fe_edge<R>(S, cfc, ne, l, S.uh, S.zh, tau, g, f);
-                    S.fl[l] = f;
-                    Fs[k] += wC * f;
-                    S.u0[l] = third * S.u0[l] + two_thirds * uc;
-                }
-            }
-            for (int l = noe + tid; l < neC; l += nt) {
-                R f;
-                const R uc = tile_fe_edge<R>(S, cfc, ne, l, S.uh, S.zh, tau, g, f);
-                S.fl[l] = f;
-                S.u0[l] = third * S.u0[l] + two_thirds * uc;
-            }
+            edge_pass<R, TM, KS, OWN>(S, cfc, ne, noe, tsl, tid, nt, 0, neC, S.uh, S.zh, tau, g,
+                                 [&](int k, int l, R uc, R f) {
+                                     S.fl[l] = f;
+                                     if (k < OWN) Fs[k] = fma_r(wC, f, Fs[k]);
+                                     S.u0[l] = comb(third, S.u0[l], two_thirds, uc);
+                                 });
             __syncthreads();
             for (int l = tid; l < ncC; l += nt) {
                 const R zc = tile_fe_cell<R>(S, dvc, nc, l, S.zh, tau);
-                S.z0[l] = third * S.z0[l] + two_thirds * zc;
+                S.z0[l] = comb(third, S.z0[l], two_thirds, zc);
             }
             __syncthreads();
         }
@@ -602,17 +791,17 @@ __global__ void __launch_bounds__(NT, 1024 / NT) k_btr_tiled(DTiles<R> t, BtrArg
         // writes only ua and the flux, which the refresh does not touch.  The
         // arriving warp, which waits for its release first, leaves its share
         // to the main stage a.
-#pragma unroll
-        for (int k = 0; k < OWN; k++) {
-            const int l = tid + k * nt;
-            if (!arriver && l < nint) {
-                R f;
-                S.ua[l] = tile_fe_edge<R>(S, cfc, ne, l, S.u0, S.z0, tau, g, f);
-                S.fl[l] = f;
-                Fs[k] = wAB * f;
-            }
+        if (!arriver)
+            edge_pass<R, TM, KS, OWN>(S, cfc, ne, noe, tsl, tid, nt, 0, nint, S.u0, S.z0, tau, g,
+                                 [&](int k, int l, R r, R f) {
+                                     S.ua[l] = r;
+                                     S.fl[l] = f;
+                                     if (k < OWN) Fs[k] = mul_r(wAB, f);
+                                 });
+        if (!grid_wait(bar, (unsigned int)(j + 1) * gridDim.x + a.stall)) {
+            ok = false;   // every thread: grid_wait's verdict is the block's
+            break;
         }
-        if (!grid_wait(bar, (unsigned int)(j + 1) * gridDim.x + a.stall)) return;
 #pragma unroll
         for (int k = 0; k < OWN; k++) {
             if (he[k] >= 0) S.u0[noe + tid + k * nt] = __ldcg(xu + he[k]);
@@ -621,6 +810,14 @@ __global__ void __launch_bounds__(NT, 1024 / NT) k_btr_tiled(DTiles<R> t, BtrArg
         buf ^= 1;
         __syncthreads();
     }
+    if constexpr (TM) {
+        // every warp's tensor-memory loads completed (each waited for its own)
+        tmem_fence_before();
+        __syncthreads();
+        tmem_fence_after();
+        if (tid < 32) tmem_dealloc(s_tmem, TM_COLS);
+    }
+    if (!ok) return;
     // ---- outputs for the owned edges and cells: starting state plus increment
 #pragma unroll
     for (int k = 0; k < OWN; k++) {
@@ -634,18 +831,25 @@ __global__ void __launch_bounds__(NT, 1024 / NT) k_btr_tiled(DTiles<R> t, BtrArg
     }
 }
 
-template <class R, int NT> const void *btr_tiled_kernel_ptr_nt(int order, int own) {
+template <class R, int NT, bool TM> const void *btr_tiled_kernel_ptr_nt(int order, int own) {
     if (own == 2)
-        return order == 2 ? (const void *)k_btr_tiled<R, 2, 2, NT>
-                          : (const void *)k_btr_tiled<R, 3, 2, NT>;
-    return order == 2 ? (const void *)k_btr_tiled<R, 2, 3, NT>
-                      : (const void *)k_btr_tiled<R, 3, 3, NT>;
+        return order == 2 ? (const void *)k_btr_tiled<R, 2, 2, NT, TM>
+                          : (const void *)k_btr_tiled<R, 3, 2, NT, TM>;
+    return order == 2 ? (const void *)k_btr_tiled<R, 2, 3, NT, TM>
+                      : (const void *)k_btr_tiled<R, 3, 3, NT, TM>;
 }
-template <class R> const void *btr_tiled_kernel_ptr(int order, int own, int nthreads) {
-    if (nthreads == 512) return btr_tiled_kernel_ptr_nt<R, 512>(order, own);
-    if (nthreads == 1024) return btr_tiled_kernel_ptr_nt<R, 1024>(order, own);
+template <class R> const void *btr_tiled_kernel_ptr(int order, int own, int nthreads, bool tm) {
+    if (tm) {
+        if constexpr (sizeof(R) == 4) {
+            if (nthreads == TM_THREADS) return btr_tiled_kernel_ptr_nt<R, TM_THREADS, true>(order, own);
+        }
+        return nullptr;
+    }
+    if (nthreads == 512) return btr_tiled_kernel_ptr_nt<R, 512, false>(order, own);
+    if (nthreads == 1024) return btr_tiled_kernel_ptr_nt<R, 1024, false>(order, own);
     return nullptr;
 }
+int btr_tiled_tmem_slots() { return TM_SLOTS; }
 
 template <class R>
 cudaError_t launch_btr_tiled(const DTiles<R> &t, const BtrArgs<R> &a, const Barrier &bar,
@@ -664,13 +868,13 @@ cudaError_t launch_btr_tiled(const DTiles<R> &t, const BtrArgs<R> &a, const Barr
     attr[0].val.cooperative = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    const void *fn = btr_tiled_kernel_ptr<R>(a.order, t.own, t.nthreads);
+    const void *fn = btr_tiled_kernel_ptr<R>(a.order, t.own, t.nthreads, t.tm != 0);
     if (!fn) return cudaErrorInvalidConfiguration;
     return cudaLaunchKernelExC(&cfg, fn, args);
 }
 
-template const void *btr_tiled_kernel_ptr<double>(int, int, int);
-template const void *btr_tiled_kernel_ptr<float>(int, int, int);
+template const void *btr_tiled_kernel_ptr<double>(int, int, int, bool);
+template const void *btr_tiled_kernel_ptr<float>(int, int, int, bool);
 template cudaError_t launch_btr_tiled<double>(const DTiles<double> &, const BtrArgs<double> &,
                                               const Barrier &, cudaStream_t);
 template cudaError_t launch_btr_tiled<float>(const DTiles<float> &, const BtrArgs<float> &,

@@ -265,13 +265,18 @@ template <class R> struct DTiles {
     R *xu[2];                        // [Ep] exchange of owned ubar, double-buffered
     R *xz[2];                        // [Cp] exchange of owned zeta
     size_t smem;                     // dynamic shared memory per block
+    int tm;                          // 1: the edges' constant data in tensor memory (FP32,
+                                     // 1024 threads; eoe then not in shared memory)
 };
 template <class R>
 cudaError_t launch_btr_tiled(const DTiles<R> &t, const BtrArgs<R> &a, const Barrier &bar,
                              cudaStream_t s);
 // kernel of the tiled sub-cycle for (order, entries per thread, threads per
-// patch: 512 or 1024); null for another thread count
-template <class R> const void *btr_tiled_kernel_ptr(int order, int own, int nthreads);
+// patch: 512 or 1024, edge data in tensor memory); null for a combination
+// that has no kernel (tensor memory: FP32 and 1024 threads only)
+template <class R> const void *btr_tiled_kernel_ptr(int order, int own, int nthreads, bool tm);
+// edges per thread the tensor-memory variant holds (a patch's edges <= this x 1024)
+int btr_tiled_tmem_slots();
 
 template <class R> struct TransportArgs {
     const R *hR;              // stage thickness [L][Cp] in the tendency precision

@@ -493,7 +493,7 @@ bool build_thick_plan(const HostMesh &hm, int Pc, ThickPlan &plan) {
     return true;
 }
 
-size_t tile_smem_bytes(const TilePlan &plan, int maxE, int maxE2, size_t sR) {
+size_t tile_smem_bytes(const TilePlan &plan, int maxE, int maxE2, size_t sR, bool eoe_smem) {
     (void)maxE;
     (void)maxE2;
     size_t best = 0;
@@ -504,7 +504,7 @@ size_t tile_smem_bytes(const TilePlan &plan, int maxE, int maxE2, size_t sR) {
         b += sR * (3 * nc);                 // z0, za, zh (increments)
         b += sR * (2 * ne + nc);            // starting forcing and ubar, starting depth
         b += 4 * ne;                        // packed local byte offsets of (c1, c2)
-        b += 2 * TILE_NE2P * ne;            // edgesOnEdge byte offsets, padded
+        if (eoe_smem) b += 2 * TILE_NE2P * ne;   // edgesOnEdge byte offsets, padded
         b += 2 * TILE_NCEP * nc;            // edgesOnCell byte offsets, padded
         b += 64 * 16;                       // alignment slack
         best = std::max(best, b);

@@ -69,8 +69,9 @@ bool build_tile_plan(const HostMesh &hm, int P, int K, TilePlan &plan);
 // cells (the TRiSK stencil): the ring counts of a plan, which decide which
 // halo values are exact after each sub-stage, rely on it.
 bool tile_stencil_ok(const HostMesh &hm);
-// Dynamic shared memory of the largest patch for element size sR.
-size_t tile_smem_bytes(const TilePlan &plan, int maxE, int maxE2, size_t sR);
+// Dynamic shared memory of the largest patch for element size sR; without
+// the edgesOnEdge offsets when eoe_smem is false (they live in tensor memory).
+size_t tile_smem_bytes(const TilePlan &plan, int maxE, int maxE2, size_t sR, bool eoe_smem = true);
 
 // Locality order of the cells of a mesh given by the cells of its edges:
 // the parts (about `leaf` cells each) of a recursive bisection of the cell

@@ -53,6 +53,35 @@ def test_barrier_timeout_is_reported_and_the_state_recovers(kernel, monkeypatch)
     ref.close()
 
 
+def test_barrier_timeout_in_the_tensor_memory_subcycle():
+    """The FP32 1024-thread sub-cycle holds its SM's tensor memory: on a
+    barrier timeout every block frees it before returning, so the launches
+    that follow (which allocate it again on the same SMs) run, and the state
+    recovers bit for bit."""
+    m, L, p, (u, h, tr), run = inputs.workload("channel_1km", perturb=True, L=4)
+    dm = binding.Mesh(m, L)
+    st = binding.State(dm, p, "mixed")
+    assert st.subcycle_shape() == (1024, True)
+    st.load_state(u, h, tr)
+    st.inject_barrier_stall(True)
+    with pytest.raises(binding.SSEError) as e:
+        st.step(run["order"], run["dt"], run["M"], 1)
+        st.read_state()
+    assert e.value.code == SYNC_TIMEOUT
+    st.inject_barrier_stall(False)
+    st.load_state(u, h, tr)
+    st.step(run["order"], run["dt"], run["M"], 2)
+    got = st.read_state()
+    ref = binding.State(dm, p, "mixed")
+    ref.load_state(u, h, tr)
+    ref.step(run["order"], run["dt"], run["M"], 2)
+    for a, b in zip(got, ref.read_state()):
+        assert np.array_equal(a, b)
+    st.close()
+    ref.close()
+    dm.close()
+
+
 def test_inject_rejects_unknown_hooks():
     m, L, p, _, _ = inputs.workload("channel_10km")
     st = binding.State(binding.Mesh(m, L), p, "mixed")

@@ -209,6 +209,39 @@ def test_tiled_subcycle_matches_global_kernel(precision, order, monkeypatch):
         assert rel(a, b) < tol
 
 
+@pytest.mark.parametrize("order", [3, 2])
+def test_tiled_subcycle_tensor_memory_keeps_the_bits(order, monkeypatch):
+    """The FP32 tiled sub-cycle with each thread's edge coefficients and
+    edgesOnEdge offsets held in tensor memory (the 1024-thread patches of the
+    92,480-cell channel) against the same sub-cycle streaming them from L2
+    (SSE_BTR_TMEM=0): the same arithmetic on the same values, so the same
+    bits, for the sub-cycle alone and for whole steps."""
+    m, L, p, (u, h, tr), run = inputs.workload("channel_1km", perturb=True, L=4)
+    rng = np.random.default_rng(5)
+    ubar = 0.05 * rng.standard_normal(m.nEdges)
+    G = 1e-6 * rng.standard_normal(m.nEdges)
+    out = {}
+    for tmem in (True, False):
+        if tmem:
+            monkeypatch.delenv("SSE_BTR_TMEM", raising=False)
+        else:
+            monkeypatch.setenv("SSE_BTR_TMEM", "0")
+        dm, st = _gpu(m, L, p, u, h, tr, "mixed")
+        assert st.subcycle_shape() == (1024, tmem)
+        st.set("ubar", ubar)
+        st.set("G", G)
+        st.barotropic_substep(order, run["dt"], run["M"])
+        res = [st.get("ubar"), st.get("Fzeta"), st.get("zeta_sub")]
+        st.load_state(u, h, tr)
+        st.step(order, run["dt"], run["M"], 2)
+        res += list(st.read_state())
+        out[tmem] = res
+        st.close()
+        dm.close()
+    for a, b in zip(out[True], out[False]):
+        assert np.array_equal(a, b)
+
+
 @pytest.mark.parametrize("order", [2, 3])
 def test_full_step_sphere(order):
     """Icosahedral sphere at level 4 with ~30 % land, bathymetry 100-5000 m,
