@@ -35,6 +35,7 @@ import argparse
 import json
 import os
 import platform
+import re
 import subprocess
 import tempfile
 import sys
@@ -132,13 +133,34 @@ KERNEL_SOURCES = ("paper_2105_13484_gb300/csrc/btr_kernel.cu",
                   "paper_2105_13484_gb300/csrc/sse_internal.cuh")
 
 
+_CXX_TOKENS = re.compile(r'//[^\n]*|/\*.*?\*/|"(?:\\.|[^"\\\n])*"|\'(?:\\.|[^\'\\\n])*\'',
+                         re.S)
+
+
+def code_of(text):
+    """A C++/CUDA source without its comments (string and character literals
+    kept) and with every run of blank space made one space: what compiles,
+    so that a comment-only edit keeps the hash of the kernels an ncu capture
+    was taken from."""
+    text = _CXX_TOKENS.sub(lambda m: " " if m.group(0)[0] == "/" else m.group(0), text)
+    return " ".join(text.split())
+
+
 def source_hashes():
+    """sha256 (16 hex digits) of the code of each kernel source."""
     import hashlib
     out = {}
     for rel in KERNEL_SOURCES:
-        with open(os.path.join(ROOT, rel), "rb") as f:
-            out[os.path.basename(rel)] = hashlib.sha256(f.read()).hexdigest()[:16]
+        with open(os.path.join(ROOT, rel), encoding="utf-8") as f:
+            out[os.path.basename(rel)] = hashlib.sha256(code_of(f.read()).encode()).hexdigest()[:16]
     return out
+
+
+def capture_hashes(line, hashes):
+    """Collect a profile summary's '- code sha256 <file>: <hash>' line."""
+    if line.startswith("- code sha256 "):
+        k, v = line[len("- code sha256 "):].strip().split(": ")
+        hashes[k] = v
 
 
 def ncu_traffic(cls, mixed, workload):
@@ -155,9 +177,7 @@ def ncu_traffic(cls, mixed, workload):
         for line in f:
             if line.startswith("| DRAM bytes read + written"):
                 traffic = float(line.split("|")[2].split()[0]) * 1e6
-            if line.startswith("- source sha256 "):
-                k, v = line[len("- source sha256 "):].strip().split(": ")
-                hashes[k] = v
+            capture_hashes(line, hashes)
     if traffic is None or not hashes:
         return None, "capture summary incomplete"
     if hashes != source_hashes():
@@ -500,9 +520,7 @@ def step_traffic(workload, mixed):
         for line in f:
             if line.startswith("| DRAM bytes per step"):
                 traffic = float(line.split("|")[2].split()[0]) * 1e6
-            if line.startswith("- source sha256 "):
-                k, v = line[len("- source sha256 "):].strip().split(": ")
-                hashes[k] = v
+            capture_hashes(line, hashes)
     if traffic is None or not hashes:
         return None, "launch list incomplete"
     if hashes != source_hashes():
@@ -540,9 +558,7 @@ def subcycle_of(prof, m, run, steps, tiled_patches, workload, mixed):
                     l2 = float(line.split("|")[2].split()[0]) * 1e6
                 if line.startswith("| DRAM bytes read + written"):
                     dram = float(line.split("|")[2].split()[0]) * 1e6
-                if line.startswith("- source sha256 "):
-                    k, v = line[len("- source sha256 "):].strip().split(": ")
-                    hashes[k] = v
+                capture_hashes(line, hashes)
         src = f"profiles/{name}"
         if hashes != source_hashes():
             l2 = dram = None
@@ -564,9 +580,7 @@ def fp64_alu_of(m, L, ms_per_step, fp64_tflops, workload):
             for line in f:
                 if line.startswith("| FP64 flops per cell-layer-step"):
                     per_cl = float(line.split("|")[2].split()[0])
-                if line.startswith("- source sha256 "):
-                    k, v = line[len("- source sha256 "):].strip().split(": ")
-                    hashes[k] = v
+                capture_hashes(line, hashes)
         src = "profiles/fp64_ops_per_cell_layer_step.md"
         if hashes != source_hashes():
             per_cl, src = None, "kernel sources changed since the FP64 operation count"

@@ -285,8 +285,9 @@ __global__ void __launch_bounds__(BTR_THREADS) k_btr(DMesh m, BtrArgs<R> a, Barr
 // ---------------------------------------------------------------------------
 // Tiled, communication-avoiding sub-cycle.  One block per patch.  The patch's
 // 2-D state (ubar, zeta and the sub-stage copies), forcing, depths and local
-// connectivity live in shared memory; the TRiSK Coriolis coefficients stream
-// from global memory.  All forward-Euler sub-stages of one sub-step run on
+// connectivity live in shared memory; each edge's TRiSK Coriolis coefficients
+// and edgesOnEdge offsets sit in tensor memory (FP32, 1024-thread patches) or
+// stream from global memory and shared memory.  All forward-Euler sub-stages of one sub-step run on
 // the patch with block-level barriers only (the halo of K >= 3 rings keeps
 // the owned values exact); after each sub-step the owned ubar and zeta go
 // through a double-buffered exchange array and one grid barrier refreshes the
