@@ -317,15 +317,22 @@ template <class T> __device__ __forceinline__ void copy_job_t(T &dst, const T &s
 // single-state and batched kernels run the body on a shared-memory copy of
 // their descriptor, so that the body compiles identically in both (a state's
 // results are the same bits alone or in a batch)
+//
+// Resident CTAs per SM asked of the compiler.  A patch is 128 cells, so the
+// level-7 sphere's 114,689 ocean cells make 925 CTAs: at the 96 registers the
+// FP32 body takes unbounded, 5 CTAs fit an SM (760 on 152 SMs) and the launch
+// runs 1.22 waves, its second a fifth full; at 7 (72 registers) the grid is
+// one wave.  0 leaves the FP64 body's register count to the compiler.
+template <class R> constexpr int thick_min_blocks() { return sizeof(R) == 4 ? 7 : 0; }
 template <class R, int NT>
-__global__ void __launch_bounds__(NT) k_thick_fused(const ThickJob<R> job) {
+__global__ void __launch_bounds__(NT, thick_min_blocks<R>()) k_thick_fused(const ThickJob<R> job) {
     __shared__ ThickJob<R> J;
     copy_job_t(J, job);
     __syncthreads();
     thick_fused_patch<R, NT>(J.m, J.p, J.t, J.a, blockIdx.x);
 }
 template <class R, int NT>
-__global__ void __launch_bounds__(NT) k_thick_fused_batch(const ThickJob<R> *__restrict__ jobs,
+__global__ void __launch_bounds__(NT, thick_min_blocks<R>()) k_thick_fused_batch(const ThickJob<R> *__restrict__ jobs,
                                                           const int *__restrict__ first,
                                                           int njobs) {
     __shared__ ThickJob<R> J;

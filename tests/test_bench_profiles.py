@@ -35,3 +35,45 @@ def test_every_profile_names_each_kernel_source_once():
             bench.capture_hashes(line, hashes)
         assert set(hashes) == names, f
         assert all(re.fullmatch(r"[0-9a-f]{16}", v) for v in hashes.values()), f
+
+
+def test_a_code_edit_voids_only_the_captures_of_the_kernels_built_from_that_source(monkeypatch):
+    names = {os.path.basename(p) for p in bench.KERNEL_SOURCES}
+    for workload, classes in bench.PROFILE_OF.items():
+        for cls in classes:
+            assert set(bench.SOURCES_OF[cls]) <= names
+    real = bench.source_hashes()
+    # pretend the recorded hashes are the current ones, then change one source
+    recorded = {}
+    for cls, name in bench.PROFILE_OF["sphere_l7"].items():
+        with open(os.path.join(bench.ROOT, "profiles", name)) as fh:
+            h = {}
+            for line in fh:
+                bench.capture_hashes(line, h)
+        recorded[cls] = h
+    for edited in names:
+        for cls, h in recorded.items():
+            now = dict(h)
+            now[edited] = "0" * 16
+            monkeypatch.setattr(bench, "source_hashes", lambda now=now: now)
+            traffic, why = bench.ncu_traffic(cls, True, "sphere_l7")
+            if edited in bench.SOURCES_OF[cls]:
+                assert traffic is None and "changed" in why
+            else:
+                assert traffic is not None and traffic > 0, (cls, edited)
+    monkeypatch.setattr(bench, "source_hashes", lambda: real)
+
+
+def test_the_step_launch_list_is_valid_only_while_every_kernel_source_is_unchanged(monkeypatch):
+    with open(os.path.join(bench.ROOT, "profiles", "launches_sphere_l7_mixed.md")) as fh:
+        h = {}
+        for line in fh:
+            bench.capture_hashes(line, h)
+    monkeypatch.setattr(bench, "source_hashes", lambda: dict(h))
+    traffic, src = bench.step_traffic("sphere_l7", True)
+    assert traffic > 0 and src.endswith("launches_sphere_l7_mixed.md")
+    for edited in h:
+        now = dict(h)
+        now[edited] = "0" * 16
+        monkeypatch.setattr(bench, "source_hashes", lambda now=now: now)
+        assert bench.step_traffic("sphere_l7", True)[0] is None
