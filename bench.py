@@ -567,7 +567,8 @@ def subcycle_of(prof, m, run, steps, tiled_patches, workload, mixed):
                     dram = float(line.split("|")[2].split()[0]) * 1e6
                 capture_hashes(line, hashes)
         src = f"profiles/{name}"
-        if hashes != source_hashes():
+        now = source_hashes()
+        if any(hashes.get(f) != now.get(f) for f in SOURCES_OF["btr"]):
             l2 = dram = None
             src = "kernel sources changed since the ncu capture"
     out.update({"l2_bytes_per_launch": l2, "dram_bytes_per_launch": dram, "traffic_source": src})

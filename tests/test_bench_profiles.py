@@ -77,3 +77,23 @@ def test_the_step_launch_list_is_valid_only_while_every_kernel_source_is_unchang
         now[edited] = "0" * 16
         monkeypatch.setattr(bench, "source_hashes", lambda now=now: now)
         assert bench.step_traffic("sphere_l7", True)[0] is None
+
+
+def test_the_subcycle_traffic_follows_the_subcycle_sources(monkeypatch):
+    class Mesh:
+        nEdges, nCells = 343016, 163842
+    with open(os.path.join(bench.ROOT, "profiles", "btr_tiled_sphere_l7.md")) as fh:
+        h = {}
+        for line in fh:
+            bench.capture_hashes(line, h)
+    run = {"order": 3, "M": 40}
+    for edited in h:
+        now = dict(h)
+        now[edited] = "0" * 16
+        monkeypatch.setattr(bench, "source_hashes", lambda now=now: now)
+        out = bench.subcycle_of({"btr": (3 * 1.7, 3)}, Mesh(), run, 1, 152, "sphere_l7", True)
+        assert out["grid_barriers_per_step"] == 120
+        if edited in bench.SOURCES_OF["btr"]:
+            assert out["l2_bytes_per_launch"] is None
+        else:
+            assert out["l2_bytes_per_launch"] > 0 and out["dram_bytes_per_launch"] > 0
