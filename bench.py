@@ -575,29 +575,54 @@ def subcycle_of(prof, m, run, steps, tiled_patches, workload, mixed):
     return out
 
 
+def oracle_flops(workload):
+    """FP64 operations per cell-layer-step of one large step of the workload as
+    the oracle computes it: the committed summary written by
+    oracle/count_flops.py from the oracle's counting build (a file read here;
+    no oracle code runs in this leg)."""
+    path = os.path.join(ROOT, "profiles", "fp64_flops_oracle.md")
+    if not os.path.exists(path):
+        return None
+    with open(path) as f:
+        for line in f:
+            cells = [c.strip() for c in line.strip().strip("|").split("|")]
+            if len(cells) == 9 and cells[0] == workload:
+                return float(cells[8])
+    return None
+
+
 def fp64_alu_of(m, L, ms_per_step, fp64_tflops, workload):
-    """The FP64 form against its arithmetic bound: FP64 operations per
-    cell-layer-step counted by ncu (dadd + dmul + 2 dfma over every launch of
-    one step, committed summary) x cell-layers / step time, against the FMA
-    rate measured by sse_probe_fma_rate."""
-    path = os.path.join(ROOT, "profiles", "fp64_ops_per_cell_layer_step.md")
-    per_cl, src = None, "no committed FP64 operation count"
-    if os.path.exists(path):
-        hashes = {}
-        with open(path) as f:
-            for line in f:
-                if line.startswith("| FP64 flops per cell-layer-step"):
-                    per_cl = float(line.split("|")[2].split()[0])
-                capture_hashes(line, hashes)
-        src = "profiles/fp64_ops_per_cell_layer_step.md"
-        if hashes != source_hashes():
-            per_cl, src = None, "kernel sources changed since the FP64 operation count"
+    """The FP64 form against its arithmetic bound, the FMA rate measured by
+    sse_probe_fma_rate: the algorithmic FP64 operations of a step (counted in
+    the oracle) x cell-layers / step time; beside it, while its capture
+    matches the kernel sources, the FP64 operations the GPU kernels executed
+    (ncu: dadd + dmul + 2 dfma over every launch of one step of the sphere
+    recipe)."""
+    per_cl = oracle_flops(workload)
+    src = ("profiles/fp64_flops_oracle.md (oracle counting build)" if per_cl is not None
+           else "no oracle operation count for this workload")
     out = {"bound": "alu", "unit": "TFLOP/s", "peak": fp64_tflops,
            "peak_source": "measured FP64 FMA rate (sse_probe_fma_rate)",
            "flops_per_cell_layer_step": per_cl, "flops_source": src}
     if per_cl is not None and fp64_tflops:
         ach = per_cl * m.nCells * L / (ms_per_step / 1e3) / 1e12
         out.update({"achieved": ach, "frac": ach / fp64_tflops})
+    path = os.path.join(ROOT, "profiles", "fp64_ops_per_cell_layer_step.md")
+    ex, ex_src = None, "no committed hardware count of the FP64 kernels for this workload"
+    if workload.startswith("sphere") and os.path.exists(path):
+        hashes = {}
+        with open(path) as f:
+            for line in f:
+                if line.startswith("| FP64 flops per cell-layer-step"):
+                    ex = float(line.split("|")[2].split()[0])
+                capture_hashes(line, hashes)
+        ex_src = "profiles/fp64_ops_per_cell_layer_step.md"
+        if hashes != source_hashes():
+            ex, ex_src = None, "kernel sources changed since the FP64 operation count"
+    out.update({"executed_flops_per_cell_layer_step": ex, "executed_flops_source": ex_src})
+    if ex is not None and fp64_tflops:
+        ach = ex * m.nCells * L / (ms_per_step / 1e3) / 1e12
+        out.update({"executed_achieved": ach, "executed_frac": ach / fp64_tflops})
     return out
 
 

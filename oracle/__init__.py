@@ -21,6 +21,8 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "sse_oracle.c")
 _LIB = os.path.join(_HERE, "libsse_oracle.so")
 _LIB_OMP = os.path.join(_HERE, "libsse_oracle_omp.so")
+_SRC_COUNT = os.path.join(_HERE, "flop_count.cpp")
+_LIB_COUNT = os.path.join(_HERE, "libsse_oracle_count.so")
 
 _dp = ct.POINTER(ct.c_double)
 _ip = ct.POINTER(ct.c_int)
@@ -40,6 +42,19 @@ def build(force: bool = False, openmp: bool = False) -> str:
                                *(["-fopenmp"] if openmp else []), _SRC, "-o", tmp, "-lm"])
         os.replace(tmp, lib)
     return lib
+
+
+def build_counting(force: bool = False) -> str:
+    """Compile the counting build (flop_count.cpp: the oracle's source with
+    every double an operation-counting wrapper), serial, no FMA contraction."""
+    deps = [_SRC, _SRC_COUNT, os.path.join(_HERE, "sse_oracle.h")]
+    if force or not os.path.exists(_LIB_COUNT) or os.path.getmtime(_LIB_COUNT) < max(
+            os.path.getmtime(d) for d in deps):
+        tmp = _LIB_COUNT + f".{os.getpid()}.tmp"
+        subprocess.check_call(["g++", "-O2", "-std=c++17", "-ffp-contract=off", "-shared",
+                               "-fPIC", "-I", _HERE, _SRC_COUNT, "-o", tmp, "-lm"])
+        os.replace(tmp, _LIB_COUNT)
+    return _LIB_COUNT
 
 
 def host_threads() -> int:
@@ -90,13 +105,18 @@ class Oracle:
     """FP64 oracle bound to one mesh, layer count and parameter set."""
 
     def __init__(self, mesh, nLayers: int, params: dict | None = None, rest_frac=None,
-                 max_level=None, rest_thickness=None, threads: int = 1):
+                 max_level=None, rest_thickness=None, threads: int = 1, counting: bool = False):
         """max_level [C] / rest_thickness [C, L]: partial bottom cells (both or
         neither; without them every column has all layers).  threads > 1 runs
-        the OpenMP build of the same source on that many host threads."""
-        self.threads = max(1, int(threads))
-        self.lib = ct.CDLL(build(openmp=self.threads > 1))
+        the OpenMP build of the same source on that many host threads;
+        counting runs the operation-counting build (serial; see flops())."""
+        self.threads = 1 if counting else max(1, int(threads))
+        self.counting = bool(counting)
+        self.lib = ct.CDLL(build_counting() if counting else build(openmp=self.threads > 1))
         self._sig()
+        if counting:
+            self.lib.om_flops_read.restype = ct.c_ulonglong
+            self.lib.om_flops_reset()
         if self.threads > 1:
             self.lib.om_set_threads(self.threads)
         self.L = int(nLayers)
@@ -156,6 +176,16 @@ class Oracle:
         L.om_pv_flux.argtypes = [ct.c_void_p, ct.c_int, _dp, _dp, _dp]
         L.om_sse_step.restype = ct.c_int
         L.om_set_threads.argtypes = [ct.c_int]
+
+    def flops(self, reset: bool = False) -> int:
+        """FP64 operations (+, -, *, /, sqrt) the counting build has executed
+        since the last reset in this process (one counter per library)."""
+        if not self.counting:
+            raise RuntimeError("flops() needs Oracle(..., counting=True)")
+        n = int(self.lib.om_flops_read())
+        if reset:
+            self.lib.om_flops_reset()
+        return n
 
     # ---- helpers -------------------------------------------------------
     @staticmethod
