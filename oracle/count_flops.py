@@ -46,11 +46,31 @@ def count_step(name: str) -> dict:
     t0 = time.perf_counter()
     o.step(run["order"], run["dt"], run["M"], u, h, tr)
     secs = time.perf_counter() - t0
-    n = o.flops()
+    n = o.flops(reset=True)
     cl = int(m.nCells) * int(L)
+    # the three parts of a step, each called alone on the initial state (the
+    # counts do not depend on the values); SSPRK3-SE calls each three times
+    # (SSPRK2-SE twice), the rest of the step is the split, the layer fluxes,
+    # the reconciliation and the stage combinations
+    calls = 3 if run["order"] == 3 else 2
+    ubar, ut = o.split(u, h)
+    zeta = o.ssh(h)
+    o.flops(reset=True)
+    o.baroclinic_feuler(u, ut, zeta, h, tr, run["dt"])
+    n_bcl = o.flops(reset=True)
+    o.barotropic_substep(run["order"], ubar, zeta, 0.0 * ubar, run["dt"], run["M"])
+    n_btr = o.flops(reset=True)
+    o.thickness_tracer_fe(h, tr, u, run["dt"])
+    n_thk = o.flops(reset=True)
+    parts = {"baroclinic stage (Algorithm 1)": n_bcl,
+             f"barotropic sub-cycle (Algorithm {4 if run['order'] == 3 else 3}, M = {run['M']})":
+                 n_btr,
+             "thickness and tracer stage": n_thk}
     return {"workload": name, "cells": int(m.nCells), "edges": int(m.nEdges), "layers": int(L),
             "tracers": int(p.get("nTracers", 1)), "order": run["order"], "M": run["M"],
-            "flops_per_step": n, "flops_per_cell_layer_step": n / cl, "seconds": secs}
+            "flops_per_step": n, "flops_per_cell_layer_step": n / cl, "seconds": secs,
+            "calls": calls, "parts": parts,
+            "rest": n - calls * (n_bcl + n_btr + n_thk), "cell_layers": cl}
 
 
 def main() -> int:
@@ -74,6 +94,16 @@ def main() -> int:
         print(f"| {r['workload']} | {r['cells']} | {r['edges']} | {r['layers']} | "
               f"{r['tracers']} | SSPRK{r['order']}-SE | {r['M']} | {r['flops_per_step']} | "
               f"{r['flops_per_cell_layer_step']:.1f} |")
+    print("\nBy part (each part's function of the oracle called alone; calls per step "
+          "from the scheme):\n")
+    print("| workload / part | calls per step | FP64 flops per call | share of the step |")
+    print("|---|---:|---:|---:|")
+    for r in rows:
+        for part, k in r["parts"].items():
+            print(f"| {r['workload']}: {part} | {r['calls']} | {k} | "
+                  f"{r['calls'] * k / r['flops_per_step']:.3f} |")
+        print(f"| {r['workload']}: split, layer fluxes, reconciliation, combinations | 1 | "
+              f"{r['rest']} | {r['rest'] / r['flops_per_step']:.3f} |")
     print("\nSources the count was taken from (sha256 of each file, 16 hex digits):\n")
     for f, v in source_hashes().items():
         print(f"- oracle sha256 {f}: {v}")

@@ -93,3 +93,10 @@ def test_the_committed_count_is_current_and_reproduces():
     r = cf.count_step("channel_1km")
     assert rows["channel_1km"][0] == r["flops_per_step"]
     assert rows["channel_1km"][1] == pytest.approx(r["flops_per_cell_layer_step"], abs=0.051)
+    # the parts: each row reproduces, and three calls of each part plus the
+    # rest make up the whole step
+    with open(SUMMARY) as f:
+        parts = dict(re.findall(r"^\| channel_1km: (.+?) \| \d+ \| (\d+) \|", f.read(), re.M))
+    assert {k: int(v) for k, v in parts.items()} == dict(
+        r["parts"], **{"split, layer fluxes, reconciliation, combinations": r["rest"]})
+    assert r["rest"] > 0 and 3 * sum(r["parts"].values()) + r["rest"] == r["flops_per_step"]
