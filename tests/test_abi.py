@@ -102,6 +102,16 @@ def test_limits(lib):
     assert lib.sse_mesh_create(ct.byref(desc), ct.byref(out)) == -1
 
 
+@pytest.mark.parametrize("field", ["nCells", "nEdges", "nVertices"])
+def test_empty_mesh_is_an_invalid_argument(lib, field):
+    m = meshgen.planar_hex(6, 8, 1e4)
+    desc, keep = _desc(m, 3)
+    setattr(desc, field, 0)
+    out = ct.c_void_p()
+    assert lib.sse_mesh_create(ct.byref(desc), ct.byref(out)) == -1
+    assert not out.value
+
+
 def test_rest_fractions_must_sum_to_one(lib):
     m = meshgen.planar_hex(6, 8, 1e4)
     desc, keep = _desc(m, 3)
