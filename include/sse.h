@@ -13,7 +13,10 @@
  *     the top layer.  The device layout is the library's own (layer-major,
  *     padded); it is never exposed.
  *   - Every function returns SSE_OK (0) or a negative SSE_ERR_* code and
- *     never throws; sse_strerror() names the code.  After a non-fatal error
+ *     never throws; sse_strerror() names the code.  A host allocation that
+ *     fails inside the library (mesh plans, staging buffers) is SSE_ERR_OOM
+ *     like a device one; any other unexpected host-side failure is
+ *     SSE_ERR_INTERNAL.  After a non-fatal error
  *     (INVALID_ARG, BAD_MESH, NONFINITE) the objects stay valid.  After
  *     SSE_ERR_CUDA or SSE_ERR_SYNC_TIMEOUT the state must be re-set with
  *     sse_state_set before it is stepped again.
@@ -42,6 +45,7 @@ extern "C" {
 #define SSE_ERR_UNSUPPORTED (-7)   /* size beyond a compiled limit              */
 #define SSE_ERR_TIMEOUT (-8)       /* sse_server_wait: the request is not done  */
 #define SSE_ERR_CANCELLED (-9)     /* request dropped when its server stopped   */
+#define SSE_ERR_INTERNAL (-10)     /* unexpected host-side failure in the library */
 
 /* ---- precision of the device arithmetic ---- */
 #define SSE_FP64 0   /* everything in FP64                                       */

@@ -29,6 +29,28 @@ using namespace sse;
 
 namespace {
 
+// No exception crosses the C ABI: the entry points run their bodies through
+// this.  The library's host containers (plans, staging vectors, graph and
+// arena caches) report a failed allocation by throwing std::bad_alloc, which
+// becomes SSE_ERR_OOM; anything else thrown becomes SSE_ERR_INTERNAL.
+template <class F> int guarded(F &&f) noexcept {
+    try {
+        return f();
+    } catch (const std::bad_alloc &) {
+        return SSE_ERR_OOM;
+    } catch (...) {
+        return SSE_ERR_INTERNAL;
+    }
+}
+
+// an NVTX range that closes however its scope is left
+struct NvtxScope {
+    explicit NvtxScope(const char *name) { nvtxRangePushA(name); }
+    ~NvtxScope() { nvtxRangePop(); }
+    NvtxScope(const NvtxScope &) = delete;
+    NvtxScope &operator=(const NvtxScope &) = delete;
+};
+
 constexpr int kAlign = 32;
 inline int pad(int n) { return (n + kAlign - 1) / kAlign * kAlign; }
 
@@ -99,7 +121,7 @@ struct sse_mesh {
 // ---------------------------------------------------------------------------
 // mesh
 // ---------------------------------------------------------------------------
-extern "C" int sse_mesh_create(const sse_mesh_desc *d, sse_mesh **out) {
+static int mesh_create_impl(const sse_mesh_desc *d, sse_mesh **out) {
     if (!d || !out) return SSE_ERR_INVALID_ARG;
     *out = nullptr;
     const int C = d->nCells, E = d->nEdges, V = d->nVertices, mE = d->maxEdges,
@@ -327,7 +349,9 @@ extern "C" int sse_mesh_create(const sse_mesh_desc *d, sse_mesh **out) {
         return std::vector<float>(x.begin(), x.end());
     };
 
-    sse_mesh *m = new (std::nothrow) sse_mesh();
+    // owned here until it is handed out, so that a failure on the way frees it
+    std::unique_ptr<sse_mesh> hold(new (std::nothrow) sse_mesh());
+    sse_mesh *m = hold.get();
     if (!m) return SSE_ERR_OOM;
     {
         HostMesh &hm = m->host;
@@ -414,12 +438,13 @@ extern "C" int sse_mesh_create(const sse_mesh_desc *d, sse_mesh **out) {
         dm.kc = A.upload(kc); dm.ke = A.upload(ke);
         dm.sfc = A.upload(sfc); dm.sfc_f = A.upload(tof(sfc));
     }
-    if (A.failed) {
-        delete m;
-        return SSE_ERR_OOM;
-    }
-    *out = m;
+    if (A.failed) return SSE_ERR_OOM;
+    *out = hold.release();
     return SSE_OK;
+}
+
+extern "C" int sse_mesh_create(const sse_mesh_desc *d, sse_mesh **out) {
+    return guarded([&] { return mesh_create_impl(d, out); });
 }
 
 extern "C" void sse_mesh_destroy(sse_mesh *m) { delete m; }
@@ -1552,7 +1577,8 @@ static int make_state(const sse_mesh *mesh, const sse_params *prm, const sse_tun
     int dev = -1;
     if (cudaGetDevice(&dev) != cudaSuccess) return SSE_ERR_CUDA;
     if (dev != mesh->device) return SSE_ERR_INVALID_ARG;
-    sse_state *st = new (std::nothrow) sse_state();
+    std::unique_ptr<sse_state> hold(new (std::nothrow) sse_state());
+    sse_state *st = hold.get();
     if (!st) return SSE_ERR_OOM;
     st->device = dev;
     const int pc = (tun && tun->patch_cells > 0) ? tun->patch_cells : 0;
@@ -1561,7 +1587,7 @@ static int make_state(const sse_mesh *mesh, const sse_params *prm, const sse_tun
     size_t b = 0;
     if (prm->precision == SSE_FP64) {
         auto *e = new (std::nothrow) Engine<double>();
-        if (!e) { delete st; return SSE_ERR_OOM; }
+        if (!e) return SSE_ERR_OOM;
         st->eng.reset(e);
         e->patch_cells = pc;
         e->bcl_cells = bpc;
@@ -1569,7 +1595,7 @@ static int make_state(const sse_mesh *mesh, const sse_params *prm, const sse_tun
         b = e->A.bytes;
     } else {
         auto *e = new (std::nothrow) Engine<float>();
-        if (!e) { delete st; return SSE_ERR_OOM; }
+        if (!e) return SSE_ERR_OOM;
         st->eng.reset(e);
         e->patch_cells = pc;
         e->bcl_cells = bpc;
@@ -1577,11 +1603,8 @@ static int make_state(const sse_mesh *mesh, const sse_params *prm, const sse_tun
         b = e->A.bytes;
     }
     if (bytes) *bytes = b;
-    if (rc != SSE_OK || count_only) {
-        delete st;
-        return rc;
-    }
-    *out = st;
+    if (rc != SSE_OK || count_only) return rc;
+    *out = hold.release();
     return SSE_OK;
 }
 
@@ -1592,10 +1615,12 @@ extern "C" int sse_state_create(const sse_mesh *mesh, const sse_params *prm, voi
 
 extern "C" int sse_state_create_ex(const sse_mesh *mesh, const sse_params *prm,
                                    const sse_tuning *tuning, void *stream, sse_state **out) {
-    if (!mesh || !prm || !out) return SSE_ERR_INVALID_ARG;
-    *out = nullptr;
-    if (!params_ok(prm) || !tuning_ok(tuning)) return SSE_ERR_INVALID_ARG;
-    return make_state(mesh, prm, tuning, stream, false, out, nullptr);
+    return guarded([&] {
+        if (!mesh || !prm || !out) return SSE_ERR_INVALID_ARG;
+        *out = nullptr;
+        if (!params_ok(prm) || !tuning_ok(tuning)) return SSE_ERR_INVALID_ARG;
+        return make_state(mesh, prm, tuning, stream, false, out, nullptr);
+    });
 }
 
 extern "C" int sse_state_init(const sse_mesh *mesh, const sse_params *prm, const double *u,
@@ -1626,9 +1651,11 @@ extern "C" int sse_state_footprint(const sse_mesh *mesh, const sse_params *prm, 
 
 extern "C" int sse_state_footprint_ex(const sse_mesh *mesh, const sse_params *prm,
                                       const sse_tuning *tuning, size_t *bytes) {
-    if (!mesh || !prm || !bytes) return SSE_ERR_INVALID_ARG;
-    if (!params_ok(prm) || !tuning_ok(tuning)) return SSE_ERR_INVALID_ARG;
-    return make_state(mesh, prm, tuning, nullptr, true, nullptr, bytes);
+    return guarded([&] {
+        if (!mesh || !prm || !bytes) return SSE_ERR_INVALID_ARG;
+        if (!params_ok(prm) || !tuning_ok(tuning)) return SSE_ERR_INVALID_ARG;
+        return make_state(mesh, prm, tuning, nullptr, true, nullptr, bytes);
+    });
 }
 
 extern "C" int sse_mesh_dims(const sse_mesh *mesh, int32_t dims[4]) {
@@ -1670,8 +1697,8 @@ extern "C" int sse_state_subcycle_shape(const sse_state *st, int *threads, int *
 // SM-time (duration x the SMs the patches hold: one per 1024-thread patch,
 // half per 512-thread patch), among those within twice the fastest.  Results
 // are cached per mesh, precision and objective.
-extern "C" int sse_tune(const sse_mesh *mesh, const sse_params *prm, int objective,
-                        sse_tuning *out) {
+static int tune_impl(const sse_mesh *mesh, const sse_params *prm, int objective,
+                     sse_tuning *out) {
     if (!mesh || !prm || !out || (objective != SSE_TUNE_LATENCY &&
                                   objective != SSE_TUNE_THROUGHPUT))
         return SSE_ERR_INVALID_ARG;
@@ -1798,49 +1825,67 @@ extern "C" int sse_tune(const sse_mesh *mesh, const sse_params *prm, int objecti
     return SSE_OK;
 }
 
+extern "C" int sse_tune(const sse_mesh *mesh, const sse_params *prm, int objective,
+                        sse_tuning *out) {
+    return guarded([&] { return tune_impl(mesh, prm, objective, out); });
+}
+
 extern "C" void sse_state_destroy(sse_state *st) { delete st; }
 
 extern "C" int sse_state_set(sse_state *st, int field, const double *host) {
-    if (!st || !host) return SSE_ERR_INVALID_ARG;
-    return st->eng->set(field, host);
+    return guarded([&] {
+        if (!st || !host) return SSE_ERR_INVALID_ARG;
+        return st->eng->set(field, host);
+    });
 }
 
 extern "C" int sse_state_get(sse_state *st, int field, double *host) {
-    if (!st || !host) return SSE_ERR_INVALID_ARG;
-    return st->eng->get(field, host);
+    return guarded([&] {
+        if (!st || !host) return SSE_ERR_INVALID_ARG;
+        return st->eng->get(field, host);
+    });
 }
 
 extern "C" int sse_state_transfer(sse_state *st, int field, void *host, int flags) {
-    if (!st || !host || (flags & ~(SSE_XFER_GET | SSE_XFER_F32 | SSE_XFER_ASYNC)) != 0)
-        return SSE_ERR_INVALID_ARG;
-    return st->eng->transfer(field, host, flags);
+    return guarded([&] {
+        if (!st || !host || (flags & ~(SSE_XFER_GET | SSE_XFER_F32 | SSE_XFER_ASYNC)) != 0)
+            return SSE_ERR_INVALID_ARG;
+        return st->eng->transfer(field, host, flags);
+    });
 }
 
 extern "C" int sse_state_sync(sse_state *st) {
-    if (!st) return SSE_ERR_INVALID_ARG;
-    return st->eng->sync();
+    return guarded([&] {
+        if (!st) return SSE_ERR_INVALID_ARG;
+        return st->eng->sync();
+    });
 }
 
 extern "C" int sse_state_set_f32(sse_state *st, int field, const float *host) {
-    if (!st || !host) return SSE_ERR_INVALID_ARG;
-    return st->eng->set_f32(field, host);
+    return guarded([&] {
+        if (!st || !host) return SSE_ERR_INVALID_ARG;
+        return st->eng->set_f32(field, host);
+    });
 }
 
 extern "C" int sse_state_get_f32(sse_state *st, int field, float *host) {
-    if (!st || !host) return SSE_ERR_INVALID_ARG;
-    return st->eng->get_f32(field, host);
+    return guarded([&] {
+        if (!st || !host) return SSE_ERR_INVALID_ARG;
+        return st->eng->get_f32(field, host);
+    });
 }
 
 extern "C" int sse_step(sse_state *st, int order, double dt, int n_substeps, int n_steps) {
-    if (!st || (order != 2 && order != 3) || !(dt > 0) || !isfinite(dt) || n_substeps < 1 ||
-        n_steps < 0)
-        return SSE_ERR_INVALID_ARG;
-    nvtxRangePushA("sse_step");
-    int i = 0, rc = SSE_OK;
-    for (; !rc && i + 2 <= n_steps; i += 2) rc = st->eng->step2(order, dt, n_substeps);
-    for (; !rc && i < n_steps; i++) rc = st->eng->step(order, dt, n_substeps);
-    nvtxRangePop();
-    return rc;
+    return guarded([&] {
+        if (!st || (order != 2 && order != 3) || !(dt > 0) || !isfinite(dt) || n_substeps < 1 ||
+            n_steps < 0)
+            return SSE_ERR_INVALID_ARG;
+        NvtxScope range("sse_step");
+        int i = 0, rc = SSE_OK;
+        for (; !rc && i + 2 <= n_steps; i += 2) rc = st->eng->step2(order, dt, n_substeps);
+        for (; !rc && i < n_steps; i++) rc = st->eng->step(order, dt, n_substeps);
+        return rc;
+    });
 }
 
 // ---------------------------------------------------------------------------
@@ -2057,51 +2102,58 @@ int step_batch_t(std::vector<Engine<R> *> &E, int order, const double *dt, const
 
 extern "C" int sse_step_batch(sse_state *const *states, int n, int order, const double *dt,
                               const int32_t *n_substeps, int n_steps, void *cuda_stream) {
-    if (!states || n < 1 || !dt || !n_substeps || (order != 2 && order != 3) || n_steps < 0)
-        return SSE_ERR_INVALID_ARG;
-    for (int i = 0; i < n; i++) {
-        if (!states[i] || !(dt[i] > 0) || !isfinite(dt[i]) || n_substeps[i] < 1)
+    return guarded([&] {
+        if (!states || n < 1 || !dt || !n_substeps || (order != 2 && order != 3) || n_steps < 0)
             return SSE_ERR_INVALID_ARG;
-        for (int j = 0; j < i; j++)
-            if (states[j] == states[i]) return SSE_ERR_INVALID_ARG;
-    }
-    if (n_steps == 0) return SSE_OK;
-    nvtxRangePushA("sse_step_batch");
-    int rc = SSE_ERR_UNSUPPORTED;
-    auto run = [&](auto *proto) {
-        using Eng = std::remove_pointer_t<decltype(proto)>;
-        std::vector<Eng *> E;
         for (int i = 0; i < n; i++) {
-            Eng *e = dynamic_cast<Eng *>(states[i]->eng.get());
-            if (!e || !e->fused || !e->fused_th || e->prof || e->inject_stall) return SSE_ERR_UNSUPPORTED;
-            E.push_back(e);
+            if (!states[i] || !(dt[i] > 0) || !isfinite(dt[i]) || n_substeps[i] < 1)
+                return SSE_ERR_INVALID_ARG;
+            for (int j = 0; j < i; j++)
+                if (states[j] == states[i]) return SSE_ERR_INVALID_ARG;
         }
-        for (int i = 1; i < n; i++)
-            if (states[i]->device != states[0]->device) return SSE_ERR_INVALID_ARG;
-        return step_batch_t(E, order, dt, n_substeps, n_steps, (cudaStream_t)cuda_stream);
-    };
-    if (dynamic_cast<Engine<float> *>(states[0]->eng.get()))
-        rc = run((Engine<float> *)nullptr);
-    else if (dynamic_cast<Engine<double> *>(states[0]->eng.get()))
-        rc = run((Engine<double> *)nullptr);
-    nvtxRangePop();
-    return rc;
+        if (n_steps == 0) return SSE_OK;
+        NvtxScope range("sse_step_batch");
+        int rc = SSE_ERR_UNSUPPORTED;
+        auto run = [&](auto *proto) {
+            using Eng = std::remove_pointer_t<decltype(proto)>;
+            std::vector<Eng *> E;
+            for (int i = 0; i < n; i++) {
+                Eng *e = dynamic_cast<Eng *>(states[i]->eng.get());
+                if (!e || !e->fused || !e->fused_th || e->prof || e->inject_stall) return SSE_ERR_UNSUPPORTED;
+                E.push_back(e);
+            }
+            for (int i = 1; i < n; i++)
+                if (states[i]->device != states[0]->device) return SSE_ERR_INVALID_ARG;
+            return step_batch_t(E, order, dt, n_substeps, n_steps, (cudaStream_t)cuda_stream);
+        };
+        if (dynamic_cast<Engine<float> *>(states[0]->eng.get()))
+            rc = run((Engine<float> *)nullptr);
+        else if (dynamic_cast<Engine<double> *>(states[0]->eng.get()))
+            rc = run((Engine<double> *)nullptr);
+        return rc;
+    });
 }
 
 extern "C" int sse_baroclinic_feuler(sse_state *st, double dt) {
-    if (!st || !(dt > 0) || !isfinite(dt)) return SSE_ERR_INVALID_ARG;
-    return st->eng->bcl_feuler(dt);
+    return guarded([&] {
+        if (!st || !(dt > 0) || !isfinite(dt)) return SSE_ERR_INVALID_ARG;
+        return st->eng->bcl_feuler(dt);
+    });
 }
 
 extern "C" int sse_barotropic_substep(sse_state *st, int order, double dt, int n_substeps) {
-    if (!st || (order != 2 && order != 3) || !(dt > 0) || !isfinite(dt) || n_substeps < 1)
-        return SSE_ERR_INVALID_ARG;
-    return st->eng->btr_substep(order, dt, n_substeps);
+    return guarded([&] {
+        if (!st || (order != 2 && order != 3) || !(dt > 0) || !isfinite(dt) || n_substeps < 1)
+            return SSE_ERR_INVALID_ARG;
+        return st->eng->btr_substep(order, dt, n_substeps);
+    });
 }
 
 extern "C" int sse_diagnostics(sse_state *st, sse_diag *out) {
-    if (!st || !out) return SSE_ERR_INVALID_ARG;
-    return st->eng->diagnostics(out);
+    return guarded([&] {
+        if (!st || !out) return SSE_ERR_INVALID_ARG;
+        return st->eng->diagnostics(out);
+    });
 }
 
 extern "C" int sse_kernels_per_step(const sse_state *st, int order) {
@@ -2120,8 +2172,10 @@ extern "C" int sse_profile(sse_state *st, int enable) {
 }
 
 extern "C" int sse_profile_read(sse_state *st, double *ms, int32_t *launches) {
-    if (!st || !ms || !launches) return SSE_ERR_INVALID_ARG;
-    return st->eng->prof_read(ms, launches);
+    return guarded([&] {
+        if (!st || !ms || !launches) return SSE_ERR_INVALID_ARG;
+        return st->eng->prof_read(ms, launches);
+    });
 }
 
 extern "C" const char *sse_strerror(int code) {
@@ -2136,6 +2190,7 @@ extern "C" const char *sse_strerror(int code) {
     case SSE_ERR_UNSUPPORTED: return "size beyond a compiled limit";
     case SSE_ERR_TIMEOUT: return "request not finished within the timeout";
     case SSE_ERR_CANCELLED: return "request cancelled when its server stopped";
+    case SSE_ERR_INTERNAL: return "unexpected host-side failure in the library";
     default: return "unknown error";
     }
 }

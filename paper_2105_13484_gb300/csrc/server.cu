@@ -432,11 +432,21 @@ extern "C" int sse_server_submit(sse_server *S, const sse_mesh *mesh, const sse_
             delete r;
             return SSE_ERR_INVALID_ARG;
         }
-        r->id = S->next_id++;
+        // registered in both containers or in neither: a failed insertion
+        // leaves no request that the worker would never see
+        const int64_t id = S->next_id;
+        r->id = id;
         r->t_submit = now_s(S->t0);
-        S->reqs[r->id] = r;
-        S->pending.push_back(r);
-        *id_out = r->id;
+        try {
+            S->reqs[id] = r;
+            S->pending.push_back(r);
+        } catch (...) {
+            S->reqs.erase(id);
+            delete r;
+            return SSE_ERR_OOM;
+        }
+        S->next_id++;
+        *id_out = id;
     }
     S->cv_work.notify_one();
     return SSE_OK;

@@ -35,6 +35,16 @@ def test_every_declared_symbol_is_exported(lib):
 def test_strerror(lib):
     assert lib.sse_strerror(0) == b"ok"
     assert b"mesh" in lib.sse_strerror(-2)
+    # every code the header defines has its own message
+    codes = {}
+    with open(os.path.join(ROOT, "include", "sse.h")) as f:
+        for line in f:
+            mm = re.match(r"#define (SSE_(?:OK|ERR_\w+)) \(?(-?\d+)\)?", line)
+            if mm:
+                codes[mm.group(1)] = int(mm.group(2))
+    assert codes["SSE_ERR_INTERNAL"] == -10 and len(codes) == 11
+    msgs = {lib.sse_strerror(c) for c in codes.values()}
+    assert len(msgs) == len(codes) and b"unknown error" not in msgs
 
 
 def test_null_arguments(lib):
