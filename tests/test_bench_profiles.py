@@ -114,3 +114,33 @@ def test_fp64_alu_roofline_uses_the_oracle_count():
     assert bench.oracle_flops("channel_1km") > 0
     # a variant of the workload (another level, partial bottom) has no count of its own
     assert "frac" not in bench.fp64_alu_of(Mesh(), 60, 47.0, 1.06, "sphere_l7 (variant)")
+
+
+def test_step_bytes_agree_with_the_fused_stage_launches():
+    """The step's algorithmic bytes per cell-layer (each 3-D array read or
+    written once per stage) against the sum of the six fused stage launches
+    of one SSPRK3-SE step, on a mesh with E = 3 C exactly and the 2-D terms
+    set aside: equal in the FP64 form; in the mixed form the launches also
+    move the FP32 copy of h, which the step's figure does not count."""
+    assert bench.step_bytes_per_cell_layer(True, 2) == 308.0
+    assert bench.step_bytes_per_cell_layer(False, 2) == 528.0
+    C, L = 1000, 60
+    E = 3 * C
+    for nT in (1, 2):
+        for mixed in (False, True):
+            sR = 4 if mixed else 8
+            total = 0
+            for stage in range(3):
+                old = stage > 0
+                total += bench.fused_stage_bytes("bcl_edge", C, E, L, nT, sR, old, mixed) - (
+                    3 * E * sR + 8 * C)
+                total += bench.fused_stage_bytes("thickness", C, E, L, nT, sR, old, mixed) - (
+                    E * (2 * sR + 8) + 8 * C)
+            step = bench.step_bytes_per_cell_layer(mixed, nT) * C * L
+            if not mixed:
+                assert total == step
+            else:
+                # bcl reads the 4-byte copy instead of the 8-byte h (3 stages:
+                # -4 B each); thickness stages read and write h with its copy
+                # (stage 1: 2 h words, stages 2-3: 3 h words, +4 B each)
+                assert total == step + 4 * C * L * (-3 + 2 + 3 + 3)
