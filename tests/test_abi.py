@@ -122,6 +122,22 @@ def test_empty_mesh_is_an_invalid_argument(lib, field):
     assert not out.value
 
 
+def test_valid_mesh_without_device_memory_fails_cleanly(lib):
+    """A valid mesh passes validation and builds its host plans; where no
+    device memory can be had (this CPU-only machine) the call returns an
+    error code, hands out nothing and frees what it built."""
+    m = meshgen.planar_hex(6, 8, 1e4)
+    desc, keep = _desc(m, 3)
+    out = ct.c_void_p()
+    rc = lib.sse_mesh_create(ct.byref(desc), ct.byref(out))
+    if rc == 0:      # a machine with a GPU: the mesh exists
+        lib.sse_mesh_destroy(out)
+        return
+    assert rc in (-3, -4) and not out.value
+    for _ in range(3):   # repeated failures stay failures, nothing crashes
+        assert lib.sse_mesh_create(ct.byref(desc), ct.byref(out)) == rc and not out.value
+
+
 def test_rest_fractions_must_sum_to_one(lib):
     m = meshgen.planar_hex(6, 8, 1e4)
     desc, keep = _desc(m, 3)
